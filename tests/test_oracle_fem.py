@@ -1,0 +1,261 @@
+"""Pins of the oracle's residual and exact Jacobian (CPU only).
+
+* central finite differences of r(y) against the dual-number Jacobian;
+* the structural zero blocks of the steady Jacobian listed in Sec. 3.1;
+* manufactured-solution convergence rates of each physics on its own:
+  Navier-Stokes (fluid), incompressible Neo-Hookean (solid) and the ALE
+  mesh operator.  Q2 fields converge as h^3 in L2, the P1disc pressure as
+  h^2; a dropped term, a wrong sign or a transposed index breaks the rate.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import sympy as sy
+
+from oracle import fem
+from oracle.fem import GAUSS_W, GAUSS_X, q2_basis
+from oracle.mesh import FLUID, IFACE, SOLID, build_level
+from oracle.solver import direct_solve
+from tests.oracle_cases import CHANNEL_2D, SMALL_3D, UNIT_FLUID, UNIT_SOLID, random_state
+
+
+def _fd_check(prob, lev, seed, ndir=3, h=1e-6):
+    y = random_state(lev, seed)
+    r, J = fem.assemble(prob, lev, y)
+    rng = np.random.default_rng(seed + 100)
+    for _ in range(ndir):
+        v = rng.standard_normal(lev.N)
+        v[lev.N - (lev.N - lev.n_nodes * 2 * lev.dim):] *= 1.0
+        rp = fem.residual_only(prob, lev, y + h * v)
+        rm = fem.residual_only(prob, lev, y - h * v)
+        fd = (rp - rm) / (2 * h)
+        jv = J @ v
+        err = np.linalg.norm(fd - jv) / np.linalg.norm(jv)
+        assert err < 1e-6, err
+    return y, J
+
+
+def test_fd_jacobian_2d():
+    lev = build_level(CHANNEL_2D, 0)
+    y, J = _fd_check(CHANNEL_2D, lev, 1)
+    # a few full columns at interface / solid / fluid / pressure unknowns
+    nd = 4
+    iface = np.nonzero(lev.node_class == IFACE)[0]
+    cols = [iface[3] * nd + 0, iface[3] * nd + 3, np.nonzero(lev.node_class == SOLID)[0][0] * nd + 1,
+            lev.n_nodes * nd + 5]
+    h = 1e-6
+    for c in cols:
+        e = np.zeros(lev.N)
+        e[c] = 1.0
+        fd = (fem.residual_only(CHANNEL_2D, lev, y + h * e) - fem.residual_only(CHANNEL_2D, lev, y - h * e)) / (2 * h)
+        col = J[:, c].toarray().ravel()
+        scale = np.abs(col).max()
+        assert np.abs(fd - col).max() <= 1e-6 * scale
+
+
+def test_fd_jacobian_2d_harmonic_ale():
+    prob = replace(CHANNEL_2D, ale_op=1)
+    _fd_check(prob, build_level(prob, 0), 2, ndir=2)
+
+
+def test_fd_jacobian_3d():
+    _fd_check(SMALL_3D, build_level(SMALL_3D, 0), 3, ndir=2)
+
+
+@pytest.mark.parametrize("prob", [CHANNEL_2D, SMALL_3D], ids=["2d", "3d"])
+def test_steady_zero_blocks(prob):
+    """Sec. 3.1: in the steady case the solid momentum does not depend on u,
+    the solid kinematic rows not on d; the interface kinematic rows take
+    nothing from fluid unknowns; ALE rows depend on d only; solid mass rows
+    on d only.  These entries must be exactly 0.0."""
+    lev = build_level(prob, 0)
+    y = random_state(lev, 4)
+    _, J = fem.assemble(prob, lev, y)
+    J = J.tocsr()
+    n, nd = lev.dim, 2 * lev.dim
+    nn = lev.n_nodes * nd
+    cls = lev.node_class
+    free = ~lev.dir_mask
+    col_node = np.arange(lev.N) // nd
+    col_slot = np.arange(lev.N) % nd
+    is_u_col = (np.arange(lev.N) < nn) & (col_slot >= n)
+    is_d_col = (np.arange(lev.N) < nn) & (col_slot < n)
+    is_p_col = np.arange(lev.N) >= nn
+    fluid_col = (np.arange(lev.N) < nn) & (cls[np.minimum(col_node, lev.n_nodes - 1)] == FLUID)
+    checked = 0
+    for node in range(lev.n_nodes):
+        for s in range(nd):
+            row = node * nd + s
+            if not free[row]:
+                continue
+            a, b = J.indptr[row], J.indptr[row + 1]
+            c = J.indices[a:b]
+            v = J.data[a:b]
+            if cls[node] == SOLID and s < n:          # S rows: no u
+                assert np.all(v[is_u_col[c]] == 0.0)
+            if cls[node] != FLUID and s >= n:          # K rows: no d, no p, no fluid unknowns
+                assert np.all(v[is_d_col[c]] == 0.0)
+                assert np.all(v[is_p_col[c]] == 0.0)
+                assert np.all(v[fluid_col[c]] == 0.0)
+            if cls[node] == FLUID and s < n:           # A rows: d only
+                assert np.all(v[~is_d_col[c]] == 0.0)
+            if cls[node] == IFACE and s < n:           # I rows: no u of pure solid nodes
+                solid_u = is_u_col[c] & (cls[np.minimum(col_node[c], lev.n_nodes - 1)] == SOLID)
+                assert np.all(v[solid_u] == 0.0)
+            checked += 1
+    for e in np.nonzero(lev.elem_solid)[0]:             # V rows: d only
+        for k in range(n + 1):
+            row = nn + e * (n + 1) + k
+            a, b = J.indptr[row], J.indptr[row + 1]
+            assert np.all(J.data[a:b][~is_d_col[J.indices[a:b]]] == 0.0)
+    assert checked > 0
+
+
+# ----------------------------------------------------------------------------
+# manufactured solutions
+# ----------------------------------------------------------------------------
+
+X, Y = sy.symbols("x y")
+
+
+def _lambdify_vec(exprs):
+    fs = [sy.lambdify((X, Y), e, "numpy") for e in exprs]
+
+    def f(xy):
+        out = np.zeros((xy.shape[0], len(fs)))
+        for i, g in enumerate(fs):
+            out[:, i] = np.broadcast_to(g(xy[:, 0], xy[:, 1]), xy.shape[0])
+        return out
+    return f
+
+
+def _l2_errors(lev, y, exact_d, exact_u, exact_p):
+    """L2 errors of d, u (Q2) and p (P1disc, mean-free difference)."""
+    nd, n = 4, 2
+    ed = lev.elem_dofs
+    err = {"d": 0.0, "u": 0.0}
+    pdiff, pw = [], []
+    for qx in range(3):
+        for qy in range(3):
+            xi = (GAUSS_X[qx], GAUSS_X[qy])
+            w = GAUSS_W[qx] * GAUSS_W[qy] * np.prod(lev.elem_h, axis=1) / 4
+            N, _ = q2_basis(2, xi)
+            xq = lev.elem_lo + (np.array(xi)[None, :] + 1) * 0.5 * lev.elem_h
+            ye = y[ed]
+            for key, off, ex in (("d", 0, exact_d), ("u", n, exact_u)):
+                val = np.stack([ye[:, np.arange(9) * nd + off + c] @ N for c in range(n)], axis=1)
+                err[key] += np.sum(w * np.sum((val - ex(xq)) ** 2, axis=1))
+            ph = ye[:, nd * 9:] @ np.array((1.0,) + xi)
+            pdiff.append(ph - exact_p(xq)[:, 0])
+            pw.append(w)
+    pdiff = np.concatenate(pdiff)
+    pw = np.concatenate(pw)
+    mean = np.sum(pdiff * pw) / np.sum(pw)
+    err["p"] = np.sum(pw * (pdiff - mean) ** 2)
+    return {k: np.sqrt(v) for k, v in err.items()}
+
+
+def _newton_direct(prob, lev, y, source, fix_pressure=False, steps=12):
+    for _ in range(steps):
+        r, J = fem.assemble(prob, lev, y, source)
+        if fix_pressure:       # remove the constant-pressure kernel (pure-Dirichlet solid)
+            J = J.tolil()
+            p0 = lev.n_nodes * 4
+            J.rows[p0] = [p0]
+            J.data[p0] = [1.0]
+            J = J.tocsr()
+            r[p0] = 0.0
+        dy = direct_solve(J, -r)
+        y = y + dy
+        if np.linalg.norm(dy) < 1e-11 * max(1.0, np.linalg.norm(y)):
+            break
+    return y
+
+
+def _rates(prob, exact, source, fix_pressure=False, levels=(1, 2, 3)):
+    ed_, eu_, ep_ = exact
+    errs = []
+    for l in levels:
+        lev = build_level(prob, l)
+        nd = 4
+        y = np.zeros(lev.N)
+        xyz = lev.node_xyz
+        dex, uex = ed_(xyz), eu_(xyz)
+        # Dirichlet data from the exact solution
+        lev.dir_val[:] = 0.0
+        for c in range(2):
+            lev.dir_val[np.arange(lev.n_nodes) * nd + c] = dex[:, c]
+            lev.dir_val[np.arange(lev.n_nodes) * nd + 2 + c] = uex[:, c]
+        y[lev.dir_mask] = lev.dir_val[lev.dir_mask]
+        y = _newton_direct(prob, lev, y, source, fix_pressure)
+        errs.append(_l2_errors(lev, y, ed_, eu_, ep_))
+    rates = {}
+    if len(errs) > 1:
+        rates = {k: np.log2(errs[-2][k] / errs[-1][k]) for k in errs[0] if errs[-1][k] > 1e-13}
+    return errs, rates
+
+
+def test_mms_navier_stokes():
+    """Steady Navier-Stokes on a fixed mesh: traction-free outflow at x = 1."""
+    rho, mu = UNIT_FLUID.rho_f, UNIT_FLUID.mu_f
+    psi = (X - 1) ** 3 * sy.sin(sy.pi * Y)
+    u = [sy.diff(psi, Y), -sy.diff(psi, X)]
+    p = (X - 1) * sy.cos(sy.pi * Y) * 3
+    grad = [[sy.diff(u[i], v) for v in (X, Y)] for i in range(2)]
+    f = []
+    for i in range(2):
+        conv = sum(grad[i][j] * u[j] for j in range(2))
+        lap = sum(sy.diff(u[i], v, 2) for v in (X, Y))
+        f.append(sy.simplify(conv - mu / rho * lap + sy.diff(p, (X, Y)[i]) / rho))
+    fm = _lambdify_vec(f)
+    src = lambda xq: (fm(xq), np.zeros(len(xq)), None)
+    ex = (_lambdify_vec([sy.Integer(0), sy.Integer(0)]), _lambdify_vec(u), _lambdify_vec([p]))
+    errs, rates = _rates(UNIT_FLUID, ex, src)
+    assert errs[-1]["d"] < 1e-12
+    assert rates["u"] > 2.7, (errs, rates)
+    assert rates["p"] > 1.8, (errs, rates)
+
+
+def test_mms_neo_hookean_solid():
+    """Incompressible Neo-Hookean (sigma = -p I + 2 C1 B): -div(J sigma F^{-T}) = rho f,
+    J - 1 = g, steady kinematic u = 0."""
+    mu = UNIT_SOLID.mu_s
+    d = [sy.Rational(1, 20) * sy.sin(sy.pi * X) * sy.sin(sy.pi * Y),
+         sy.Rational(1, 10) * X * Y * (1 - X) * (1 + Y)]
+    p = sy.cos(sy.pi * X) * sy.cos(sy.pi * Y)
+    F = sy.Matrix([[1 + sy.diff(d[0], X), sy.diff(d[0], Y)], [sy.diff(d[1], X), 1 + sy.diff(d[1], Y)]])
+    J = F.det()
+    P = -p * J * F.inv().T + mu * J * F
+    f = [-(sy.diff(P[i, 0], X) + sy.diff(P[i, 1], Y)) / UNIT_SOLID.rho_s for i in range(2)]
+    fm = _lambdify_vec(f)
+    gm = _lambdify_vec([J - 1])
+    src = lambda xq: (fm(xq), gm(xq)[:, 0], None)
+    ex = (_lambdify_vec(d), _lambdify_vec([sy.Integer(0), sy.Integer(0)]), _lambdify_vec([p]))
+    errs, rates = _rates(UNIT_SOLID, ex, src, fix_pressure=True)
+    assert errs[-1]["u"] < 1e-12
+    assert rates["d"] > 2.7, (errs, rates)
+    assert rates["p"] > 1.8, (errs, rates)
+
+
+def test_mms_ale_operator():
+    """Mesh equation -div(k (grad d + grad d^T)) = g, k = 1/V_el, with u = p = 0."""
+    d = [sy.sin(sy.pi * X) * Y * Y * sy.Rational(1, 10), sy.cos(sy.pi * Y) * X * sy.Rational(1, 10)]
+    g = []
+    for i in range(2):
+        s = 0
+        for j, v in enumerate((X, Y)):
+            s += sy.diff(sy.diff(d[i], v) + sy.diff(d[j], (X, Y)[i]), v)
+        g.append(-s)
+    gf = _lambdify_vec(g)
+    ex = (_lambdify_vec(d), _lambdify_vec([sy.Integer(0)] * 2), _lambdify_vec([sy.Integer(0)]))
+    errs = []
+    for l in (1, 2, 3):
+        h = 0.5 / 2 ** l
+        k = 1.0 / (h * h)
+        src = lambda xq, k=k: (np.zeros((len(xq), 2)), np.zeros(len(xq)), k * gf(xq))
+        e, _ = _rates(UNIT_FLUID, ex, src, levels=(l,))
+        errs.append(e[0])
+    rate = np.log2(errs[-2]["d"] / errs[-1]["d"])
+    assert rate > 2.7, errs
+    assert errs[-1]["u"] < 1e-12

@@ -1,0 +1,232 @@
+"""Pins of the oracle's multigrid / Schwarz / Krylov parts (CPU only).
+
+* prolongation reproduces coarse Q2 and P1disc fields exactly, checked by an
+  independent evaluation in physical coordinates (natural injection, Sec. 3.2);
+* restriction = transpose of prolongation except the interface rule of
+  Sec. 3.2, entry by entry;
+* Galerkin coarse operator = rediscretisation on the coarse mesh for the
+  Jacobian at y = 0, where every physics is a constant-coefficient bilinear
+  form integrated exactly (ALE rows scale with k = 1/V_el, i.e. 2^dim);
+* restricted additive Schwarz: one subdomain + omega = 1 converges in one
+  Richardson step; two subdomains match the dense formula of Sec. 3.3;
+* FGMRES: identity preconditioner on a diagonal system converges in at most
+  n steps; with the V-cycle it reproduces the sparse direct solve.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import fem, solver
+from oracle.mesh import FLUID, IFACE, SOLID, Patch, build_level, initial_state
+from paper_1709_05660_gb300.workloads import CONFIGS, SolverOpts, noise
+from tests.oracle_cases import CHANNEL_2D, SMALL_3D, random_state
+
+
+def _lagrange_phys(nodes, x):
+    """1D quadratic Lagrange basis through 3 physical nodes, evaluated at x."""
+    out = []
+    for m in range(3):
+        v = np.ones_like(x)
+        for k in range(3):
+            if k != m:
+                v = v * (x - nodes[k]) / (nodes[m] - nodes[k])
+        out.append(v)
+    return out
+
+
+@pytest.mark.parametrize("prob", [CHANNEL_2D, replace(SMALL_3D, levels=2)], ids=["2d", "3d"])
+def test_prolongation_reproduces_coarse_fields(prob):
+    coarse, fine = build_level(prob, 0), build_level(prob, 1)
+    P = solver.prolongation(coarse, fine)
+    rng = np.random.default_rng(0)
+    vc = rng.standard_normal(coarse.N)
+    vf = P @ vc
+    dim, nd = prob.dim, 2 * prob.dim
+    # nodal fields: evaluate coarse interpolant at every fine node in physical coordinates
+    for f in range(fine.n_nodes):
+        x = fine.node_xyz[f]
+        cell = [min(np.searchsorted(coarse.verts[d], x[d], side="right") - 1, coarse.cells[d] - 1)
+                for d in range(dim)]
+        w1d = []
+        for d in range(dim):
+            nodes = coarse.coords[d][2 * cell[d]: 2 * cell[d] + 3]
+            w1d.append(_lagrange_phys(nodes, np.array(x[d])))
+        for s in range(nd):
+            val = 0.0
+            for a in range(3 ** dim):
+                idx = [(a // 3 ** d) % 3 for d in range(dim)]
+                wgt = np.prod([w1d[d][idx[d]] for d in range(dim)])
+                cn = 0
+                stride = 1
+                for d in range(dim):
+                    cn += (2 * cell[d] + idx[d]) * stride
+                    stride *= coarse.nodes_ax[d]
+                val += wgt * vc[cn * nd + s]
+            assert abs(vf[f * nd + s] - val) <= 1e-13 * (1 + abs(val))
+    # pressures: coarse linear function vs fine linear function at fine-element corners
+    for ef in range(fine.n_elem):
+        lo, h = fine.elem_lo[ef], fine.elem_h[ef]
+        cen = lo + 0.5 * h
+        ec = 0
+        stride = 1
+        clo = np.zeros(dim)
+        ch = np.zeros(dim)
+        for d in range(dim):
+            ci = np.searchsorted(coarse.verts[d], cen[d]) - 1
+            ec += ci * stride
+            stride *= coarse.cells[d]
+            clo[d], ch[d] = coarse.verts[d][ci], coarse.verts[d][ci + 1] - coarse.verts[d][ci]
+        pc = vc[coarse.n_nodes * nd + ec * (dim + 1):][: dim + 1]
+        pf = vf[fine.n_nodes * nd + ef * (dim + 1):][: dim + 1]
+        for corner in range(2 ** dim):
+            xp = lo + np.array([(corner >> d) & 1 for d in range(dim)]) * h
+            xi_c = 2 * (xp - clo) / ch - 1
+            xi_f = 2 * (xp - lo) / h - 1
+            assert abs(pc[0] + pc[1:] @ xi_c - (pf[0] + pf[1:] @ xi_f)) <= 1e-13 * (1 + np.abs(pc).sum())
+
+
+def _kind(lev, dof):
+    nd = 2 * lev.dim
+    node, slot = dof // nd, dof % nd
+    c = lev.node_class[node]
+    if c == FLUID:
+        return "A" if slot < lev.dim else "M"
+    return "M" if slot < lev.dim else "K"
+
+
+def test_restriction_is_transpose_with_interface_rule():
+    coarse, fine = build_level(CHANNEL_2D, 0), build_level(CHANNEL_2D, 1)
+    P0 = solver.prolongation(coarse, fine).tocsr()
+    Pm, R = solver.transfer_operators(coarse, fine)
+    nd, dim = 4, 2
+    nnc, nnf = coarse.n_nodes * nd, fine.n_nodes * nd
+    Rd = R.tocsr()
+    # pressure part and masked P: exact transposes of the injection
+    assert abs(Rd[nnc:, nnf:] - P0[nnf:, nnc:].T).max() == 0
+    keep = sp.diags((~fine.dir_mask).astype(float)) @ P0 @ sp.diags((~coarse.dir_mask).astype(float))
+    assert abs(Pm - keep).max() == 0
+    # node part: R[(C,sc),(f,sf)] = phi_C(f) iff same component and same equation kind
+    S = solver.scalar_node_prolongation(coarse, fine).tocsr()
+    cross = 0
+    for C in range(coarse.n_nodes):
+        for sc in range(nd):
+            row = C * nd + sc
+            a, b = Rd.indptr[row], Rd.indptr[row + 1]
+            got = dict(zip(Rd.indices[a:b], Rd.data[a:b]))
+            want = {}
+            if not coarse.dir_mask[row]:
+                col = S[:, C].tocoo()
+                for f, w in zip(col.row, col.data):
+                    for sf in range(nd):
+                        if sf % dim != sc % dim or fine.dir_mask[f * nd + sf]:
+                            continue
+                        if _kind(coarse, row) == _kind(fine, f * nd + sf):
+                            want[f * nd + sf] = w
+                            if sf != sc:
+                                cross += 1
+            assert got.keys() == want.keys()
+            for k in got:
+                assert got[k] == want[k]
+    assert cross > 0   # interface momentum rows gather fine fluid u-rows
+
+
+@pytest.mark.parametrize("prob", [CHANNEL_2D, replace(SMALL_3D, levels=2)], ids=["2d", "3d"])
+def test_galerkin_equals_rediscretisation_at_zero(prob):
+    coarse, fine = build_level(prob, 0), build_level(prob, 1)
+    Pm, R = solver.transfer_operators(coarse, fine)
+    _, Jf = fem.assemble(prob, fine, np.zeros(fine.N))
+    Jg = solver.galerkin(Jf, Pm, R, coarse).toarray()
+    _, Jc = fem.assemble(prob, coarse, np.zeros(coarse.N))
+    Jc = Jc.toarray()
+    nd = 2 * prob.dim
+    free = ~coarse.dir_mask
+    scale = np.ones(coarse.N)
+    for C in range(coarse.n_nodes):
+        if coarse.node_class[C] == FLUID:
+            scale[C * nd: C * nd + prob.dim] = 2.0 ** prob.dim     # ALE rows: k_fine = 2^dim k_coarse
+    A = Jg[np.ix_(free, free)]
+    B = (scale[:, None] * Jc)[np.ix_(free, free)]
+    assert np.abs(A - B).max() <= 1e-9 * np.abs(B).max()
+    # coarse Dirichlet rows are identity rows, their columns empty
+    d = np.nonzero(coarse.dir_mask)[0]
+    assert np.all(Jg[d][:, d] == np.eye(len(d)))
+    assert np.all(Jg[np.ix_(free, d)] == 0)
+
+
+def _small_system():
+    prob = replace(CHANNEL_2D, levels=1)
+    lev = build_level(prob, 0)
+    y = initial_state(prob, lev, noise(lev.N, 0))
+    r, J = fem.assemble(prob, lev, y)
+    return lev, J.tocsr(), -r
+
+
+def test_ras_one_subdomain_one_step():
+    lev, J, b = _small_system()
+    ops = solver.LevelOps(lev=lev, J=J, patches=[Patch(elems=np.arange(lev.n_elem), dofs=np.arange(lev.N),
+                                                     owned=np.ones(lev.N, dtype=bool), solid=False)])
+    solver.factor_patches(ops)
+    x = np.zeros(lev.N)
+    x = x + 1.0 * solver.ras_apply(ops, b - J @ x)
+    assert np.linalg.norm(b - J @ x) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_ras_matches_dense_formula():
+    lev, J, b = _small_system()
+    from oracle.mesh import build_patches
+    pts = build_patches(lev, (8, 4))
+    assert len(pts) >= 2
+    ops = solver.LevelOps(lev=lev, J=J, patches=pts)
+    solver.factor_patches(ops)
+    Jd = J.toarray()
+    M = np.zeros_like(Jd)
+    for pt in pts:
+        Rd = np.zeros((len(pt.dofs), lev.N))
+        Rd[np.arange(len(pt.dofs)), pt.dofs] = 1.0
+        R0 = Rd * pt.owned[:, None]
+        M += R0.T @ np.linalg.inv(Rd @ Jd @ Rd.T) @ Rd
+    r = np.random.default_rng(1).standard_normal(lev.N)
+    want = M @ r
+    got = solver.ras_apply(ops, r)
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+
+
+def test_fgmres_identity_diagonal():
+    A = sp.diags([1.0, 2.0, 3.0, 4.0, 5.0]).tocsr()
+    b = np.ones(5)
+    x, st = solver.fgmres(A, b, lambda v: v, restart=30, rtol=1e-12)
+    assert st.iters <= 5
+    assert np.allclose(x, 1.0 / np.arange(1, 6), rtol=1e-12)
+
+
+def test_fgmres_vcycle_matches_direct_solve():
+    prob, opts = CONFIGS["c1_2d_l3"]
+    prob = replace(prob, levels=2)
+    orc = solver.Oracle(prob, opts)
+    y = initial_state(prob, orc.fine, noise(orc.fine.N, 0))
+    r, J = orc.assemble(y)
+    orc.factor()
+    x, st = orc.solve(-r, rtol=1e-12)
+    xs = solver.direct_solve(J, -r)
+    assert st.rel_res <= 1e-12
+    assert st.iters < 30
+    assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_newton_converges_quadratically():
+    prob, opts = CONFIGS["c1_2d_l3"]
+    prob = replace(prob, levels=2)
+    orc = solver.Oracle(prob, opts)
+    lev = orc.fine
+    y0 = np.zeros(lev.N)
+    y0[lev.dir_mask] = lev.dir_val[lev.dir_mask]
+    y, hist = orc.newton(y0, tol=1e-8, linear="direct")
+    rels = [h[0] for h in hist]
+    assert rels[-1] < 1e-8 and len(rels) <= 15
+    # quadratic tail of the exact Newton method (exact Jacobian): the last
+    # steps square the relative update up to a modest factor
+    assert rels[-1] < 1e3 * rels[-2] ** 2
+    assert rels[-2] < rels[-3] * 1e-1
