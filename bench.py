@@ -1,0 +1,383 @@
+"""Benchmark: Newton-step solves/s of the 2D channel-with-flap FSI problem.
+
+One step = one whole Newton step through the libfsi C-ABI on resident device
+data: residual + exact Jacobian assembly, Galerkin coarse operators, Schwarz
+block and coarse factorisation, FGMRES(30) with the multigrid V-cycle to
+rtol 1e-10, and the Newton update (fsi_newton_step).  Every step starts from
+the same seeded linearisation state, so every step does the same work.
+
+Default workload: 5 levels (finest 256x64 quads, 313,860 unknowns), shear
+modulus 2e6, mean inflow 1.0, 4x4-element Schwarz blocks, FP64.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+For N > 1 (torchrun) every rank runs an independent replica of the workload
+(the path is not sharded; "scaling": "weak").
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1709_05660_gb300.workloads import CONFIGS, noise  # noqa: E402
+
+METRIC = "Newton-step solves/s (rel. residual 1e-10, FP64 path)"
+UNIT = "solves/s"
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+# FP64 ALU peak derived from the unit counts and clocks: 152 SMs x 2.07 GHz x
+# 4 FP64 flop / clock / SM (the 1.25 TFLOP/s nominal FP64 rate of the part).
+FP64_ALU_PEAK_GFLOPS = 152 * 2.07 * 4.0
+HBM_BOUND = {"patch_apply", "spmv", "transfer", "krylov", "scatter"}
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return None, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+
+class OracleSampler:
+    """Times bounded samples of one Newton step of the CPU oracle, scaled to a
+    full step: assembly of `frac` of the finest elements, the full Galerkin
+    hierarchy, partial-pivot LU of `frac` of every level's Schwarz blocks
+    plus the coarse LU, and one FGMRES iteration (V-cycle, product, CGS2)
+    scaled by `iters` iterations.  The operators the sample needs are built
+    once, untimed, by `__init__`."""
+
+    def __init__(self, cfg: str):
+        from oracle import fem, solver as osolver
+        from oracle.mesh import initial_state
+        self.fem, self.osolver = fem, osolver
+        self.prob, self.opts = CONFIGS[cfg]
+        self.orc = osolver.Oracle(self.prob, self.opts)
+        lev = self.orc.fine
+        self.y = initial_state(self.prob, lev, noise(lev.N, 0))
+        self.r, self.J = self.orc.assemble(self.y)
+        self.orc.factor()
+
+    def sample(self, frac: float, iters: int):
+        import scipy.linalg as sla
+        fem, osolver, orc, prob, opts = self.fem, self.osolver, self.orc, self.prob, self.opts
+        lev = orc.fine
+        rng = np.random.default_rng(0)
+        ne = max(1, int(frac * lev.n_elem))
+        sel = np.sort(rng.choice(lev.n_elem, ne, replace=False))
+        t0 = time.perf_counter()
+        for solid in (True, False):
+            es = sel[lev.elem_solid[sel] == solid]
+            for s0 in range(0, len(es), 2048):
+                fem.element_system(prob, lev, es[s0:s0 + 2048], self.y)
+        t_asm = (time.perf_counter() - t0) / frac
+        t0 = time.perf_counter()
+        Jc = self.J
+        for l in range(prob.levels - 1, 0, -1):
+            P, R = orc._transfers[l - 1]
+            Jc = osolver.galerkin(Jc, P, R, orc.levels_mesh[l - 1])
+        t_gal = time.perf_counter() - t0
+        t_fac = 0.0
+        for l, op in enumerate(orc.ops):
+            if l == 0:
+                t0 = time.perf_counter()
+                sla.lu_factor(op.J.toarray())
+                t_fac += time.perf_counter() - t0
+                continue
+            Jd = op.J.tocsr()
+            npch = len(op.patches)
+            k = max(1, int(frac * npch))
+            t0 = time.perf_counter()
+            for i in range(k):
+                pt = op.patches[i]
+                sla.lu_factor(Jd[pt.dofs][:, pt.dofs].toarray())
+            t_fac += (time.perf_counter() - t0) * npch / k
+        t0 = time.perf_counter()
+        osolver.fgmres(self.J, -self.r, orc.precond, restart=opts.restart, rtol=opts.rtol, max_iters=1)
+        t_it = time.perf_counter() - t0
+        total = t_asm + t_gal + t_fac + iters * t_it
+        detail = {"assemble_s": t_asm, "galerkin_s": t_gal, "factor_s": t_fac, "fgmres_iter_s": t_it,
+                  "iters": iters, "frac": frac}
+        return total, detail
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = args.config
+    iters = args.ref_iters
+    times = []
+    detail = None
+    smp = OracleSampler(cfg)
+    for i in range(args.warmup + args.steps):
+        t, detail = smp.sample(args.ref_frac, iters)
+        if i >= args.warmup:
+            times.append(t)
+    per = statistics.mean(times)
+    val = 1.0 / per
+    prob, opts = CONFIGS[cfg]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg, "levels": prob.levels, "tile": list(opts.tile)},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                         "sample": f"per step: {args.ref_frac:.3f} of the finest-level element assembly and of "
+                                   f"each level's Schwarz block LUs (scaled), full Galerkin hierarchy and coarse LU, "
+                                   f"one FGMRES iteration scaled by {iters} iterations", "detail": detail},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1709_05660_gb300 import fsi
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cfg = args.config
+    prob, opts = CONFIGS[cfg]
+    stream = torch.cuda.current_stream()
+    s = fsi.FSI(prob, opts, stream=stream.cuda_stream)
+    N = int(s.N[-1])
+    nz = torch.tensor(noise(N, 0), dtype=torch.float64, device="cuda")
+    y0 = torch.empty(N, dtype=torch.float64, device="cuda")
+    s.initial_state(nz, y0)
+    dx = torch.empty(N, dtype=torch.float64, device="cuda")
+
+    def step():
+        s.set_state(y0)
+        return s.newton_step(dx)
+
+    for _ in range(args.warmup):
+        rel, st = step()
+    launches0 = s.launch_count()
+    s.set_profiling(True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        rel, st = step()
+        iters.append(st.iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kst = s.kernel_stats()
+    launches = s.launch_count() - launches0
+    s.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # end-to-end through the C-ABI with host buffers (pinned), copies inside the timed region
+    yh = y0.cpu().pin_memory()
+    dxh = torch.empty(N, dtype=torch.float64).pin_memory()
+    yh_np, dxh_np = yh.numpy(), dxh.numpy()
+    s.set_state(yh_np)
+    s.newton_step(dxh_np)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_state(yh_np)
+        s.newton_step(dxh_np)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+           "d2h_bytes_per_step": N * 8}
+
+    # roofline of the dominant kernel class in the timed region
+    peaks, kind = _peaks()
+    dom = max(kst, key=lambda k: kst[k]["ms"])
+    d = kst[dom]
+    per_launch_ms = d["ms"] / max(1, d["launches"])
+    if dom in HBM_BOUND:
+        peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": kind}
+    else:
+        peak = FP64_ALU_PEAK_GFLOPS
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": peak / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": "derived FP64 ALU peak (152 SM x 2.07 GHz x 4 flop/clk)"}
+    roof.update({"kernel": dom, "traffic": _traffic(dom), "launches": d["launches"],
+                 "avg_launch_ms": per_launch_ms})
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
+    classes = {k: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"],
+                   "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None,
+                   "hbm_frac": (v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm_peak) if v["ms"] > 0 else None,
+                   "GFLOPs": (v["flops"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
+               for k, v in kst.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, detail = OracleSampler(cfg).sample(args.cpu_frac, int(round(statistics.mean(iters))))
+        cpu = {"value": 1.0 / est, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+               "sample": f"{args.cpu_frac:.3f} of the finest-level element assembly and of each level's "
+                         f"Schwarz block LUs (scaled), full Galerkin hierarchy and coarse LU, one FGMRES "
+                         f"iteration scaled by the GPU's iteration count", "detail": detail}
+    ws_bytes = s.hbm_bytes
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded channel-with-flap state)",
+            "config": {"workload": cfg, "unknowns": N, "levels": prob.levels, "tile": list(opts.tile),
+                       "mu_s": prob.mu_s, "U": prob.U, "restart": opts.restart, "rtol": opts.rtol,
+                       "smoothing": [opts.n_pre, opts.n_post], "omega": opts.omega,
+                       "l2": f"working set {ws_bytes / 1e9:.2f} GB > L2 (129 MB); no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "fgmres_iters": iters, "rel_step": rel,
+            "phase_ms": {"assemble": st.t_assemble_ms, "factor": st.t_factor_ms, "solve": st.t_solve_ms},
+            "roofline": roof, "kernel_classes": classes, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _traffic(kernel_class: str):
+    """DRAM bytes per launch of the class's kernel from the committed ncu
+    summary, or None when none has been captured for the current kernel."""
+    try:
+        d = json.load(open(_TRAFFIC_FILE))
+        return d.get(kernel_class)
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="c2_2d_l5")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frac", type=float, default=0.25)
+    ap.add_argument("--ref-frac", type=float, default=1.0 / 16)
+    ap.add_argument("--ref-iters", type=int, default=15)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

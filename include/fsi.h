@@ -1,0 +1,218 @@
+/*
+ * libfsi - GB300-native Newton-step solver for monolithic ALE fluid-structure
+ * interaction (Aulisa, Bna, Bornia, arXiv 1709.05660).
+ *
+ * The library computes, for one Newton step of the steady Q2-P1disc FSI
+ * problem, the exact Jacobian J = dr/dy of the discrete residual (Sec. 2.3,
+ * 2.5, 3), the Galerkin coarse operators of the geometric multigrid hierarchy
+ * (Sec. 3.2), the restricted additive Schwarz subdomain inverses of the
+ * Richardson smoother (Sec. 3.3), the coarse direct solve, and the
+ * right-preconditioned FGMRES solve of J dy = -r (Sec. 3, 4.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status: every call returns an int, FSI_OK (0) or a negative FSI_E_* code;
+ *   fsi_last_error(ctx) gives a message for the last failure on that ctx.
+ * - Vectors of unknowns use the canonical numbering of length N (finest level
+ *   unless a level is given): Q2 nodes lexicographic (x fastest), node
+ *   unknown = node*2n + c with c in [d_0..d_{n-1}, u_0..u_{n-1}], then the
+ *   P1disc pressures, element-lexicographic, n+1 per element
+ *   ({1, xi, eta(, zeta)} in reference coordinates).
+ * - Vector arguments may be device pointers (e.g. torch.Tensor.data_ptr()) or
+ *   ordinary host pointers; the library detects which with
+ *   cudaPointerGetAttributes and stages host data through its own buffers.
+ *   The caller owns every buffer it passes; the ctx owns everything else.
+ * - All device work of a ctx runs on the cudaStream_t given at build time.
+ *   Calls return after that work has completed (they synchronise the stream
+ *   whenever a host-side decision or a host output needs it).
+ * - Calls on one ctx are not thread safe; distinct ctxs are independent.
+ * - There is no CPU fallback: without a usable CUDA device every call that
+ *   needs one returns FSI_E_CUDA.
+ */
+#ifndef FSI_H_
+#define FSI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FSI_OK = 0,
+  FSI_E_INVALID = -1,       /* bad argument or descriptor */
+  FSI_E_OOM = -2,           /* device allocation failed */
+  FSI_E_CUDA = -3,          /* CUDA runtime error (no device, launch failure) */
+  FSI_E_SINGULAR = -4,      /* zero / non-finite pivot in a patch or coarse LU */
+  FSI_E_NOT_CONVERGED = -5, /* FGMRES hit max_iters; stats still filled */
+  FSI_E_NONFINITE = -6,     /* NaN / Inf in the state, residual or Krylov data */
+  FSI_E_MESH_TANGLED = -7,  /* det F <= 0 at a quadrature point */
+  FSI_E_TIMEOUT = -8,       /* a bounded device wait gave up */
+  FSI_PENDING = 1           /* serving poll: not finished yet */
+};
+
+enum { FSI_FP64 = 0, FSI_MIXED = 1 };
+enum { FSI_MAX_BREAKS = 65 };
+
+/* Problem descriptor (Sec. 2, 4).  The coarse tensor grid is given by its
+ * cell boundaries per axis; every finer level is one midpoint refinement
+ * (Sec. 3.2).  Elements whose centroid lies inside [flap_lo, flap_hi] are
+ * solid, the rest fluid.  Boundary conditions: d = 0 on the whole outer
+ * boundary; u = inflow profile on x = 0 (1.5 U y(H-y)/(H/2)^2 in 2D, the
+ * product parabola 36 U y(H-y) z(H-z)/H^4 in 3D), u = 0 on the other walls,
+ * stress-free outflow at x = x_max. */
+typedef struct {
+  int dim;                              /* 2 or 3 */
+  int levels;                           /* total levels incl. the coarse one (>= 1) */
+  int n_breaks[3];                      /* number of cell boundaries per axis */
+  double breaks[3][FSI_MAX_BREAKS];     /* coarse cell boundaries, ascending */
+  double flap_lo[3], flap_hi[3];        /* solid box */
+  double rho_f, mu_f, rho_s, mu_s;      /* densities, viscosity, shear modulus (C1 = mu_s/2) */
+  double U;                             /* mean inflow velocity */
+  int transient;                        /* must be 0 (steady); reserved */
+  double dt;                            /* reserved */
+  int ale_op;                           /* 0: k(grad d + grad d^T), k = 1/V_el; 1: k grad d */
+} fsi_problem_desc;
+
+/* Solver options (Sec. 3.3, 4.1). */
+typedef struct {
+  int tile[3];         /* Schwarz block = aligned tile of elements per axis */
+  int n_pre, n_post;   /* Richardson smoothing steps before / after the coarse correction */
+  double omega;        /* Richardson damping */
+  int restart;         /* FGMRES restart length (<= 64) */
+  double rtol;         /* stop when ||b - J x|| <= rtol ||b|| (true residual) */
+  int max_iters;       /* total FGMRES iterations */
+  int precision;       /* FSI_FP64 (FSI_MIXED is reserved) */
+} fsi_solver_opts;
+
+typedef struct {
+  int iters;             /* FGMRES iterations (Arnoldi steps) */
+  int restarts;          /* completed restart cycles */
+  double rel_res;        /* final true ||b - J x|| / ||b|| */
+  double rho;            /* average convergence rate (rel_res)^(1/iters) (Sec. 4.2) */
+  double t_assemble_ms, t_factor_ms, t_solve_ms;  /* device time of the last calls */
+} fsi_solve_stats;
+
+typedef struct fsi_ctx fsi_ctx;
+
+/* Builds the mesh hierarchy, unknown numbering, block-sparse patterns, grid
+ * transfers, Schwarz blocks and all device workspaces (Sec. 2.5, 3.2, 3.3).
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  On success
+ * *out owns all device memory of the instance; free it with fsi_destroy. */
+int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opts,
+                        void* stream, fsi_ctx** out);
+/* Host-only variant: builds the same hierarchy, numbering, patterns,
+ * transfers and Schwarz blocks on the host without touching any GPU.  The
+ * resulting ctx answers fsi_get_sizes and the structural exports
+ * (fsi_export_csr with val = NULL, fsi_export_dofmap, fsi_export_patches,
+ * fsi_export_transfer); compute calls on it return FSI_E_INVALID.  Used to
+ * size an instance before admitting it, and to check the numbering without
+ * a device. */
+int fsi_plan_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opts, fsi_ctx** out);
+void fsi_destroy(fsi_ctx* ctx);
+const char* fsi_last_error(const fsi_ctx* ctx);
+
+/* Sizes: N (canonical unknowns) and scalar nnz of J per level (arrays of
+ * `levels` entries, level 0 = coarse) and the device bytes held by ctx. */
+int fsi_get_sizes(const fsi_ctx* ctx, int64_t* n_per_level, int64_t* nnz_per_level,
+                  int64_t* hbm_bytes);
+
+/* Benchmark linearisation state: d = 0, p = 0, u_x = inflow profile at every
+ * fluid node whose u_x is free (0 at solid and interface nodes), Dirichlet
+ * values at Dirichlet unknowns, then noise[i] added at every free
+ * displacement unknown.  noise and y_out: N doubles (host or device). */
+int fsi_initial_state(fsi_ctx* ctx, const double* noise, double* y_out);
+
+/* Sets the Newton state y (N doubles).  y_prev, y_prev2 and t are reserved
+ * for transient problems and must be NULL / ignored for steady ones. */
+int fsi_set_state(fsi_ctx* ctx, const double* y, const double* y_prev,
+                  const double* y_prev2, double t);
+int fsi_get_state(fsi_ctx* ctx, double* y_out);
+
+/* Residual r(y) and exact Jacobian J(y) on the finest level (element-batched
+ * forward-mode dual numbers, coloured scatter into block-sparse storage),
+ * Dirichlet rows replaced by identity rows with r_i = y_i - g_i, then the
+ * Galerkin operators J_{l-1} = R J_l P of every coarser level (Sec. 3.2).
+ * residual_out (N doubles) may be NULL.  Returns FSI_E_MESH_TANGLED if
+ * det F <= 0 at a quadrature point and FSI_E_NONFINITE on NaN / Inf. */
+int fsi_assemble_jacobian(fsi_ctx* ctx, double* residual_out);
+
+/* Factors every Schwarz block B_k = J_l[R^delta_k, R^delta_k] of the levels
+ * l >= 1 (partial-pivot Gauss-Jordan; only the owned rows of B_k^{-1} are
+ * kept, as the restricted Schwarz update uses nothing else) and the coarse
+ * operator J_0 (Sec. 3.3).  FSI_E_SINGULAR on a zero pivot. */
+int fsi_factor_schwarz(fsi_ctx* ctx);
+
+/* Right-preconditioned FGMRES(restart) on J x = b with the multigrid V-cycle
+ * as preconditioner (Sec. 3, 4.1).  x holds the initial guess on entry and
+ * the solution on exit (N doubles each).  stats may be NULL. */
+int fsi_solve(fsi_ctx* ctx, const double* b, double* x, fsi_solve_stats* stats);
+
+/* Newton update y += dx (Sec. 3.1, 4.1); *rel_step_out = ||dx|| / ||y_new||. */
+int fsi_newton_update(fsi_ctx* ctx, const double* dx, double* rel_step_out);
+
+/* One whole Newton step at the current state: assemble, factor, solve
+ * J dx = -r, update.  dx_out (N doubles, may be NULL) receives dx. */
+int fsi_newton_step(fsi_ctx* ctx, double* dx_out, double* rel_step_out, fsi_solve_stats* stats);
+
+/* ---- parity / diagnostics ------------------------------------------- */
+
+/* J_level in canonical CSR (host buffers): rowptr[N+1], col[nnz], val[nnz];
+ * columns ascending; the pattern is the full FE graph (explicit zeros kept). */
+int fsi_export_csr(fsi_ctx* ctx, int level, int64_t* rowptr, int32_t* col, double* val);
+/* node_class[n_nodes] (0 fluid, 1 solid, 2 interface), elem_solid[n_elem],
+ * dirichlet[N] (0/1), dir_val[N]; any pointer may be NULL; host buffers. */
+int fsi_export_dofmap(fsi_ctx* ctx, int level, uint8_t* node_class, uint8_t* elem_solid,
+                      uint8_t* dirichlet, double* dir_val);
+/* Schwarz blocks of a level >= 1: n_patches (may be NULL); ptr[n_patches+1]
+ * offsets into dofs / owned; dofs ascending canonical unknowns (R^delta_k);
+ * owned[i] = 1 if dofs[i] is in R^0_k.  Pass ptr = NULL to query the total
+ * length through *total_len. */
+int fsi_export_patches(fsi_ctx* ctx, int level, int* n_patches, int64_t* total_len,
+                       int64_t* ptr, int32_t* dofs, uint8_t* owned);
+/* Grid transfer matrices between level and level-1 in canonical CSR (host
+ * buffers): which = 0 prolongation P (N_level rows), which = 1 restriction R
+ * (N_{level-1} rows); rowptr[rows+1], col[nnz], val[nnz], columns ascending.
+ * Pass col = NULL to query *nnz only. */
+int fsi_export_transfer(fsi_ctx* ctx, int level, int which, int64_t* nnz, int64_t* rowptr, int32_t* col,
+                        double* val);
+/* y = J_level x (level's canonical numbering). */
+int fsi_apply_operator(fsi_ctx* ctx, int level, const double* x, double* y);
+/* z = one V-cycle applied to b on the finest level (the preconditioner). */
+int fsi_apply_vcycle(fsi_ctx* ctx, const double* b, double* z);
+/* x_out = x + omega sum_k (R^0_k)^T B_k^{-1} R^delta_k (b - J_level x), one
+ * Richardson-Schwarz step on a level >= 1 (Sec. 3.3). */
+int fsi_apply_smoother(fsi_ctx* ctx, int level, const double* b, const double* x, double* x_out);
+/* Grid transfers between level and level-1: restriction (fine -> coarse) and
+ * prolongation (coarse -> fine), canonical numbering of each level. */
+int fsi_restrict(fsi_ctx* ctx, int level, const double* fine, double* coarse);
+int fsi_prolong(fsi_ctx* ctx, int level, const double* coarse, double* fine);
+/* Number of kernel launches issued by this ctx since it was built. */
+int64_t fsi_launch_count(const fsi_ctx* ctx);
+
+/* Per-kernel-class timing.  With profiling on, every launch of a class is
+ * bracketed by CUDA events on the ctx stream, and its algorithmic traffic
+ * (bytes the operation must move at least once: matrix, index and vector
+ * entries it reads or writes) and arithmetic (flops of the operation's
+ * definition) are accumulated.  fsi_set_profiling(ctx, 1) clears the
+ * counters; fsi_kernel_stats synchronises the stream and reports totals. */
+enum {
+  FSI_K_ASSEMBLE = 0,      /* element residual + Jacobian (dual numbers) */
+  FSI_K_GALERKIN = 1,      /* element-wise Galerkin coarse matrices */
+  FSI_K_SCATTER = 2,       /* coloured scatter of element matrices, Dirichlet rows */
+  FSI_K_PATCH_FACTOR = 3,  /* Schwarz block gather + Gauss-Jordan inversion */
+  FSI_K_COARSE_FACTOR = 4, /* coarse dense gather + cooperative Gauss-Jordan */
+  FSI_K_PATCH_APPLY = 5,   /* restricted Schwarz update (owned inverse rows x residual) */
+  FSI_K_SPMV = 6,          /* block-sparse residual / product */
+  FSI_K_TRANSFER = 7,      /* restriction / prolongation / coarse apply */
+  FSI_K_KRYLOV = 8,        /* dots, Gram-Schmidt updates, norms, combinations */
+  FSI_K_COUNT = 9
+};
+int fsi_set_profiling(fsi_ctx* ctx, int on);
+int fsi_kernel_stats(fsi_ctx* ctx, int kind, double* device_ms, int64_t* launches, double* alg_bytes,
+                     double* alg_flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSI_H_ */

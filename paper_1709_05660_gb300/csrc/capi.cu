@@ -1,0 +1,1035 @@
+// C-ABI of libfsi: context construction, device uploads, and the host-side
+// orchestration of assembly, factorisation, the multigrid V-cycle and FGMRES
+// (Sec. 3, 4.1).  Every arithmetic step runs in the kernels of k_*.cu; the
+// host only sequences launches, reads the few scalars FGMRES needs for its
+// Givens rotations and stopping test, and converts between the canonical
+// numbering and the padded device layout.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "fsi_internal.h"
+#include "kernels.h"
+
+using namespace fsi;
+
+struct fsi_ctx : public Ctx {};
+
+namespace {
+
+struct ApiError : public std::runtime_error {
+  int code;
+  ApiError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw ApiError(e == cudaErrorMemoryAllocation ? FSI_E_OOM : FSI_E_CUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+template <class T>
+T* dalloc(Ctx& c, size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  ck(cudaMalloc(&p, n * sizeof(T)), "cudaMalloc");
+  c.allocs.push_back(p);
+  c.bytes += (int64_t)(n * sizeof(T));
+  return static_cast<T*>(p);
+}
+
+template <class T>
+T* upload(Ctx& c, const std::vector<T>& v) {
+  T* p = dalloc<T>(c, v.size());
+  if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c.stream), "upload");
+  return p;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline void sync(Ctx& c) {
+  ck(cudaStreamSynchronize(c.stream), "stream sync");
+  ck(cudaGetLastError(), "kernel launch");
+}
+
+inline void counted(Ctx& c, int n = 1) { c.launches += n; }
+
+int nblk_red(const Ctx& c) { return c.red_blocks; }
+
+cudaEvent_t get_event(Ctx& c) {
+  if (!c.event_pool.empty()) {
+    cudaEvent_t e = c.event_pool.back();
+    c.event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  ck(cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+
+// Brackets the launches of one kernel class with events (profiling only) and
+// accumulates their algorithmic bytes / flops.
+struct Prof {
+  Ctx& c;
+  int kind;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Prof(Ctx& c_, int k, double bytes, double flops, int launches = 1) : c(c_), kind(k) {
+    if (!c.prof) return;
+    e0 = get_event(c);
+    e1 = get_event(c);
+    cudaEventRecord(e0, c.stream);
+    c.kstat[k].bytes += bytes;
+    c.kstat[k].flops += flops;
+    c.kstat[k].launches += launches;
+  }
+  ~Prof() {
+    if (!e0) return;
+    cudaEventRecord(e1, c.stream);
+    c.kstat[kind].pending.push_back({e0, e1});
+  }
+};
+
+void harvest(Ctx& c) {
+  sync(c);
+  for (auto& ks : c.kstat) {
+    for (auto& pr : ks.pending) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      ks.ms += ms;
+      c.event_pool.push_back(pr.first);
+      c.event_pool.push_back(pr.second);
+    }
+    ks.pending.clear();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// canonical <-> internal vectors
+// ---------------------------------------------------------------------------
+// in (canonical, host or device, length N of level l) -> out (internal, device)
+void to_internal(Ctx& c, int l, const double* in, double* out) {
+  const DevLevel& D = c.dl[l];
+  const double* src = in;
+  if (!is_device_ptr(in)) {
+    ck(cudaMemcpyAsync(c.stage_a, in, D.N * sizeof(double), cudaMemcpyHostToDevice, c.stream), "H2D");
+    src = c.stage_a;
+  }
+  launch_gather(D.Ni, D.canon_of_int, src, out, c.stream);
+  counted(c);
+}
+
+void to_canonical(Ctx& c, int l, const double* in, double* out) {
+  const DevLevel& D = c.dl[l];
+  if (is_device_ptr(out)) {
+    launch_gather(D.N, D.int_of_canon, in, out, c.stream);
+    counted(c);
+  } else {
+    launch_gather(D.N, D.int_of_canon, in, c.stage_b, c.stream);
+    counted(c);
+    ck(cudaMemcpyAsync(out, c.stage_b, D.N * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "D2H");
+  }
+}
+
+double dev_norm(Ctx& c, int64_t n, const double* v, double* slot) {
+  launch_norm_partial(n, v, c.partial, nblk_red(c), c.stream);
+  launch_reduce(c.partial, 1, nblk_red(c), slot, true, c.stream);
+  counted(c, 2);
+  double h = 0.0;
+  ck(cudaMemcpyAsync(c.host_small, slot, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "D2H");
+  sync(c);
+  h = c.host_small[0];
+  return h;
+}
+
+void check_status(Ctx& c) {
+  int32_t st[ST_COUNT];
+  ck(cudaMemcpyAsync(st, c.status, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "D2H status");
+  sync(c);
+  ck(cudaMemsetAsync(c.status, 0, sizeof(st), c.stream), "memset");
+  if (st[ST_TANGLED]) throw ApiError(FSI_E_MESH_TANGLED, "det F <= 0 at a quadrature point");
+  if (st[ST_NONFINITE]) throw ApiError(FSI_E_NONFINITE, "non-finite values");
+  if (st[ST_SINGULAR]) throw ApiError(FSI_E_SINGULAR, "zero or non-finite pivot in a Schwarz block or coarse LU");
+}
+
+// ---------------------------------------------------------------------------
+// build
+// ---------------------------------------------------------------------------
+void build_device(Ctx& c) {
+  const int L = (int)c.hl.size();
+  c.dl.assign(L, DevLevel());
+  const int dim = c.dim, B = c.B, nloc = c.nloc, nd = c.ndofe;
+  int64_t max_dense = 0;
+  for (int l = 0; l < L; ++l) {
+    HostLevel& H = c.hl[l];
+    DevLevel& D = c.dl[l];
+    D.n_nodes = H.n_nodes; D.n_elem = H.n_elem; D.N = H.N; D.nb = H.nb; D.Ni = H.Ni; D.nnzb = H.nnzb;
+    for (int a = 0; a < 3; ++a) D.cells[a] = H.cells[a];
+    D.rowptr = upload(c, H.rowptr);
+    D.col = upload(c, H.col);
+    D.val = dalloc<double>(c, (size_t)H.nnzb * B * B);
+    D.Ke = dalloc<double>(c, (size_t)H.n_elem * nd * nd);
+    D.elem_nodes = upload(c, H.elem_nodes);
+    D.elem_solid = upload(c, H.elem_solid);
+    D.node_class = upload(c, H.node_class);
+    std::vector<double> geo(H.n_elem * 2 * dim);
+    for (int64_t e = 0; e < H.n_elem; ++e) {
+      int idx[3] = {(int)(e % H.cells[0]), (int)((e / H.cells[0]) % H.cells[1]),
+                    (int)(e / ((int64_t)H.cells[0] * H.cells[1]))};
+      for (int a = 0; a < dim; ++a) {
+        geo[e * 2 * dim + a] = H.verts[a][idx[a]];
+        geo[e * 2 * dim + dim + a] = H.verts[a][idx[a] + 1] - H.verts[a][idx[a]];
+      }
+    }
+    D.elem_geo = upload(c, geo);
+    D.dir = upload(c, H.dir);
+    D.dir_val = upload(c, H.dir_val);
+    std::vector<int32_t> dl;
+    for (int64_t i = 0; i < H.Ni; ++i)
+      if (H.dir[i]) dl.push_back((int32_t)i);
+    D.n_dir = (int64_t)dl.size();
+    D.dir_list = upload(c, dl);
+    D.canon_of_int = upload(c, H.canon_of_int);
+    std::vector<int32_t> ioc(H.N, -1);
+    for (int64_t i = 0; i < H.Ni; ++i)
+      if (H.canon_of_int[i] >= 0) ioc[H.canon_of_int[i]] = (int32_t)i;
+    D.int_of_canon = upload(c, ioc);
+    D.elem_map = upload(c, H.elem_map);
+    D.color_list = upload(c, H.color_list);
+    D.color_ptr = H.color_ptr;
+    if (l > 0) {
+      D.P_ptr = upload(c, H.P_ptr); D.P_col = upload(c, H.P_col); D.P_val = upload(c, H.P_val);
+      D.R_ptr = upload(c, H.R_ptr); D.R_col = upload(c, H.R_col); D.R_val = upload(c, H.R_val);
+      D.n_patches = H.n_patches;
+      D.max_n = H.max_n;
+      D.p_n = upload(c, H.p_n); D.p_nown = upload(c, H.p_nown);
+      D.p_idx_off = upload(c, H.p_idx_off); D.p_own_off = upload(c, H.p_own_off);
+      D.p_dense_off = upload(c, H.p_dense_off); D.p_inv_off = upload(c, H.p_inv_off);
+      D.p_gmap_off = upload(c, H.p_gmap_off); D.p_pad_off = upload(c, H.p_pad_off);
+      D.p_idx = upload(c, H.p_idx); D.p_own = upload(c, H.p_own);
+      D.p_gmap = upload(c, H.p_gmap); D.p_padpos = upload(c, H.p_padpos);
+      D.inv_total = H.inv_total;
+      D.dense_total = H.dense_total;
+      D.inv = dalloc<double>(c, (size_t)H.inv_total);
+      max_dense = std::max(max_dense, H.dense_total);
+      for (int p = 0; p < H.n_patches; ++p) {
+        const double n = H.p_n[p], no = H.p_nown[p];
+        D.apply_bytes += no * n * 8.0 + n * 12.0 + no * 20.0;
+        D.apply_flops += 2.0 * no * n;
+        D.factor_flops += 2.0 * n * n * n;
+        D.factor_bytes += n * n * 8.0 + no * n * 8.0;
+      }
+      D.factor_bytes += (double)H.p_gmap.size() / 3.0 * (B * B * 8.0 + 12.0);
+      D.R_bytes = (double)H.R_col.size() * 12.0 + (double)H.Ni * 8.0 + (double)c.hl[l - 1].Ni * 8.0;
+      D.P_bytes = (double)H.P_col.size() * 12.0 + (double)H.Ni * 16.0 + (double)c.hl[l - 1].Ni * 8.0;
+    }
+    D.spmv_bytes = (double)H.nnzb * (B * B * 8.0 + 4.0) + (double)(H.nb + 1) * 4.0 + 3.0 * H.Ni * 8.0;
+    D.spmv_flops = 2.0 * (double)H.nnzb * B * B;
+    D.x = dalloc<double>(c, H.Ni);
+    D.b = dalloc<double>(c, H.Ni);
+    D.r = dalloc<double>(c, H.Ni);
+    ck(cudaMemsetAsync(D.x, 0, H.Ni * sizeof(double), c.stream), "memset");
+    ck(cudaMemsetAsync(D.b, 0, H.Ni * sizeof(double), c.stream), "memset");
+    ck(cudaMemsetAsync(D.r, 0, H.Ni * sizeof(double), c.stream), "memset");
+  }
+  const HostLevel& F = c.hl[L - 1];
+  const int64_t Ni = F.Ni;
+  const int m = c.opts.restart;
+  c.y = dalloc<double>(c, Ni);
+  c.res = dalloc<double>(c, Ni);
+  ck(cudaMemsetAsync(c.y, 0, Ni * sizeof(double), c.stream), "memset");
+  c.V = dalloc<double>(c, (size_t)(m + 1) * Ni);
+  c.Z = dalloc<double>(c, (size_t)m * Ni);
+  c.w = dalloc<double>(c, Ni);
+  c.xk = dalloc<double>(c, Ni);
+  c.bk = dalloc<double>(c, Ni);
+  c.tmp = dalloc<double>(c, Ni);
+  ck(cudaMemsetAsync(c.V, 0, (size_t)(m + 1) * Ni * sizeof(double), c.stream), "memset");
+  c.red_blocks = std::max(1, c.sm_count * 2);
+  c.partial = dalloc<double>(c, (size_t)c.red_blocks * 130);
+  c.small = dalloc<double>(c, 512);
+  ck(cudaMallocHost((void**)&c.host_small, 512 * sizeof(double)), "cudaMallocHost");
+  c.stage_a = dalloc<double>(c, F.N);
+  c.stage_b = dalloc<double>(c, F.N);
+  c.dense_ws_len = std::max<int64_t>(max_dense, 1);
+  c.dense_ws = dalloc<double>(c, (size_t)c.dense_ws_len);
+  // coarse dense operator
+  const int64_t n0 = c.hl[0].Ni;
+  c.c_A = dalloc<double>(c, (size_t)n0 * n0);
+  c.c_B = dalloc<double>(c, (size_t)n0 * n0);
+  c.c_inv = dalloc<double>(c, (size_t)n0 * n0);
+  c.c_piv = dalloc<int32_t>(c, n0);
+  c.status = dalloc<int32_t>(c, ST_COUNT);
+  ck(cudaMemsetAsync(c.status, 0, ST_COUNT * sizeof(int32_t), c.stream), "memset");
+  (void)nloc;
+  ck(cudaEventCreate(&c.ev0), "event");
+  ck(cudaEventCreate(&c.ev1), "event");
+  sync(c);
+}
+
+// coarse pad list (internal indices of padding slots of the level-0 layout)
+std::vector<int32_t> coarse_pads(const Ctx& c) {
+  const HostLevel& H = c.hl[0];
+  std::vector<int32_t> v;
+  for (int64_t i = 0; i < H.Ni; ++i)
+    if (H.canon_of_int[i] < 0) v.push_back((int32_t)i);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// assembly
+// ---------------------------------------------------------------------------
+void assemble(Ctx& c, bool want_res) {
+  const int L = (int)c.dl.size();
+  const int B = c.B;
+  DevLevel& F = c.dl[L - 1];
+  PhysParams pp{c.desc.rho_f, c.desc.mu_f, c.desc.rho_s, c.desc.mu_s, c.desc.ale_op};
+  double* Re = c.tmp_re;
+  const double nd = c.ndofe;
+  ck(cudaMemsetAsync(F.val, 0, (size_t)F.nnzb * B * B * sizeof(double), c.stream), "memset");
+  ck(cudaMemsetAsync(c.res, 0, F.Ni * sizeof(double), c.stream), "memset");
+  const int ngroups = (int)F.color_ptr.size() - 1;
+  {
+    // bytes: element state in, element matrix + residual out
+    Prof pr(c, FSI_K_ASSEMBLE, (double)F.n_elem * (nd * 8.0 + nd * nd * 8.0 + nd * 8.0), 0.0, ngroups);
+    for (int g = 0; g < ngroups; ++g) {
+      const int ne = F.color_ptr[g + 1] - F.color_ptr[g];
+      launch_assemble_2d((g & 1) == 1, F.color_list + F.color_ptr[g], ne, c.y, F.elem_nodes, F.node_class,
+                         F.elem_geo, F.n_nodes, pp, F.Ke, Re, c.status, c.stream);
+      if (ne > 0) counted(c);
+    }
+  }
+  {
+    Prof pr(c, FSI_K_SCATTER, (double)F.n_elem * nd * nd * 8.0 + (double)F.nnzb * B * B * 16.0, 0.0, ngroups + 1);
+    for (int g = 0; g < ngroups; ++g) {
+      const int ne = F.color_ptr[g + 1] - F.color_ptr[g];
+      launch_scatter_2d(F.color_list + F.color_ptr[g], ne, F.Ke, Re, F.elem_nodes, F.elem_map, F.n_nodes, F.val,
+                        c.res, c.stream);
+      if (ne > 0) counted(c);
+    }
+    launch_dirichlet(F.dir_list, F.n_dir, F.rowptr, F.col, F.val, B, c.y, F.dir_val, c.res, c.stream);
+    counted(c);
+  }
+  launch_nonfinite_check(F.Ni, c.res, c.status, c.stream);
+  counted(c);
+  for (int l = L - 1; l >= 1; --l) {
+    DevLevel& Fi = c.dl[l];
+    DevLevel& Co = c.dl[l - 1];
+    {
+      Prof pr(c, FSI_K_GALERKIN, (double)Fi.n_elem * nd * nd * 8.0 + (double)Co.n_elem * nd * nd * 8.0, 0.0);
+      launch_galerkin_2d(Co.cells[0], Co.cells[1], Fi.Ke, Fi.elem_nodes, Fi.node_class, Fi.dir, Co.elem_nodes,
+                         Co.node_class, Co.dir, Co.Ke, c.stream);
+      counted(c);
+    }
+    ck(cudaMemsetAsync(Co.val, 0, (size_t)Co.nnzb * B * B * sizeof(double), c.stream), "memset");
+    const int ng = (int)Co.color_ptr.size() - 1;
+    Prof pr(c, FSI_K_SCATTER, (double)Co.n_elem * nd * nd * 8.0 + (double)Co.nnzb * B * B * 16.0, 0.0, ng + 1);
+    for (int g = 0; g < ng; ++g) {
+      const int ne = Co.color_ptr[g + 1] - Co.color_ptr[g];
+      launch_scatter_2d(Co.color_list + Co.color_ptr[g], ne, Co.Ke, nullptr, Co.elem_nodes, Co.elem_map, Co.n_nodes,
+                        Co.val, nullptr, c.stream);
+      if (ne > 0) counted(c);
+    }
+    launch_dirichlet(Co.dir_list, Co.n_dir, Co.rowptr, Co.col, Co.val, B, nullptr, nullptr, nullptr, c.stream);
+    counted(c);
+  }
+  check_status(c);
+  (void)want_res;
+}
+
+// ---------------------------------------------------------------------------
+// factorisation
+// ---------------------------------------------------------------------------
+void factor(Ctx& c) {
+  const int L = (int)c.dl.size();
+  const int B = c.B;
+  for (int l = 1; l < L; ++l) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_PATCH_FACTOR, D.factor_bytes, D.factor_flops, 2);
+    launch_patch_gather(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off, D.p_padpos, D.val, B,
+                        c.dense_ws, c.stream);
+    launch_patch_gj(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own, D.p_inv_off,
+                    c.dense_ws, D.inv, c.status, c.stream);
+    counted(c, 2);
+  }
+  DevLevel& C = c.dl[0];
+  const int64_t n0 = C.Ni;
+  {
+    const double nn = (double)n0;
+    Prof pr(c, FSI_K_COARSE_FACTOR, nn * nn * 8.0 * 2.0, 2.0 * nn * nn * nn, 4);
+    launch_dense_gather(B, C.nb, C.rowptr, C.col, C.val, c.coarse_pad_list, c.n_coarse_pads, n0, c.c_A, c.stream);
+    counted(c, c.n_coarse_pads > 0 ? 2 : 1);
+    if (launch_coarse_gj(n0, c.c_A, c.c_B, c.c_inv, c.c_piv, c.status, c.sm_count, c.stream) != 0)
+      throw ApiError(FSI_E_CUDA, "cooperative launch of the coarse Gauss-Jordan kernel failed");
+    counted(c, 2);
+  }
+  check_status(c);
+}
+
+// ---------------------------------------------------------------------------
+// multigrid V-cycle (Sec. 3, 3.3): internal vectors of level l
+// ---------------------------------------------------------------------------
+void spmv(Ctx& c, int l, const double* x, const double* b, double* y) {
+  DevLevel& D = c.dl[l];
+  Prof pr(c, FSI_K_SPMV, D.spmv_bytes - (b ? 0.0 : D.Ni * 8.0), D.spmv_flops);
+  launch_bsr_residual(c.B, D.nb, D.rowptr, D.col, D.val, x, b, y, c.stream);
+  counted(c);
+}
+
+void smooth_step(Ctx& c, int l, const double* b, double* x, bool x_is_zero) {
+  DevLevel& D = c.dl[l];
+  const double* r = b;
+  if (!x_is_zero) {
+    spmv(c, l, x, b, D.r);
+    r = D.r;
+  }
+  Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes, D.apply_flops);
+  launch_patch_apply(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off, D.p_own, D.p_inv_off,
+                     D.inv, r, x, c.opts.omega, c.stream);
+  counted(c);
+}
+
+void vcycle(Ctx& c, int l, const double* b, double* x) {
+  if (l == 0) {
+    const double n0 = (double)c.dl[0].Ni;
+    Prof pr(c, FSI_K_TRANSFER, n0 * n0 * 8.0 + 2.0 * n0 * 8.0, 2.0 * n0 * n0);
+    launch_gemv(c.dl[0].Ni, c.c_inv, b, x, c.stream);
+    counted(c);
+    return;
+  }
+  DevLevel& D = c.dl[l];
+  DevLevel& C = c.dl[l - 1];
+  ck(cudaMemsetAsync(x, 0, D.Ni * sizeof(double), c.stream), "memset");
+  for (int s = 0; s < c.opts.n_pre; ++s) smooth_step(c, l, b, x, s == 0);
+  spmv(c, l, x, b, D.r);
+  {
+    Prof pr(c, FSI_K_TRANSFER, D.R_bytes, 2.0 * (double)c.hl[l].R_col.size());
+    launch_csr_spmv(C.Ni, D.R_ptr, D.R_col, D.R_val, D.r, C.b, false, c.stream);
+    counted(c);
+  }
+  vcycle(c, l - 1, C.b, C.x);
+  {
+    Prof pr(c, FSI_K_TRANSFER, D.P_bytes, 2.0 * (double)c.hl[l].P_col.size());
+    launch_csr_spmv(D.Ni, D.P_ptr, D.P_col, D.P_val, C.x, x, true, c.stream);
+    counted(c);
+  }
+  for (int s = 0; s < c.opts.n_post; ++s) smooth_step(c, l, b, x, false);
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES(m), right preconditioned, CGS2, true residual at restart / exit
+// ---------------------------------------------------------------------------
+void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
+  const int L = (int)c.dl.size();
+  DevLevel& F = c.dl[L - 1];
+  const int64_t n = F.Ni;
+  const int m = c.opts.restart;
+  const int nb = nblk_red(c);
+  double* sm = c.small;
+  double* hs = c.host_small;
+  const double bnorm = dev_norm(c, n, b, sm + 300);
+  int iters = 0, restarts = 0;
+  double rel = 0.0;
+  if (!std::isfinite(bnorm)) throw ApiError(FSI_E_NONFINITE, "non-finite right-hand side");
+  if (bnorm == 0.0) {
+    if (st) { st->iters = 0; st->restarts = 0; st->rel_res = 0.0; st->rho = 0.0; }
+    return;
+  }
+  launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, x, b, c.w, c.stream);
+  counted(c);
+  double beta = dev_norm(c, n, c.w, sm + 301);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yv(m);
+  auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  while (true) {
+    if (!std::isfinite(beta)) throw ApiError(FSI_E_NONFINITE, "non-finite residual in FGMRES");
+    if (beta <= c.opts.rtol * bnorm || iters >= c.opts.max_iters) { rel = beta / bnorm; break; }
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    launch_scale_by(n, c.w, sm + 301, c.V, c.stream);
+    counted(c);
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = c.V + (size_t)j * n;
+      double* zj = c.Z + (size_t)j * n;
+      vcycle(c, L - 1, vj, zj);
+      spmv(c, L - 1, zj, nullptr, c.w);
+      Prof pr(c, FSI_K_KRYLOV, (4.0 * (j + 1) + 10.0) * n * 8.0, (8.0 * (j + 1) + 6.0) * n, 11);
+      launch_norm_partial(n, c.w, c.partial, nb, c.stream);
+      launch_reduce(c.partial, 1, nb, sm + 256, true, c.stream);
+      launch_dots(n, c.V, n, j + 1, c.w, c.partial, nb, c.stream);
+      launch_reduce(c.partial, j + 1, nb, sm, false, c.stream);
+      launch_cgs_update(n, c.V, n, j + 1, sm, c.w, c.stream);
+      launch_dots(n, c.V, n, j + 1, c.w, c.partial, nb, c.stream);
+      launch_reduce(c.partial, j + 1, nb, sm + 128, false, c.stream);
+      launch_cgs_update(n, c.V, n, j + 1, sm + 128, c.w, c.stream);
+      launch_norm_partial(n, c.w, c.partial, nb, c.stream);
+      launch_reduce(c.partial, 1, nb, sm + 257, true, c.stream);
+      launch_scale_by(n, c.w, sm + 257, c.V + (size_t)(j + 1) * n, c.stream);
+      counted(c, 11);
+      ck(cudaMemcpyAsync(hs, sm, 260 * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "D2H");
+      sync(c);
+      for (int i = 0; i <= j; ++i) Hc(i, j) = hs[i] + hs[128 + i];
+      const double hn = hs[257], wn0 = hs[256];
+      if (!std::isfinite(hn)) throw ApiError(FSI_E_NONFINITE, "non-finite Krylov vector");
+      Hc(j + 1, j) = hn;
+      const bool breakdown = hn <= 1e-14 * wn0;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+        Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+        Hc(i, j) = t;
+      }
+      const double den = std::hypot(Hc(j, j), Hc(j + 1, j));
+      cs[j] = Hc(j, j) / den;
+      sn[j] = Hc(j + 1, j) / den;
+      Hc(j, j) = den;
+      Hc(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++iters;
+      k = j + 1;
+      if (std::fabs(g[j + 1]) <= c.opts.rtol * bnorm || breakdown || iters >= c.opts.max_iters) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < k; ++q) s -= Hc(i, q) * yv[q];
+      yv[i] = s / Hc(i, i);
+    }
+    std::memcpy(hs + 384, yv.data(), k * sizeof(double));
+    ck(cudaMemcpyAsync(sm + 384, hs + 384, k * sizeof(double), cudaMemcpyHostToDevice, c.stream), "H2D");
+    launch_combo(n, c.Z, n, k, sm + 384, x, c.stream);
+    launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, x, b, c.w, c.stream);
+    counted(c, 2);
+    beta = dev_norm(c, n, c.w, sm + 301);
+    ++restarts;
+    if (beta <= c.opts.rtol * bnorm || iters >= c.opts.max_iters) { rel = beta / bnorm; break; }
+  }
+  if (st) {
+    st->iters = iters;
+    st->restarts = restarts;
+    st->rel_res = rel;
+    st->rho = iters > 0 ? std::pow(rel, 1.0 / iters) : 0.0;
+  }
+  if (!(rel <= c.opts.rtol)) throw ApiError(FSI_E_NOT_CONVERGED, "FGMRES reached max_iters");
+}
+
+float elapsed(Ctx& c) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+  return ms;
+}
+
+template <class F>
+int guard(fsi_ctx* c, F&& f) {
+  if (!c) return FSI_E_INVALID;
+  try {
+    f();
+    return FSI_OK;
+  } catch (const ApiError& e) {
+    c->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return FSI_E_OOM;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return FSI_E_INVALID;
+  }
+}
+
+void need_device(const Ctx& c) {
+  if (c.dl.empty()) throw ApiError(FSI_E_INVALID, "ctx was planned without a device");
+}
+
+int check_level(const Ctx& c, int level, bool need_fine_side) {
+  if (level < 0 || level >= (int)c.hl.size()) throw ApiError(FSI_E_INVALID, "level out of range");
+  if (need_fine_side && level < 1) throw ApiError(FSI_E_INVALID, "level must be >= 1");
+  return level;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts* opts) {
+  if (desc->transient != 0) throw ApiError(FSI_E_INVALID, "only steady problems are supported");
+  if (opts->precision != FSI_FP64) throw ApiError(FSI_E_INVALID, "only FSI_FP64 is supported");
+  if (opts->restart < 1 || opts->restart > 64) throw ApiError(FSI_E_INVALID, "restart must be in [1, 64]");
+  if (opts->n_pre < 0 || opts->n_post < 0 || opts->max_iters < 1 || !(opts->rtol > 0.0))
+    throw ApiError(FSI_E_INVALID, "bad solver options");
+  std::string err;
+  if (!build_host_hierarchy(*desc, *opts, c->hl, err)) throw ApiError(FSI_E_INVALID, err);
+  c->dim = desc->dim;
+  c->B = 2 * desc->dim;
+  c->nloc = desc->dim == 2 ? 9 : 27;
+  c->ndofe = c->B * c->nloc + desc->dim + 1;
+}
+
+int fsi_plan_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opts, fsi_ctx** out) {
+  if (!desc || !opts || !out) return FSI_E_INVALID;
+  *out = nullptr;
+  fsi_ctx* c = new (std::nothrow) fsi_ctx();
+  if (!c) return FSI_E_OOM;
+  c->desc = *desc;
+  c->opts = *opts;
+  int rc = guard(c, [&] { plan(c, desc, opts); });
+  if (rc != FSI_OK) {
+    std::fprintf(stderr, "fsi_plan_hierarchy: %s\n", c->err.c_str());
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return FSI_OK;
+}
+
+int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opts, void* stream, fsi_ctx** out) {
+  if (!desc || !opts || !out) return FSI_E_INVALID;
+  *out = nullptr;
+  fsi_ctx* c = new (std::nothrow) fsi_ctx();
+  if (!c) return FSI_E_OOM;
+  c->desc = *desc;
+  c->opts = *opts;
+  c->stream = static_cast<cudaStream_t>(stream);
+  int rc = guard(c, [&] {
+    if (desc->dim != 2) throw ApiError(FSI_E_INVALID, "the device path supports dim = 2");
+    plan(c, desc, opts);
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    ck(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev), "attr");
+    int coop = 0;
+    ck(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "attr");
+    if (!coop) throw ApiError(FSI_E_CUDA, "device lacks cooperative launch");
+    build_device(*c);
+    c->tmp_re = dalloc<double>(*c, (size_t)c->hl.back().n_elem * c->ndofe);
+    std::vector<int32_t> pads = coarse_pads(*c);
+    c->coarse_pad_list = upload(*c, pads);
+    c->n_coarse_pads = (int)pads.size();
+    sync(*c);
+  });
+  if (rc != FSI_OK) {
+    std::fprintf(stderr, "fsi_build_hierarchy: %s\n", c->err.c_str());
+    fsi_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return FSI_OK;
+}
+
+void fsi_destroy(fsi_ctx* c) {
+  if (!c) return;
+  if (c->dl.empty() && c->allocs.empty()) {   // planned ctx: no CUDA state
+    delete c;
+    return;
+  }
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->host_small) cudaFreeHost(c->host_small);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  for (auto& ks : c->kstat)
+    for (auto& pr : ks.pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete c;
+}
+
+const char* fsi_last_error(const fsi_ctx* c) { return c ? c->err.c_str() : "null ctx"; }
+
+int64_t fsi_launch_count(const fsi_ctx* c) { return c ? c->launches : 0; }
+
+int fsi_get_sizes(const fsi_ctx* c, int64_t* n_per_level, int64_t* nnz_per_level, int64_t* hbm_bytes) {
+  if (!c) return FSI_E_INVALID;
+  for (size_t l = 0; l < c->hl.size(); ++l) {
+    const HostLevel& H = c->hl[l];
+    if (n_per_level) n_per_level[l] = H.N;
+    if (nnz_per_level) {
+      int64_t nnz = 0;
+      const int np = H.dim + 1;
+      for (int64_t br = 0; br < H.nb; ++br) {
+        const int rows = br < H.n_nodes ? H.B : np;
+        for (int32_t k = H.rowptr[br]; k < H.rowptr[br + 1]; ++k) nnz += (int64_t)rows * (H.col[k] < H.n_nodes ? H.B : np);
+      }
+      nnz_per_level[l] = nnz;
+    }
+  }
+  if (hbm_bytes) *hbm_bytes = c->bytes;
+  return FSI_OK;
+}
+
+int fsi_initial_state(fsi_ctx* c, const double* noise, double* y_out) {
+  return guard(c, [&] {
+    need_device(*c);
+    if (!noise || !y_out) throw ApiError(FSI_E_INVALID, "null pointer");
+    const HostLevel& H = c->hl.back();
+    std::vector<double> nz(H.N), y(H.N, 0.0);
+    ck(cudaMemcpy(nz.data(), noise, H.N * sizeof(double), cudaMemcpyDefault), "copy noise");
+    const int dim = H.dim, B = H.B;
+    const double Hy = c->desc.breaks[1][c->desc.n_breaks[1] - 1];
+    const double Hz = dim == 3 ? c->desc.breaks[2][c->desc.n_breaks[2] - 1] : 1.0;
+    for (int64_t n = 0; n < H.n_nodes; ++n) {
+      if (H.node_class[n] != kFluid) continue;
+      const int iy = (int)((n / H.nodes_ax[0]) % H.nodes_ax[1]);
+      const int iz = dim == 3 ? (int)(n / ((int64_t)H.nodes_ax[0] * H.nodes_ax[1])) : 0;
+      const double yy = iy % 2 == 0 ? H.verts[1][iy / 2] : (H.verts[1][iy / 2] + H.verts[1][iy / 2 + 1]) / 2.0;
+      double v;
+      if (dim == 2) {
+        v = 1.5 * c->desc.U * yy * (Hy - yy) / ((Hy / 2.0) * (Hy / 2.0));
+      } else {
+        const double zz = iz % 2 == 0 ? H.verts[2][iz / 2] : (H.verts[2][iz / 2] + H.verts[2][iz / 2 + 1]) / 2.0;
+        v = 36.0 * c->desc.U * yy * (Hy - yy) * zz * (Hz - zz) / (Hy * Hy * Hz * Hz);
+      }
+      y[n * B + dim] = v;
+    }
+    for (int64_t i = 0; i < H.Ni; ++i) {
+      const int32_t cidx = H.canon_of_int[i];
+      if (cidx < 0) continue;
+      if (H.dir[i]) y[cidx] = H.dir_val[i];
+      else if (i < H.n_nodes * B && (i % B) < dim) y[cidx] += nz[cidx];
+    }
+    ck(cudaMemcpy(y_out, y.data(), H.N * sizeof(double), cudaMemcpyDefault), "copy state");
+  });
+}
+
+int fsi_set_state(fsi_ctx* c, const double* y, const double* y_prev, const double* y_prev2, double t) {
+  (void)y_prev; (void)y_prev2; (void)t;
+  return guard(c, [&] {
+    need_device(*c);
+    if (!y) throw ApiError(FSI_E_INVALID, "null state");
+    to_internal(*c, (int)c->dl.size() - 1, y, c->y);
+    sync(*c);
+  });
+}
+
+int fsi_get_state(fsi_ctx* c, double* y_out) {
+  return guard(c, [&] {
+    need_device(*c);
+    if (!y_out) throw ApiError(FSI_E_INVALID, "null pointer");
+    to_canonical(*c, (int)c->dl.size() - 1, c->y, y_out);
+    sync(*c);
+  });
+}
+
+int fsi_assemble_jacobian(fsi_ctx* c, double* residual_out) {
+  return guard(c, [&] {
+    need_device(*c);
+    ck(cudaEventRecord(c->ev0, c->stream), "event");
+    assemble(*c, residual_out != nullptr);
+    ck(cudaEventRecord(c->ev1, c->stream), "event");
+    if (residual_out) to_canonical(*c, (int)c->dl.size() - 1, c->res, residual_out);
+    sync(*c);
+    c->t_assemble = elapsed(*c);
+  });
+}
+
+int fsi_factor_schwarz(fsi_ctx* c) {
+  return guard(c, [&] {
+    need_device(*c);
+    ck(cudaEventRecord(c->ev0, c->stream), "event");
+    factor(*c);
+    ck(cudaEventRecord(c->ev1, c->stream), "event");
+    sync(*c);
+    c->t_factor = elapsed(*c);
+  });
+}
+
+int fsi_solve(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
+  return guard(c, [&] {
+    need_device(*c);
+    if (!b || !x) throw ApiError(FSI_E_INVALID, "null pointer");
+    const int L = (int)c->dl.size();
+    to_internal(*c, L - 1, b, c->bk);
+    to_internal(*c, L - 1, x, c->xk);
+    ck(cudaEventRecord(c->ev0, c->stream), "event");
+    int rc = FSI_OK;
+    std::string msg;
+    try {
+      fgmres(*c, c->bk, c->xk, st);
+    } catch (const ApiError& e) {
+      if (e.code != FSI_E_NOT_CONVERGED) throw;
+      rc = e.code;
+      msg = e.what();
+    }
+    ck(cudaEventRecord(c->ev1, c->stream), "event");
+    to_canonical(*c, L - 1, c->xk, x);
+    sync(*c);
+    c->t_solve = elapsed(*c);
+    if (st) { st->t_assemble_ms = c->t_assemble; st->t_factor_ms = c->t_factor; st->t_solve_ms = c->t_solve; }
+    if (rc != FSI_OK) throw ApiError(rc, msg);
+  });
+}
+
+int fsi_newton_update(fsi_ctx* c, const double* dx, double* rel_step_out) {
+  return guard(c, [&] {
+    need_device(*c);
+    if (!dx) throw ApiError(FSI_E_INVALID, "null pointer");
+    const int L = (int)c->dl.size();
+    const int64_t n = c->dl[L - 1].Ni;
+    to_internal(*c, L - 1, dx, c->tmp);
+    launch_axpby(n, 1.0, c->tmp, 1.0, c->y, c->stream);
+    counted(*c);
+    const double dn = dev_norm(*c, n, c->tmp, c->small + 310);
+    const double yn = dev_norm(*c, n, c->y, c->small + 311);
+    if (!std::isfinite(dn) || !std::isfinite(yn)) throw ApiError(FSI_E_NONFINITE, "non-finite Newton update");
+    if (rel_step_out) *rel_step_out = yn > 0 ? dn / yn : dn;
+  });
+}
+
+int fsi_newton_step(fsi_ctx* c, double* dx_out, double* rel_step_out, fsi_solve_stats* st) {
+  return guard(c, [&] {
+    need_device(*c);
+    const int L = (int)c->dl.size();
+    const int64_t n = c->dl[L - 1].Ni;
+    ck(cudaEventRecord(c->ev0, c->stream), "event");
+    assemble(*c, true);
+    ck(cudaEventRecord(c->ev1, c->stream), "event");
+    sync(*c);
+    c->t_assemble = elapsed(*c);
+    ck(cudaEventRecord(c->ev0, c->stream), "event");
+    factor(*c);
+    ck(cudaEventRecord(c->ev1, c->stream), "event");
+    sync(*c);
+    c->t_factor = elapsed(*c);
+    launch_axpby(n, -1.0, c->res, 0.0, c->bk, c->stream);
+    ck(cudaMemsetAsync(c->xk, 0, n * sizeof(double), c->stream), "memset");
+    counted(*c);
+    ck(cudaEventRecord(c->ev0, c->stream), "event");
+    fgmres(*c, c->bk, c->xk, st);
+    ck(cudaEventRecord(c->ev1, c->stream), "event");
+    sync(*c);
+    c->t_solve = elapsed(*c);
+    launch_axpby(n, 1.0, c->xk, 1.0, c->y, c->stream);
+    counted(*c);
+    const double dn = dev_norm(*c, n, c->xk, c->small + 310);
+    const double yn = dev_norm(*c, n, c->y, c->small + 311);
+    if (rel_step_out) *rel_step_out = yn > 0 ? dn / yn : dn;
+    if (dx_out) to_canonical(*c, L - 1, c->xk, dx_out);
+    sync(*c);
+    if (st) { st->t_assemble_ms = c->t_assemble; st->t_factor_ms = c->t_factor; st->t_solve_ms = c->t_solve; }
+  });
+}
+
+int fsi_export_csr(fsi_ctx* c, int level, int64_t* rowptr, int32_t* col, double* val) {
+  return guard(c, [&] {
+    check_level(*c, level, false);
+    if (!rowptr) throw ApiError(FSI_E_INVALID, "null rowptr");
+    const HostLevel& H = c->hl[level];
+    const int B = H.B, np = H.dim + 1;
+    std::vector<double> v;
+    if (val) {
+      need_device(*c);
+      v.resize((size_t)H.nnzb * B * B);
+      ck(cudaMemcpy(v.data(), c->dl[level].val, v.size() * sizeof(double), cudaMemcpyDeviceToHost), "D2H");
+    }
+    // canonical rows in order: node rows (internal order), then pressure rows
+    int64_t pos = 0;
+    int64_t crow = 0;
+    rowptr[0] = 0;
+    for (int64_t br = 0; br < H.nb; ++br) {
+      const int rows = br < H.n_nodes ? B : np;
+      for (int ci = 0; ci < rows; ++ci) {
+        for (int32_t k = H.rowptr[br]; k < H.rowptr[br + 1]; ++k) {
+          const int64_t bc = H.col[k];
+          const int cols = bc < H.n_nodes ? B : np;
+          for (int cj = 0; cj < cols; ++cj) {
+            if (col) col[pos] = H.canon_of_int[bc * B + cj];
+            if (val) val[pos] = v[(size_t)k * B * B + ci * B + cj];
+            ++pos;
+          }
+        }
+        rowptr[++crow] = pos;
+      }
+    }
+  });
+}
+
+int fsi_export_dofmap(fsi_ctx* c, int level, uint8_t* node_class, uint8_t* elem_solid, uint8_t* dirichlet,
+                      double* dir_val) {
+  return guard(c, [&] {
+    check_level(*c, level, false);
+    const HostLevel& H = c->hl[level];
+    if (node_class) std::memcpy(node_class, H.node_class.data(), H.n_nodes);
+    if (elem_solid) std::memcpy(elem_solid, H.elem_solid.data(), H.n_elem);
+    for (int64_t i = 0; i < H.Ni; ++i) {
+      const int32_t ci = H.canon_of_int[i];
+      if (ci < 0) continue;
+      if (dirichlet) dirichlet[ci] = H.dir[i];
+      if (dir_val) dir_val[ci] = H.dir_val[i];
+    }
+  });
+}
+
+int fsi_export_patches(fsi_ctx* c, int level, int* n_patches, int64_t* total_len, int64_t* ptr, int32_t* dofs,
+                       uint8_t* owned) {
+  return guard(c, [&] {
+    check_level(*c, level, true);
+    const HostLevel& H = c->hl[level];
+    if (n_patches) *n_patches = H.n_patches;
+    std::vector<uint8_t> own_flag(H.idx_total, 0);
+    for (int p = 0; p < H.n_patches; ++p)
+      for (int64_t o = H.p_own_off[p]; o < H.p_own_off[p + 1]; ++o) own_flag[H.p_idx_off[p] + H.p_own[o]] = 1;
+    int64_t tot = 0;
+    for (int64_t i = 0; i < H.idx_total; ++i)
+      if (H.canon_of_int[H.p_idx[i]] >= 0) ++tot;
+    if (total_len) *total_len = tot;
+    if (!ptr) return;
+    int64_t pos = 0;
+    ptr[0] = 0;
+    for (int p = 0; p < H.n_patches; ++p) {
+      for (int64_t i = H.p_idx_off[p]; i < H.p_idx_off[p + 1]; ++i) {
+        const int32_t ci = H.canon_of_int[H.p_idx[i]];
+        if (ci < 0) continue;
+        if (dofs) dofs[pos] = ci;
+        if (owned) owned[pos] = own_flag[i];
+        ++pos;
+      }
+      ptr[p + 1] = pos;
+    }
+  });
+}
+
+int fsi_export_transfer(fsi_ctx* c, int level, int which, int64_t* nnz, int64_t* rowptr, int32_t* col, double* val) {
+  return guard(c, [&] {
+    check_level(*c, level, true);
+    if (which != 0 && which != 1) throw ApiError(FSI_E_INVALID, "which must be 0 (P) or 1 (R)");
+    const HostLevel& F = c->hl[level];
+    const HostLevel& C = c->hl[level - 1];
+    const HostLevel& Rw = which == 0 ? F : C;     // row level
+    const HostLevel& Cl = which == 0 ? C : F;     // column level
+    const std::vector<int32_t>& ptr = which == 0 ? F.P_ptr : F.R_ptr;
+    const std::vector<int32_t>& cols = which == 0 ? F.P_col : F.R_col;
+    const std::vector<double>& vals = which == 0 ? F.P_val : F.R_val;
+    if (nnz) *nnz = (int64_t)cols.size();
+    if (!rowptr) return;
+    // canonical row order: internal rows that map to canonical rows, ascending canonical index
+    std::vector<int64_t> order(Rw.N, -1);
+    for (int64_t i = 0; i < Rw.Ni; ++i)
+      if (Rw.canon_of_int[i] >= 0) order[Rw.canon_of_int[i]] = i;
+    int64_t pos = 0;
+    rowptr[0] = 0;
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t r = 0; r < Rw.N; ++r) {
+      const int64_t i = order[r];
+      row.clear();
+      for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) row.push_back({Cl.canon_of_int[cols[k]], vals[k]});
+      std::sort(row.begin(), row.end());
+      for (auto& e : row) {
+        if (col) col[pos] = e.first;
+        if (val) val[pos] = e.second;
+        ++pos;
+      }
+      rowptr[r + 1] = pos;
+    }
+  });
+}
+
+int fsi_apply_operator(fsi_ctx* c, int level, const double* x, double* y) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, false);
+    DevLevel& D = c->dl[level];
+    to_internal(*c, level, x, D.x);
+    launch_bsr_residual(c->B, D.nb, D.rowptr, D.col, D.val, D.x, nullptr, D.r, c->stream);
+    counted(*c);
+    to_canonical(*c, level, D.r, y);
+    sync(*c);
+  });
+}
+
+int fsi_apply_vcycle(fsi_ctx* c, const double* b, double* z) {
+  return guard(c, [&] {
+    need_device(*c);
+    const int L = (int)c->dl.size();
+    to_internal(*c, L - 1, b, c->bk);
+    vcycle(*c, L - 1, c->bk, c->xk);
+    to_canonical(*c, L - 1, c->xk, z);
+    sync(*c);
+  });
+}
+
+int fsi_apply_smoother(fsi_ctx* c, int level, const double* b, const double* x, double* x_out) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, true);
+    DevLevel& D = c->dl[level];
+    to_internal(*c, level, b, D.b);
+    to_internal(*c, level, x, D.x);
+    smooth_step(*c, level, D.b, D.x, false);
+    to_canonical(*c, level, D.x, x_out);
+    sync(*c);
+  });
+}
+
+int fsi_restrict(fsi_ctx* c, int level, const double* fine, double* coarse) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, true);
+    DevLevel& D = c->dl[level];
+    DevLevel& C = c->dl[level - 1];
+    to_internal(*c, level, fine, D.r);
+    launch_csr_spmv(C.Ni, D.R_ptr, D.R_col, D.R_val, D.r, C.b, false, c->stream);
+    counted(*c);
+    to_canonical(*c, level - 1, C.b, coarse);
+    sync(*c);
+  });
+}
+
+int fsi_prolong(fsi_ctx* c, int level, const double* coarse, double* fine) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, true);
+    DevLevel& D = c->dl[level];
+    DevLevel& C = c->dl[level - 1];
+    to_internal(*c, level - 1, coarse, C.x);
+    launch_csr_spmv(D.Ni, D.P_ptr, D.P_col, D.P_val, C.x, D.r, false, c->stream);
+    counted(*c);
+    to_canonical(*c, level, D.r, fine);
+    sync(*c);
+  });
+}
+
+int fsi_set_profiling(fsi_ctx* c, int on) {
+  return guard(c, [&] {
+    need_device(*c);
+    harvest(*c);
+    for (auto& ks : c->kstat) {
+      ks.ms = ks.bytes = ks.flops = 0.0;
+      ks.launches = 0;
+    }
+    c->prof = on != 0;
+  });
+}
+
+int fsi_kernel_stats(fsi_ctx* c, int kind, double* device_ms, int64_t* launches, double* alg_bytes,
+                     double* alg_flops) {
+  return guard(c, [&] {
+    need_device(*c);
+    if (kind < 0 || kind >= FSI_K_COUNT) throw ApiError(FSI_E_INVALID, "bad kernel class");
+    harvest(*c);
+    const auto& ks = c->kstat[kind];
+    if (device_ms) *device_ms = ks.ms;
+    if (launches) *launches = ks.launches;
+    if (alg_bytes) *alg_bytes = ks.bytes;
+    if (alg_flops) *alg_flops = ks.flops;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal data structures of libfsi (host builder, kernels, C-ABI).
+//
+// Device layout ("internal" numbering): a level with Nn Q2 nodes and Ne
+// elements has nb = Nn + Ne blocks of B = 2*dim unknowns.  Node block a holds
+// [d_0..d_{n-1}, u_0..u_{n-1}] of node a (identical to the canonical
+// numbering); element block Nn + e holds the n+1 pressures of element e and
+// B-(n+1) padding slots that are always zero.  The Jacobian of every level is
+// a block-sparse (BSR) matrix with B x B row-major blocks on the FE graph
+// (node-node blocks for nodes sharing an element, node-pressure and
+// pressure-node blocks inside an element; no pressure-pressure blocks).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fsi.h"
+
+namespace fsi {
+
+constexpr int kFluid = 0, kSolid = 1, kIface = 2;
+
+struct HostLevel {
+  int dim = 2;
+  int cells[3] = {1, 1, 1};
+  int nodes_ax[3] = {1, 1, 1};
+  int64_t n_nodes = 0, n_elem = 0, N = 0, nb = 0, Ni = 0;
+  int B = 4, nloc = 9, ndofe = 39;
+  std::vector<double> verts[3];
+  std::vector<int32_t> elem_nodes;     // n_elem * nloc
+  std::vector<uint8_t> elem_solid;     // n_elem
+  std::vector<uint8_t> node_class;     // n_nodes
+  std::vector<uint8_t> dir;            // Ni (internal), 1 = Dirichlet unknown
+  std::vector<double> dir_val;         // Ni
+  std::vector<int32_t> canon_of_int;   // Ni -> canonical index or -1 (padding)
+  // block-sparse pattern
+  std::vector<int32_t> rowptr, col;    // nb+1, nnzb
+  int64_t nnzb = 0;
+  std::vector<int32_t> elem_map;       // n_elem * (nloc+1)^2 block index or -1
+  std::vector<int32_t> color_list;     // elements ordered by (color, material)
+  std::vector<int32_t> color_ptr;      // (2^dim * 2) + 1 offsets into color_list
+  // grid transfers from level-1 into this level (scalar CSR, internal indices)
+  std::vector<int32_t> P_ptr, P_col;   // Ni rows
+  std::vector<double> P_val;
+  std::vector<int32_t> R_ptr, R_col;   // Ni(l-1) rows
+  std::vector<double> R_val;
+  // Schwarz blocks (levels >= 1)
+  int n_patches = 0;
+  std::vector<int32_t> p_n, p_nown;            // per patch sizes (padded) / owned rows
+  std::vector<int64_t> p_idx_off;              // into p_idx (sum n_k)
+  std::vector<int64_t> p_own_off;              // into p_own (sum nown_k)
+  std::vector<int64_t> p_dense_off;            // into dense workspace (sum n_k^2)
+  std::vector<int64_t> p_inv_off;              // into owned inverse rows (sum nown_k*n_k)
+  std::vector<int64_t> p_gmap_off;             // into p_gmap triples
+  std::vector<int32_t> p_idx;                  // internal unknown of each patch-local unknown (-1: pad)
+  std::vector<int32_t> p_own;                  // patch-local row of each owned row
+  std::vector<int32_t> p_gmap;                 // (bsr block, local block row, local block col)
+  std::vector<int32_t> p_padpos;               // patch-local pad positions (identity diag), flat
+  std::vector<int64_t> p_pad_off;
+  std::vector<int32_t> p_elems;                // elements of each patch (for export)
+  std::vector<int64_t> p_elem_off;
+  int64_t dense_total = 0, inv_total = 0, idx_total = 0, own_total = 0;
+  int max_n = 0;
+};
+
+bool build_host_hierarchy(const fsi_problem_desc& d, const fsi_solver_opts& o,
+                          std::vector<HostLevel>& lv, std::string& err);
+
+// ---------------------------------------------------------------------------
+// device side
+// ---------------------------------------------------------------------------
+struct DevLevel {
+  int64_t n_nodes = 0, n_elem = 0, N = 0, nb = 0, Ni = 0, nnzb = 0;
+  int cells[3] = {1, 1, 1};
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;          // nnzb * B*B
+  double* Ke = nullptr;           // n_elem * ndofe^2 element matrices
+  int32_t* elem_nodes = nullptr;
+  uint8_t* elem_solid = nullptr;
+  uint8_t* node_class = nullptr;
+  double* elem_geo = nullptr;     // n_elem * 2*dim (lower corner, edge lengths)
+  uint8_t* dir = nullptr;
+  double* dir_val = nullptr;
+  int32_t* dir_list = nullptr;    // internal Dirichlet unknowns
+  int64_t n_dir = 0;
+  int32_t* canon_of_int = nullptr;
+  int32_t* int_of_canon = nullptr;
+  int32_t* elem_map = nullptr;
+  int32_t* color_list = nullptr;
+  std::vector<int32_t> color_ptr;  // host copy
+  int32_t *P_ptr = nullptr, *P_col = nullptr, *R_ptr = nullptr, *R_col = nullptr;
+  double *P_val = nullptr, *R_val = nullptr;
+  // patches
+  int n_patches = 0, max_n = 0;
+  int32_t *p_n = nullptr, *p_nown = nullptr;
+  int64_t *p_idx_off = nullptr, *p_own_off = nullptr, *p_dense_off = nullptr, *p_inv_off = nullptr,
+          *p_gmap_off = nullptr, *p_pad_off = nullptr;
+  int32_t *p_idx = nullptr, *p_own = nullptr, *p_gmap = nullptr, *p_padpos = nullptr;
+  double* inv = nullptr;          // owned rows of B_k^{-1}
+  int64_t inv_total = 0, dense_total = 0;
+  // work vectors (internal layout)
+  double *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  // algorithmic traffic / arithmetic of one launch (profiling)
+  double apply_bytes = 0, apply_flops = 0, spmv_bytes = 0, spmv_flops = 0;
+  double factor_bytes = 0, factor_flops = 0, R_bytes = 0, P_bytes = 0;
+};
+
+struct Ctx {
+  fsi_problem_desc desc;
+  fsi_solver_opts opts;
+  cudaStream_t stream = nullptr;
+  std::vector<HostLevel> hl;
+  std::vector<DevLevel> dl;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  std::string err;
+  int64_t launches = 0;
+  int dim = 2, B = 4, nloc = 9, ndofe = 39;
+  int sm_count = 0;
+  // finest-level state and vectors (internal layout)
+  double *y = nullptr, *res = nullptr;
+  double *V = nullptr, *Z = nullptr;     // Krylov bases
+  double *w = nullptr, *xk = nullptr, *bk = nullptr, *tmp = nullptr;
+  double* partial = nullptr;              // reduction partials
+  double* small = nullptr;                // device scalars
+  double* host_small = nullptr;           // pinned mirror
+  double *stage_a = nullptr, *stage_b = nullptr;  // canonical staging vectors
+  double* dense_ws = nullptr;             // patch factorisation workspace
+  int64_t dense_ws_len = 0;
+  int32_t *piv_ws = nullptr;              // per-patch pivots
+  // coarse dense inverse
+  double *c_A = nullptr, *c_B = nullptr, *c_inv = nullptr;
+  int32_t* c_piv = nullptr;
+  int32_t* status = nullptr;              // device status flags
+  double* tmp_re = nullptr;               // finest element residuals (n_elem * ndofe)
+  int32_t* coarse_pad_list = nullptr;     // padding slots of the coarse dense operator
+  int n_coarse_pads = 0;
+  float t_assemble = 0.f, t_factor = 0.f, t_solve = 0.f;
+  int red_blocks = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-kernel-class profiling
+  bool prof = false;
+  struct KStat {
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
+    int64_t launches = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  } kstat[FSI_K_COUNT];
+  std::vector<cudaEvent_t> event_pool;
+};
+
+// status flag slots
+enum { ST_SINGULAR = 0, ST_TANGLED = 1, ST_NONFINITE = 2, ST_COUNT = 4 };
+
+}  // namespace fsi

@@ -1,0 +1,422 @@
+// Element-batched residual + exact Jacobian assembly and Galerkin coarsening.
+//
+// Assembly (Sec. 2.3, 2.5, 3): one thread per (element, unknown j) evaluates
+// the element residual in forward-mode dual arithmetic seeded along e_j, so
+// it produces column j of the exact element Jacobian (the derivative of the
+// discrete residual, as the paper obtains with automatic differentiation)
+// and the value of residual row j.  Element matrices are written to an
+// element-matrix buffer; a coloured scatter adds them into the block-sparse
+// Jacobian (elements of one colour share no node, so no atomics are needed
+// and the summation order is fixed).
+//
+// Galerkin (Sec. 3.2): J_{l-1} = R J_l P is formed element by element.  A
+// coarse element matrix is sum_children R_c A_c P_c, where P_c interpolates
+// the coarse element's Q2 / P1disc unknowns to the child's and R_c is its
+// transpose restricted to equations of the same kind (momentum, solid
+// kinematic, ALE) with Dirichlet rows and columns dropped.
+#include <cooperative_groups.h>
+
+#include "kernels.h"
+
+namespace fsi {
+
+namespace {
+
+struct Dual {
+  double v, d;
+};
+__device__ __forceinline__ Dual mk(double v, double d) { return Dual{v, d}; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, double s) { return {a.v * s, a.d * s}; }
+__device__ __forceinline__ Dual operator+(Dual a, double s) { return {a.v + s, a.d}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+  const double inv = 1.0 / b.v;
+  const double q = a.v * inv;
+  return {q, (a.d - b.d * q) * inv};
+}
+
+// 1D quadratic Lagrange basis (nodes -1, 0, 1) and derivative at the three
+// Gauss points -sqrt(3/5), 0, sqrt(3/5).
+__device__ __forceinline__ double gp(int q) { return q == 0 ? -0.7745966692414834 : (q == 1 ? 0.0 : 0.7745966692414834); }
+__device__ __forceinline__ double gw(int q) { return q == 1 ? 8.0 / 9.0 : 5.0 / 9.0; }
+__device__ __forceinline__ double L1(int m, double x) {
+  return m == 0 ? 0.5 * x * (x - 1.0) : (m == 1 ? 1.0 - x * x : 0.5 * x * (x + 1.0));
+}
+__device__ __forceinline__ double dL1(int m, double x) { return m == 0 ? x - 0.5 : (m == 1 ? -2.0 * x : x + 0.5); }
+
+constexpr int kDim = 2;
+constexpr int kB = 4;           // unknowns per node block
+constexpr int kNloc = 9;        // Q2 nodes per element
+constexpr int kNN = kB * kNloc; // node unknowns per element
+constexpr int kNdofe = kNN + kDim + 1;   // 39
+constexpr int kEPB = 4;         // elements per thread block
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// element residual + Jacobian column (2D)
+// ---------------------------------------------------------------------------
+template <bool SOLID>
+__global__ void __launch_bounds__(kEPB * kNdofe)
+k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ y,
+              const int32_t* __restrict__ elem_nodes, const uint8_t* __restrict__ node_class,
+              const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp,
+              double* __restrict__ Ke, double* __restrict__ Re, int32_t* __restrict__ status) {
+  __shared__ double s_y[kEPB][kNdofe];
+  __shared__ double s_geo[kEPB][2 * kDim];
+  __shared__ unsigned s_iface[kEPB];
+  const int le = threadIdx.x / kNdofe;
+  const int j = threadIdx.x % kNdofe;
+  const int el = blockIdx.x * kEPB + le;
+  const bool active = le < kEPB && el < ne;
+  const int e = active ? elems[el] : 0;
+  if (active) {
+    if (j < kNN) {
+      const int a = j / kB, s = j % kB;
+      s_y[le][j] = y[(int64_t)elem_nodes[(int64_t)e * kNloc + a] * kB + s];
+    } else {
+      s_y[le][j] = y[(n_nodes + e) * kB + (j - kNN)];
+    }
+    if (j < 2 * kDim) s_geo[le][j] = elem_geo[(int64_t)e * 2 * kDim + j];
+    if (j == 0) {
+      unsigned m = 0;
+      for (int a = 0; a < kNloc; ++a)
+        if (node_class[elem_nodes[(int64_t)e * kNloc + a]] == kIface) m |= 1u << a;
+      s_iface[le] = m;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const double* ye = s_y[le];
+  const double hx = s_geo[le][2], hy = s_geo[le][3];
+  const double vol = hx * hy;
+  const double kale = 1.0 / vol;
+  const unsigned iface = s_iface[le];
+  // seed: which unknown this thread differentiates along
+  const int aj = j < kNN ? j / kB : -1;
+  const int sj = j < kNN ? j % kB : -1;
+  const int pk = j >= kNN ? j - kNN : -1;
+
+  double acc[kNdofe];
+#pragma unroll
+  for (int i = 0; i < kNdofe; ++i) acc[i] = 0.0;
+  double vj = 0.0;
+  bool tangled = false;
+
+#pragma unroll 1
+  for (int qy = 0; qy < 3; ++qy) {
+#pragma unroll 1
+    for (int qx = 0; qx < 3; ++qx) {
+      const double xi = gp(qx), eta = gp(qy);
+      const double wq = gw(qx) * gw(qy) * vol * 0.25;
+      double Nb[kNloc], Gx[kNloc], Gy[kNloc];
+#pragma unroll
+      for (int a = 0; a < kNloc; ++a) {
+        const int ia = a % 3, ja = a / 3;
+        const double lx = L1(ia, xi), ly = L1(ja, eta);
+        Nb[a] = lx * ly;
+        Gx[a] = dL1(ia, xi) * ly * (2.0 / hx);
+        Gy[a] = lx * dL1(ja, eta) * (2.0 / hy);
+      }
+      // fields at the quadrature point (values), derivatives from the seed
+      double gdv[2][2] = {{0, 0}, {0, 0}}, guv[2][2] = {{0, 0}, {0, 0}}, uv[2] = {0, 0};
+#pragma unroll
+      for (int a = 0; a < kNloc; ++a) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const double dv = ye[a * kB + i], vv = ye[a * kB + 2 + i];
+          gdv[i][0] += dv * Gx[a];
+          gdv[i][1] += dv * Gy[a];
+          guv[i][0] += vv * Gx[a];
+          guv[i][1] += vv * Gy[a];
+          uv[i] += vv * Nb[a];
+        }
+      }
+      const double psi[3] = {1.0, xi, eta};
+      const double pv = ye[kNN] + ye[kNN + 1] * xi + ye[kNN + 2] * eta;
+      const double gxj = aj >= 0 ? Gx[aj] : 0.0, gyj = aj >= 0 ? Gy[aj] : 0.0, nj = aj >= 0 ? Nb[aj] : 0.0;
+      Dual gd[2][2], gu[2][2], u[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        gd[i][0] = mk(gdv[i][0], sj == i ? gxj : 0.0);
+        gd[i][1] = mk(gdv[i][1], sj == i ? gyj : 0.0);
+        gu[i][0] = mk(guv[i][0], sj == 2 + i ? gxj : 0.0);
+        gu[i][1] = mk(guv[i][1], sj == 2 + i ? gyj : 0.0);
+        u[i] = mk(uv[i], sj == 2 + i ? nj : 0.0);
+      }
+      const Dual p = mk(pv, pk >= 0 ? psi[pk] : 0.0);
+      Dual F[2][2];
+      F[0][0] = gd[0][0] + 1.0; F[0][1] = gd[0][1];
+      F[1][0] = gd[1][0];       F[1][1] = gd[1][1] + 1.0;
+      const Dual J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+      if (!(J.v > 0.0)) tangled = true;
+      Dual Fi[2][2];
+      Fi[0][0] = F[1][1] / J; Fi[0][1] = -F[0][1] / J;
+      Fi[1][0] = -F[1][0] / J; Fi[1][1] = F[0][0] / J;
+      Dual mass;
+      if (SOLID) {
+        // P = J sigma F^{-T} = -p J F^{-T} + mu_s J F   (sigma = -p I + 2 C1 B, C1 = mu_s / 2)
+        const Dual pJ = p * J;
+        const Dual muJ = J * pp.mu_s;
+        Dual T[2][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) T[i][k] = muJ * F[i][k] - pJ * Fi[k][i];
+#pragma unroll
+        for (int a = 0; a < kNloc; ++a) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const Dual m = (T[c][0] * Gx[a] + T[c][1] * Gy[a]) * wq;
+            acc[a * kB + c] += m.d;
+            if (a * kB + c == j) vj += m.v;
+            const Dual kin = u[c] * (Nb[a] * wq);
+            acc[a * kB + 2 + c] += kin.d;
+            if (a * kB + 2 + c == j) vj += kin.v;
+          }
+        }
+        mass = J + (-1.0);
+      } else {
+        Dual gx[2][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) gx[i][k] = gu[i][0] * Fi[0][k] + gu[i][1] * Fi[1][k];
+        Dual sig[2][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) sig[i][k] = (gx[i][k] + gx[k][i]) * pp.mu_f;
+        sig[0][0] = sig[0][0] - p;
+        sig[1][1] = sig[1][1] - p;
+        Dual T[2][2], conv[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+#pragma unroll
+          for (int k = 0; k < 2; ++k) T[c][k] = (sig[c][0] * Fi[k][0] + sig[c][1] * Fi[k][1]) * J * wq;
+          conv[c] = (gx[c][0] * u[0] + gx[c][1] * u[1]) * J * (pp.rho_f * wq);
+        }
+        Dual A[2][2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            A[c][k] = (pp.ale_op == 0 ? gd[c][k] + gd[k][c] : gd[c][k]) * (kale * wq);
+#pragma unroll
+        for (int a = 0; a < kNloc; ++a) {
+          const bool ifc = (iface >> a) & 1u;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const Dual m = T[c][0] * Gx[a] + T[c][1] * Gy[a] + conv[c] * Nb[a];
+            const Dual al = A[c][0] * Gx[a] + A[c][1] * Gy[a];
+            // interface node: momentum in the d-row, no ALE row (psi = 0 on the interface)
+            // fluid node: ALE in the d-row, momentum in the u-row
+            const Dual rd = ifc ? m : al;
+            acc[a * kB + c] += rd.d;
+            if (a * kB + c == j) vj += rd.v;
+            if (!ifc) {
+              acc[a * kB + 2 + c] += m.d;
+              if (a * kB + 2 + c == j) vj += m.v;
+            }
+          }
+        }
+        mass = J * (gx[0][0] + gx[1][1]);
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const Dual t = mass * (psi[k] * wq);
+        acc[kNN + k] += t.d;
+        if (kNN + k == j) vj += t.v;
+      }
+    }
+  }
+  if (tangled && j == 0) atomicExch(&status[ST_TANGLED], 1);
+  double* K = Ke + (int64_t)e * kNdofe * kNdofe;
+#pragma unroll
+  for (int i = 0; i < kNdofe; ++i) K[i * kNdofe + j] = acc[i];
+  Re[(int64_t)e * kNdofe + j] = vj;
+}
+
+// coloured scatter of element matrices into the BSR values (+ residual)
+__global__ void k_scatter_2d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ Ke,
+                             const double* __restrict__ Re, const int32_t* __restrict__ elem_nodes,
+                             const int32_t* __restrict__ elem_map, int64_t n_nodes, double* __restrict__ val,
+                             double* __restrict__ res) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)kNdofe * kNdofe;
+  if (t >= (int64_t)ne * per) return;
+  const int el = (int)(t / per);
+  const int ij = (int)(t % per);
+  const int i = ij / kNdofe, j = ij % kNdofe;
+  if (i >= kNN && j >= kNN) return;
+  const int e = elems[el];
+  const int lr = i < kNN ? i / kB : kNloc, ci = i < kNN ? i % kB : i - kNN;
+  const int lc = j < kNN ? j / kB : kNloc, cj = j < kNN ? j % kB : j - kNN;
+  const int32_t blk = elem_map[((int64_t)e * (kNloc + 1) + lr) * (kNloc + 1) + lc];
+  val[(int64_t)blk * kB * kB + ci * kB + cj] += Ke[(int64_t)e * per + ij];
+  if (res != nullptr && j == 0) {
+    const int64_t row = i < kNN ? (int64_t)elem_nodes[(int64_t)e * kNloc + lr] * kB + ci
+                                : (n_nodes + e) * kB + ci;
+    res[row] += Re[(int64_t)e * kNdofe + i];
+  }
+}
+
+// Dirichlet rows -> identity rows; residual r_i = y_i - g_i
+__global__ void k_dirichlet(const int32_t* __restrict__ dir_list, int64_t n_dir, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ col, double* __restrict__ val, int B,
+                            const double* __restrict__ y, const double* __restrict__ g, double* __restrict__ res) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_dir) return;
+  const int32_t i = dir_list[t];
+  const int32_t br = i / B, ci = i % B;
+  for (int32_t k = rowptr[br]; k < rowptr[br + 1]; ++k) {
+    double* v = val + (int64_t)k * B * B + ci * B;
+    for (int cj = 0; cj < B; ++cj) v[cj] = (col[k] == br && cj == ci) ? 1.0 : 0.0;
+  }
+  if (res != nullptr) res[i] = y[i] - g[i];
+}
+
+// ---------------------------------------------------------------------------
+// element-wise Galerkin coarsening (2D)
+// ---------------------------------------------------------------------------
+namespace {
+// weight of parent node m at the child's local node i, child side s:
+// parent reference coordinate -1 + (2 s + i) / 2
+__device__ __forceinline__ double qw(int s, int i, int m) { return L1(m, -1.0 + 0.5 * (double)(2 * s + i)); }
+__device__ __forceinline__ int row_kind(int cls, int slot) {
+  if (cls == kFluid) return slot < kDim ? 2 : 0;
+  return slot < kDim ? 0 : 1;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256)
+k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __restrict__ f_nodes,
+              const uint8_t* __restrict__ f_class, const uint8_t* __restrict__ f_dir,
+              const int32_t* __restrict__ c_nodes, const uint8_t* __restrict__ c_class,
+              const uint8_t* __restrict__ c_dir, double* __restrict__ Kc) {
+  __shared__ double sA[kNdofe * kNdofe];
+  __shared__ double sT[kNdofe * kNdofe];
+  __shared__ double sC[kNdofe * kNdofe];
+  __shared__ uint8_t c_cls[kNloc], c_msk[kNN], f_cls[kNloc], f_msk[kNN];
+  const int E = blockIdx.x;
+  const int cx = E % ncx, cy = E / ncx;
+  const int fcx = 2 * ncx;
+  for (int t = threadIdx.x; t < kNdofe * kNdofe; t += blockDim.x) sC[t] = 0.0;
+  if (threadIdx.x < kNloc) c_cls[threadIdx.x] = c_class[c_nodes[(int64_t)E * kNloc + threadIdx.x]];
+  if (threadIdx.x < kNN) {
+    const int a = threadIdx.x / kB, s = threadIdx.x % kB;
+    c_msk[threadIdx.x] = c_dir[(int64_t)c_nodes[(int64_t)E * kNloc + a] * kB + s] ? 0 : 1;
+  }
+  for (int ch = 0; ch < 4; ++ch) {
+    const int sx = ch & 1, sy = ch >> 1;
+    const int64_t ef = (2 * cx + sx) + (int64_t)fcx * (2 * cy + sy);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kNdofe * kNdofe; t += blockDim.x) sA[t] = Kf[ef * kNdofe * kNdofe + t];
+    if (threadIdx.x < kNloc) f_cls[threadIdx.x] = f_class[f_nodes[ef * kNloc + threadIdx.x]];
+    if (threadIdx.x < kNN) {
+      const int a = threadIdx.x / kB, s = threadIdx.x % kB;
+      f_msk[threadIdx.x] = f_dir[(int64_t)f_nodes[ef * kNloc + a] * kB + s] ? 0 : 1;
+    }
+    __syncthreads();
+    // T = A_c P_c
+    for (int t = threadIdx.x; t < kNdofe * kNdofe; t += blockDim.x) {
+      const int i = t / kNdofe, J = t % kNdofe;
+      double acc = 0.0;
+      if (J < kNN) {
+        const int b = J / kB, s = J % kB;
+        if (c_msk[J]) {
+          const int ib = b % 3, jb = b / 3;
+          for (int a = 0; a < kNloc; ++a) {
+            const int ia = a % 3, ja = a / 3;
+            const double q = qw(sx, ia, ib) * qw(sy, ja, jb);
+            if (q != 0.0 && f_msk[a * kB + s]) acc += sA[i * kNdofe + a * kB + s] * q;
+          }
+        }
+      } else {
+        const int k = J - kNN;
+        // child coefficients: c0 = p0 + sum_d sig_d/2 p_d ; c_d = p_d / 2
+        if (k == 0) acc = sA[i * kNdofe + kNN];
+        else {
+          const double sig = k == 1 ? (sx ? 0.5 : -0.5) : (sy ? 0.5 : -0.5);
+          acc = sA[i * kNdofe + kNN] * sig + sA[i * kNdofe + kNN + k] * 0.5;
+        }
+      }
+      sT[t] = acc;
+    }
+    __syncthreads();
+    // C += R_c T
+    for (int t = threadIdx.x; t < kNdofe * kNdofe; t += blockDim.x) {
+      const int I = t / kNdofe, J = t % kNdofe;
+      double acc = 0.0;
+      if (I < kNN) {
+        const int b = I / kB, sc = I % kB;
+        if (c_msk[I]) {
+          const int ib = b % 3, jb = b / 3;
+          const int comp = sc % kDim;
+          const int kc = row_kind(c_cls[b], sc);
+          for (int a = 0; a < kNloc; ++a) {
+            const int ia = a % 3, ja = a / 3;
+            const double q = qw(sx, ia, ib) * qw(sy, ja, jb);
+            if (q == 0.0) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int sf = h == 0 ? comp : kDim + comp;
+              if (f_msk[a * kB + sf] && row_kind(f_cls[a], sf) == kc) acc += q * sT[(a * kB + sf) * kNdofe + J];
+            }
+          }
+        }
+      } else {
+        const int k = I - kNN;
+        if (k == 0) acc = sT[kNN * kNdofe + J];
+        else {
+          const double sig = k == 1 ? (sx ? 0.5 : -0.5) : (sy ? 0.5 : -0.5);
+          acc = sT[kNN * kNdofe + J] * sig + sT[(kNN + k) * kNdofe + J] * 0.5;
+        }
+      }
+      sC[t] += acc;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kNdofe * kNdofe; t += blockDim.x) Kc[(int64_t)E * kNdofe * kNdofe + t] = sC[t];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+                        const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
+                        double* Ke, double* Re, int32_t* status, cudaStream_t st) {
+  if (ne <= 0) return;
+  const int grid = (ne + kEPB - 1) / kEPB;
+  if (solid)
+    k_assemble_2d<true><<<grid, kEPB * kNdofe, 0, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp,
+                                                        Ke, Re, status);
+  else
+    k_assemble_2d<false><<<grid, kEPB * kNdofe, 0, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp,
+                                                         Ke, Re, status);
+}
+
+void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
+                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st) {
+  if (ne <= 0) return;
+  const int64_t n = (int64_t)ne * kNdofe * kNdofe;
+  k_scatter_2d<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(elems, ne, Ke, Re, elem_nodes, elem_map, n_nodes, val,
+                                                            res);
+}
+
+void launch_dirichlet(const int32_t* dir_list, int64_t n_dir, const int32_t* rowptr, const int32_t* col, double* val,
+                      int B, const double* y, const double* g, double* res, cudaStream_t st) {
+  if (n_dir <= 0) return;
+  k_dirichlet<<<(unsigned)((n_dir + 255) / 256), 256, 0, st>>>(dir_list, n_dir, rowptr, col, val, B, y, g, res);
+}
+
+void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
+                        const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,
+                        double* Kc, cudaStream_t st) {
+  k_galerkin_2d<<<ncx * ncy, 256, 0, st>>>(ncx, ncy, Kf, f_nodes, f_class, f_dir, c_nodes, c_class, c_dir, Kc);
+}
+
+}  // namespace fsi

@@ -1,0 +1,61 @@
+// Kernel launchers shared between the .cu translation units of libfsi.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "fsi_internal.h"
+
+namespace fsi {
+
+struct PhysParams {
+  double rho_f, mu_f, rho_s, mu_s;
+  int ale_op;
+};
+
+// k_assemble.cu
+void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+                        const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
+                        double* Ke, double* Re, int32_t* status, cudaStream_t st);
+void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
+                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st);
+void launch_dirichlet(const int32_t* dir_list, int64_t n_dir, const int32_t* rowptr, const int32_t* col, double* val,
+                      int B, const double* y, const double* g, double* res, cudaStream_t st);
+void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
+                        const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,
+                        double* Kc, cudaStream_t st);
+
+// k_linalg.cu
+void launch_bsr_residual(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
+                         const double* x, const double* b, double* y, cudaStream_t st);
+void launch_csr_spmv(int64_t nrows, const int32_t* ptr, const int32_t* col, const double* val, const double* x,
+                     double* y, bool add, cudaStream_t st);
+void launch_gather(int64_t n, const int32_t* map, const double* in, double* out, cudaStream_t st);
+void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
+void launch_scale_by(int64_t n, const double* src, const double* dev_scalar, double* dst, cudaStream_t st);
+void launch_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, double* partial, int nblk,
+                 cudaStream_t st);
+void launch_reduce(const double* partial, int nvec, int nblk, double* out, bool sqrt_out, cudaStream_t st);
+void launch_cgs_update(int64_t n, const double* V, int64_t ldv, int nvec, const double* h, double* w, cudaStream_t st);
+void launch_combo(int64_t n, const double* Z, int64_t ldz, int nvec, const double* coef, double* x, cudaStream_t st);
+void launch_norm_partial(int64_t n, const double* w, double* partial, int nblk, cudaStream_t st);
+void launch_nonfinite_check(int64_t n, const double* v, int32_t* status, cudaStream_t st);
+
+void launch_patch_gather(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
+                         const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos, const double* bsr_val,
+                         int B, double* dense, cudaStream_t st);
+void launch_patch_gj(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
+                     const int64_t* own_off, const int32_t* own, const int64_t* inv_off, double* dense, double* inv,
+                     int32_t* status, cudaStream_t st);
+void launch_patch_apply(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* idx_off,
+                        const int32_t* idx, const int64_t* own_off, const int32_t* own, const int64_t* inv_off,
+                        const double* inv, const double* r, double* x, double omega, cudaStream_t st);
+
+void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
+                         const int32_t* pad_list, int npad, int64_t n, double* A, cudaStream_t st);
+int launch_coarse_gj(int64_t n, double* A, double* Bm, double* inv, int32_t* piv, int32_t* status, int sm_count,
+                     cudaStream_t st);
+void launch_gemv(int64_t n, const double* A, const double* x, double* y, cudaStream_t st);
+
+}  // namespace fsi

@@ -1,0 +1,312 @@
+"""Thin ctypes binding of the libfsi C-ABI (argument marshalling only).
+
+Every step of the Newton-step solve runs in libfsi's CUDA kernels; this
+module converts Python descriptors into the C structs, passes pointers
+(torch tensors on the GPU or numpy arrays on the host) and turns non-zero
+status codes into exceptions.  There is no CPU fallback: if ``libfsi.so`` is
+missing or no CUDA device is usable, calls raise.
+"""
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from .workloads import Problem, SolverOpts
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfsi.so")
+
+FSI_OK = 0
+ERRORS = {
+    -1: "FSI_E_INVALID", -2: "FSI_E_OOM", -3: "FSI_E_CUDA", -4: "FSI_E_SINGULAR",
+    -5: "FSI_E_NOT_CONVERGED", -6: "FSI_E_NONFINITE", -7: "FSI_E_MESH_TANGLED",
+    -8: "FSI_E_TIMEOUT", 1: "FSI_PENDING",
+}
+MAX_BREAKS = 65
+
+# exported symbols declared in include/fsi.h
+SYMBOLS = (
+    "fsi_build_hierarchy", "fsi_destroy", "fsi_last_error", "fsi_get_sizes", "fsi_initial_state",
+    "fsi_set_state", "fsi_get_state", "fsi_assemble_jacobian", "fsi_factor_schwarz", "fsi_solve",
+    "fsi_newton_update", "fsi_newton_step", "fsi_export_csr", "fsi_export_dofmap", "fsi_export_patches",
+    "fsi_apply_operator", "fsi_apply_vcycle", "fsi_apply_smoother", "fsi_restrict", "fsi_prolong",
+    "fsi_launch_count", "fsi_plan_hierarchy", "fsi_export_transfer", "fsi_set_profiling",
+    "fsi_kernel_stats",
+)
+
+# kernel classes for fsi_kernel_stats
+KERNEL_CLASSES = ("assemble", "galerkin", "scatter", "patch_factor", "coarse_factor", "patch_apply",
+                  "spmv", "transfer", "krylov")
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("levels", ctypes.c_int), ("n_breaks", ctypes.c_int * 3),
+        ("breaks", (ctypes.c_double * MAX_BREAKS) * 3), ("flap_lo", ctypes.c_double * 3),
+        ("flap_hi", ctypes.c_double * 3), ("rho_f", ctypes.c_double), ("mu_f", ctypes.c_double),
+        ("rho_s", ctypes.c_double), ("mu_s", ctypes.c_double), ("U", ctypes.c_double),
+        ("transient", ctypes.c_int), ("dt", ctypes.c_double), ("ale_op", ctypes.c_int),
+    ]
+
+
+class SolverOptsC(ctypes.Structure):
+    _fields_ = [
+        ("tile", ctypes.c_int * 3), ("n_pre", ctypes.c_int), ("n_post", ctypes.c_int),
+        ("omega", ctypes.c_double), ("restart", ctypes.c_int), ("rtol", ctypes.c_double),
+        ("max_iters", ctypes.c_int), ("precision", ctypes.c_int),
+    ]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_res", ctypes.c_double),
+        ("rho", ctypes.c_double), ("t_assemble_ms", ctypes.c_double), ("t_factor_ms", ctypes.c_double),
+        ("t_solve_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libfsi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfsi.so not found at {path}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+    lib.fsi_build_hierarchy.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOptsC), vp,
+                                        ctypes.POINTER(vp)]
+    lib.fsi_plan_hierarchy.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOptsC),
+                                       ctypes.POINTER(vp)]
+    lib.fsi_export_transfer.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, vp, vp, vp]
+    lib.fsi_destroy.argtypes = [vp]
+    lib.fsi_destroy.restype = None
+    lib.fsi_last_error.argtypes = [vp]
+    lib.fsi_last_error.restype = ctypes.c_char_p
+    lib.fsi_get_sizes.argtypes = [vp, i64p, i64p, i64p]
+    lib.fsi_initial_state.argtypes = [vp, vp, vp]
+    lib.fsi_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_double]
+    lib.fsi_get_state.argtypes = [vp, vp]
+    lib.fsi_assemble_jacobian.argtypes = [vp, vp]
+    lib.fsi_factor_schwarz.argtypes = [vp]
+    lib.fsi_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveStats)]
+    lib.fsi_newton_update.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.fsi_newton_step.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveStats)]
+    lib.fsi_export_csr.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.fsi_export_dofmap.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
+    lib.fsi_export_patches.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, vp, vp, vp]
+    lib.fsi_apply_operator.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.fsi_apply_vcycle.argtypes = [vp, vp, vp]
+    lib.fsi_apply_smoother.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.fsi_restrict.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.fsi_prolong.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.fsi_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.fsi_kernel_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.fsi_launch_count.argtypes = [vp]
+    lib.fsi_launch_count.restype = ctypes.c_int64
+    _lib = lib
+    return lib
+
+
+def make_desc(p: Problem) -> ProblemDesc:
+    d = ProblemDesc()
+    d.dim = p.dim
+    d.levels = p.levels
+    for a in range(p.dim):
+        br = p.breaks[a]
+        if len(br) > MAX_BREAKS:
+            raise ValueError("too many coarse breaks")
+        d.n_breaks[a] = len(br)
+        for i, v in enumerate(br):
+            d.breaks[a][i] = float(v)
+        d.flap_lo[a] = p.flap_lo[a]
+        d.flap_hi[a] = p.flap_hi[a]
+    d.rho_f, d.mu_f, d.rho_s, d.mu_s, d.U = p.rho_f, p.mu_f, p.rho_s, p.mu_s, p.U
+    d.transient, d.dt, d.ale_op = p.transient, p.dt, p.ale_op
+    return d
+
+
+def make_opts(o: SolverOpts) -> SolverOptsC:
+    c = SolverOptsC()
+    for a, t in enumerate(o.tile):
+        c.tile[a] = t
+    c.n_pre, c.n_post, c.omega = o.n_pre, o.n_post, o.omega
+    c.restart, c.rtol, c.max_iters, c.precision = o.restart, o.rtol, o.max_iters, o.precision
+    return c
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw address of a torch tensor (device or host) or numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+class FSIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class FSI:
+    """One Newton-step solver instance (owns an ``fsi_ctx``)."""
+
+    def __init__(self, prob: Problem, opts: SolverOpts, stream: Optional[int] = None, plan_only: bool = False):
+        """Builds the instance on the current CUDA device (``plan_only``:
+        host structures only, no GPU needed)."""
+        self.lib = load_library()
+        self.prob, self.opts = prob, opts
+        self._desc, self._opts = make_desc(prob), make_opts(opts)
+        h = ctypes.c_void_p()
+        if plan_only:
+            rc = self.lib.fsi_plan_hierarchy(ctypes.byref(self._desc), ctypes.byref(self._opts), ctypes.byref(h))
+        else:
+            rc = self.lib.fsi_build_hierarchy(ctypes.byref(self._desc), ctypes.byref(self._opts),
+                                              ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if rc != FSI_OK:
+            raise FSIError(rc, "fsi_build_hierarchy failed (see stderr)")
+        self.h = h
+        L = prob.levels
+        self.N = np.zeros(L, dtype=np.int64)
+        self.nnz = np.zeros(L, dtype=np.int64)
+        hb = ctypes.c_int64()
+        self._check(self.lib.fsi_get_sizes(self.h, self.N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           self.nnz.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           ctypes.byref(hb)))
+        self.hbm_bytes = hb.value
+
+    def _check(self, rc):
+        if rc != FSI_OK:
+            msg = self.lib.fsi_last_error(self.h).decode()
+            raise FSIError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fsi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- hot path ---------------------------------------------------------
+    def initial_state(self, noise, y_out):
+        self._check(self.lib.fsi_initial_state(self.h, _ptr(noise), _ptr(y_out)))
+
+    def set_state(self, y):
+        self._check(self.lib.fsi_set_state(self.h, _ptr(y), None, None, 0.0))
+
+    def get_state(self, y_out):
+        self._check(self.lib.fsi_get_state(self.h, _ptr(y_out)))
+
+    def assemble(self, residual_out=None):
+        self._check(self.lib.fsi_assemble_jacobian(self.h, _ptr(residual_out)))
+
+    def factor(self):
+        self._check(self.lib.fsi_factor_schwarz(self.h))
+
+    def solve(self, b, x) -> SolveStats:
+        st = SolveStats()
+        self._check(self.lib.fsi_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(st)))
+        return st
+
+    def newton_update(self, dx) -> float:
+        rel = ctypes.c_double()
+        self._check(self.lib.fsi_newton_update(self.h, _ptr(dx), ctypes.byref(rel)))
+        return rel.value
+
+    def newton_step(self, dx_out=None):
+        rel = ctypes.c_double()
+        st = SolveStats()
+        self._check(self.lib.fsi_newton_step(self.h, _ptr(dx_out), ctypes.byref(rel), ctypes.byref(st)))
+        return rel.value, st
+
+    # -- parity / diagnostics --------------------------------------------
+    def export_csr(self, level: int, values: bool = True):
+        """J_level as scipy CSR (values = False: pattern only, zero data)."""
+        import scipy.sparse as sp
+        n = int(self.N[level])
+        nnz = int(self.nnz[level])
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        col = np.zeros(nnz, dtype=np.int32)
+        val = np.zeros(nnz, dtype=np.float64)
+        self._check(self.lib.fsi_export_csr(self.h, level, _ptr(rowptr), _ptr(col),
+                                            _ptr(val) if values else None))
+        return rowptr, col, val
+
+    def export_transfer(self, level: int, which: int):
+        """(rowptr, col, val) of P (which=0) or R (which=1) between level and level-1."""
+        nnz = ctypes.c_int64()
+        self._check(self.lib.fsi_export_transfer(self.h, level, which, ctypes.byref(nnz), None, None, None))
+        rows = int(self.N[level] if which == 0 else self.N[level - 1])
+        rowptr = np.zeros(rows + 1, dtype=np.int64)
+        col = np.zeros(nnz.value, dtype=np.int32)
+        val = np.zeros(nnz.value, dtype=np.float64)
+        self._check(self.lib.fsi_export_transfer(self.h, level, which, None, _ptr(rowptr), _ptr(col), _ptr(val)))
+        return rowptr, col, val
+
+    def export_dofmap(self, level: int, n_nodes: int, n_elem: int):
+        n = int(self.N[level])
+        nc = np.zeros(n_nodes, dtype=np.uint8)
+        es = np.zeros(n_elem, dtype=np.uint8)
+        dm = np.zeros(n, dtype=np.uint8)
+        dv = np.zeros(n, dtype=np.float64)
+        self._check(self.lib.fsi_export_dofmap(self.h, level, _ptr(nc), _ptr(es), _ptr(dm), _ptr(dv)))
+        return nc, es, dm.astype(bool), dv
+
+    def export_patches(self, level: int):
+        npch = ctypes.c_int()
+        tot = ctypes.c_int64()
+        self._check(self.lib.fsi_export_patches(self.h, level, ctypes.byref(npch), ctypes.byref(tot),
+                                                None, None, None))
+        ptr = np.zeros(npch.value + 1, dtype=np.int64)
+        dofs = np.zeros(tot.value, dtype=np.int32)
+        owned = np.zeros(tot.value, dtype=np.uint8)
+        self._check(self.lib.fsi_export_patches(self.h, level, None, None, _ptr(ptr), _ptr(dofs), _ptr(owned)))
+        return [(dofs[ptr[k]:ptr[k + 1]], owned[ptr[k]:ptr[k + 1]].astype(bool)) for k in range(npch.value)]
+
+    def apply_operator(self, level, x, y):
+        self._check(self.lib.fsi_apply_operator(self.h, level, _ptr(x), _ptr(y)))
+
+    def apply_vcycle(self, b, z):
+        self._check(self.lib.fsi_apply_vcycle(self.h, _ptr(b), _ptr(z)))
+
+    def apply_smoother(self, level, b, x, x_out):
+        self._check(self.lib.fsi_apply_smoother(self.h, level, _ptr(b), _ptr(x), _ptr(x_out)))
+
+    def restrict(self, level, fine, coarse):
+        self._check(self.lib.fsi_restrict(self.h, level, _ptr(fine), _ptr(coarse)))
+
+    def prolong(self, level, coarse, fine):
+        self._check(self.lib.fsi_prolong(self.h, level, _ptr(coarse), _ptr(fine)))
+
+    def set_profiling(self, on: bool):
+        self._check(self.lib.fsi_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_stats(self):
+        """{class: dict(ms, launches, bytes, flops)} accumulated since set_profiling(True)."""
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            ms, b, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            n = ctypes.c_int64()
+            self._check(self.lib.fsi_kernel_stats(self.h, k, ctypes.byref(ms), ctypes.byref(n),
+                                                  ctypes.byref(b), ctypes.byref(f)))
+            out[name] = dict(ms=ms.value, launches=n.value, bytes=b.value, flops=f.value)
+        return out
+
+    def launch_count(self) -> int:
+        return int(self.lib.fsi_launch_count(self.h))
