@@ -7,7 +7,10 @@ rtol 1e-10, and the Newton update (fsi_newton_step).  Every step starts from
 the same seeded linearisation state, so every step does the same work.
 
 Default workload: 5 levels (finest 256x64 quads, 313,860 unknowns), shear
-modulus 2e6, mean inflow 1.0, 4x4-element Schwarz blocks, FP64.
+modulus 2e6, mean inflow 1.0, 4x4-element Schwarz blocks.  Both solver paths
+are timed: the mixed path (FP32 V-cycle and Schwarz inverses, FP64 FGMRES,
+true-residual products and coarse LU) gives `value`; the plain FP64 path is
+reported under `fp64_path`.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 For N > 1 (torchrun) every rank runs an independent replica of the workload
@@ -30,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 from paper_1709_05660_gb300.workloads import CONFIGS, noise  # noqa: E402
 
-METRIC = "Newton-step solves/s (rel. residual 1e-10, FP64 path)"
+METRIC = "Newton-step solves/s (FGMRES to true rel. residual 1e-10; mixed FP32/FP64 vs FP64 path)"
 UNIT = "solves/s"
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -210,24 +213,14 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, rank, world):
+def _measure(args, prec, stream, barrier, dist, world, local):
+    """Times args.steps Newton steps of one precision; returns a result dict."""
     import torch
+    from dataclasses import replace
     from paper_1709_05660_gb300 import fsi
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    cfg = args.config
-    prob, opts = CONFIGS[cfg]
-    stream = torch.cuda.current_stream()
+    prob, opts = CONFIGS[args.config]
+    opts = replace(opts, precision=prec)
     s = fsi.FSI(prob, opts, stream=stream.cuda_stream)
     N = int(s.N[-1])
     nz = torch.tensor(noise(N, 0), dtype=torch.float64, device="cuda")
@@ -250,10 +243,11 @@ def run_gpu(args, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    iters = []
+    iters, rel_res = [], []
     for _ in range(args.steps):
         rel, st = step()
         iters.append(st.iters)
+        rel_res.append(st.rel_res)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -266,9 +260,10 @@ def run_gpu(args, rank, world):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
-
+    out = {"N": N, "ms": ms, "per_step": ms / args.steps, "value": world * args.steps / (ms / 1e3),
+           "iters": iters, "rel_res": max(rel_res), "rel_step": rel, "kst": kst, "launches": launches,
+           "clocks": clk, "hbm_bytes": s.hbm_bytes,
+           "phase_ms": {"assemble": st.t_assemble_ms, "factor": st.t_factor_ms, "solve": st.t_solve_ms}}
     # end-to-end through the C-ABI with host buffers (pinned), copies inside the timed region
     yh = y0.cpu().pin_memory()
     dxh = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -288,18 +283,21 @@ def run_gpu(args, rank, world):
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 8,
-           "d2h_bytes_per_step": N * 8}
+    out["e2e"] = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+                  "d2h_bytes_per_step": N * 8}
+    s.close()
+    return out
 
-    # roofline of the dominant kernel class in the timed region
+
+def _roofline(kst, steps):
     peaks, kind = _peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
     dom = max(kst, key=lambda k: kst[k]["ms"])
     d = kst[dom]
     per_launch_ms = d["ms"] / max(1, d["launches"])
     if dom in HBM_BOUND:
-        peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_source": kind}
     else:
         peak = FP64_ALU_PEAK_GFLOPS
@@ -308,38 +306,63 @@ def run_gpu(args, rank, world):
                 "frac": achieved / peak, "peak_source": "derived FP64 ALU peak (152 SM x 2.07 GHz x 4 flop/clk)"}
     roof.update({"kernel": dom, "traffic": _traffic(dom), "launches": d["launches"],
                  "avg_launch_ms": per_launch_ms})
-    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
-    classes = {k: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"],
+    classes = {k: {"ms_per_step": v["ms"] / steps, "launches": v["launches"],
                    "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None,
                    "hbm_frac": (v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm_peak) if v["ms"] > 0 else None,
                    "GFLOPs": (v["flops"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                for k, v in kst.items()}
+    return roof, classes
 
+
+def run_gpu(args, rank, world):
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    prob, opts = CONFIGS[args.config]
+    main = _measure(args, 1, stream, barrier, dist, world, local)        # mixed FP32 / FP64
+    fp64 = _measure(args, 0, stream, barrier, dist, world, local) if not args.mixed_only else None
+    roof, classes = _roofline(main["kst"], args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, detail = OracleSampler(cfg).sample(args.cpu_frac, int(round(statistics.mean(iters))))
+        est, detail = OracleSampler(args.config).sample(args.cpu_frac, int(round(statistics.mean(main["iters"]))))
         cpu = {"value": 1.0 / est, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                "sample": f"{args.cpu_frac:.3f} of the finest-level element assembly and of each level's "
                          f"Schwarz block LUs (scaled), full Galerkin hierarchy and coarse LU, one FGMRES "
                          f"iteration scaled by the GPU's iteration count", "detail": detail}
-    ws_bytes = s.hbm_bytes
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded channel-with-flap state)",
-            "config": {"workload": cfg, "unknowns": N, "levels": prob.levels, "tile": list(opts.tile),
-                       "mu_s": prob.mu_s, "U": prob.U, "restart": opts.restart, "rtol": opts.rtol,
-                       "smoothing": [opts.n_pre, opts.n_post], "omega": opts.omega,
-                       "l2": f"working set {ws_bytes / 1e9:.2f} GB > L2 (129 MB); no flush",
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded channel-with-flap state)",
+            "config": {"workload": args.config, "unknowns": main["N"], "levels": prob.levels,
+                       "tile": list(opts.tile), "mu_s": prob.mu_s, "U": prob.U, "restart": opts.restart,
+                       "rtol": opts.rtol, "smoothing": [opts.n_pre, opts.n_post], "omega": opts.omega,
+                       "precision": "mixed: FP32 V-cycle and Schwarz inverses, FP64 FGMRES / SpMV / coarse LU",
+                       "l2": f"working set {main['hbm_bytes'] / 1e9:.2f} GB > L2 (129 MB); no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "fgmres_iters": iters, "rel_step": rel,
-            "phase_ms": {"assemble": st.t_assemble_ms, "factor": st.t_factor_ms, "solve": st.t_solve_ms},
-            "roofline": roof, "kernel_classes": classes, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk,
+            "fgmres_iters": main["iters"], "max_true_rel_residual": main["rel_res"], "rel_step": main["rel_step"],
+            "phase_ms": main["phase_ms"], "roofline": roof, "kernel_classes": classes, "cpu_baseline": cpu,
+            "e2e": main["e2e"], "gpu_launches": main["launches"], "clocks": main["clocks"],
         }
+        if fp64 is not None:
+            r64, c64 = _roofline(fp64["kst"], args.steps)
+            line["fp64_path"] = {"value": fp64["value"], "ms_per_step": fp64["per_step"],
+                                 "fgmres_iters": fp64["iters"], "max_true_rel_residual": fp64["rel_res"],
+                                 "phase_ms": fp64["phase_ms"], "e2e": fp64["e2e"], "gpu_launches": fp64["launches"],
+                                 "roofline": r64, "kernel_classes": c64, "clocks": fp64["clocks"]}
+            line["mixed_over_fp64"] = main["value"] / fp64["value"]
         print(json.dumps(line), flush=True)
-    s.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -365,6 +388,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="c2_2d_l5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-only", action="store_true", help="skip the FP64-path measurement")
     ap.add_argument("--cpu-frac", type=float, default=0.25)
     ap.add_argument("--ref-frac", type=float, default=1.0 / 16)
     ap.add_argument("--ref-iters", type=int, default=15)

@@ -215,6 +215,7 @@ void build_device(Ctx& c) {
       D.R_ptr = upload(c, H.R_ptr); D.R_col = upload(c, H.R_col); D.R_val = upload(c, H.R_val);
       D.n_patches = H.n_patches;
       D.max_n = H.max_n;
+      D.max_nown = H.max_nown;
       D.p_n = upload(c, H.p_n); D.p_nown = upload(c, H.p_nown);
       D.p_idx_off = upload(c, H.p_idx_off); D.p_own_off = upload(c, H.p_own_off);
       D.p_dense_off = upload(c, H.p_dense_off); D.p_inv_off = upload(c, H.p_inv_off);
@@ -223,11 +224,20 @@ void build_device(Ctx& c) {
       D.p_gmap = upload(c, H.p_gmap); D.p_padpos = upload(c, H.p_padpos);
       D.inv_total = H.inv_total;
       D.dense_total = H.dense_total;
-      D.inv = dalloc<double>(c, (size_t)H.inv_total);
+      if (c.mixed) {
+        D.inv32 = dalloc<float>(c, (size_t)H.inv_total);
+        D.val32 = dalloc<float>(c, (size_t)H.nnzb * B * B);
+        std::vector<float> pv(H.P_val.begin(), H.P_val.end()), rv(H.R_val.begin(), H.R_val.end());
+        D.P_val32 = upload(c, pv);
+        D.R_val32 = upload(c, rv);
+      } else {
+        D.inv = dalloc<double>(c, (size_t)H.inv_total);
+      }
       max_dense = std::max(max_dense, H.dense_total);
       for (int p = 0; p < H.n_patches; ++p) {
         const double n = H.p_n[p], no = H.p_nown[p];
         D.apply_bytes += no * n * 8.0 + n * 12.0 + no * 20.0;
+        D.apply_bytes32 += no * n * 4.0 + n * 8.0 + no * 12.0;
         D.apply_flops += 2.0 * no * n;
         D.factor_flops += 2.0 * n * n * n;
         D.factor_bytes += n * n * 8.0 + no * n * 8.0;
@@ -235,9 +245,20 @@ void build_device(Ctx& c) {
       D.factor_bytes += (double)H.p_gmap.size() / 3.0 * (B * B * 8.0 + 12.0);
       D.R_bytes = (double)H.R_col.size() * 12.0 + (double)H.Ni * 8.0 + (double)c.hl[l - 1].Ni * 8.0;
       D.P_bytes = (double)H.P_col.size() * 12.0 + (double)H.Ni * 16.0 + (double)c.hl[l - 1].Ni * 8.0;
+      D.R_bytes32 = (double)H.R_col.size() * 8.0 + (double)H.Ni * 4.0 + (double)c.hl[l - 1].Ni * 4.0;
+      D.P_bytes32 = (double)H.P_col.size() * 8.0 + (double)H.Ni * 8.0 + (double)c.hl[l - 1].Ni * 4.0;
     }
     D.spmv_bytes = (double)H.nnzb * (B * B * 8.0 + 4.0) + (double)(H.nb + 1) * 4.0 + 3.0 * H.Ni * 8.0;
     D.spmv_flops = 2.0 * (double)H.nnzb * B * B;
+    D.spmv_bytes32 = (double)H.nnzb * (B * B * 4.0 + 4.0) + (double)(H.nb + 1) * 4.0 + 3.0 * H.Ni * 4.0;
+    if (c.mixed) {
+      D.x32 = dalloc<float>(c, H.Ni);
+      D.b32 = dalloc<float>(c, H.Ni);
+      D.r32 = dalloc<float>(c, H.Ni);
+      ck(cudaMemsetAsync(D.x32, 0, H.Ni * sizeof(float), c.stream), "memset");
+      ck(cudaMemsetAsync(D.b32, 0, H.Ni * sizeof(float), c.stream), "memset");
+      ck(cudaMemsetAsync(D.r32, 0, H.Ni * sizeof(float), c.stream), "memset");
+    }
     D.x = dalloc<double>(c, H.Ni);
     D.b = dalloc<double>(c, H.Ni);
     D.r = dalloc<double>(c, H.Ni);
@@ -252,7 +273,8 @@ void build_device(Ctx& c) {
   c.res = dalloc<double>(c, Ni);
   ck(cudaMemsetAsync(c.y, 0, Ni * sizeof(double), c.stream), "memset");
   c.V = dalloc<double>(c, (size_t)(m + 1) * Ni);
-  c.Z = dalloc<double>(c, (size_t)m * Ni);
+  if (c.mixed) c.Z32 = dalloc<float>(c, (size_t)m * Ni);
+  else c.Z = dalloc<double>(c, (size_t)m * Ni);
   c.w = dalloc<double>(c, Ni);
   c.xk = dalloc<double>(c, Ni);
   c.bk = dalloc<double>(c, Ni);
@@ -346,6 +368,14 @@ void assemble(Ctx& c, bool want_res) {
     launch_dirichlet(Co.dir_list, Co.n_dir, Co.rowptr, Co.col, Co.val, B, nullptr, nullptr, nullptr, c.stream);
     counted(c);
   }
+  if (c.mixed)
+    for (int l = 1; l < L; ++l) {
+      DevLevel& D = c.dl[l];
+      const int64_t nv = D.nnzb * B * B;
+      Prof pr(c, FSI_K_SCATTER, (double)nv * 12.0, 0.0);
+      launch_to_f32(nv, D.val, D.val32, c.stream);
+      counted(c);
+    }
   check_status(c);
   (void)want_res;
 }
@@ -359,10 +389,18 @@ void factor(Ctx& c) {
   for (int l = 1; l < L; ++l) {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_FACTOR, D.factor_bytes, D.factor_flops, 2);
-    launch_patch_gather(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off, D.p_padpos, D.val, B,
-                        c.dense_ws, c.stream);
-    launch_patch_gj(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own, D.p_inv_off,
-                    c.dense_ws, D.inv, c.status, c.stream);
+    if (c.mixed) {
+      float* ws = reinterpret_cast<float*>(c.dense_ws);
+      launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
+                                   D.p_padpos, D.val, B, ws, c.stream);
+      launch_patch_gj_t<float>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
+                               D.p_inv_off, ws, D.inv32, c.status, c.stream);
+    } else {
+      launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
+                                    D.p_padpos, D.val, B, c.dense_ws, c.stream);
+      launch_patch_gj_t<double>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
+                                D.p_inv_off, c.dense_ws, D.inv, c.status, c.stream);
+    }
     counted(c, 2);
   }
   DevLevel& C = c.dl[0];
@@ -389,44 +427,116 @@ void spmv(Ctx& c, int l, const double* x, const double* b, double* y) {
   counted(c);
 }
 
-void smooth_step(Ctx& c, int l, const double* b, double* x, bool x_is_zero) {
-  DevLevel& D = c.dl[l];
-  const double* r = b;
-  if (!x_is_zero) {
-    spmv(c, l, x, b, D.r);
-    r = D.r;
+// Level data of the V-cycle in precision T (double: FP64 path, float: mixed).
+template <typename T> struct VC;
+template <> struct VC<double> {
+  static double* x(DevLevel& D) { return D.x; }
+  static double* b(DevLevel& D) { return D.b; }
+  static double* r(DevLevel& D) { return D.r; }
+  static void residual(Ctx& c, int l, const double* x, const double* b, double* y) { spmv(c, l, x, b, y); }
+  static void apply(Ctx& c, int l, const double* r, double* x) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes, D.apply_flops);
+    launch_patch_apply_t<double>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
+                                 D.p_own_off, D.p_own, D.p_inv_off, D.inv, r, x, c.opts.omega, c.stream);
+    counted(c);
   }
-  Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes, D.apply_flops);
-  launch_patch_apply(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off, D.p_own, D.p_inv_off,
-                     D.inv, r, x, c.opts.omega, c.stream);
-  counted(c);
-}
-
-void vcycle(Ctx& c, int l, const double* b, double* x) {
-  if (l == 0) {
+  static void restrict_(Ctx& c, int l, const double* r, double* bc) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_TRANSFER, D.R_bytes, 2.0 * (double)c.hl[l].R_col.size());
+    launch_csr_spmv(c.dl[l - 1].Ni, D.R_ptr, D.R_col, D.R_val, r, bc, false, c.stream);
+    counted(c);
+  }
+  static void prolong_add(Ctx& c, int l, const double* xc, double* x) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_TRANSFER, D.P_bytes, 2.0 * (double)c.hl[l].P_col.size());
+    launch_csr_spmv(D.Ni, D.P_ptr, D.P_col, D.P_val, xc, x, true, c.stream);
+    counted(c);
+  }
+  static void coarse(Ctx& c, const double* b, double* x) {
     const double n0 = (double)c.dl[0].Ni;
     Prof pr(c, FSI_K_TRANSFER, n0 * n0 * 8.0 + 2.0 * n0 * 8.0, 2.0 * n0 * n0);
     launch_gemv(c.dl[0].Ni, c.c_inv, b, x, c.stream);
     counted(c);
+  }
+};
+template <> struct VC<float> {
+  static float* x(DevLevel& D) { return D.x32; }
+  static float* b(DevLevel& D) { return D.b32; }
+  static float* r(DevLevel& D) { return D.r32; }
+  static void residual(Ctx& c, int l, const float* x, const float* b, float* y) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_SPMV, D.spmv_bytes32, D.spmv_flops);
+    launch_bsr_residual_f32(c.B, D.nb, D.rowptr, D.col, D.val32, x, b, y, c.stream);
+    counted(c);
+  }
+  static void apply(Ctx& c, int l, const float* r, float* x) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes32, D.apply_flops);
+    launch_patch_apply_t<float>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
+                                D.p_own_off, D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, c.stream);
+    counted(c);
+  }
+  static void restrict_(Ctx& c, int l, const float* r, float* bc) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_TRANSFER, D.R_bytes32, 2.0 * (double)c.hl[l].R_col.size());
+    launch_csr_spmv_f32(c.dl[l - 1].Ni, D.R_ptr, D.R_col, D.R_val32, r, bc, false, c.stream);
+    counted(c);
+  }
+  static void prolong_add(Ctx& c, int l, const float* xc, float* x) {
+    DevLevel& D = c.dl[l];
+    Prof pr(c, FSI_K_TRANSFER, D.P_bytes32, 2.0 * (double)c.hl[l].P_col.size());
+    launch_csr_spmv_f32(D.Ni, D.P_ptr, D.P_col, D.P_val32, xc, x, true, c.stream);
+    counted(c);
+  }
+  static void coarse(Ctx& c, const float* b, float* x) {
+    // the coarsest-grid solve stays FP64 (FP64 inverse, FP64 accumulation)
+    const double n0 = (double)c.dl[0].Ni;
+    Prof pr(c, FSI_K_TRANSFER, n0 * n0 * 8.0 + 2.0 * n0 * 4.0, 2.0 * n0 * n0);
+    launch_gemv_f32io(c.dl[0].Ni, c.c_inv, b, x, c.stream);
+    counted(c);
+  }
+};
+
+template <typename T>
+void smooth_step_t(Ctx& c, int l, const T* b, T* x, bool x_is_zero) {
+  DevLevel& D = c.dl[l];
+  const T* r = b;
+  if (!x_is_zero) {
+    VC<T>::residual(c, l, x, b, VC<T>::r(D));
+    r = VC<T>::r(D);
+  }
+  VC<T>::apply(c, l, r, x);
+}
+
+template <typename T>
+void vcycle_t(Ctx& c, int l, const T* b, T* x) {
+  if (l == 0) {
+    VC<T>::coarse(c, b, x);
     return;
   }
   DevLevel& D = c.dl[l];
   DevLevel& C = c.dl[l - 1];
-  ck(cudaMemsetAsync(x, 0, D.Ni * sizeof(double), c.stream), "memset");
-  for (int s = 0; s < c.opts.n_pre; ++s) smooth_step(c, l, b, x, s == 0);
-  spmv(c, l, x, b, D.r);
-  {
-    Prof pr(c, FSI_K_TRANSFER, D.R_bytes, 2.0 * (double)c.hl[l].R_col.size());
-    launch_csr_spmv(C.Ni, D.R_ptr, D.R_col, D.R_val, D.r, C.b, false, c.stream);
-    counted(c);
+  ck(cudaMemsetAsync(x, 0, D.Ni * sizeof(T), c.stream), "memset");
+  for (int s = 0; s < c.opts.n_pre; ++s) smooth_step_t<T>(c, l, b, x, s == 0);
+  VC<T>::residual(c, l, x, b, VC<T>::r(D));
+  VC<T>::restrict_(c, l, VC<T>::r(D), VC<T>::b(C));
+  vcycle_t<T>(c, l - 1, VC<T>::b(C), VC<T>::x(C));
+  VC<T>::prolong_add(c, l, VC<T>::x(C), x);
+  for (int s = 0; s < c.opts.n_post; ++s) smooth_step_t<T>(c, l, b, x, false);
+}
+
+// z = M^{-1} v on the finest level (FP64 in and out; FP32 inside on the mixed path)
+void precondition(Ctx& c, const double* v, double* z64, float* z32) {
+  const int L = (int)c.dl.size();
+  if (!c.mixed) {
+    vcycle_t<double>(c, L - 1, v, z64);
+    return;
   }
-  vcycle(c, l - 1, C.b, C.x);
-  {
-    Prof pr(c, FSI_K_TRANSFER, D.P_bytes, 2.0 * (double)c.hl[l].P_col.size());
-    launch_csr_spmv(D.Ni, D.P_ptr, D.P_col, D.P_val, C.x, x, true, c.stream);
-    counted(c);
-  }
-  for (int s = 0; s < c.opts.n_post; ++s) smooth_step(c, l, b, x, false);
+  DevLevel& F = c.dl[L - 1];
+  launch_to_f32(F.Ni, v, F.b32, c.stream);
+  counted(c);
+  vcycle_t<float>(c, L - 1, F.b32, z32);
 }
 
 // ---------------------------------------------------------------------------
@@ -464,9 +574,17 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
     int k = 0;
     for (int j = 0; j < m; ++j) {
       double* vj = c.V + (size_t)j * n;
-      double* zj = c.Z + (size_t)j * n;
-      vcycle(c, L - 1, vj, zj);
-      spmv(c, L - 1, zj, nullptr, c.w);
+      if (c.mixed) {
+        float* zj = c.Z32 + (size_t)j * n;
+        precondition(c, vj, nullptr, zj);
+        Prof pr(c, FSI_K_SPMV, F.spmv_bytes - n * 4.0, F.spmv_flops);
+        launch_bsr_apply_mixed(c.B, F.nb, F.rowptr, F.col, F.val, zj, c.w, c.stream);
+        counted(c);
+      } else {
+        double* zj = c.Z + (size_t)j * n;
+        precondition(c, vj, zj, nullptr);
+        spmv(c, L - 1, zj, nullptr, c.w);
+      }
       Prof pr(c, FSI_K_KRYLOV, (4.0 * (j + 1) + 10.0) * n * 8.0, (8.0 * (j + 1) + 6.0) * n, 11);
       launch_norm_partial(n, c.w, c.partial, nb, c.stream);
       launch_reduce(c.partial, 1, nb, sm + 256, true, c.stream);
@@ -510,7 +628,8 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
     }
     std::memcpy(hs + 384, yv.data(), k * sizeof(double));
     ck(cudaMemcpyAsync(sm + 384, hs + 384, k * sizeof(double), cudaMemcpyHostToDevice, c.stream), "H2D");
-    launch_combo(n, c.Z, n, k, sm + 384, x, c.stream);
+    if (c.mixed) launch_combo_mixed(n, c.Z32, n, k, sm + 384, x, c.stream);
+    else launch_combo(n, c.Z, n, k, sm + 384, x, c.stream);
     launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, x, b, c.w, c.stream);
     counted(c, 2);
     beta = dev_norm(c, n, c.w, sm + 301);
@@ -569,7 +688,7 @@ extern "C" {
 
 static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts* opts) {
   if (desc->transient != 0) throw ApiError(FSI_E_INVALID, "only steady problems are supported");
-  if (opts->precision != FSI_FP64) throw ApiError(FSI_E_INVALID, "only FSI_FP64 is supported");
+  if (opts->precision != FSI_FP64 && opts->precision != FSI_MIXED) throw ApiError(FSI_E_INVALID, "bad precision");
   if (opts->restart < 1 || opts->restart > 64) throw ApiError(FSI_E_INVALID, "restart must be in [1, 64]");
   if (opts->n_pre < 0 || opts->n_post < 0 || opts->max_iters < 1 || !(opts->rtol > 0.0))
     throw ApiError(FSI_E_INVALID, "bad solver options");
@@ -609,6 +728,7 @@ int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opt
   int rc = guard(c, [&] {
     if (desc->dim != 2) throw ApiError(FSI_E_INVALID, "the device path supports dim = 2");
     plan(c, desc, opts);
+    c->mixed = opts->precision == FSI_MIXED;
     int dev = 0;
     ck(cudaGetDevice(&dev), "cudaGetDevice");
     ck(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev), "attr");
@@ -959,7 +1079,14 @@ int fsi_apply_vcycle(fsi_ctx* c, const double* b, double* z) {
     need_device(*c);
     const int L = (int)c->dl.size();
     to_internal(*c, L - 1, b, c->bk);
-    vcycle(*c, L - 1, c->bk, c->xk);
+    if (c->mixed) {
+      DevLevel& F = c->dl[L - 1];
+      precondition(*c, c->bk, nullptr, F.x32);
+      launch_axpby_f32_to_f64(F.Ni, F.x32, c->xk, c->stream);
+      counted(*c);
+    } else {
+      precondition(*c, c->bk, c->xk, nullptr);
+    }
     to_canonical(*c, L - 1, c->xk, z);
     sync(*c);
   });
@@ -972,7 +1099,15 @@ int fsi_apply_smoother(fsi_ctx* c, int level, const double* b, const double* x, 
     DevLevel& D = c->dl[level];
     to_internal(*c, level, b, D.b);
     to_internal(*c, level, x, D.x);
-    smooth_step(*c, level, D.b, D.x, false);
+    if (c->mixed) {
+      launch_to_f32(D.Ni, D.b, D.b32, c->stream);
+      launch_to_f32(D.Ni, D.x, D.x32, c->stream);
+      smooth_step_t<float>(*c, level, D.b32, D.x32, false);
+      launch_axpby_f32_to_f64(D.Ni, D.x32, D.x, c->stream);
+      counted(*c, 3);
+    } else {
+      smooth_step_t<double>(*c, level, D.b, D.x, false);
+    }
     to_canonical(*c, level, D.x, x_out);
     sync(*c);
   });

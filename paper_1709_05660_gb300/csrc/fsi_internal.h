@@ -62,7 +62,7 @@ struct HostLevel {
   std::vector<int32_t> p_elems;                // elements of each patch (for export)
   std::vector<int64_t> p_elem_off;
   int64_t dense_total = 0, inv_total = 0, idx_total = 0, own_total = 0;
-  int max_n = 0;
+  int max_n = 0, max_nown = 0;
 };
 
 bool build_host_hierarchy(const fsi_problem_desc& d, const fsi_solver_opts& o,
@@ -94,7 +94,7 @@ struct DevLevel {
   int32_t *P_ptr = nullptr, *P_col = nullptr, *R_ptr = nullptr, *R_col = nullptr;
   double *P_val = nullptr, *R_val = nullptr;
   // patches
-  int n_patches = 0, max_n = 0;
+  int n_patches = 0, max_n = 0, max_nown = 0;
   int32_t *p_n = nullptr, *p_nown = nullptr;
   int64_t *p_idx_off = nullptr, *p_own_off = nullptr, *p_dense_off = nullptr, *p_inv_off = nullptr,
           *p_gmap_off = nullptr, *p_pad_off = nullptr;
@@ -103,7 +103,11 @@ struct DevLevel {
   int64_t inv_total = 0, dense_total = 0;
   // work vectors (internal layout)
   double *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  // mixed-precision copies (FSI_MIXED): FP32 values, inverses, vectors
+  float *val32 = nullptr, *inv32 = nullptr, *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+  float *P_val32 = nullptr, *R_val32 = nullptr;
   // algorithmic traffic / arithmetic of one launch (profiling)
+  double apply_bytes32 = 0, spmv_bytes32 = 0, R_bytes32 = 0, P_bytes32 = 0;
   double apply_bytes = 0, apply_flops = 0, spmv_bytes = 0, spmv_flops = 0;
   double factor_bytes = 0, factor_flops = 0, R_bytes = 0, P_bytes = 0;
 };
@@ -123,6 +127,8 @@ struct Ctx {
   // finest-level state and vectors (internal layout)
   double *y = nullptr, *res = nullptr;
   double *V = nullptr, *Z = nullptr;     // Krylov bases
+  float* Z32 = nullptr;                  // preconditioned vectors (mixed path)
+  bool mixed = false;
   double *w = nullptr, *xk = nullptr, *bk = nullptr, *tmp = nullptr;
   double* partial = nullptr;              // reduction partials
   double* small = nullptr;                // device scalars

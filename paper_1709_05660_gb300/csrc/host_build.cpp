@@ -334,6 +334,7 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
   L.p_elem_off.assign(np + 1, 0);
   L.p_idx.clear(); L.p_own.clear(); L.p_gmap.clear(); L.p_padpos.clear(); L.p_elems.clear();
   L.max_n = 0;
+  L.max_nown = 0;
   for (int p = 0; p < np; ++p) {
     std::vector<int32_t> nodes;
     for (int32_t e : pel[p])
@@ -359,6 +360,7 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
       }
     }
     L.p_nown[p] = nown;
+    L.max_nown = std::max(L.max_nown, nown);
     for (int lb = 0; lb < nbk; ++lb) {
       const int32_t br = blocks[lb];
       for (int32_t k = L.rowptr[br]; k < L.rowptr[br + 1]; ++k) {

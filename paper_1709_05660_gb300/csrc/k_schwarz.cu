@@ -1,0 +1,412 @@
+// Restricted additive Schwarz blocks of the Richardson smoother (Sec. 3.3),
+// templated on the storage precision T (double: FP64 path, float: mixed path).
+//
+//  * k_patch_gather: B_k = J_l[R^delta_k, R^delta_k] copied from the BSR values
+//    of level l into a dense n_k x n_k workspace (padding slots get 1 on the
+//    diagonal so every block stays invertible).
+//  * k_patch_gj: in-place Gauss-Jordan with partial (row) pivoting, one thread
+//    block per Schwarz block.  Only the rows of B_k^{-1} that belong to R^0_k
+//    are written out, transposed (column-major in the owned row index) so the
+//    smoother's batched product reads them with coalesced loads.
+//  * k_patch_apply: x[own] += omega * (B_k^{-1} r[R^delta_k])[own]; one thread
+//    per owned row, the block residual broadcast from shared memory.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace fsi {
+
+namespace {
+constexpr int kWarp = 32;
+
+__device__ int block_argmax_abs(double v, int idx, double* sv, int* si) {
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, v, o);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) { v = ov; idx = oi; }
+  }
+  __syncthreads();
+  if (lane == 0) { sv[wid] = v; si[wid] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + kWarp - 1) / kWarp;
+    double bv = sv[0];
+    int bi = si[0];
+    for (int w = 1; w < nw; ++w)
+      if (sv[w] > bv || (sv[w] == bv && si[w] >= 0 && (bi < 0 || si[w] < bi))) { bv = sv[w]; bi = si[w]; }
+    si[0] = bi;
+  }
+  __syncthreads();
+  const int r = si[0];
+  __syncthreads();
+  return r;
+}
+}  // namespace
+
+template <typename T>
+__global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t* __restrict__ dense_off,
+                                 const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
+                                 const int64_t* __restrict__ pad_off, const int32_t* __restrict__ padpos,
+                                 const double* __restrict__ bsr_val, int B, T* __restrict__ dense) {
+  const int p = blockIdx.x;
+  const int n = p_n[p];
+  T* D = dense + dense_off[p];
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) D[t] = T(0);
+  __syncthreads();
+  const int BB = B * B;
+  const int64_t g0 = gmap_off[p], g1 = gmap_off[p + 1];
+  for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
+    const int64_t g = g0 + t / BB;
+    const int e = (int)(t % BB), ci = e / B, cj = e % B;
+    const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
+    D[(int64_t)(lr * B + ci) * n + lc * B + cj] = T(bsr_val[(int64_t)blk * BB + e]);
+  }
+  __syncthreads();
+  for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
+    const int q = padpos[t];
+    D[(int64_t)q * n + q] = T(1);
+  }
+}
+
+// Step k pivots on the unused row p with the largest |M[p][k]|; all rows are
+// updated from shared-memory copies of row p and column k, so no element is
+// read after it was overwritten in the same step.  Rows whose multiplier is
+// exactly zero are skipped (most of a Schwarz block is zero early on).  At the
+// end M[p_k][q_c] = (B^{-1})[k][c], q the inverse pivot permutation.
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(512)
+k_patch_gj_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
+             const int64_t* __restrict__ dense_off, const int64_t* __restrict__ own_off,
+             const int32_t* __restrict__ own, const int64_t* __restrict__ inv_off, T* __restrict__ dense,
+             T* __restrict__ invT, int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = blockIdx.x;
+  const int n = p_n[p];
+  T* prow = reinterpret_cast<T*>(smem_raw);
+  T* pcol = prow + n;
+  int* piv = reinterpret_cast<int*>(pcol + n);
+  int* qinv = piv + n;
+  uint8_t* used = reinterpret_cast<uint8_t*>(qinv + n);
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_sing;
+  __shared__ T tile[32][33];
+  T* Mg = dense + dense_off[p];
+  T* M = Mg;
+  if (SMEM) {
+    M = reinterpret_cast<T*>(used + ((n + 15) / 16) * 16);
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) M[t] = Mg[t];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
+  if (threadIdx.x == 0) s_sing = 0;
+  __syncthreads();
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = -1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (used[i]) continue;
+      double a = fabs((double)M[(int64_t)i * n + k]);
+      if (!(a >= 0.0)) a = 0.0;   // NaN never wins, but an unused row always exists
+      if (a > best) { best = a; bi = i; }
+    }
+    const int pr = block_argmax_abs(best, bi, sv, si);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      prow[j] = M[(int64_t)pr * n + j];
+      pcol[j] = M[(int64_t)j * n + k];
+    }
+    if (threadIdx.x == 0) { used[pr] = 1; piv[k] = pr; }
+    __syncthreads();
+    T pv = prow[k];
+    if (!(fabs((double)pv) > 0.0) || !isfinite((double)pv)) {
+      if (threadIdx.x == 0) s_sing = 1;
+      pv = T(1);
+    }
+    const T rp = T(1) / pv;
+    for (int i = wid; i < n; i += nw) {
+      T* Mi = M + (int64_t)i * n;
+      if (i == pr) {
+        for (int j = lane; j < n; j += kWarp) Mi[j] = (j == k) ? rp : prow[j] * rp;
+      } else {
+        const T f = pcol[i] * rp;
+        if (f != T(0))
+          for (int j = lane; j < n; j += kWarp) Mi[j] = (j == k) ? -f : Mi[j] - f * prow[j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
+  __syncthreads();
+  // owned rows of the inverse, written transposed through a shared tile
+  const int nown = p_nown[p];
+  const int32_t* ow = own + own_off[p];
+  T* out = invT + inv_off[p];
+  for (int o0 = 0; o0 < nown; o0 += 32) {
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int oo = t / 32, cc = t % 32;
+        const int o = o0 + oo, c = c0 + cc;
+        if (o < nown && c < n) tile[oo][cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int cc = t / 32, oo = t % 32;
+        const int o = o0 + oo, c = c0 + cc;
+        if (o < nown && c < n) out[(int64_t)c * nown + o] = tile[oo][cc];
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
+}
+
+// Panel-blocked form of the same in-place Gauss-Jordan sweep.  For a panel of
+// W columns K = [k0, k0+W): (1) the n x W panel G = M[:, K] is swept in shared
+// memory (pivot search and rank-1 updates touch only panel columns); (2) the
+// pivot rows P of the panel are read from M (old values) into R; (3) the
+// panel is written back; (4) every other column is updated at once by the
+// composite transform of the W steps, M[:, rest] += (G - E_P) R[:, rest],
+// with E_P the identity columns at the pivot rows - a rank-W update that reads
+// and writes each block once per panel instead of once per pivot step.
+template <typename T, int W>
+__global__ void __launch_bounds__(512)
+k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
+               const int64_t* __restrict__ dense_off, const int64_t* __restrict__ own_off,
+               const int32_t* __restrict__ own, const int64_t* __restrict__ inv_off, T* __restrict__ dense,
+               T* __restrict__ invT, int32_t* __restrict__ status, int max_n) {
+  constexpr int GS = W + 1;   // padded panel row stride (bank conflicts)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = blockIdx.x;
+  const int n = p_n[p];
+  // regions sized for the largest block of the launch (max_n), so the output
+  // tile (32 x 33, placed in G; the host checks max_n * GS >= 32 * 33) never
+  // overlaps the pivot arrays, whatever this block's n
+  T* G = reinterpret_cast<T*>(smem_raw);              // max_n * GS
+  T* R = G + (size_t)max_n * GS;                      // W * max_n
+  T* pcol = R + (size_t)W * max_n;                    // max_n
+  T* prow = pcol + max_n;                             // W
+  int* piv = reinterpret_cast<int*>(prow + W);        // max_n
+  int* qinv = piv + max_n;                            // max_n
+  uint8_t* used = reinterpret_cast<uint8_t*>(qinv + max_n);   // max_n
+  uint8_t* live = used + max_n;                       // max_n: row touched by this panel
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_sing;
+  T* M = dense + dense_off[p];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
+  if (threadIdx.x == 0) s_sing = 0;
+  __syncthreads();
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+  for (int k0 = 0; k0 < n; k0 += W) {
+    const int wp = min(W, n - k0);
+    for (int i = wid; i < n; i += nw)
+      for (int m = lane; m < W; m += kWarp) G[i * GS + m] = m < wp ? M[(int64_t)i * n + k0 + m] : T(0);
+    __syncthreads();
+    for (int m = 0; m < wp; ++m) {
+      double best = -1.0;
+      int bi = -1;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (used[i]) continue;
+        double a = fabs((double)G[i * GS + m]);
+        if (!(a >= 0.0)) a = 0.0;
+        if (a > best) { best = a; bi = i; }
+      }
+      const int pr = block_argmax_abs(best, bi, sv, si);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) pcol[i] = G[i * GS + m];
+      if (threadIdx.x < W) prow[threadIdx.x] = G[pr * GS + threadIdx.x];
+      if (threadIdx.x == 0) { used[pr] = 1; piv[k0 + m] = pr; }
+      __syncthreads();
+      T pv = prow[m];
+      if (!(fabs((double)pv) > 0.0) || !isfinite((double)pv)) {
+        if (threadIdx.x == 0) s_sing = 1;
+        pv = T(1);
+      }
+      const T rp = T(1) / pv;
+      for (int i = wid; i < n; i += nw) {
+        if (lane >= wp) continue;
+        T* Gi = G + i * GS;
+        if (i == pr) {
+          Gi[lane] = (lane == m) ? rp : prow[lane] * rp;
+        } else {
+          const T f = pcol[i] * rp;
+          if (f != T(0)) Gi[lane] = (lane == m) ? -f : Gi[lane] - f * prow[lane];
+        }
+      }
+      __syncthreads();
+    }
+    // old pivot rows, panel write-back, G - E_P, live rows
+    for (int m = wid; m < wp; m += nw) {
+      const T* Mp = M + (int64_t)piv[k0 + m] * n;
+      for (int j = lane; j < n; j += kWarp) R[m * n + j] = Mp[j];
+    }
+    for (int i = wid; i < n; i += nw)
+      if (lane < wp) M[(int64_t)i * n + k0 + lane] = G[i * GS + lane];
+    __syncthreads();
+    if (threadIdx.x < wp) G[piv[k0 + threadIdx.x] * GS + threadIdx.x] -= T(1);
+    __syncthreads();
+    for (int i = wid; i < n; i += nw) {
+      const bool nz = lane < wp && G[i * GS + lane] != T(0);
+      const unsigned any = __ballot_sync(0xffffffffu, nz);
+      if (lane == 0) live[i] = any != 0u;
+    }
+    __syncthreads();
+    // trailing rank-wp update, 4 rows per warp pass sharing each R load
+    for (int g = wid; 4 * g < n; g += nw) {
+      const int i0 = 4 * g;
+      bool any = false;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) any |= (i0 + r < n) && live[i0 + r];
+      if (!any) continue;
+      for (int j = lane; j < n; j += kWarp) {
+        if (j >= k0 && j < k0 + wp) continue;
+        T acc[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] = T(0);
+        for (int m = 0; m < wp; ++m) {
+          const T rv = R[m * n + j];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (i0 + r < n) acc[r] += G[(i0 + r) * GS + m] * rv;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i0 + r < n && live[i0 + r]) M[(int64_t)(i0 + r) * n + j] += acc[r];
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
+  __syncthreads();
+  // owned rows of the inverse, transposed through a shared tile (reuses G)
+  T* tile = G;   // 32 x 33
+  const int nown = p_nown[p];
+  const int32_t* ow = own + own_off[p];
+  T* out = invT + inv_off[p];
+  for (int o0 = 0; o0 < nown; o0 += 32) {
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int oo = t / 32, cc = t % 32;
+        const int o = o0 + oo, c = c0 + cc;
+        if (o < nown && c < n) tile[oo * 33 + cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int cc = t / 32, oo = t % 32;
+        const int o = o0 + oo, c = c0 + cc;
+        if (o < nown && c < n) out[(int64_t)c * nown + o] = tile[oo * 33 + cc];
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
+}
+
+template <typename T, int W>
+size_t gj_blk_smem(int n) {
+  return (size_t)n * (W + 1) * sizeof(T) + (size_t)W * n * sizeof(T) + (size_t)n * sizeof(T) + W * sizeof(T) +
+         2 * (size_t)n * sizeof(int) + 2 * (size_t)n + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
+                const int64_t* __restrict__ idx_off, const int32_t* __restrict__ idx,
+                const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
+                const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
+                T* __restrict__ x, T omega) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* rs = reinterpret_cast<T*>(smem_raw);
+  const int p = blockIdx.x;
+  const int n = p_n[p];
+  const int32_t* id = idx + idx_off[p];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]];
+  __syncthreads();
+  const int nown = p_nown[p];
+  const int32_t* ow = own + own_off[p];
+  const T* Bi = invT + inv_off[p];
+  for (int o = threadIdx.x; o < nown; o += blockDim.x) {
+    const T* col = Bi + o;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int c = 0;
+    for (; c + 4 <= n; c += 4) {
+      a0 += col[(int64_t)c * nown] * rs[c];
+      a1 += col[(int64_t)(c + 1) * nown] * rs[c + 1];
+      a2 += col[(int64_t)(c + 2) * nown] * rs[c + 2];
+      a3 += col[(int64_t)(c + 3) * nown] * rs[c + 3];
+    }
+    for (; c < n; ++c) a0 += col[(int64_t)c * nown] * rs[c];
+    x[id[ow[o]]] += omega * ((a0 + a1) + (a2 + a3));
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
+                           const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
+                           const double* bsr_val, int B, T* dense, cudaStream_t st) {
+  if (np <= 0) return;
+  k_patch_gather_t<T><<<np, 256, 0, st>>>(p_n, dense_off, gmap_off, gmap, pad_off, padpos, bsr_val, B, dense);
+}
+
+template <typename T, int W>
+bool try_gj_blk(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
+                const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
+                int32_t* status, cudaStream_t st) {
+  const size_t smem = gj_blk_smem<T, W>(max_n);
+  if (smem > 220 * 1024 || (size_t)32 * 33 > (size_t)max_n * (W + 1)) return false;
+  cudaFuncSetAttribute(k_patch_gj_blk<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_patch_gj_blk<T, W><<<np, 512, smem, st>>>(p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status,
+                                               max_n);
+  return true;
+}
+
+template <typename T>
+void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
+                       const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
+                       int32_t* status, cudaStream_t st) {
+  if (np <= 0) return;
+  // small blocks: the whole matrix fits in shared memory (unblocked sweep)
+  const size_t base = (size_t)max_n * (2 * sizeof(T) + 2 * sizeof(int)) + ((max_n + 15) / 16) * 16;
+  const size_t with_m = base + (size_t)max_n * max_n * sizeof(T);
+  if (with_m <= 190 * 1024) {
+    cudaFuncSetAttribute(k_patch_gj_t<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)with_m);
+    k_patch_gj_t<T, true><<<np, 512, with_m, st>>>(p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT,
+                                                   status);
+    return;
+  }
+  // larger blocks: panel-blocked sweep with the widest panel that fits
+  if (try_gj_blk<T, 32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status, st)) return;
+  if (try_gj_blk<T, 16>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status, st)) return;
+  if (try_gj_blk<T, 8>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status, st)) return;
+  cudaFuncSetAttribute(k_patch_gj_t<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
+  k_patch_gj_t<T, false><<<np, 512, base, st>>>(p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT,
+                                                status);
+}
+
+template <typename T>
+void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
+                          const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
+                          const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, cudaStream_t st) {
+  if (np <= 0) return;
+  int threads = ((max_nown + 31) / 32) * 32;
+  if (threads > 1024) threads = 1024;
+  if (threads < 64) threads = 64;
+  k_patch_apply_t<T><<<np, threads, (size_t)max_n * sizeof(T), st>>>(p_n, p_nown, idx_off, idx, own_off, own,
+                                                                     inv_off, invT, r, x, T(omega));
+}
+
+#define FSI_INST(T)                                                                                              \
+  template void launch_patch_gather_t<T>(int, const int32_t*, const int64_t*, const int64_t*, const int32_t*,  \
+                                         const int64_t*, const int32_t*, const double*, int, T*, cudaStream_t); \
+  template void launch_patch_gj_t<T>(int, int, const int32_t*, const int32_t*, const int64_t*, const int64_t*, \
+                                     const int32_t*, const int64_t*, T*, T*, int32_t*, cudaStream_t);           \
+  template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \
+                                        const int32_t*, const int64_t*, const int32_t*, const int64_t*,        \
+                                        const T*, const T*, T*, double, cudaStream_t);
+FSI_INST(double)
+FSI_INST(float)
+#undef FSI_INST
+
+}  // namespace fsi

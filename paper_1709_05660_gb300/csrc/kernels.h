@@ -29,6 +29,10 @@ void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nod
 // k_linalg.cu
 void launch_bsr_residual(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const double* x, const double* b, double* y, cudaStream_t st);
+void launch_bsr_residual_f32(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const float* val,
+                             const float* x, const float* b, float* y, cudaStream_t st);
+void launch_bsr_apply_mixed(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
+                            const float* x, double* y, cudaStream_t st);
 void launch_csr_spmv(int64_t nrows, const int32_t* ptr, const int32_t* col, const double* val, const double* x,
                      double* y, bool add, cudaStream_t st);
 void launch_gather(int64_t n, const int32_t* map, const double* in, double* out, cudaStream_t st);
@@ -42,20 +46,31 @@ void launch_combo(int64_t n, const double* Z, int64_t ldz, int nvec, const doubl
 void launch_norm_partial(int64_t n, const double* w, double* partial, int nblk, cudaStream_t st);
 void launch_nonfinite_check(int64_t n, const double* v, int32_t* status, cudaStream_t st);
 
-void launch_patch_gather(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
-                         const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos, const double* bsr_val,
-                         int B, double* dense, cudaStream_t st);
-void launch_patch_gj(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
-                     const int64_t* own_off, const int32_t* own, const int64_t* inv_off, double* dense, double* inv,
-                     int32_t* status, cudaStream_t st);
-void launch_patch_apply(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* idx_off,
-                        const int32_t* idx, const int64_t* own_off, const int32_t* own, const int64_t* inv_off,
-                        const double* inv, const double* r, double* x, double omega, cudaStream_t st);
+// k_schwarz.cu (T = double: FP64 path, T = float: mixed path)
+template <typename T>
+void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
+                           const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
+                           const double* bsr_val, int B, T* dense, cudaStream_t st);
+template <typename T>
+void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
+                       const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
+                       int32_t* status, cudaStream_t st);
+template <typename T>
+void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
+                          const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
+                          const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, cudaStream_t st);
 
 void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const int32_t* pad_list, int npad, int64_t n, double* A, cudaStream_t st);
 int launch_coarse_gj(int64_t n, double* A, double* Bm, double* inv, int32_t* piv, int32_t* status, int sm_count,
                      cudaStream_t st);
 void launch_gemv(int64_t n, const double* A, const double* x, double* y, cudaStream_t st);
+void launch_gemv_f32io(int64_t n, const double* A, const float* x, float* y, cudaStream_t st);
+void launch_csr_spmv_f32(int64_t nrows, const int32_t* ptr, const int32_t* col, const float* val, const float* x,
+                         float* y, bool add, cudaStream_t st);
+void launch_to_f32(int64_t n, const double* in, float* out, cudaStream_t st);
+void launch_axpby_f32_to_f64(int64_t n, const float* in, double* out, cudaStream_t st);
+void launch_combo_mixed(int64_t n, const float* Z, int64_t ldz, int nvec, const double* coef, double* x,
+                        cudaStream_t st);
 
 }  // namespace fsi

@@ -13,7 +13,8 @@ Tolerances (FP64 everywhere on this path):
 * one Richardson-Schwarz step / one V-cycle: the oracle solves each block by
   partial-pivot LU, the GPU applies the explicit Gauss-Jordan inverse; both are
   backward stable, so the difference is bounded by c * n * eps * cond(B_k),
-  with cond(B_k) computed here from the oracle's blocks;
+  with cond(B_k) the condition number of the row/column-equilibrated block
+  computed here from the oracle's blocks;
 * FGMRES / Newton step: relative error against the oracle's direct solution
   x* <= 1e-10 (rtol 1e-10 on the true residual; the oracle's own FGMRES
   reaches ~2e-11 on this workload) and Krylov iteration counts within 10%
@@ -143,11 +144,20 @@ def test_spmv_and_transfers_parity(c1):
 
 
 def _block_cond(ops):
+    """Largest condition number of the row/column-equilibrated Schwarz blocks.
+
+    The raw blocks mix rows scaled by mu_s, by the ALE stiffness 1/V_el and by
+    the kinematic mass matrix, so their condition numbers (1e16-1e19) only
+    measure that scaling; partial pivoting is insensitive to it, and the
+    accuracy of either inverse follows the equilibrated condition number."""
     Jd = ops.J.tocsr()
     worst, nmax = 1.0, 1
     for pt in ops.patches:
         B = Jd[pt.dofs][:, pt.dofs].toarray()
-        worst = max(worst, np.linalg.cond(B))
+        dr = 1.0 / np.abs(B).max(axis=1)
+        Bs = dr[:, None] * B
+        dc = 1.0 / np.abs(Bs).max(axis=0)
+        worst = max(worst, np.linalg.cond(Bs * dc[None, :]))
         nmax = max(nmax, len(pt.dofs))
     return worst, nmax
 
@@ -284,10 +294,11 @@ def _oracle_rows(prob, lev, y, nodes):
     return rows, rres
 
 
-@pytest.mark.parametrize("cfg", ["c2_2d_l5"])
-def test_full_size_newton_step_sampled(cfg):
+@pytest.mark.parametrize("cfg,precision", [("c2_2d_l5", 0), ("c2_2d_l5", 1)], ids=["fp64", "mixed"])
+def test_full_size_newton_step_sampled(cfg, precision):
     fsi = _fsi()
     prob, opts = CONFIGS[cfg]
+    opts = replace(opts, precision=precision)
     s = fsi.FSI(prob, opts, stream=torch.cuda.current_stream().cuda_stream)
     N = int(s.N[-1])
     lev = build_level(prob, prob.levels - 1)
@@ -320,4 +331,87 @@ def test_full_size_newton_step_sampled(cfg):
     res = np.linalg.norm(rg + Jg @ d) / np.linalg.norm(rg)
     assert res <= 2 * opts.rtol, res
     assert st.iters < 200
+    s.close()
+
+
+# ----------------------------------------------------------------------------
+# 4x4-element Schwarz blocks (n = 388: panel-blocked Gauss-Jordan) and the
+# mixed-precision path (FP32 V-cycle and block inverses, FP64 FGMRES / coarse)
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def c1_t4():
+    prob, opts = CONFIGS["c1_2d_l3"]
+    opts = replace(opts, tile=(4, 4))
+    orc = osolver.Oracle(prob, opts)
+    N = orc.fine.N
+    y0 = initial_state(prob, orc.fine, noise(N, 0))
+    r, J = orc.assemble(y0)
+    orc.factor()
+    xs = osolver.direct_solve(J, -r)
+    return dict(orc=orc, prob=prob, opts=opts, y0=y0, r=r, xs=xs, N=N)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_blocked_factor_smoother_and_newton_step(c1_t4, precision):
+    fsi = _fsi()
+    opts = replace(c1_t4["opts"], precision=precision)
+    s = fsi.FSI(c1_t4["prob"], opts, stream=torch.cuda.current_stream().cuda_stream)
+    orc = c1_t4["orc"]
+    s.set_state(_dev(c1_t4["y0"]))
+    s.assemble()
+    s.factor()
+    rng = np.random.default_rng(5)
+    L = c1_t4["prob"].levels
+    for l in range(1, L):
+        ops = orc.ops[l]
+        n = ops.J.shape[0]
+        b = rng.standard_normal(n)
+        x = rng.standard_normal(n)
+        want = x + opts.omega * osolver.ras_apply(ops, b - ops.J @ x)
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        s.apply_smoother(l, _dev(b), _dev(x), out)
+        err = np.linalg.norm(_host(out) - want) / np.linalg.norm(want)
+        if precision == 0:
+            cond, nmax = _block_cond(ops)
+            assert err <= 10 * nmax * EPS * cond, (l, err)
+        else:
+            # FP32 residual, inverse and update: block inverses carry ~1e-7
+            # relative error (FP32 eps 6e-8 times a modest equilibrated
+            # condition number), amplified by at most the smoother's norm
+            assert err <= 1e-4, (l, err)
+    dx = torch.empty(c1_t4["N"], dtype=torch.float64, device="cuda")
+    rel, st = s.newton_step(dx)
+    xs = c1_t4["xs"]
+    err = np.linalg.norm(_host(dx) - xs) / np.linalg.norm(xs)
+    assert err <= (1e-10 if precision == 0 else 1e-8), err
+    assert st.rel_res <= opts.rtol
+    if precision == 0:
+        _, sto = orc.solve(-c1_t4["r"])
+        assert abs(st.iters - sto.iters) <= max(1, int(0.1 * sto.iters)), (st.iters, sto.iters)
+    s.close()
+
+
+def test_mixed_newton_step_config1():
+    fsi = _fsi()
+    prob, opts = CONFIGS["c1_2d_l3"]
+    opts = replace(opts, precision=1)
+    orc = osolver.Oracle(prob, opts)
+    N = orc.fine.N
+    y0 = initial_state(prob, orc.fine, noise(N, 0))
+    r, J = orc.assemble(y0)
+    xs = osolver.direct_solve(J, -r)
+    s = fsi.FSI(prob, opts, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_state(_dev(y0))
+    dx = torch.empty(N, dtype=torch.float64, device="cuda")
+    rel, st = s.newton_step(dx)
+    err = np.linalg.norm(_host(dx) - xs) / np.linalg.norm(xs)
+    assert err <= 1e-8, err
+    # the FP32 V-cycle agrees with the FP64 one to FP32 accuracy
+    orc.factor()
+    b = np.random.default_rng(2).standard_normal(N)
+    z = torch.empty(N, dtype=torch.float64, device="cuda")
+    s.apply_vcycle(_dev(b), z)
+    want = orc.precond(b)
+    assert np.linalg.norm(_host(z) - want) <= 1e-3 * np.linalg.norm(want)
     s.close()
