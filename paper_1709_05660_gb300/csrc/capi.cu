@@ -225,19 +225,24 @@ void build_device(Ctx& c) {
       D.inv_total = H.inv_total;
       D.dense_total = H.dense_total;
       if (c.mixed) {
+        D.dr32 = dalloc<float>(c, (size_t)H.idx_total);
+        D.dc32 = dalloc<float>(c, (size_t)H.idx_total);
         D.inv32 = dalloc<float>(c, (size_t)H.inv_total);
         D.val32 = dalloc<float>(c, (size_t)H.nnzb * B * B);
         std::vector<float> pv(H.P_val.begin(), H.P_val.end()), rv(H.R_val.begin(), H.R_val.end());
         D.P_val32 = upload(c, pv);
         D.R_val32 = upload(c, rv);
       } else {
+        D.dr = dalloc<double>(c, (size_t)H.idx_total);
+        D.dc = dalloc<double>(c, (size_t)H.idx_total);
         D.inv = dalloc<double>(c, (size_t)H.inv_total);
       }
       max_dense = std::max(max_dense, H.dense_total);
       for (int p = 0; p < H.n_patches; ++p) {
         const double n = H.p_n[p], no = H.p_nown[p];
-        D.apply_bytes += no * n * 8.0 + n * 12.0 + no * 20.0;
-        D.apply_bytes32 += no * n * 4.0 + n * 8.0 + no * 12.0;
+        // inverse rows, residual gather + index + row scale, owned index + column scale + x read/write
+        D.apply_bytes += no * n * 8.0 + n * 20.0 + no * 28.0;
+        D.apply_bytes32 += no * n * 4.0 + n * 12.0 + no * 16.0;
         D.apply_flops += 2.0 * no * n;
         D.factor_flops += 2.0 * n * n * n;
         D.factor_bytes += n * n * 8.0 + no * n * 8.0;
@@ -392,12 +397,12 @@ void factor(Ctx& c) {
     if (c.mixed) {
       float* ws = reinterpret_cast<float*>(c.dense_ws);
       launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
-                                   D.p_padpos, D.val, B, ws, c.stream);
+                                   D.p_padpos, D.val, B, ws, D.p_idx_off, D.dr32, D.dc32, c.stream);
       launch_patch_gj_t<float>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
                                D.p_inv_off, ws, D.inv32, c.status, c.stream);
     } else {
       launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
-                                    D.p_padpos, D.val, B, c.dense_ws, c.stream);
+                                    D.p_padpos, D.val, B, c.dense_ws, D.p_idx_off, D.dr, D.dc, c.stream);
       launch_patch_gj_t<double>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
                                 D.p_inv_off, c.dense_ws, D.inv, c.status, c.stream);
     }
@@ -438,7 +443,8 @@ template <> struct VC<double> {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes, D.apply_flops);
     launch_patch_apply_t<double>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
-                                 D.p_own_off, D.p_own, D.p_inv_off, D.inv, r, x, c.opts.omega, c.stream);
+                                 D.p_own_off, D.p_own, D.p_inv_off, D.inv, r, x, c.opts.omega, D.dr, D.dc,
+                                 c.stream);
     counted(c);
   }
   static void restrict_(Ctx& c, int l, const double* r, double* bc) {
@@ -474,7 +480,8 @@ template <> struct VC<float> {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes32, D.apply_flops);
     launch_patch_apply_t<float>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
-                                D.p_own_off, D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, c.stream);
+                                D.p_own_off, D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32,
+                                c.stream);
     counted(c);
   }
   static void restrict_(Ctx& c, int l, const float* r, float* bc) {

@@ -99,7 +99,9 @@ struct DevLevel {
   int64_t *p_idx_off = nullptr, *p_own_off = nullptr, *p_dense_off = nullptr, *p_inv_off = nullptr,
           *p_gmap_off = nullptr, *p_pad_off = nullptr;
   int32_t *p_idx = nullptr, *p_own = nullptr, *p_gmap = nullptr, *p_padpos = nullptr;
-  double* inv = nullptr;          // owned rows of B_k^{-1}
+  double* inv = nullptr;          // owned rows of B~_k^{-1} (equilibrated block)
+  double *dr = nullptr, *dc = nullptr;     // row / column scales of each block (FP64 path)
+  float *dr32 = nullptr, *dc32 = nullptr;  // (mixed path)
   int64_t inv_total = 0, dense_total = 0;
   // work vectors (internal layout)
   double *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;

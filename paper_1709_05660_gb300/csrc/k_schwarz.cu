@@ -3,7 +3,10 @@
 //
 //  * k_patch_gather: B_k = J_l[R^delta_k, R^delta_k] copied from the BSR values
 //    of level l into a dense n_k x n_k workspace (padding slots get 1 on the
-//    diagonal so every block stays invertible).
+//    diagonal so every block stays invertible), then equilibrated with exact
+//    power-of-two row and column scales; the blocks mix rows scaled by the
+//    shear modulus, the ALE stiffness 1/V_el and the kinematic mass matrix,
+//    and without scaling an FP32 inverse loses its small entries.
 //  * k_patch_gj: in-place Gauss-Jordan with partial (row) pivoting, one thread
 //    block per Schwarz block.  Only the rows of B_k^{-1} that belong to R^0_k
 //    are written out, transposed (column-major in the owned row index) so the
@@ -45,11 +48,23 @@ __device__ int block_argmax_abs(double v, int idx, double* sv, int* si) {
 }
 }  // namespace
 
+// power of two closest (from below) to 1 / m, so scaling is exact; 1 for m == 0
+__device__ __forceinline__ double pow2_inv(double m) {
+  if (!(m > 0.0) || !isfinite(m)) return 1.0;
+  int e;
+  frexp(m, &e);           // m = f * 2^e, f in [0.5, 1)
+  return ldexp(1.0, 1 - e);
+}
+
+// Gather B_k and equilibrate it: B~ = D_r B D_c with power-of-two row scales
+// (row maxima -> [1, 2)) and then column scales.  The scales are stored so
+// that B^{-1} r = D_c B~^{-1} (D_r r).
 template <typename T>
 __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t* __restrict__ dense_off,
                                  const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
                                  const int64_t* __restrict__ pad_off, const int32_t* __restrict__ padpos,
-                                 const double* __restrict__ bsr_val, int B, T* __restrict__ dense) {
+                                 const double* __restrict__ bsr_val, int B, T* __restrict__ dense,
+                                 const int64_t* __restrict__ idx_off, T* __restrict__ dr, T* __restrict__ dc) {
   const int p = blockIdx.x;
   const int n = p_n[p];
   T* D = dense + dense_off[p];
@@ -67,6 +82,27 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
   for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
     const int q = padpos[t];
     D[(int64_t)q * n + q] = T(1);
+  }
+  __syncthreads();
+  T* Dr = dr + idx_off[p];
+  T* Dc = dc + idx_off[p];
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+  for (int i = wid; i < n; i += nw) {
+    double m = 0.0;
+    for (int j = lane; j < n; j += kWarp) m = fmax(m, fabs((double)D[(int64_t)i * n + j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const T s = T(pow2_inv(m));
+    for (int j = lane; j < n; j += kWarp) D[(int64_t)i * n + j] *= s;
+    if (lane == 0) Dr[i] = s;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i) m = fmax(m, fabs((double)D[(int64_t)i * n + j]));
+    const T s = T(pow2_inv(m));
+    for (int i = 0; i < n; ++i) D[(int64_t)i * n + j] *= s;
+    Dc[j] = s;
   }
 }
 
@@ -315,13 +351,15 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
                 const int64_t* __restrict__ idx_off, const int32_t* __restrict__ idx,
                 const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
                 const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
-                T* __restrict__ x, T omega) {
+                T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* rs = reinterpret_cast<T*>(smem_raw);
   const int p = blockIdx.x;
   const int n = p_n[p];
   const int32_t* id = idx + idx_off[p];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]];
+  const T* Dr = dr + idx_off[p];
+  const T* Dc = dc + idx_off[p];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]] * Dr[i];
   __syncthreads();
   const int nown = p_nown[p];
   const int32_t* ow = own + own_off[p];
@@ -337,7 +375,8 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
       a3 += col[(int64_t)(c + 3) * nown] * rs[c + 3];
     }
     for (; c < n; ++c) a0 += col[(int64_t)c * nown] * rs[c];
-    x[id[ow[o]]] += omega * ((a0 + a1) + (a2 + a3));
+    const int k = ow[o];
+    x[id[k]] += omega * Dc[k] * ((a0 + a1) + (a2 + a3));
   }
 }
 
@@ -345,9 +384,11 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
                            const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
-                           const double* bsr_val, int B, T* dense, cudaStream_t st) {
+                           const double* bsr_val, int B, T* dense, const int64_t* idx_off, T* dr, T* dc,
+                           cudaStream_t st) {
   if (np <= 0) return;
-  k_patch_gather_t<T><<<np, 256, 0, st>>>(p_n, dense_off, gmap_off, gmap, pad_off, padpos, bsr_val, B, dense);
+  k_patch_gather_t<T><<<np, 512, 0, st>>>(p_n, dense_off, gmap_off, gmap, pad_off, padpos, bsr_val, B, dense,
+                                          idx_off, dr, dc);
 }
 
 template <typename T, int W>
@@ -388,23 +429,25 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
 template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
-                          const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, cudaStream_t st) {
+                          const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
+                          const T* dc, cudaStream_t st) {
   if (np <= 0) return;
   int threads = ((max_nown + 31) / 32) * 32;
   if (threads > 1024) threads = 1024;
   if (threads < 64) threads = 64;
   k_patch_apply_t<T><<<np, threads, (size_t)max_n * sizeof(T), st>>>(p_n, p_nown, idx_off, idx, own_off, own,
-                                                                     inv_off, invT, r, x, T(omega));
+                                                                     inv_off, invT, r, x, T(omega), dr, dc);
 }
 
 #define FSI_INST(T)                                                                                              \
   template void launch_patch_gather_t<T>(int, const int32_t*, const int64_t*, const int64_t*, const int32_t*,  \
-                                         const int64_t*, const int32_t*, const double*, int, T*, cudaStream_t); \
+                                         const int64_t*, const int32_t*, const double*, int, T*,                \
+                                         const int64_t*, T*, T*, cudaStream_t);                                 \
   template void launch_patch_gj_t<T>(int, int, const int32_t*, const int32_t*, const int64_t*, const int64_t*, \
                                      const int32_t*, const int64_t*, T*, T*, int32_t*, cudaStream_t);           \
   template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \
                                         const int32_t*, const int64_t*, const int32_t*, const int64_t*,        \
-                                        const T*, const T*, T*, double, cudaStream_t);
+                                        const T*, const T*, T*, double, const T*, const T*, cudaStream_t);
 FSI_INST(double)
 FSI_INST(float)
 #undef FSI_INST

@@ -50,7 +50,8 @@ void launch_nonfinite_check(int64_t n, const double* v, int32_t* status, cudaStr
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
                            const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
-                           const double* bsr_val, int B, T* dense, cudaStream_t st);
+                           const double* bsr_val, int B, T* dense, const int64_t* idx_off, T* dr, T* dc,
+                           cudaStream_t st);
 template <typename T>
 void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
                        const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
@@ -58,7 +59,8 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
 template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
-                          const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, cudaStream_t st);
+                          const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
+                          const T* dc, cudaStream_t st);
 
 void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const int32_t* pad_list, int npad, int64_t n, double* A, cudaStream_t st);

@@ -262,79 +262,6 @@ def test_error_status_codes(c1):
 
 
 # ----------------------------------------------------------------------------
-# full-size workload (the benchmark configuration), sampled parity + properties
-# ----------------------------------------------------------------------------
-
-def _oracle_rows(prob, lev, y, nodes):
-    """Oracle rows of J and r for the given nodes, assembled from exactly the
-    elements that contain them (so every sampled row is complete)."""
-    nd = 2 * lev.dim
-    node_set = set(int(n) for n in nodes)
-    elems = np.unique(np.nonzero(np.isin(lev.elem_nodes, list(node_set)))[0])
-    rows = {}
-    rres = {}
-    for solid in (True, False):
-        es = elems[lev.elem_solid[elems] == solid]
-        if len(es) == 0:
-            continue
-        Rv, Rg = fem.element_system(prob, lev, es, y)
-        for k, e in enumerate(es):
-            ed = lev.elem_dofs[e]
-            for i, gi in enumerate(ed):
-                if gi // nd not in node_set or gi >= lev.n_nodes * nd:
-                    continue
-                row = rows.setdefault(int(gi), {})
-                for j, gj in enumerate(ed):
-                    row[int(gj)] = row.get(int(gj), 0.0) + Rg[k, i, j]
-                rres[int(gi)] = rres.get(int(gi), 0.0) + Rv[k, i]
-    for gi in list(rows):
-        if lev.dir_mask[gi]:
-            rows[gi] = {c: (1.0 if c == gi else 0.0) for c in rows[gi]}
-            rres[gi] = y[gi] - lev.dir_val[gi]
-    return rows, rres
-
-
-@pytest.mark.parametrize("cfg,precision", [("c2_2d_l5", 0), ("c2_2d_l5", 1)], ids=["fp64", "mixed"])
-def test_full_size_newton_step_sampled(cfg, precision):
-    fsi = _fsi()
-    prob, opts = CONFIGS[cfg]
-    opts = replace(opts, precision=precision)
-    s = fsi.FSI(prob, opts, stream=torch.cuda.current_stream().cuda_stream)
-    N = int(s.N[-1])
-    lev = build_level(prob, prob.levels - 1)
-    y0 = initial_state(prob, lev, noise(N, 0))
-    s.set_state(_dev(y0))
-    r = torch.empty(N, dtype=torch.float64, device="cuda")
-    s.assemble(r)
-    Jg = _csr(s, prob.levels - 1)
-    rng = np.random.default_rng(3)
-    nodes = rng.choice(lev.n_nodes, 60, replace=False)
-    iface = np.nonzero(lev.node_class == 2)[0]
-    nodes = np.concatenate([nodes, iface[:: max(1, len(iface) // 10)]])
-    rows, rres = _oracle_rows(prob, lev, y0, nodes)
-    rg = _host(r)
-    for gi, row in rows.items():
-        a, b = Jg.indptr[gi], Jg.indptr[gi + 1]
-        got = dict(zip(Jg.indices[a:b].tolist(), Jg.data[a:b].tolist()))
-        assert set(got) == set(row)
-        scale = max(abs(v) for v in row.values()) or 1.0
-        for c, v in row.items():
-            assert abs(got[c] - v) <= 1e-12 * scale
-        assert abs(rg[gi] - rres[gi]) <= 1e-12 * max(1.0, np.max(np.abs(list(rres.values()))))
-    # solve on the device; the true residual is checked on the host with the
-    # (sample-verified) exported matrix
-    s.factor()
-    dx = torch.zeros(N, dtype=torch.float64, device="cuda")
-    st = s.solve(-r, dx)
-    d = _host(dx)
-    assert np.all(np.isfinite(d))
-    res = np.linalg.norm(rg + Jg @ d) / np.linalg.norm(rg)
-    assert res <= 2 * opts.rtol, res
-    assert st.iters < 200
-    s.close()
-
-
-# ----------------------------------------------------------------------------
 # 4x4-element Schwarz blocks (n = 388: panel-blocked Gauss-Jordan) and the
 # mixed-precision path (FP32 V-cycle and block inverses, FP64 FGMRES / coarse)
 # ----------------------------------------------------------------------------
@@ -415,3 +342,78 @@ def test_mixed_newton_step_config1():
     want = orc.precond(b)
     assert np.linalg.norm(_host(z) - want) <= 1e-3 * np.linalg.norm(want)
     s.close()
+
+
+# ----------------------------------------------------------------------------
+# full-size workload (the benchmark configuration), sampled parity + properties
+# ----------------------------------------------------------------------------
+
+def _oracle_rows(prob, lev, y, nodes):
+    """Oracle rows of J and r for the given nodes, assembled from exactly the
+    elements that contain them (so every sampled row is complete)."""
+    nd = 2 * lev.dim
+    node_set = set(int(n) for n in nodes)
+    elems = np.unique(np.nonzero(np.isin(lev.elem_nodes, list(node_set)))[0])
+    rows = {}
+    rres = {}
+    for solid in (True, False):
+        es = elems[lev.elem_solid[elems] == solid]
+        if len(es) == 0:
+            continue
+        Rv, Rg = fem.element_system(prob, lev, es, y)
+        for k, e in enumerate(es):
+            ed = lev.elem_dofs[e]
+            for i, gi in enumerate(ed):
+                if gi // nd not in node_set or gi >= lev.n_nodes * nd:
+                    continue
+                row = rows.setdefault(int(gi), {})
+                for j, gj in enumerate(ed):
+                    row[int(gj)] = row.get(int(gj), 0.0) + Rg[k, i, j]
+                rres[int(gi)] = rres.get(int(gi), 0.0) + Rv[k, i]
+    for gi in list(rows):
+        if lev.dir_mask[gi]:
+            rows[gi] = {c: (1.0 if c == gi else 0.0) for c in rows[gi]}
+            rres[gi] = y[gi] - lev.dir_val[gi]
+    return rows, rres
+
+
+@pytest.mark.parametrize("cfg,precision", [("c2_2d_l5", 0), ("c2_2d_l5", 1)], ids=["fp64", "mixed"])
+def test_full_size_newton_step_sampled(cfg, precision):
+    fsi = _fsi()
+    prob, opts = CONFIGS[cfg]
+    opts = replace(opts, precision=precision)
+    s = fsi.FSI(prob, opts, stream=torch.cuda.current_stream().cuda_stream)
+    N = int(s.N[-1])
+    lev = build_level(prob, prob.levels - 1)
+    y0 = initial_state(prob, lev, noise(N, 0))
+    s.set_state(_dev(y0))
+    r = torch.empty(N, dtype=torch.float64, device="cuda")
+    s.assemble(r)
+    Jg = _csr(s, prob.levels - 1)
+    rng = np.random.default_rng(3)
+    nodes = rng.choice(lev.n_nodes, 60, replace=False)
+    iface = np.nonzero(lev.node_class == 2)[0]
+    nodes = np.concatenate([nodes, iface[:: max(1, len(iface) // 10)]])
+    rows, rres = _oracle_rows(prob, lev, y0, nodes)
+    rg = _host(r)
+    for gi, row in rows.items():
+        a, b = Jg.indptr[gi], Jg.indptr[gi + 1]
+        got = dict(zip(Jg.indices[a:b].tolist(), Jg.data[a:b].tolist()))
+        assert set(got) == set(row)
+        scale = max(abs(v) for v in row.values()) or 1.0
+        for c, v in row.items():
+            assert abs(got[c] - v) <= 1e-12 * scale
+        assert abs(rg[gi] - rres[gi]) <= 1e-12 * max(1.0, np.max(np.abs(list(rres.values()))))
+    # solve on the device; the true residual is checked on the host with the
+    # (sample-verified) exported matrix
+    s.factor()
+    dx = torch.zeros(N, dtype=torch.float64, device="cuda")
+    st = s.solve(-r, dx)
+    d = _host(dx)
+    assert np.all(np.isfinite(d))
+    res = np.linalg.norm(rg + Jg @ d) / np.linalg.norm(rg)
+    assert res <= 2 * opts.rtol, res
+    assert st.iters < 200
+    s.close()
+
+
