@@ -40,6 +40,8 @@ FALLBACK_BF16_TFLOPS = 1900.0
 # FP64 ALU peak derived from the unit counts and clocks: 152 SMs x 2.07 GHz x
 # 4 FP64 flop / clock / SM (the 1.25 TFLOP/s nominal FP64 rate of the part).
 FP64_ALU_PEAK_GFLOPS = 152 * 2.07 * 4.0
+# FP32 CUDA-core peak: 152 SMs x 2.07 GHz x 128 FP32 FMA / clock / SM x 2 flop.
+FP32_ALU_PEAK_GFLOPS = 152 * 2.07 * 256.0
 HBM_BOUND = {"patch_apply", "spmv", "transfer", "krylov", "scatter"}
 L2_BYTES = 129 * 1024 * 1024
 
@@ -289,7 +291,7 @@ def _measure(args, prec, stream, barrier, dist, world, local):
     return out
 
 
-def _roofline(kst, steps):
+def _roofline(kst, steps, fp32_classes=()):
     peaks, kind = _peaks()
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
     dom = max(kst, key=lambda k: kst[k]["ms"])
@@ -300,10 +302,13 @@ def _roofline(kst, steps):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_source": kind}
     else:
-        peak = FP64_ALU_PEAK_GFLOPS
+        fp32 = dom in fp32_classes
+        peak = FP32_ALU_PEAK_GFLOPS if fp32 else FP64_ALU_PEAK_GFLOPS
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e9
+        src = ("derived FP32 ALU peak (152 SM x 2.07 GHz x 256 flop/clk)" if fp32 else
+               "derived FP64 ALU peak (152 SM x 2.07 GHz x 4 flop/clk)")
         roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": peak / 1e3, "unit": "TFLOP/s",
-                "frac": achieved / peak, "peak_source": "derived FP64 ALU peak (152 SM x 2.07 GHz x 4 flop/clk)"}
+                "frac": achieved / peak, "peak_source": src, "dtype": "f32" if fp32 else "f64"}
     roof.update({"kernel": dom, "traffic": _traffic(dom), "launches": d["launches"],
                  "avg_launch_ms": per_launch_ms})
     classes = {k: {"ms_per_step": v["ms"] / steps, "launches": v["launches"],
@@ -332,7 +337,7 @@ def run_gpu(args, rank, world):
     prob, opts = CONFIGS[args.config]
     main = _measure(args, 1, stream, barrier, dist, world, local)        # mixed FP32 / FP64
     fp64 = _measure(args, 0, stream, barrier, dist, world, local) if not args.mixed_only else None
-    roof, classes = _roofline(main["kst"], args.steps)
+    roof, classes = _roofline(main["kst"], args.steps, fp32_classes=("patch_factor",))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, detail = OracleSampler(args.config).sample(args.cpu_frac, int(round(statistics.mean(main["iters"]))))

@@ -296,7 +296,7 @@ void build_device(Ctx& c) {
   // coarse dense operator
   const int64_t n0 = c.hl[0].Ni;
   c.c_A = dalloc<double>(c, (size_t)n0 * n0);
-  c.c_B = dalloc<double>(c, (size_t)n0 * n0);
+  c.c_B = dalloc<double>(c, (size_t)2 * n0);   // pivot-column buffer of the coarse sweep
   c.c_inv = dalloc<double>(c, (size_t)n0 * n0);
   c.c_piv = dalloc<int32_t>(c, n0);
   c.status = dalloc<int32_t>(c, ST_COUNT);

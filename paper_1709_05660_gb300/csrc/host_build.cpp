@@ -376,7 +376,7 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
     L.p_idx_off[p + 1] = L.p_idx_off[p] + n;
     L.p_own_off[p + 1] = L.p_own_off[p] + nown;
     L.p_dense_off[p + 1] = L.p_dense_off[p] + (int64_t)n * n;
-    L.p_inv_off[p + 1] = L.p_inv_off[p] + (int64_t)nown * n;
+    L.p_inv_off[p + 1] = L.p_inv_off[p] + (int64_t)((nown + 3) & ~3) * n;   // owned rows padded to 4
     L.p_gmap_off[p + 1] = (int64_t)L.p_gmap.size() / 3;
     L.p_pad_off[p + 1] = (int64_t)L.p_padpos.size();
     L.p_elem_off[p + 1] = (int64_t)L.p_elems.size();

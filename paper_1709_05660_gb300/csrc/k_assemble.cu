@@ -300,6 +300,8 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
   __shared__ double sA[kNdofe * kNdofe];
   __shared__ double sT[kNdofe * kNdofe];
   __shared__ double sC[kNdofe * kNdofe];
+  __shared__ double wP[kNN * kNloc];        // T[i][(b,s)] = sum_a A[i][(a,s)] wP[(b,s)][a]
+  __shared__ double wR[kNN * kNloc * 2];    // C[(b,sc)][J] += sum_a sum_h wR[.][a][h] T[(a, sf_h)][J]
   __shared__ uint8_t c_cls[kNloc], c_msk[kNN], f_cls[kNloc], f_msk[kNN];
   const int E = blockIdx.x;
   const int cx = E % ncx, cy = E / ncx;
@@ -321,27 +323,38 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
       f_msk[threadIdx.x] = f_dir[(int64_t)f_nodes[ef * kNloc + a] * kB + s] ? 0 : 1;
     }
     __syncthreads();
+    // weight tables of this child: coarse basis b at the child's node a
+    for (int t = threadIdx.x; t < kNN * kNloc; t += blockDim.x) {
+      const int J = t / kNloc, a = t % kNloc;        // J = (b, s)
+      const int b = J / kB, sl = J % kB;
+      const double q = qw(sx, a % 3, b % 3) * qw(sy, a / 3, b / 3);
+      wP[t] = (c_msk[J] && f_msk[a * kB + sl]) ? q : 0.0;
+      const int comp = sl % kDim;
+      const int kc = row_kind(c_cls[b], sl);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int sf = h == 0 ? comp : kDim + comp;
+        wR[t * 2 + h] = (c_msk[J] && f_msk[a * kB + sf] && row_kind(f_cls[a], sf) == kc) ? q : 0.0;
+      }
+    }
+    __syncthreads();
     // T = A_c P_c
     for (int t = threadIdx.x; t < kNdofe * kNdofe; t += blockDim.x) {
       const int i = t / kNdofe, J = t % kNdofe;
+      const double* Ai = sA + i * kNdofe;
       double acc = 0.0;
       if (J < kNN) {
-        const int b = J / kB, s = J % kB;
-        if (c_msk[J]) {
-          const int ib = b % 3, jb = b / 3;
-          for (int a = 0; a < kNloc; ++a) {
-            const int ia = a % 3, ja = a / 3;
-            const double q = qw(sx, ia, ib) * qw(sy, ja, jb);
-            if (q != 0.0 && f_msk[a * kB + s]) acc += sA[i * kNdofe + a * kB + s] * q;
-          }
-        }
+        const int sl = J % kB;
+        const double* w = wP + J * kNloc;
+#pragma unroll
+        for (int a = 0; a < kNloc; ++a) acc += Ai[a * kB + sl] * w[a];
       } else {
         const int k = J - kNN;
         // child coefficients: c0 = p0 + sum_d sig_d/2 p_d ; c_d = p_d / 2
-        if (k == 0) acc = sA[i * kNdofe + kNN];
+        if (k == 0) acc = Ai[kNN];
         else {
           const double sig = k == 1 ? (sx ? 0.5 : -0.5) : (sy ? 0.5 : -0.5);
-          acc = sA[i * kNdofe + kNN] * sig + sA[i * kNdofe + kNN + k] * 0.5;
+          acc = Ai[kNN] * sig + Ai[kNN + k] * 0.5;
         }
       }
       sT[t] = acc;
@@ -352,22 +365,11 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
       const int I = t / kNdofe, J = t % kNdofe;
       double acc = 0.0;
       if (I < kNN) {
-        const int b = I / kB, sc = I % kB;
-        if (c_msk[I]) {
-          const int ib = b % 3, jb = b / 3;
-          const int comp = sc % kDim;
-          const int kc = row_kind(c_cls[b], sc);
-          for (int a = 0; a < kNloc; ++a) {
-            const int ia = a % 3, ja = a / 3;
-            const double q = qw(sx, ia, ib) * qw(sy, ja, jb);
-            if (q == 0.0) continue;
+        const int comp = (I % kB) % kDim;
+        const double* w = wR + I * kNloc * 2;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int sf = h == 0 ? comp : kDim + comp;
-              if (f_msk[a * kB + sf] && row_kind(f_cls[a], sf) == kc) acc += q * sT[(a * kB + sf) * kNdofe + J];
-            }
-          }
-        }
+        for (int a = 0; a < kNloc; ++a)
+          acc += w[2 * a] * sT[(a * kB + comp) * kNdofe + J] + w[2 * a + 1] * sT[(a * kB + kDim + comp) * kNdofe + J];
       } else {
         const int k = I - kNN;
         if (k == 0) acc = sT[kNN * kNdofe + J];

@@ -337,6 +337,7 @@ void launch_nonfinite_check(int64_t n, const double* v, int32_t* status, cudaStr
 // ---------------------------------------------------------------------------
 // coarse level
 // ---------------------------------------------------------------------------
+// Dense coarse operator in column-major order: A[col * n + row].
 __global__ void k_dense_gather(int B, int64_t nb, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                const double* __restrict__ val, int64_t n, double* __restrict__ A) {
   const int64_t br = blockIdx.x;
@@ -345,7 +346,7 @@ __global__ void k_dense_gather(int B, int64_t nb, const int32_t* __restrict__ ro
   for (int32_t k = rowptr[br]; k < rowptr[br + 1]; ++k)
     for (int e = threadIdx.x; e < BB; e += blockDim.x) {
       const int ci = e / B, cj = e % B;
-      A[(br * B + ci) * n + (int64_t)col[k] * B + cj] = val[(int64_t)k * BB + e];
+      A[((int64_t)col[k] * B + cj) * n + br * B + ci] = val[(int64_t)k * BB + e];
     }
 }
 
@@ -361,89 +362,96 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
   if (npad > 0) k_set_diag<<<(npad + 255) / 256, 256, 0, st>>>(pad_list, npad, n, A);
 }
 
-// Cooperative Gauss-Jordan with partial pivoting on the coarse operator, in
-// place.  Each step has two grid-wide phases: (A) every block finds the pivot
-// row p of column k itself (same deterministic rule everywhere), copies row p
-// into shared memory and reads the multipliers M[i][k] of the rows it owns;
-// (B) after a grid barrier every block updates its rows (rows whose
-// multiplier is exactly zero are left untouched) and the owner of row p
-// writes the normalised pivot row; a second barrier ends the step.
-__global__ void __launch_bounds__(512) k_coarse_gj(int64_t n, double* __restrict__ M, int32_t* __restrict__ piv,
-                                                   int32_t* __restrict__ status) {
+// Cooperative in-place Gauss-Jordan with partial pivoting on the coarse
+// operator, stored column-major; block b owns the columns j = b (mod grid).
+// Step k: every block reads the current column k from a two-slot buffer,
+// finds the pivot row p itself (same deterministic rule everywhere) and
+// updates the columns it owns,
+//     M[:, j] -= (M[:, k] / M[p][k]) M[p][j],  M[p][j] /= M[p][k],
+// column k becoming the multiplier column.  The owner of column k+1 publishes
+// its updated copy into the other buffer slot, which nobody reads before the
+// next grid barrier; one barrier per step.
+__global__ void __launch_bounds__(512) k_coarse_gj(int64_t n, double* __restrict__ M, double* __restrict__ colbuf,
+                                                   int32_t* __restrict__ piv, int32_t* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* prow = reinterpret_cast<double*>(smem_raw);                  // n
-  double* fmul = prow + n;                                              // rows owned by this block
-  uint8_t* used = reinterpret_cast<uint8_t*>(fmul + (n + gridDim.x - 1) / gridDim.x);
+  double* pc = reinterpret_cast<double*>(smem_raw);     // column k, n
+  uint8_t* used = reinterpret_cast<uint8_t*>(pc + n);   // n
   __shared__ double sv[32];
   __shared__ int si[32];
+  const int64_t G = gridDim.x;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
-  __syncthreads();
-  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+  if (blockIdx.x == 0)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) colbuf[i] = M[i];
+  grid.sync();
   for (int64_t k = 0; k < n; ++k) {
+    const double* cb = colbuf + (k & 1) * n;
     double best = -1.0;
     int bi = -1;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = cb[i];
+      pc[i] = v;
       if (used[i]) continue;
-      double a = fabs(M[i * n + k]);
+      double a = fabs(v);
       if (!(a >= 0.0)) a = 0.0;
       if (a > best) { best = a; bi = (int)i; }
     }
-    const int pr = block_argmax(best, bi, sv, si);
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) prow[j] = M[(int64_t)pr * n + j];
-    int r = 0;
-    for (int64_t i = blockIdx.x; i < n; i += gridDim.x, ++r)
-      if (threadIdx.x == 0) fmul[r] = M[i * n + k];
-    if (threadIdx.x == 0) used[pr] = 1;
-    __syncthreads();
-    double pv = prow[k];
+    const int pr = block_argmax(best, bi, sv, si);   // contains barriers: pc is complete
+    double pv = pc[pr];
     if (!(fabs(pv) > 0.0) || !isfinite(pv)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&status[ST_SINGULAR], 1);
       pv = 1.0;
     }
     const double rp = 1.0 / pv;
-    grid.sync();
-    r = 0;
-    for (int64_t i = blockIdx.x; i < n; i += gridDim.x, ++r) {
-      double* Mi = M + i * n;
-      if (i == pr) {
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) Mi[j] = (j == k) ? rp : prow[j] * rp;
+    if (threadIdx.x == 0) used[pr] = 1;
+    for (int64_t j = blockIdx.x; j < n; j += G) {
+      double* Mj = M + j * n;
+      if (j == k) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Mj[i] = (i == pr) ? rp : -pc[i] * rp;
       } else {
-        const double f = fmul[r] * rp;
-        if (f != 0.0)
-          for (int64_t j = threadIdx.x; j < n; j += blockDim.x) Mi[j] = (j == k) ? -f : Mi[j] - f * prow[j];
+        const double t = Mj[pr];
+        __syncthreads();   // every thread has read M[p][j] before row p is overwritten
+        if (t != 0.0) {
+          const double tp = t * rp;
+          for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Mj[i] = (i == pr) ? tp : Mj[i] - pc[i] * tp;
+        }
+      }
+      if (j == k + 1) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) colbuf[((k + 1) & 1) * n + i] = Mj[i];
       }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = pr;
-    (void)lane; (void)wid; (void)nw;
+    __syncthreads();
     grid.sync();
   }
 }
 
+// inverse (row-major, for the V-cycle GEMV): inv[k][c] = M[p_k][q_c], M column-major
 __global__ void k_coarse_permute(int64_t n, const double* __restrict__ M, const int32_t* __restrict__ piv,
                                  double* __restrict__ inv) {
   extern __shared__ int qinv_s[];
   for (int64_t k = threadIdx.x; k < n; k += blockDim.x) qinv_s[piv[k]] = (int)k;
   __syncthreads();
   for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
-    const double* Mr = M + (int64_t)piv[k] * n;
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) inv[k * n + c] = Mr[qinv_s[c]];
+    const int64_t pk = piv[k];
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) inv[k * n + c] = M[(int64_t)qinv_s[c] * n + pk];
   }
 }
 
 int launch_coarse_gj(int64_t n, double* A, double* Bm, double* inv, int32_t* piv, int32_t* status, int sm_count,
                      cudaStream_t st) {
-  (void)Bm;
   const int threads = 512;
   int grid = std::min<int64_t>((int64_t)sm_count, n);
   if (grid < 1) grid = 1;
-  const size_t smem = (size_t)n * sizeof(double) + (size_t)((n + grid - 1) / grid) * sizeof(double) + (size_t)n + 16;
+  const size_t smem = (size_t)n * sizeof(double) + (size_t)n + 16;
   if (smem > 200 * 1024) return -3;
   cudaFuncSetAttribute(k_coarse_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_gj, threads, smem);
   if (per_sm < 1) return -1;
-  void* args[] = {(void*)&n, (void*)&A, (void*)&piv, (void*)&status};
+  double* colbuf = Bm;   // 2 n doubles of scratch
+  void* args[] = {(void*)&n, (void*)&A, (void*)&colbuf, (void*)&piv, (void*)&status};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_coarse_gj, grid, threads, args, smem, st);
   if (e != cudaSuccess) return -2;
   k_coarse_permute<<<std::min<int64_t>(n, 1024), 256, (size_t)n * sizeof(int), st>>>(n, A, piv, inv);

@@ -22,6 +22,11 @@ namespace fsi {
 namespace {
 constexpr int kWarp = 32;
 
+// Owned inverse rows are stored column-major with the owned count padded to a
+// multiple of 4 (pad rows are zero), so each thread of the apply streams 4
+// (FP32) or 2 (FP64) rows with one vector load.
+__host__ __device__ __forceinline__ int own_pad(int nown) { return (nown + 3) & ~3; }
+
 __device__ int block_argmax_abs(double v, int idx, double* sv, int* si) {
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
 #pragma unroll
@@ -179,7 +184,7 @@ k_patch_gj_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown
   const int nown = p_nown[p];
   const int32_t* ow = own + own_off[p];
   T* out = invT + inv_off[p];
-  for (int o0 = 0; o0 < nown; o0 += 32) {
+  for (int o0 = 0; o0 < own_pad(nown); o0 += 32) {
     for (int c0 = 0; c0 < n; c0 += 32) {
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int oo = t / 32, cc = t % 32;
@@ -190,7 +195,7 @@ k_patch_gj_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int cc = t / 32, oo = t % 32;
         const int o = o0 + oo, c = c0 + cc;
-        if (o < nown && c < n) out[(int64_t)c * nown + o] = tile[oo][cc];
+        if (o < own_pad(nown) && c < n) out[(int64_t)c * own_pad(nown) + o] = o < nown ? tile[oo][cc] : T(0);
       }
       __syncthreads();
     }
@@ -288,27 +293,45 @@ k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
       if (lane == 0) live[i] = any != 0u;
     }
     __syncthreads();
-    // trailing rank-wp update, 4 rows per warp pass sharing each R load
+    // trailing rank-wp update: each thread owns a 4-row x 4-column register
+    // tile (rows i0..i0+3 of its warp's group, columns j0 + lane + 32 q)
     for (int g = wid; 4 * g < n; g += nw) {
       const int i0 = 4 * g;
       bool any = false;
 #pragma unroll
       for (int r = 0; r < 4; ++r) any |= (i0 + r < n) && live[i0 + r];
       if (!any) continue;
-      for (int j = lane; j < n; j += kWarp) {
-        if (j >= k0 && j < k0 + wp) continue;
-        T acc[4];
+      for (int j0 = 0; j0 < n; j0 += 4 * kWarp) {
+        int jq[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[r] = T(0);
-        for (int m = 0; m < wp; ++m) {
-          const T rv = R[m * n + j];
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-            if (i0 + r < n) acc[r] += G[(i0 + r) * GS + m] * rv;
+        for (int q = 0; q < 4; ++q) {
+          const int j = j0 + lane + kWarp * q;
+          jq[q] = (j < n && !(j >= k0 && j < k0 + wp)) ? j : -1;
         }
+        T acc[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-          if (i0 + r < n && live[i0 + r]) M[(int64_t)(i0 + r) * n + j] += acc[r];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
+        for (int m = 0; m < wp; ++m) {
+          T gv[4], rv[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) gv[r] = (i0 + r < n) ? G[(i0 + r) * GS + m] : T(0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) rv[q] = jq[q] >= 0 ? R[m * n + jq[q]] : T(0);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] += gv[r] * rv[q];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (i0 + r >= n || !live[i0 + r]) continue;
+          T* Mi = M + (int64_t)(i0 + r) * n;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (jq[q] >= 0) Mi[jq[q]] += acc[r][q];
+        }
       }
     }
     __syncthreads();
@@ -320,7 +343,7 @@ k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
   const int nown = p_nown[p];
   const int32_t* ow = own + own_off[p];
   T* out = invT + inv_off[p];
-  for (int o0 = 0; o0 < nown; o0 += 32) {
+  for (int o0 = 0; o0 < own_pad(nown); o0 += 32) {
     for (int c0 = 0; c0 < n; c0 += 32) {
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int oo = t / 32, cc = t % 32;
@@ -331,7 +354,7 @@ k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int cc = t / 32, oo = t % 32;
         const int o = o0 + oo, c = c0 + cc;
-        if (o < nown && c < n) out[(int64_t)c * nown + o] = tile[oo * 33 + cc];
+        if (o < own_pad(nown) && c < n) out[(int64_t)c * own_pad(nown) + o] = o < nown ? tile[oo * 33 + cc] : T(0);
       }
       __syncthreads();
     }
@@ -345,13 +368,33 @@ size_t gj_blk_smem(int n) {
          2 * (size_t)n * sizeof(int) + 2 * (size_t)n + 64;
 }
 
+// owned-row vectors of the apply: 4 rows per thread in FP32, 2 in FP64
+template <typename T> struct VecT;
+template <> struct VecT<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  static __device__ __forceinline__ void fma(float (&a)[4], const V& v, float r) {
+    a[0] += v.x * r; a[1] += v.y * r; a[2] += v.z * r; a[3] += v.w * r;
+  }
+};
+template <> struct VecT<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  static __device__ __forceinline__ void fma(double (&a)[2], const V& v, double r) {
+    a[0] += v.x * r; a[1] += v.y * r;
+  }
+};
+
+
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
                 const int64_t* __restrict__ idx_off, const int32_t* __restrict__ idx,
                 const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
                 const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
                 T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc) {
+  using VT = VecT<T>;
+  constexpr int W = VT::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* rs = reinterpret_cast<T*>(smem_raw);
   const int p = blockIdx.x;
@@ -362,21 +405,34 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
   for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]] * Dr[i];
   __syncthreads();
   const int nown = p_nown[p];
+  const int np = own_pad(nown);
+  const int nvec = np / W;
   const int32_t* ow = own + own_off[p];
-  const T* Bi = invT + inv_off[p];
-  for (int o = threadIdx.x; o < nown; o += blockDim.x) {
-    const T* col = Bi + o;
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  const typename VT::V* Bi = reinterpret_cast<const typename VT::V*>(invT + inv_off[p]);
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    T a0[W], a1[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) { a0[q] = T(0); a1[q] = T(0); }
     int c = 0;
     for (; c + 4 <= n; c += 4) {
-      a0 += col[(int64_t)c * nown] * rs[c];
-      a1 += col[(int64_t)(c + 1) * nown] * rs[c + 1];
-      a2 += col[(int64_t)(c + 2) * nown] * rs[c + 2];
-      a3 += col[(int64_t)(c + 3) * nown] * rs[c + 3];
+      const typename VT::V b0 = __ldg(Bi + (int64_t)c * nvec + v);
+      const typename VT::V b1 = __ldg(Bi + (int64_t)(c + 1) * nvec + v);
+      const typename VT::V b2 = __ldg(Bi + (int64_t)(c + 2) * nvec + v);
+      const typename VT::V b3 = __ldg(Bi + (int64_t)(c + 3) * nvec + v);
+      VT::fma(a0, b0, rs[c]);
+      VT::fma(a1, b1, rs[c + 1]);
+      VT::fma(a0, b2, rs[c + 2]);
+      VT::fma(a1, b3, rs[c + 3]);
     }
-    for (; c < n; ++c) a0 += col[(int64_t)c * nown] * rs[c];
-    const int k = ow[o];
-    x[id[k]] += omega * Dc[k] * ((a0 + a1) + (a2 + a3));
+    for (; c < n; ++c) VT::fma(a0, __ldg(Bi + (int64_t)c * nvec + v), rs[c]);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const int o = v * W + q;
+      if (o < nown) {
+        const int k = ow[o];
+        x[id[k]] += omega * Dc[k] * (a0[q] + a1[q]);
+      }
+    }
   }
 }
 
@@ -432,9 +488,10 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
                           const T* dc, cudaStream_t st) {
   if (np <= 0) return;
-  int threads = ((max_nown + 31) / 32) * 32;
-  if (threads > 1024) threads = 1024;
-  if (threads < 64) threads = 64;
+  const int nvec = own_pad(max_nown) / VecT<T>::W;
+  int threads = ((nvec + 31) / 32) * 32;
+  if (threads > 256) threads = 256;
+  if (threads < 32) threads = 32;
   k_patch_apply_t<T><<<np, threads, (size_t)max_n * sizeof(T), st>>>(p_n, p_nown, idx_off, idx, own_off, own,
                                                                      inv_off, invT, r, x, T(omega), dr, dc);
 }
