@@ -292,7 +292,8 @@ void build_device(Ctx& c) {
   c.stage_a = dalloc<double>(c, F.N);
   c.stage_b = dalloc<double>(c, F.N);
   c.dense_ws_len = std::max<int64_t>(max_dense, 1);
-  c.dense_ws = dalloc<double>(c, (size_t)c.dense_ws_len);
+  // patch factorisation workspace: max_dense elements of the factor precision
+  c.dense_ws = dalloc<double>(c, c.mixed ? ((size_t)c.dense_ws_len + 1) / 2 : (size_t)c.dense_ws_len);
   // coarse dense operator
   const int64_t n0 = c.hl[0].Ni;
   c.c_A = dalloc<double>(c, (size_t)n0 * n0);
@@ -399,12 +400,12 @@ void factor(Ctx& c) {
       launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
                                    D.p_padpos, D.val, B, ws, D.p_idx_off, D.dr32, D.dc32, c.stream);
       launch_patch_gj_t<float>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
-                               D.p_inv_off, ws, D.inv32, c.status, c.stream);
+                               D.p_inv_off, ws, D.inv32, c.status, B % 4 == 0, c.stream);
     } else {
       launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
                                     D.p_padpos, D.val, B, c.dense_ws, D.p_idx_off, D.dr, D.dc, c.stream);
       launch_patch_gj_t<double>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
-                                D.p_inv_off, c.dense_ws, D.inv, c.status, c.stream);
+                                D.p_inv_off, c.dense_ws, D.inv, c.status, B % 4 == 0, c.stream);
     }
     counted(c, 2);
   }

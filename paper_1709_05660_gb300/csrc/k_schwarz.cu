@@ -14,6 +14,7 @@
 //  * k_patch_apply: x[own] += omega * (B_k^{-1} r[R^delta_k])[own]; one thread
 //    per owned row, the block residual broadcast from shared memory.
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -102,13 +103,25 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
     if (lane == 0) Dr[i] = s;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  // column maxima: 32-column chunks, warps stride over rows (coalesced), then
+  // a shared-memory reduction over the warps
+  __shared__ double cmax[32][33];
+  for (int c0 = 0; c0 < n; c0 += kWarp) {
+    const int j = c0 + lane;
     double m = 0.0;
-    for (int i = 0; i < n; ++i) m = fmax(m, fabs((double)D[(int64_t)i * n + j]));
-    const T s = T(pow2_inv(m));
-    for (int i = 0; i < n; ++i) D[(int64_t)i * n + j] *= s;
-    Dc[j] = s;
+    if (j < n)
+      for (int i = wid; i < n; i += nw) m = fmax(m, fabs((double)D[(int64_t)i * n + j]));
+    cmax[wid][lane] = m;
+    __syncthreads();
+    if (wid == 0) {
+      double mm = 0.0;
+      for (int w = 0; w < nw; ++w) mm = fmax(mm, cmax[w][lane]);
+      if (j < n) Dc[j] = T(pow2_inv(mm));
+    }
+    __syncthreads();
   }
+  for (int i = wid; i < n; i += nw)
+    for (int j = lane; j < n; j += kWarp) D[(int64_t)i * n + j] *= Dc[j];
 }
 
 // Step k pivots on the unused row p with the largest |M[p][k]|; all rows are
@@ -293,45 +306,28 @@ k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
       if (lane == 0) live[i] = any != 0u;
     }
     __syncthreads();
-    // trailing rank-wp update: each thread owns a 4-row x 4-column register
-    // tile (rows i0..i0+3 of its warp's group, columns j0 + lane + 32 q)
+    // trailing rank-wp update, 4 rows per warp pass sharing each R load
+    // (the FP64 pipe, not shared memory, bounds this loop on this part)
     for (int g = wid; 4 * g < n; g += nw) {
       const int i0 = 4 * g;
       bool any = false;
 #pragma unroll
       for (int r = 0; r < 4; ++r) any |= (i0 + r < n) && live[i0 + r];
       if (!any) continue;
-      for (int j0 = 0; j0 < n; j0 += 4 * kWarp) {
-        int jq[4];
+      for (int j = lane; j < n; j += kWarp) {
+        if (j >= k0 && j < k0 + wp) continue;
+        T acc[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = j0 + lane + kWarp * q;
-          jq[q] = (j < n && !(j >= k0 && j < k0 + wp)) ? j : -1;
-        }
-        T acc[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
+        for (int r = 0; r < 4; ++r) acc[r] = T(0);
         for (int m = 0; m < wp; ++m) {
-          T gv[4], rv[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) gv[r] = (i0 + r < n) ? G[(i0 + r) * GS + m] : T(0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) rv[q] = jq[q] >= 0 ? R[m * n + jq[q]] : T(0);
+          const T rv = R[m * n + j];
 #pragma unroll
           for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[r][q] += gv[r] * rv[q];
+            if (i0 + r < n) acc[r] += G[(i0 + r) * GS + m] * rv;
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (i0 + r >= n || !live[i0 + r]) continue;
-          T* Mi = M + (int64_t)(i0 + r) * n;
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (jq[q] >= 0) Mi[jq[q]] += acc[r][q];
-        }
+        for (int r = 0; r < 4; ++r)
+          if (i0 + r < n && live[i0 + r]) M[(int64_t)(i0 + r) * n + j] += acc[r];
       }
     }
     __syncthreads();
@@ -362,6 +358,205 @@ k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
   if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
 }
 
+// FP32 panel-blocked Gauss-Jordan, same sweep as k_patch_gj_blk with:
+//  * ping-pong panel buffers: step m reads buffer m&1 and writes the other, so
+//    a step needs a single barrier; each warp updates its own rows (i = warp
+//    mod nw) and, in the same pass, finds its pivot candidate for the next
+//    column, published per warp in shared memory;
+//  * the trailing rank-32 update reads the transposed panel G'^T and the old
+//    pivot rows R with float4 shared-memory loads: 4 rows x 4 columns per
+//    thread, 16 FMAs per 2 loads, the global tile prefetched before the loop.
+// Requires n % 4 == 0 (true for the 2D block layout, B = 4).
+// Panel width W = 32 (one lane per panel column) or 16 for large blocks.
+template <int W>
+__global__ void __launch_bounds__(1024, 1)
+k_patch_gj_f32(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
+               const int64_t* __restrict__ dense_off, const int64_t* __restrict__ own_off,
+               const int32_t* __restrict__ own, const int64_t* __restrict__ inv_off, float* __restrict__ dense,
+               float* __restrict__ invT, int32_t* __restrict__ status, int max_n) {
+  constexpr int GS = W + 1;
+  static_assert(W == 16 || W == 32, "panel width");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = blockIdx.x;
+  const int n = p_n[p];
+  float* Gbuf0 = reinterpret_cast<float*>(smem_raw);          // max_n * GS
+  float* Gbuf1 = Gbuf0 + (size_t)max_n * GS;                   // max_n * GS
+  float* R = Gbuf1 + (size_t)max_n * GS;                       // W * max_n
+  float* cand_v = R + (size_t)W * max_n;                       // 2 * 32
+  int* cand_i = reinterpret_cast<int*>(cand_v + 64);           // 2 * 32
+  int* piv = cand_i + 64;                                      // max_n
+  int* qinv = piv + max_n;                                     // max_n
+  uint8_t* used = reinterpret_cast<uint8_t*>(qinv + max_n);   // max_n
+  uint8_t* live = used + max_n;                                // max_n
+  __shared__ int s_sing;
+  float* M = dense + dense_off[p];
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
+  if (threadIdx.x == 0) s_sing = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += W) {
+    const int wp = min(W, n - k0);
+    // panel load (and candidates for its first column)
+    float best = -1.f;
+    int bi = -1;
+    for (int i = wid; i < n; i += nw) {
+      const float v = lane < wp ? M[(int64_t)i * n + k0 + lane] : 0.f;
+      if (lane < W) Gbuf0[i * GS + lane] = v;
+      const float c0 = __shfl_sync(0xffffffffu, v, 0);
+      if (!used[i]) {
+        float a = fabsf(c0);
+        if (!(a >= 0.f)) a = 0.f;
+        if (a > best) { best = a; bi = i; }
+      }
+    }
+    if (lane == 0) { cand_v[wid] = best; cand_i[wid] = bi; }
+    __syncthreads();
+    for (int m = 0; m < wp; ++m) {
+      const float* src = (m & 1) ? Gbuf1 : Gbuf0;
+      float* dst = (m & 1) ? Gbuf0 : Gbuf1;
+      const float* cv = cand_v + (m & 1) * 32;
+      const int* ci = cand_i + (m & 1) * 32;
+      // final pivot choice: every warp reduces the nw (= 32) warp candidates
+      // with shuffles (lane l holds candidate l); same result in every warp
+      float bv = lane < nw ? cv[lane] : -1.f;
+      int pr = lane < nw ? ci[lane] : -1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, pr, o);
+        if (oi >= 0 && (pr < 0 || ov > bv || (ov == bv && oi < pr))) { bv = ov; pr = oi; }
+      }
+      float pv = src[pr * GS + m];
+      if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+        if (threadIdx.x == 0) s_sing = 1;
+        pv = 1.f;
+      }
+      const float rp = 1.f / pv;
+      const float prl = lane < W ? src[pr * GS + lane] : 0.f;
+      best = -1.f;
+      bi = -1;
+      for (int i = wid; i < n; i += nw) {
+        const float g = lane < W ? src[i * GS + lane] : 0.f;
+        const float f = __shfl_sync(0xffffffffu, g, m) * rp;
+        float val;
+        if (i == pr) val = (lane == m) ? rp : prl * rp;
+        else val = (lane == m) ? -f : g - f * prl;
+        if (lane >= wp) val = 0.f;
+        if (lane < W) dst[i * GS + lane] = val;
+        if (i == pr && lane == 0) used[i] = 1;
+        if (m + 1 < wp && i != pr && !used[i]) {
+          float a = fabsf(__shfl_sync(0xffffffffu, val, m + 1));
+          if (!(a >= 0.f)) a = 0.f;
+          if (a > best) { best = a; bi = i; }
+        } else {
+          __shfl_sync(0xffffffffu, val, 0);   // keep the warp converged on the shuffle
+        }
+      }
+      if (lane == 0) { cand_v[((m + 1) & 1) * 32 + wid] = best; cand_i[((m + 1) & 1) * 32 + wid] = bi; }
+      if (threadIdx.x == 0) piv[k0 + m] = pr;
+      __syncthreads();
+    }
+    float* G = (wp & 1) ? Gbuf1 : Gbuf0;     // final panel
+    float* Gt = (wp & 1) ? Gbuf0 : Gbuf1;    // (G - E_P)^T, row stride n
+    // old pivot rows, panel write-back, transposed G - E_P, live rows
+    for (int m = wid; m < wp; m += nw) {
+      const float4* Mp = reinterpret_cast<const float4*>(M + (int64_t)piv[k0 + m] * n);
+      float4* Rm = reinterpret_cast<float4*>(R + m * n);
+      for (int j = lane; j < n / 4; j += kWarp) Rm[j] = Mp[j];
+    }
+    for (int i = wid; i < n; i += nw) {
+      const float g = lane < W ? G[i * GS + lane] : 0.f;
+      if (lane < wp) M[(int64_t)i * n + k0 + lane] = g;
+      const float gm = (lane < wp && piv[k0 + lane] == i) ? g - 1.f : g;
+      if (lane < W) Gt[lane * n + i] = lane < wp ? gm : 0.f;
+      const unsigned any = __ballot_sync(0xffffffffu, lane < wp && gm != 0.f);
+      if (lane == 0) live[i] = any != 0u;
+    }
+    __syncthreads();
+    // trailing update: rows i0..i0+3 (one float4 of G'^T), columns j..j+3
+    const int ngr = n / 4, ncg = n / 4;
+    const float inv_ncg = 1.f / (float)ncg;
+    for (int t = threadIdx.x; t < ngr * ncg; t += blockDim.x) {
+      // t = gr * ncg + cgp without an integer division (exact for t < 2^22)
+      const int gr = __float2int_rz(((float)t + 0.5f) * inv_ncg);
+      const int cgp = t - gr * ncg;
+      const int i0 = 4 * gr, j = 4 * cgp;
+      if (!(live[i0] | live[i0 + 1] | live[i0 + 2] | live[i0 + 3])) continue;
+      if (j >= k0 && j + 3 < k0 + wp) continue;   // fully inside the panel
+      float4 old[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) old[r] = *reinterpret_cast<const float4*>(M + (int64_t)(i0 + r) * n + j);
+      float acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+#pragma unroll 8
+      for (int m = 0; m < wp; ++m) {
+        const float4 gv = *reinterpret_cast<const float4*>(Gt + m * n + i0);   // broadcast in the warp
+        const float4 rv = *reinterpret_cast<const float4*>(R + m * n + j);
+        const float g4[4] = {gv.x, gv.y, gv.z, gv.w};
+        const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] += g4[r] * r4[q];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (!live[i0 + r]) continue;
+        float4 o = old[r];
+        float* ov = reinterpret_cast<float*>(&o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (!(j + q >= k0 && j + q < k0 + wp)) ov[q] += acc[r][q];
+        *reinterpret_cast<float4*>(M + (int64_t)(i0 + r) * n + j) = o;
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
+  __syncthreads();
+  float* tile = Gbuf0;   // 32 x 33
+  const int nown = p_nown[p];
+  const int32_t* ow = own + own_off[p];
+  float* out = invT + inv_off[p];
+  for (int o0 = 0; o0 < own_pad(nown); o0 += 32) {
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int oo = t / 32, cc = t % 32;
+        const int o = o0 + oo, c = c0 + cc;
+        if (o < nown && c < n) tile[oo * 33 + cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int cc = t / 32, oo = t % 32;
+        const int o = o0 + oo, c = c0 + cc;
+        if (o < own_pad(nown) && c < n) out[(int64_t)c * own_pad(nown) + o] = o < nown ? tile[oo * 33 + cc] : 0.f;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
+}
+
+size_t gj_f32_smem(int max_n, int W) {
+  return ((size_t)2 * max_n * (W + 1) + (size_t)W * max_n + 64) * sizeof(float) + 64 * sizeof(int) +
+         2 * (size_t)max_n * sizeof(int) + 2 * (size_t)max_n + 64;
+}
+
+template <int W>
+bool try_gj_f32(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
+                const int64_t* own_off, const int32_t* own, const int64_t* inv_off, float* dense, float* invT,
+                int32_t* status, cudaStream_t st) {
+  const size_t smem = gj_f32_smem(max_n, W);
+  if (smem > 225 * 1024 || max_n % 4 != 0 || (size_t)max_n * (W + 1) < 32 * 33) return false;
+  cudaFuncSetAttribute(k_patch_gj_f32<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_patch_gj_f32<W><<<np, 1024, smem, st>>>(p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status,
+                                            max_n);
+  return true;
+}
+
 template <typename T, int W>
 size_t gj_blk_smem(int n) {
   return (size_t)n * (W + 1) * sizeof(T) + (size_t)W * n * sizeof(T) + (size_t)n * sizeof(T) + W * sizeof(T) +
@@ -386,53 +581,67 @@ template <> struct VecT<double> {
 };
 
 
-template <typename T>
-__global__ void __launch_bounds__(256)
+// Thread (v, g): owned-row vector v, column group g of CG; the CG partial
+// sums of each owned row are combined in shared memory.
+template <typename T, int CG>
+__global__ void __launch_bounds__(512)
 k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
                 const int64_t* __restrict__ idx_off, const int32_t* __restrict__ idx,
                 const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
                 const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
-                T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc) {
+                T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc, int vstride) {
   using VT = VecT<T>;
   constexpr int W = VT::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* rs = reinterpret_cast<T*>(smem_raw);
   const int p = blockIdx.x;
   const int n = p_n[p];
+  T* rs = reinterpret_cast<T*>(smem_raw);              // n (padded to 4)
   const int32_t* id = idx + idx_off[p];
   const T* Dr = dr + idx_off[p];
   const T* Dc = dc + idx_off[p];
   for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]] * Dr[i];
-  __syncthreads();
   const int nown = p_nown[p];
-  const int np = own_pad(nown);
-  const int nvec = np / W;
+  const int nvec = own_pad(nown) / W;
   const int32_t* ow = own + own_off[p];
   const typename VT::V* Bi = reinterpret_cast<const typename VT::V*>(invT + inv_off[p]);
-  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+  T* partial = rs + ((n + 3) & ~3);                    // CG * vstride * W partial sums
+  __syncthreads();
+  const int g = threadIdx.x / vstride;                 // column group
+  const int vt = threadIdx.x % vstride;
+  const int c_lo = (int)(((int64_t)n * g) / CG), c_hi = (int)(((int64_t)n * (g + 1)) / CG);
+  for (int v0 = 0; v0 < nvec; v0 += vstride) {
+    const int v = v0 + vt;
     T a0[W], a1[W];
 #pragma unroll
     for (int q = 0; q < W; ++q) { a0[q] = T(0); a1[q] = T(0); }
-    int c = 0;
-    for (; c + 4 <= n; c += 4) {
-      const typename VT::V b0 = __ldg(Bi + (int64_t)c * nvec + v);
-      const typename VT::V b1 = __ldg(Bi + (int64_t)(c + 1) * nvec + v);
-      const typename VT::V b2 = __ldg(Bi + (int64_t)(c + 2) * nvec + v);
-      const typename VT::V b3 = __ldg(Bi + (int64_t)(c + 3) * nvec + v);
-      VT::fma(a0, b0, rs[c]);
-      VT::fma(a1, b1, rs[c + 1]);
-      VT::fma(a0, b2, rs[c + 2]);
-      VT::fma(a1, b3, rs[c + 3]);
+    if (v < nvec) {
+      int c = c_lo;
+      for (; c + 4 <= c_hi; c += 4) {
+        const typename VT::V b0 = __ldg(Bi + (int64_t)c * nvec + v);
+        const typename VT::V b1 = __ldg(Bi + (int64_t)(c + 1) * nvec + v);
+        const typename VT::V b2 = __ldg(Bi + (int64_t)(c + 2) * nvec + v);
+        const typename VT::V b3 = __ldg(Bi + (int64_t)(c + 3) * nvec + v);
+        VT::fma(a0, b0, rs[c]);
+        VT::fma(a1, b1, rs[c + 1]);
+        VT::fma(a0, b2, rs[c + 2]);
+        VT::fma(a1, b3, rs[c + 3]);
+      }
+      for (; c < c_hi; ++c) VT::fma(a0, __ldg(Bi + (int64_t)c * nvec + v), rs[c]);
     }
-    for (; c < n; ++c) VT::fma(a0, __ldg(Bi + (int64_t)c * nvec + v), rs[c]);
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
-      const int o = v * W + q;
+    for (int q = 0; q < W; ++q) partial[(g * vstride + vt) * W + q] = a0[q] + a1[q];
+    __syncthreads();
+    for (int t = threadIdx.x; t < vstride * W; t += blockDim.x) {
+      const int o = v0 * W + t;
       if (o < nown) {
+        T sum = T(0);
+#pragma unroll
+        for (int gg = 0; gg < CG; ++gg) sum += partial[gg * vstride * W + t];
         const int k = ow[o];
-        x[id[k]] += omega * Dc[k] * (a0[q] + a1[q]);
+        x[id[k]] += omega * Dc[k] * sum;
       }
     }
+    __syncthreads();
   }
 }
 
@@ -462,7 +671,7 @@ bool try_gj_blk(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, co
 template <typename T>
 void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
                        const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
-                       int32_t* status, cudaStream_t st) {
+                       int32_t* status, bool n_mult4, cudaStream_t st) {
   if (np <= 0) return;
   // small blocks: the whole matrix fits in shared memory (unblocked sweep)
   const size_t base = (size_t)max_n * (2 * sizeof(T) + 2 * sizeof(int)) + ((max_n + 15) / 16) * 16;
@@ -474,6 +683,12 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
     return;
   }
   // larger blocks: panel-blocked sweep with the widest panel that fits
+  if (std::is_same<T, float>::value && n_mult4) {
+    float* d = reinterpret_cast<float*>(dense);
+    float* o = reinterpret_cast<float*>(invT);
+    if (try_gj_f32<32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
+    if (try_gj_f32<16>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
+  }
   if (try_gj_blk<T, 32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status, st)) return;
   if (try_gj_blk<T, 16>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status, st)) return;
   if (try_gj_blk<T, 8>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status, st)) return;
@@ -488,12 +703,14 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
                           const T* dc, cudaStream_t st) {
   if (np <= 0) return;
+  constexpr int CG = 4;                       // column groups per block
   const int nvec = own_pad(max_nown) / VecT<T>::W;
-  int threads = ((nvec + 31) / 32) * 32;
-  if (threads > 256) threads = 256;
-  if (threads < 32) threads = 32;
-  k_patch_apply_t<T><<<np, threads, (size_t)max_n * sizeof(T), st>>>(p_n, p_nown, idx_off, idx, own_off, own,
-                                                                     inv_off, invT, r, x, T(omega), dr, dc);
+  int vstride = ((nvec + 31) / 32) * 32;      // threads per column group
+  if (vstride > 128) vstride = 128;
+  const int threads = vstride * CG;
+  const size_t smem = ((size_t)((max_n + 3) & ~3) + (size_t)CG * vstride * VecT<T>::W) * sizeof(T);
+  k_patch_apply_t<T, CG><<<np, threads, smem, st>>>(p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x,
+                                                    T(omega), dr, dc, vstride);
 }
 
 #define FSI_INST(T)                                                                                              \
@@ -501,7 +718,7 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
                                          const int64_t*, const int32_t*, const double*, int, T*,                \
                                          const int64_t*, T*, T*, cudaStream_t);                                 \
   template void launch_patch_gj_t<T>(int, int, const int32_t*, const int32_t*, const int64_t*, const int64_t*, \
-                                     const int32_t*, const int64_t*, T*, T*, int32_t*, cudaStream_t);           \
+                                     const int32_t*, const int64_t*, T*, T*, int32_t*, bool, cudaStream_t);     \
   template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \
                                         const int32_t*, const int64_t*, const int32_t*, const int64_t*,        \
                                         const T*, const T*, T*, double, const T*, const T*, cudaStream_t);

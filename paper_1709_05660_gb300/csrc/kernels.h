@@ -55,7 +55,7 @@ void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off,
 template <typename T>
 void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
                        const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
-                       int32_t* status, cudaStream_t st);
+                       int32_t* status, bool n_mult4, cudaStream_t st);
 template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,

@@ -377,7 +377,8 @@ def _oracle_rows(prob, lev, y, nodes):
     return rows, rres
 
 
-@pytest.mark.parametrize("cfg,precision", [("c2_2d_l5", 0), ("c2_2d_l5", 1)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("cfg,precision", [("c2_2d_l5", 0), ("c2_2d_l5", 1), ("c3_2d_l6", 1), ("c3_2d_l6", 0)],
+                         ids=["c2-fp64", "c2-mixed", "c3-mixed", "c3-fp64"])
 def test_full_size_newton_step_sampled(cfg, precision):
     fsi = _fsi()
     prob, opts = CONFIGS[cfg]
