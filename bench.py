@@ -360,6 +360,8 @@ def run_gpu(args, rank, world):
             "phase_ms": main["phase_ms"], "roofline": roof, "kernel_classes": classes, "cpu_baseline": cpu,
             "e2e": main["e2e"], "gpu_launches": main["launches"], "clocks": main["clocks"],
         }
+        if not args.no_serve and world == 1:
+            line["served"] = run_serve(args, n_requests=32, max_levels=4, quiet=True)
         if fp64 is not None:
             r64, c64 = _roofline(fp64["kst"], args.steps)
             line["fp64_path"] = {"value": fp64["value"], "ms_per_step": fp64["per_step"],
@@ -370,6 +372,102 @@ def run_gpu(args, rank, world):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+
+# ----------------------------------------------------------------------------
+# serving (continuous batching of Newton-step requests)
+# ----------------------------------------------------------------------------
+
+def serve_mix(seed: int, n_requests: int, max_levels: int):
+    """Seeded request mix: 2D channel instances with levels uniform in
+    [3, max_levels], shear modulus log-uniform in [1e4, 1e6], mean inflow
+    uniform in [0.1, 1], 3-8 Newton steps each (tiles 2x2 up to 4 levels,
+    4x4 above)."""
+    from paper_1709_05660_gb300.workloads import Problem, SolverOpts
+    rng = np.random.Generator(np.random.PCG64(seed))
+    insts, total = [], 0
+    iid = 1
+    while total < n_requests:
+        lv = int(rng.integers(3, max_levels + 1))
+        mu = float(10 ** rng.uniform(4, 6))
+        U = float(rng.uniform(0.1, 1.0))
+        steps = int(rng.integers(3, 9))
+        steps = min(steps, n_requests - total)
+        insts.append((iid, Problem(levels=lv, mu_s=mu, U=U), SolverOpts(tile=(2, 2) if lv <= 4 else (4, 4)), steps))
+        total += steps
+        iid += 1
+    # arrival order: interleave instances at random, keeping each instance's steps in order
+    order = []
+    remaining = {i[0]: i[3] for i in insts}
+    while remaining:
+        keys = sorted(remaining)
+        k = keys[int(rng.integers(0, len(keys)))]
+        order.append(k)
+        remaining[k] -= 1
+        if remaining[k] == 0:
+            del remaining[k]
+    return insts, order, rng
+
+
+def _serve_once(insts, order, prec, slots, budget, arrivals=None):
+    from dataclasses import replace
+    from paper_1709_05660_gb300 import fsi
+    spec = {i[0]: i for i in insts}
+    sizes = {}
+    for iid, prob, opts, _ in insts:
+        plan = fsi.FSI(prob, opts, plan_only=True)
+        sizes[iid] = int(plan.N[-1])
+        plan.close()
+    srv = fsi.Server(hbm_budget_bytes=budget, max_slots=slots)
+    done_steps = {iid: 0 for iid in spec}
+    tickets = []
+    t0 = time.perf_counter()
+    for r, iid in enumerate(order):
+        if arrivals is not None:
+            dt = arrivals[r] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+        _, prob, opts, steps = spec[iid]
+        k = done_steps[iid]
+        tickets.append(srv.submit(iid, prob, replace(opts, precision=prec),
+                                  noise=noise(sizes[iid], iid) if k == 0 else None, last=(k == steps - 1)))
+        done_steps[iid] += 1
+    srv.drain()
+    wall = time.perf_counter() - t0
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = all(r["status"] == 0 for r in res)
+    worst = max(r["rel_res"] for r in res)
+    return {"solves_per_s": len(res) / wall, "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "requests": len(res), "all_ok": ok,
+            "max_true_rel_residual": worst}
+
+
+def run_serve(args, n_requests=None, max_levels=None, quiet=False):
+    n_requests = n_requests or args.serve_requests
+    max_levels = max_levels or args.serve_max_levels
+    insts, order, rng = serve_mix(0, n_requests, max_levels)
+    budget = int(args.serve_budget_gb * 1e9)
+    out = {}
+    for prec, name in ((1, "mixed"), (0, "fp64")):
+        closed = _serve_once(insts, order, prec, args.serve_slots, budget)
+        lam = 0.8 * closed["solves_per_s"]
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=len(order)))
+        pois = _serve_once(insts, order, prec, args.serve_slots, budget, arrivals=arr)
+        pois["arrival_rate_per_s"] = lam
+        out[name] = {"closed_loop": closed, "poisson": pois}
+    summary = {"requests": len(order), "instances": len(insts), "levels": [3, max_levels], "slots": args.serve_slots,
+               "budget_gb": args.serve_budget_gb, "mix": "2D channel, mu_s log-U[1e4,1e6], U U[0.1,1], 3-8 steps",
+               **out}
+    if not quiet:
+        line = {"metric": "served Newton-step solves/s and p50/p99 latency (Poisson arrivals at 0.8x capacity)",
+                "value": out["mixed"]["poisson"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic (seeded request mix)",
+                "config": {"workload": "serving"}, "serving": summary}
+        print(json.dumps(line), flush=True)
+    return summary
 
 
 _TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
@@ -394,6 +492,12 @@ def main():
     ap.add_argument("--config", default="c2_2d_l5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed-only", action="store_true", help="skip the FP64-path measurement")
+    ap.add_argument("--serve", action="store_true", help="serving benchmark (request mix) instead")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-max-levels", type=int, default=6)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the small served run of the default line")
     ap.add_argument("--cpu-frac", type=float, default=0.25)
     ap.add_argument("--ref-frac", type=float, default=1.0 / 16)
     ap.add_argument("--ref-iters", type=int, default=15)
@@ -404,6 +508,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.serve:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if rank == 0:
+            run_serve(args)
     else:
         run_gpu(args, rank, world)
 

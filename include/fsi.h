@@ -113,7 +113,8 @@ void fsi_destroy(fsi_ctx* ctx);
 const char* fsi_last_error(const fsi_ctx* ctx);
 
 /* Sizes: N (canonical unknowns) and scalar nnz of J per level (arrays of
- * `levels` entries, level 0 = coarse) and the device bytes held by ctx. */
+ * `levels` entries, level 0 = coarse) and the device bytes held by ctx (for a
+ * planned ctx: the bytes fsi_build_hierarchy would allocate). */
 int fsi_get_sizes(const fsi_ctx* ctx, int64_t* n_per_level, int64_t* nnz_per_level,
                   int64_t* hbm_bytes);
 
@@ -211,6 +212,58 @@ enum {
 int fsi_set_profiling(fsi_ctx* ctx, int on);
 int fsi_kernel_stats(fsi_ctx* ctx, int kind, double* device_ms, int64_t* launches, double* alg_bytes,
                      double* alg_flops);
+
+/* ---- serving: continuous batching of Newton-step requests ---------------
+ *
+ * A server owns `max_slots` worker threads, each with its own CUDA stream, and
+ * a device-memory budget.  A request asks for one Newton step (assemble,
+ * Galerkin, factor, FGMRES solve, update) of an instance identified by the
+ * caller.  The first request of an instance builds its hierarchy (admitted
+ * only when the planned device bytes fit in the budget left; otherwise it
+ * waits while other requests proceed); later requests reuse the resident
+ * hierarchy, state and factors; the request flagged `last` frees them.
+ * Requests of one instance run in submission order; requests of different
+ * instances run concurrently on different streams as slots free up.  Results
+ * do not depend on what else is running: every instance computes on its own
+ * buffers with a fixed reduction order. */
+typedef struct fsi_server fsi_server;
+
+typedef struct {
+  uint64_t instance;          /* caller-chosen instance id */
+  fsi_problem_desc desc;      /* read when the instance is first seen */
+  fsi_solver_opts opts;       /* read when the instance is first seen */
+  const double* noise;        /* first request: N host doubles for fsi_initial_state (copied at submit) */
+  int last;                   /* 1: free the instance after this step */
+  int keep_dx;                /* 1: keep the Newton update for fsi_serve_poll */
+} fsi_request;
+
+typedef struct {
+  int status;                 /* FSI_OK or the step's error code */
+  int iters;                  /* FGMRES iterations */
+  double rel_step;            /* ||dx|| / ||y|| */
+  double rel_res;             /* true relative residual of the solve */
+  double queue_ms;            /* submit -> start */
+  double run_ms;              /* start -> end */
+  double latency_ms;          /* submit -> end */
+  int64_t n;                  /* number of unknowns of the instance */
+} fsi_result;
+
+/* hbm_budget_bytes: device bytes the server may hold for instances; 0 = no
+ * limit.  max_slots: concurrent requests (1..64). */
+int fsi_server_create(int64_t hbm_budget_bytes, int max_slots, fsi_server** out);
+/* Queues a request; *ticket identifies it.  FSI_E_INVALID if the descriptor
+ * of a new instance is invalid or its planned size exceeds the whole budget. */
+int fsi_serve_submit(fsi_server* srv, const fsi_request* req, uint64_t* ticket);
+/* FSI_PENDING while queued or running; otherwise fills *out (and dx_out, N
+ * host doubles, when the request had keep_dx) and returns FSI_OK; the ticket
+ * is then released. */
+int fsi_serve_poll(fsi_server* srv, uint64_t ticket, fsi_result* out, double* dx_out);
+/* Blocks until every queued request has finished (results stay pollable). */
+int fsi_serve_drain(fsi_server* srv);
+/* Device bytes currently held by resident instances. */
+int64_t fsi_server_resident_bytes(const fsi_server* srv);
+/* Waits for running requests, frees every instance and the server. */
+int fsi_server_destroy(fsi_server* srv);
 
 #ifdef __cplusplus
 }

@@ -694,6 +694,34 @@ int check_level(const Ctx& c, int level, bool need_fine_side) {
 // ===========================================================================
 extern "C" {
 
+// Device bytes fsi_build_hierarchy will allocate for this plan (same sizes as
+// build_device), used for admission by device memory.
+static int64_t estimate_device_bytes(const Ctx& c) {
+  const bool mixed = c.opts.precision == FSI_MIXED;
+  const double fs = mixed ? 4.0 : 8.0;
+  const int B = c.B, nd = c.ndofe, m = c.opts.restart;
+  double b = 0.0, max_dense = 0.0;
+  const size_t L = c.hl.size();
+  for (size_t l = 0; l < L; ++l) {
+    const HostLevel& H = c.hl[l];
+    b += (H.nb + 1) * 4.0 + H.nnzb * 4.0 + H.nnzb * B * B * 8.0 + H.n_elem * (double)nd * nd * 8.0;
+    b += H.n_elem * (H.nloc * 4.0 + 1.0 + 2.0 * H.dim * 8.0 + (H.nloc + 1.0) * (H.nloc + 1.0) * 4.0 + 4.0);
+    b += H.n_nodes + H.Ni * (1.0 + 8.0 + 4.0 + 4.0) + H.N * 4.0 + H.Ni * 3.0 * 8.0;
+    if (l > 0) {
+      b += (H.P_ptr.size() + H.R_ptr.size()) * 4.0 + (H.P_col.size() + H.R_col.size()) * 12.0;
+      b += H.idx_total * 4.0 + H.own_total * 4.0 + H.n_patches * 8.0 * 8.0 + H.p_gmap.size() * 4.0 +
+           H.p_padpos.size() * 4.0 + H.inv_total * fs + 2.0 * H.idx_total * fs;
+      if (mixed) b += H.nnzb * B * B * 4.0 + (H.P_col.size() + H.R_col.size()) * 4.0 + H.Ni * 3.0 * 4.0;
+      max_dense = std::max(max_dense, (double)H.dense_total);
+    }
+  }
+  const HostLevel& F = c.hl.back();
+  const double n0 = (double)c.hl[0].Ni;
+  b += F.Ni * 8.0 * 2 + (m + 1.0) * F.Ni * 8.0 + m * (double)F.Ni * fs + F.Ni * 8.0 * 4 + F.N * 8.0 * 2;
+  b += max_dense * fs + 3.0 * n0 * n0 * 8.0 + F.n_elem * (double)nd * 8.0 + 1e6;
+  return (int64_t)b;
+}
+
 static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts* opts) {
   if (desc->transient != 0) throw ApiError(FSI_E_INVALID, "only steady problems are supported");
   if (opts->precision != FSI_FP64 && opts->precision != FSI_MIXED) throw ApiError(FSI_E_INVALID, "bad precision");
@@ -706,6 +734,7 @@ static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts
   c->B = 2 * desc->dim;
   c->nloc = desc->dim == 2 ? 9 : 27;
   c->ndofe = c->B * c->nloc + desc->dim + 1;
+  c->est_bytes = estimate_device_bytes(*c);
 }
 
 int fsi_plan_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opts, fsi_ctx** out) {
@@ -799,7 +828,7 @@ int fsi_get_sizes(const fsi_ctx* c, int64_t* n_per_level, int64_t* nnz_per_level
       nnz_per_level[l] = nnz;
     }
   }
-  if (hbm_bytes) *hbm_bytes = c->bytes;
+  if (hbm_bytes) *hbm_bytes = c->dl.empty() ? c->est_bytes : c->bytes;
   return FSI_OK;
 }
 

@@ -122,6 +122,7 @@ struct Ctx {
   std::vector<DevLevel> dl;
   std::vector<void*> allocs;
   int64_t bytes = 0;
+  int64_t est_bytes = 0;                  // planned device bytes (before building)
   std::string err;
   int64_t launches = 0;
   int dim = 2, B = 4, nloc = 9, ndofe = 39;

@@ -1,0 +1,253 @@
+// Continuous-batching server for Newton-step requests (the serving form of
+// the solver): worker threads with their own CUDA streams pick the oldest
+// runnable request - an instance not already running, admitted by planned
+// device bytes against the budget - and run one fsi_newton_step on that
+// instance's resident hierarchy.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fsi.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Instance {
+  fsi_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;   // stream the ctx was built on
+  int64_t bytes = 0;
+  bool busy = false;
+  int64_t n = 0;
+};
+
+struct Ticket {
+  uint64_t id = 0;
+  fsi_request req{};
+  std::vector<double> noise;       // copy of the first request's noise
+  std::vector<double> dx;          // kept update (keep_dx)
+  fsi_result res{};
+  Clock::time_point t_submit, t_start, t_end;
+  int state = 0;                   // 0 queued, 1 running, 2 done
+  int64_t planned = 0;             // planned bytes when the request creates the instance
+};
+
+double ms(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+
+struct fsi_server {
+  int64_t budget = 0;
+  int64_t resident = 0;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<Ticket*> queue;
+  std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
+  std::map<uint64_t, Instance> inst;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;   // one per worker; destroyed after the instances
+  uint64_t next = 1;
+  int running = 0;
+  bool stop = false;
+
+  // first runnable ticket in arrival order (caller holds mu)
+  Ticket* pick() {
+    for (auto it = queue.begin(); it != queue.end(); ++it) {
+      Ticket* t = *it;
+      auto f = inst.find(t->req.instance);
+      if (f != inst.end() && f->second.busy) continue;                 // in order per instance
+      bool earlier_same = false;                                       // an older request of it waits
+      for (auto jt = queue.begin(); jt != it; ++jt)
+        if ((*jt)->req.instance == t->req.instance) { earlier_same = true; break; }
+      if (earlier_same) continue;
+      if (f == inst.end() && budget > 0 && resident + t->planned > budget) continue;   // admission
+      queue.erase(it);
+      return t;
+    }
+    return nullptr;
+  }
+
+  void work(int slot) {
+    cudaStream_t stream = streams[slot];
+    std::vector<double> dxbuf;
+    while (true) {
+      Ticket* t = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || (t = pick()) != nullptr; });
+        if (!t) break;
+        auto& in = inst[t->req.instance];
+        in.busy = true;
+        if (!in.ctx) resident += t->planned;   // reserve before building
+        t->state = 1;
+        t->t_start = Clock::now();
+        ++running;
+      }
+      Instance* in;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        in = &inst[t->req.instance];
+      }
+      int rc = FSI_OK;
+      if (!in->ctx) {
+        rc = fsi_build_hierarchy(&t->req.desc, &t->req.opts, stream, &in->ctx);
+        if (rc == FSI_OK) {
+          in->stream = stream;
+          int64_t nl[16], hb = 0;
+          fsi_get_sizes(in->ctx, nl, nullptr, &hb);
+          in->n = nl[t->req.desc.levels - 1];
+          in->bytes = hb;
+          std::vector<double> y(in->n);
+          rc = fsi_initial_state(in->ctx, t->noise.data(), y.data());
+          if (rc == FSI_OK) rc = fsi_set_state(in->ctx, y.data(), nullptr, nullptr, 0.0);
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        resident += (rc == FSI_OK ? in->bytes : 0) - t->planned;
+        if (rc != FSI_OK && in->ctx) {
+          fsi_destroy(in->ctx);
+          in->ctx = nullptr;
+        }
+      }
+      fsi_solve_stats st{};
+      double rel = 0.0;
+      if (rc == FSI_OK) {
+        // a ctx stays bound to the stream it was built on
+        dxbuf.assign(t->req.keep_dx ? in->n : 0, 0.0);
+        rc = fsi_newton_step(in->ctx, t->req.keep_dx ? dxbuf.data() : nullptr, &rel, &st);
+      }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        t->t_end = Clock::now();
+        t->res.status = rc;
+        t->res.iters = st.iters;
+        t->res.rel_step = rel;
+        t->res.rel_res = st.rel_res;
+        t->res.n = in->n;
+        t->res.queue_ms = ms(t->t_submit, t->t_start);
+        t->res.run_ms = ms(t->t_start, t->t_end);
+        t->res.latency_ms = ms(t->t_submit, t->t_end);
+        if (t->req.keep_dx) t->dx.swap(dxbuf);
+        t->noise.clear();
+        if (t->req.last || rc != FSI_OK) {
+          if (in->ctx) {
+            fsi_destroy(in->ctx);
+            in->ctx = nullptr;
+            resident -= in->bytes;
+          }
+          inst.erase(t->req.instance);
+        } else {
+          in->busy = false;
+        }
+        t->state = 2;
+        --running;
+      }
+      cv.notify_all();
+      done_cv.notify_all();
+    }
+  }
+};
+
+extern "C" {
+
+int fsi_server_create(int64_t hbm_budget_bytes, int max_slots, fsi_server** out) {
+  if (!out || max_slots < 1 || max_slots > 64 || hbm_budget_bytes < 0) return FSI_E_INVALID;
+  fsi_server* s = new fsi_server();
+  s->budget = hbm_budget_bytes;
+  s->streams.assign(max_slots, nullptr);
+  for (int i = 0; i < max_slots; ++i)
+    if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < i; ++j) cudaStreamDestroy(s->streams[j]);
+      delete s;
+      return FSI_E_CUDA;
+    }
+  for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s, i] { s->work(i); });
+  *out = s;
+  return FSI_OK;
+}
+
+int fsi_serve_submit(fsi_server* s, const fsi_request* req, uint64_t* ticket) {
+  if (!s || !req || !ticket) return FSI_E_INVALID;
+  std::unique_ptr<Ticket> t(new Ticket());
+  t->req = *req;
+  t->t_submit = Clock::now();
+  bool known;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    known = s->inst.count(req->instance) != 0;
+    for (Ticket* q : s->queue)
+      if (q->req.instance == req->instance) known = true;
+  }
+  if (!known) {
+    // new instance: validate the descriptor and plan its size on the host
+    fsi_ctx* plan = nullptr;
+    int rc = fsi_plan_hierarchy(&req->desc, &req->opts, &plan);
+    if (rc != FSI_OK) return rc;
+    int64_t nl[16], hb = 0;
+    fsi_get_sizes(plan, nl, nullptr, &hb);
+    const int64_t n = nl[req->desc.levels - 1];
+    fsi_destroy(plan);
+    if (s->budget > 0 && hb > s->budget) return FSI_E_INVALID;
+    if (!req->noise) return FSI_E_INVALID;
+    t->planned = hb;
+    t->noise.assign(req->noise, req->noise + n);
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  t->id = s->next++;
+  *ticket = t->id;
+  s->queue.push_back(t.get());
+  s->tickets[t->id] = std::move(t);
+  s->cv.notify_all();
+  return FSI_OK;
+}
+
+int fsi_serve_poll(fsi_server* s, uint64_t ticket, fsi_result* out, double* dx_out) {
+  if (!s) return FSI_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->tickets.find(ticket);
+  if (it == s->tickets.end()) return FSI_E_INVALID;
+  Ticket* t = it->second.get();
+  if (t->state != 2) return FSI_PENDING;
+  if (out) *out = t->res;
+  if (dx_out && !t->dx.empty()) std::memcpy(dx_out, t->dx.data(), t->dx.size() * sizeof(double));
+  s->tickets.erase(it);
+  return FSI_OK;
+}
+
+int fsi_serve_drain(fsi_server* s) {
+  if (!s) return FSI_E_INVALID;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->done_cv.wait(lk, [&] { return s->queue.empty() && s->running == 0; });
+  return FSI_OK;
+}
+
+int64_t fsi_server_resident_bytes(const fsi_server* s) { return s ? s->resident : 0; }
+
+int fsi_server_destroy(fsi_server* s) {
+  if (!s) return FSI_E_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->queue.clear();
+  }
+  s->cv.notify_all();
+  for (auto& w : s->workers) w.join();
+  for (auto& kv : s->inst)
+    if (kv.second.ctx) fsi_destroy(kv.second.ctx);
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamDestroy(st);
+  delete s;
+  return FSI_OK;
+}
+
+}  // extern "C"

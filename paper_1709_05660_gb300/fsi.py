@@ -32,7 +32,8 @@ SYMBOLS = (
     "fsi_newton_update", "fsi_newton_step", "fsi_export_csr", "fsi_export_dofmap", "fsi_export_patches",
     "fsi_apply_operator", "fsi_apply_vcycle", "fsi_apply_smoother", "fsi_restrict", "fsi_prolong",
     "fsi_launch_count", "fsi_plan_hierarchy", "fsi_export_transfer", "fsi_set_profiling",
-    "fsi_kernel_stats",
+    "fsi_kernel_stats", "fsi_server_create", "fsi_serve_submit", "fsi_serve_poll", "fsi_serve_drain",
+    "fsi_server_resident_bytes", "fsi_server_destroy",
 )
 
 # kernel classes for fsi_kernel_stats
@@ -63,6 +64,24 @@ class SolveStats(ctypes.Structure):
         ("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_res", ctypes.c_double),
         ("rho", ctypes.c_double), ("t_assemble_ms", ctypes.c_double), ("t_factor_ms", ctypes.c_double),
         ("t_solve_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("instance", ctypes.c_uint64), ("desc", ProblemDesc), ("opts", SolverOptsC),
+        ("noise", ctypes.c_void_p), ("last", ctypes.c_int), ("keep_dx", ctypes.c_int),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("iters", ctypes.c_int), ("rel_step", ctypes.c_double),
+        ("rel_res", ctypes.c_double), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+        ("latency_ms", ctypes.c_double), ("n", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -110,6 +129,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fsi_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.fsi_kernel_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.fsi_server_create.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.fsi_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.fsi_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result), vp]
+    lib.fsi_serve_drain.argtypes = [vp]
+    lib.fsi_server_resident_bytes.argtypes = [vp]
+    lib.fsi_server_resident_bytes.restype = ctypes.c_int64
+    lib.fsi_server_destroy.argtypes = [vp]
     lib.fsi_launch_count.argtypes = [vp]
     lib.fsi_launch_count.restype = ctypes.c_int64
     _lib = lib
@@ -310,3 +336,59 @@ class FSI:
 
     def launch_count(self) -> int:
         return int(self.lib.fsi_launch_count(self.h))
+
+
+class Server:
+    """Continuous-batching server of Newton-step requests (fsi_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_slots: int = 4):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self.lib.fsi_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h))
+        if rc != FSI_OK:
+            raise FSIError(rc, "fsi_server_create failed")
+        self.h = h
+
+    def submit(self, instance: int, prob: Problem, opts: SolverOpts, noise=None, last: bool = False,
+               keep_dx: bool = False) -> int:
+        r = Request()
+        r.instance = instance
+        r.desc = make_desc(prob)
+        r.opts = make_opts(opts)
+        if noise is not None:
+            noise = np.ascontiguousarray(noise, dtype=np.float64)
+            r.noise = noise.ctypes.data
+        r.last = 1 if last else 0
+        r.keep_dx = 1 if keep_dx else 0
+        t = ctypes.c_uint64()
+        rc = self.lib.fsi_serve_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if rc != FSI_OK:
+            raise FSIError(rc, "fsi_serve_submit rejected the request")
+        return t.value
+
+    def poll(self, ticket: int, dx_out=None):
+        """None while pending, else the result dict (dx written to dx_out)."""
+        res = Result()
+        rc = self.lib.fsi_serve_poll(self.h, ticket, ctypes.byref(res), _ptr(dx_out))
+        if rc == 1:
+            return None
+        if rc != FSI_OK:
+            raise FSIError(rc, "fsi_serve_poll failed")
+        return res.as_dict()
+
+    def drain(self):
+        self.lib.fsi_serve_drain(self.h)
+
+    def resident_bytes(self) -> int:
+        return int(self.lib.fsi_server_resident_bytes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fsi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,103 @@
+"""Serving form of the solver (continuous batching of Newton-step requests).
+
+* every result is bit-identical whether its instance runs alone or mixed with
+  other instances on other streams (each instance computes on its own buffers
+  with fixed reduction orders);
+* admission by device bytes: with a budget that holds one instance, a second
+  instance waits until the first one is freed, and both finish;
+* an instance larger than the whole budget is rejected at submit.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1709_05660_gb300.workloads import Problem, SolverOpts, noise  # noqa: E402
+
+INSTANCES = [
+    (11, Problem(levels=3, mu_s=1e5, U=0.3), SolverOpts(tile=(2, 2), precision=1)),
+    (12, Problem(levels=3, mu_s=8e5, U=0.9), SolverOpts(tile=(2, 2), precision=0)),
+    (13, Problem(levels=4, mu_s=3e4, U=0.5), SolverOpts(tile=(2, 2), precision=1)),
+]
+STEPS = 3
+
+
+def _fsi():
+    from paper_1709_05660_gb300 import fsi
+    return fsi
+
+
+def _n(prob):
+    from paper_1709_05660_gb300 import fsi
+    s = fsi.FSI(prob, SolverOpts(), plan_only=True)
+    n = int(s.N[-1])
+    s.close()
+    return n
+
+
+def _run(server, instances, order):
+    """Submits STEPS requests per instance in the given interleaving."""
+    tickets = {}
+    sizes = {iid: _n(p) for iid, p, _ in instances}
+    step = {iid: 0 for iid, _, _ in instances}
+    spec = {iid: (p, o) for iid, p, o in instances}
+    for iid in order:
+        p, o = spec[iid]
+        k = step[iid]
+        tickets[(iid, k)] = server.submit(iid, p, o, noise=noise(sizes[iid], iid) if k == 0 else None,
+                                          last=(k == STEPS - 1), keep_dx=True)
+        step[iid] += 1
+    server.drain()
+    out = {}
+    for key, t in tickets.items():
+        dx = np.empty(sizes[key[0]])
+        res = server.poll(t, dx)
+        assert res is not None and res["status"] == 0, res
+        out[key] = (dx, res)
+    return out
+
+
+def test_alone_vs_mixed_bitwise():
+    fsi = _fsi()
+    torch.cuda.set_device(0)
+    order = [iid for _ in range(STEPS) for iid, _, _ in INSTANCES]     # round-robin interleaving
+    srv = fsi.Server(hbm_budget_bytes=0, max_slots=3)
+    mixed = _run(srv, INSTANCES, order)
+    srv.close()
+    for inst in INSTANCES:
+        srv = fsi.Server(hbm_budget_bytes=0, max_slots=1)
+        alone = _run(srv, [inst], [inst[0]] * STEPS)
+        srv.close()
+        for k in range(STEPS):
+            a, _ = alone[(inst[0], k)]
+            m, res = mixed[(inst[0], k)]
+            assert np.array_equal(a, m), (inst[0], k, np.max(np.abs(a - m)))
+            assert res["rel_res"] <= inst[2].rtol
+    # Newton converges across the 3 steps of each instance
+    for iid, _, _ in INSTANCES:
+        assert mixed[(iid, STEPS - 1)][1]["rel_step"] < mixed[(iid, 0)][1]["rel_step"]
+
+
+def test_admission_by_device_bytes():
+    fsi = _fsi()
+    p, o = Problem(levels=3), SolverOpts(tile=(2, 2), precision=1)
+    plan = fsi.FSI(p, o, plan_only=True)
+    one = plan.hbm_bytes
+    n = int(plan.N[-1])
+    plan.close()
+    srv = fsi.Server(hbm_budget_bytes=int(one * 1.5), max_slots=2)
+    t1 = srv.submit(1, p, o, noise=noise(n, 1), last=True)
+    t2 = srv.submit(2, p, o, noise=noise(n, 2), last=True)
+    srv.drain()
+    r1, r2 = srv.poll(t1), srv.poll(t2)
+    assert r1["status"] == 0 and r2["status"] == 0
+    # the second instance could only start after the first was freed
+    assert r2["queue_ms"] >= r1["run_ms"] * 0.5 or r1["queue_ms"] >= r2["run_ms"] * 0.5
+    assert srv.resident_bytes() == 0
+    with pytest.raises(fsi.FSIError):
+        srv.submit(3, replace(p, levels=5), o, noise=noise(313860, 3))
+    srv.close()
