@@ -138,7 +138,9 @@ struct fsi_server {
         t->res.latency_ms = ms(t->t_submit, t->t_end);
         if (t->req.keep_dx) t->dx.swap(dxbuf);
         t->noise.clear();
-        if (t->req.last || rc != FSI_OK) {
+        // a step that did not converge leaves the instance (and its state) in
+        // place; other failures and the last request free it
+        if (t->req.last || (rc != FSI_OK && rc != FSI_E_NOT_CONVERGED)) {
           if (in->ctx) {
             fsi_destroy(in->ctx);
             in->ctx = nullptr;
