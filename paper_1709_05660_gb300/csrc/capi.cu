@@ -296,10 +296,19 @@ void build_device(Ctx& c) {
   c.dense_ws = dalloc<double>(c, c.mixed ? ((size_t)c.dense_ws_len + 1) / 2 : (size_t)c.dense_ws_len);
   // coarse dense operator
   const int64_t n0 = c.hl[0].Ni;
-  c.c_A = dalloc<double>(c, (size_t)n0 * n0);
+  c.c_A = dalloc<double>(c, (size_t)n0 * n0);   // banded LU in dense column-major storage
   c.c_B = dalloc<double>(c, (size_t)2 * n0);   // pivot-column buffer of the coarse sweep
-  c.c_inv = dalloc<double>(c, (size_t)n0 * n0);
+  c.c_inv = dalloc<double>(c, (size_t)n0 * n0);   // column-major inverse
   c.c_piv = dalloc<int32_t>(c, n0);
+  c.c_part = dalloc<double>(c, (size_t)((n0 + 31) / 32) * n0);   // coarse GEMV chunk partials
+  {
+    const HostLevel& H0 = c.hl[0];
+    std::vector<int32_t> pinv(H0.Ni);
+    for (int64_t i = 0; i < H0.Ni; ++i) pinv[H0.coarse_perm[i]] = (int32_t)i;
+    c.coarse_perm = upload(c, H0.coarse_perm);
+    c.coarse_pinv = upload(c, pinv);
+    c.coarse_bw = H0.coarse_bw;
+  }
   c.status = dalloc<int32_t>(c, ST_COUNT);
   ck(cudaMemsetAsync(c.status, 0, ST_COUNT * sizeof(int32_t), c.stream), "memset");
   (void)nloc;
@@ -413,11 +422,15 @@ void factor(Ctx& c) {
   const int64_t n0 = C.Ni;
   {
     const double nn = (double)n0;
-    Prof pr(c, FSI_K_COARSE_FACTOR, nn * nn * 8.0 * 2.0, 2.0 * nn * nn * nn, 4);
-    launch_dense_gather(B, C.nb, C.rowptr, C.col, C.val, c.coarse_pad_list, c.n_coarse_pads, n0, c.c_A, c.stream);
+    // banded LU (2 n kl (kl + ku) flops) + inverse columns (~2 n^2 (kl + ku) flops, sparsity aside)
+    const double bw = (double)c.coarse_bw;
+    Prof pr(c, FSI_K_COARSE_FACTOR, nn * nn * 8.0 * 3.0, 2.0 * nn * bw * 2.0 * bw + 2.0 * nn * nn * 2.0 * bw, 4);
+    launch_dense_gather(B, C.nb, C.rowptr, C.col, C.val, c.coarse_pad_list, c.n_coarse_pads, c.coarse_perm, n0,
+                        c.c_A, c.stream);
     counted(c, c.n_coarse_pads > 0 ? 2 : 1);
-    if (launch_coarse_gj(n0, c.c_A, c.c_B, c.c_inv, c.c_piv, c.status, c.sm_count, c.stream) != 0)
-      throw ApiError(FSI_E_CUDA, "cooperative launch of the coarse Gauss-Jordan kernel failed");
+    const int rc = launch_coarse_lu_inverse(n0, c.coarse_bw, c.coarse_bw, c.c_A, c.c_B, c.c_inv, c.c_piv,
+                                            c.coarse_perm, c.coarse_pinv, c.status, c.sm_count, c.stream);
+    if (rc != 0) throw ApiError(FSI_E_CUDA, "banded coarse LU launch failed (" + std::to_string(rc) + ")");
     counted(c, 2);
   }
   check_status(c);
@@ -463,8 +476,8 @@ template <> struct VC<double> {
   static void coarse(Ctx& c, const double* b, double* x) {
     const double n0 = (double)c.dl[0].Ni;
     Prof pr(c, FSI_K_TRANSFER, n0 * n0 * 8.0 + 2.0 * n0 * 8.0, 2.0 * n0 * n0);
-    launch_gemv(c.dl[0].Ni, c.c_inv, b, x, c.stream);
-    counted(c);
+    launch_gemv(c.dl[0].Ni, c.c_inv, b, x, c.c_part, c.stream);
+    counted(c, 2);
   }
 };
 template <> struct VC<float> {
@@ -501,8 +514,8 @@ template <> struct VC<float> {
     // the coarsest-grid solve stays FP64 (FP64 inverse, FP64 accumulation)
     const double n0 = (double)c.dl[0].Ni;
     Prof pr(c, FSI_K_TRANSFER, n0 * n0 * 8.0 + 2.0 * n0 * 4.0, 2.0 * n0 * n0);
-    launch_gemv_f32io(c.dl[0].Ni, c.c_inv, b, x, c.stream);
-    counted(c);
+    launch_gemv_f32io(c.dl[0].Ni, c.c_inv, b, x, c.c_part, c.stream);
+    counted(c, 2);
   }
 };
 

@@ -63,6 +63,9 @@ struct HostLevel {
   std::vector<int64_t> p_elem_off;
   int64_t dense_total = 0, inv_total = 0, idx_total = 0, own_total = 0;
   int max_n = 0, max_nown = 0;
+  // coarse level: bandwidth-reducing ordering (internal unknown -> position)
+  std::vector<int32_t> coarse_perm;
+  int coarse_bw = 0;
 };
 
 bool build_host_hierarchy(const fsi_problem_desc& d, const fsi_solver_opts& o,
@@ -143,9 +146,13 @@ struct Ctx {
   // coarse dense inverse
   double *c_A = nullptr, *c_B = nullptr, *c_inv = nullptr;
   int32_t* c_piv = nullptr;
+  double* c_part = nullptr;               // coarse GEMV partial sums
   int32_t* status = nullptr;              // device status flags
   double* tmp_re = nullptr;               // finest element residuals (n_elem * ndofe)
   int32_t* coarse_pad_list = nullptr;     // padding slots of the coarse dense operator
+  int32_t* coarse_perm = nullptr;         // internal unknown -> banded position
+  int32_t* coarse_pinv = nullptr;         // banded position -> internal unknown
+  int coarse_bw = 0;
   int n_coarse_pads = 0;
   float t_assemble = 0.f, t_factor = 0.f, t_solve = 0.f;
   int red_blocks = 0;

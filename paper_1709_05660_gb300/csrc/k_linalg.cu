@@ -337,148 +337,238 @@ void launch_nonfinite_check(int64_t n, const double* v, int32_t* status, cudaStr
 // ---------------------------------------------------------------------------
 // coarse level
 // ---------------------------------------------------------------------------
-// Dense coarse operator in column-major order: A[col * n + row].
+// Dense coarse operator in the banded ordering, column-major:
+// A[perm[col] * n + perm[row]] (padding slots get 1 on the diagonal).
 __global__ void k_dense_gather(int B, int64_t nb, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                               const double* __restrict__ val, int64_t n, double* __restrict__ A) {
+                               const double* __restrict__ val, const int32_t* __restrict__ perm, int64_t n,
+                               double* __restrict__ A) {
   const int64_t br = blockIdx.x;
   if (br >= nb) return;
   const int BB = B * B;
   for (int32_t k = rowptr[br]; k < rowptr[br + 1]; ++k)
     for (int e = threadIdx.x; e < BB; e += blockDim.x) {
       const int ci = e / B, cj = e % B;
-      A[((int64_t)col[k] * B + cj) * n + br * B + ci] = val[(int64_t)k * BB + e];
+      const int64_t r = perm[br * B + ci], c = perm[(int64_t)col[k] * B + cj];
+      A[c * n + r] = val[(int64_t)k * BB + e];
     }
 }
 
-__global__ void k_set_diag(const int32_t* __restrict__ list, int cnt, int64_t n, double* __restrict__ A) {
+__global__ void k_set_diag(const int32_t* __restrict__ list, int cnt, const int32_t* __restrict__ perm, int64_t n,
+                           double* __restrict__ A) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < cnt) A[(int64_t)list[t] * n + list[t]] = 1.0;
+  if (t < cnt) {
+    const int64_t q = perm[list[t]];
+    A[q * n + q] = 1.0;
+  }
 }
 
 void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
-                         const int32_t* pad_list, int npad, int64_t n, double* A, cudaStream_t st) {
+                         const int32_t* pad_list, int npad, const int32_t* perm, int64_t n, double* A,
+                         cudaStream_t st) {
   cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(double), st);
-  k_dense_gather<<<(unsigned)nb, 64, 0, st>>>(B, nb, rowptr, col, val, n, A);
-  if (npad > 0) k_set_diag<<<(npad + 255) / 256, 256, 0, st>>>(pad_list, npad, n, A);
+  k_dense_gather<<<(unsigned)nb, 64, 0, st>>>(B, nb, rowptr, col, val, perm, n, A);
+  if (npad > 0) k_set_diag<<<(npad + 255) / 256, 256, 0, st>>>(pad_list, npad, perm, n, A);
 }
 
-// Cooperative in-place Gauss-Jordan with partial pivoting on the coarse
-// operator, stored column-major; block b owns the columns j = b (mod grid).
-// Step k: every block reads the current column k from a two-slot buffer,
-// finds the pivot row p itself (same deterministic rule everywhere) and
-// updates the columns it owns,
-//     M[:, j] -= (M[:, k] / M[p][k]) M[p][j],  M[p][j] /= M[p][k],
-// column k becoming the multiplier column.  The owner of column k+1 publishes
-// its updated copy into the other buffer slot, which nobody reads before the
-// next grid barrier; one barrier per step.
-__global__ void __launch_bounds__(512) k_coarse_gj(int64_t n, double* __restrict__ M, double* __restrict__ colbuf,
-                                                   int32_t* __restrict__ piv, int32_t* __restrict__ status) {
+// Banded LU with partial pivoting (FP64) of the coarse operator, stored
+// column-major in dense form; lower half-bandwidth kl, upper ku (row
+// interchanges widen U to kl + ku).  Cooperative: block b owns the columns
+// j = b (mod grid).  Step k reads the pivot column from a two-slot buffer,
+// picks the row p in [k, k + kl] with the largest |entry| (same rule in every
+// block), and every block swaps rows k and p and applies the rank-1 update
+// to its columns in the window (k, k + kl + ku]; column k keeps the
+// multipliers of L.  The owner of column k+1 publishes its updated copy into
+// the other buffer slot; one grid barrier per step.
+__global__ void __launch_bounds__(256) k_band_lu(int64_t n, int kl, int ku, double* __restrict__ M,
+                                                 double* __restrict__ colbuf, int32_t* __restrict__ piv,
+                                                 int32_t* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* pc = reinterpret_cast<double*>(smem_raw);     // column k, n
-  uint8_t* used = reinterpret_cast<uint8_t*>(pc + n);   // n
+  double* pc = reinterpret_cast<double*>(smem_raw);   // kl + 1 entries of the pivot column (rows k..k+kl)
   __shared__ double sv[32];
   __shared__ int si[32];
   const int64_t G = gridDim.x;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
+  const int64_t wmax = (int64_t)kl + ku;
   if (blockIdx.x == 0)
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) colbuf[i] = M[i];
+    for (int64_t r = threadIdx.x; r <= kl && r < n; r += blockDim.x) colbuf[r] = M[r];
   grid.sync();
   for (int64_t k = 0; k < n; ++k) {
-    const double* cb = colbuf + (k & 1) * n;
+    const int64_t r_hi = min(n - 1, k + (int64_t)kl);
+    const int64_t nr = r_hi - k + 1;
+    const double* cb = colbuf + (k & 1) * (kl + 1);
     double best = -1.0;
     int bi = -1;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const double v = cb[i];
-      pc[i] = v;
-      if (used[i]) continue;
+    for (int64_t r = threadIdx.x; r < nr; r += blockDim.x) {
+      const double v = cb[r];
+      pc[r] = v;
       double a = fabs(v);
       if (!(a >= 0.0)) a = 0.0;
-      if (a > best) { best = a; bi = (int)i; }
+      if (a > best) { best = a; bi = (int)r; }
     }
-    const int pr = block_argmax(best, bi, sv, si);   // contains barriers: pc is complete
-    double pv = pc[pr];
+    const int pr_off = block_argmax(best, bi, sv, si);   // barriers inside: pc complete
+    const int64_t pr = k + pr_off;
+    double pv = pc[pr_off];
     if (!(fabs(pv) > 0.0) || !isfinite(pv)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&status[ST_SINGULAR], 1);
       pv = 1.0;
     }
     const double rp = 1.0 / pv;
-    if (threadIdx.x == 0) used[pr] = 1;
-    for (int64_t j = blockIdx.x; j < n; j += G) {
+    // pivot column after the interchange: rows k <-> pr
+    const double ck = pc[0];
+    const int64_t j_hi = min(n - 1, k + wmax);
+    int64_t j0 = k + ((blockIdx.x - k % G) + G) % G;   // first owned column >= k
+    for (int64_t j = j0; j <= j_hi; j += G) {
       double* Mj = M + j * n;
+      const double tk = Mj[k], tp = Mj[pr];
+      __syncthreads();   // all threads read rows k and p of column j before they change
+      const double t = (pr != k) ? tp : tk;   // M[k][j] after the interchange
+      // row k gets the old row-p entry; row p is written by exactly one thread:
+      // the elimination loop below when it runs for row p, thread 0 otherwise
+      if (pr != k && threadIdx.x == 0) {
+        Mj[k] = tp;
+        if (j != k && t == 0.0) Mj[pr] = tk;
+      }
       if (j == k) {
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Mj[i] = (i == pr) ? rp : -pc[i] * rp;
-      } else {
-        const double t = Mj[pr];
-        __syncthreads();   // every thread has read M[p][j] before row p is overwritten
-        if (t != 0.0) {
-          const double tp = t * rp;
-          for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Mj[i] = (i == pr) ? tp : Mj[i] - pc[i] * tp;
+        for (int64_t r = threadIdx.x + 1; r < nr; r += blockDim.x) {
+          const int64_t row = k + r;
+          const double v = (row == pr) ? ck : pc[r];
+          Mj[row] = v * rp;
+        }
+      } else if (t != 0.0) {
+        const double ts = t * rp;
+        for (int64_t r = threadIdx.x + 1; r < nr; r += blockDim.x) {
+          const int64_t row = k + r;
+          const double l = (row == pr) ? ck : pc[r];
+          if (row != pr) Mj[row] -= l * ts;
+          else Mj[row] = tk - l * ts;   // row p received the old row-k entry
         }
       }
       if (j == k + 1) {
         __syncthreads();
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) colbuf[((k + 1) & 1) * n + i] = Mj[i];
+        const int64_t r_hi1 = min(n - 1, k + 1 + (int64_t)kl);
+        for (int64_t r = threadIdx.x; r <= r_hi1 - (k + 1); r += blockDim.x)
+          colbuf[((k + 1) & 1) * (kl + 1) + r] = Mj[k + 1 + r];
       }
+      __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = pr;
-    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = (int32_t)pr;
     grid.sync();
   }
 }
 
-// inverse (row-major, for the V-cycle GEMV): inv[k][c] = M[p_k][q_c], M column-major
-__global__ void k_coarse_permute(int64_t n, const double* __restrict__ M, const int32_t* __restrict__ piv,
-                                 double* __restrict__ inv) {
-  extern __shared__ int qinv_s[];
-  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) qinv_s[piv[k]] = (int)k;
-  __syncthreads();
-  for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
-    const int64_t pk = piv[k];
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) inv[k * n + c] = M[(int64_t)qinv_s[c] * n + pk];
+// Columns of the inverse from the banded LU: one warp per right-hand side
+// e_c (banded ordering), forward substitution with the row interchanges and
+// unit L, back substitution with U; the column is written to the inverse in
+// the original internal ordering, column-major:
+// Ainv[pinv(c) * n + i] = x[perm[i]].
+__global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, const double* __restrict__ M,
+                                                  const int32_t* __restrict__ piv, const int32_t* __restrict__ perm,
+                                                  const int32_t* __restrict__ pinv, double* __restrict__ Ainv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / kWarp) + wid;
+  if (c >= n) return;
+  double* x = reinterpret_cast<double*>(smem_raw) + (int64_t)wid * n;
+  for (int64_t i = lane; i < n; i += kWarp) x[i] = (i == c) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int64_t k = 0; k < n; ++k) {
+    const int64_t p = piv[k];
+    if (p != k) {
+      if (lane == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+      __syncwarp();
+    }
+    const double xk = x[k];
+    if (xk != 0.0) {
+      const int64_t r_hi = min(n - 1, k + (int64_t)kl);
+      const double* Lk = M + k * n;
+      for (int64_t r = k + 1 + lane; r <= r_hi; r += kWarp) x[r] -= Lk[r] * xk;
+    }
+    __syncwarp();
   }
+  const int64_t w = (int64_t)kl + ku;
+  for (int64_t k = n - 1; k >= 0; --k) {
+    const double* Uk = M + k * n;
+    if (lane == 0) x[k] /= Uk[k];
+    __syncwarp();
+    const double xk = x[k];
+    if (xk != 0.0) {
+      const int64_t r_lo = max((int64_t)0, k - w);
+      for (int64_t r = r_lo + lane; r < k; r += kWarp) x[r] -= Uk[r] * xk;
+    }
+    __syncwarp();
+  }
+  double* out = Ainv + (int64_t)pinv[c] * n;
+  for (int64_t i = lane; i < n; i += kWarp) out[i] = x[perm[i]];
 }
 
-int launch_coarse_gj(int64_t n, double* A, double* Bm, double* inv, int32_t* piv, int32_t* status, int sm_count,
-                     cudaStream_t st) {
-  const int threads = 512;
-  int grid = std::min<int64_t>((int64_t)sm_count, n);
+int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbuf, double* Ainv, int32_t* piv,
+                             const int32_t* perm, const int32_t* pinv, int32_t* status, int sm_count,
+                             cudaStream_t st) {
+  const int threads = 256;
+  // about 8 window columns per block: a step has kl + ku + 1 columns of work,
+  // and fewer blocks make each grid barrier cheaper
+  int grid = (int)std::min<int64_t>((int64_t)sm_count, ((int64_t)kl + ku + 1 + 7) / 8);
+  grid = (int)std::min<int64_t>(std::max(grid, 8), n);
   if (grid < 1) grid = 1;
-  const size_t smem = (size_t)n * sizeof(double) + (size_t)n + 16;
+  const size_t smem = (size_t)(kl + 1) * sizeof(double) + 16;
   if (smem > 200 * 1024) return -3;
-  cudaFuncSetAttribute(k_coarse_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_band_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_gj, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_lu, threads, smem);
   if (per_sm < 1) return -1;
-  double* colbuf = Bm;   // 2 n doubles of scratch
-  void* args[] = {(void*)&n, (void*)&A, (void*)&colbuf, (void*)&piv, (void*)&status};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_coarse_gj, grid, threads, args, smem, st);
-  if (e != cudaSuccess) return -2;
-  k_coarse_permute<<<std::min<int64_t>(n, 1024), 256, (size_t)n * sizeof(int), st>>>(n, A, piv, inv);
+  void* args[] = {(void*)&n, (void*)&kl, (void*)&ku, (void*)&M, (void*)&colbuf, (void*)&piv, (void*)&status};
+  if (cudaLaunchCooperativeKernel((const void*)k_band_lu, grid, threads, args, smem, st) != cudaSuccess) return -2;
+  // inverse columns: 4 warps (right-hand sides) per block, x in shared memory
+  const int wpb = 4;
+  const size_t ismem = (size_t)wpb * n * sizeof(double);
+  if (ismem > 200 * 1024) return -4;
+  cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+  k_band_inv<<<(unsigned)((n + wpb - 1) / wpb), wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, perm, pinv, Ainv);
   return 0;
 }
 
-// y = A x, one warp per row (A row-major FP64, n x n); TX / TY vector types
-template <typename TX, typename TY>
-__global__ void k_gemv(int64_t n, const double* __restrict__ A, const TX* __restrict__ x, TY* __restrict__ y) {
-  const int lane = threadIdx.x % kWarp;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
-  if (row >= n) return;
-  const double* Ar = A + row * n;
-  double acc = 0.0;
-  for (int64_t c = lane; c < n; c += kWarp) acc += Ar[c] * (double)x[c];
-  acc = warp_sum(acc);
-  if (lane == 0) y[row] = TY(acc);
+// y = A x with A column-major FP64 (n x n).  Stage 1: block (rb, cb) forms
+// the partial product of rows [256 rb, 256 rb + 256) over the column chunk
+// cb (kGemvChunk columns), one thread per row, coalesced column reads;
+// stage 2 adds the chunk partials in a fixed order.
+constexpr int kGemvChunk = 32;
+
+template <typename TX>
+__global__ void __launch_bounds__(256) k_gemv_cm_part(int64_t n, const double* __restrict__ A,
+                                                      const TX* __restrict__ x, double* __restrict__ part) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.y * kGemvChunk;
+  const int64_t c1 = min(n, c0 + kGemvChunk);
+  if (i >= n) return;
+  double a0 = 0.0, a1 = 0.0;
+  int64_t c = c0;
+  for (; c + 1 < c1; c += 2) {
+    a0 += A[c * n + i] * (double)x[c];
+    a1 += A[(c + 1) * n + i] * (double)x[c + 1];
+  }
+  if (c < c1) a0 += A[c * n + i] * (double)x[c];
+  part[(int64_t)blockIdx.y * n + i] = a0 + a1;
 }
 
-void launch_gemv(int64_t n, const double* A, const double* x, double* y, cudaStream_t st) {
-  const int64_t threads = n * kWarp;
-  k_gemv<double, double><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, A, x, y);
+template <typename TY>
+__global__ void k_gemv_cm_sum(int64_t n, int nchunk, const double* __restrict__ part, TY* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int q = 0; q < nchunk; ++q) s += part[(int64_t)q * n + i];
+  y[i] = TY(s);
 }
 
-void launch_gemv_f32io(int64_t n, const double* A, const float* x, float* y, cudaStream_t st) {
-  const int64_t threads = n * kWarp;
-  k_gemv<float, float><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, A, x, y);
+void launch_gemv(int64_t n, const double* A, const double* x, double* y, double* part, cudaStream_t st) {
+  const int nchunk = (int)((n + kGemvChunk - 1) / kGemvChunk);
+  k_gemv_cm_part<double><<<dim3((unsigned)((n + 255) / 256), nchunk), 256, 0, st>>>(n, A, x, part);
+  k_gemv_cm_sum<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nchunk, part, y);
+}
+
+void launch_gemv_f32io(int64_t n, const double* A, const float* x, float* y, double* part, cudaStream_t st) {
+  const int nchunk = (int)((n + kGemvChunk - 1) / kGemvChunk);
+  k_gemv_cm_part<float><<<dim3((unsigned)((n + 255) / 256), nchunk), 256, 0, st>>>(n, A, x, part);
+  k_gemv_cm_sum<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nchunk, part, y);
 }
 
 }  // namespace fsi

@@ -63,11 +63,14 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
                           const T* dc, cudaStream_t st);
 
 void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
-                         const int32_t* pad_list, int npad, int64_t n, double* A, cudaStream_t st);
-int launch_coarse_gj(int64_t n, double* A, double* Bm, double* inv, int32_t* piv, int32_t* status, int sm_count,
-                     cudaStream_t st);
-void launch_gemv(int64_t n, const double* A, const double* x, double* y, cudaStream_t st);
-void launch_gemv_f32io(int64_t n, const double* A, const float* x, float* y, cudaStream_t st);
+                         const int32_t* pad_list, int npad, const int32_t* perm, int64_t n, double* A,
+                         cudaStream_t st);
+int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbuf, double* Ainv, int32_t* piv,
+                             const int32_t* perm, const int32_t* pinv, int32_t* status, int sm_count,
+                             cudaStream_t st);
+// coarse apply: part holds ceil(n / 32) * n doubles of scratch
+void launch_gemv(int64_t n, const double* A, const double* x, double* y, double* part, cudaStream_t st);
+void launch_gemv_f32io(int64_t n, const double* A, const float* x, float* y, double* part, cudaStream_t st);
 void launch_csr_spmv_f32(int64_t nrows, const int32_t* ptr, const int32_t* col, const float* val, const float* x,
                          float* y, bool add, cudaStream_t st);
 void launch_to_f32(int64_t n, const double* in, float* out, cudaStream_t st);
