@@ -28,6 +28,14 @@ ones the Schwarz subdomains of Sec. 3.3 are extracted from):
     element pressure rows:   mass balance of that element.
 Dirichlet unknowns get the row e_i^T and residual y_i - g_i (pattern kept).
 
+Transient form (BDF reading of the time-discretised operators of Sec. 2.5;
+the paper's own Crank-Nicolson form is not built): with q_t = (a0 q + a1 q_n +
+a2 q_{n-1}) / dt (BDF1: 1, -1, 0; BDF2: 3/2, -2, 1/2) applied to nodal values,
+    fluid momentum  J [ rho_f (u_t + (grad u)(u - w)) . phi + sigma_f : grad phi ],  w = d_t
+    solid momentum  rho_s J u_t . phi + P : grad_hat phi
+    kinematic       (u - d_t) . psi
+and the inflow Dirichlet data scaled by alpha(t) = (1 + sin 2 pi t) / 2.
+
 Quadrature: 3 Gauss points per axis (the paper does not state its rule; three
 points integrate the Q2 x Q2 products exactly on rectangles).
 P1disc basis per element: {1, xi, eta(, zeta)} in reference coordinates.
@@ -132,7 +140,7 @@ def _det_inv(F):
 
 
 def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
-                   source: Optional[Callable] = None):
+                   source: Optional[Callable] = None, tr: Optional[dict] = None):
     """Element residuals (E, ndofe) and exact Jacobians (E, ndofe, ndofe) for a
     batch of elements sharing one material.
 
@@ -140,6 +148,9 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
     is an optional body force / mass / mesh-equation source used only by
     manufactured-solution tests; it adds -(rho f, phi) to the momentum rows,
     -(g, q) to the mass rows and -(g_ale, psi) to the ALE rows.
+
+    ``tr = dict(yn=..., ynm1=..., a=(a0, a1, a2), dt=...)`` switches on the
+    transient (BDF) terms; ``None`` is the steady form.
     """
     dim = lev.dim
     n = dim
@@ -154,6 +165,10 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
     vol = np.prod(h, axis=1)
     kale = 1.0 / vol
     ye = y[lev.elem_dofs[elems]]                 # (E, m)
+    if tr is not None:
+        a0, a1, a2 = tr["a"]
+        idt = 1.0 / tr["dt"]
+        yold = (a1 * tr["yn"] + a2 * tr["ynm1"])[lev.elem_dofs[elems]]   # constant part of q_t * dt
     iface = lev.node_class[lev.elem_nodes[elems]] == IFACE   # (E, nloc)
 
     Rv = np.zeros((E, m))
@@ -198,6 +213,12 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
         gd = [[field(Gh[:, :, j], i) for j in range(n)] for i in range(n)]
         gu = [[field(Gh[:, :, j], n + i) for j in range(n)] for i in range(n)]
         u = [field(Nb, n + i) for i in range(n)]
+        if tr is not None:
+            # nodal BDF time derivatives interpolated at the quadrature point
+            ut = [(field(Nb, n + i) * a0 + np.einsum("ea,a->e", yold[:, np.arange(nloc) * nd + n + i], Nq)) * idt
+                  for i in range(n)]
+            dt_ = [(field(Nb, i) * a0 + np.einsum("ea,a->e", yold[:, np.arange(nloc) * nd + i], Nq)) * idt
+                   for i in range(n)]
         p = pfield(psi)
         F = [[gd[i][j] + (1.0 if i == j else 0.0) for j in range(n)] for i in range(n)]
         J, Finv = _det_inv(F)
@@ -209,7 +230,10 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
             for c in range(n):
                 for j in range(n):
                     add_rows(a_idx * nd + c, T[c][j] * wq, Gh[:, :, j])
-                add_rows(a_idx * nd + n + c, u[c] * wq, Nb)
+                kin = u[c] if tr is None else u[c] - dt_[c]
+                add_rows(a_idx * nd + n + c, kin * wq, Nb)
+                if tr is not None:
+                    add_rows(a_idx * nd + c, ut[c] * J * (prob.rho_s * wq), Nb)
             mass = J - 1.0
         else:
             gux = [[None] * n for _ in range(n)]
@@ -228,10 +252,13 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
                 sig[i][i] = sig[i][i] - p
             mom_rows = np.where(iface, a_idx[None, :] * nd, a_idx[None, :] * nd + n)
             ale_rows = np.where(iface, -1, a_idx[None, :] * nd)
+            adv = u if tr is None else [u[j] - dt_[j] for j in range(n)]   # u - w
             for c in range(n):
-                conv = gux[c][0] * u[0]
+                conv = gux[c][0] * adv[0]
                 for j in range(1, n):
-                    conv = conv + gux[c][j] * u[j]
+                    conv = conv + gux[c][j] * adv[j]
+                if tr is not None:
+                    conv = conv + ut[c]
                 rows_c = mom_rows + c
                 add_rows(rows_c, conv * J * (prob.rho_f * wq), Nb)
                 for k in range(n):
@@ -311,9 +338,15 @@ def place_on_pattern(pattern: sp.csr_matrix, M: sp.spmatrix) -> sp.csr_matrix:
     return out
 
 
-def assemble(prob, lev: Level, y: np.ndarray, source=None, chunk: int = 2048):
+def inflow_alpha(t: float) -> float:
+    """Pulsating inflow amplitude of the transient workload."""
+    return 0.5 * (1.0 + np.sin(2.0 * np.pi * t))
+
+
+def assemble(prob, lev: Level, y: np.ndarray, source=None, chunk: int = 2048, tr: Optional[dict] = None):
     """Global residual r(y) and exact Jacobian J(y) (CSR on the FE pattern),
-    Dirichlet rows replaced by identity rows (Sec. 2.3 / 3.1)."""
+    Dirichlet rows replaced by identity rows (Sec. 2.3 / 3.1).  With ``tr``
+    (transient) the Dirichlet data are those at time tr["t"]."""
     r = np.zeros(lev.N)
     rows_all, cols_all, vals_all = [], [], []
     nd = 2 * lev.dim
@@ -322,7 +355,7 @@ def assemble(prob, lev: Level, y: np.ndarray, source=None, chunk: int = 2048):
         elems_all = np.nonzero(lev.elem_solid == solid)[0]
         for s in range(0, len(elems_all), chunk):
             elems = elems_all[s:s + chunk]
-            Rv, Rg = element_system(prob, lev, elems, y, source)
+            Rv, Rg = element_system(prob, lev, elems, y, source, tr)
             ed = lev.elem_dofs[elems]
             np.add.at(r, ed, Rv)
             m = ed.shape[1]
@@ -337,7 +370,8 @@ def assemble(prob, lev: Level, y: np.ndarray, source=None, chunk: int = 2048):
                        shape=(lev.N, lev.N))
     J = place_on_pattern(fe_pattern(lev), Jc)
     apply_dirichlet_rows(J, lev.dir_mask)
-    r[lev.dir_mask] = y[lev.dir_mask] - lev.dir_val[lev.dir_mask]
+    alpha = 1.0 if tr is None else inflow_alpha(tr["t"])
+    r[lev.dir_mask] = y[lev.dir_mask] - alpha * lev.dir_val[lev.dir_mask]
     return r, J
 
 
@@ -350,5 +384,10 @@ def apply_dirichlet_rows(J: sp.csr_matrix, mask: np.ndarray) -> None:
         J.data[k] = 1.0
 
 
-def residual_only(prob, lev: Level, y: np.ndarray, source=None) -> np.ndarray:
-    return assemble(prob, lev, y, source)[0]
+def residual_only(prob, lev: Level, y: np.ndarray, source=None, tr=None) -> np.ndarray:
+    return assemble(prob, lev, y, source, tr=tr)[0]
+
+
+def bdf_coefficients(order: int):
+    """BDF time-derivative coefficients (a0, a1, a2) of q^{n+1}, q^n, q^{n-1}."""
+    return (1.0, -1.0, 0.0) if order == 1 else (1.5, -2.0, 0.5)

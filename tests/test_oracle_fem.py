@@ -259,3 +259,68 @@ def test_mms_ale_operator():
     rate = np.log2(errs[-2]["d"] / errs[-1]["d"])
     assert rate > 2.7, errs
     assert errs[-1]["u"] < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# transient (BDF) form
+# ----------------------------------------------------------------------------
+
+def _tr_state(lev, seed):
+    rng = np.random.default_rng(seed)
+    y = random_state(lev, seed)
+    yn = y + 1e-3 * rng.standard_normal(lev.N)
+    ynm1 = yn + 1e-3 * rng.standard_normal(lev.N)
+    return y, yn, ynm1
+
+
+@pytest.mark.parametrize("prob,order", [(CHANNEL_2D, 2), (CHANNEL_2D, 1), (SMALL_3D, 2)], ids=["2d-bdf2", "2d-bdf1", "3d-bdf2"])
+def test_fd_jacobian_transient(prob, order):
+    lev = build_level(prob, 0)
+    y, yn, ynm1 = _tr_state(lev, 7)
+    tr = dict(yn=yn, ynm1=ynm1, a=fem.bdf_coefficients(order), dt=0.01, t=0.13)
+    r, J = fem.assemble(prob, lev, y, tr=tr)
+    rng = np.random.default_rng(8)
+    h = 1e-6
+    for _ in range(2):
+        v = rng.standard_normal(lev.N)
+        fd = (fem.residual_only(prob, lev, y + h * v, tr=tr) - fem.residual_only(prob, lev, y - h * v, tr=tr)) / (2 * h)
+        jv = J @ v
+        assert np.linalg.norm(fd - jv) <= 1e-6 * np.linalg.norm(jv)
+
+
+def test_transient_reduces_to_steady_for_constant_history():
+    """y_n = y_{n-1} = y: every BDF derivative vanishes (a0 + a1 + a2 = 0) and
+    the mesh velocity is zero, so the transient residual is the steady one
+    (alpha(1/4) = 1 keeps the inflow data equal)."""
+    prob = CHANNEL_2D
+    lev = build_level(prob, 0)
+    y = random_state(lev, 9)
+    r0, J0 = fem.assemble(prob, lev, y)
+    tr = dict(yn=y.copy(), ynm1=y.copy(), a=fem.bdf_coefficients(2), dt=0.01, t=0.25)
+    r1, _ = fem.assemble(prob, lev, y, tr=tr)
+    assert np.max(np.abs(r1 - r0)) <= 1e-12 * np.max(np.abs(r0))
+
+
+def test_transient_kinematic_rows_vanish_for_consistent_velocity():
+    """Solid kinematic rows: with d linear in time and nodal u equal to its
+    BDF derivative, (u - d_t, psi) = 0 exactly (BDF1 and BDF2)."""
+    prob = CHANNEL_2D
+    lev = build_level(prob, 0)
+    rng = np.random.default_rng(10)
+    nd, n = 4, 2
+    dt = 0.02
+    for order in (1, 2):
+        y = np.zeros(lev.N)
+        delta = np.zeros(lev.N)
+        for c in range(n):
+            delta[c:lev.n_nodes * nd:nd] = 1e-3 * rng.standard_normal(lev.n_nodes)
+        y[:] = delta * 3
+        yn, ynm1 = y - delta, y - 2 * delta
+        for c in range(n):
+            y[n + c:lev.n_nodes * nd:nd] = delta[c:lev.n_nodes * nd:nd] / dt
+        tr = dict(yn=yn, ynm1=ynm1, a=fem.bdf_coefficients(order), dt=dt, t=0.0)
+        r, _ = fem.assemble(prob, lev, y, tr=tr)
+        kin_rows = [node * nd + n + c for node in np.nonzero(lev.node_class != FLUID)[0] for c in range(n)
+                    if not lev.dir_mask[node * nd + n + c]]
+        scale = np.max(np.abs(y[n:lev.n_nodes * nd:nd])) * np.max(lev.elem_h) ** 2
+        assert np.max(np.abs(r[kin_rows])) <= 1e-12 * scale
