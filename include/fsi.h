@@ -69,8 +69,8 @@ typedef struct {
   double flap_lo[3], flap_hi[3];        /* solid box */
   double rho_f, mu_f, rho_s, mu_s;      /* densities, viscosity, shear modulus (C1 = mu_s/2) */
   double U;                             /* mean inflow velocity */
-  int transient;                        /* must be 0 (steady); reserved */
-  double dt;                            /* reserved */
+  int transient;                        /* 0: steady; 1: time step of the BDF form (Sec. 2) */
+  double dt;                            /* time step (transient only, > 0) */
   int ale_op;                           /* 0: k(grad d + grad d^T), k = 1/V_el; 1: k grad d */
 } fsi_problem_desc;
 
@@ -124,8 +124,13 @@ int fsi_get_sizes(const fsi_ctx* ctx, int64_t* n_per_level, int64_t* nnz_per_lev
  * displacement unknown.  noise and y_out: N doubles (host or device). */
 int fsi_initial_state(fsi_ctx* ctx, const double* noise, double* y_out);
 
-/* Sets the Newton state y (N doubles).  y_prev, y_prev2 and t are reserved
- * for transient problems and must be NULL / ignored for steady ones. */
+/* Sets the Newton state y (N doubles).  Steady problems ignore y_prev,
+ * y_prev2 and t.  Transient problems (desc.transient = 1) need the state of
+ * the previous time step y_prev; with y_prev2 (the one before) the time
+ * derivative is BDF2, q_t = (1.5 q - 2 q_n + 0.5 q_{n-1}) / dt, without it
+ * BDF1, q_t = (q - q_n) / dt (start-up step).  t is the new time level: the
+ * inflow data are scaled by alpha(t) = (1 + sin 2 pi t) / 2, so Dirichlet
+ * residual rows read r_i = y_i - alpha(t) g_i.  Host or device buffers. */
 int fsi_set_state(fsi_ctx* ctx, const double* y, const double* y_prev,
                   const double* y_prev2, double t);
 int fsi_get_state(fsi_ctx* ctx, double* y_out);
@@ -134,6 +139,9 @@ int fsi_get_state(fsi_ctx* ctx, double* y_out);
  * forward-mode dual numbers, coloured scatter into block-sparse storage),
  * Dirichlet rows replaced by identity rows with r_i = y_i - g_i, then the
  * Galerkin operators J_{l-1} = R J_l P of every coarser level (Sec. 3.2).
+ * Transient problems add the BDF inertia terms, the mesh velocity in the
+ * fluid convection and the BDF velocity in the solid kinematic rows, with
+ * the history given to fsi_set_state (FSI_E_INVALID before the first one).
  * residual_out (N doubles) may be NULL.  Returns FSI_E_MESH_TANGLED if
  * det F <= 0 at a quadrature point and FSI_E_NONFINITE on NaN / Inf. */
 int fsi_assemble_jacobian(fsi_ctx* ctx, double* residual_out);

@@ -322,9 +322,10 @@ class Oracle:
     def fine(self) -> Level:
         return self.levels_mesh[-1]
 
-    def assemble(self, y: np.ndarray, source=None):
-        """Finest r, J and all Galerkin levels."""
-        r, J = fem.assemble(self.prob, self.fine, y, source)
+    def assemble(self, y: np.ndarray, source=None, tr=None):
+        """Finest r, J and all Galerkin levels (tr: transient history, see
+        fem.assemble)."""
+        r, J = fem.assemble(self.prob, self.fine, y, source, tr=tr)
         L = self.prob.levels
         Js = [None] * L
         Js[L - 1] = J

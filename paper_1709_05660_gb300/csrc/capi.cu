@@ -284,6 +284,10 @@ void build_device(Ctx& c) {
   c.xk = dalloc<double>(c, Ni);
   c.bk = dalloc<double>(c, Ni);
   c.tmp = dalloc<double>(c, Ni);
+  if (c.desc.transient != 0) {
+    c.yold = dalloc<double>(c, Ni);
+    ck(cudaMemsetAsync(c.yold, 0, Ni * sizeof(double), c.stream), "memset");
+  }
   ck(cudaMemsetAsync(c.V, 0, (size_t)(m + 1) * Ni * sizeof(double), c.stream), "memset");
   c.red_blocks = std::max(1, c.sm_count * 2);
   c.partial = dalloc<double>(c, (size_t)c.red_blocks * 130);
@@ -334,6 +338,14 @@ void assemble(Ctx& c, bool want_res) {
   const int B = c.B;
   DevLevel& F = c.dl[L - 1];
   PhysParams pp{c.desc.rho_f, c.desc.mu_f, c.desc.rho_s, c.desc.mu_s, c.desc.ale_op};
+  const bool transient = c.desc.transient != 0;
+  if (transient) {
+    if (!c.have_history) throw ApiError(FSI_E_INVALID, "transient problem: fsi_set_state needs y_prev first");
+    pp.transient = 1;
+    pp.a0 = c.bdf_a0;
+    pp.idt = 1.0 / c.desc.dt;
+    pp.yold = c.yold;
+  }
   double* Re = c.tmp_re;
   const double nd = c.ndofe;
   ck(cudaMemsetAsync(F.val, 0, (size_t)F.nnzb * B * B * sizeof(double), c.stream), "memset");
@@ -357,7 +369,8 @@ void assemble(Ctx& c, bool want_res) {
                         c.res, c.stream);
       if (ne > 0) counted(c);
     }
-    launch_dirichlet(F.dir_list, F.n_dir, F.rowptr, F.col, F.val, B, c.y, F.dir_val, c.res, c.stream);
+    launch_dirichlet(F.dir_list, F.n_dir, F.rowptr, F.col, F.val, B, c.y, F.dir_val, transient ? c.inflow_alpha : 1.0,
+                     c.res, c.stream);
     counted(c);
   }
   launch_nonfinite_check(F.Ni, c.res, c.status, c.stream);
@@ -380,7 +393,7 @@ void assemble(Ctx& c, bool want_res) {
                         Co.val, nullptr, c.stream);
       if (ne > 0) counted(c);
     }
-    launch_dirichlet(Co.dir_list, Co.n_dir, Co.rowptr, Co.col, Co.val, B, nullptr, nullptr, nullptr, c.stream);
+    launch_dirichlet(Co.dir_list, Co.n_dir, Co.rowptr, Co.col, Co.val, B, nullptr, nullptr, 1.0, nullptr, c.stream);
     counted(c);
   }
   if (c.mixed)
@@ -731,12 +744,13 @@ static int64_t estimate_device_bytes(const Ctx& c) {
   const HostLevel& F = c.hl.back();
   const double n0 = (double)c.hl[0].Ni;
   b += F.Ni * 8.0 * 2 + (m + 1.0) * F.Ni * 8.0 + m * (double)F.Ni * fs + F.Ni * 8.0 * 4 + F.N * 8.0 * 2;
+  if (c.desc.transient != 0) b += F.Ni * 8.0;
   b += max_dense * fs + 3.0 * n0 * n0 * 8.0 + F.n_elem * (double)nd * 8.0 + 1e6;
   return (int64_t)b;
 }
 
 static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts* opts) {
-  if (desc->transient != 0) throw ApiError(FSI_E_INVALID, "only steady problems are supported");
+  if (desc->transient != 0 && !(desc->dt > 0.0)) throw ApiError(FSI_E_INVALID, "transient problem needs dt > 0");
   if (opts->precision != FSI_FP64 && opts->precision != FSI_MIXED) throw ApiError(FSI_E_INVALID, "bad precision");
   if (opts->restart < 1 || opts->restart > 64) throw ApiError(FSI_E_INVALID, "restart must be in [1, 64]");
   if (opts->n_pre < 0 || opts->n_post < 0 || opts->max_iters < 1 || !(opts->rtol > 0.0))
@@ -880,11 +894,28 @@ int fsi_initial_state(fsi_ctx* c, const double* noise, double* y_out) {
 }
 
 int fsi_set_state(fsi_ctx* c, const double* y, const double* y_prev, const double* y_prev2, double t) {
-  (void)y_prev; (void)y_prev2; (void)t;
   return guard(c, [&] {
     need_device(*c);
     if (!y) throw ApiError(FSI_E_INVALID, "null state");
-    to_internal(*c, (int)c->dl.size() - 1, y, c->y);
+    const int L = (int)c->dl.size();
+    to_internal(*c, L - 1, y, c->y);
+    if (c->desc.transient != 0) {
+      if (!y_prev) throw ApiError(FSI_E_INVALID, "transient problem: y_prev is required");
+      // BDF2 with two history states, BDF1 (start-up step) with one
+      const double a0 = y_prev2 ? 1.5 : 1.0, a1 = y_prev2 ? -2.0 : -1.0, a2 = 0.5;
+      const int64_t Ni = c->dl[L - 1].Ni;
+      to_internal(*c, L - 1, y_prev, c->tmp);
+      launch_axpby(Ni, a1, c->tmp, 0.0, c->yold, c->stream);
+      counted(*c);
+      if (y_prev2) {
+        to_internal(*c, L - 1, y_prev2, c->tmp);
+        launch_axpby(Ni, a2, c->tmp, 1.0, c->yold, c->stream);
+        counted(*c);
+      }
+      c->bdf_a0 = a0;
+      c->inflow_alpha = 0.5 * (1.0 + std::sin(2.0 * M_PI * t));
+      c->have_history = true;
+    }
     sync(*c);
   });
 }

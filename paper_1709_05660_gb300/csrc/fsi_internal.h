@@ -149,6 +149,10 @@ struct Ctx {
   double* c_part = nullptr;               // coarse GEMV partial sums
   int32_t* status = nullptr;              // device status flags
   double* tmp_re = nullptr;               // finest element residuals (n_elem * ndofe)
+  // transient (BDF) state: yold = a1 y_n + a2 y_{n-1} (internal layout)
+  double* yold = nullptr;
+  double bdf_a0 = 0.0, inflow_alpha = 1.0;
+  bool have_history = false;
   int32_t* coarse_pad_list = nullptr;     // padding slots of the coarse dense operator
   int32_t* coarse_perm = nullptr;         // internal unknown -> banded position
   int32_t* coarse_pinv = nullptr;         // banded position -> internal unknown

@@ -59,13 +59,14 @@ constexpr int kEPB = 4;         // elements per thread block
 // ---------------------------------------------------------------------------
 // element residual + Jacobian column (2D)
 // ---------------------------------------------------------------------------
-template <bool SOLID>
+template <bool SOLID, bool TRANS>
 __global__ void __launch_bounds__(kEPB * kNdofe)
 k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ y,
               const int32_t* __restrict__ elem_nodes, const uint8_t* __restrict__ node_class,
               const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp,
               double* __restrict__ Ke, double* __restrict__ Re, int32_t* __restrict__ status) {
   __shared__ double s_y[kEPB][kNdofe];
+  __shared__ double s_yo[kEPB][kNN];
   __shared__ double s_geo[kEPB][2 * kDim];
   __shared__ unsigned s_iface[kEPB];
   const int le = threadIdx.x / kNdofe;
@@ -76,7 +77,9 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   if (active) {
     if (j < kNN) {
       const int a = j / kB, s = j % kB;
-      s_y[le][j] = y[(int64_t)elem_nodes[(int64_t)e * kNloc + a] * kB + s];
+      const int64_t gi = (int64_t)elem_nodes[(int64_t)e * kNloc + a] * kB + s;
+      s_y[le][j] = y[gi];
+      if (TRANS) s_yo[le][j] = pp.yold[gi];
     } else {
       s_y[le][j] = y[(n_nodes + e) * kB + (j - kNN)];
     }
@@ -91,6 +94,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   __syncthreads();
   if (!active) return;
   const double* ye = s_y[le];
+  const double* yo = s_yo[le];
   const double hx = s_geo[le][2], hy = s_geo[le][3];
   const double vol = hx * hy;
   const double kale = 1.0 / vol;
@@ -122,7 +126,8 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         Gy[a] = lx * dL1(ja, eta) * (2.0 / hy);
       }
       // fields at the quadrature point (values), derivatives from the seed
-      double gdv[2][2] = {{0, 0}, {0, 0}}, guv[2][2] = {{0, 0}, {0, 0}}, uv[2] = {0, 0};
+      double gdv[2][2] = {{0, 0}, {0, 0}}, guv[2][2] = {{0, 0}, {0, 0}}, uv[2] = {0, 0}, dvv[2] = {0, 0};
+      double uo[2] = {0, 0}, dold[2] = {0, 0};
 #pragma unroll
       for (int a = 0; a < kNloc; ++a) {
 #pragma unroll
@@ -133,12 +138,17 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
           guv[i][0] += vv * Gx[a];
           guv[i][1] += vv * Gy[a];
           uv[i] += vv * Nb[a];
+          dvv[i] += dv * Nb[a];
+          if (TRANS) {
+            uo[i] += yo[a * kB + 2 + i] * Nb[a];
+            dold[i] += yo[a * kB + i] * Nb[a];
+          }
         }
       }
       const double psi[3] = {1.0, xi, eta};
       const double pv = ye[kNN] + ye[kNN + 1] * xi + ye[kNN + 2] * eta;
       const double gxj = aj >= 0 ? Gx[aj] : 0.0, gyj = aj >= 0 ? Gy[aj] : 0.0, nj = aj >= 0 ? Nb[aj] : 0.0;
-      Dual gd[2][2], gu[2][2], u[2];
+      Dual gd[2][2], gu[2][2], u[2], ut[2], dt_[2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         gd[i][0] = mk(gdv[i][0], sj == i ? gxj : 0.0);
@@ -146,6 +156,11 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         gu[i][0] = mk(guv[i][0], sj == 2 + i ? gxj : 0.0);
         gu[i][1] = mk(guv[i][1], sj == 2 + i ? gyj : 0.0);
         u[i] = mk(uv[i], sj == 2 + i ? nj : 0.0);
+        // BDF derivatives of u and d at the quadrature point (zero when steady)
+        if (TRANS) {
+          ut[i] = mk((pp.a0 * uv[i] + uo[i]) * pp.idt, sj == 2 + i ? pp.a0 * pp.idt * nj : 0.0);
+          dt_[i] = mk((pp.a0 * dvv[i] + dold[i]) * pp.idt, sj == i ? pp.a0 * pp.idt * nj : 0.0);
+        }
       }
       const Dual p = mk(pv, pk >= 0 ? psi[pk] : 0.0);
       Dual F[2][2];
@@ -170,10 +185,11 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         for (int a = 0; a < kNloc; ++a) {
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            const Dual m = (T[c][0] * Gx[a] + T[c][1] * Gy[a]) * wq;
+            Dual m = (T[c][0] * Gx[a] + T[c][1] * Gy[a]) * wq;
+            if (TRANS) m = m + ut[c] * J * (pp.rho_s * Nb[a] * wq);
             acc[a * kB + c] += m.d;
             if (a * kB + c == j) vj += m.v;
-            const Dual kin = u[c] * (Nb[a] * wq);
+            const Dual kin = (TRANS ? u[c] - dt_[c] : u[c]) * (Nb[a] * wq);
             acc[a * kB + 2 + c] += kin.d;
             if (a * kB + 2 + c == j) vj += kin.v;
           }
@@ -197,7 +213,9 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         for (int c = 0; c < 2; ++c) {
 #pragma unroll
           for (int k = 0; k < 2; ++k) T[c][k] = (sig[c][0] * Fi[k][0] + sig[c][1] * Fi[k][1]) * J * wq;
-          conv[c] = (gx[c][0] * u[0] + gx[c][1] * u[1]) * J * (pp.rho_f * wq);
+          Dual cv = TRANS ? gx[c][0] * (u[0] - dt_[0]) + gx[c][1] * (u[1] - dt_[1]) + ut[c]
+                                 : gx[c][0] * u[0] + gx[c][1] * u[1];
+          conv[c] = cv * J * (pp.rho_f * wq);
         }
         Dual A[2][2];
 #pragma unroll
@@ -267,7 +285,8 @@ __global__ void k_scatter_2d(const int32_t* __restrict__ elems, int ne, const do
 // Dirichlet rows -> identity rows; residual r_i = y_i - g_i
 __global__ void k_dirichlet(const int32_t* __restrict__ dir_list, int64_t n_dir, const int32_t* __restrict__ rowptr,
                             const int32_t* __restrict__ col, double* __restrict__ val, int B,
-                            const double* __restrict__ y, const double* __restrict__ g, double* __restrict__ res) {
+                            const double* __restrict__ y, const double* __restrict__ g, double alpha,
+                            double* __restrict__ res) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_dir) return;
   const int32_t i = dir_list[t];
@@ -276,7 +295,7 @@ __global__ void k_dirichlet(const int32_t* __restrict__ dir_list, int64_t n_dir,
     double* v = val + (int64_t)k * B * B + ci * B;
     for (int cj = 0; cj < B; ++cj) v[cj] = (col[k] == br && cj == ci) ? 1.0 : 0.0;
   }
-  if (res != nullptr) res[i] = y[i] - g[i];
+  if (res != nullptr) res[i] = y[i] - alpha * g[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -386,6 +405,353 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
 }
 
 // ---------------------------------------------------------------------------
+// 3D: element residual + Jacobian (27-node hexahedra, 166 unknowns)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int k3Dim = 3;
+constexpr int k3B = 6;
+constexpr int k3Nloc = 27;
+constexpr int k3NN = k3B * k3Nloc;        // 162
+constexpr int k3Ndofe = k3NN + k3Dim + 1; // 166
+constexpr int k3Fields = 31;              // gd 9, gu 9, u 3, d 3, p 1, u_old 3, d_old 3
+__device__ __forceinline__ int row_kind3(int cls, int slot) {
+  if (cls == kFluid) return slot < k3Dim ? 2 : 0;
+  return slot < k3Dim ? 0 : 1;
+}
+}  // namespace
+
+size_t assemble_3d_smem() {
+  return ((size_t)k3Ndofe * k3Ndofe + k3Ndofe + k3NN + k3Nloc * 4 + k3Fields + 1) * sizeof(double);
+}
+
+// One thread block per element; thread j < 166 differentiates along unknown j
+// (forward-mode dual seeded with e_j) and owns column j of the 166 x 166
+// element Jacobian, which is accumulated in shared memory (no two threads
+// write the same entry).  Per quadrature point the basis table and the field
+// values are computed once by the block and shared.
+template <bool SOLID, bool TRANS>
+__global__ void __launch_bounds__(192)
+k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
+              const int32_t* __restrict__ elem_nodes, const uint8_t* __restrict__ node_class,
+              const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp,
+              double* __restrict__ Ke, double* __restrict__ Re, int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* K = reinterpret_cast<double*>(smem_raw);   // [i][j]
+  double* ye = K + k3Ndofe * k3Ndofe;
+  double* yo = ye + k3Ndofe;
+  double* bt = yo + k3NN;                             // per node: N, Gx, Gy, Gz
+  double* fv = bt + k3Nloc * 4;
+  __shared__ double geo[2 * k3Dim];
+  __shared__ unsigned s_iface;
+  __shared__ int s_tangled;
+  const int e = elems[blockIdx.x];
+  const int j = threadIdx.x;
+  for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) K[t] = 0.0;
+  for (int t = threadIdx.x; t < k3Ndofe; t += blockDim.x) {
+    if (t < k3NN) {
+      const int64_t gi = (int64_t)elem_nodes[(int64_t)e * k3Nloc + t / k3B] * k3B + t % k3B;
+      ye[t] = y[gi];
+      yo[t] = TRANS ? pp.yold[gi] : 0.0;
+    } else {
+      ye[t] = y[(n_nodes + e) * k3B + (t - k3NN)];
+    }
+  }
+  if (threadIdx.x < 2 * k3Dim) geo[threadIdx.x] = elem_geo[(int64_t)e * 2 * k3Dim + threadIdx.x];
+  if (threadIdx.x == 0) {
+    unsigned m = 0;
+    for (int a = 0; a < k3Nloc; ++a)
+      if (node_class[elem_nodes[(int64_t)e * k3Nloc + a]] == kIface) m |= 1u << a;
+    s_iface = m;
+    s_tangled = 0;
+  }
+  __syncthreads();
+  const double hx = geo[3], hy = geo[4], hz = geo[5];
+  const double vol = hx * hy * hz;
+  const double kale = 1.0 / vol;
+  const unsigned iface = s_iface;
+  const bool act = j < k3Ndofe;
+  const int aj = (act && j < k3NN) ? j / k3B : -1;
+  const int sj = (act && j < k3NN) ? j % k3B : -1;
+  const int pk = (act && j >= k3NN) ? j - k3NN : -1;
+  double vj = 0.0;
+  for (int q = 0; q < 27; ++q) {
+    const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+    const double xi = gp(qx), eta = gp(qy), zeta = gp(qz);
+    const double wq = gw(qx) * gw(qy) * gw(qz) * vol * 0.125;
+    if (threadIdx.x < k3Nloc) {
+      const int a = threadIdx.x, ia = a % 3, ja = (a / 3) % 3, ka = a / 9;
+      const double lx = L1(ia, xi), ly = L1(ja, eta), lz = L1(ka, zeta);
+      bt[a * 4 + 0] = lx * ly * lz;
+      bt[a * 4 + 1] = dL1(ia, xi) * ly * lz * (2.0 / hx);
+      bt[a * 4 + 2] = lx * dL1(ja, eta) * lz * (2.0 / hy);
+      bt[a * 4 + 3] = lx * ly * dL1(ka, zeta) * (2.0 / hz);
+    }
+    __syncthreads();
+    if (threadIdx.x < k3Fields) {
+      const int t = threadIdx.x;
+      double acc = 0.0;
+      if (t < 18) {           // gd (t < 9) and gu: d_i / dx_k of d or u
+        const int i = (t % 9) / 3, k = t % 3, off = t < 9 ? 0 : 3;
+        for (int a = 0; a < k3Nloc; ++a) acc += ye[a * k3B + off + i] * bt[a * 4 + 1 + k];
+      } else if (t < 24) {    // u (18..20), d (21..23)
+        const int i = (t - 18) % 3, off = t < 21 ? 3 : 0;
+        for (int a = 0; a < k3Nloc; ++a) acc += ye[a * k3B + off + i] * bt[a * 4];
+      } else if (t == 24) {   // pressure
+        acc = ye[k3NN] + ye[k3NN + 1] * xi + ye[k3NN + 2] * eta + ye[k3NN + 3] * zeta;
+      } else {                // u_old (25..27), d_old (28..30)
+        const int i = (t - 25) % 3, off = t < 28 ? 3 : 0;
+        for (int a = 0; a < k3Nloc; ++a) acc += yo[a * k3B + off + i] * bt[a * 4];
+      }
+      fv[t] = acc;
+    }
+    __syncthreads();
+    if (act) {
+      const double nj = aj >= 0 ? bt[aj * 4] : 0.0;
+      double gj[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gj[k] = aj >= 0 ? bt[aj * 4 + 1 + k] : 0.0;
+      const double psi[4] = {1.0, xi, eta, zeta};
+      Dual gd[3][3], u[3], ut[3], dt_[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gd[i][k] = mk(fv[i * 3 + k], sj == i ? gj[k] : 0.0);
+        u[i] = mk(fv[18 + i], sj == 3 + i ? nj : 0.0);
+        ut[i] = mk((pp.a0 * fv[18 + i] + fv[25 + i]) * pp.idt, sj == 3 + i ? pp.a0 * pp.idt * nj : 0.0);
+        dt_[i] = mk((pp.a0 * fv[21 + i] + fv[28 + i]) * pp.idt, sj == i ? pp.a0 * pp.idt * nj : 0.0);
+      }
+      const Dual p = mk(fv[24], pk >= 0 ? psi[pk] : 0.0);
+      Dual F[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) F[i][k] = i == k ? gd[i][k] + 1.0 : gd[i][k];
+      Dual C[3][3];   // cofactors
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+          C[i][k] = F[i1][k1] * F[i2][k2] - F[i1][k2] * F[i2][k1];
+        }
+      const Dual J = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
+      if (!(J.v > 0.0)) s_tangled = 1;
+      Dual Fi[3][3];   // F^{-1} = C^T / J
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Fi[i][k] = C[k][i] / J;
+      Dual mass;
+      if (SOLID) {
+        const Dual pJ = p * J;
+        const Dual muJ = J * pp.mu_s;
+        Dual T[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) T[i][k] = (muJ * F[i][k] - pJ * Fi[k][i]) * wq;
+        Dual inert[3], kin[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          inert[c] = TRANS ? ut[c] * J * (pp.rho_s * wq) : mk(0.0, 0.0);
+          kin[c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
+        }
+        for (int a = 0; a < k3Nloc; ++a) {
+          const double Na = bt[a * 4], G0 = bt[a * 4 + 1], G1 = bt[a * 4 + 2], G2 = bt[a * 4 + 3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const Dual m = T[c][0] * G0 + T[c][1] * G1 + T[c][2] * G2 + inert[c] * Na;
+            const int rd = a * k3B + c, ru = a * k3B + 3 + c;
+            K[rd * k3Ndofe + j] += m.d;
+            if (rd == j) vj += m.v;
+            const Dual kk = kin[c] * Na;
+            K[ru * k3Ndofe + j] += kk.d;
+            if (ru == j) vj += kk.v;
+          }
+        }
+        mass = J + (-1.0);
+      } else {
+        Dual gx[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const Dual gu0 = mk(fv[9 + i * 3 + 0], sj == 3 + i ? gj[0] : 0.0);
+            const Dual gu1 = mk(fv[9 + i * 3 + 1], sj == 3 + i ? gj[1] : 0.0);
+            const Dual gu2 = mk(fv[9 + i * 3 + 2], sj == 3 + i ? gj[2] : 0.0);
+            gx[i][k] = gu0 * Fi[0][k] + gu1 * Fi[1][k] + gu2 * Fi[2][k];
+          }
+        Dual T[3][3], conv[3], A[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Dual sig[3];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            sig[m] = (gx[c][m] + gx[m][c]) * pp.mu_f;
+            if (m == c) sig[m] = sig[m] - p;
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) T[c][k] = (sig[0] * Fi[k][0] + sig[1] * Fi[k][1] + sig[2] * Fi[k][2]) * J * wq;
+          Dual cv = TRANS
+                        ? gx[c][0] * (u[0] - dt_[0]) + gx[c][1] * (u[1] - dt_[1]) + gx[c][2] * (u[2] - dt_[2]) + ut[c]
+                        : gx[c][0] * u[0] + gx[c][1] * u[1] + gx[c][2] * u[2];
+          conv[c] = cv * J * (pp.rho_f * wq);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) A[c][k] = (pp.ale_op == 0 ? gd[c][k] + gd[k][c] : gd[c][k]) * (kale * wq);
+        }
+        for (int a = 0; a < k3Nloc; ++a) {
+          const double Na = bt[a * 4], G0 = bt[a * 4 + 1], G1 = bt[a * 4 + 2], G2 = bt[a * 4 + 3];
+          const bool ifc = (iface >> a) & 1u;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const Dual m = T[c][0] * G0 + T[c][1] * G1 + T[c][2] * G2 + conv[c] * Na;
+            const Dual al = A[c][0] * G0 + A[c][1] * G1 + A[c][2] * G2;
+            const Dual rdv = ifc ? m : al;
+            const int rd = a * k3B + c, ru = a * k3B + 3 + c;
+            K[rd * k3Ndofe + j] += rdv.d;
+            if (rd == j) vj += rdv.v;
+            if (!ifc) {
+              K[ru * k3Ndofe + j] += m.d;
+              if (ru == j) vj += m.v;
+            }
+          }
+        }
+        mass = J * (gx[0][0] + gx[1][1] + gx[2][2]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const Dual t = mass * (psi[k] * wq);
+        K[(k3NN + k) * k3Ndofe + j] += t.d;
+        if (k3NN + k == j) vj += t.v;
+      }
+    }
+    __syncthreads();
+  }
+  double* Kg = Ke + (int64_t)e * k3Ndofe * k3Ndofe;
+  for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) Kg[t] = K[t];
+  if (act) Re[(int64_t)e * k3Ndofe + j] = vj;
+  if (threadIdx.x == 0 && s_tangled) atomicExch(&status[ST_TANGLED], 1);
+}
+
+// coloured scatter of 3D element matrices (B = 6)
+__global__ void k_scatter_3d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ Ke,
+                             const double* __restrict__ Re, const int32_t* __restrict__ elem_nodes,
+                             const int32_t* __restrict__ elem_map, int64_t n_nodes, double* __restrict__ val,
+                             double* __restrict__ res) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)k3Ndofe * k3Ndofe;
+  if (t >= (int64_t)ne * per) return;
+  const int el = (int)(t / per);
+  const int ij = (int)(t % per);
+  const int i = ij / k3Ndofe, jj = ij % k3Ndofe;
+  if (i >= k3NN && jj >= k3NN) return;
+  const int e = elems[el];
+  const int lr = i < k3NN ? i / k3B : k3Nloc, ci = i < k3NN ? i % k3B : i - k3NN;
+  const int lc = jj < k3NN ? jj / k3B : k3Nloc, cj = jj < k3NN ? jj % k3B : jj - k3NN;
+  const int32_t blk = elem_map[((int64_t)e * (k3Nloc + 1) + lr) * (k3Nloc + 1) + lc];
+  val[(int64_t)blk * k3B * k3B + ci * k3B + cj] += Ke[(int64_t)e * per + ij];
+  if (res != nullptr && jj == 0) {
+    const int64_t row = i < k3NN ? (int64_t)elem_nodes[(int64_t)e * k3Nloc + lr] * k3B + ci
+                                 : (n_nodes + e) * k3B + ci;
+    res[row] += Re[(int64_t)e * k3Ndofe + i];
+  }
+}
+
+// Element-wise Galerkin coarsening in 3D.  Per child: T = A_c P_c is formed
+// in shared memory from the child's matrix (global), then the coarse element
+// matrix (global, accumulated over the 8 children) gets R_c T.  Interpolation
+// weights are products of the 1D quarter-point weights; zero weights are
+// skipped.
+size_t galerkin_3d_smem() { return (size_t)k3Ndofe * k3Ndofe * sizeof(double); }
+
+__global__ void __launch_bounds__(512)
+k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const int32_t* __restrict__ f_nodes,
+              const uint8_t* __restrict__ f_class, const uint8_t* __restrict__ f_dir,
+              const int32_t* __restrict__ c_nodes, const uint8_t* __restrict__ c_class,
+              const uint8_t* __restrict__ c_dir, double* __restrict__ Kc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* T = reinterpret_cast<double*>(smem_raw);   // [i][J]
+  __shared__ uint8_t c_cls[k3Nloc], c_msk[k3NN], f_cls[k3Nloc], f_msk[k3NN];
+  const int E = blockIdx.x;
+  const int cx = E % ncx, cy = (E / ncx) % ncy, cz = E / (ncx * ncy);
+  const int fcx = 2 * ncx, fcy = 2 * ncy;
+  double* C = Kc + (int64_t)E * k3Ndofe * k3Ndofe;
+  for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) C[t] = 0.0;
+  if (threadIdx.x < k3Nloc) c_cls[threadIdx.x] = c_class[c_nodes[(int64_t)E * k3Nloc + threadIdx.x]];
+  if (threadIdx.x < k3NN) {
+    const int a = threadIdx.x / k3B, s = threadIdx.x % k3B;
+    c_msk[threadIdx.x] = c_dir[(int64_t)c_nodes[(int64_t)E * k3Nloc + a] * k3B + s] ? 0 : 1;
+  }
+  for (int ch = 0; ch < 8; ++ch) {
+    const int sx = ch & 1, sy = (ch >> 1) & 1, sz = ch >> 2;
+    const int64_t ef = (2 * cx + sx) + (int64_t)fcx * ((2 * cy + sy) + (int64_t)fcy * (2 * cz + sz));
+    const double* A = Kf + ef * k3Ndofe * k3Ndofe;
+    __syncthreads();
+    if (threadIdx.x < k3Nloc) f_cls[threadIdx.x] = f_class[f_nodes[ef * k3Nloc + threadIdx.x]];
+    if (threadIdx.x < k3NN) {
+      const int a = threadIdx.x / k3B, s = threadIdx.x % k3B;
+      f_msk[threadIdx.x] = f_dir[(int64_t)f_nodes[ef * k3Nloc + a] * k3B + s] ? 0 : 1;
+    }
+    __syncthreads();
+    // T = A P  (J fastest: coalesced reads of A's row i)
+    for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) {
+      const int i = t / k3Ndofe, J = t % k3Ndofe;
+      const double* Ai = A + (int64_t)i * k3Ndofe;
+      double acc = 0.0;
+      if (J < k3NN) {
+        const int b = J / k3B, sl = J % k3B;
+        if (c_msk[J]) {
+          const int ib = b % 3, jb = (b / 3) % 3, kb = b / 9;
+          for (int a = 0; a < k3Nloc; ++a) {
+            const double q = qw(sx, a % 3, ib) * qw(sy, (a / 3) % 3, jb) * qw(sz, a / 9, kb);
+            if (q != 0.0 && f_msk[a * k3B + sl]) acc += Ai[a * k3B + sl] * q;
+          }
+        }
+      } else {
+        const int k = J - k3NN;
+        if (k == 0) acc = Ai[k3NN];
+        else {
+          const int sd = k == 1 ? sx : (k == 2 ? sy : sz);
+          acc = Ai[k3NN] * (sd ? 0.5 : -0.5) + Ai[k3NN + k] * 0.5;
+        }
+      }
+      T[t] = acc;
+    }
+    __syncthreads();
+    // C += R T
+    for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) {
+      const int I = t / k3Ndofe, J = t % k3Ndofe;
+      double acc = 0.0;
+      if (I < k3NN) {
+        const int b = I / k3B, sc = I % k3B;
+        if (c_msk[I]) {
+          const int ib = b % 3, jb = (b / 3) % 3, kb = b / 9;
+          const int comp = sc % k3Dim;
+          const int kc = row_kind3(c_cls[b], sc);
+          for (int a = 0; a < k3Nloc; ++a) {
+            const double q = qw(sx, a % 3, ib) * qw(sy, (a / 3) % 3, jb) * qw(sz, a / 9, kb);
+            if (q == 0.0) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int sf = h == 0 ? comp : k3Dim + comp;
+              if (f_msk[a * k3B + sf] && row_kind3(f_cls[a], sf) == kc) acc += q * T[(a * k3B + sf) * k3Ndofe + J];
+            }
+          }
+        }
+      } else {
+        const int k = I - k3NN;
+        if (k == 0) acc = T[k3NN * k3Ndofe + J];
+        else {
+          const int sd = k == 1 ? sx : (k == 2 ? sy : sz);
+          acc = T[k3NN * k3Ndofe + J] * (sd ? 0.5 : -0.5) + T[(k3NN + k) * k3Ndofe + J] * 0.5;
+        }
+      }
+      C[t] += acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
@@ -393,12 +759,13 @@ void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* 
                         double* Ke, double* Re, int32_t* status, cudaStream_t st) {
   if (ne <= 0) return;
   const int grid = (ne + kEPB - 1) / kEPB;
+  auto go = [&](auto kern) {
+    kern<<<grid, kEPB * kNdofe, 0, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp, Ke, Re, status);
+  };
   if (solid)
-    k_assemble_2d<true><<<grid, kEPB * kNdofe, 0, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp,
-                                                        Ke, Re, status);
+    pp.transient ? go(k_assemble_2d<true, true>) : go(k_assemble_2d<true, false>);
   else
-    k_assemble_2d<false><<<grid, kEPB * kNdofe, 0, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp,
-                                                         Ke, Re, status);
+    pp.transient ? go(k_assemble_2d<false, true>) : go(k_assemble_2d<false, false>);
 }
 
 void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
@@ -410,15 +777,52 @@ void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const dou
 }
 
 void launch_dirichlet(const int32_t* dir_list, int64_t n_dir, const int32_t* rowptr, const int32_t* col, double* val,
-                      int B, const double* y, const double* g, double* res, cudaStream_t st) {
+                      int B, const double* y, const double* g, double alpha, double* res, cudaStream_t st) {
   if (n_dir <= 0) return;
-  k_dirichlet<<<(unsigned)((n_dir + 255) / 256), 256, 0, st>>>(dir_list, n_dir, rowptr, col, val, B, y, g, res);
+  k_dirichlet<<<(unsigned)((n_dir + 255) / 256), 256, 0, st>>>(dir_list, n_dir, rowptr, col, val, B, y, g, alpha,
+                                                               res);
 }
 
 void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
                         const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,
                         double* Kc, cudaStream_t st) {
   k_galerkin_2d<<<ncx * ncy, 256, 0, st>>>(ncx, ncy, Kf, f_nodes, f_class, f_dir, c_nodes, c_class, c_dir, Kc);
+}
+
+}  // namespace fsi
+
+namespace fsi {
+
+void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+                        const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
+                        double* Ke, double* Re, int32_t* status, cudaStream_t st) {
+  if (ne <= 0) return;
+  const size_t smem = assemble_3d_smem();
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<ne, 192, smem, st>>>(elems, y, elem_nodes, node_class, elem_geo, n_nodes, pp, Ke, Re, status);
+  };
+  if (solid)
+    pp.transient ? go(k_assemble_3d<true, true>) : go(k_assemble_3d<true, false>);
+  else
+    pp.transient ? go(k_assemble_3d<false, true>) : go(k_assemble_3d<false, false>);
+}
+
+void launch_scatter_3d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
+                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st) {
+  if (ne <= 0) return;
+  const int64_t n = (int64_t)ne * k3Ndofe * k3Ndofe;
+  k_scatter_3d<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(elems, ne, Ke, Re, elem_nodes, elem_map, n_nodes, val,
+                                                            res);
+}
+
+void launch_galerkin_3d(int ncx, int ncy, int ncz, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
+                        const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,
+                        double* Kc, cudaStream_t st) {
+  const size_t smem = galerkin_3d_smem();
+  cudaFuncSetAttribute(k_galerkin_3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_galerkin_3d<<<ncx * ncy * ncz, 512, smem, st>>>(ncx, ncy, ncz, Kf, f_nodes, f_class, f_dir, c_nodes, c_class,
+                                                     c_dir, Kc);
 }
 
 }  // namespace fsi

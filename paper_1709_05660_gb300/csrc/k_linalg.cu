@@ -505,10 +505,9 @@ int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbu
                              const int32_t* perm, const int32_t* pinv, int32_t* status, int sm_count,
                              cudaStream_t st) {
   const int threads = 256;
-  // about 8 window columns per block: a step has kl + ku + 1 columns of work,
-  // and fewer blocks make each grid barrier cheaper
-  int grid = (int)std::min<int64_t>((int64_t)sm_count, ((int64_t)kl + ku + 1 + 7) / 8);
-  grid = (int)std::min<int64_t>(std::max(grid, 8), n);
+  // one block per SM: spreading each step's window over more blocks measured
+  // faster than fewer blocks with cheaper grid barriers
+  int grid = (int)std::min<int64_t>((int64_t)sm_count, n);
   if (grid < 1) grid = 1;
   const size_t smem = (size_t)(kl + 1) * sizeof(double) + 16;
   if (smem > 200 * 1024) return -3;

@@ -12,16 +12,28 @@ namespace fsi {
 struct PhysParams {
   double rho_f, mu_f, rho_s, mu_s;
   int ale_op;
+  // transient (BDF) terms: q_t = (a0 q + yold) * idt with yold = a1 q_n + a2 q_{n-1}
+  int transient;
+  double a0, idt;
+  const double* yold;   // internal layout, finest level (nullptr when steady)
 };
 
 // k_assemble.cu
 void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
                         double* Ke, double* Re, int32_t* status, cudaStream_t st);
+void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+                        const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
+                        double* Ke, double* Re, int32_t* status, cudaStream_t st);
+void launch_scatter_3d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
+                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st);
+void launch_galerkin_3d(int ncx, int ncy, int ncz, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
+                        const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,
+                        double* Kc, cudaStream_t st);
 void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
                        const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st);
 void launch_dirichlet(const int32_t* dir_list, int64_t n_dir, const int32_t* rowptr, const int32_t* col, double* val,
-                      int B, const double* y, const double* g, double* res, cudaStream_t st);
+                      int B, const double* y, const double* g, double alpha, double* res, cudaStream_t st);
 void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
                         const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,
                         double* Kc, cudaStream_t st);

@@ -233,8 +233,10 @@ class FSI:
     def initial_state(self, noise, y_out):
         self._check(self.lib.fsi_initial_state(self.h, _ptr(noise), _ptr(y_out)))
 
-    def set_state(self, y):
-        self._check(self.lib.fsi_set_state(self.h, _ptr(y), None, None, 0.0))
+    def set_state(self, y, y_prev=None, y_prev2=None, t: float = 0.0):
+        """Newton state; transient problems also take the previous time
+        step(s) (BDF2 with y_prev2, BDF1 without) and the new time t."""
+        self._check(self.lib.fsi_set_state(self.h, _ptr(y), _ptr(y_prev), _ptr(y_prev2), float(t)))
 
     def get_state(self, y_out):
         self._check(self.lib.fsi_get_state(self.h, _ptr(y_out)))
