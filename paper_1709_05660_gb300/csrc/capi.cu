@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -302,9 +303,35 @@ void build_device(Ctx& c) {
   const int64_t n0 = c.hl[0].Ni;
   c.c_A = dalloc<double>(c, (size_t)n0 * n0);   // banded LU in dense column-major storage
   c.c_B = dalloc<double>(c, (size_t)2 * n0);   // pivot-column buffer of the coarse sweep
-  c.c_inv = dalloc<double>(c, (size_t)n0 * n0);   // column-major inverse
   c.c_piv = dalloc<int32_t>(c, n0);
-  c.c_part = dalloc<double>(c, (size_t)((n0 + 31) / 32) * n0);   // coarse GEMV chunk partials
+  c.coarse_slab = c.dim == 3 && !c.hl[0].slab_off.empty();
+  if (!c.coarse_slab) {
+    c.c_inv = dalloc<double>(c, (size_t)n0 * n0);   // column-major inverse
+    c.c_part = dalloc<double>(c, (size_t)((n0 + 31) / 32) * n0);   // coarse GEMV chunk partials
+  } else {
+    // block-tridiagonal slab factorisation: inverse Schur complements Sinv_k
+    const HostLevel& H0 = c.hl[0];
+    c.slab_off = H0.slab_off;
+    c.slab_p = H0.slab_p;
+    const int K = (int)c.slab_off.size() - 1;
+    c.sinv_off.assign(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+      const int64_t m = c.slab_off[k + 1] - c.slab_off[k];
+      c.slab_mmax = std::max<int>(c.slab_mmax, (int)m);
+      c.sinv_off[k + 1] = c.sinv_off[k] + m * m;
+    }
+    const int64_t mm = c.slab_mmax;
+    c.c_sinv = dalloc<double>(c, (size_t)c.sinv_off[K]);
+    c.c_S = dalloc<double>(c, (size_t)mm * mm);
+    c.c_T = dalloc<double>(c, (size_t)c.slab_p * mm);
+    c.c_zb = dalloc<double>(c, n0);
+    c.c_xb = dalloc<double>(c, n0);
+    c.c_tp = dalloc<double>(c, c.slab_p);
+    c.c_part = dalloc<double>(c, (size_t)((mm + 31) / 32) * mm);
+    std::vector<int32_t> iota(mm);
+    std::iota(iota.begin(), iota.end(), 0);
+    c.c_iota = upload(c, iota);
+  }
   {
     const HostLevel& H0 = c.hl[0];
     std::vector<int32_t> pinv(H0.Ni);
@@ -356,8 +383,9 @@ void assemble(Ctx& c, bool want_res) {
     Prof pr(c, FSI_K_ASSEMBLE, (double)F.n_elem * (nd * 8.0 + nd * nd * 8.0 + nd * 8.0), 0.0, ngroups);
     for (int g = 0; g < ngroups; ++g) {
       const int ne = F.color_ptr[g + 1] - F.color_ptr[g];
-      launch_assemble_2d((g & 1) == 1, F.color_list + F.color_ptr[g], ne, c.y, F.elem_nodes, F.node_class,
-                         F.elem_geo, F.n_nodes, pp, F.Ke, Re, c.status, c.stream);
+      (c.dim == 2 ? launch_assemble_2d : launch_assemble_3d)((g & 1) == 1, F.color_list + F.color_ptr[g], ne, c.y,
+                                                              F.elem_nodes, F.node_class, F.elem_geo, F.n_nodes, pp,
+                                                              F.Ke, Re, c.status, c.stream);
       if (ne > 0) counted(c);
     }
   }
@@ -365,8 +393,9 @@ void assemble(Ctx& c, bool want_res) {
     Prof pr(c, FSI_K_SCATTER, (double)F.n_elem * nd * nd * 8.0 + (double)F.nnzb * B * B * 16.0, 0.0, ngroups + 1);
     for (int g = 0; g < ngroups; ++g) {
       const int ne = F.color_ptr[g + 1] - F.color_ptr[g];
-      launch_scatter_2d(F.color_list + F.color_ptr[g], ne, F.Ke, Re, F.elem_nodes, F.elem_map, F.n_nodes, F.val,
-                        c.res, c.stream);
+      (c.dim == 2 ? launch_scatter_2d : launch_scatter_3d)(F.color_list + F.color_ptr[g], ne, F.Ke, Re,
+                                                            F.elem_nodes, F.elem_map, F.n_nodes, F.val, c.res,
+                                                            c.stream);
       if (ne > 0) counted(c);
     }
     launch_dirichlet(F.dir_list, F.n_dir, F.rowptr, F.col, F.val, B, c.y, F.dir_val, transient ? c.inflow_alpha : 1.0,
@@ -380,8 +409,12 @@ void assemble(Ctx& c, bool want_res) {
     DevLevel& Co = c.dl[l - 1];
     {
       Prof pr(c, FSI_K_GALERKIN, (double)Fi.n_elem * nd * nd * 8.0 + (double)Co.n_elem * nd * nd * 8.0, 0.0);
-      launch_galerkin_2d(Co.cells[0], Co.cells[1], Fi.Ke, Fi.elem_nodes, Fi.node_class, Fi.dir, Co.elem_nodes,
-                         Co.node_class, Co.dir, Co.Ke, c.stream);
+      if (c.dim == 2)
+        launch_galerkin_2d(Co.cells[0], Co.cells[1], Fi.Ke, Fi.elem_nodes, Fi.node_class, Fi.dir, Co.elem_nodes,
+                           Co.node_class, Co.dir, Co.Ke, c.stream);
+      else
+        launch_galerkin_3d(Co.cells[0], Co.cells[1], Co.cells[2], Fi.Ke, Fi.elem_nodes, Fi.node_class, Fi.dir,
+                           Co.elem_nodes, Co.node_class, Co.dir, Co.Ke, c.stream);
       counted(c);
     }
     ck(cudaMemsetAsync(Co.val, 0, (size_t)Co.nnzb * B * B * sizeof(double), c.stream), "memset");
@@ -389,8 +422,9 @@ void assemble(Ctx& c, bool want_res) {
     Prof pr(c, FSI_K_SCATTER, (double)Co.n_elem * nd * nd * 8.0 + (double)Co.nnzb * B * B * 16.0, 0.0, ng + 1);
     for (int g = 0; g < ng; ++g) {
       const int ne = Co.color_ptr[g + 1] - Co.color_ptr[g];
-      launch_scatter_2d(Co.color_list + Co.color_ptr[g], ne, Co.Ke, nullptr, Co.elem_nodes, Co.elem_map, Co.n_nodes,
-                        Co.val, nullptr, c.stream);
+      (c.dim == 2 ? launch_scatter_2d : launch_scatter_3d)(Co.color_list + Co.color_ptr[g], ne, Co.Ke, nullptr,
+                                                            Co.elem_nodes, Co.elem_map, Co.n_nodes, Co.val, nullptr,
+                                                            c.stream);
       if (ne > 0) counted(c);
     }
     launch_dirichlet(Co.dir_list, Co.n_dir, Co.rowptr, Co.col, Co.val, B, nullptr, nullptr, 1.0, nullptr, c.stream);
@@ -409,7 +443,100 @@ void assemble(Ctx& c, bool want_res) {
 }
 
 // ---------------------------------------------------------------------------
-// factorisation
+// slab-blocked coarse LU (3D).  In the banded (x-slab) ordering the coarse
+// operator is block tridiagonal over slabs; block elimination gives the
+// Schur complements S_0 = A_00, S_k = A_kk - A_{k,k-1} S_{k-1}^{-1} A_{k-1,k},
+// each inverted by partial-pivot LU.  As A_{k,k-1} and A_{k-1,k} are nonzero
+// only on the last x-plane P of slab k-1, the update is
+// A_{k,k-1}[:,P] (S_{k-1}^{-1}[P,P] A_{k-1,k}[P,:]).
+// ---------------------------------------------------------------------------
+void coarse_factor_slab(Ctx& c) {
+  DevLevel& C = c.dl[0];
+  const int64_t n0 = C.Ni;
+  const int K = (int)c.slab_off.size() - 1;
+  const int p = c.slab_p;
+  double flops = 0.0, bytes = (double)n0 * n0 * 8.0;
+  for (int k = 0; k < K; ++k) {
+    const double m = (double)(c.slab_off[k + 1] - c.slab_off[k]);
+    flops += 2.0 * m * m * m * (2.0 / 3.0 + 1.0);   // LU + inverse columns
+    if (k > 0) flops += 2.0 * p * (double)p * m + 2.0 * m * p * m;
+    bytes += 3.0 * m * m * 8.0;
+  }
+  Prof pr(c, FSI_K_COARSE_FACTOR, bytes, flops, (c.n_coarse_pads > 0 ? 2 : 1) + 3 * K + 2 * (K - 1));
+  launch_dense_gather(c.B, C.nb, C.rowptr, C.col, C.val, c.coarse_pad_list, c.n_coarse_pads, c.coarse_perm, n0,
+                      c.c_A, c.stream);
+  counted(c, c.n_coarse_pads > 0 ? 2 : 1);
+  for (int k = 0; k < K; ++k) {
+    const int64_t o = c.slab_off[k];
+    const int m = (int)(c.slab_off[k + 1] - o);
+    double* Akk = c.c_A + o * n0 + o;
+    launch_copy2d(m, m, Akk, n0, c.c_S, m, c.stream);
+    counted(c);
+    if (k > 0) {
+      const int64_t op = c.slab_off[k - 1];
+      const int mp = (int)(o - op);
+      const double* Sp = c.c_sinv + c.sinv_off[k - 1];
+      // T = S_{k-1}^{-1}[P,P] A_{k-1,k}[P,:]   (p x m)
+      launch_dgemm_nn(p, m, p, 1.0, Sp + (int64_t)(mp - p) * mp + (mp - p), mp, c.c_A + o * n0 + (o - p), n0, 0.0,
+                      c.c_T, p, c.stream);
+      // S -= A_{k,k-1}[:,P] T
+      launch_dgemm_nn(m, m, p, -1.0, c.c_A + (o - p) * n0 + o, n0, c.c_T, p, 1.0, c.c_S, m, c.stream);
+      counted(c, 2);
+    }
+    const int rc = launch_coarse_lu_inverse(m, m - 1, m - 1, c.c_S, c.c_B, c.c_sinv + c.sinv_off[k], c.c_piv,
+                                            c.c_iota, c.c_iota, c.status, c.sm_count, c.stream);
+    if (rc != 0) throw ApiError(FSI_E_CUDA, "slab LU launch failed (" + std::to_string(rc) + ")");
+    counted(c, 2);
+  }
+}
+
+// x = A_0^{-1} b (internal ordering, FP64): forward block elimination
+// w_k = b_k - A_{k,k-1}[:,P] (S_{k-1}^{-1}[P,:] w_{k-1}), then back
+// substitution x_k = S_k^{-1} (w_k - A_{k,k+1} x_{k+1}) with A_{k,k+1}
+// nonzero in the rows P of slab k only.
+void coarse_apply_slab(Ctx& c, const double* b, double* x) {
+  const int64_t n0 = c.dl[0].Ni;
+  const int K = (int)c.slab_off.size() - 1;
+  const int p = c.slab_p;
+  launch_gather(n0, c.coarse_pinv, b, c.c_zb, c.stream);
+  counted(c);
+  for (int k = 1; k < K; ++k) {
+    const int64_t o = c.slab_off[k], op = c.slab_off[k - 1];
+    const int m = (int)(c.slab_off[k + 1] - o), mp = (int)(o - op);
+    const double* Sp = c.c_sinv + c.sinv_off[k - 1];
+    launch_gemv_sub(p, mp, 1.0, Sp + (mp - p), mp, c.c_zb + op, 0.0, c.c_tp, c.c_part, c.stream);
+    launch_gemv_sub(m, p, -1.0, c.c_A + (o - p) * n0 + o, n0, c.c_tp, 1.0, c.c_zb + o, c.c_part, c.stream);
+    counted(c, 4);
+  }
+  for (int k = K - 1; k >= 0; --k) {
+    const int64_t o = c.slab_off[k];
+    const int m = (int)(c.slab_off[k + 1] - o);
+    if (k < K - 1) {
+      const int64_t on = c.slab_off[k + 1];
+      const int mn = (int)(c.slab_off[k + 2] - on);
+      launch_gemv_sub(p, mn, -1.0, c.c_A + on * n0 + (on - p), n0, c.c_xb + on, 1.0, c.c_zb + (on - p), c.c_part,
+                      c.stream);
+      counted(c, 2);
+    }
+    launch_gemv_sub(m, m, 1.0, c.c_sinv + c.sinv_off[k], m, c.c_zb + o, 0.0, c.c_xb + o, c.c_part, c.stream);
+    counted(c, 2);
+  }
+  launch_gather(n0, c.coarse_perm, c.c_xb, x, c.stream);
+  counted(c);
+}
+
+double coarse_slab_apply_bytes(const Ctx& c) {
+  const int K = (int)c.slab_off.size() - 1;
+  double b = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double m = (double)(c.slab_off[k + 1] - c.slab_off[k]);
+    b += m * m * 8.0 + (k > 0 ? 2.0 * c.slab_p * m * 8.0 : 0.0);
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Schwarz factorisation (all levels >= 1) + coarse LU
 // ---------------------------------------------------------------------------
 void factor(Ctx& c) {
   const int L = (int)c.dl.size();
@@ -433,7 +560,9 @@ void factor(Ctx& c) {
   }
   DevLevel& C = c.dl[0];
   const int64_t n0 = C.Ni;
-  {
+  if (c.coarse_slab) {
+    coarse_factor_slab(c);
+  } else {
     const double nn = (double)n0;
     // banded LU (2 n kl (kl + ku) flops) + inverse columns (~2 n^2 (kl + ku) flops, sparsity aside)
     const double bw = (double)c.coarse_bw;
@@ -488,6 +617,12 @@ template <> struct VC<double> {
   }
   static void coarse(Ctx& c, const double* b, double* x) {
     const double n0 = (double)c.dl[0].Ni;
+    if (c.coarse_slab) {
+      const double by = coarse_slab_apply_bytes(c);
+      Prof pr(c, FSI_K_TRANSFER, by + 4.0 * n0 * 8.0, by / 4.0, 2 + 8 * ((int)c.slab_off.size() - 1));
+      coarse_apply_slab(c, b, x);
+      return;
+    }
     Prof pr(c, FSI_K_TRANSFER, n0 * n0 * 8.0 + 2.0 * n0 * 8.0, 2.0 * n0 * n0);
     launch_gemv(c.dl[0].Ni, c.c_inv, b, x, c.c_part, c.stream);
     counted(c, 2);
@@ -526,6 +661,16 @@ template <> struct VC<float> {
   static void coarse(Ctx& c, const float* b, float* x) {
     // the coarsest-grid solve stays FP64 (FP64 inverse, FP64 accumulation)
     const double n0 = (double)c.dl[0].Ni;
+    if (c.coarse_slab) {
+      const double by = coarse_slab_apply_bytes(c);
+      Prof pr(c, FSI_K_TRANSFER, by + 4.0 * n0 * 8.0 + 2.0 * n0 * 4.0, by / 4.0, 4 + 8 * ((int)c.slab_off.size() - 1));
+      launch_axpby_f32_to_f64(c.dl[0].Ni, b, c.c_xb, c.stream);
+      counted(c);
+      coarse_apply_slab(c, c.c_xb, c.c_zb);   // both buffers are free again when it writes its result
+      launch_to_f32(c.dl[0].Ni, c.c_zb, x, c.stream);
+      counted(c);
+      return;
+    }
     Prof pr(c, FSI_K_TRANSFER, n0 * n0 * 8.0 + 2.0 * n0 * 4.0, 2.0 * n0 * n0);
     launch_gemv_f32io(c.dl[0].Ni, c.c_inv, b, x, c.c_part, c.stream);
     counted(c, 2);
@@ -745,7 +890,20 @@ static int64_t estimate_device_bytes(const Ctx& c) {
   const double n0 = (double)c.hl[0].Ni;
   b += F.Ni * 8.0 * 2 + (m + 1.0) * F.Ni * 8.0 + m * (double)F.Ni * fs + F.Ni * 8.0 * 4 + F.N * 8.0 * 2;
   if (c.desc.transient != 0) b += F.Ni * 8.0;
-  b += max_dense * fs + 3.0 * n0 * n0 * 8.0 + F.n_elem * (double)nd * 8.0 + 1e6;
+  b += max_dense * fs + F.n_elem * (double)nd * 8.0 + 1e6;
+  const std::vector<int64_t>& so = c.hl[0].slab_off;
+  if (c.dim == 3 && !so.empty()) {
+    // dense banded-order operator + Sinv_k blocks + LU scratch + vectors
+    double mm = 0.0, sum = 0.0;
+    for (size_t k = 0; k + 1 < so.size(); ++k) {
+      const double m = (double)(so[k + 1] - so[k]);
+      mm = std::max(mm, m);
+      sum += m * m;
+    }
+    b += n0 * n0 * 8.0 + (sum + mm * mm + c.hl[0].slab_p * mm + mm * mm / 32.0 + mm) * 8.0 + 6.0 * n0 * 8.0;
+  } else {
+    b += 2.0 * n0 * n0 * 8.0 + (n0 / 32.0 + 1.0) * n0 * 8.0 + 2.0 * n0 * 8.0;
+  }
   return (int64_t)b;
 }
 
@@ -790,7 +948,6 @@ int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opt
   c->opts = *opts;
   c->stream = static_cast<cudaStream_t>(stream);
   int rc = guard(c, [&] {
-    if (desc->dim != 2) throw ApiError(FSI_E_INVALID, "the device path supports dim = 2");
     plan(c, desc, opts);
     c->mixed = opts->precision == FSI_MIXED;
     int dev = 0;

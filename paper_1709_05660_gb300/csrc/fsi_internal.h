@@ -66,6 +66,11 @@ struct HostLevel {
   // coarse level: bandwidth-reducing ordering (internal unknown -> position)
   std::vector<int32_t> coarse_perm;
   int coarse_bw = 0;
+  // slab partition of the banded ordering (block-tridiagonal coarse solve):
+  // slab k = positions [slab_off[k], slab_off[k+1]); the coupling of slabs k-1
+  // and k runs only through the last slab_p positions of slab k-1
+  std::vector<int64_t> slab_off;
+  int slab_p = 0;
 };
 
 bool build_host_hierarchy(const fsi_problem_desc& d, const fsi_solver_opts& o,
@@ -158,6 +163,12 @@ struct Ctx {
   int32_t* coarse_pinv = nullptr;         // banded position -> internal unknown
   int coarse_bw = 0;
   int n_coarse_pads = 0;
+  // slab-blocked coarse solve (3D): Sinv_k blocks, LU scratch, vectors
+  bool coarse_slab = false;
+  std::vector<int64_t> slab_off, sinv_off;
+  int slab_p = 0, slab_mmax = 0;
+  double *c_sinv = nullptr, *c_S = nullptr, *c_T = nullptr, *c_zb = nullptr, *c_xb = nullptr, *c_tp = nullptr;
+  int32_t* c_iota = nullptr;
   float t_assemble = 0.f, t_factor = 0.f, t_solve = 0.f;
   int red_blocks = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <numeric>
 
 #include "fsi_internal.h"
@@ -410,6 +411,40 @@ void build_coarse_ordering(HostLevel& L) {
     for (int32_t k = L.rowptr[b]; k < L.rowptr[b + 1]; ++k)
       bw = std::max<int64_t>(bw, std::llabs((int64_t)pos[b] - pos[L.col[k]]) * L.B + L.B - 1);
   L.coarse_bw = (int)bw;
+  // slabs: nodes of x-planes 0..2 and element layer 0 form slab 0; x-planes
+  // 2k+1, 2k+2 and element layer k form slab k.  An element of layer k
+  // touches x-planes 2k, 2k+1, 2k+2 only, so slabs k-1 and k couple through
+  // x-plane 2k alone, the last plane of slab k-1 in the banded ordering.
+  const int K = L.cells[0];
+  auto slab_of = [&](int64_t b) -> int {
+    if (b < L.n_nodes) {
+      const int ix = (int)(b % L.nodes_ax[0]);
+      return ix <= 2 ? 0 : (ix - 1) / 2;
+    }
+    return (int)((b - L.n_nodes) % L.cells[0]);
+  };
+  std::vector<int64_t> cnt(K + 1, 0);
+  for (int64_t b = 0; b < nb; ++b) cnt[slab_of(b) + 1] += L.B;
+  L.slab_off.assign(K + 1, 0);
+  for (int k = 0; k < K; ++k) L.slab_off[k + 1] = L.slab_off[k] + cnt[k + 1];
+  L.slab_p = (int)((L.n_nodes / L.nodes_ax[0]) * L.B);
+  bool ok = L.slab_off[K] == L.Ni;
+  for (int64_t b = 0; b < nb && ok; ++b) {
+    const int64_t q = (int64_t)pos[b] * L.B;
+    const int sb = slab_of(b);
+    ok = q >= L.slab_off[sb] && q < L.slab_off[sb + 1];
+    for (int32_t k = L.rowptr[b]; k < L.rowptr[b + 1] && ok; ++k) {
+      const int64_t qc = (int64_t)pos[L.col[k]] * L.B;
+      const int sc = slab_of(L.col[k]);
+      if (sc == sb) continue;
+      if (std::abs(sc - sb) != 1) { ok = false; break; }
+      // the slab-(min) side of the coupling lies in the last plane of that slab
+      const int lo = std::min(sb, sc);
+      const int64_t qlo = sb < sc ? q : qc;
+      ok = qlo >= L.slab_off[lo + 1] - L.slab_p;
+    }
+  }
+  if (!ok) L.slab_off.clear();   // no slab structure: the banded solve is used
 }
 
 }  // namespace

@@ -570,4 +570,118 @@ void launch_gemv_f32io(int64_t n, const double* A, const float* x, float* y, dou
   k_gemv_cm_sum<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nchunk, part, y);
 }
 
+// ---------------------------------------------------------------------------
+// slab-blocked coarse solve (3D): dense FP64 building blocks on column-major
+// sub-matrices with explicit leading dimensions
+// ---------------------------------------------------------------------------
+
+// C (m x n, ldc) = beta C + alpha A (m x k, lda) B (k x n, ldb).  64 x 64
+// output tile per block, k in steps of 16 staged in shared memory, 4 x 4
+// outputs per thread (rows tx + 16 i, columns ty + 16 j).
+__global__ void __launch_bounds__(256) k_dgemm_nn(int m, int n, int k, double alpha, const double* __restrict__ A,
+                                                 int64_t lda, const double* __restrict__ Bm, int64_t ldb, double beta,
+                                                 double* __restrict__ C, int64_t ldc) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < k; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int r = e % 64, kk = e / 64;            // A tile: rows fastest (coalesced columns)
+      const int gr = r0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < m && gk < k) ? A[(int64_t)gk * lda + gr] : 0.0;
+      const int kb = e % 16, cb = e / 16;           // B tile: k fastest (coalesced columns)
+      const int gkb = k0 + kb, gc = c0 + cb;
+      Bs[kb][cb] = (gkb < k && gc < n) ? Bm[(int64_t)gc * ldb + gkb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gr = r0 + tx + 16 * i, gc = c0 + ty + 16 * j;
+      if (gr < m && gc < n) {
+        double* cp = C + (int64_t)gc * ldc + gr;
+        *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * acc[i][j];
+      }
+    }
+}
+
+void launch_dgemm_nn(int m, int n, int k, double alpha, const double* A, int64_t lda, const double* Bm, int64_t ldb,
+                     double beta, double* C, int64_t ldc, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return;
+  k_dgemm_nn<<<dim3((unsigned)((m + 63) / 64), (unsigned)((n + 63) / 64)), 256, 0, st>>>(m, n, k, alpha, A, lda, Bm,
+                                                                                          ldb, beta, C, ldc);
+}
+
+// dst (m x n, ldd) = src (m x n, lds), column-major
+__global__ void k_copy2d(int m, int n, const double* __restrict__ src, int64_t lds, double* __restrict__ dst,
+                         int64_t ldd) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * n) return;
+  const int64_t c = t / m, r = t % m;
+  dst[c * ldd + r] = src[c * lds + r];
+}
+
+void launch_copy2d(int m, int n, const double* src, int64_t lds, double* dst, int64_t ldd, cudaStream_t st) {
+  const int64_t t = (int64_t)m * n;
+  if (t <= 0) return;
+  k_copy2d<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(m, n, src, lds, dst, ldd);
+}
+
+// y (m) = beta y + alpha A (m x nc, lda) x, A column-major.  Stage 1: block
+// (rb, cb) forms the partial product of rows [256 rb, 256 rb + 256) over the
+// column chunk cb; stage 2 adds the chunk partials in a fixed order.  x and y
+// must not overlap.
+__global__ void __launch_bounds__(256) k_gemv_sub_part(int m, int nc, const double* __restrict__ A, int64_t lda,
+                                                       const double* __restrict__ x, double* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c0 = blockIdx.y * kGemvChunk;
+  const int c1 = min(nc, c0 + kGemvChunk);
+  if (i >= m) return;
+  double a0 = 0.0, a1 = 0.0;
+  int c = c0;
+  for (; c + 1 < c1; c += 2) {
+    a0 += A[(int64_t)c * lda + i] * x[c];
+    a1 += A[(int64_t)(c + 1) * lda + i] * x[c + 1];
+  }
+  if (c < c1) a0 += A[(int64_t)c * lda + i] * x[c];
+  part[(int64_t)blockIdx.y * m + i] = a0 + a1;
+}
+
+__global__ void k_gemv_sub_sum(int m, int nchunk, const double* __restrict__ part, double alpha, double beta,
+                               double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int q = 0; q < nchunk; ++q) s += part[(int64_t)q * m + i];
+  y[i] = (beta == 0.0 ? 0.0 : beta * y[i]) + alpha * s;
+}
+
+void launch_gemv_sub(int m, int nc, double alpha, const double* A, int64_t lda, const double* x, double beta,
+                     double* y, double* part, cudaStream_t st) {
+  if (m <= 0) return;
+  const int nchunk = (nc + kGemvChunk - 1) / kGemvChunk;
+  if (nchunk > 0)
+    k_gemv_sub_part<<<dim3((unsigned)((m + 255) / 256), (unsigned)nchunk), 256, 0, st>>>(m, nc, A, lda, x, part);
+  k_gemv_sub_sum<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, nchunk, part, alpha, beta, y);
+}
+
 }  // namespace fsi

@@ -83,6 +83,13 @@ int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbu
 // coarse apply: part holds ceil(n / 32) * n doubles of scratch
 void launch_gemv(int64_t n, const double* A, const double* x, double* y, double* part, cudaStream_t st);
 void launch_gemv_f32io(int64_t n, const double* A, const float* x, float* y, double* part, cudaStream_t st);
+// slab-blocked coarse solve: column-major FP64 sub-matrices with leading dimensions
+void launch_dgemm_nn(int m, int n, int k, double alpha, const double* A, int64_t lda, const double* Bm, int64_t ldb,
+                     double beta, double* C, int64_t ldc, cudaStream_t st);
+void launch_copy2d(int m, int n, const double* src, int64_t lds, double* dst, int64_t ldd, cudaStream_t st);
+// y = beta y + alpha A x; part holds ceil(nc / 32) * m doubles of scratch
+void launch_gemv_sub(int m, int nc, double alpha, const double* A, int64_t lda, const double* x, double beta,
+                     double* y, double* part, cudaStream_t st);
 void launch_csr_spmv_f32(int64_t nrows, const int32_t* ptr, const int32_t* col, const float* val, const float* x,
                          float* y, bool add, cudaStream_t st);
 void launch_to_f32(int64_t n, const double* in, float* out, cudaStream_t st);
