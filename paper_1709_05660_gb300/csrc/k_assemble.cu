@@ -162,7 +162,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
           dt_[i] = mk((pp.a0 * dvv[i] + dold[i]) * pp.idt, sj == i ? pp.a0 * pp.idt * nj : 0.0);
         }
       }
-      const Dual p = mk(pv, pk >= 0 ? psi[pk] : 0.0);
+      const Dual p = mk(pv, pk == 0 ? 1.0 : (pk == 1 ? xi : (pk == 2 ? eta : 0.0)));
       Dual F[2][2];
       F[0][0] = gd[0][0] + 1.0; F[0][1] = gd[0][1];
       F[1][0] = gd[1][0];       F[1][1] = gd[1][1] + 1.0;
@@ -181,17 +181,29 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         for (int i = 0; i < 2; ++i)
 #pragma unroll
           for (int k = 0; k < 2; ++k) T[i][k] = muJ * F[i][k] - pJ * Fi[k][i];
+        Dual Tw[2][2], inert[2], kin[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          Tw[c][0] = T[c][0] * wq;
+          Tw[c][1] = T[c][1] * wq;
+          inert[c] = TRANS ? ut[c] * J * (pp.rho_s * wq) : mk(0.0, 0.0);
+          kin[c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
+        }
+        // derivative parts for column j; the value part only for this
+        // thread's own residual row j
 #pragma unroll
         for (int a = 0; a < kNloc; ++a) {
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            Dual m = (T[c][0] * Gx[a] + T[c][1] * Gy[a]) * wq;
-            if (TRANS) m = m + ut[c] * J * (pp.rho_s * Nb[a] * wq);
-            acc[a * kB + c] += m.d;
-            if (a * kB + c == j) vj += m.v;
-            const Dual kin = (TRANS ? u[c] - dt_[c] : u[c]) * (Nb[a] * wq);
-            acc[a * kB + 2 + c] += kin.d;
-            if (a * kB + 2 + c == j) vj += kin.v;
+            acc[a * kB + c] += Tw[c][0].d * Gx[a] + Tw[c][1].d * Gy[a] + inert[c].d * Nb[a];
+            acc[a * kB + 2 + c] += kin[c].d * Nb[a];
+          }
+        }
+        if (aj >= 0) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (sj == c) vj += Tw[c][0].v * gxj + Tw[c][1].v * gyj + inert[c].v * nj;
+            if (sj == 2 + c) vj += kin[c].v * nj;
           }
         }
         mass = J + (-1.0);
@@ -228,17 +240,24 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
           const bool ifc = (iface >> a) & 1u;
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            const Dual m = T[c][0] * Gx[a] + T[c][1] * Gy[a] + conv[c] * Nb[a];
-            const Dual al = A[c][0] * Gx[a] + A[c][1] * Gy[a];
+            const double md = T[c][0].d * Gx[a] + T[c][1].d * Gy[a] + conv[c].d * Nb[a];
             // interface node: momentum in the d-row, no ALE row (psi = 0 on the interface)
             // fluid node: ALE in the d-row, momentum in the u-row
-            const Dual rd = ifc ? m : al;
-            acc[a * kB + c] += rd.d;
-            if (a * kB + c == j) vj += rd.v;
-            if (!ifc) {
-              acc[a * kB + 2 + c] += m.d;
-              if (a * kB + 2 + c == j) vj += m.v;
+            if (ifc) {
+              acc[a * kB + c] += md;
+            } else {
+              acc[a * kB + c] += A[c][0].d * Gx[a] + A[c][1].d * Gy[a];
+              acc[a * kB + 2 + c] += md;
             }
+          }
+        }
+        if (aj >= 0) {
+          const bool ifc = (iface >> aj) & 1u;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const double mv = T[c][0].v * gxj + T[c][1].v * gyj + conv[c].v * nj;
+            if (sj == c) vj += ifc ? mv : A[c][0].v * gxj + A[c][1].v * gyj;
+            if (sj == 2 + c && !ifc) vj += mv;
           }
         }
         mass = J * (gx[0][0] + gx[1][1]);
@@ -520,7 +539,7 @@ k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
         ut[i] = mk((pp.a0 * fv[18 + i] + fv[25 + i]) * pp.idt, sj == 3 + i ? pp.a0 * pp.idt * nj : 0.0);
         dt_[i] = mk((pp.a0 * fv[21 + i] + fv[28 + i]) * pp.idt, sj == i ? pp.a0 * pp.idt * nj : 0.0);
       }
-      const Dual p = mk(fv[24], pk >= 0 ? psi[pk] : 0.0);
+      const Dual p = mk(fv[24], pk == 0 ? 1.0 : (pk == 1 ? xi : (pk == 2 ? eta : (pk == 3 ? zeta : 0.0))));
       Dual F[3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -556,17 +575,23 @@ k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
           inert[c] = TRANS ? ut[c] * J * (pp.rho_s * wq) : mk(0.0, 0.0);
           kin[c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
         }
+        // derivative parts for column j; the value part only for this
+        // thread's own residual row j
         for (int a = 0; a < k3Nloc; ++a) {
           const double Na = bt[a * 4], G0 = bt[a * 4 + 1], G1 = bt[a * 4 + 2], G2 = bt[a * 4 + 3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const Dual m = T[c][0] * G0 + T[c][1] * G1 + T[c][2] * G2 + inert[c] * Na;
             const int rd = a * k3B + c, ru = a * k3B + 3 + c;
-            K[rd * k3Ndofe + j] += m.d;
-            if (rd == j) vj += m.v;
-            const Dual kk = kin[c] * Na;
-            K[ru * k3Ndofe + j] += kk.d;
-            if (ru == j) vj += kk.v;
+            K[rd * k3Ndofe + j] += T[c][0].d * G0 + T[c][1].d * G1 + T[c][2].d * G2 + inert[c].d * Na;
+            K[ru * k3Ndofe + j] += kin[c].d * Na;
+          }
+        }
+        if (aj >= 0) {
+          const double Na = bt[aj * 4], G0 = bt[aj * 4 + 1], G1 = bt[aj * 4 + 2], G2 = bt[aj * 4 + 3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {   // unrolled select: no dynamic register-array index
+            if (sj == c) vj += T[c][0].v * G0 + T[c][1].v * G1 + T[c][2].v * G2 + inert[c].v * Na;
+            if (sj == 3 + c) vj += kin[c].v * Na;
           }
         }
         mass = J + (-1.0);
@@ -604,16 +629,24 @@ k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
           const bool ifc = (iface >> a) & 1u;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const Dual m = T[c][0] * G0 + T[c][1] * G1 + T[c][2] * G2 + conv[c] * Na;
-            const Dual al = A[c][0] * G0 + A[c][1] * G1 + A[c][2] * G2;
-            const Dual rdv = ifc ? m : al;
+            const double md = T[c][0].d * G0 + T[c][1].d * G1 + T[c][2].d * G2 + conv[c].d * Na;
             const int rd = a * k3B + c, ru = a * k3B + 3 + c;
-            K[rd * k3Ndofe + j] += rdv.d;
-            if (rd == j) vj += rdv.v;
-            if (!ifc) {
-              K[ru * k3Ndofe + j] += m.d;
-              if (ru == j) vj += m.v;
+            if (ifc) {
+              K[rd * k3Ndofe + j] += md;
+            } else {
+              K[rd * k3Ndofe + j] += A[c][0].d * G0 + A[c][1].d * G1 + A[c][2].d * G2;
+              K[ru * k3Ndofe + j] += md;
             }
+          }
+        }
+        if (aj >= 0) {
+          const double Na = bt[aj * 4], G0 = bt[aj * 4 + 1], G1 = bt[aj * 4 + 2], G2 = bt[aj * 4 + 3];
+          const bool ifc = (iface >> aj) & 1u;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double mv = T[c][0].v * G0 + T[c][1].v * G1 + T[c][2].v * G2 + conv[c].v * Na;
+            if (sj == c) vj += ifc ? mv : A[c][0].v * G0 + A[c][1].v * G1 + A[c][2].v * G2;
+            if (sj == 3 + c && !ifc) vj += mv;
           }
         }
         mass = J * (gx[0][0] + gx[1][1] + gx[2][2]);
@@ -658,10 +691,12 @@ __global__ void k_scatter_3d(const int32_t* __restrict__ elems, int ne, const do
 }
 
 // Element-wise Galerkin coarsening in 3D.  Per child: T = A_c P_c is formed
-// in shared memory from the child's matrix (global), then the coarse element
-// matrix (global, accumulated over the 8 children) gets R_c T.  Interpolation
-// weights are products of the 1D quarter-point weights; zero weights are
-// skipped.
+// in shared memory from the child's matrix (global, row-major), then the
+// coarse element matrix (global, accumulated over the 8 children) gets
+// R_c T.  The interpolation weights of a child are products of 1D
+// quarter-point weights; each coarse node b keeps the compact list of the
+// child nodes a with a nonzero weight (125 of the 27 x 27 pairs), built from
+// an 18-entry 1D table, so no FP64 work is spent on zero weights.
 size_t galerkin_3d_smem() { return (size_t)k3Ndofe * k3Ndofe * sizeof(double); }
 
 __global__ void __launch_bounds__(512)
@@ -671,12 +706,21 @@ k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const in
               const uint8_t* __restrict__ c_dir, double* __restrict__ Kc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* T = reinterpret_cast<double*>(smem_raw);   // [i][J]
+  __shared__ double w1[2][3][3];                     // [side][fine 1D][coarse 1D]
+  __shared__ double l_w[125];
+  __shared__ uint8_t l_a[125];
+  __shared__ int l_ptr[k3Nloc + 1];
   __shared__ uint8_t c_cls[k3Nloc], c_msk[k3NN], f_cls[k3Nloc], f_msk[k3NN];
   const int E = blockIdx.x;
   const int cx = E % ncx, cy = (E / ncx) % ncy, cz = E / (ncx * ncy);
   const int fcx = 2 * ncx, fcy = 2 * ncy;
+  (void)ncz;
   double* C = Kc + (int64_t)E * k3Ndofe * k3Ndofe;
   for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) C[t] = 0.0;
+  if (threadIdx.x < 18) {
+    const int sd = threadIdx.x / 9, i = (threadIdx.x / 3) % 3, m = threadIdx.x % 3;
+    w1[sd][i][m] = qw(sd, i, m);
+  }
   if (threadIdx.x < k3Nloc) c_cls[threadIdx.x] = c_class[c_nodes[(int64_t)E * k3Nloc + threadIdx.x]];
   if (threadIdx.x < k3NN) {
     const int a = threadIdx.x / k3B, s = threadIdx.x % k3B;
@@ -692,6 +736,43 @@ k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const in
       const int a = threadIdx.x / k3B, s = threadIdx.x % k3B;
       f_msk[threadIdx.x] = f_dir[(int64_t)f_nodes[ef * k3Nloc + a] * k3B + s] ? 0 : 1;
     }
+    // nonzero pattern of the child's weights: count per coarse node
+    if (threadIdx.x < k3Nloc) {
+      const int b = threadIdx.x, mx = b % 3, my = (b / 3) % 3, mz = b / 9;
+      int n = 1;
+      const int sd[3] = {sx, sy, sz}, mm[3] = {mx, my, mz};
+      for (int d = 0; d < 3; ++d) {
+        int c = 0;
+        for (int i = 0; i < 3; ++i) c += w1[sd[d]][i][mm[d]] != 0.0;
+        n *= c;
+      }
+      l_ptr[b + 1] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      l_ptr[0] = 0;
+      for (int b = 0; b < k3Nloc; ++b) l_ptr[b + 1] += l_ptr[b];
+    }
+    __syncthreads();
+    if (threadIdx.x < k3Nloc) {
+      const int b = threadIdx.x, mx = b % 3, my = (b / 3) % 3, mz = b / 9;
+      int q = l_ptr[b];
+      for (int iz = 0; iz < 3; ++iz) {
+        const double wz = w1[sz][iz][mz];
+        if (wz == 0.0) continue;
+        for (int iy = 0; iy < 3; ++iy) {
+          const double wy = w1[sy][iy][my];
+          if (wy == 0.0) continue;
+          for (int ix = 0; ix < 3; ++ix) {
+            const double wx = w1[sx][ix][mx];
+            if (wx == 0.0) continue;
+            l_a[q] = (uint8_t)(ix + 3 * iy + 9 * iz);
+            l_w[q] = wx * wy * wz;
+            ++q;
+          }
+        }
+      }
+    }
     __syncthreads();
     // T = A P  (J fastest: coalesced reads of A's row i)
     for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) {
@@ -700,13 +781,11 @@ k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const in
       double acc = 0.0;
       if (J < k3NN) {
         const int b = J / k3B, sl = J % k3B;
-        if (c_msk[J]) {
-          const int ib = b % 3, jb = (b / 3) % 3, kb = b / 9;
-          for (int a = 0; a < k3Nloc; ++a) {
-            const double q = qw(sx, a % 3, ib) * qw(sy, (a / 3) % 3, jb) * qw(sz, a / 9, kb);
-            if (q != 0.0 && f_msk[a * k3B + sl]) acc += Ai[a * k3B + sl] * q;
+        if (c_msk[J])
+          for (int q = l_ptr[b]; q < l_ptr[b + 1]; ++q) {
+            const int a = l_a[q];
+            if (f_msk[a * k3B + sl]) acc += Ai[a * k3B + sl] * l_w[q];
           }
-        }
       } else {
         const int k = J - k3NN;
         if (k == 0) acc = Ai[k3NN];
@@ -718,23 +797,21 @@ k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const in
       T[t] = acc;
     }
     __syncthreads();
-    // C += R T
+    // C += R T  (row I uniform across a warp: uniform lists and masks)
     for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) {
       const int I = t / k3Ndofe, J = t % k3Ndofe;
       double acc = 0.0;
       if (I < k3NN) {
         const int b = I / k3B, sc = I % k3B;
         if (c_msk[I]) {
-          const int ib = b % 3, jb = (b / 3) % 3, kb = b / 9;
           const int comp = sc % k3Dim;
           const int kc = row_kind3(c_cls[b], sc);
-          for (int a = 0; a < k3Nloc; ++a) {
-            const double q = qw(sx, a % 3, ib) * qw(sy, (a / 3) % 3, jb) * qw(sz, a / 9, kb);
-            if (q == 0.0) continue;
+          for (int q = l_ptr[b]; q < l_ptr[b + 1]; ++q) {
+            const int a = l_a[q];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int sf = h == 0 ? comp : k3Dim + comp;
-              if (f_msk[a * k3B + sf] && row_kind3(f_cls[a], sf) == kc) acc += q * T[(a * k3B + sf) * k3Ndofe + J];
+              if (f_msk[a * k3B + sf] && row_kind3(f_cls[a], sf) == kc) acc += l_w[q] * T[(a * k3B + sf) * k3Ndofe + J];
             }
           }
         }
