@@ -199,6 +199,33 @@ int fsi_prolong(fsi_ctx* ctx, int level, const double* coarse, double* fine);
 /* Number of kernel launches issued by this ctx since it was built. */
 int64_t fsi_launch_count(const fsi_ctx* ctx);
 
+/* ---- coarse solve without allocation (no counterpart in the paper) ---- */
+
+/* Largest level-0 internal length (N_0 plus the zero padding of element
+ * pressure blocks) the static variant accepts, and the size in doubles of
+ * its file-scope scratch array: ceil(4096 / 32) * 4096 = 2^19 (4 MiB). */
+enum { FSI_STATIC_COARSE_MAX = 4096, FSI_STATIC_PART_MAX = 1 << 19 };
+
+/* x = J_0^{-1} b on level 0 (canonical numbering, FP64; host or device
+ * buffers) with the dense coarse inverse of fsi_factor_schwarz: the same
+ * kernels and summation order as the coarse step of fsi_apply_vcycle, so the
+ * result equals that of fsi_apply_vcycle on a one-level instance bit for
+ * bit.  The GEMV partial sums live in a file-scope device array of
+ * FSI_STATIC_PART_MAX doubles instead of instance scratch, and the call
+ * allocates no device or pinned memory.  It is meant for callers that cannot
+ * allocate at call time: a serving worker whose instances were admitted
+ * against a fixed device-memory budget byte for byte, and callers driving
+ * several streams at once, for whom a cudaMalloc / cudaFree could
+ * synchronise the device and stall the other streams.
+ * Limits: FSI_E_INVALID when the level-0 internal length exceeds
+ * FSI_STATIC_COARSE_MAX, and for 3D instances (slab-blocked coarse LU).
+ * The array is shared by every instance on a device: calls that overlap in
+ * time (two threads or two streams) race on it and must be serialised by the
+ * caller.  The first call on a device resolves the array's address once
+ * (cudaGetSymbolAddress); make that first call before any stream capture on
+ * the device.  Nothing in the array has to start at zero. */
+int fsi_coarse_solve_static(fsi_ctx* ctx, const double* b, double* x);
+
 /* Per-kernel-class timing.  With profiling on, every launch of a class is
  * bracketed by CUDA events on the ctx stream, and its algorithmic traffic
  * (bytes the operation must move at least once: matrix, index and vector

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <stdexcept>
@@ -1326,6 +1327,55 @@ int fsi_apply_vcycle(fsi_ctx* c, const double* b, double* z) {
       precondition(*c, c->bk, c->xk, nullptr);
     }
     to_canonical(*c, L - 1, c->xk, z);
+    sync(*c);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// coarse solve with file-scope scratch (allocates nothing)
+// ---------------------------------------------------------------------------
+// GEMV partial sums of fsi_coarse_solve_static.  Shared by every instance on
+// a device; the first GEMV stage writes every partial the second stage
+// reads, so nothing in it has to start at zero.
+static __device__ __align__(256) double g_coarse_part[FSI_STATIC_PART_MAX];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_part_mu;
+double* g_part_addr[kMaxDevices] = {};
+
+// device address of g_coarse_part, resolved once per device
+double* static_part(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) throw ApiError(FSI_E_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_part_mu);
+  if (!g_part_addr[dev]) {
+    void* p = nullptr;
+    ck(cudaGetSymbolAddress(&p, g_coarse_part), "cudaGetSymbolAddress");
+    g_part_addr[dev] = static_cast<double*>(p);
+  }
+  return g_part_addr[dev];
+}
+}  // namespace
+
+int fsi_coarse_solve_static(fsi_ctx* c, const double* b, double* x) {
+  return guard(c, [&] {
+    need_device(*c);
+    if (!b || !x) throw ApiError(FSI_E_INVALID, "null pointer");
+    if (c->coarse_slab)
+      throw ApiError(FSI_E_INVALID, "fsi_coarse_solve_static: the slab-blocked (3D) coarse LU is not supported");
+    DevLevel& C = c->dl[0];
+    const int64_t n0 = C.Ni;
+    const int64_t need = ((n0 + 31) / 32) * n0;
+    if (need > FSI_STATIC_PART_MAX)
+      throw ApiError(FSI_E_INVALID, "fsi_coarse_solve_static: level-0 internal length " + std::to_string(n0) +
+                                        " exceeds the static scratch limit of " + std::to_string(FSI_STATIC_COARSE_MAX));
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    double* part = static_part(dev);
+    to_internal(*c, 0, b, C.b);
+    launch_gemv(n0, c->c_inv, C.b, C.x, part, c->stream);
+    counted(*c, 2);
+    to_canonical(*c, 0, C.x, x);
     sync(*c);
   });
 }

@@ -33,7 +33,7 @@ SYMBOLS = (
     "fsi_apply_operator", "fsi_apply_vcycle", "fsi_apply_smoother", "fsi_restrict", "fsi_prolong",
     "fsi_launch_count", "fsi_plan_hierarchy", "fsi_export_transfer", "fsi_set_profiling",
     "fsi_kernel_stats", "fsi_server_create", "fsi_serve_submit", "fsi_serve_poll", "fsi_serve_drain",
-    "fsi_server_resident_bytes", "fsi_server_destroy",
+    "fsi_server_resident_bytes", "fsi_server_destroy", "fsi_coarse_solve_static",
 )
 
 # kernel classes for fsi_kernel_stats
@@ -123,6 +123,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fsi_export_patches.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, vp, vp, vp]
     lib.fsi_apply_operator.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.fsi_apply_vcycle.argtypes = [vp, vp, vp]
+    lib.fsi_coarse_solve_static.argtypes = [vp, vp, vp]
     lib.fsi_apply_smoother.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.fsi_restrict.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.fsi_prolong.argtypes = [vp, ctypes.c_int, vp, vp]
@@ -312,6 +313,11 @@ class FSI:
 
     def apply_vcycle(self, b, z):
         self._check(self.lib.fsi_apply_vcycle(self.h, _ptr(b), _ptr(z)))
+
+    def coarse_solve_static(self, b, x):
+        """x = J_0^{-1} b with the coarse solve's scratch in a fixed
+        file-scope device array (the call allocates nothing)."""
+        self._check(self.lib.fsi_coarse_solve_static(self.h, _ptr(b), _ptr(x)))
 
     def apply_smoother(self, level, b, x, x_out):
         self._check(self.lib.fsi_apply_smoother(self.h, level, _ptr(b), _ptr(x), _ptr(x_out)))
