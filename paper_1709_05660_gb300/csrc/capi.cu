@@ -162,6 +162,7 @@ void check_status(Ctx& c) {
   ck(cudaMemcpyAsync(st, c.status, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "D2H status");
   sync(c);
   ck(cudaMemsetAsync(c.status, 0, sizeof(st), c.stream), "memset");
+  if (st[ST_TIMEOUT]) throw ApiError(FSI_E_TIMEOUT, "a bounded wait on the tensor core gave up");
   if (st[ST_TANGLED]) throw ApiError(FSI_E_MESH_TANGLED, "det F <= 0 at a quadrature point");
   if (st[ST_NONFINITE]) throw ApiError(FSI_E_NONFINITE, "non-finite values");
   if (st[ST_SINGULAR]) throw ApiError(FSI_E_SINGULAR, "zero or non-finite pivot in a Schwarz block or coarse LU");

@@ -183,6 +183,6 @@ struct Ctx {
 };
 
 // status flag slots
-enum { ST_SINGULAR = 0, ST_TANGLED = 1, ST_NONFINITE = 2, ST_COUNT = 4 };
+enum { ST_SINGULAR = 0, ST_TANGLED = 1, ST_NONFINITE = 2, ST_TIMEOUT = 3, ST_COUNT = 4 };
 
 }  // namespace fsi
