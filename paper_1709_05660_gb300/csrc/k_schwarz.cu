@@ -562,42 +562,48 @@ bool try_gj_f32(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, co
 // FP32 Gauss-Jordan with the trailing update on the tensor cores (tcgen05).
 //
 // Thread i owns row i of the block (n <= 1024).  A panel of W columns is
-// factored in registers: per pivot step every warp offers its best unused
-// row (largest |entry| of the pivot column) together with that row's panel
-// values in shared memory, every thread picks the same pivot from the 32
-// offers and updates its own row (one block barrier per step).  The rank-W
-// update of the whole matrix, M += (G - E_P) R with R the old pivot rows,
-// then runs as UMMAs: a 128 x N tile of M is loaded into tensor memory,
-// D += A B is issued with A = G - E_P (rows of the tile) and B = R (columns
-// of the tile) in K-major shared-memory layout, split into TF32 high and low
-// parts (A_hi B_hi + A_hi B_lo + A_lo B_hi: products at FP32 accuracy), and
-// the tile is written back except for the panel columns.  Requires
-// n % 4 == 0.  The wait on the tensor core is bounded; on time-out the block
-// records ST_TIMEOUT, stops issuing work and releases its tensor memory.
+// factored in registers: per pivot step every warp holding rows offers its
+// best unused row (largest |entry| of the pivot column) together with that
+// row's panel values in shared memory, and every thread picks the same pivot
+// from the 32 offers and updates its own row (one block barrier per step).
+// The rank-W update of the whole matrix, M += (G - E_P) R with R the old
+// pivot rows, then runs as UMMAs on 128 x N tiles of M loaded into tensor
+// memory: A = G - E_P is written by its row owners straight into tensor
+// memory (TF32 high and low parts), B = R sits in shared memory in K-major
+// layout (high and low parts), and D += A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (products at FP32 accuracy).  The tile is written back except for the
+// panel columns.  Tensor memory: D in columns [0, 256), the A parts of row
+// tile t at 256 + 2 W t.  Requires n % 4 == 0.  The wait on the tensor core is
+// bounded; on time-out the block records ST_TIMEOUT, stops issuing work and
+// releases its tensor memory.
 // ---------------------------------------------------------------------------
 template <int W>
 size_t gj_tc_smem(int max_n) {
-  const size_t n128 = ((size_t)max_n + 127) / 128 * 128, n16 = ((size_t)max_n + 15) / 16 * 16;
-  return (2 * n128 * W + 2 * n16 * W + 2 * 32 * (size_t)(W + 1)) * sizeof(float) + 2 * 32 * sizeof(int) +
+  const size_t n16 = ((size_t)max_n + 15) / 16 * 16;
+  return (2 * n16 * W + 2 * 32 * (size_t)W + 2 * 32) * sizeof(float) + 2 * 32 * sizeof(int) +
          2 * (size_t)max_n * sizeof(int) + (size_t)max_n + 64;
 }
+template <int W>
+__host__ __device__ constexpr int gj_tc_max_n() { return W == 32 ? 512 : 1024; }   // A parts of every row tile + D fit 512 columns
+template <int W>
+__host__ __device__ constexpr int gj_tc_threads() { return gj_tc_max_n<W>(); }   // one thread per row
 
 template <int W>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(gj_tc_threads<W>(), 1)
 k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
               const int64_t* __restrict__ dense_off, const int64_t* __restrict__ own_off,
               const int32_t* __restrict__ own, const int64_t* __restrict__ inv_off, float* __restrict__ dense,
               float* __restrict__ invT, int32_t* __restrict__ status, int max_n) {
   static_assert(W == 16 || W == 32, "panel width");
-  constexpr int OS = W + 1;   // offer record: |pivot candidate|, then the row's W panel values
+  constexpr int NWARP = gj_tc_threads<W>() / kWarp;   // 16 or 32 warps; thread i owns row i
+  constexpr int CGN = NWARP / 4;                       // 32-column groups of a D tile handled at once
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n128 = (max_n + 127) / 128 * 128, n16 = (max_n + 15) / 16 * 16;
-  float* Ahi = reinterpret_cast<float*>(smem_raw);        // n128 x W, K-major
-  float* Alo = Ahi + (size_t)n128 * W;
-  float* Bhi = Alo + (size_t)n128 * W;                      // n16 x W, K-major
+  const int n16 = (max_n + 15) / 16 * 16;
+  float* Bhi = reinterpret_cast<float*>(smem_raw);          // n16 x W, K-major
   float* Blo = Bhi + (size_t)n16 * W;
-  float* offer = Blo + (size_t)n16 * W;                     // [2][32][OS]
-  int* offer_i = reinterpret_cast<int*>(offer + 2 * 32 * OS);   // [2][32]
+  float* offer_row = Blo + (size_t)n16 * W;                 // [2][32][W] panel values of each warp's offer
+  float* offer_v = offer_row + 2 * 32 * W;                  // [2][32] |pivot candidate|
+  int* offer_i = reinterpret_cast<int*>(offer_v + 64);      // [2][32] its row
   int* piv = offer_i + 64;                                  // max_n
   int* qinv = piv + max_n;                                  // max_n
   uint8_t* live = reinterpret_cast<uint8_t*>(qinv + max_n);  // max_n
@@ -610,19 +616,17 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
   const int me = threadIdx.x;
   const bool has_row = me < n;
-  constexpr uint32_t kCols = 256;
+  const bool warp_rows = wid * kWarp < n;     // this warp owns at least one row
+  constexpr uint32_t kCols = 512, kD = 256;
   if (wid == 0) tc::tmem_alloc(&tslot, kCols);
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar, 1);
     s_sing = 0;
     s_abort = 0;
   }
-  // operand rows beyond n stay zero
-  for (int e = threadIdx.x; e < (n128 - n) * W; e += blockDim.x) {
-    const int r = n + e / W, k = e % W;
-    Ahi[tc::kmajor_off<W>(r, k)] = 0.f;
-    Alo[tc::kmajor_off<W>(r, k)] = 0.f;
-  }
+  if (lane == 0 && !warp_rows)
+    for (int h = 0; h < 2; ++h) { offer_v[h * 32 + wid] = -1.f; offer_i[h * 32 + wid] = -1; }
+  // B rows (matrix columns) beyond n stay zero
   for (int e = threadIdx.x; e < (n16 - n) * W; e += blockDim.x) {
     const int r = n + e / W, k = e % W;
     Bhi[tc::kmajor_off<W>(r, k)] = 0.f;
@@ -634,7 +638,7 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   const uint32_t tbase = tslot;
   uint32_t phase = 0;
   bool used = false;
-  const int q = wid % 4, cgi = wid / 4;   // TMEM lane quarter, 32-column group of a tile
+  const int q = wid % 4, cgi = wid / 4;   // TMEM lane quarter, first 32-column group of a D tile
   for (int k0 = 0; k0 < n; k0 += W) {
     const int wp = min(W, n - k0);
     float row[W];
@@ -645,8 +649,7 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
       row[4 * c4] = x.x; row[4 * c4 + 1] = x.y; row[4 * c4 + 2] = x.z; row[4 * c4 + 3] = x.w;
     }
     int my_step = -1;
-    // offers for column 0 of the panel
-    {
+    if (warp_rows) {   // offers for column 0 of the panel
       float a = (has_row && !used) ? fabsf(row[0]) : -1.f;
       if (!(a >= -1.f)) a = 0.f;   // NaN
       int ai = (has_row && !used) ? me : -1;
@@ -656,69 +659,85 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
         const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
         if (oi >= 0 && (ai < 0 || ov > a || (ov == a && oi < ai))) { a = ov; ai = oi; }
       }
-      if (lane == 0) { offer[wid * OS] = a; offer_i[wid] = ai; }
-      if (ai >= 0 && ai == me)
+      if (lane == 0) { offer_v[wid] = a; offer_i[wid] = ai; }
+      if (ai >= 0 && ai == me) {
+        float4* dst = reinterpret_cast<float4*>(offer_row + wid * W);
 #pragma unroll
-        for (int c = 0; c < W; ++c) offer[wid * OS + 1 + c] = row[c];
+        for (int c4 = 0; c4 < W / 4; ++c4)
+          dst[c4] = make_float4(row[4 * c4], row[4 * c4 + 1], row[4 * c4 + 2], row[4 * c4 + 3]);
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < W; ++m) {
       if (m >= wp) break;
       const int par = m & 1;
-      const float* of = offer + par * 32 * OS;
-      const int* oi_ = offer_i + par * 32;
-      // the same pivot in every warp: best of the 32 offers (ties: lowest row)
-      float bv = of[lane * OS];
-      int bi = oi_[lane], bw = lane;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
-        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; bw = ow; }
-      }
-      if (bi < 0) { bi = 0; bw = 0; }   // cannot happen while unused rows remain
-      const float* prow = of + bw * OS + 1;
-      float pv = prow[m];
-      if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
-        if (threadIdx.x == 0) s_sing = 1;
-        pv = 1.f;
-      }
-      const float rp = 1.f / pv;
-      if (has_row) {
-        if (me == bi) {
-#pragma unroll
-          for (int c = 0; c < W; ++c) row[c] = (c == m) ? rp : prow[c] * rp;
-          used = true;
-          my_step = m;
-        } else {
-          const float f = row[m] * rp;
-#pragma unroll
-          for (int c = 0; c < W; ++c) row[c] = (c == m) ? -f : row[c] - f * prow[c];
-        }
-      }
-      if (threadIdx.x == 0) piv[k0 + m] = bi;
-      if (m + 1 < wp) {
-        float* of2 = offer + (par ^ 1) * 32 * OS;
-        float a = (has_row && !used) ? fabsf(row[m + 1]) : -1.f;
-        if (!(a >= -1.f)) a = 0.f;
-        int ai = (has_row && !used) ? me : -1;
+      if (warp_rows) {
+        // the same pivot in every warp: best of the 32 offers (ties: lowest row)
+        float bv = lane < NWARP ? offer_v[par * 32 + lane] : -1.f;
+        int bi = lane < NWARP ? offer_i[par * 32 + lane] : -1, bw = lane;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, a, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
-          if (oi >= 0 && (ai < 0 || ov > a || (ov == a && oi < ai))) { a = ov; ai = oi; }
+          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+          if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; bw = ow; }
         }
-        if (lane == 0) { of2[wid * OS] = a; offer_i[(par ^ 1) * 32 + wid] = ai; }
-        if (ai >= 0 && ai == me)
+        if (bi < 0) { bi = 0; bw = 0; }   // cannot happen while unused rows remain
+        // pivot row read from shared memory four values at a time (few live registers)
+        const float4* src = reinterpret_cast<const float4*>(offer_row + (par * 32 + bw) * W);
+        float pv = offer_row[(par * 32 + bw) * W + m];
+        if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+          if (lane == 0) s_sing = 1;
+          pv = 1.f;
+        }
+        const float rp = 1.f / pv;
+        if (has_row) {
+          if (me == bi) {
 #pragma unroll
-          for (int c = 0; c < W; ++c) of2[wid * OS + 1 + c] = row[c];
+            for (int c4 = 0; c4 < W / 4; ++c4) {
+              const float4 x = src[c4];
+              const float pr4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) row[4 * c4 + e] = (4 * c4 + e == m) ? rp : pr4[e] * rp;
+            }
+            used = true;
+            my_step = m;
+          } else {
+            const float f = row[m] * rp;
+#pragma unroll
+            for (int c4 = 0; c4 < W / 4; ++c4) {
+              const float4 x = src[c4];
+              const float pr4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) row[4 * c4 + e] = (4 * c4 + e == m) ? -f : row[4 * c4 + e] - f * pr4[e];
+            }
+          }
+        }
+        if (threadIdx.x == 0) piv[k0 + m] = bi;
+        if (m + 1 < wp) {
+          float a = (has_row && !used) ? fabsf(row[m + 1]) : -1.f;
+          if (!(a >= -1.f)) a = 0.f;
+          int ai = (has_row && !used) ? me : -1;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, a, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
+            if (oi >= 0 && (ai < 0 || ov > a || (ov == a && oi < ai))) { a = ov; ai = oi; }
+          }
+          if (lane == 0) { offer_v[(par ^ 1) * 32 + wid] = a; offer_i[(par ^ 1) * 32 + wid] = ai; }
+          if (ai >= 0 && ai == me) {
+            float4* dst = reinterpret_cast<float4*>(offer_row + ((par ^ 1) * 32 + wid) * W);
+#pragma unroll
+            for (int c4 = 0; c4 < W / 4; ++c4)
+              dst[c4] = make_float4(row[4 * c4], row[4 * c4 + 1], row[4 * c4 + 2], row[4 * c4 + 3]);
+          }
+        }
       }
       __syncthreads();
     }
     // B = old pivot rows (k = panel column, row index = matrix column j)
-    for (int m = wid; m < W; m += kWarp) {
+    for (int m = wid; m < W; m += NWARP) {
       const float* Mp = m < wp ? M + (int64_t)piv[k0 + m] * n : nullptr;
       for (int j = lane; j < n; j += kWarp) {
         const float b = Mp ? Mp[j] : 0.f, hi = tc::to_tf32(b);
@@ -726,18 +745,27 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
         Blo[tc::kmajor_off<W>(j, m)] = b - hi;
       }
     }
-    // A = G - E_P from the thread's own row; live rows
-    if (has_row) {
+    // A = G - E_P from the thread's own row into tensor memory; live rows
+    const int n128 = (n + 127) / 128 * 128;
+    if (wid * kWarp < n128) {
       bool any = false;
+      const uint32_t col = kD + 2u * W * (uint32_t)(me / 128);
 #pragma unroll
-      for (int c = 0; c < W; ++c) {
-        const float a = c < wp ? (c == my_step ? row[c] - 1.f : row[c]) : 0.f;
-        any |= a != 0.f;
-        const float hi = tc::to_tf32(a);
-        Ahi[tc::kmajor_off<W>(me, c)] = hi;
-        Alo[tc::kmajor_off<W>(me, c)] = a - hi;
+      for (int h = 0; h < W / 16; ++h) {   // 16 columns at a time: hi part, then lo part
+        float ahi[16], alo[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int cc = 16 * h + c;
+          const float a = (has_row && cc < wp) ? (cc == my_step ? row[cc] - 1.f : row[cc]) : 0.f;
+          any |= a != 0.f;
+          ahi[c] = tc::to_tf32(a);
+          alo[c] = a - ahi[c];
+        }
+        tc::tmem_st16(tc::taddr(tbase, 32 * q, col + 16 * h), ahi);
+        tc::tmem_st16(tc::taddr(tbase, 32 * q, col + W + 16 * h), alo);
       }
-      live[me] = any;
+      tc::tmem_wait_st();
+      if (has_row) live[me] = any;
     }
     __syncthreads();   // every B read of the old pivot rows precedes the write-back
     if (has_row) {
@@ -753,20 +781,23 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
     tc::fence_after_sync();
     // trailing update, one 128 x nt tile at a time
     for (int i0 = 0; i0 < n; i0 += 128) {
-      for (int j0 = 0; j0 < n; j0 += (int)kCols) {
-        const int nt = min((int)kCols, (n - j0 + 15) / 16 * 16);
+      const bool qrows = i0 + 32 * q < n;    // this warp's lane quarter holds rows of the block
+      for (int j0 = 0; j0 < n; j0 += (int)kD) {
+        const int nt = min((int)kD, (n - j0 + 15) / 16 * 16);
         const int r = i0 + 32 * q + lane;
-        const int cb = j0 + 32 * cgi;
         const bool rl = r < n && live[r];
-        if (32 * cgi < nt) {
-          float v[32];
+        if (qrows) {
+          for (int cg = cgi; 32 * cg < nt; cg += CGN) {
+            const int cb = j0 + 32 * cg;
+            float v[32];
 #pragma unroll
-          for (int c4 = 0; c4 < 8; ++c4) {
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rl && cb + 4 * c4 < n) x = *reinterpret_cast<const float4*>(M + (int64_t)r * n + cb + 4 * c4);
-            v[4 * c4] = x.x; v[4 * c4 + 1] = x.y; v[4 * c4 + 2] = x.z; v[4 * c4 + 3] = x.w;
+            for (int c4 = 0; c4 < 8; ++c4) {
+              float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (rl && cb + 4 * c4 < n) x = *reinterpret_cast<const float4*>(M + (int64_t)r * n + cb + 4 * c4);
+              v[4 * c4] = x.x; v[4 * c4 + 1] = x.y; v[4 * c4 + 2] = x.z; v[4 * c4 + 3] = x.w;
+            }
+            tc::tmem_st32(tc::taddr(tbase, 32 * q, 32 * cg), v);
           }
-          tc::tmem_st32(tc::taddr(tbase, 32 * q, 32 * cgi), v);
           tc::tmem_wait_st();
         }
         tc::fence_before_sync();
@@ -775,16 +806,15 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
           tc::fence_after_sync();
           const uint32_t id = tc::idesc_tf32(128, nt);
           const uint32_t lbo = tc::kmajor_lbo<W>(), sbo = tc::kmajor_sbo<W>();
-          const uint32_t a0 = tc::smem_u32(Ahi) + (uint32_t)(i0 / 8) * sbo;
-          const uint32_t a1 = tc::smem_u32(Alo) + (uint32_t)(i0 / 8) * sbo;
+          const uint32_t ahi = tbase + kD + 2u * W * (uint32_t)(i0 / 128), alo = ahi + W;
           const uint32_t b0 = tc::smem_u32(Bhi) + (uint32_t)(j0 / 8) * sbo;
           const uint32_t b1 = tc::smem_u32(Blo) + (uint32_t)(j0 / 8) * sbo;
 #pragma unroll
-          for (int st8 = 0; st8 < W / 8; ++st8) {
-            const uint32_t ko = 256u * st8;   // two core matrices (8 k-values) per UMMA
-            tc::mma_tf32(tbase, tc::smem_desc(a1 + ko, lbo, sbo), tc::smem_desc(b0 + ko, lbo, sbo), id, 1);
-            tc::mma_tf32(tbase, tc::smem_desc(a0 + ko, lbo, sbo), tc::smem_desc(b1 + ko, lbo, sbo), id, 1);
-            tc::mma_tf32(tbase, tc::smem_desc(a0 + ko, lbo, sbo), tc::smem_desc(b0 + ko, lbo, sbo), id, 1);
+          for (int s8 = 0; s8 < W / 8; ++s8) {
+            const uint32_t ko = 256u * s8;   // two core matrices (8 k-values) of B per UMMA
+            tc::mma_tf32_ts(tbase, alo + 8 * s8, tc::smem_desc(b0 + ko, lbo, sbo), id, 1);
+            tc::mma_tf32_ts(tbase, ahi + 8 * s8, tc::smem_desc(b1 + ko, lbo, sbo), id, 1);
+            tc::mma_tf32_ts(tbase, ahi + 8 * s8, tc::smem_desc(b0 + ko, lbo, sbo), id, 1);
           }
           tc::commit(&mbar);
           // one thread waits; the others rest at the barrier below
@@ -794,17 +824,20 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
         __syncthreads();
         if (s_abort) goto done;
         tc::fence_after_sync();
-        if (32 * cgi < nt) {
-          float v[32];
-          tc::tmem_ld32(tc::taddr(tbase, 32 * q, 32 * cgi), v);
-          tc::tmem_wait_ld();
-          if (rl) {
+        if (qrows) {
+          for (int cg = cgi; 32 * cg < nt; cg += CGN) {
+            const int cb = j0 + 32 * cg;
+            float v[32];
+            tc::tmem_ld32(tc::taddr(tbase, 32 * q, 32 * cg), v);
+            tc::tmem_wait_ld();
+            if (rl) {
 #pragma unroll
-            for (int c4 = 0; c4 < 8; ++c4) {
-              const int j = cb + 4 * c4;
-              if (j < n && !(j >= k0 && j < k0 + wp))
-                *reinterpret_cast<float4*>(M + (int64_t)r * n + j) =
-                    make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+              for (int c4 = 0; c4 < 8; ++c4) {
+                const int j = cb + 4 * c4;
+                if (j < n && !(j >= k0 && j < k0 + wp))
+                  *reinterpret_cast<float4*>(M + (int64_t)r * n + j) =
+                      make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+              }
             }
           }
         }
@@ -816,7 +849,7 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
   __syncthreads();
   {
-    float* tile = Ahi;   // 32 x 33 (the A operand is free now)
+    float* tile = Bhi;   // 32 x 33 (the B operand is free now; 2 n16 W >= 2048 floats)
     const int nown = p_nown[p];
     const int32_t* ow = own + own_off[p];
     float* out = invT + inv_off[p];
@@ -857,10 +890,10 @@ bool try_gj_tc(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, con
                const int64_t* own_off, const int32_t* own, const int64_t* inv_off, float* dense, float* invT,
                int32_t* status, cudaStream_t st) {
   const size_t smem = gj_tc_smem<W>(max_n);
-  if (smem > 225 * 1024 || max_n % 4 != 0 || max_n > 1024 || max_n < 64) return false;
+  if (smem > 225 * 1024 || max_n % 4 != 0 || max_n > gj_tc_max_n<W>() || max_n < 64) return false;
   cudaFuncSetAttribute(k_patch_gj_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_patch_gj_tc<W><<<np, 1024, smem, st>>>(p_n, p_nown, dense_off, own_off, own, inv_off, dense, invT, status,
-                                           max_n);
+  k_patch_gj_tc<W><<<np, gj_tc_threads<W>(), smem, st>>>(p_n, p_nown, dense_off, own_off, own, inv_off, dense,
+                                                         invT, status, max_n);
   return true;
 }
 
