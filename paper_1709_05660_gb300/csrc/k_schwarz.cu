@@ -562,31 +562,44 @@ bool try_gj_f32(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, co
 // FP32 Gauss-Jordan with the trailing update on the tensor cores (tcgen05).
 //
 // Thread i owns row i of the block (n <= 1024).  A panel of W columns is
-// factored in registers: per pivot step every warp holding rows offers its
-// best unused row (largest |entry| of the pivot column) together with that
-// row's panel values in shared memory, and every thread picks the same pivot
-// from the 32 offers and updates its own row (one block barrier per step).
+// factored in registers.  Pivot choice per step: every warp holding rows
+// offers its best unused row as a 32-bit key (|entry| with the 10 low
+// mantissa bits replaced by 1023 - row, so one integer max-reduction picks
+// the largest magnitude, ties to the lowest row) and stores that row's panel
+// values in shared memory; every thread reduces the 32 keys to the same
+// pivot and updates its own row (one block barrier per step).
 // The rank-W update of the whole matrix, M += (G - E_P) R with R the old
-// pivot rows, then runs as UMMAs on 128 x N tiles of M loaded into tensor
-// memory: A = G - E_P is written by its row owners straight into tensor
-// memory (TF32 high and low parts), B = R sits in shared memory in K-major
-// layout (high and low parts), and D += A_hi B_hi + A_hi B_lo + A_lo B_hi
-// (products at FP32 accuracy).  The tile is written back except for the
-// panel columns.  Tensor memory: D in columns [0, 256), the A parts of row
-// tile t at 256 + 2 W t.  Requires n % 4 == 0.  The wait on the tensor core is
+// pivot rows, runs as UMMAs on 128 x 128 tiles: A = G - E_P is written by its
+// row owners straight into tensor memory (TF32 high and low parts), B = R
+// sits in shared memory in K-major layout (high and low parts), and
+// D = A_lo B_hi + A_hi B_lo + A_hi B_hi (products at FP32 accuracy) goes to
+// one of two accumulators, so the UMMAs of tile t + 1 run while tile t is
+// added to M: D is staged through shared memory and each warp adds whole
+// rows of it to M with coalesced loads and stores (panel columns excluded).
+// Tensor memory: accumulators in columns [0, 256), the A parts of row tile t
+// at 256 + 2 W t.  Requires n % 4 == 0.  The waits on the tensor core are
 // bounded; on time-out the block records ST_TIMEOUT, stops issuing work and
 // releases its tensor memory.
 // ---------------------------------------------------------------------------
 template <int W>
-size_t gj_tc_smem(int max_n) {
-  const size_t n16 = ((size_t)max_n + 15) / 16 * 16;
-  return (2 * n16 * W + 2 * 32 * (size_t)W + 2 * 32) * sizeof(float) + 2 * 32 * sizeof(int) +
-         2 * (size_t)max_n * sizeof(int) + (size_t)max_n + 64;
-}
-template <int W>
-__host__ __device__ constexpr int gj_tc_max_n() { return W == 32 ? 512 : 1024; }   // A parts of every row tile + D fit 512 columns
+__host__ __device__ constexpr int gj_tc_max_n() { return W == 32 ? 512 : 1024; }   // A parts + accumulators fit 512 columns
 template <int W>
 __host__ __device__ constexpr int gj_tc_threads() { return gj_tc_max_n<W>(); }   // one thread per row
+constexpr int kStage = 129;   // row stride of the staged accumulator tile (conflict-free banks)
+
+template <int W>
+size_t gj_tc_smem(int max_n) {
+  const size_t n16 = ((size_t)max_n + 15) / 16 * 16;
+  return (2 * n16 * W + 2 * 32 * (size_t)W + 128 * (size_t)kStage) * sizeof(float) + 2 * 32 * sizeof(uint32_t) +
+         2 * (size_t)max_n * sizeof(int) + (size_t)max_n + 64;
+}
+
+// pivot key: larger |a| wins, ties to the lower row; 0 = no candidate
+__device__ __forceinline__ uint32_t piv_key(float a, int row) {
+  uint32_t b = __float_as_uint(fabsf(a));
+  if (!(fabsf(a) <= 3.402823466e38f)) b = 0u;   // NaN / Inf never win
+  return (b & ~0x3FFu) | (uint32_t)(1023 - row);
+}
 
 template <int W>
 __global__ void __launch_bounds__(gj_tc_threads<W>(), 1)
@@ -595,19 +608,20 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
               const int32_t* __restrict__ own, const int64_t* __restrict__ inv_off, float* __restrict__ dense,
               float* __restrict__ invT, int32_t* __restrict__ status, int max_n) {
   static_assert(W == 16 || W == 32, "panel width");
-  constexpr int NWARP = gj_tc_threads<W>() / kWarp;   // 16 or 32 warps; thread i owns row i
-  constexpr int CGN = NWARP / 4;                       // 32-column groups of a D tile handled at once
+  constexpr int NWARP = gj_tc_threads<W>() / kWarp;   // 16 or 32 warps
+  constexpr int CGN = NWARP / 4;                       // column chunks of a tile per lane quarter
+  constexpr int CW = 128 / CGN;                        // chunk width: 32 (512 threads) or 16 (1024)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n16 = (max_n + 15) / 16 * 16;
   float* Bhi = reinterpret_cast<float*>(smem_raw);          // n16 x W, K-major
   float* Blo = Bhi + (size_t)n16 * W;
   float* offer_row = Blo + (size_t)n16 * W;                 // [2][32][W] panel values of each warp's offer
-  float* offer_v = offer_row + 2 * 32 * W;                  // [2][32] |pivot candidate|
-  int* offer_i = reinterpret_cast<int*>(offer_v + 64);      // [2][32] its row
-  int* piv = offer_i + 64;                                  // max_n
+  float* stage = offer_row + 2 * 32 * W;                    // 128 x kStage accumulator tile
+  uint32_t* offer_key = reinterpret_cast<uint32_t*>(stage + 128 * kStage);   // [2][32]
+  int* piv = reinterpret_cast<int*>(offer_key + 64);        // max_n
   int* qinv = piv + max_n;                                  // max_n
   uint8_t* live = reinterpret_cast<uint8_t*>(qinv + max_n);  // max_n
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar2[2];
   __shared__ uint32_t tslot;
   __shared__ int s_sing, s_abort;
   const int p = blockIdx.x;
@@ -620,12 +634,13 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   constexpr uint32_t kCols = 512, kD = 256;
   if (wid == 0) tc::tmem_alloc(&tslot, kCols);
   if (threadIdx.x == 0) {
-    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mbar2[0], 1);
+    tc::mbar_init(&mbar2[1], 1);
     s_sing = 0;
     s_abort = 0;
   }
-  if (lane == 0 && !warp_rows)
-    for (int h = 0; h < 2; ++h) { offer_v[h * 32 + wid] = -1.f; offer_i[h * 32 + wid] = -1; }
+  if (lane == 0 && !warp_rows) { offer_key[wid] = 0u; offer_key[32 + wid] = 0u; }
+  for (int w = NWARP + threadIdx.x; w < 32; w += blockDim.x) { offer_key[w] = 0u; offer_key[32 + w] = 0u; }
   // B rows (matrix columns) beyond n stay zero
   for (int e = threadIdx.x; e < (n16 - n) * W; e += blockDim.x) {
     const int r = n + e / W, k = e % W;
@@ -636,9 +651,9 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tslot;
-  uint32_t phase = 0;
+  uint32_t bphase = 0;   // bit b: phase of accumulator b's barrier
   bool used = false;
-  const int q = wid % 4, cgi = wid / 4;   // TMEM lane quarter, first 32-column group of a D tile
+  const int q = wid % 4, cgi = wid / 4;   // TMEM lane quarter, first column chunk of a tile
   for (int k0 = 0; k0 < n; k0 += W) {
     const int wp = min(W, n - k0);
     float row[W];
@@ -650,17 +665,10 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
     }
     int my_step = -1;
     if (warp_rows) {   // offers for column 0 of the panel
-      float a = (has_row && !used) ? fabsf(row[0]) : -1.f;
-      if (!(a >= -1.f)) a = 0.f;   // NaN
-      int ai = (has_row && !used) ? me : -1;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, a, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
-        if (oi >= 0 && (ai < 0 || ov > a || (ov == a && oi < ai))) { a = ov; ai = oi; }
-      }
-      if (lane == 0) { offer_v[wid] = a; offer_i[wid] = ai; }
-      if (ai >= 0 && ai == me) {
+      const uint32_t key = (has_row && !used) ? piv_key(row[0], me) : 0u;
+      const uint32_t best = __reduce_max_sync(0xffffffffu, key);
+      if (lane == 0) offer_key[wid] = best;
+      if (best != 0u && key == best) {
         float4* dst = reinterpret_cast<float4*>(offer_row + wid * W);
 #pragma unroll
         for (int c4 = 0; c4 < W / 4; ++c4)
@@ -673,21 +681,13 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
       if (m >= wp) break;
       const int par = m & 1;
       if (warp_rows) {
-        // the same pivot in every warp: best of the 32 offers (ties: lowest row)
-        float bv = lane < NWARP ? offer_v[par * 32 + lane] : -1.f;
-        int bi = lane < NWARP ? offer_i[par * 32 + lane] : -1, bw = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
-          if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; bw = ow; }
-        }
-        if (bi < 0) { bi = 0; bw = 0; }   // cannot happen while unused rows remain
-        // pivot row read from shared memory four values at a time (few live registers)
-        const float4* src = reinterpret_cast<const float4*>(offer_row + (par * 32 + bw) * W);
-        float pv = offer_row[(par * 32 + bw) * W + m];
-        if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+        // the same pivot in every warp: the largest of the 32 offered keys
+        const uint32_t best = __reduce_max_sync(0xffffffffu, offer_key[par * 32 + lane]);
+        const int bi = best != 0u ? 1023 - (int)(best & 0x3FFu) : 0;   // a row of warp bi / 32
+        const float* prow_s = offer_row + (par * 32 + bi / kWarp) * W;
+        const float4* src = reinterpret_cast<const float4*>(prow_s);
+        float pv = prow_s[m];
+        if (best == 0u || !(fabsf(pv) > 0.f) || !isfinite(pv)) {
           if (lane == 0) s_sing = 1;
           pv = 1.f;
         }
@@ -716,17 +716,10 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
         }
         if (threadIdx.x == 0) piv[k0 + m] = bi;
         if (m + 1 < wp) {
-          float a = (has_row && !used) ? fabsf(row[m + 1]) : -1.f;
-          if (!(a >= -1.f)) a = 0.f;
-          int ai = (has_row && !used) ? me : -1;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, a, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
-            if (oi >= 0 && (ai < 0 || ov > a || (ov == a && oi < ai))) { a = ov; ai = oi; }
-          }
-          if (lane == 0) { offer_v[(par ^ 1) * 32 + wid] = a; offer_i[(par ^ 1) * 32 + wid] = ai; }
-          if (ai >= 0 && ai == me) {
+          const uint32_t key = (has_row && !used) ? piv_key(row[m + 1], me) : 0u;
+          const uint32_t wbest = __reduce_max_sync(0xffffffffu, key);
+          if (lane == 0) offer_key[(par ^ 1) * 32 + wid] = wbest;
+          if (wbest != 0u && key == wbest) {
             float4* dst = reinterpret_cast<float4*>(offer_row + ((par ^ 1) * 32 + wid) * W);
 #pragma unroll
             for (int c4 = 0; c4 < W / 4; ++c4)
@@ -739,10 +732,22 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
     // B = old pivot rows (k = panel column, row index = matrix column j)
     for (int m = wid; m < W; m += NWARP) {
       const float* Mp = m < wp ? M + (int64_t)piv[k0 + m] * n : nullptr;
-      for (int j = lane; j < n; j += kWarp) {
-        const float b = Mp ? Mp[j] : 0.f, hi = tc::to_tf32(b);
-        Bhi[tc::kmajor_off<W>(j, m)] = hi;
-        Blo[tc::kmajor_off<W>(j, m)] = b - hi;
+      for (int j0 = 0; j0 < n; j0 += 4 * kWarp) {   // four loads in flight per lane
+        float b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * kWarp + lane;
+          b[u] = (Mp && j < n) ? Mp[j] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * kWarp + lane;
+          if (j < n) {
+            const float hi = tc::to_tf32(b[u]);
+            Bhi[tc::kmajor_off<W>(j, m)] = hi;
+            Blo[tc::kmajor_off<W>(j, m)] = b[u] - hi;
+          }
+        }
       }
     }
     // A = G - E_P from the thread's own row into tensor memory; live rows
@@ -779,69 +784,87 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    // trailing update, one 128 x nt tile at a time
-    for (int i0 = 0; i0 < n; i0 += 128) {
-      const bool qrows = i0 + 32 * q < n;    // this warp's lane quarter holds rows of the block
-      for (int j0 = 0; j0 < n; j0 += (int)kD) {
-        const int nt = min((int)kD, (n - j0 + 15) / 16 * 16);
-        const int r = i0 + 32 * q + lane;
-        const bool rl = r < n && live[r];
-        if (qrows) {
-          for (int cg = cgi; 32 * cg < nt; cg += CGN) {
-            const int cb = j0 + 32 * cg;
-            float v[32];
+    // trailing update: tile t's UMMAs into accumulator t % 2, issued one tile
+    // ahead of the epilogue that adds the previous tile to M
+    {
+      const int ntc = (n + 127) / 128, ntiles = ntc * ntc;
+      auto issue = [&](int t) {
+        const int i0 = (t / ntc) * 128, j0 = (t % ntc) * 128, b = t & 1;
+        const int nt = min(128, (n - j0 + 15) / 16 * 16);
+        const uint32_t id = tc::idesc_tf32(128, nt);
+        const uint32_t lbo = tc::kmajor_lbo<W>(), sbo = tc::kmajor_sbo<W>();
+        const uint32_t ahi = tbase + kD + 2u * W * (uint32_t)(i0 / 128), alo = ahi + W;
+        const uint32_t b0 = tc::smem_u32(Bhi) + (uint32_t)(j0 / 8) * sbo;
+        const uint32_t b1 = tc::smem_u32(Blo) + (uint32_t)(j0 / 8) * sbo;
+        const uint32_t d = tbase + 128u * b;
 #pragma unroll
-            for (int c4 = 0; c4 < 8; ++c4) {
-              float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (rl && cb + 4 * c4 < n) x = *reinterpret_cast<const float4*>(M + (int64_t)r * n + cb + 4 * c4);
-              v[4 * c4] = x.x; v[4 * c4 + 1] = x.y; v[4 * c4 + 2] = x.z; v[4 * c4 + 3] = x.w;
-            }
-            tc::tmem_st32(tc::taddr(tbase, 32 * q, 32 * cg), v);
-          }
-          tc::tmem_wait_st();
+        for (int s8 = 0; s8 < W / 8; ++s8) {
+          const uint32_t ko = 256u * s8;   // two core matrices (8 k-values) of B per UMMA
+          tc::mma_tf32_ts(d, alo + 8 * s8, tc::smem_desc(b0 + ko, lbo, sbo), id, s8 > 0);
+          tc::mma_tf32_ts(d, ahi + 8 * s8, tc::smem_desc(b1 + ko, lbo, sbo), id, 1);
+          tc::mma_tf32_ts(d, ahi + 8 * s8, tc::smem_desc(b0 + ko, lbo, sbo), id, 1);
         }
-        tc::fence_before_sync();
-        __syncthreads();
+        tc::commit(&mbar2[b]);
+      };
+      if (threadIdx.x == 0) issue(0);
+      for (int t = 0; t < ntiles; ++t) {
+        const int i0 = (t / ntc) * 128, j0 = (t % ntc) * 128, b = t & 1;
+        const int nt = min(128, (n - j0 + 15) / 16 * 16);
         if (threadIdx.x == 0) {
           tc::fence_after_sync();
-          const uint32_t id = tc::idesc_tf32(128, nt);
-          const uint32_t lbo = tc::kmajor_lbo<W>(), sbo = tc::kmajor_sbo<W>();
-          const uint32_t ahi = tbase + kD + 2u * W * (uint32_t)(i0 / 128), alo = ahi + W;
-          const uint32_t b0 = tc::smem_u32(Bhi) + (uint32_t)(j0 / 8) * sbo;
-          const uint32_t b1 = tc::smem_u32(Blo) + (uint32_t)(j0 / 8) * sbo;
-#pragma unroll
-          for (int s8 = 0; s8 < W / 8; ++s8) {
-            const uint32_t ko = 256u * s8;   // two core matrices (8 k-values) of B per UMMA
-            tc::mma_tf32_ts(tbase, alo + 8 * s8, tc::smem_desc(b0 + ko, lbo, sbo), id, 1);
-            tc::mma_tf32_ts(tbase, ahi + 8 * s8, tc::smem_desc(b1 + ko, lbo, sbo), id, 1);
-            tc::mma_tf32_ts(tbase, ahi + 8 * s8, tc::smem_desc(b0 + ko, lbo, sbo), id, 1);
+          if (t + 1 < ntiles) issue(t + 1);   // its accumulator was drained in iteration t - 1
+          if (!tc::mbar_wait(&mbar2[b], (bphase >> b) & 1u, 1LL << 22)) {
+            // one more bounded wait for tile t and for tile t + 1 before the
+            // tensor memory is released
+            tc::mbar_wait(&mbar2[b], (bphase >> b) & 1u, 1LL << 22);
+            if (t + 1 < ntiles) tc::mbar_wait(&mbar2[b ^ 1], (bphase >> (b ^ 1)) & 1u, 1LL << 22);
+            s_abort = 1;
           }
-          tc::commit(&mbar);
-          // one thread waits; the others rest at the barrier below
-          if (!tc::mbar_wait(&mbar, phase, 1LL << 22)) s_abort = 1;
         }
-        phase ^= 1u;
+        bphase ^= 1u << b;
         __syncthreads();
         if (s_abort) goto done;
         tc::fence_after_sync();
-        if (qrows) {
-          for (int cg = cgi; 32 * cg < nt; cg += CGN) {
-            const int cb = j0 + 32 * cg;
-            float v[32];
-            tc::tmem_ld32(tc::taddr(tbase, 32 * q, 32 * cg), v);
+        // accumulator -> shared memory (thread = tile row)
+        if (i0 + 32 * q < n) {
+          for (int cg = cgi; cg * CW < nt; cg += CGN) {
+            float v[CW];
+            tc::tmem_ld<CW>(tc::taddr(tbase, 32 * q, 128u * b + cg * CW), v);
             tc::tmem_wait_ld();
-            if (rl) {
+            float* srow = stage + (32 * q + lane) * kStage + cg * CW;
 #pragma unroll
-              for (int c4 = 0; c4 < 8; ++c4) {
-                const int j = cb + 4 * c4;
-                if (j < n && !(j >= k0 && j < k0 + wp))
-                  *reinterpret_cast<float4*>(M + (int64_t)r * n + j) =
-                      make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
-              }
-            }
+            for (int c = 0; c < CW; ++c) srow[c] = v[c];
           }
         }
         tc::fence_before_sync();
+        __syncthreads();
+        // M += D for live rows, panel columns excluded: lane l adds columns
+        // l, l + 32, l + 64, l + 96 of a row (coalesced)
+        {
+          constexpr int RPW = 128 / NWARP;   // rows per warp; all their loads in flight at once
+          float old[RPW][4];
+#pragma unroll
+          for (int k = 0; k < RPW; ++k) {
+            const int rr = wid + NWARP * k, r = i0 + rr;
+            const bool ok = r < n && live[r];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int c = lane + 32 * e, j = j0 + c;
+              old[k][e] = (ok && c < nt && j < n) ? M[(int64_t)r * n + j] : 0.f;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < RPW; ++k) {
+            const int rr = wid + NWARP * k, r = i0 + rr;
+            if (!(r < n && live[r])) continue;
+            const float* srow = stage + rr * kStage;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int c = lane + 32 * e, j = j0 + c;
+              if (c < nt && j < n && !(j >= k0 && j < k0 + wp)) M[(int64_t)r * n + j] = old[k][e] + srow[c];
+            }
+          }
+        }
       }
     }
     __syncthreads();
@@ -849,37 +872,34 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
   __syncthreads();
   {
-    float* tile = Bhi;   // 32 x 33 (the B operand is free now; 2 n16 W >= 2048 floats)
-    const int nown = p_nown[p];
+    // owned rows of the inverse, transposed: out[c][o] = Binv[own[o]][c]; o is
+    // the fastest index (coalesced writes), reads hit rows of M just written
+    const int nown = p_nown[p], opad = own_pad(nown);
     const int32_t* ow = own + own_off[p];
     float* out = invT + inv_off[p];
-    for (int o0 = 0; o0 < own_pad(nown); o0 += 32) {
-      for (int c0 = 0; c0 < n; c0 += 32) {
-        for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-          const int oo = t / 32, cc = t % 32;
-          const int o = o0 + oo, c = c0 + cc;
-          if (o < nown && c < n) tile[oo * 33 + cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-          const int cc = t / 32, oo = t % 32;
-          const int o = o0 + oo, c = c0 + cc;
-          if (o < own_pad(nown) && c < n) out[(int64_t)c * own_pad(nown) + o] = o < nown ? tile[oo * 33 + cc] : 0.f;
-        }
-        __syncthreads();
+    int* roff = reinterpret_cast<int*>(stage);   // row offset of B^{-1} row own[o] in M
+    for (int o = threadIdx.x; o < nown; o += blockDim.x) roff[o] = piv[ow[o]] * n;
+    __syncthreads();
+    const int tot = n * opad;
+    for (int t0 = threadIdx.x; t0 < tot; t0 += 4 * (int)blockDim.x) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * blockDim.x;
+        const int c = t / opad, o = t - c * opad;
+        v[u] = (t < tot && o < nown) ? M[roff[o] + qinv[c]] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < tot) out[t] = v[u];
       }
     }
   }
 done:
   tc::fence_before_sync();
   __syncthreads();
-  if (s_abort && threadIdx.x == 0) {
-    // let the tensor core finish what was issued before its memory is released
-    // (phase was advanced past the wait that gave up)
-    tc::mbar_wait(&mbar, phase ^ 1u, 1LL << 22);
-    atomicExch(&status[ST_TIMEOUT], 1);
-  }
-  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicExch(&status[ST_TIMEOUT], 1);
   tc::fence_after_sync();
   if (wid == 0) tc::tmem_dealloc(tbase, kCols);
   if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
