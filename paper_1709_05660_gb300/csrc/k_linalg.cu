@@ -83,30 +83,6 @@ __device__ __forceinline__ TA block_row_dot(const TV* __restrict__ v, const TX* 
   for (int c = 0; c < B; ++c) acc += TA(v[c]) * TA(xb[c]);
   return acc;
 }
-template <>
-__device__ __forceinline__ double block_row_dot<4, double, double, double>(const double* __restrict__ v,
-                                                                          const double* __restrict__ xb) {
-  const double2 a0 = __ldg(reinterpret_cast<const double2*>(v));
-  const double2 a1 = __ldg(reinterpret_cast<const double2*>(v + 2));
-  const double2 x0 = __ldg(reinterpret_cast<const double2*>(xb));
-  const double2 x1 = __ldg(reinterpret_cast<const double2*>(xb + 2));
-  return a0.x * x0.x + a0.y * x0.y + a1.x * x1.x + a1.y * x1.y;
-}
-template <>
-__device__ __forceinline__ float block_row_dot<4, float, float, float>(const float* __restrict__ v,
-                                                                      const float* __restrict__ xb) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(v));
-  const float4 x = __ldg(reinterpret_cast<const float4*>(xb));
-  return a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
-}
-template <>
-__device__ __forceinline__ double block_row_dot<4, double, float, double>(const double* __restrict__ v,
-                                                                         const float* __restrict__ xb) {
-  const double2 a0 = __ldg(reinterpret_cast<const double2*>(v));
-  const double2 a1 = __ldg(reinterpret_cast<const double2*>(v + 2));
-  const float4 x = __ldg(reinterpret_cast<const float4*>(xb));
-  return a0.x * (double)x.x + a0.y * (double)x.y + a1.x * (double)x.z + a1.y * (double)x.w;
-}
 }  // namespace
 
 template <int B, typename TV, typename TX, typename TY>
@@ -130,11 +106,89 @@ __global__ void k_bsr_residual(int64_t nb, const int32_t* __restrict__ rowptr, c
   y[i] = b ? b[i] - acc : acc;
 }
 
+// B = 4 variant with SUB threads per scalar row: thread sub takes blocks
+// rowptr + sub, rowptr + sub + SUB, ... in rounds of four; a round issues the
+// column, value and vector loads of its four blocks before any product, so
+// one thread keeps up to 12 loads in flight instead of a dependent chain per
+// block.  The partial sums are combined with warp shuffles (sub is the
+// fastest index, so a row's threads are adjacent lanes); a warp reads
+// consecutive blocks of two block-rows (coalesced).
+template <typename TV> struct BlkRow;
+template <> struct BlkRow<double> {   // one row of a 4 x 4 FP64 block
+  double2 a, b;
+  __device__ __forceinline__ void load(const double* p) {
+    a = __ldg(reinterpret_cast<const double2*>(p));
+    b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  }
+  __device__ __forceinline__ void zero() { a = make_double2(0.0, 0.0); b = a; }
+  template <typename TY> __device__ __forceinline__ TY dot(const TY (&x)[4]) const {
+    return TY(a.x) * x[0] + TY(a.y) * x[1] + TY(b.x) * x[2] + TY(b.y) * x[3];
+  }
+};
+template <> struct BlkRow<float> {
+  float4 a;
+  __device__ __forceinline__ void load(const float* p) { a = __ldg(reinterpret_cast<const float4*>(p)); }
+  __device__ __forceinline__ void zero() { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+  template <typename TY> __device__ __forceinline__ TY dot(const TY (&x)[4]) const {
+    return TY(a.x) * x[0] + TY(a.y) * x[1] + TY(a.z) * x[2] + TY(a.w) * x[3];
+  }
+};
+template <typename TX, typename TY>
+__device__ __forceinline__ void load_x4(const TX* p, TY (&x)[4]) {
+  if constexpr (sizeof(TX) == 8) {
+    const double2 u = __ldg(reinterpret_cast<const double2*>(p)), v = __ldg(reinterpret_cast<const double2*>(p + 2));
+    x[0] = TY(u.x); x[1] = TY(u.y); x[2] = TY(v.x); x[3] = TY(v.y);
+  } else {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    x[0] = TY(u.x); x[1] = TY(u.y); x[2] = TY(u.z); x[3] = TY(u.w);
+  }
+}
+
+template <int SUB, typename TV, typename TX, typename TY>
+__global__ void __launch_bounds__(256) k_bsr4_residual_sub(int64_t nb, const int32_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                                          const TX* __restrict__ x, const TY* __restrict__ b,
+                                                          TY* __restrict__ y) {
+  constexpr int B = 4, R = 4;   // blocks per thread and round
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / SUB;
+  const int sub = (int)(t % SUB);
+  TY acc = TY(0);
+  if (i < nb * B) {
+    const int64_t br = i / B;
+    const int ci = (int)(i % B);
+    const int32_t k0 = rowptr[br], k1 = rowptr[br + 1];
+    for (int32_t kb = k0 + sub; kb < k1; kb += R * SUB) {
+      int32_t c[R];
+      BlkRow<TV> v[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const int32_t k = kb + u * SUB;
+        c[u] = k < k1 ? __ldg(col + k) : -1;
+        if (k < k1) v[u].load(val + (int64_t)k * B * B + ci * B);
+        else v[u].zero();
+      }
+      TY xv[R][4];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        if (c[u] >= 0) load_x4<TX, TY>(x + (int64_t)c[u] * B, xv[u]);
+        else xv[u][0] = xv[u][1] = xv[u][2] = xv[u][3] = TY(0);
+      }
+#pragma unroll
+      for (int u = 0; u < R; ++u) acc += v[u].template dot<TY>(xv[u]);
+    }
+  }
+#pragma unroll
+  for (int o = SUB / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (sub == 0 && i < nb * B) y[i] = b ? b[i] - acc : acc;
+}
+
 void launch_bsr_residual(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const double* x, const double* b, double* y, cudaStream_t st) {
   const int64_t n = nb * B;
   const unsigned grid = (unsigned)((n + 255) / 256);
-  if (B == 4) k_bsr_residual<4, double, double, double><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
+  const unsigned grid4 = (unsigned)((n * 4 + 255) / 256);
+  if (B == 4) k_bsr4_residual_sub<4, double, double, double><<<grid4, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
   else k_bsr_residual<6, double, double, double><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
 }
 
@@ -142,7 +196,8 @@ void launch_bsr_residual_f32(int B, int64_t nb, const int32_t* rowptr, const int
                              const float* x, const float* b, float* y, cudaStream_t st) {
   const int64_t n = nb * B;
   const unsigned grid = (unsigned)((n + 255) / 256);
-  if (B == 4) k_bsr_residual<4, float, float, float><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
+  const unsigned grid4 = (unsigned)((n * 4 + 255) / 256);
+  if (B == 4) k_bsr4_residual_sub<4, float, float, float><<<grid4, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
   else k_bsr_residual<6, float, float, float><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
 }
 
@@ -150,8 +205,9 @@ void launch_bsr_apply_mixed(int B, int64_t nb, const int32_t* rowptr, const int3
                             const float* x, double* y, cudaStream_t st) {
   const int64_t n = nb * B;
   const unsigned grid = (unsigned)((n + 255) / 256);
+  const unsigned grid4 = (unsigned)((n * 4 + 255) / 256);
   if (B == 4)
-    k_bsr_residual<4, double, float, double><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, nullptr, y);
+    k_bsr4_residual_sub<4, double, float, double><<<grid4, 256, 0, st>>>(nb, rowptr, col, val, x, nullptr, y);
   else
     k_bsr_residual<6, double, float, double><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, nullptr, y);
 }
