@@ -551,12 +551,12 @@ void factor(Ctx& c) {
       launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
                                    D.p_padpos, D.val, B, ws, D.p_idx_off, D.dr32, D.dc32, c.stream);
       launch_patch_gj_t<float>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
-                               D.p_inv_off, ws, D.inv32, c.status, B % 4 == 0, c.stream);
+                               D.p_inv_off, ws, D.inv32, c.status, true, c.stream);   // block sizes are multiples of 4
     } else {
       launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
                                     D.p_padpos, D.val, B, c.dense_ws, D.p_idx_off, D.dr, D.dc, c.stream);
       launch_patch_gj_t<double>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
-                                D.p_inv_off, c.dense_ws, D.inv, c.status, B % 4 == 0, c.stream);
+                                D.p_inv_off, c.dense_ws, D.inv, c.status, true, c.stream);
     }
     counted(c, 2);
   }

@@ -345,7 +345,12 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
     std::vector<int32_t> blocks(nodes);
     for (int32_t e : pel[p]) blocks.push_back((int32_t)(L.n_nodes + e));   // elements ascending
     const int nbk = (int)blocks.size();
-    const int n = nbk * B;
+    // block sizes are padded to a multiple of 4 (the FP32 factorisation
+    // kernels move rows as float4): the extra positions are identity rows /
+    // columns whose index is an element padding slot (its vector entries are
+    // always zero), never owned
+    const int n_blk = nbk * B;
+    const int n = (n_blk + 3) & ~3;
     L.p_n[p] = n;
     L.max_n = std::max(L.max_n, n);
     int nown = 0;
@@ -359,6 +364,10 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
         const bool own = is_node ? (patch_of[owner[blk]] == p) : !pad;
         if (own) { L.p_own.push_back(lb * B + c); ++nown; }
       }
+    }
+    for (int q = n_blk; q < n; ++q) {
+      L.p_idx.push_back((int32_t)((L.n_nodes + pel[p][0]) * B + B - 1));
+      L.p_padpos.push_back(q);
     }
     L.p_nown[p] = nown;
     L.max_nown = std::max(L.max_nown, nown);
