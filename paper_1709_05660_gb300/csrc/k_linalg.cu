@@ -1,8 +1,10 @@
 // Sparse / dense linear-algebra kernels of the Newton-step solve:
 //  * BSR residual / SpMV on the block-sparse Jacobian of each level;
 //  * scalar CSR SpMV for the grid transfers (Sec. 3.2);
-//  * coarse level: dense gather, cooperative multi-block Gauss-Jordan with
-//    partial pivoting (FP64), dense GEMV apply;
+//  * coarse level (FP64): dense gather in the banded x-slab ordering, blocked
+//    banded LU with partial pivoting (cooperative), inverse columns by
+//    triangular solves, dense GEMV apply; for the slab-blocked 3D solve also
+//    dense GEMM / GEMV on column-major sub-matrices;
 //  * Krylov helpers: multi-vector dot products, classical Gram-Schmidt
 //    updates, norms, linear combinations (Sec. 4.1 FGMRES).
 #include <cooperative_groups.h>
@@ -426,90 +428,199 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
   if (npad > 0) k_set_diag<<<(npad + 255) / 256, 256, 0, st>>>(pad_list, npad, perm, n, A);
 }
 
-// Banded LU with partial pivoting (FP64) of the coarse operator, stored
-// column-major in dense form; lower half-bandwidth kl, upper ku (row
-// interchanges widen U to kl + ku).  Cooperative: block b owns the columns
-// j = b (mod grid).  Step k reads the pivot column from a two-slot buffer,
-// picks the row p in [k, k + kl] with the largest |entry| (same rule in every
-// block), and every block swaps rows k and p and applies the rank-1 update
-// to its columns in the window (k, k + kl + ku]; column k keeps the
-// multipliers of L.  The owner of column k+1 publishes its updated copy into
-// the other buffer slot; one grid barrier per step.
-__global__ void __launch_bounds__(256) k_band_lu(int64_t n, int kl, int ku, double* __restrict__ M,
-                                                 double* __restrict__ colbuf, int32_t* __restrict__ piv,
-                                                 int32_t* __restrict__ status) {
+
+// Blocked banded LU with partial pivoting of a matrix stored column-major in
+// dense form (lower half-bandwidth kl, upper ku; row interchanges widen U to
+// kl + ku).  Factors as in the unblocked band algorithm: multipliers of step j
+// in column j rows j+1..j+kl in the row order of step j (later interchanges are
+// not applied to them), U up to kl + ku above the diagonal, piv[j] the row
+// swapped with j.  Panels of NB columns; per panel two grid barriers instead of NB:
+//  A. block 0 factors the panel (rows k0 .. k0+nb-1+kl) in shared memory with
+//     the unblocked steps, row swaps applied to the panel's columns right of
+//     the step only, and writes panel and pivots back;
+//  B. every block stages the panel's multipliers and pivots, and each warp
+//     applies the panel's NB steps (swap, then the multiplier update) to one
+//     trailing column in shared memory: columns k0+nb .. k0+nb-1+kl+ku.
+template <int NB>
+__global__ void __launch_bounds__(128) k_band_lu_blk(int64_t n, int kl, int ku, double* __restrict__ M,
+                                                    int32_t* __restrict__ piv, int32_t* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* pc = reinterpret_cast<double*>(smem_raw);   // kl + 1 entries of the pivot column (rows k..k+kl)
+  const int R = NB + kl;                                  // panel rows (at most)
+  double* P = reinterpret_cast<double*>(smem_raw);        // R x NB, column-major
+  double* S = P + (size_t)R * NB;                         // per warp: R entries of one trailing column
+  __shared__ int s_piv[NB];
   __shared__ double sv[32];
   __shared__ int si[32];
-  const int64_t G = gridDim.x;
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
   const int64_t wmax = (int64_t)kl + ku;
-  if (blockIdx.x == 0)
-    for (int64_t r = threadIdx.x; r <= kl && r < n; r += blockDim.x) colbuf[r] = M[r];
-  grid.sync();
-  for (int64_t k = 0; k < n; ++k) {
-    const int64_t r_hi = min(n - 1, k + (int64_t)kl);
-    const int64_t nr = r_hi - k + 1;
-    const double* cb = colbuf + (k & 1) * (kl + 1);
-    double best = -1.0;
-    int bi = -1;
-    for (int64_t r = threadIdx.x; r < nr; r += blockDim.x) {
-      const double v = cb[r];
-      pc[r] = v;
-      double a = fabs(v);
-      if (!(a >= 0.0)) a = 0.0;
-      if (a > best) { best = a; bi = (int)r; }
-    }
-    const int pr_off = block_argmax(best, bi, sv, si);   // barriers inside: pc complete
-    const int64_t pr = k + pr_off;
-    double pv = pc[pr_off];
-    if (!(fabs(pv) > 0.0) || !isfinite(pv)) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&status[ST_SINGULAR], 1);
-      pv = 1.0;
-    }
-    const double rp = 1.0 / pv;
-    // pivot column after the interchange: rows k <-> pr
-    const double ck = pc[0];
-    const int64_t j_hi = min(n - 1, k + wmax);
-    int64_t j0 = k + ((blockIdx.x - k % G) + G) % G;   // first owned column >= k
-    for (int64_t j = j0; j <= j_hi; j += G) {
-      double* Mj = M + j * n;
-      const double tk = Mj[k], tp = Mj[pr];
-      __syncthreads();   // all threads read rows k and p of column j before they change
-      const double t = (pr != k) ? tp : tk;   // M[k][j] after the interchange
-      // row k gets the old row-p entry; row p is written by exactly one thread:
-      // the elimination loop below when it runs for row p, thread 0 otherwise
-      if (pr != k && threadIdx.x == 0) {
-        Mj[k] = tp;
-        if (j != k && t == 0.0) Mj[pr] = tk;
-      }
-      if (j == k) {
-        for (int64_t r = threadIdx.x + 1; r < nr; r += blockDim.x) {
-          const int64_t row = k + r;
-          const double v = (row == pr) ? ck : pc[r];
-          Mj[row] = v * rp;
-        }
-      } else if (t != 0.0) {
-        const double ts = t * rp;
-        for (int64_t r = threadIdx.x + 1; r < nr; r += blockDim.x) {
-          const int64_t row = k + r;
-          const double l = (row == pr) ? ck : pc[r];
-          if (row != pr) Mj[row] -= l * ts;
-          else Mj[row] = tk - l * ts;   // row p received the old row-k entry
-        }
-      }
-      if (j == k + 1) {
-        __syncthreads();
-        const int64_t r_hi1 = min(n - 1, k + 1 + (int64_t)kl);
-        for (int64_t r = threadIdx.x; r <= r_hi1 - (k + 1); r += blockDim.x)
-          colbuf[((k + 1) & 1) * (kl + 1) + r] = Mj[k + 1 + r];
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int nb = (int)min((int64_t)NB, n - k0);
+    const int nr = (int)(min(n, k0 + nb + kl) - k0);
+    if (blockIdx.x == 0) {
+      for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) {
+        const int r = t % nr, j = t / nr;
+        P[j * R + r] = M[(k0 + j) * n + k0 + r];
       }
       __syncthreads();
+      for (int j = 0; j < nb; ++j) {
+        const int rhi = min(j + kl, nr - 1);
+        double best = -1.0;
+        int bi = -1;
+        for (int r = j + threadIdx.x; r <= rhi; r += blockDim.x) {
+          double a = fabs(P[j * R + r]);
+          if (!(a >= 0.0)) a = 0.0;
+          if (a > best) { best = a; bi = r; }
+        }
+        int pr = block_argmax(best, bi, sv, si);
+        if (pr < 0) pr = j;
+        if (pr != j)
+          for (int c = j + threadIdx.x; c < nb; c += blockDim.x) {
+            const double t0 = P[c * R + j];
+            P[c * R + j] = P[c * R + pr];
+            P[c * R + pr] = t0;
+          }
+        __syncthreads();
+        double pv = P[j * R + j];
+        if (!(fabs(pv) > 0.0) || !isfinite(pv)) {
+          if (threadIdx.x == 0) atomicExch(&status[ST_SINGULAR], 1);
+          pv = 1.0;
+        }
+        const double rp = 1.0 / pv;
+        for (int r = j + 1 + threadIdx.x; r <= rhi; r += blockDim.x) P[j * R + r] *= rp;
+        __syncthreads();
+        const int nrow = rhi - j, ncol = nb - 1 - j;
+        for (int t = threadIdx.x; t < nrow * ncol; t += blockDim.x) {
+          const int c = j + 1 + t / nrow, r = j + 1 + t % nrow;
+          P[c * R + r] -= P[j * R + r] * P[c * R + j];
+        }
+        if (threadIdx.x == 0) s_piv[j] = pr;
+        __syncthreads();
+      }
+      for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) {
+        const int r = t % nr, j = t / nr;
+        M[(k0 + j) * n + k0 + r] = P[j * R + r];
+      }
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) piv[k0 + j] = (int32_t)(k0 + s_piv[j]);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = (int32_t)pr;
+    grid.sync();
+    const int64_t c_lo = k0 + nb, c_hi = min(n - 1, k0 + nb - 1 + wmax);
+    if (c_lo <= c_hi) {
+      // stage multipliers and pivots (every block)
+      for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) {
+        const int r = t % nr, j = t / nr;
+        P[j * R + r] = M[(k0 + j) * n + k0 + r];
+      }
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) s_piv[j] = (int)(piv[k0 + j] - k0);
+      __syncthreads();
+      double* Sw = S + (size_t)wid * R;
+      for (int64_t c = c_lo + (int64_t)blockIdx.x * nw + wid; c <= c_hi; c += (int64_t)gridDim.x * nw) {
+        double* Mc = M + c * n + k0;
+        for (int r = lane; r < nr; r += kWarp) Sw[r] = Mc[r];
+        __syncwarp();
+        for (int j = 0; j < nb; ++j) {
+          const int pr = s_piv[j];
+          if (pr != j && lane == 0) {
+            const double t0 = Sw[j];
+            Sw[j] = Sw[pr];
+            Sw[pr] = t0;
+          }
+          __syncwarp();
+          const double t = Sw[j];
+          if (t != 0.0) {
+            const int rhi = min(j + kl, nr - 1);
+            for (int r = j + 1 + lane; r <= rhi; r += kWarp) Sw[r] -= P[j * R + r] * t;
+          }
+          __syncwarp();
+        }
+        for (int r = lane; r < nr; r += kWarp) Mc[r] = Sw[r];
+        __syncwarp();
+      }
+    }
     grid.sync();
   }
+}
+
+template <int NB>
+size_t band_lu_blk_smem(int kl) { return ((size_t)(NB + kl) * NB + 4 * (size_t)(NB + kl)) * sizeof(double); }
+
+// Narrow-band variant of k_band_inv (kl + ku <= 32 MR): each lane holds at
+// most MR rows of a factor column, and the column of step k + 1 is loaded
+// into registers before the updates of step k, so a step waits on shared
+// memory only, not on a fresh global load.
+template <int MR>
+__global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, const double* __restrict__ M,
+                                                     const int32_t* __restrict__ piv,
+                                                     const int32_t* __restrict__ perm,
+                                                     const int32_t* __restrict__ pinv, double* __restrict__ Ainv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / kWarp) + wid;
+  if (c >= n) return;
+  double* x = reinterpret_cast<double*>(smem_raw) + (int64_t)wid * n;
+  for (int64_t i = lane; i < n; i += kWarp) x[i] = (i == c) ? 1.0 : 0.0;
+  __syncwarp();
+  // forward: rows k+1 .. k+kl of column k; lane's m-th row is k + 1 + lane + 32 m
+  const int64_t k_start = max((int64_t)0, c - (int64_t)kl);
+  double cur[MR], nxt[MR];
+  auto load_l = [&](int64_t k, double (&v)[MR]) {
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+      const int64_t r = k + 1 + lane + 32 * m;
+      v[m] = (k < n && r <= min(n - 1, k + (int64_t)kl)) ? M[k * n + r] : 0.0;
+    }
+  };
+  load_l(k_start, cur);
+  for (int64_t k = k_start; k < n; ++k) {
+    load_l(k + 1, nxt);
+    const int64_t p = piv[k];
+    if (p != k) {
+      if (lane == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+      __syncwarp();
+    }
+    const double xk = x[k];
+    if (xk != 0.0) {
+#pragma unroll
+      for (int m = 0; m < MR; ++m) {
+        const int64_t r = k + 1 + lane + 32 * m;
+        if (r <= min(n - 1, k + (int64_t)kl)) x[r] -= cur[m] * xk;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < MR; ++m) cur[m] = nxt[m];
+  }
+  // backward: rows k - w .. k - 1 of column k (w = kl + ku); lane's m-th row is k - 1 - lane - 32 m
+  const int64_t w = (int64_t)kl + ku;
+  auto load_u = [&](int64_t k, double (&v)[MR], double& d) {
+    d = k >= 0 ? M[k * n + k] : 1.0;
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+      const int64_t r = k - 1 - lane - 32 * m;
+      v[m] = (k >= 0 && r >= 0 && r >= k - w) ? M[k * n + r] : 0.0;
+    }
+  };
+  double dcur, dnxt;
+  load_u(n - 1, cur, dcur);
+  for (int64_t k = n - 1; k >= 0; --k) {
+    load_u(k - 1, nxt, dnxt);
+    const double xk = x[k] / dcur;
+    __syncwarp();
+    if (lane == 0) x[k] = xk;
+    if (xk != 0.0) {
+#pragma unroll
+      for (int m = 0; m < MR; ++m) {
+        const int64_t r = k - 1 - lane - 32 * m;
+        if (r >= 0 && r >= k - w) x[r] -= cur[m] * xk;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < MR; ++m) cur[m] = nxt[m];
+    dcur = dnxt;
+  }
+  double* out = Ainv + (int64_t)pinv[c] * n;
+  for (int64_t i = lane; i < n; i += kWarp) out[i] = x[perm[i]];
 }
 
 // Columns of the inverse from the banded LU: one warp per right-hand side
@@ -560,25 +671,37 @@ __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, con
 int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbuf, double* Ainv, int32_t* piv,
                              const int32_t* perm, const int32_t* pinv, int32_t* status, int sm_count,
                              cudaStream_t st) {
-  const int threads = 256;
-  // one block per SM: spreading each step's window over more blocks measured
-  // faster than fewer blocks with cheaper grid barriers
+  // blocked LU: 16-column panels when they fit in shared memory, else 8
+  const int threads = 128;
   int grid = (int)std::min<int64_t>((int64_t)sm_count, n);
   if (grid < 1) grid = 1;
-  const size_t smem = (size_t)(kl + 1) * sizeof(double) + 16;
-  if (smem > 200 * 1024) return -3;
-  cudaFuncSetAttribute(k_band_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_lu, threads, smem);
-  if (per_sm < 1) return -1;
-  void* args[] = {(void*)&n, (void*)&kl, (void*)&ku, (void*)&M, (void*)&colbuf, (void*)&piv, (void*)&status};
-  if (cudaLaunchCooperativeKernel((const void*)k_band_lu, grid, threads, args, smem, st) != cudaSuccess) return -2;
+  void* args[] = {(void*)&n, (void*)&kl, (void*)&ku, (void*)&M, (void*)&piv, (void*)&status};
+  auto go = [&](auto kern, size_t smem) -> int {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (per_sm < 1) return -1;
+    if (cudaLaunchCooperativeKernel((const void*)kern, grid, threads, args, smem, st) != cudaSuccess) return -2;
+    return 0;
+  };
+  (void)colbuf;
+  int rc;
+  if (band_lu_blk_smem<16>(kl) <= 200 * 1024) rc = go(k_band_lu_blk<16>, band_lu_blk_smem<16>(kl));
+  else if (band_lu_blk_smem<8>(kl) <= 200 * 1024) rc = go(k_band_lu_blk<8>, band_lu_blk_smem<8>(kl));
+  else return -3;
+  if (rc != 0) return rc;
   // inverse columns: 4 warps (right-hand sides) per block, x in shared memory
   const int wpb = 4;
   const size_t ismem = (size_t)wpb * n * sizeof(double);
   if (ismem > 200 * 1024) return -4;
-  cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-  k_band_inv<<<(unsigned)((n + wpb - 1) / wpb), wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, perm, pinv, Ainv);
+  const unsigned nblk = (unsigned)((n + wpb - 1) / wpb);
+  if ((int64_t)kl + ku <= 32 * 8) {   // narrow band: register prefetch of the next factor column
+    cudaFuncSetAttribute(k_band_inv_pf<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    k_band_inv_pf<8><<<nblk, wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, perm, pinv, Ainv);
+  } else {
+    cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    k_band_inv<<<nblk, wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, perm, pinv, Ainv);
+  }
   return 0;
 }
 
