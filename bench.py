@@ -37,6 +37,7 @@ METRIC = "Newton-step solves/s (FGMRES to true rel. residual 1e-10; mixed FP32/F
 UNIT = "solves/s"
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
+FALLBACK_BF16_SUSTAINED_TFLOPS = 1700.0
 # FP64 ALU peak derived from the unit counts and clocks: 152 SMs x 2.07 GHz x
 # 4 FP64 flop / clock / SM (the 1.25 TFLOP/s nominal FP64 rate of the part).
 FP64_ALU_PEAK_GFLOPS = 152 * 2.07 * 4.0
@@ -291,6 +292,57 @@ def _measure(args, prec, stream, barrier, dist, world, local):
     return out
 
 
+def _measure_transient_3d(args, stream):
+    """3D time-dependent workload (box channel with a plate, 27-node hexahedra,
+    3 levels, 908,422 unknowns, mixed precision): args.t3d_steps BDF time steps
+    of dt = 0.01 (BDF1 start-up step, then BDF2) at t = dt, 2 dt, ..., each
+    solved by Newton to ||dx|| <= 1e-8 ||y|| with the pulsating inflow
+    alpha(t) = (1 + sin 2 pi t) / 2.  Device time of every Newton step (CUDA
+    events on the stream), kernel-class breakdown with profiling on."""
+    import torch
+    from dataclasses import replace
+    from paper_1709_05660_gb300 import fsi
+
+    prob, opts = CONFIGS["c4_3d_l3"]
+    s = fsi.FSI(prob, opts, stream=stream.cuda_stream)
+    N = int(s.N[-1])
+    y = torch.empty(N, dtype=torch.float64, device="cuda")
+    s.initial_state(torch.tensor(noise(N, 0), dtype=torch.float64, device="cuda"), y)
+    yp, ypp = y.clone(), None
+    s.set_profiling(True)
+    newton, iters, rel_res, ms_tot = 0, [], 0.0, 0.0
+    per_step = []
+    for n in range(1, args.t3d_steps + 1):
+        s.set_state(yp, yp, ypp, n * prob.dt)
+        k = 0
+        for k in range(1, 11):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rel, st = s.newton_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_tot += e0.elapsed_time(e1)
+            newton += 1
+            iters.append(st.iters)
+            rel_res = max(rel_res, st.rel_res)
+            if rel < 1e-8:
+                break
+        per_step.append(k)
+        ynew = torch.empty_like(y)
+        s.get_state(ynew)
+        ypp, yp = yp, ynew
+    kst = s.kernel_stats()
+    s.set_profiling(False)
+    s.close()
+    _, classes = _roofline(kst, newton, fp32_classes=("patch_factor",))
+    return {"workload": "c4_3d_l3 (3D BDF2, dt 0.01, 64x16x16 hexahedra, 3 levels, mixed)", "unknowns": N,
+            "time_steps": args.t3d_steps, "newton_steps_per_time_step": per_step,
+            "newton_solves_per_s": newton / (ms_tot / 1e3), "time_steps_per_s": args.t3d_steps / (ms_tot / 1e3),
+            "ms_per_newton_step": ms_tot / newton, "fgmres_iters": iters, "max_true_rel_residual": rel_res,
+            "kernel_classes": classes}
+
+
 def _roofline(kst, steps, fp32_classes=()):
     peaks, kind = _peaks()
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
@@ -301,14 +353,24 @@ def _roofline(kst, steps, fp32_classes=()):
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_source": kind}
+    elif dom in fp32_classes:
+        # the mixed path's Schwarz factorisation: its contraction (the rank-W
+        # trailing update) runs on the tensor cores in TF32 (3xTF32 split);
+        # peak = the bf16 dense peak (sustained: the kernel is timed inside a
+        # long step) x the nominal TF32 / BF16 ratio 1.1 / 2.25
+        bf16 = float(peaks.get("bf16_tflops_sustained", FALLBACK_BF16_SUSTAINED_TFLOPS)) if peaks else \
+            FALLBACK_BF16_SUSTAINED_TFLOPS
+        peak = bf16 * 1.1 / 2.25
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{kind} bf16 sustained {bf16:.0f} TFLOP/s x nominal tf32/bf16 1.1/2.25",
+                "dtype": "tf32 (3xTF32 split, FP32 accumulate)",
+                "flops": "algorithmic Gauss-Jordan flops 2 n^3 per block (the tensor pipe executes 3x that)"}
     else:
-        fp32 = dom in fp32_classes
-        peak = FP32_ALU_PEAK_GFLOPS if fp32 else FP64_ALU_PEAK_GFLOPS
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e9
-        src = ("derived FP32 ALU peak (152 SM x 2.07 GHz x 256 flop/clk)" if fp32 else
-               "derived FP64 ALU peak (152 SM x 2.07 GHz x 4 flop/clk)")
-        roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": peak / 1e3, "unit": "TFLOP/s",
-                "frac": achieved / peak, "peak_source": src, "dtype": "f32" if fp32 else "f64"}
+        roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": FP64_ALU_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / FP64_ALU_PEAK_GFLOPS,
+                "peak_source": "derived FP64 ALU peak (152 SM x 2.07 GHz x 4 flop/clk)", "dtype": "f64"}
     roof.update({"kernel": dom, "traffic": _traffic(dom), "launches": d["launches"],
                  "avg_launch_ms": per_launch_ms})
     classes = {k: {"ms_per_step": v["ms"] / steps, "launches": v["launches"],
@@ -362,6 +424,8 @@ def run_gpu(args, rank, world):
         }
         if not args.no_serve and world == 1:
             line["served"] = run_serve(args, n_requests=32, max_levels=4, quiet=True)
+        if args.t3d_steps > 0 and world == 1:
+            line["transient_3d"] = _measure_transient_3d(args, stream)
         if fp64 is not None:
             r64, c64 = _roofline(fp64["kst"], args.steps)
             line["fp64_path"] = {"value": fp64["value"], "ms_per_step": fp64["per_step"],
@@ -379,23 +443,30 @@ def run_gpu(args, rank, world):
 # serving (continuous batching of Newton-step requests)
 # ----------------------------------------------------------------------------
 
-def serve_mix(seed: int, n_requests: int, max_levels: int):
+def serve_mix(seed: int, n_requests: int, max_levels: int, frac_3d: float = 0.25):
     """Seeded request mix: 2D channel instances with levels uniform in
-    [3, max_levels], shear modulus log-uniform in [1e4, 1e6], mean inflow
-    uniform in [0.1, 0.3] (faster inflows make plain Newton with this smoother
-    stall on the coarser meshes, in the oracle as on the GPU), 3-8 Newton
-    steps each (tiles 2x2 up to 4 levels, 4x4 above)."""
-    from paper_1709_05660_gb300.workloads import Problem, SolverOpts
+    [3, max_levels] and, with probability frac_3d, 3D box-channel instances
+    at 2 levels (120,902 unknowns; the 3-level 3D problem is measured on its
+    own), shear modulus log-uniform in [1e4, 1e6], mean inflow uniform in
+    [0.1, 0.3] (faster inflows make plain Newton with this smoother stall on
+    the coarser meshes, in the oracle as on the GPU), 3-8 Newton steps each
+    (tiles 2x2 up to 4 levels, 4x4 above, 2x2x2 in 3D)."""
+    from paper_1709_05660_gb300.workloads import Problem, SolverOpts, problem_3d
     rng = np.random.Generator(np.random.PCG64(seed))
     insts, total = [], 0
     iid = 1
     while total < n_requests:
-        lv = int(rng.integers(3, max_levels + 1))
+        is3d = rng.uniform() < frac_3d
+        lv = 2 if is3d else int(rng.integers(3, max_levels + 1))
         mu = float(10 ** rng.uniform(4, 6))
         U = float(rng.uniform(0.1, 0.3))
         steps = int(rng.integers(3, 9))
         steps = min(steps, n_requests - total)
-        insts.append((iid, Problem(levels=lv, mu_s=mu, U=U), SolverOpts(tile=(2, 2) if lv <= 4 else (4, 4)), steps))
+        if is3d:
+            insts.append((iid, problem_3d(levels=lv, mu_s=mu, U=U), SolverOpts(tile=(2, 2, 2)), steps))
+        else:
+            insts.append((iid, Problem(levels=lv, mu_s=mu, U=U), SolverOpts(tile=(2, 2) if lv <= 4 else (4, 4)),
+                          steps))
         total += steps
         iid += 1
     # arrival order: interleave instances at random, keeping each instance's steps in order
@@ -451,14 +522,14 @@ def _serve_once(insts, order, prec, slots, budget, arrivals=None):
     return {"solves_per_s": len(good) / wall, "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "requests": len(order), "completed": len(good),
             "statuses": statuses, "rejected": len(rejected),
-            "failed_instances": [(i, spec[i][1].levels, spec[i][1].mu_s, spec[i][1].U) for i in failed],
+            "failed_instances": [(i, spec[i][1].dim, spec[i][1].levels, spec[i][1].mu_s, spec[i][1].U) for i in failed],
             "max_true_rel_residual": max([r["rel_res"] for r in good] or [0.0])}
 
 
 def run_serve(args, n_requests=None, max_levels=None, quiet=False):
     n_requests = n_requests or args.serve_requests
     max_levels = max_levels or args.serve_max_levels
-    insts, order, rng = serve_mix(0, n_requests, max_levels)
+    insts, order, rng = serve_mix(0, n_requests, max_levels, args.serve_3d_frac)
     budget = int(args.serve_budget_gb * 1e9)
     out = {}
     for prec, name in ((1, "mixed"), (0, "fp64")):
@@ -469,7 +540,9 @@ def run_serve(args, n_requests=None, max_levels=None, quiet=False):
         pois["arrival_rate_per_s"] = lam
         out[name] = {"closed_loop": closed, "poisson": pois}
     summary = {"requests": len(order), "instances": len(insts), "levels": [3, max_levels], "slots": args.serve_slots,
-               "budget_gb": args.serve_budget_gb, "mix": "2D channel, mu_s log-U[1e4,1e6], U U[0.1,0.3], 3-8 steps",
+               "budget_gb": args.serve_budget_gb, "mix": f"2D channel (levels 3-{max_levels}) and, with probability {args.serve_3d_frac}, 3D box channel "
+                      f"(2 levels); mu_s log-U[1e4,1e6], U U[0.1,0.3], 3-8 Newton steps per instance",
+               "instances_3d": sum(1 for i in insts if i[1].dim == 3),
                **out}
     if not quiet:
         line = {"metric": "served Newton-step solves/s and p50/p99 latency (Poisson arrivals at 0.8x capacity)",
@@ -508,6 +581,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the small served run of the default line")
+    ap.add_argument("--t3d-steps", type=int, default=2,
+                    help="BDF time steps of the 3D transient workload in the default line (0: skip)")
+    ap.add_argument("--serve-3d-frac", type=float, default=0.25, help="share of 3D instances in the request mix")
     ap.add_argument("--cpu-frac", type=float, default=0.25)
     ap.add_argument("--ref-frac", type=float, default=1.0 / 16)
     ap.add_argument("--ref-iters", type=int, default=15)

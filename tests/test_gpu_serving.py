@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from paper_1709_05660_gb300.workloads import Problem, SolverOpts, noise  # noqa: E402
+from paper_1709_05660_gb300.workloads import Problem, SolverOpts, noise, problem_3d  # noqa: E402
 
 # parameters inside the range where plain Newton with this smoother converges
 # on these coarse meshes (U <= 0.3; the oracle fails at U >= 0.6 on 3 levels)
@@ -24,6 +24,7 @@ INSTANCES = [
     (11, Problem(levels=3, mu_s=1e5, U=0.3), SolverOpts(tile=(2, 2), precision=1)),
     (12, Problem(levels=3, mu_s=8e5, U=0.2), SolverOpts(tile=(2, 2), precision=0)),
     (13, Problem(levels=4, mu_s=3e4, U=0.15), SolverOpts(tile=(2, 2), precision=1)),
+    (14, problem_3d(levels=2, mu_s=5e5, U=0.2), SolverOpts(tile=(2, 2, 2), precision=1)),
 ]
 STEPS = 3
 
@@ -67,7 +68,7 @@ def test_alone_vs_mixed_bitwise():
     fsi = _fsi()
     torch.cuda.set_device(0)
     order = [iid for _ in range(STEPS) for iid, _, _ in INSTANCES]     # round-robin interleaving
-    srv = fsi.Server(hbm_budget_bytes=0, max_slots=3)
+    srv = fsi.Server(hbm_budget_bytes=0, max_slots=len(INSTANCES))
     mixed = _run(srv, INSTANCES, order)
     srv.close()
     for inst in INSTANCES:
