@@ -60,7 +60,7 @@ constexpr int kEPB = 4;         // elements per thread block
 // element residual + Jacobian column (2D)
 // ---------------------------------------------------------------------------
 template <bool SOLID, bool TRANS>
-__global__ void __launch_bounds__(kEPB * kNdofe)
+__global__ void __launch_bounds__(kEPB * kNdofe, 2)
 k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ y,
               const int32_t* __restrict__ elem_nodes, const uint8_t* __restrict__ node_class,
               const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp,
@@ -104,9 +104,12 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   const int sj = j < kNN ? j % kB : -1;
   const int pk = j >= kNN ? j - kNN : -1;
 
-  double acc[kNdofe];
+  // column j of the element Jacobian accumulates in shared memory (registers
+  // would spill with the dual-number temporaries)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Kc = reinterpret_cast<double*>(smem_raw) + (size_t)le * kNdofe * kNdofe + j;
 #pragma unroll
-  for (int i = 0; i < kNdofe; ++i) acc[i] = 0.0;
+  for (int i = 0; i < kNdofe; ++i) Kc[i * kNdofe] = 0.0;
   double vj = 0.0;
   bool tangled = false;
 
@@ -147,7 +150,10 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
       }
       const double psi[3] = {1.0, xi, eta};
       const double pv = ye[kNN] + ye[kNN + 1] * xi + ye[kNN + 2] * eta;
-      const double gxj = aj >= 0 ? Gx[aj] : 0.0, gyj = aj >= 0 ? Gy[aj] : 0.0, nj = aj >= 0 ? Nb[aj] : 0.0;
+      double gxj = 0.0, gyj = 0.0, nj = 0.0;   // basis of the seeded node (unrolled select: no local memory)
+#pragma unroll
+      for (int a = 0; a < kNloc; ++a)
+        if (a == aj) { gxj = Gx[a]; gyj = Gy[a]; nj = Nb[a]; }
       Dual gd[2][2], gu[2][2], u[2], ut[2], dt_[2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
@@ -195,8 +201,8 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         for (int a = 0; a < kNloc; ++a) {
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            acc[a * kB + c] += Tw[c][0].d * Gx[a] + Tw[c][1].d * Gy[a] + inert[c].d * Nb[a];
-            acc[a * kB + 2 + c] += kin[c].d * Nb[a];
+            Kc[(a * kB + c) * kNdofe] += Tw[c][0].d * Gx[a] + Tw[c][1].d * Gy[a] + inert[c].d * Nb[a];
+            Kc[(a * kB + 2 + c) * kNdofe] += kin[c].d * Nb[a];
           }
         }
         if (aj >= 0) {
@@ -244,10 +250,10 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
             // interface node: momentum in the d-row, no ALE row (psi = 0 on the interface)
             // fluid node: ALE in the d-row, momentum in the u-row
             if (ifc) {
-              acc[a * kB + c] += md;
+              Kc[(a * kB + c) * kNdofe] += md;
             } else {
-              acc[a * kB + c] += A[c][0].d * Gx[a] + A[c][1].d * Gy[a];
-              acc[a * kB + 2 + c] += md;
+              Kc[(a * kB + c) * kNdofe] += A[c][0].d * Gx[a] + A[c][1].d * Gy[a];
+              Kc[(a * kB + 2 + c) * kNdofe] += md;
             }
           }
         }
@@ -265,7 +271,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const Dual t = mass * (psi[k] * wq);
-        acc[kNN + k] += t.d;
+        Kc[(kNN + k) * kNdofe] += t.d;
         if (kNN + k == j) vj += t.v;
       }
     }
@@ -273,7 +279,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   if (tangled && j == 0) atomicExch(&status[ST_TANGLED], 1);
   double* K = Ke + (int64_t)e * kNdofe * kNdofe;
 #pragma unroll
-  for (int i = 0; i < kNdofe; ++i) K[i * kNdofe + j] = acc[i];
+  for (int i = 0; i < kNdofe; ++i) K[i * kNdofe + j] = Kc[i * kNdofe];
   Re[(int64_t)e * kNdofe + j] = vj;
 }
 
@@ -836,8 +842,11 @@ void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* 
                         double* Ke, double* Re, int32_t* status, cudaStream_t st) {
   if (ne <= 0) return;
   const int grid = (ne + kEPB - 1) / kEPB;
+  const size_t smem = (size_t)kEPB * kNdofe * kNdofe * sizeof(double);
   auto go = [&](auto kern) {
-    kern<<<grid, kEPB * kNdofe, 0, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp, Ke, Re, status);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, kEPB * kNdofe, smem, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp, Ke, Re,
+                                           status);
   };
   if (solid)
     pp.transient ? go(k_assemble_2d<true, true>) : go(k_assemble_2d<true, false>);
