@@ -56,6 +56,8 @@ __device__ int block_argmax_abs(double v, int idx, double* sv, int* si) {
 }  // namespace
 
 // power of two closest (from below) to 1 / m, so scaling is exact; 1 for m == 0
+constexpr int kGatherMaxN = 1024;   // blocks up to this size take the sparse-pass gather
+
 __device__ __forceinline__ double pow2_inv(double m) {
   if (!(m > 0.0) || !isfinite(m)) return 1.0;
   int e;
@@ -79,6 +81,60 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
   __syncthreads();
   const int BB = B * B;
   const int64_t g0 = gmap_off[p], g1 = gmap_off[p + 1];
+  if (n <= kGatherMaxN) {
+    // scales from the block-sparse entries (row and column maxima by integer
+    // max on the bits of non-negative doubles), then one scattered write of
+    // the equilibrated entries: the dense block is written once
+    __shared__ unsigned long long rmx[kGatherMaxN], cmx[kGatherMaxN];
+    __shared__ T srw[kGatherMaxN], scl[kGatherMaxN];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { rmx[i] = 0ull; cmx[i] = 0ull; }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
+      const int64_t g = g0 + t / BB;
+      const int e = (int)(t % BB), ci = e / B;
+      const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1];
+      const double a = fabs((double)T(bsr_val[(int64_t)blk * BB + e]));
+      atomicMax(&rmx[lr * B + ci], (unsigned long long)__double_as_longlong(a));
+    }
+    for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x)
+      atomicMax(&rmx[padpos[t]], (unsigned long long)__double_as_longlong(1.0));
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) srw[i] = T(pow2_inv(__longlong_as_double((long long)rmx[i])));
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
+      const int64_t g = g0 + t / BB;
+      const int e = (int)(t % BB), ci = e / B, cj = e % B;
+      const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
+      const double a = fabs((double)(T(bsr_val[(int64_t)blk * BB + e]) * srw[lr * B + ci]));
+      atomicMax(&cmx[lc * B + cj], (unsigned long long)__double_as_longlong(a));
+    }
+    for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
+      const int q = padpos[t];
+      atomicMax(&cmx[q], (unsigned long long)__double_as_longlong(fabs((double)(T(1) * srw[q]))));
+    }
+    __syncthreads();
+    T* Dr = dr + idx_off[p];
+    T* Dc = dc + idx_off[p];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      scl[i] = T(pow2_inv(__longlong_as_double((long long)cmx[i])));
+      Dr[i] = srw[i];
+      Dc[i] = scl[i];
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
+      const int64_t g = g0 + t / BB;
+      const int e = (int)(t % BB), ci = e / B, cj = e % B;
+      const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
+      const int i = lr * B + ci, j = lc * B + cj;
+      D[(int64_t)i * n + j] = T(T(bsr_val[(int64_t)blk * BB + e]) * srw[i]) * scl[j];
+    }
+    __syncthreads();   // padding rows / columns of the block matrix hold zeros: the diagonal goes last
+    for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
+      const int q = padpos[t];
+      D[(int64_t)q * n + q] = T(T(1) * srw[q]) * scl[q];
+    }
+    return;
+  }
   for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
     const int64_t g = g0 + t / BB;
     const int e = (int)(t % BB), ci = e / B, cj = e % B;
