@@ -298,7 +298,11 @@ void build_device(Ctx& c) {
   ck(cudaMallocHost((void**)&c.host_small, 512 * sizeof(double)), "cudaMallocHost");
   c.stage_a = dalloc<double>(c, F.N);
   c.stage_b = dalloc<double>(c, F.N);
-  c.dense_ws_len = std::max<int64_t>(max_dense, 1);
+  // the mixed path factors the blocks of all levels in one launch: one
+  // workspace region per level
+  int64_t sum_dense = 0;
+  for (int l = 1; l < L; ++l) sum_dense += c.hl[l].dense_total;
+  c.dense_ws_len = std::max<int64_t>(c.mixed ? sum_dense : max_dense, 1);
   // patch factorisation workspace: max_dense elements of the factor precision
   c.dense_ws = dalloc<double>(c, c.mixed ? ((size_t)c.dense_ws_len + 1) / 2 : (size_t)c.dense_ws_len);
   // coarse dense operator
@@ -543,21 +547,55 @@ double coarse_slab_apply_bytes(const Ctx& c) {
 void factor(Ctx& c) {
   const int L = (int)c.dl.size();
   const int B = c.B;
-  for (int l = 1; l < L; ++l) {
+  if (c.mixed && L > 1) {
+    // gather every level into its own workspace region, then factor the
+    // blocks of all levels in one tensor-core launch (the smaller levels fill
+    // the GPU beside the finest one)
+    float* ws = reinterpret_cast<float*>(c.dense_ws);
+    GjLevels lv{};
+    lv.nlev = 0;
+    int first = 0, max_n = 0;
+    double by = 0.0, fl = 0.0;
+    int64_t off = 0;
+    std::vector<int64_t> base(L, 0);
+    for (int l = 1; l < L; ++l) {
+      DevLevel& D = c.dl[l];
+      base[l] = off;
+      off += D.dense_total;
+      by += D.factor_bytes;
+      fl += D.factor_flops;
+    }
+    Prof pr(c, FSI_K_PATCH_FACTOR, by, fl, L);
+    for (int l = 1; l < L; ++l) {
+      DevLevel& D = c.dl[l];
+      launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
+                                   D.p_padpos, D.val, B, ws + base[l], D.p_idx_off, D.dr32, D.dc32, c.stream);
+      counted(c);
+      if (D.n_patches > 0 && lv.nlev < kGjMaxLevels) {
+        lv.l[lv.nlev++] = GjLevel{D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own, D.p_inv_off, ws + base[l],
+                                  D.inv32, first};
+        first += D.n_patches;
+        max_n = std::max(max_n, D.max_n);
+      }
+    }
+    if (lv.nlev == L - 1 && launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream)) {
+      counted(c);
+    } else {
+      for (int l = 1; l < L; ++l) {   // blocks too large for the tensor-core kernel: level by level
+        DevLevel& D = c.dl[l];
+        launch_patch_gj_t<float>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
+                                 D.p_inv_off, ws + base[l], D.inv32, c.status, true, c.stream);
+        counted(c);
+      }
+    }
+  }
+  for (int l = 1; l < L && !c.mixed; ++l) {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_FACTOR, D.factor_bytes, D.factor_flops, 2);
-    if (c.mixed) {
-      float* ws = reinterpret_cast<float*>(c.dense_ws);
-      launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
-                                   D.p_padpos, D.val, B, ws, D.p_idx_off, D.dr32, D.dc32, c.stream);
-      launch_patch_gj_t<float>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
-                               D.p_inv_off, ws, D.inv32, c.status, true, c.stream);   // block sizes are multiples of 4
-    } else {
-      launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
-                                    D.p_padpos, D.val, B, c.dense_ws, D.p_idx_off, D.dr, D.dc, c.stream);
-      launch_patch_gj_t<double>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
-                                D.p_inv_off, c.dense_ws, D.inv, c.status, true, c.stream);
-    }
+    launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
+                                  D.p_padpos, D.val, B, c.dense_ws, D.p_idx_off, D.dr, D.dc, c.stream);
+    launch_patch_gj_t<double>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
+                              D.p_inv_off, c.dense_ws, D.inv, c.status, true, c.stream);
     counted(c, 2);
   }
   DevLevel& C = c.dl[0];
@@ -892,7 +930,9 @@ static int64_t estimate_device_bytes(const Ctx& c) {
   const double n0 = (double)c.hl[0].Ni;
   b += F.Ni * 8.0 * 2 + (m + 1.0) * F.Ni * 8.0 + m * (double)F.Ni * fs + F.Ni * 8.0 * 4 + F.N * 8.0 * 2;
   if (c.desc.transient != 0) b += F.Ni * 8.0;
-  b += max_dense * fs + F.n_elem * (double)nd * 8.0 + 1e6;
+  double sum_dense = 0.0;
+  for (size_t l = 1; l < L; ++l) sum_dense += (double)c.hl[l].dense_total;
+  b += (mixed ? sum_dense : max_dense) * fs + F.n_elem * (double)nd * 8.0 + 1e6;
   const std::vector<int64_t>& so = c.hl[0].slab_off;
   if (c.dim == 3 && !so.empty()) {
     // dense banded-order operator + Sinv_k blocks + LU scratch + vectors

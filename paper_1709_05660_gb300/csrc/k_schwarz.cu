@@ -659,10 +659,7 @@ __device__ __forceinline__ uint32_t piv_key(float a, int row) {
 
 template <int W>
 __global__ void __launch_bounds__(gj_tc_threads<W>(), 1)
-k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
-              const int64_t* __restrict__ dense_off, const int64_t* __restrict__ own_off,
-              const int32_t* __restrict__ own, const int64_t* __restrict__ inv_off, float* __restrict__ dense,
-              float* __restrict__ invT, int32_t* __restrict__ status, int max_n) {
+k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
   static_assert(W == 16 || W == 32, "panel width");
   constexpr int NWARP = gj_tc_threads<W>() / kWarp;   // 16 or 32 warps
   constexpr int CGN = NWARP / 4;                       // column chunks of a tile per lane quarter
@@ -680,9 +677,13 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   __shared__ __align__(8) uint64_t mbar2[2];
   __shared__ uint32_t tslot;
   __shared__ int s_sing, s_abort;
-  const int p = blockIdx.x;
-  const int n = p_n[p];
-  float* M = dense + dense_off[p];
+  // the blocks of several levels share one launch: find this block's level
+  int lvl = 0;
+  while (lvl + 1 < lv.nlev && (int)blockIdx.x >= lv.l[lvl + 1].first) ++lvl;
+  const GjLevel& L = lv.l[lvl];
+  const int p = (int)blockIdx.x - L.first;
+  const int n = L.p_n[p];
+  float* M = L.dense + L.dense_off[p];
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
   const int me = threadIdx.x;
   const bool has_row = me < n;
@@ -930,9 +931,9 @@ k_patch_gj_tc(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_now
   {
     // owned rows of the inverse, transposed: out[c][o] = Binv[own[o]][c]; o is
     // the fastest index (coalesced writes), reads hit rows of M just written
-    const int nown = p_nown[p], opad = own_pad(nown);
-    const int32_t* ow = own + own_off[p];
-    float* out = invT + inv_off[p];
+    const int nown = L.p_nown[p], opad = own_pad(nown);
+    const int32_t* ow = L.own + L.own_off[p];
+    float* out = L.invT + L.inv_off[p];
     int* roff = reinterpret_cast<int*>(stage);   // row offset of B^{-1} row own[o] in M
     for (int o = threadIdx.x; o < nown; o += blockDim.x) roff[o] = piv[ow[o]] * n;
     __syncthreads();
@@ -962,15 +963,18 @@ done:
 }
 
 template <int W>
-bool try_gj_tc(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
-               const int64_t* own_off, const int32_t* own, const int64_t* inv_off, float* dense, float* invT,
-               int32_t* status, cudaStream_t st) {
+bool try_gj_tc(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st) {
   const size_t smem = gj_tc_smem<W>(max_n);
   if (smem > 225 * 1024 || max_n % 4 != 0 || max_n > gj_tc_max_n<W>() || max_n < 64) return false;
   cudaFuncSetAttribute(k_patch_gj_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_patch_gj_tc<W><<<np, gj_tc_threads<W>(), smem, st>>>(p_n, p_nown, dense_off, own_off, own, inv_off, dense,
-                                                         invT, status, max_n);
+  k_patch_gj_tc<W><<<nblocks, gj_tc_threads<W>(), smem, st>>>(lv, status, max_n);
   return true;
+}
+
+bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st) {
+  if (nblocks <= 0 || lv.nlev < 1 || lv.nlev > kGjMaxLevels) return false;
+  if (try_gj_tc<32>(lv, nblocks, max_n, status, st)) return true;
+  return try_gj_tc<16>(lv, nblocks, max_n, status, st);
 }
 
 template <typename T, int W>
@@ -1102,8 +1106,10 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
   if (std::is_same<T, float>::value && n_mult4) {
     float* d = reinterpret_cast<float*>(dense);
     float* o = reinterpret_cast<float*>(invT);
-    if (try_gj_tc<32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
-    if (try_gj_tc<16>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
+    GjLevels lv{};
+    lv.nlev = 1;
+    lv.l[0] = GjLevel{p_n, p_nown, dense_off, own_off, own, inv_off, d, o, 0};
+    if (launch_patch_gj_tc_levels(lv, np, max_n, status, st)) return;
     if (try_gj_f32<32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
     if (try_gj_f32<16>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
   }

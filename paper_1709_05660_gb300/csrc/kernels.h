@@ -59,6 +59,27 @@ void launch_norm_partial(int64_t n, const double* w, double* partial, int nblk, 
 void launch_nonfinite_check(int64_t n, const double* v, int32_t* status, cudaStream_t st);
 
 // k_schwarz.cu (T = double: FP64 path, T = float: mixed path)
+// Schwarz blocks of one level for the tensor-core factorisation; several
+// levels can share one launch (blocks first .. first + n_patches - 1)
+constexpr int kGjMaxLevels = 10;
+struct GjLevel {
+  const int32_t* p_n;
+  const int32_t* p_nown;
+  const int64_t* dense_off;
+  const int64_t* own_off;
+  const int32_t* own;
+  const int64_t* inv_off;
+  float* dense;
+  float* invT;
+  int first;
+};
+struct GjLevels {
+  int nlev;
+  GjLevel l[kGjMaxLevels];
+};
+// false when the blocks do not fit the tensor-core kernel (the caller then
+// factors level by level)
+bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st);
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
                            const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
