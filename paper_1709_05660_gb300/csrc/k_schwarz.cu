@@ -1036,6 +1036,16 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
     for (int q = 0; q < W; ++q) { a0[q] = T(0); a1[q] = T(0); }
     if (v < nvec) {
       int c = c_lo;
+      for (; c + 8 <= c_hi; c += 8) {   // eight column loads in flight per thread
+        typename VT::V bb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bb[u] = __ldg(Bi + (int64_t)(c + u) * nvec + v);
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          VT::fma(a0, bb[u], rs[c + u]);
+          VT::fma(a1, bb[u + 1], rs[c + u + 1]);
+        }
+      }
       for (; c + 4 <= c_hi; c += 4) {
         const typename VT::V b0 = __ldg(Bi + (int64_t)c * nvec + v);
         const typename VT::V b1 = __ldg(Bi + (int64_t)(c + 1) * nvec + v);
