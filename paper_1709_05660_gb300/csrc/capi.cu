@@ -745,9 +745,72 @@ void vcycle_t(Ctx& c, int l, const T* b, T* x) {
   for (int s = 0; s < c.opts.n_post; ++s) smooth_step_t<T>(c, l, b, x, false);
 }
 
+// Records one V-cycle of the finest level, from its own b to its own x
+// buffer (FP32 on the mixed path), as a CUDA graph.  The V-cycle uses the same
+// buffers and launch parameters on every call, so the graph stays valid for
+// the ctx's lifetime; on any capture error the direct launches are used.
+void capture_vcycle(Ctx& c) {
+  const int L = (int)c.dl.size();
+  DevLevel& F = c.dl[L - 1];
+  if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c.cap_stream = nullptr;
+    c.vc_graph_failed = true;
+    return;
+  }
+  const cudaStream_t saved = c.stream;
+  const int64_t l0 = c.launches;
+  c.stream = c.cap_stream;
+  bool ok = cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    try {
+      if (c.mixed) vcycle_t<float>(c, L - 1, F.b32, F.x32);
+      else vcycle_t<double>(c, L - 1, F.b, F.x);
+    } catch (const ApiError&) {
+      ok = false;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(c.cap_stream, &g) != cudaSuccess || !ok || !g) {
+      ok = false;
+      if (g) cudaGraphDestroy(g);
+    } else {
+      c.vc_graph = g;
+      ok = cudaGraphInstantiate(&c.vc_exec, g, 0) == cudaSuccess;
+    }
+  }
+  c.stream = saved;
+  c.vc_launches = c.launches - l0;
+  c.launches = l0;
+  if (!ok) {
+    c.vc_exec = nullptr;
+    c.vc_graph_failed = true;
+    cudaGetLastError();
+  }
+}
+
 // z = M^{-1} v on the finest level (FP64 in and out; FP32 inside on the mixed path)
 void precondition(Ctx& c, const double* v, double* z64, float* z32) {
   const int L = (int)c.dl.size();
+  if (!c.prof && !c.vc_graph_failed) {
+    if (!c.vc_exec) capture_vcycle(c);
+    if (c.vc_exec) {
+      DevLevel& F = c.dl[L - 1];
+      if (c.mixed) {
+        launch_to_f32(F.Ni, v, F.b32, c.stream);
+        counted(c);
+      } else {
+        ck(cudaMemcpyAsync(F.b, v, F.Ni * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "copy");
+      }
+      ck(cudaGraphLaunch(c.vc_exec, c.stream), "cudaGraphLaunch");
+      c.launches += c.vc_launches;
+      if (c.mixed) {
+        if (z32 != F.x32)
+          ck(cudaMemcpyAsync(z32, F.x32, F.Ni * sizeof(float), cudaMemcpyDeviceToDevice, c.stream), "copy");
+      } else if (z64 != F.x) {
+        ck(cudaMemcpyAsync(z64, F.x, F.Ni * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "copy");
+      }
+      return;
+    }
+  }
   if (!c.mixed) {
     vcycle_t<double>(c, L - 1, v, z64);
     return;
@@ -1031,6 +1094,9 @@ void fsi_destroy(fsi_ctx* c) {
       cudaEventDestroy(pr.second);
     }
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  if (c->vc_exec) cudaGraphExecDestroy(c->vc_exec);
+  if (c->vc_graph) cudaGraphDestroy(c->vc_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaGetLastError();
   delete c;
 }

@@ -172,6 +172,13 @@ struct Ctx {
   float t_assemble = 0.f, t_factor = 0.f, t_solve = 0.f;
   int red_blocks = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // the V-cycle as a CUDA graph (captured once on a private stream, replayed
+  // on the ctx stream; not used while per-class profiling is on)
+  cudaGraph_t vc_graph = nullptr;
+  cudaGraphExec_t vc_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int64_t vc_launches = 0;
+  bool vc_graph_failed = false;
   // per-kernel-class profiling
   bool prof = false;
   struct KStat {
