@@ -347,6 +347,9 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
   __shared__ double wP[kNN * kNloc];        // T[i][(b,s)] = sum_a A[i][(a,s)] wP[(b,s)][a]
   __shared__ double wR[kNN * kNloc * 2];    // C[(b,sc)][J] += sum_a sum_h wR[.][a][h] T[(a, sf_h)][J]
   __shared__ uint8_t c_cls[kNloc], c_msk[kNN], f_cls[kNloc], f_msk[kNN];
+  // nonzero entries of each table row (zero weights cost no FP64 work; adding
+  // an exact zero would not change the sums)
+  __shared__ uint8_t nP[kNN], lP[kNN][kNloc], nR[kNN], lR[kNN][2 * kNloc];
   const int E = blockIdx.x;
   const int cx = E % ncx, cy = E / ncx;
   const int fcx = 2 * ncx;
@@ -382,6 +385,18 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
       }
     }
     __syncthreads();
+    if (threadIdx.x < kNN) {
+      const int J = threadIdx.x;
+      int np = 0, nq = 0;
+      for (int a = 0; a < kNloc; ++a) {
+        if (wP[J * kNloc + a] != 0.0) lP[J][np++] = (uint8_t)a;
+        for (int h = 0; h < 2; ++h)
+          if (wR[(J * kNloc + a) * 2 + h] != 0.0) lR[J][nq++] = (uint8_t)(2 * a + h);
+      }
+      nP[J] = (uint8_t)np;
+      nR[J] = (uint8_t)nq;
+    }
+    __syncthreads();
     // T = A_c P_c
     for (int t = threadIdx.x; t < kNdofe * kNdofe; t += blockDim.x) {
       const int i = t / kNdofe, J = t % kNdofe;
@@ -390,8 +405,10 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
       if (J < kNN) {
         const int sl = J % kB;
         const double* w = wP + J * kNloc;
-#pragma unroll
-        for (int a = 0; a < kNloc; ++a) acc += Ai[a * kB + sl] * w[a];
+        for (int q = 0; q < nP[J]; ++q) {
+          const int a = lP[J][q];
+          acc += Ai[a * kB + sl] * w[a];
+        }
       } else {
         const int k = J - kNN;
         // child coefficients: c0 = p0 + sum_d sig_d/2 p_d ; c_d = p_d / 2
@@ -411,9 +428,10 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
       if (I < kNN) {
         const int comp = (I % kB) % kDim;
         const double* w = wR + I * kNloc * 2;
-#pragma unroll
-        for (int a = 0; a < kNloc; ++a)
-          acc += w[2 * a] * sT[(a * kB + comp) * kNdofe + J] + w[2 * a + 1] * sT[(a * kB + kDim + comp) * kNdofe + J];
+        for (int q = 0; q < nR[I]; ++q) {
+          const int ah = lR[I][q], a = ah >> 1, h = ah & 1;
+          acc += w[ah] * sT[(a * kB + h * kDim + comp) * kNdofe + J];
+        }
       } else {
         const int k = I - kNN;
         if (k == 0) acc = sT[kNN * kNdofe + J];
