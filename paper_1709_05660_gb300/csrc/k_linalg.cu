@@ -566,6 +566,7 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
   auto load_l = [&](int64_t k, double (&v)[MR]) {
 #pragma unroll
     for (int m = 0; m < MR; ++m) {
+      if (32 * m >= kl) { v[m] = 0.0; continue; }
       const int64_t r = k + 1 + lane + 32 * m;
       v[m] = (k < n && r <= min(n - 1, k + (int64_t)kl)) ? M[k * n + r] : 0.0;
     }
@@ -582,6 +583,7 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
     if (xk != 0.0) {
 #pragma unroll
       for (int m = 0; m < MR; ++m) {
+        if (32 * m >= kl) break;   // warp-uniform: no issue slots for rows beyond the band
         const int64_t r = k + 1 + lane + 32 * m;
         if (r <= min(n - 1, k + (int64_t)kl)) x[r] -= cur[m] * xk;
       }
@@ -596,6 +598,7 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
     d = k >= 0 ? M[k * n + k] : 1.0;
 #pragma unroll
     for (int m = 0; m < MR; ++m) {
+      if (32 * m >= w) { v[m] = 0.0; continue; }
       const int64_t r = k - 1 - lane - 32 * m;
       v[m] = (k >= 0 && r >= 0 && r >= k - w) ? M[k * n + r] : 0.0;
     }
@@ -610,6 +613,7 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
     if (xk != 0.0) {
 #pragma unroll
       for (int m = 0; m < MR; ++m) {
+        if (32 * m >= w) break;
         const int64_t r = k - 1 - lane - 32 * m;
         if (r >= 0 && r >= k - w) x[r] -= cur[m] * xk;
       }
