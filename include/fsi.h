@@ -22,7 +22,10 @@
  *   ordinary host pointers; the library detects which with
  *   cudaPointerGetAttributes and stages host data through its own buffers.
  *   The caller owns every buffer it passes; the ctx owns everything else.
- * - All device work of a ctx runs on the cudaStream_t given at build time.
+ * - All device work of a ctx is ordered on the cudaStream_t given at build
+ *   time.  fsi_factor_schwarz forks the coarse factorisation onto a private
+ *   stream of the ctx (highest priority) and makes the given stream wait for
+ *   it before the call's own final work, so to the caller it is one stream.
  *   Calls return after that work has completed (they synchronise the stream
  *   whenever a host-side decision or a host output needs it).
  * - Calls on one ctx are not thread safe; distinct ctxs are independent.
@@ -149,7 +152,8 @@ int fsi_assemble_jacobian(fsi_ctx* ctx, double* residual_out);
 /* Factors every Schwarz block B_k = J_l[R^delta_k, R^delta_k] of the levels
  * l >= 1 (partial-pivot Gauss-Jordan; only the owned rows of B_k^{-1} are
  * kept, as the restricted Schwarz update uses nothing else) and the coarse
- * operator J_0 (Sec. 3.3).  FSI_E_SINGULAR on a zero pivot. */
+ * operator J_0 (Sec. 3.3), the two concurrently (they are independent; the
+ * coarse part on the ctx's private stream).  FSI_E_SINGULAR on a zero pivot. */
 int fsi_factor_schwarz(fsi_ctx* ctx);
 
 /* Right-preconditioned FGMRES(restart) on J x = b with the multigrid V-cycle

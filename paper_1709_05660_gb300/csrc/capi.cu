@@ -308,7 +308,7 @@ void build_device(Ctx& c) {
   // coarse dense operator
   const int64_t n0 = c.hl[0].Ni;
   c.c_A = dalloc<double>(c, (size_t)n0 * n0);   // banded LU in dense column-major storage
-  c.c_B = dalloc<double>(c, (size_t)2 * n0);   // pivot-column buffer of the coarse sweep
+  c.c_B = dalloc<double>(c, (size_t)2 * n0);   // reciprocal pivots of the coarse LU
   c.c_piv = dalloc<int32_t>(c, n0);
   c.coarse_slab = c.dim == 3 && !c.hl[0].slab_off.empty();
   if (!c.coarse_slab) {
@@ -544,7 +544,7 @@ double coarse_slab_apply_bytes(const Ctx& c) {
 // ---------------------------------------------------------------------------
 // Schwarz factorisation (all levels >= 1) + coarse LU
 // ---------------------------------------------------------------------------
-void factor(Ctx& c) {
+void schwarz_factor(Ctx& c) {
   const int L = (int)c.dl.size();
   const int B = c.B;
   if (c.mixed && L > 1) {
@@ -598,6 +598,10 @@ void factor(Ctx& c) {
                               D.p_inv_off, c.dense_ws, D.inv, c.status, true, c.stream);
     counted(c, 2);
   }
+}
+
+void coarse_factor(Ctx& c) {
+  const int B = c.B;
   DevLevel& C = c.dl[0];
   const int64_t n0 = C.Ni;
   if (c.coarse_slab) {
@@ -615,6 +619,54 @@ void factor(Ctx& c) {
     if (rc != 0) throw ApiError(FSI_E_CUDA, "banded coarse LU launch failed (" + std::to_string(rc) + ")");
     counted(c, 2);
   }
+}
+
+// Private stream (highest priority) and fork / join events for the coarse
+// factorisation; false if they cannot be created (then everything stays on
+// the ctx stream).
+bool aux_stream(Ctx& c) {
+  if (c.aux_stream) return true;
+  if (c.aux_failed) return false;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (cudaStreamCreateWithPriority(&c.aux_stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    c.aux_failed = true;
+    return false;
+  }
+  return true;
+}
+
+struct StreamSwap {   // launches of the enclosing scope go to another stream
+  Ctx& c;
+  cudaStream_t saved;
+  StreamSwap(Ctx& ctx, cudaStream_t s) : c(ctx), saved(ctx.stream) { c.stream = s; }
+  ~StreamSwap() { c.stream = saved; }
+};
+
+// The coarse LU (level 0) and the Schwarz blocks (levels >= 1) depend only on
+// the assembled operators, not on each other.  The coarse factorisation is a
+// chain of latency-bound launches that fills a fraction of the SMs, so it runs
+// on the private stream while the block factorisations take the rest of the
+// GPU; the ctx stream waits for it before anything that follows.  With
+// per-class profiling on (events on the ctx stream) the two run one after the
+// other.
+void factor(Ctx& c) {
+  const bool fork = !c.prof && aux_stream(c);
+  if (fork) {
+    cudaEventRecord(c.ev_fork, c.stream);
+    cudaStreamWaitEvent(c.aux_stream, c.ev_fork, 0);
+    {
+      StreamSwap sw(c, c.aux_stream);
+      coarse_factor(c);
+    }
+    cudaEventRecord(c.ev_join, c.aux_stream);
+  }
+  schwarz_factor(c);
+  if (fork) cudaStreamWaitEvent(c.stream, c.ev_join, 0);
+  else coarse_factor(c);
   check_status(c);
 }
 
@@ -1097,6 +1149,9 @@ void fsi_destroy(fsi_ctx* c) {
   if (c->vc_exec) cudaGraphExecDestroy(c->vc_exec);
   if (c->vc_graph) cudaGraphDestroy(c->vc_graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   cudaGetLastError();
   delete c;
 }

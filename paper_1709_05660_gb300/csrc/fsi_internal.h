@@ -177,6 +177,11 @@ struct Ctx {
   cudaGraph_t vc_graph = nullptr;
   cudaGraphExec_t vc_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // the coarse factorisation runs on this higher-priority stream beside the
+  // Schwarz factorisation (fork / join events on the ctx stream)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool aux_failed = false;
   int64_t vc_launches = 0;
   bool vc_graph_failed = false;
   // per-kernel-class profiling

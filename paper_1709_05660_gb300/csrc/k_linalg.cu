@@ -434,7 +434,8 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
 // kl + ku).  Factors as in the unblocked band algorithm: multipliers of step j
 // in column j rows j+1..j+kl in the row order of step j (later interchanges are
 // not applied to them), U up to kl + ku above the diagonal, piv[j] the row
-// swapped with j.  Panels of NB columns; per panel two grid barriers instead of NB:
+// swapped with j, rdiag[j] = 1 / U_jj (the reciprocal the step scales its
+// multipliers with; 1 where the pivot is zero, which also flags the status).  Panels of NB columns; per panel two grid barriers instead of NB:
 //  A. block 0 factors the panel (rows k0 .. k0+nb-1+kl) in shared memory with
 //     the unblocked steps, row swaps applied to the panel's columns right of
 //     the step only, and writes panel and pivots back;
@@ -443,7 +444,8 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
 //     trailing column in shared memory: columns k0+nb .. k0+nb-1+kl+ku.
 template <int NB>
 __global__ void __launch_bounds__(128) k_band_lu_blk(int64_t n, int kl, int ku, double* __restrict__ M,
-                                                    int32_t* __restrict__ piv, int32_t* __restrict__ status) {
+                                                    int32_t* __restrict__ piv, double* __restrict__ rdiag,
+                                                    int32_t* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int R = NB + kl;                                  // panel rows (at most)
@@ -487,6 +489,7 @@ __global__ void __launch_bounds__(128) k_band_lu_blk(int64_t n, int kl, int ku, 
           pv = 1.0;
         }
         const double rp = 1.0 / pv;
+        if (threadIdx.x == 0) rdiag[k0 + j] = rp;
         for (int r = j + 1 + threadIdx.x; r <= rhi; r += blockDim.x) P[j * R + r] *= rp;
         __syncthreads();
         const int nrow = rhi - j, ncol = nb - 1 - j;
@@ -551,6 +554,7 @@ size_t band_lu_blk_smem(int kl) { return ((size_t)(NB + kl) * NB + 4 * (size_t)(
 template <int MR>
 __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, const double* __restrict__ M,
                                                      const int32_t* __restrict__ piv,
+                                                     const double* __restrict__ rdiag,
                                                      const int32_t* __restrict__ perm,
                                                      const int32_t* __restrict__ pinv, double* __restrict__ Ainv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -572,9 +576,11 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
     }
   };
   load_l(k_start, cur);
+  int64_t pcur = piv[k_start];
   for (int64_t k = k_start; k < n; ++k) {
     load_l(k + 1, nxt);
-    const int64_t p = piv[k];
+    const int64_t pnxt = k + 1 < n ? piv[k + 1] : 0;
+    const int64_t p = pcur;
     if (p != k) {
       if (lane == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
       __syncwarp();
@@ -591,11 +597,12 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < MR; ++m) cur[m] = nxt[m];
+    pcur = pnxt;
   }
   // backward: rows k - w .. k - 1 of column k (w = kl + ku); lane's m-th row is k - 1 - lane - 32 m
   const int64_t w = (int64_t)kl + ku;
   auto load_u = [&](int64_t k, double (&v)[MR], double& d) {
-    d = k >= 0 ? M[k * n + k] : 1.0;
+    d = k >= 0 ? rdiag[k] : 1.0;
 #pragma unroll
     for (int m = 0; m < MR; ++m) {
       if (32 * m >= w) { v[m] = 0.0; continue; }
@@ -607,7 +614,7 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
   load_u(n - 1, cur, dcur);
   for (int64_t k = n - 1; k >= 0; --k) {
     load_u(k - 1, nxt, dnxt);
-    const double xk = x[k] / dcur;
+    const double xk = x[k] * dcur;   // reciprocal pivot: no FP64 division on the critical chain
     __syncwarp();
     if (lane == 0) x[k] = xk;
     if (xk != 0.0) {
@@ -633,7 +640,8 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
 // the original internal ordering, column-major:
 // Ainv[pinv(c) * n + i] = x[perm[i]].
 __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, const double* __restrict__ M,
-                                                  const int32_t* __restrict__ piv, const int32_t* __restrict__ perm,
+                                                  const int32_t* __restrict__ piv, const double* __restrict__ rdiag,
+                                                  const int32_t* __restrict__ perm,
                                                   const int32_t* __restrict__ pinv, double* __restrict__ Ainv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
@@ -659,7 +667,7 @@ __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, con
   const int64_t w = (int64_t)kl + ku;
   for (int64_t k = n - 1; k >= 0; --k) {
     const double* Uk = M + k * n;
-    if (lane == 0) x[k] /= Uk[k];
+    if (lane == 0) x[k] *= rdiag[k];
     __syncwarp();
     const double xk = x[k];
     if (xk != 0.0) {
@@ -672,14 +680,17 @@ __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, con
   for (int64_t i = lane; i < n; i += kWarp) out[i] = x[perm[i]];
 }
 
-int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbuf, double* Ainv, int32_t* piv,
+int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* rdiag, double* Ainv, int32_t* piv,
                              const int32_t* perm, const int32_t* pinv, int32_t* status, int sm_count,
                              cudaStream_t st) {
-  // blocked LU: 16-column panels when they fit in shared memory, else 8
+  // blocked LU: 16-column panels when they fit in shared memory, else 8.
+  // The kl + ku trailing columns of a panel are spread at about three per
+  // warp: more blocks only add grid-barrier cost and take SMs from the work
+  // that runs beside the coarse factorisation.
   const int threads = 128;
-  int grid = (int)std::min<int64_t>((int64_t)sm_count, n);
+  int grid = (int)std::min(std::min((int64_t)sm_count, n), std::max<int64_t>(8, ((int64_t)kl + ku + 11) / 12));
   if (grid < 1) grid = 1;
-  void* args[] = {(void*)&n, (void*)&kl, (void*)&ku, (void*)&M, (void*)&piv, (void*)&status};
+  void* args[] = {(void*)&n, (void*)&kl, (void*)&ku, (void*)&M, (void*)&piv, (void*)&rdiag, (void*)&status};
   auto go = [&](auto kern, size_t smem) -> int {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -688,7 +699,6 @@ int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbu
     if (cudaLaunchCooperativeKernel((const void*)kern, grid, threads, args, smem, st) != cudaSuccess) return -2;
     return 0;
   };
-  (void)colbuf;
   int rc;
   if (band_lu_blk_smem<16>(kl) <= 200 * 1024) rc = go(k_band_lu_blk<16>, band_lu_blk_smem<16>(kl));
   else if (band_lu_blk_smem<8>(kl) <= 200 * 1024) rc = go(k_band_lu_blk<8>, band_lu_blk_smem<8>(kl));
@@ -701,10 +711,10 @@ int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbu
   const unsigned nblk = (unsigned)((n + wpb - 1) / wpb);
   if ((int64_t)kl + ku <= 32 * 8) {   // narrow band: register prefetch of the next factor column
     cudaFuncSetAttribute(k_band_inv_pf<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-    k_band_inv_pf<8><<<nblk, wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, perm, pinv, Ainv);
+    k_band_inv_pf<8><<<nblk, wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, rdiag, perm, pinv, Ainv);
   } else {
     cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
-    k_band_inv<<<nblk, wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, perm, pinv, Ainv);
+    k_band_inv<<<nblk, wpb * kWarp, ismem, st>>>(n, kl, ku, M, piv, rdiag, perm, pinv, Ainv);
   }
   return 0;
 }

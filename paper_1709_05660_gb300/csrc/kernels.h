@@ -98,7 +98,7 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
 void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const int32_t* pad_list, int npad, const int32_t* perm, int64_t n, double* A,
                          cudaStream_t st);
-int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* colbuf, double* Ainv, int32_t* piv,
+int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* rdiag, double* Ainv, int32_t* piv,
                              const int32_t* perm, const int32_t* pinv, int32_t* status, int sm_count,
                              cudaStream_t st);
 // coarse apply: part holds ceil(n / 32) * n doubles of scratch
