@@ -692,7 +692,7 @@ template <> struct VC<double> {
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes, D.apply_flops);
     launch_patch_apply_t<double>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
                                  D.p_own_off, D.p_own, D.p_inv_off, D.inv, r, x, c.opts.omega, D.dr, D.dc,
-                                 c.stream);
+                                 c.sm_count, c.stream);
     counted(c);
   }
   static void restrict_(Ctx& c, int l, const double* r, double* bc) {
@@ -735,7 +735,7 @@ template <> struct VC<float> {
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes32, D.apply_flops);
     launch_patch_apply_t<float>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
                                 D.p_own_off, D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32,
-                                c.stream);
+                                c.sm_count, c.stream);
     counted(c);
   }
   static void restrict_(Ctx& c, int l, const float* r, float* bc) {

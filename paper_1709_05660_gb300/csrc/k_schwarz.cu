@@ -1131,12 +1131,96 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
                                                 status);
 }
 
+// Row-sliced variant for levels with few patches, where one block per patch
+// leaves most SMs idle and each block streams its inverse alone at the
+// latency of one block: block b applies the owned-row vectors
+// [s vps, (s + 1) vps) of patch b / S (s = b % S) over all n columns.  Its
+// threads form cg column groups of vps lanes; the cg partial sums of each row
+// are added in a fixed order, and the slices write disjoint rows of x, so the
+// result does not depend on scheduling.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_patch_apply_rows(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown,
+                   const int64_t* __restrict__ idx_off, const int32_t* __restrict__ idx,
+                   const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
+                   const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
+                   T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc, int S, int vps,
+                   int cg) {
+  using VT = VecT<T>;
+  constexpr int W = VT::W;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = blockIdx.x / S, s = blockIdx.x % S;
+  const int nown = p_nown[p];
+  const int nvec = own_pad(nown) / W;
+  const int v_lo = s * vps;
+  if (v_lo >= nvec) return;                            // whole block: before any barrier
+  const int v_hi = min(nvec, v_lo + vps);
+  const int n = p_n[p];
+  T* rs = reinterpret_cast<T*>(smem_raw);              // n (padded to 4)
+  const int32_t* id = idx + idx_off[p];
+  const T* Dr = dr + idx_off[p];
+  const T* Dc = dc + idx_off[p];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]] * Dr[i];
+  const int32_t* ow = own + own_off[p];
+  const typename VT::V* Bi = reinterpret_cast<const typename VT::V*>(invT + inv_off[p]);
+  T* partial = rs + ((n + 3) & ~3);                    // cg * vps * W partial sums
+  __syncthreads();
+  const int g = threadIdx.x / vps;
+  const int vt = threadIdx.x % vps;
+  const int v = v_lo + vt;
+  T a0[W], a1[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) { a0[q] = T(0); a1[q] = T(0); }
+  if (g < cg && v < v_hi) {
+    const int c_lo = (int)(((int64_t)n * g) / cg), c_hi = (int)(((int64_t)n * (g + 1)) / cg);
+    int c = c_lo;
+    for (; c + 8 <= c_hi; c += 8) {
+      typename VT::V bb[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) bb[u] = __ldg(Bi + (int64_t)(c + u) * nvec + v);
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        VT::fma(a0, bb[u], rs[c + u]);
+        VT::fma(a1, bb[u + 1], rs[c + u + 1]);
+      }
+    }
+    for (; c < c_hi; ++c) VT::fma(a0, __ldg(Bi + (int64_t)c * nvec + v), rs[c]);
+  }
+  if (g < cg) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) partial[(g * vps + vt) * W + q] = a0[q] + a1[q];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < (v_hi - v_lo) * W; t += blockDim.x) {
+    const int o = v_lo * W + t;
+    if (o < nown) {
+      T sum = T(0);
+      for (int gg = 0; gg < cg; ++gg) sum += partial[gg * vps * W + t];
+      const int k = ow[o];
+      x[id[k]] += omega * Dc[k] * sum;
+    }
+  }
+}
+
 template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
-                          const T* dc, cudaStream_t st) {
+                          const T* dc, int sm_count, cudaStream_t st) {
   if (np <= 0) return;
+  const int nvec_max = own_pad(max_nown) / VecT<T>::W;
+  const int target = 4 * sm_count;            // about one wave of the one-block-per-patch kernel
+  int S = std::max(1, std::min(nvec_max, (target + np - 1) / np));
+  const int vps = (nvec_max + S - 1) / S;
+  if (2 * np < target && S >= 2 && vps <= 256) {
+    S = (nvec_max + vps - 1) / vps;
+    const int cg = std::max(1, std::min(32, 256 / vps));
+    const int threads = vps * cg;
+    const size_t smem = ((size_t)((max_n + 3) & ~3) + (size_t)cg * vps * VecT<T>::W) * sizeof(T);
+    k_patch_apply_rows<T><<<(unsigned)((int64_t)np * S), threads, smem, st>>>(
+        p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x, T(omega), dr, dc, S, vps, cg);
+    return;
+  }
   constexpr int CG = 4;                       // column groups per block
   const int nvec = own_pad(max_nown) / VecT<T>::W;
   int vstride = ((nvec + 31) / 32) * 32;      // threads per column group
@@ -1155,7 +1239,7 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
                                      const int32_t*, const int64_t*, T*, T*, int32_t*, bool, cudaStream_t);     \
   template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \
                                         const int32_t*, const int64_t*, const int32_t*, const int64_t*,        \
-                                        const T*, const T*, T*, double, const T*, const T*, cudaStream_t);
+                                        const T*, const T*, T*, double, const T*, const T*, int, cudaStream_t);
 FSI_INST(double)
 FSI_INST(float)
 #undef FSI_INST

@@ -93,7 +93,7 @@ template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
-                          const T* dc, cudaStream_t st);
+                          const T* dc, int sm_count, cudaStream_t st);
 
 void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const int32_t* pad_list, int npad, const int32_t* perm, int64_t n, double* A,
