@@ -139,6 +139,7 @@ struct Ctx {
   double *y = nullptr, *res = nullptr;
   double *V = nullptr, *Z = nullptr;     // Krylov bases
   float* Z32 = nullptr;                  // preconditioned vectors (mixed path)
+  double* zd = nullptr;                  // one of them widened to FP64 for the operator product
   bool mixed = false;
   double *w = nullptr, *xk = nullptr, *bk = nullptr, *tmp = nullptr;
   double* partial = nullptr;              // reduction partials

@@ -123,16 +123,22 @@ template <> struct BlkRow<double> {   // one row of a 4 x 4 FP64 block
     b = __ldg(reinterpret_cast<const double2*>(p + 2));
   }
   __device__ __forceinline__ void zero() { a = make_double2(0.0, 0.0); b = a; }
-  template <typename TY> __device__ __forceinline__ TY dot(const TY (&x)[4]) const {
-    return TY(a.x) * x[0] + TY(a.y) * x[1] + TY(b.x) * x[2] + TY(b.y) * x[3];
+  template <typename TY> __device__ __forceinline__ void fma_into(TY& acc, const TY (&x)[4]) const {
+    acc = fma(TY(a.x), x[0], acc);
+    acc = fma(TY(a.y), x[1], acc);
+    acc = fma(TY(b.x), x[2], acc);
+    acc = fma(TY(b.y), x[3], acc);
   }
 };
 template <> struct BlkRow<float> {
   float4 a;
   __device__ __forceinline__ void load(const float* p) { a = __ldg(reinterpret_cast<const float4*>(p)); }
   __device__ __forceinline__ void zero() { a = make_float4(0.f, 0.f, 0.f, 0.f); }
-  template <typename TY> __device__ __forceinline__ TY dot(const TY (&x)[4]) const {
-    return TY(a.x) * x[0] + TY(a.y) * x[1] + TY(a.z) * x[2] + TY(a.w) * x[3];
+  template <typename TY> __device__ __forceinline__ void fma_into(TY& acc, const TY (&x)[4]) const {
+    acc = fma(TY(a.x), x[0], acc);
+    acc = fma(TY(a.y), x[1], acc);
+    acc = fma(TY(a.z), x[2], acc);
+    acc = fma(TY(a.w), x[3], acc);
   }
 };
 template <typename TX, typename TY>
@@ -176,8 +182,12 @@ __global__ void __launch_bounds__(256) k_bsr4_residual_sub(int64_t nb, const int
         if (c[u] >= 0) load_x4<TX, TY>(x + (int64_t)c[u] * B, xv[u]);
         else xv[u][0] = xv[u][1] = xv[u][2] = xv[u][3] = TY(0);
       }
+      // four fused multiply-adds per block (FP64: the pipe that bounds this
+      // kernel on GB300); slots past the row's last block are skipped, which
+      // a warp does as a whole when both of its block-rows have ended
 #pragma unroll
-      for (int u = 0; u < R; ++u) acc += v[u].template dot<TY>(xv[u]);
+      for (int u = 0; u < R; ++u)
+        if (c[u] >= 0) v[u].template fma_into<TY>(acc, xv[u]);
     }
   }
 #pragma unroll
@@ -201,17 +211,6 @@ void launch_bsr_residual_f32(int B, int64_t nb, const int32_t* rowptr, const int
   const unsigned grid4 = (unsigned)((n * 4 + 255) / 256);
   if (B == 4) k_bsr4_residual_sub<4, float, float, float><<<grid4, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
   else k_bsr_residual<6, float, float, float><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
-}
-
-void launch_bsr_apply_mixed(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
-                            const float* x, double* y, cudaStream_t st) {
-  const int64_t n = nb * B;
-  const unsigned grid = (unsigned)((n + 255) / 256);
-  const unsigned grid4 = (unsigned)((n * 4 + 255) / 256);
-  if (B == 4)
-    k_bsr4_residual_sub<4, double, float, double><<<grid4, 256, 0, st>>>(nb, rowptr, col, val, x, nullptr, y);
-  else
-    k_bsr_residual<6, double, float, double><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, nullptr, y);
 }
 
 template <typename TV, typename TX, typename TY>

@@ -43,8 +43,6 @@ void launch_bsr_residual(int B, int64_t nb, const int32_t* rowptr, const int32_t
                          const double* x, const double* b, double* y, cudaStream_t st);
 void launch_bsr_residual_f32(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const float* val,
                              const float* x, const float* b, float* y, cudaStream_t st);
-void launch_bsr_apply_mixed(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
-                            const float* x, double* y, cudaStream_t st);
 void launch_csr_spmv(int64_t nrows, const int32_t* ptr, const int32_t* col, const double* val, const double* x,
                      double* y, bool add, cudaStream_t st);
 void launch_gather(int64_t n, const int32_t* map, const double* in, double* out, cudaStream_t st);
