@@ -395,8 +395,8 @@ void assemble(Ctx& c, bool want_res) {
       const int ne = F.color_ptr[g + 1] - F.color_ptr[g];
       (c.dim == 2 ? launch_assemble_2d : launch_assemble_3d)((g & 1) == 1, F.color_list + F.color_ptr[g], ne, c.y,
                                                               F.elem_nodes, F.node_class, F.elem_geo, F.n_nodes, pp,
-                                                              F.Ke, Re, c.status, c.stream);
-      if (ne > 0) counted(c);
+                                                              F.Ke, Re, c.status, c.asm_scratch, c.stream);
+      counted(c, assemble_launches(c.dim, ne));
     }
   }
   {
@@ -1030,6 +1030,14 @@ extern "C" {
 
 // Device bytes fsi_build_hierarchy will allocate for this plan (same sizes as
 // build_device), used for admission by device memory.
+// largest element count of one colour / material group of the finest level
+static int max_color_group(const Ctx& c) {
+  const HostLevel& F = c.hl.back();
+  int m = 0;
+  for (size_t g = 0; g + 1 < F.color_ptr.size(); ++g) m = std::max(m, (int)(F.color_ptr[g + 1] - F.color_ptr[g]));
+  return m;
+}
+
 static int64_t estimate_device_bytes(const Ctx& c) {
   const bool mixed = c.opts.precision == FSI_MIXED;
   const double fs = mixed ? 4.0 : 8.0;
@@ -1054,6 +1062,7 @@ static int64_t estimate_device_bytes(const Ctx& c) {
   b += F.Ni * 8.0 * 2 + (m + 1.0) * F.Ni * 8.0 + m * (double)F.Ni * fs + F.Ni * 8.0 * 4 + F.N * 8.0 * 2;
   if (mixed) b += F.Ni * 8.0;   // the widened preconditioned vector
   if (c.desc.transient != 0) b += F.Ni * 8.0;
+  if (c.dim == 3) b += (double)assemble_3d_scratch_doubles(max_color_group(c)) * 8.0;
   double sum_dense = 0.0;
   for (size_t l = 1; l < L; ++l) sum_dense += (double)c.hl[l].dense_total;
   b += (mixed ? sum_dense : max_dense) * fs + F.n_elem * (double)nd * 8.0 + 1e6;
@@ -1124,6 +1133,7 @@ int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opt
     if (!coop) throw ApiError(FSI_E_CUDA, "device lacks cooperative launch");
     build_device(*c);
     c->tmp_re = dalloc<double>(*c, (size_t)c->hl.back().n_elem * c->ndofe);
+    if (c->dim == 3) c->asm_scratch = dalloc<double>(*c, assemble_3d_scratch_doubles(max_color_group(*c)));
     std::vector<int32_t> pads = coarse_pads(*c);
     c->coarse_pad_list = upload(*c, pads);
     c->n_coarse_pads = (int)pads.size();

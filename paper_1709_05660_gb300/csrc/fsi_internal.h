@@ -140,6 +140,7 @@ struct Ctx {
   double *V = nullptr, *Z = nullptr;     // Krylov bases
   float* Z32 = nullptr;                  // preconditioned vectors (mixed path)
   double* zd = nullptr;                  // one of them widened to FP64 for the operator product
+  double* asm_scratch = nullptr;         // 3D assembly: flux derivatives of one chunk of elements
   bool mixed = false;
   double *w = nullptr, *xk = nullptr, *bk = nullptr, *tmp = nullptr;
   double* partial = nullptr;              // reduction partials

@@ -521,33 +521,42 @@ __device__ __forceinline__ int row_kind3(int cls, int slot) {
 }
 }  // namespace
 
-size_t assemble_3d_smem() {
-  return ((size_t)k3Ndofe * k3Ndofe + k3Ndofe + k3NN + k3Nloc * 4 + k3Fields + 1) * sizeof(double);
+// As in 2D, the fluxes at a quadrature point depend on the element unknowns
+// only through the fields (grad d 9, grad u 9, u 3, d 3, p 1: 25 directions
+// against 166 unknowns).  k_flux_3d evaluates them along the 25 directions in
+// dual arithmetic (27 x 25 = 675 evaluations per element) and stores the
+// derivatives and values of the 22 flux outputs; k_assemble_3d then builds
+// column j of the exact element Jacobian by the chain rule through the basis
+// coefficients of unknown j (its value and three gradient components, or psi
+// for a pressure unknown) and the test functions.  The 166 x 166 element
+// matrix fills shared memory, so the flux derivatives (119 KB per element)
+// pass through a global scratch, one chunk of elements at a time.
+namespace {
+constexpr int k3Q = 27;
+constexpr int k3NF = 25;   // differentiated fields (fv indices 0..24)
+constexpr int k3NO = 22;   // outputs: 0..8 T_ck (3 c + k) | 9..11 convection / inertia_c |
+                           // solid 12..14 kinematic_c, fluid 12..20 ALE A_ck (12 + 3 c + k) | 21 mass
+constexpr size_t k3FluxDoubles = (size_t)k3Q * k3NF * k3NO + (size_t)k3Q * k3NO;   // per element
+constexpr int k3Chunk = 1024;                                                      // elements per pass
+}  // namespace
+
+size_t assemble_3d_smem() { return ((size_t)k3Ndofe * k3Ndofe + k3Nloc * 4) * sizeof(double); }
+
+size_t assemble_3d_scratch_doubles(int max_ne) {
+  return (size_t)std::min(max_ne, k3Chunk) * k3FluxDoubles;
 }
 
-// One thread block per element; thread j < 166 differentiates along unknown j
-// (forward-mode dual seeded with e_j) and owns column j of the 166 x 166
-// element Jacobian, which is accumulated in shared memory (no two threads
-// write the same entry).  Per quadrature point the basis table and the field
-// values are computed once by the block and shared.
+// fields at the 27 points, then flux values and derivatives along each field
 template <bool SOLID, bool TRANS>
-__global__ void __launch_bounds__(192)
-k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
-              const int32_t* __restrict__ elem_nodes, const uint8_t* __restrict__ node_class,
-              const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp,
-              double* __restrict__ Ke, double* __restrict__ Re, int32_t* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* K = reinterpret_cast<double*>(smem_raw);   // [i][j]
-  double* ye = K + k3Ndofe * k3Ndofe;
-  double* yo = ye + k3Ndofe;
-  double* bt = yo + k3NN;                             // per node: N, Gx, Gy, Gz
-  double* fv = bt + k3Nloc * 4;
+__global__ void __launch_bounds__(256)
+k_flux_3d(const int32_t* __restrict__ elems, const double* __restrict__ y, const int32_t* __restrict__ elem_nodes,
+          const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp, double* __restrict__ Dg,
+          int32_t* __restrict__ status) {
+  __shared__ double ye[k3Ndofe], yo[k3NN];
+  __shared__ double bt[k3Q][k3Nloc][4];   // physical basis: N, d/dx, d/dy, d/dz
+  __shared__ double fvs[k3Q][k3Fields];
   __shared__ double geo[2 * k3Dim];
-  __shared__ unsigned s_iface;
-  __shared__ int s_tangled;
   const int e = elems[blockIdx.x];
-  const int j = threadIdx.x;
-  for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) K[t] = 0.0;
   for (int t = threadIdx.x; t < k3Ndofe; t += blockDim.x) {
     if (t < k3NN) {
       const int64_t gi = (int64_t)elem_nodes[(int64_t)e * k3Nloc + t / k3B] * k3B + t % k3B;
@@ -558,27 +567,181 @@ k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
     }
   }
   if (threadIdx.x < 2 * k3Dim) geo[threadIdx.x] = elem_geo[(int64_t)e * 2 * k3Dim + threadIdx.x];
+  __syncthreads();
+  const double hx = geo[3], hy = geo[4], hz = geo[5];
+  const double vol = hx * hy * hz;
+  const double kale = 1.0 / vol;
+  for (int t = threadIdx.x; t < k3Q * k3Nloc; t += blockDim.x) {
+    const int q = t / k3Nloc, a = t % k3Nloc;
+    const double xi = gp(q % 3), eta = gp((q / 3) % 3), zeta = gp(q / 9);
+    const int ia = a % 3, ja = (a / 3) % 3, ka = a / 9;
+    const double lx = L1(ia, xi), ly = L1(ja, eta), lz = L1(ka, zeta);
+    bt[q][a][0] = lx * ly * lz;
+    bt[q][a][1] = dL1(ia, xi) * ly * lz * (2.0 / hx);
+    bt[q][a][2] = lx * dL1(ja, eta) * lz * (2.0 / hy);
+    bt[q][a][3] = lx * ly * dL1(ka, zeta) * (2.0 / hz);
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < k3Q * k3Fields; it += blockDim.x) {
+    const int q = it / k3Fields, t = it % k3Fields;
+    double acc = 0.0;
+    if (t < 18) {           // gd (t < 9) and gu: d_i / dx_k of d or u
+      const int i = (t % 9) / 3, k = t % 3, off = t < 9 ? 0 : 3;
+      for (int a = 0; a < k3Nloc; ++a) acc += ye[a * k3B + off + i] * bt[q][a][1 + k];
+    } else if (t < 24) {    // u (18..20), d (21..23)
+      const int i = (t - 18) % 3, off = t < 21 ? 3 : 0;
+      for (int a = 0; a < k3Nloc; ++a) acc += ye[a * k3B + off + i] * bt[q][a][0];
+    } else if (t == 24) {   // pressure
+      acc = ye[k3NN] + ye[k3NN + 1] * gp(q % 3) + ye[k3NN + 2] * gp((q / 3) % 3) + ye[k3NN + 3] * gp(q / 9);
+    } else if (TRANS) {     // u_old (25..27), d_old (28..30)
+      const int i = (t - 25) % 3, off = t < 28 ? 3 : 0;
+      for (int a = 0; a < k3Nloc; ++a) acc += yo[a * k3B + off + i] * bt[q][a][0];
+    }
+    fvs[q][t] = acc;
+  }
+  __syncthreads();
+  double* De = Dg + (size_t)blockIdx.x * k3FluxDoubles;   // [q][f][o], then values [q][o]
+  double* Ve = De + (size_t)k3Q * k3NF * k3NO;
+  bool tangled = false;
+#pragma unroll 1
+  for (int it = threadIdx.x; it < k3Q * k3NF; it += blockDim.x) {
+    const int q = it / k3NF, f = it % k3NF;
+    double* dout = De + (size_t)(q * k3NF + f) * k3NO;
+    if (!TRANS && f >= 21 && f < 24) {   // d itself enters only the BDF terms
+      for (int o = 0; o < k3NO; ++o) dout[o] = 0.0;
+      continue;
+    }
+    const double* fv = fvs[q];
+    const double wq = gw(q % 3) * gw((q / 3) % 3) * gw(q / 9) * vol * 0.125;
+    Dual gd[3][3], u[3], ut[3], dt_[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gd[i][k] = mk(fv[i * 3 + k], f == i * 3 + k ? 1.0 : 0.0);
+      u[i] = mk(fv[18 + i], f == 18 + i ? 1.0 : 0.0);
+      if (TRANS) {
+        const Dual di = mk(fv[21 + i], f == 21 + i ? 1.0 : 0.0);
+        ut[i] = (u[i] * pp.a0 + fv[25 + i]) * pp.idt;
+        dt_[i] = (di * pp.a0 + fv[28 + i]) * pp.idt;
+      }
+    }
+    const Dual p = mk(fv[24], f == 24 ? 1.0 : 0.0);
+    Dual F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) F[i][k] = i == k ? gd[i][k] + 1.0 : gd[i][k];
+    Dual C[3][3];   // cofactors
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        C[i][k] = F[i1][k1] * F[i2][k2] - F[i1][k2] * F[i2][k1];
+      }
+    const Dual J = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
+    if (!(J.v > 0.0)) tangled = true;
+    const double iJ = 1.0 / J.v;
+    const Dual rJ = mk(iJ, -J.d * iJ * iJ);   // 1 / J
+    Dual Fi[3][3];   // F^{-1} = C^T / J
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Fi[i][k] = C[k][i] * rJ;
+    Dual out[k3NO];
+#pragma unroll
+    for (int o = 0; o < k3NO; ++o) out[o] = mk(0.0, 0.0);
+    if (SOLID) {
+      const Dual pJ = p * J;
+      const Dual muJ = J * pp.mu_s;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[3 * c + k] = (muJ * F[c][k] - pJ * Fi[k][c]) * wq;
+        if (TRANS) out[9 + c] = ut[c] * J * (pp.rho_s * wq);
+        out[12 + c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
+      }
+      out[21] = (J + (-1.0)) * wq;
+    } else {
+      Dual gx[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const Dual gu0 = mk(fv[9 + i * 3 + 0], f == 9 + i * 3 + 0 ? 1.0 : 0.0);
+          const Dual gu1 = mk(fv[9 + i * 3 + 1], f == 9 + i * 3 + 1 ? 1.0 : 0.0);
+          const Dual gu2 = mk(fv[9 + i * 3 + 2], f == 9 + i * 3 + 2 ? 1.0 : 0.0);
+          gx[i][k] = gu0 * Fi[0][k] + gu1 * Fi[1][k] + gu2 * Fi[2][k];
+        }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Dual sig[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          sig[m] = (gx[c][m] + gx[m][c]) * pp.mu_f;
+          if (m == c) sig[m] = sig[m] - p;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[3 * c + k] = (sig[0] * Fi[k][0] + sig[1] * Fi[k][1] + sig[2] * Fi[k][2]) * J * wq;
+        const Dual cv = TRANS
+                            ? gx[c][0] * (u[0] - dt_[0]) + gx[c][1] * (u[1] - dt_[1]) + gx[c][2] * (u[2] - dt_[2]) + ut[c]
+                            : gx[c][0] * u[0] + gx[c][1] * u[1] + gx[c][2] * u[2];
+        out[9 + c] = cv * J * (pp.rho_f * wq);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          out[12 + 3 * c + k] = (pp.ale_op == 0 ? gd[c][k] + gd[k][c] : gd[c][k]) * (kale * wq);
+      }
+      out[21] = J * (gx[0][0] + gx[1][1] + gx[2][2]) * wq;
+    }
+#pragma unroll
+    for (int o = 0; o < k3NO; ++o) dout[o] = out[o].d;
+    if (f == 24) {   // any direction carries the values
+#pragma unroll
+      for (int o = 0; o < k3NO; ++o) Ve[q * k3NO + o] = out[o].v;
+    }
+  }
+  if (tangled) atomicExch(&status[ST_TANGLED], 1);
+}
+
+// One thread block per element; thread j < 166 owns column j of the 166 x 166
+// element Jacobian, accumulated in shared memory (no two threads write the
+// same entry), and the value of residual row j.
+template <bool SOLID>
+__global__ void __launch_bounds__(192)
+k_assemble_3d(const int32_t* __restrict__ elems, const int32_t* __restrict__ elem_nodes,
+              const uint8_t* __restrict__ node_class, const double* __restrict__ elem_geo,
+              const double* __restrict__ Dg, double* __restrict__ Ke, double* __restrict__ Re) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* K = reinterpret_cast<double*>(smem_raw);   // [i][j]
+  double* bt = K + k3Ndofe * k3Ndofe;                 // per node: N, Gx, Gy, Gz
+  __shared__ double geo[2 * k3Dim];
+  __shared__ unsigned s_iface;
+  const int e = elems[blockIdx.x];
+  const int j = threadIdx.x;
+  for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) K[t] = 0.0;
+  if (threadIdx.x < 2 * k3Dim) geo[threadIdx.x] = elem_geo[(int64_t)e * 2 * k3Dim + threadIdx.x];
   if (threadIdx.x == 0) {
     unsigned m = 0;
     for (int a = 0; a < k3Nloc; ++a)
       if (node_class[elem_nodes[(int64_t)e * k3Nloc + a]] == kIface) m |= 1u << a;
     s_iface = m;
-    s_tangled = 0;
   }
   __syncthreads();
   const double hx = geo[3], hy = geo[4], hz = geo[5];
-  const double vol = hx * hy * hz;
-  const double kale = 1.0 / vol;
   const unsigned iface = s_iface;
   const bool act = j < k3Ndofe;
   const int aj = (act && j < k3NN) ? j / k3B : -1;
   const int sj = (act && j < k3NN) ? j % k3B : -1;
   const int pk = (act && j >= k3NN) ? j - k3NN : -1;
+  // the fields unknown j moves: value and gradient of its component, or p
+  const int ci = sj >= 3 ? sj - 3 : sj;
+  const int f_val = sj < 0 ? 24 : (sj < 3 ? 21 + ci : 18 + ci);
+  const int f_grad = sj < 3 ? 3 * ci : 9 + 3 * ci;
+  const double* De = Dg + (size_t)blockIdx.x * k3FluxDoubles;
+  const double* Ve = De + (size_t)k3Q * k3NF * k3NO;
   double vj = 0.0;
-  for (int q = 0; q < 27; ++q) {
-    const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-    const double xi = gp(qx), eta = gp(qy), zeta = gp(qz);
-    const double wq = gw(qx) * gw(qy) * gw(qz) * vol * 0.125;
+  for (int q = 0; q < k3Q; ++q) {
+    const double xi = gp(q % 3), eta = gp((q / 3) % 3), zeta = gp(q / 9);
     if (threadIdx.x < k3Nloc) {
       const int a = threadIdx.x, ia = a % 3, ja = (a / 3) % 3, ka = a / 9;
       const double lx = L1(ia, xi), ly = L1(ja, eta), lz = L1(ka, zeta);
@@ -588,156 +751,68 @@ k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
       bt[a * 4 + 3] = lx * ly * dL1(ka, zeta) * (2.0 / hz);
     }
     __syncthreads();
-    if (threadIdx.x < k3Fields) {
-      const int t = threadIdx.x;
-      double acc = 0.0;
-      if (t < 18) {           // gd (t < 9) and gu: d_i / dx_k of d or u
-        const int i = (t % 9) / 3, k = t % 3, off = t < 9 ? 0 : 3;
-        for (int a = 0; a < k3Nloc; ++a) acc += ye[a * k3B + off + i] * bt[a * 4 + 1 + k];
-      } else if (t < 24) {    // u (18..20), d (21..23)
-        const int i = (t - 18) % 3, off = t < 21 ? 3 : 0;
-        for (int a = 0; a < k3Nloc; ++a) acc += ye[a * k3B + off + i] * bt[a * 4];
-      } else if (t == 24) {   // pressure
-        acc = ye[k3NN] + ye[k3NN + 1] * xi + ye[k3NN + 2] * eta + ye[k3NN + 3] * zeta;
-      } else {                // u_old (25..27), d_old (28..30)
-        const int i = (t - 25) % 3, off = t < 28 ? 3 : 0;
-        for (int a = 0; a < k3Nloc; ++a) acc += yo[a * k3B + off + i] * bt[a * 4];
-      }
-      fv[t] = acc;
-    }
-    __syncthreads();
     if (act) {
-      const double nj = aj >= 0 ? bt[aj * 4] : 0.0;
-      double gj[3];
+      const double* dq = De + (size_t)q * k3NF * k3NO;
+      const double* vq = Ve + (size_t)q * k3NO;
+      double dj[k3NO];
+      double nj = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+      if (pk < 0) {
+        nj = bt[aj * 4];
+        g0 = bt[aj * 4 + 1];
+        g1 = bt[aj * 4 + 2];
+        g2 = bt[aj * 4 + 3];
+        const double* d0 = dq + f_val * k3NO;
+        const double* d1 = dq + f_grad * k3NO;
+        const double* d2 = d1 + k3NO;
+        const double* d3 = d2 + k3NO;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) gj[k] = aj >= 0 ? bt[aj * 4 + 1 + k] : 0.0;
-      const double psi[4] = {1.0, xi, eta, zeta};
-      Dual gd[3][3], u[3], ut[3], dt_[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) gd[i][k] = mk(fv[i * 3 + k], sj == i ? gj[k] : 0.0);
-        u[i] = mk(fv[18 + i], sj == 3 + i ? nj : 0.0);
-        ut[i] = mk((pp.a0 * fv[18 + i] + fv[25 + i]) * pp.idt, sj == 3 + i ? pp.a0 * pp.idt * nj : 0.0);
-        dt_[i] = mk((pp.a0 * fv[21 + i] + fv[28 + i]) * pp.idt, sj == i ? pp.a0 * pp.idt * nj : 0.0);
-      }
-      const Dual p = mk(fv[24], pk == 0 ? 1.0 : (pk == 1 ? xi : (pk == 2 ? eta : (pk == 3 ? zeta : 0.0))));
-      Dual F[3][3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) F[i][k] = i == k ? gd[i][k] + 1.0 : gd[i][k];
-      Dual C[3][3];   // cofactors
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-          C[i][k] = F[i1][k1] * F[i2][k2] - F[i1][k2] * F[i2][k1];
-        }
-      const Dual J = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
-      if (!(J.v > 0.0)) s_tangled = 1;
-      Dual Fi[3][3];   // F^{-1} = C^T / J
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Fi[i][k] = C[k][i] / J;
-      Dual mass;
-      if (SOLID) {
-        const Dual pJ = p * J;
-        const Dual muJ = J * pp.mu_s;
-        Dual T[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) T[i][k] = (muJ * F[i][k] - pJ * Fi[k][i]) * wq;
-        Dual inert[3], kin[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          inert[c] = TRANS ? ut[c] * J * (pp.rho_s * wq) : mk(0.0, 0.0);
-          kin[c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
-        }
-        // derivative parts for column j; the value part only for this
-        // thread's own residual row j
-        for (int a = 0; a < k3Nloc; ++a) {
-          const double Na = bt[a * 4], G0 = bt[a * 4 + 1], G1 = bt[a * 4 + 2], G2 = bt[a * 4 + 3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const int rd = a * k3B + c, ru = a * k3B + 3 + c;
-            K[rd * k3Ndofe + j] += T[c][0].d * G0 + T[c][1].d * G1 + T[c][2].d * G2 + inert[c].d * Na;
-            K[ru * k3Ndofe + j] += kin[c].d * Na;
-          }
-        }
-        if (aj >= 0) {
-          const double Na = bt[aj * 4], G0 = bt[aj * 4 + 1], G1 = bt[aj * 4 + 2], G2 = bt[aj * 4 + 3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {   // unrolled select: no dynamic register-array index
-            if (sj == c) vj += T[c][0].v * G0 + T[c][1].v * G1 + T[c][2].v * G2 + inert[c].v * Na;
-            if (sj == 3 + c) vj += kin[c].v * Na;
-          }
-        }
-        mass = J + (-1.0);
+        for (int o = 0; o < k3NO; ++o) dj[o] = d0[o] * nj + d1[o] * g0 + d2[o] * g1 + d3[o] * g2;
       } else {
-        Dual gx[3][3];
+        const double ps = pk == 0 ? 1.0 : (pk == 1 ? xi : (pk == 2 ? eta : zeta));
+        const double* d0 = dq + 24 * k3NO;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const Dual gu0 = mk(fv[9 + i * 3 + 0], sj == 3 + i ? gj[0] : 0.0);
-            const Dual gu1 = mk(fv[9 + i * 3 + 1], sj == 3 + i ? gj[1] : 0.0);
-            const Dual gu2 = mk(fv[9 + i * 3 + 2], sj == 3 + i ? gj[2] : 0.0);
-            gx[i][k] = gu0 * Fi[0][k] + gu1 * Fi[1][k] + gu2 * Fi[2][k];
-          }
-        Dual T[3][3], conv[3], A[3][3];
+        for (int o = 0; o < k3NO; ++o) dj[o] = d0[o] * ps;
+      }
+      for (int a = 0; a < k3Nloc; ++a) {
+        const double Na = bt[a * 4], G0 = bt[a * 4 + 1], G1 = bt[a * 4 + 2], G2 = bt[a * 4 + 3];
+        const bool ifc = (iface >> a) & 1u;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          Dual sig[3];
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            sig[m] = (gx[c][m] + gx[m][c]) * pp.mu_f;
-            if (m == c) sig[m] = sig[m] - p;
-          }
-#pragma unroll
-          for (int k = 0; k < 3; ++k) T[c][k] = (sig[0] * Fi[k][0] + sig[1] * Fi[k][1] + sig[2] * Fi[k][2]) * J * wq;
-          Dual cv = TRANS
-                        ? gx[c][0] * (u[0] - dt_[0]) + gx[c][1] * (u[1] - dt_[1]) + gx[c][2] * (u[2] - dt_[2]) + ut[c]
-                        : gx[c][0] * u[0] + gx[c][1] * u[1] + gx[c][2] * u[2];
-          conv[c] = cv * J * (pp.rho_f * wq);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) A[c][k] = (pp.ale_op == 0 ? gd[c][k] + gd[k][c] : gd[c][k]) * (kale * wq);
-        }
-        for (int a = 0; a < k3Nloc; ++a) {
-          const double Na = bt[a * 4], G0 = bt[a * 4 + 1], G1 = bt[a * 4 + 2], G2 = bt[a * 4 + 3];
-          const bool ifc = (iface >> a) & 1u;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const double md = T[c][0].d * G0 + T[c][1].d * G1 + T[c][2].d * G2 + conv[c].d * Na;
-            const int rd = a * k3B + c, ru = a * k3B + 3 + c;
-            if (ifc) {
-              K[rd * k3Ndofe + j] += md;
-            } else {
-              K[rd * k3Ndofe + j] += A[c][0].d * G0 + A[c][1].d * G1 + A[c][2].d * G2;
-              K[ru * k3Ndofe + j] += md;
-            }
+          const double md = dj[3 * c] * G0 + dj[3 * c + 1] * G1 + dj[3 * c + 2] * G2 + dj[9 + c] * Na;
+          const int rd = a * k3B + c, ru = a * k3B + 3 + c;
+          if (SOLID) {
+            K[rd * k3Ndofe + j] += md;
+            K[ru * k3Ndofe + j] += dj[12 + c] * Na;
+          } else if (ifc) {
+            // interface node: momentum in the d-row, no ALE row (psi = 0 on the interface)
+            K[rd * k3Ndofe + j] += md;
+          } else {
+            // fluid node: ALE in the d-row, momentum in the u-row
+            K[rd * k3Ndofe + j] += dj[12 + 3 * c] * G0 + dj[13 + 3 * c] * G1 + dj[14 + 3 * c] * G2;
+            K[ru * k3Ndofe + j] += md;
           }
         }
-        if (aj >= 0) {
-          const double Na = bt[aj * 4], G0 = bt[aj * 4 + 1], G1 = bt[aj * 4 + 2], G2 = bt[aj * 4 + 3];
-          const bool ifc = (iface >> aj) & 1u;
+      }
+      K[k3NN * k3Ndofe + j] += dj[21];
+      K[(k3NN + 1) * k3Ndofe + j] += dj[21] * xi;
+      K[(k3NN + 2) * k3Ndofe + j] += dj[21] * eta;
+      K[(k3NN + 3) * k3Ndofe + j] += dj[21] * zeta;
+      // residual row j from the flux values
+      if (pk < 0) {
+        const bool ifc = (iface >> aj) & 1u;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const double mv = T[c][0].v * G0 + T[c][1].v * G1 + T[c][2].v * G2 + conv[c].v * Na;
-            if (sj == c) vj += ifc ? mv : A[c][0].v * G0 + A[c][1].v * G1 + A[c][2].v * G2;
+        for (int c = 0; c < 3; ++c) {   // unrolled select: no dynamic register-array index
+          const double mv = vq[3 * c] * g0 + vq[3 * c + 1] * g1 + vq[3 * c + 2] * g2 + vq[9 + c] * nj;
+          if (SOLID) {
+            if (sj == c) vj += mv;
+            if (sj == 3 + c) vj += vq[12 + c] * nj;
+          } else {
+            if (sj == c) vj += ifc ? mv : vq[12 + 3 * c] * g0 + vq[13 + 3 * c] * g1 + vq[14 + 3 * c] * g2;
             if (sj == 3 + c && !ifc) vj += mv;
           }
         }
-        mass = J * (gx[0][0] + gx[1][1] + gx[2][2]);
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const Dual t = mass * (psi[k] * wq);
-        K[(k3NN + k) * k3Ndofe + j] += t.d;
-        if (k3NN + k == j) vj += t.v;
+      } else {
+        vj += vq[21] * (pk == 0 ? 1.0 : (pk == 1 ? xi : (pk == 2 ? eta : zeta)));
       }
     }
     __syncthreads();
@@ -745,7 +820,6 @@ k_assemble_3d(const int32_t* __restrict__ elems, const double* __restrict__ y,
   double* Kg = Ke + (int64_t)e * k3Ndofe * k3Ndofe;
   for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) Kg[t] = K[t];
   if (act) Re[(int64_t)e * k3Ndofe + j] = vj;
-  if (threadIdx.x == 0 && s_tangled) atomicExch(&status[ST_TANGLED], 1);
 }
 
 // coloured scatter of 3D element matrices (B = 6)
@@ -915,7 +989,8 @@ k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const in
 // ---------------------------------------------------------------------------
 void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, cudaStream_t st) {
+                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st) {
+  (void)scratch;
   if (ne <= 0) return;
   const int grid = (ne + kEPB - 1) / kEPB;
   const size_t smem = (size_t)kEPB * kAsmElemDoubles * sizeof(double);
@@ -957,18 +1032,25 @@ namespace fsi {
 
 void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, cudaStream_t st) {
+                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st) {
   if (ne <= 0) return;
   const size_t smem = assemble_3d_smem();
-  auto go = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<ne, 192, smem, st>>>(elems, y, elem_nodes, node_class, elem_geo, n_nodes, pp, Ke, Re, status);
+  auto go = [&](auto flux, auto cols) {
+    cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int e0 = 0; e0 < ne; e0 += k3Chunk) {
+      const int nc = std::min(k3Chunk, ne - e0);
+      flux<<<nc, 256, 0, st>>>(elems + e0, y, elem_nodes, elem_geo, n_nodes, pp, scratch, status);
+      cols<<<nc, 192, smem, st>>>(elems + e0, elem_nodes, node_class, elem_geo, scratch, Ke, Re);
+    }
   };
   if (solid)
-    pp.transient ? go(k_assemble_3d<true, true>) : go(k_assemble_3d<true, false>);
+    pp.transient ? go(k_flux_3d<true, true>, k_assemble_3d<true>) : go(k_flux_3d<true, false>, k_assemble_3d<true>);
   else
-    pp.transient ? go(k_assemble_3d<false, true>) : go(k_assemble_3d<false, false>);
+    pp.transient ? go(k_flux_3d<false, true>, k_assemble_3d<false>)
+                 : go(k_flux_3d<false, false>, k_assemble_3d<false>);
 }
+
+int assemble_launches(int dim, int ne) { return dim == 2 || ne <= 0 ? (ne > 0) : 2 * ((ne + k3Chunk - 1) / k3Chunk); }
 
 void launch_scatter_3d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
                        const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st) {

@@ -19,12 +19,15 @@ struct PhysParams {
 };
 
 // k_assemble.cu
+// scratch: 3D only, assemble_3d_scratch_doubles(largest ne of one launch) doubles (2D: unused)
 void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, cudaStream_t st);
+                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st);
 void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, cudaStream_t st);
+                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st);
+size_t assemble_3d_scratch_doubles(int max_ne);
+int assemble_launches(int dim, int ne);   // kernel launches of one launch_assemble_* call
 void launch_scatter_3d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
                        const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st);
 void launch_galerkin_3d(int ncx, int ncy, int ncz, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
