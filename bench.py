@@ -278,7 +278,7 @@ def _measure(args, prec, stream, barrier, dist, world, local):
     out = {"N": N, "ms": ms, "per_step": ms / args.steps, "value": world * args.steps / (ms / 1e3),
            "profiled_ms_per_step": ms_prof / args.steps,
            "iters": iters, "rel_res": max(rel_res), "rel_step": rel, "kst": kst, "launches": launches,
-           "clocks": clk, "hbm_bytes": s.hbm_bytes,
+           "clocks": clk, "hbm_bytes": s.hbm_bytes, "tuned": s.tuning is not None,
            "phase_ms": {"assemble": st.t_assemble_ms, "factor": st.t_factor_ms, "solve": st.t_solve_ms}}
     # end-to-end through the C-ABI with host buffers (pinned), copies inside the timed region
     yh = y0.cpu().pin_memory()
@@ -430,7 +430,9 @@ def run_gpu(args, rank, world):
                        "rtol": opts.rtol, "smoothing": [opts.n_pre, opts.n_post], "omega": opts.omega,
                        "precision": "mixed: FP32 V-cycle and Schwarz inverses, FP64 FGMRES / SpMV / coarse LU",
                        "l2": f"working set {main['hbm_bytes'] / 1e9:.2f} GB > L2 (129 MB); no flush",
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "launch_shapes": ("autotuned (paper_1709_05660_gb300/tuning.json)" if main["tuned"]
+                                         else "built-in")},
             "fgmres_iters": main["iters"], "max_true_rel_residual": main["rel_res"], "rel_step": main["rel_step"],
             "phase_ms": main["phase_ms"], "roofline": roof, "kernel_classes": classes,
             "kernel_classes_pass": "a second timed pass of the same steps with per-class CUDA events "

@@ -252,6 +252,39 @@ int fsi_set_profiling(fsi_ctx* ctx, int on);
 int fsi_kernel_stats(fsi_ctx* ctx, int kind, double* device_ms, int64_t* launches, double* alg_bytes,
                      double* alg_flops);
 
+/* ---- launch parameters and their autotuner (no counterpart in the paper) --
+ *
+ * Launch shapes of one level's kernels.  They change how work is mapped to
+ * threads, and with it the rounding order of sums, never what is computed.
+ * A zero field keeps the built-in choice.
+ *   apply_slices  Schwarz apply (the smoother's restricted update): 1 = one
+ *                 thread block per Schwarz block; s >= 2 = the owned rows of
+ *                 every block split over s thread blocks (capped at the
+ *                 number of 4-row vectors).
+ *   apply_groups  with row slices: column groups per thread block (1..256,
+ *                 capped so a block has at most 256 threads).
+ *   spmv_sub      threads per scalar row of the level's block-sparse residual
+ *                 in the V-cycle (mixed path; B = 4 blocks): 2, 4 or 8.
+ *   gj_panel      panel width of the tensor-core Gauss-Jordan of the Schwarz
+ *                 blocks (16 or 32).  One launch factors every level, so only
+ *                 the value set on the finest level counts.
+ * The values are a property of the ctx; setting them waits for the ctx's
+ * stream and drops the recorded V-cycle graph, which is recorded again at the
+ * next solve.  FSI_E_INVALID for a bad level or out-of-range values. */
+typedef struct {
+  int32_t apply_slices, apply_groups, spmv_sub, gj_panel;
+} fsi_launch_params;
+int fsi_set_launch_params(fsi_ctx* ctx, int level, const fsi_launch_params* params);
+/* The shapes in effect on `level` (the built-in choice resolved). */
+int fsi_get_launch_params(fsi_ctx* ctx, int level, fsi_launch_params* out);
+/* Device time (CUDA events on the ctx stream) of one launch of the level's
+ * Schwarz apply and of its block-sparse residual, averaged over `reps`
+ * launches each, in the ctx's V-cycle precision and launch shapes.  Runs on
+ * the level's own work vectors (set to zero first; their contents are lost).
+ * Needs a prior fsi_factor_schwarz; FSI_E_INVALID otherwise or for reps
+ * outside [1, 10000]. */
+int fsi_time_level_kernels(fsi_ctx* ctx, int level, int reps, double* apply_ms, double* spmv_ms);
+
 /* ---- serving: continuous batching of Newton-step requests ---------------
  *
  * A server owns `max_slots` worker threads, each with its own CUDA stream, and

@@ -582,7 +582,7 @@ void schwarz_factor(Ctx& c) {
         max_n = std::max(max_n, D.max_n);
       }
     }
-    if (lv.nlev == L - 1 && launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream)) {
+    if (lv.nlev == L - 1 && launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream, c.gj_panel)) {
       counted(c);
     } else {
       for (int l = 1; l < L; ++l) {   // blocks too large for the tensor-core kernel: level by level
@@ -672,6 +672,7 @@ void factor(Ctx& c) {
   if (fork) cudaStreamWaitEvent(c.stream, c.ev_join, 0);
   else coarse_factor(c);
   check_status(c);
+  c.factored = true;
 }
 
 // ---------------------------------------------------------------------------
@@ -696,7 +697,7 @@ template <> struct VC<double> {
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes, D.apply_flops);
     launch_patch_apply_t<double>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
                                  D.p_own_off, D.p_own, D.p_inv_off, D.inv, r, x, c.opts.omega, D.dr, D.dc,
-                                 c.sm_count, c.stream);
+                                 c.sm_count, D.apply_slices, D.apply_groups, c.stream);
     counted(c);
   }
   static void restrict_(Ctx& c, int l, const double* r, double* bc) {
@@ -731,7 +732,7 @@ template <> struct VC<float> {
   static void residual(Ctx& c, int l, const float* x, const float* b, float* y) {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_SPMV, D.spmv_bytes32, D.spmv_flops);
-    launch_bsr_residual_f32(c.B, D.nb, D.rowptr, D.col, D.val32, x, b, y, c.stream);
+    launch_bsr_residual_f32(c.B, D.nb, D.rowptr, D.col, D.val32, x, b, y, D.spmv_sub, c.stream);
     counted(c);
   }
   static void apply(Ctx& c, int l, const float* r, float* x) {
@@ -739,7 +740,7 @@ template <> struct VC<float> {
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes32, D.apply_flops);
     launch_patch_apply_t<float>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
                                 D.p_own_off, D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32,
-                                c.sm_count, c.stream);
+                                c.sm_count, D.apply_slices, D.apply_groups, c.stream);
     counted(c);
   }
   static void restrict_(Ctx& c, int l, const float* r, float* bc) {
@@ -1619,6 +1620,88 @@ int fsi_set_profiling(fsi_ctx* c, int on) {
       ks.launches = 0;
     }
     c->prof = on != 0;
+  });
+}
+
+// ---------------------------------------------------------------------------
+// launch parameters (autotuner)
+// ---------------------------------------------------------------------------
+static void drop_vcycle_graph(Ctx& c) {
+  if (c.vc_exec) cudaGraphExecDestroy(c.vc_exec);
+  if (c.vc_graph) cudaGraphDestroy(c.vc_graph);
+  c.vc_exec = nullptr;
+  c.vc_graph = nullptr;
+  c.vc_graph_failed = false;
+}
+
+int fsi_set_launch_params(fsi_ctx* c, int level, const fsi_launch_params* p) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, true);
+    if (!p) throw ApiError(FSI_E_INVALID, "null launch parameters");
+    if (p->apply_slices < 0 || p->apply_slices > 4096 || p->apply_groups < 0 || p->apply_groups > 256 ||
+        (p->spmv_sub != 0 && p->spmv_sub != 2 && p->spmv_sub != 4 && p->spmv_sub != 8) ||
+        (p->gj_panel != 0 && p->gj_panel != 16 && p->gj_panel != 32))
+      throw ApiError(FSI_E_INVALID, "launch parameters out of range");
+    sync(*c);   // nothing in flight uses the old shapes or the graph
+    DevLevel& D = c->dl[level];
+    D.apply_slices = p->apply_slices;
+    D.apply_groups = p->apply_groups;
+    D.spmv_sub = p->spmv_sub;
+    if (level == (int)c->dl.size() - 1) c->gj_panel = p->gj_panel;
+    drop_vcycle_graph(*c);
+  });
+}
+
+int fsi_get_launch_params(fsi_ctx* c, int level, fsi_launch_params* out) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, true);
+    if (!out) throw ApiError(FSI_E_INVALID, "null output");
+    const DevLevel& D = c->dl[level];
+    const ApplyShape a = apply_shape(D.n_patches, D.max_nown, c->mixed ? 4 : 2, c->sm_count, D.apply_slices,
+                                     D.apply_groups);
+    out->apply_slices = a.kind == 0 ? 1 : a.slices;
+    out->apply_groups = a.kind == 0 ? 4 : a.groups;
+    out->spmv_sub = D.spmv_sub == 0 ? 4 : D.spmv_sub;
+    out->gj_panel = c->gj_panel;
+  });
+}
+
+int fsi_time_level_kernels(fsi_ctx* c, int level, int reps, double* apply_ms, double* spmv_ms) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, true);
+    if (reps < 1 || reps > 10000) throw ApiError(FSI_E_INVALID, "reps must be in [1, 10000]");
+    if (!c->factored) throw ApiError(FSI_E_INVALID, "fsi_factor_schwarz first");
+    DevLevel& D = c->dl[level];
+    cudaEvent_t e[3];
+    for (auto& ev : e) ck(cudaEventCreate(&ev), "event");
+    const size_t nv = (size_t)D.Ni * (c->mixed ? sizeof(float) : sizeof(double));
+    void* x = c->mixed ? (void*)D.x32 : (void*)D.x;
+    void* b = c->mixed ? (void*)D.b32 : (void*)D.b;
+    void* r = c->mixed ? (void*)D.r32 : (void*)D.r;
+    ck(cudaMemsetAsync(x, 0, nv, c->stream), "memset");
+    ck(cudaMemsetAsync(b, 0, nv, c->stream), "memset");
+    ck(cudaMemsetAsync(r, 0, nv, c->stream), "memset");
+    ck(cudaEventRecord(e[0], c->stream), "event");
+    for (int k = 0; k < reps; ++k) {
+      if (c->mixed) VC<float>::apply(*c, level, D.r32, D.x32);
+      else VC<double>::apply(*c, level, D.r, D.x);
+    }
+    ck(cudaEventRecord(e[1], c->stream), "event");
+    for (int k = 0; k < reps; ++k) {
+      if (c->mixed) VC<float>::residual(*c, level, D.x32, D.b32, D.r32);
+      else VC<double>::residual(*c, level, D.x, D.b, D.r);
+    }
+    ck(cudaEventRecord(e[2], c->stream), "event");
+    sync(*c);
+    float t0 = 0.f, t1 = 0.f;
+    cudaEventElapsedTime(&t0, e[0], e[1]);
+    cudaEventElapsedTime(&t1, e[1], e[2]);
+    for (auto& ev : e) cudaEventDestroy(ev);
+    if (apply_ms) *apply_ms = t0 / reps;
+    if (spmv_ms) *spmv_ms = t1 / reps;
   });
 }
 

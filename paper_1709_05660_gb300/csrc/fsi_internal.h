@@ -103,6 +103,8 @@ struct DevLevel {
   double *P_val = nullptr, *R_val = nullptr;
   // patches
   int n_patches = 0, max_n = 0, max_nown = 0;
+  // launch parameters (0 = built-in choice; set by fsi_set_launch_params)
+  int apply_slices = 0, apply_groups = 0, spmv_sub = 0;
   int32_t *p_n = nullptr, *p_nown = nullptr;
   int64_t *p_idx_off = nullptr, *p_own_off = nullptr, *p_dense_off = nullptr, *p_inv_off = nullptr,
           *p_gmap_off = nullptr, *p_pad_off = nullptr;
@@ -160,6 +162,7 @@ struct Ctx {
   double* yold = nullptr;
   double bdf_a0 = 0.0, inflow_alpha = 1.0;
   bool have_history = false;
+  bool factored = false;   // fsi_factor_schwarz has run at least once
   int32_t* coarse_pad_list = nullptr;     // padding slots of the coarse dense operator
   int32_t* coarse_perm = nullptr;         // internal unknown -> banded position
   int32_t* coarse_pinv = nullptr;         // banded position -> internal unknown
@@ -181,6 +184,7 @@ struct Ctx {
   cudaStream_t cap_stream = nullptr;
   // the coarse factorisation runs on this higher-priority stream beside the
   // Schwarz factorisation (fork / join events on the ctx stream)
+  int gj_panel = 0;   // preferred Gauss-Jordan panel width on the tensor cores (0, 16, 32)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool aux_failed = false;

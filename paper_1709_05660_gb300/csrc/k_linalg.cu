@@ -205,12 +205,19 @@ void launch_bsr_residual(int B, int64_t nb, const int32_t* rowptr, const int32_t
 }
 
 void launch_bsr_residual_f32(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const float* val,
-                             const float* x, const float* b, float* y, cudaStream_t st) {
+                             const float* x, const float* b, float* y, int sub, cudaStream_t st) {
   const int64_t n = nb * B;
   const unsigned grid = (unsigned)((n + 255) / 256);
-  const unsigned grid4 = (unsigned)((n * 4 + 255) / 256);
-  if (B == 4) k_bsr4_residual_sub<4, float, float, float><<<grid4, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
-  else k_bsr_residual<6, float, float, float><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
+  if (B == 4) {
+    // threads per scalar row: 4 unless a tuned mapping says 2 or 8
+    const int S = (sub == 2 || sub == 8) ? sub : 4;
+    const unsigned gs = (unsigned)((n * S + 255) / 256);
+    if (S == 2) k_bsr4_residual_sub<2, float, float, float><<<gs, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
+    else if (S == 8) k_bsr4_residual_sub<8, float, float, float><<<gs, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
+    else k_bsr4_residual_sub<4, float, float, float><<<gs, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
+  } else {
+    k_bsr_residual<6, float, float, float><<<grid, 256, 0, st>>>(nb, rowptr, col, val, x, b, y);
+  }
 }
 
 template <typename TV, typename TX, typename TY>

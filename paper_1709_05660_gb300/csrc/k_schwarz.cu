@@ -971,8 +971,10 @@ bool try_gj_tc(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cuda
   return true;
 }
 
-bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st) {
+bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st,
+                               int panel) {
   if (nblocks <= 0 || lv.nlev < 1 || lv.nlev > kGjMaxLevels) return false;
+  if (panel == 16 && try_gj_tc<16>(lv, nblocks, max_n, status, st)) return true;
   if (try_gj_tc<32>(lv, nblocks, max_n, status, st)) return true;
   return try_gj_tc<16>(lv, nblocks, max_n, status, st);
 }
@@ -1202,23 +1204,42 @@ k_patch_apply_rows(const int32_t* __restrict__ p_n, const int32_t* __restrict__ 
   }
 }
 
+ApplyShape apply_shape(int np, int max_nown, int vec_width, int sm_count, int want_slices, int want_groups) {
+  ApplyShape a{0, 1, 0, 4};
+  const int nvec = own_pad(max_nown) / vec_width;
+  if (np <= 0 || nvec < 2 || want_slices == 1) return a;
+  int S;
+  if (want_slices >= 2) {
+    S = std::min(want_slices, nvec);
+  } else {
+    // built-in rule: row slices when one block per patch fills less than half
+    // of about one wave (four blocks per SM) of the one-block kernel
+    const int target = 4 * sm_count;
+    if (2 * np >= target) return a;
+    S = std::max(1, std::min(nvec, (target + np - 1) / np));
+  }
+  const int vps = (nvec + S - 1) / S;
+  if (S < 2 || vps > 256) return a;
+  a.kind = 1;
+  a.vps = vps;
+  a.slices = (nvec + vps - 1) / vps;
+  const int cap = std::max(1, 256 / vps);
+  a.groups = want_groups > 0 ? std::min(want_groups, cap) : std::min(32, cap);
+  return a;
+}
+
 template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
-                          const T* dc, int sm_count, cudaStream_t st) {
+                          const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st) {
   if (np <= 0) return;
-  const int nvec_max = own_pad(max_nown) / VecT<T>::W;
-  const int target = 4 * sm_count;            // about one wave of the one-block-per-patch kernel
-  int S = std::max(1, std::min(nvec_max, (target + np - 1) / np));
-  const int vps = (nvec_max + S - 1) / S;
-  if (2 * np < target && S >= 2 && vps <= 256) {
-    S = (nvec_max + vps - 1) / vps;
-    const int cg = std::max(1, std::min(32, 256 / vps));
-    const int threads = vps * cg;
-    const size_t smem = ((size_t)((max_n + 3) & ~3) + (size_t)cg * vps * VecT<T>::W) * sizeof(T);
-    k_patch_apply_rows<T><<<(unsigned)((int64_t)np * S), threads, smem, st>>>(
-        p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x, T(omega), dr, dc, S, vps, cg);
+  const ApplyShape a = apply_shape(np, max_nown, VecT<T>::W, sm_count, want_slices, want_groups);
+  if (a.kind == 1) {
+    const int threads = a.vps * a.groups;
+    const size_t smem = ((size_t)((max_n + 3) & ~3) + (size_t)a.groups * a.vps * VecT<T>::W) * sizeof(T);
+    k_patch_apply_rows<T><<<(unsigned)((int64_t)np * a.slices), threads, smem, st>>>(
+        p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x, T(omega), dr, dc, a.slices, a.vps, a.groups);
     return;
   }
   constexpr int CG = 4;                       // column groups per block
@@ -1239,7 +1260,8 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
                                      const int32_t*, const int64_t*, T*, T*, int32_t*, bool, cudaStream_t);     \
   template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \
                                         const int32_t*, const int64_t*, const int32_t*, const int64_t*,        \
-                                        const T*, const T*, T*, double, const T*, const T*, int, cudaStream_t);
+                                        const T*, const T*, T*, double, const T*, const T*, int, int, int,     \
+                                        cudaStream_t);
 FSI_INST(double)
 FSI_INST(float)
 #undef FSI_INST

@@ -45,7 +45,7 @@ void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nod
 void launch_bsr_residual(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const double* x, const double* b, double* y, cudaStream_t st);
 void launch_bsr_residual_f32(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const float* val,
-                             const float* x, const float* b, float* y, cudaStream_t st);
+                             const float* x, const float* b, float* y, int sub, cudaStream_t st);
 void launch_csr_spmv(int64_t nrows, const int32_t* ptr, const int32_t* col, const double* val, const double* x,
                      double* y, bool add, cudaStream_t st);
 void launch_gather(int64_t n, const int32_t* map, const double* in, double* out, cudaStream_t st);
@@ -80,7 +80,9 @@ struct GjLevels {
 };
 // false when the blocks do not fit the tensor-core kernel (the caller then
 // factors level by level)
-bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st);
+// panel: preferred panel width (16 or 32; 0 = 32 when the blocks fit, else 16)
+bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st,
+                               int panel = 0);
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
                            const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
@@ -94,7 +96,13 @@ template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
-                          const T* dc, int sm_count, cudaStream_t st);
+                          const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st);
+// Launch shape of one level's Schwarz apply: kind 0 = one block per patch
+// (k_patch_apply_t), kind 1 = `slices` row slices per patch of `vps` owned-row
+// vectors, `groups` column groups per block (k_patch_apply_rows).
+// want_slices 0 / want_groups 0 = the built-in rule; want_slices 1 = kind 0.
+struct ApplyShape { int kind, slices, vps, groups; };
+ApplyShape apply_shape(int np, int max_nown, int vec_width, int sm_count, int want_slices, int want_groups);
 
 void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t* col, const double* val,
                          const int32_t* pad_list, int npad, const int32_t* perm, int64_t n, double* A,

@@ -33,7 +33,8 @@ SYMBOLS = (
     "fsi_apply_operator", "fsi_apply_vcycle", "fsi_apply_smoother", "fsi_restrict", "fsi_prolong",
     "fsi_launch_count", "fsi_plan_hierarchy", "fsi_export_transfer", "fsi_set_profiling",
     "fsi_kernel_stats", "fsi_server_create", "fsi_serve_submit", "fsi_serve_poll", "fsi_serve_drain",
-    "fsi_server_resident_bytes", "fsi_server_destroy", "fsi_coarse_solve_static",
+    "fsi_server_resident_bytes", "fsi_server_destroy", "fsi_coarse_solve_static", "fsi_set_launch_params",
+    "fsi_get_launch_params", "fsi_time_level_kernels",
 )
 
 # kernel classes for fsi_kernel_stats
@@ -49,6 +50,11 @@ class ProblemDesc(ctypes.Structure):
         ("rho_s", ctypes.c_double), ("mu_s", ctypes.c_double), ("U", ctypes.c_double),
         ("transient", ctypes.c_int), ("dt", ctypes.c_double), ("ale_op", ctypes.c_int),
     ]
+
+
+class LaunchParams(ctypes.Structure):
+    _fields_ = [("apply_slices", ctypes.c_int32), ("apply_groups", ctypes.c_int32),
+                ("spmv_sub", ctypes.c_int32), ("gj_panel", ctypes.c_int32)]
 
 
 class SolverOptsC(ctypes.Structure):
@@ -139,6 +145,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fsi_server_destroy.argtypes = [vp]
     lib.fsi_launch_count.argtypes = [vp]
     lib.fsi_launch_count.restype = ctypes.c_int64
+    lib.fsi_set_launch_params.argtypes = [vp, ctypes.c_int, ctypes.POINTER(LaunchParams)]
+    lib.fsi_get_launch_params.argtypes = [vp, ctypes.c_int, ctypes.POINTER(LaunchParams)]
+    lib.fsi_time_level_kernels.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]
     _lib = lib
     return lib
 
@@ -190,9 +200,12 @@ class FSIError(RuntimeError):
 class FSI:
     """One Newton-step solver instance (owns an ``fsi_ctx``)."""
 
-    def __init__(self, prob: Problem, opts: SolverOpts, stream: Optional[int] = None, plan_only: bool = False):
+    def __init__(self, prob: Problem, opts: SolverOpts, stream: Optional[int] = None, plan_only: bool = False,
+                 tuned: bool = True):
         """Builds the instance on the current CUDA device (``plan_only``:
-        host structures only, no GPU needed)."""
+        host structures only, no GPU needed).  ``tuned``: apply the launch
+        shapes of the autotuner's table for this GPU and problem, if it has
+        an entry (``autotune.py``); otherwise the library's built-in choice."""
         self.lib = load_library()
         self.prob, self.opts = prob, opts
         self._desc, self._opts = make_desc(prob), make_opts(opts)
@@ -213,6 +226,10 @@ class FSI:
                                            self.nnz.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                            ctypes.byref(hb)))
         self.hbm_bytes = hb.value
+        self.tuning = None
+        if tuned and not plan_only:
+            from . import autotune
+            self.tuning = autotune.apply_table(self)
 
     def _check(self, rc):
         if rc != FSI_OK:
@@ -344,6 +361,24 @@ class FSI:
 
     def launch_count(self) -> int:
         return int(self.lib.fsi_launch_count(self.h))
+
+    def set_launch_params(self, level: int, apply_slices: int = 0, apply_groups: int = 0, spmv_sub: int = 0,
+                          gj_panel: int = 0):
+        p = LaunchParams(apply_slices, apply_groups, spmv_sub, gj_panel)
+        self._check(self.lib.fsi_set_launch_params(self.h, level, ctypes.byref(p)))
+
+    def get_launch_params(self, level: int) -> dict:
+        p = LaunchParams()
+        self._check(self.lib.fsi_get_launch_params(self.h, level, ctypes.byref(p)))
+        return dict(apply_slices=p.apply_slices, apply_groups=p.apply_groups, spmv_sub=p.spmv_sub,
+                    gj_panel=p.gj_panel)
+
+    def time_level_kernels(self, level: int, reps: int):
+        """(apply_ms, spmv_ms): device time of one launch of the level's
+        Schwarz apply and residual product (fsi_time_level_kernels)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.fsi_time_level_kernels(self.h, level, reps, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
 
 class Server:
