@@ -864,9 +864,24 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
         tc::commit(&mbar2[b]);
       };
       if (threadIdx.x == 0) issue(0);
+      constexpr int RPW = 128 / NWARP;   // epilogue rows per warp
       for (int t = 0; t < ntiles; ++t) {
         const int i0 = (t / ntc) * 128, j0 = (t % ntc) * 128, b = t & 1;
         const int nt = min(128, (n - j0 + 15) / 16 * 16);
+        // the tile's old values (lane l: columns l, l + 32, l + 64, l + 96 of
+        // its warp's rows) are loaded before waiting for the tile's UMMAs, so
+        // their L2 round trip overlaps the tensor-core work and the staging
+        float old[RPW][4];
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+          const int r = i0 + wid + NWARP * k;
+          const bool ok = r < n && live[r];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = lane + 32 * e, j = j0 + c;
+            old[k][e] = (ok && c < nt && j < n) ? M[(int64_t)r * n + j] : 0.f;
+          }
+        }
         if (threadIdx.x == 0) {
           tc::fence_after_sync();
           if (t + 1 < ntiles) issue(t + 1);   // its accumulator was drained in iteration t - 1
@@ -882,15 +897,18 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
         __syncthreads();
         if (s_abort) goto done;
         tc::fence_after_sync();
-        // accumulator -> shared memory (thread = tile row)
+        // accumulator -> shared memory (thread = tile row), 16 columns at a time
         if (i0 + 32 * q < n) {
           for (int cg = cgi; cg * CW < nt; cg += CGN) {
-            float v[CW];
-            tc::tmem_ld<CW>(tc::taddr(tbase, 32 * q, 128u * b + cg * CW), v);
-            tc::tmem_wait_ld();
-            float* srow = stage + (32 * q + lane) * kStage + cg * CW;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) srow[c] = v[c];
+            for (int h = 0; h < CW / 16; ++h) {
+              float v[16];
+              tc::tmem_ld<16>(tc::taddr(tbase, 32 * q, 128u * b + cg * CW + 16 * h), v);
+              tc::tmem_wait_ld();
+              float* srow = stage + (32 * q + lane) * kStage + cg * CW + 16 * h;
+#pragma unroll
+              for (int c = 0; c < 16; ++c) srow[c] = v[c];
+            }
           }
         }
         tc::fence_before_sync();
@@ -898,18 +916,6 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
         // M += D for live rows, panel columns excluded: lane l adds columns
         // l, l + 32, l + 64, l + 96 of a row (coalesced)
         {
-          constexpr int RPW = 128 / NWARP;   // rows per warp; all their loads in flight at once
-          float old[RPW][4];
-#pragma unroll
-          for (int k = 0; k < RPW; ++k) {
-            const int rr = wid + NWARP * k, r = i0 + rr;
-            const bool ok = r < n && live[r];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int c = lane + 32 * e, j = j0 + c;
-              old[k][e] = (ok && c < nt && j < n) ? M[(int64_t)r * n + j] : 0.f;
-            }
-          }
 #pragma unroll
           for (int k = 0; k < RPW; ++k) {
             const int rr = wid + NWARP * k, r = i0 + rr;
