@@ -305,6 +305,52 @@ def _measure(args, prec, stream, barrier, dist, world, local):
     return out
 
 
+def _measure_full_newton(args, prec, stream, U=None, max_steps=20):
+    """Config 2's nonlinear driver: Newton from d = 0, u = the boundary-condition
+    lift, p = 0 (no noise) until ||dx|| <= 1e-8 ||y||, each step assembling
+    the exact Jacobian, the Galerkin hierarchy and the Schwarz / coarse
+    factors on the device and solving with FGMRES.  Device time of every
+    Newton step (CUDA events on the stream); solves/s averaged over the steps."""
+    import torch
+    from dataclasses import replace
+    from paper_1709_05660_gb300 import fsi
+
+    prob, opts = CONFIGS[args.config]
+    opts = replace(opts, precision=prec)
+    if U is not None:
+        prob = replace(prob, U=U)
+    s = fsi.FSI(prob, opts, stream=stream.cuda_stream)
+    N = int(s.N[-1])
+    y = torch.empty(N, dtype=torch.float64, device="cuda")
+    s.initial_state(torch.zeros(N, dtype=torch.float64, device="cuda"), y)
+    s.set_state(y)
+    ms, iters, rels, rel_res, status = [], [], [], 0.0, "converged"
+    for _ in range(max_steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        try:
+            rel, st = s.newton_step()
+        except fsi.FSIError as err:
+            status = str(err).split(":")[0]
+            break
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters.append(st.iters)
+        rels.append(rel)
+        rel_res = max(rel_res, st.rel_res)
+        if rel <= 1e-8:
+            break
+    else:
+        status = "max_steps"
+    s.close()
+    tot = sum(ms)
+    return {"newton_steps": len(ms), "status": status, "rel_step": rels, "fgmres_iters": iters,
+            "ms_per_newton_step": tot / max(1, len(ms)), "newton_solves_per_s": len(ms) / (tot / 1e3) if tot else None,
+            "ms_to_steady_state": tot, "max_true_rel_residual": rel_res}
+
+
 def _measure_transient_3d(args, stream):
     """3D time-dependent workload (box channel with a plate, 27-node hexahedra,
     3 levels, 908,422 unknowns, mixed precision): args.t3d_steps BDF time steps
@@ -444,6 +490,17 @@ def run_gpu(args, rank, world):
             line["served"] = run_serve(args, n_requests=32, max_levels=4, quiet=True)
         if args.t3d_steps > 0 and world == 1:
             line["transient_3d"] = _measure_transient_3d(args, stream)
+        if not args.no_full_newton and world == 1:
+            fn = {"start": "d = 0, u = boundary-condition lift, p = 0; stop at ||dx|| <= 1e-8 ||y||",
+                  "note": "plain Newton (no damping or continuation); at the workload's mean inflow it diverges "
+                          "from the lift in the oracle too, with direct solves, so the driver is also run at "
+                          "mean inflow 0.2 on the same mesh"}
+            for U in (prob.U, 0.2):
+                key = f"U={U:g}"
+                fn[key] = {"mixed": _measure_full_newton(args, 1, stream, U=U)}
+                if not args.mixed_only:
+                    fn[key]["fp64"] = _measure_full_newton(args, 0, stream, U=U)
+            line["full_newton"] = fn
         if fp64 is not None:
             r64, c64 = _roofline(fp64["kst"], args.steps)
             line["fp64_path"] = {"value": fp64["value"], "ms_per_step": fp64["per_step"],
@@ -599,6 +656,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the small served run of the default line")
+    ap.add_argument("--no-full-newton", action="store_true", help="skip the full Newton run to steady state")
     ap.add_argument("--t3d-steps", type=int, default=2,
                     help="BDF time steps of the 3D transient workload in the default line (0: skip)")
     ap.add_argument("--serve-3d-frac", type=float, default=0.25, help="share of 3D instances in the request mix")
