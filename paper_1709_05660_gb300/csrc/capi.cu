@@ -928,23 +928,22 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
         precondition(c, vj, zj, nullptr);
         spmv(c, L - 1, zj, nullptr, c.w);
       }
-      Prof pr(c, FSI_K_KRYLOV, (4.0 * (j + 1) + 10.0) * n * 8.0, (8.0 * (j + 1) + 6.0) * n, 11);
-      launch_norm_partial(n, c.w, c.partial, nb, c.stream);
-      launch_reduce(c.partial, 1, nb, sm + 256, true, c.stream);
-      launch_dots(n, c.V, n, j + 1, c.w, c.partial, nb, c.stream);
-      launch_reduce(c.partial, j + 1, nb, sm, false, c.stream);
+      // CGS2: h1 = V^T w (with ||w||^2), w -= V h1, h2 = V^T w, w -= V h2 (with
+      // ||w||^2), v_{j+1} = w / ||w||; every V^T w is one pass over V for all j + 1 dots
+      Prof pr(c, FSI_K_KRYLOV, (4.0 * (j + 1) + 8.0) * n * 8.0, (8.0 * (j + 1) + 4.0) * n, 8);
+      launch_arnoldi_dots(n, c.V, n, j + 1, c.w, true, c.partial, nb, c.stream);
+      launch_reduce(c.partial, j + 2, nb, sm, false, c.stream);             // h1 = sm[0..j], ||w||^2 = sm[j+1]
       launch_cgs_update(n, c.V, n, j + 1, sm, c.w, c.stream);
-      launch_dots(n, c.V, n, j + 1, c.w, c.partial, nb, c.stream);
-      launch_reduce(c.partial, j + 1, nb, sm + 128, false, c.stream);
-      launch_cgs_update(n, c.V, n, j + 1, sm + 128, c.w, c.stream);
-      launch_norm_partial(n, c.w, c.partial, nb, c.stream);
-      launch_reduce(c.partial, 1, nb, sm + 257, true, c.stream);
+      launch_arnoldi_dots(n, c.V, n, j + 1, c.w, false, c.partial, nb, c.stream);
+      launch_reduce(c.partial, j + 1, nb, sm + 128, false, c.stream);       // h2
+      launch_arnoldi_update_norm(n, c.V, n, j + 1, sm + 128, c.w, c.partial, nb, c.stream);
+      launch_reduce(c.partial, 1, nb, sm + 257, true, c.stream);            // ||w|| after both passes
       launch_scale_by(n, c.w, sm + 257, c.V + (size_t)(j + 1) * n, c.stream);
-      counted(c, 11);
+      counted(c, 8);
       ck(cudaMemcpyAsync(hs, sm, 260 * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "D2H");
       sync(c);
       for (int i = 0; i <= j; ++i) Hc(i, j) = hs[i] + hs[128 + i];
-      const double hn = hs[257], wn0 = hs[256];
+      const double hn = hs[257], wn0 = std::sqrt(hs[j + 1]);
       if (!std::isfinite(hn)) throw ApiError(FSI_E_NONFINITE, "non-finite Krylov vector");
       Hc(j + 1, j) = hn;
       const bool breakdown = hn <= 1e-14 * wn0;

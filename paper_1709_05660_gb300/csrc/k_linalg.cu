@@ -371,6 +371,107 @@ void launch_cgs_update(int64_t n, const double* V, int64_t ldv, int nvec, const 
   k_cgs_update<<<grid, 256, 0, st>>>(n, V, ldv, nvec, h, w);
 }
 
+// ---------------------------------------------------------------------------
+// Fused Arnoldi (CGS2) passes.  One pass over the rows i of a block's chunk
+// forms all nvec partial dot products V[v] . w at once (one accumulator per
+// vector, NV >= nvec, so w and every V[v][i] are read once); the Gram-Schmidt
+// updates w -= sum_v V[v] h[v] are fused with the partial sums the next step
+// needs (the second pass's dots, or ||w||^2).  Partial sums are reduced within
+// a warp by shuffles, then across the block's warps in a fixed order, and
+// k_reduce adds the blocks' partials in a fixed order: the result does not
+// depend on scheduling.
+// ---------------------------------------------------------------------------
+// out[v * out_stride] (v < nacc) = the block's sums of acc[v]; with has_extra,
+// out[nacc * out_stride] = the block's sum of `extra`.  red: 8 * (NV + 1) doubles.
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&acc)[NV], int nacc, double extra, bool has_extra,
+                                               double* red, double* out, int64_t out_stride) {
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v < nacc) {   // warp-uniform; no early exit, so acc stays in registers
+      double a = acc[v];
+#pragma unroll
+      for (int o = kWarp / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red[wid * (NV + 1) + v] = a;
+    }
+  }
+  if (has_extra) {
+#pragma unroll
+    for (int o = kWarp / 2; o > 0; o >>= 1) extra += __shfl_xor_sync(0xffffffffu, extra, o);
+    if (lane == 0) red[wid * (NV + 1) + nacc] = extra;
+  }
+  __syncthreads();
+  const int nout = nacc + (has_extra ? 1 : 0);
+  for (int v = threadIdx.x; v < nout; v += blockDim.x) {
+    double a = 0.0;
+    for (int k = 0; k < nw; ++k) a += red[k * (NV + 1) + v];
+    out[(int64_t)v * out_stride] = a;
+  }
+}
+
+// partial[v * nblk + b] = V[v] . w over block b's rows (v < nvec); with
+// with_norm, partial[nvec * nblk + b] = w . w
+template <int NV>
+__global__ void __launch_bounds__(256) k_arnoldi_dots(int64_t n, const double* __restrict__ V, int64_t ldv, int nvec,
+                                                      const double* __restrict__ w, int with_norm,
+                                                      double* __restrict__ partial) {
+  __shared__ double red[8 * (NV + 1)];
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  double nn = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    nn += wi * wi;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (v < nvec) acc[v] += V[(int64_t)v * ldv + i] * wi;
+  }
+  block_partials<NV>(acc, nvec, nn, with_norm != 0, red, partial + blockIdx.x, gridDim.x);
+}
+
+// w -= sum_v V[v] h[v], fused with the partial sums of the new w . w
+template <int NV>
+__global__ void __launch_bounds__(256) k_arnoldi_update_norm(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                                             int nvec, const double* __restrict__ h,
+                                                             double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double red[8 * 2];
+  __shared__ double sh[NV];
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) sh[v] = h[v];
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double wi = w[i];
+    for (int v = 0; v < nvec; ++v) wi -= V[(int64_t)v * ldv + i] * sh[v];
+    w[i] = wi;
+    acc[0] += wi * wi;
+  }
+  block_partials<1>(acc, 1, 0.0, false, red, partial + blockIdx.x, gridDim.x);
+}
+
+template <int NV>
+static bool arnoldi_go_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, bool with_norm,
+                            double* partial, int nblk, cudaStream_t st) {
+  if (nvec > NV) return false;
+  k_arnoldi_dots<NV><<<nblk, 256, 0, st>>>(n, V, ldv, nvec, w, with_norm ? 1 : 0, partial);
+  return true;
+}
+
+void launch_arnoldi_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, bool with_norm,
+                         double* partial, int nblk, cudaStream_t st) {
+  if (arnoldi_go_dots<8>(n, V, ldv, nvec, w, with_norm, partial, nblk, st)) return;
+  if (arnoldi_go_dots<16>(n, V, ldv, nvec, w, with_norm, partial, nblk, st)) return;
+  if (arnoldi_go_dots<32>(n, V, ldv, nvec, w, with_norm, partial, nblk, st)) return;
+  arnoldi_go_dots<72>(n, V, ldv, nvec, w, with_norm, partial, nblk, st);   // restart <= 64: nvec <= 65
+}
+
+void launch_arnoldi_update_norm(int64_t n, const double* V, int64_t ldv, int nvec, const double* h, double* w,
+                                double* partial, int nblk, cudaStream_t st) {
+  if (nvec <= 64) k_arnoldi_update_norm<64><<<nblk, 256, 0, st>>>(n, V, ldv, nvec, h, w, partial);
+  else k_arnoldi_update_norm<128><<<nblk, 256, 0, st>>>(n, V, ldv, nvec, h, w, partial);
+}
+
 // x += sum_v Z[v] coef[v]
 __global__ void k_combo(int64_t n, const double* __restrict__ Z, int64_t ldz, int nvec, const double* __restrict__ c,
                         double* __restrict__ x) {

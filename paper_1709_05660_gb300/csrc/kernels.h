@@ -54,6 +54,11 @@ void launch_scale_by(int64_t n, const double* src, const double* dev_scalar, dou
 void launch_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, double* partial, int nblk,
                  cudaStream_t st);
 void launch_reduce(const double* partial, int nvec, int nblk, double* out, bool sqrt_out, cudaStream_t st);
+// fused Arnoldi passes (nvec <= 72; partial holds (nvec + 1) * nblk doubles)
+void launch_arnoldi_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, bool with_norm,
+                         double* partial, int nblk, cudaStream_t st);
+void launch_arnoldi_update_norm(int64_t n, const double* V, int64_t ldv, int nvec, const double* h, double* w,
+                                double* partial, int nblk, cudaStream_t st);
 void launch_cgs_update(int64_t n, const double* V, int64_t ldv, int nvec, const double* h, double* w, cudaStream_t st);
 void launch_combo(int64_t n, const double* Z, int64_t ldz, int nvec, const double* coef, double* x, cudaStream_t st);
 void launch_norm_partial(int64_t n, const double* w, double* partial, int nblk, cudaStream_t st);
