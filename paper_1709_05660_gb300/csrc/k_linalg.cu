@@ -549,8 +549,10 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
 //  B. every block stages the panel's multipliers and pivots, and each warp
 //     applies the panel's NB steps (swap, then the multiplier update) to one
 //     trailing column in shared memory: columns k0+nb .. k0+nb-1+kl+ku.
+constexpr int kLuColWarps = 4;   // warps per block in the trailing update of k_band_lu_blk
+
 template <int NB>
-__global__ void __launch_bounds__(128) k_band_lu_blk(int64_t n, int kl, int ku, double* __restrict__ M,
+__global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, double* __restrict__ M,
                                                     int32_t* __restrict__ piv, double* __restrict__ rdiag,
                                                     int32_t* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
@@ -562,15 +564,16 @@ __global__ void __launch_bounds__(128) k_band_lu_blk(int64_t n, int kl, int ku, 
   __shared__ double sv[32];
   __shared__ int si[32];
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
+  // the trailing update of phase B uses kLuColWarps warps per block (one
+  // shared-memory column buffer each); all warps work in phase A
+  const int nwb = min(nw, kLuColWarps);
   const int64_t wmax = (int64_t)kl + ku;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)min((int64_t)NB, n - k0);
     const int nr = (int)(min(n, k0 + nb + kl) - k0);
     if (blockIdx.x == 0) {
-      for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) {
-        const int r = t % nr, j = t / nr;
-        P[j * R + r] = M[(k0 + j) * n + k0 + r];
-      }
+      for (int j = 0; j < nb; ++j)
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) P[j * R + r] = M[(k0 + j) * n + k0 + r];
       __syncthreads();
       for (int j = 0; j < nb; ++j) {
         const int rhi = min(j + kl, nr - 1);
@@ -599,32 +602,31 @@ __global__ void __launch_bounds__(128) k_band_lu_blk(int64_t n, int kl, int ku, 
         if (threadIdx.x == 0) rdiag[k0 + j] = rp;
         for (int r = j + 1 + threadIdx.x; r <= rhi; r += blockDim.x) P[j * R + r] *= rp;
         __syncthreads();
-        const int nrow = rhi - j, ncol = nb - 1 - j;
-        for (int t = threadIdx.x; t < nrow * ncol; t += blockDim.x) {
-          const int c = j + 1 + t / nrow, r = j + 1 + t % nrow;
-          P[c * R + r] -= P[j * R + r] * P[c * R + j];
+        // rank-1 update of the panel's columns right of j: a warp per column,
+        // lanes over rows (the column's multiplier is warp-uniform)
+        for (int c = j + 1 + wid; c < nb; c += nw) {
+          const double pc = P[c * R + j];
+          if (pc != 0.0)
+            for (int r = j + 1 + lane; r <= rhi; r += kWarp) P[c * R + r] -= P[j * R + r] * pc;
         }
         if (threadIdx.x == 0) s_piv[j] = pr;
         __syncthreads();
       }
-      for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) {
-        const int r = t % nr, j = t / nr;
-        M[(k0 + j) * n + k0 + r] = P[j * R + r];
-      }
+      for (int j = 0; j < nb; ++j)
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) M[(k0 + j) * n + k0 + r] = P[j * R + r];
       for (int j = threadIdx.x; j < nb; j += blockDim.x) piv[k0 + j] = (int32_t)(k0 + s_piv[j]);
     }
     grid.sync();
     const int64_t c_lo = k0 + nb, c_hi = min(n - 1, k0 + nb - 1 + wmax);
     if (c_lo <= c_hi) {
       // stage multipliers and pivots (every block)
-      for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) {
-        const int r = t % nr, j = t / nr;
-        P[j * R + r] = M[(k0 + j) * n + k0 + r];
-      }
+      for (int j = 0; j < nb; ++j)
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) P[j * R + r] = M[(k0 + j) * n + k0 + r];
       for (int j = threadIdx.x; j < nb; j += blockDim.x) s_piv[j] = (int)(piv[k0 + j] - k0);
       __syncthreads();
       double* Sw = S + (size_t)wid * R;
-      for (int64_t c = c_lo + (int64_t)blockIdx.x * nw + wid; c <= c_hi; c += (int64_t)gridDim.x * nw) {
+      for (int64_t c = c_lo + (int64_t)blockIdx.x * nwb + wid; wid < nwb && c <= c_hi;
+           c += (int64_t)gridDim.x * nwb) {
         double* Mc = M + c * n + k0;
         for (int r = lane; r < nr; r += kWarp) Sw[r] = Mc[r];
         __syncwarp();
@@ -652,7 +654,9 @@ __global__ void __launch_bounds__(128) k_band_lu_blk(int64_t n, int kl, int ku, 
 }
 
 template <int NB>
-size_t band_lu_blk_smem(int kl) { return ((size_t)(NB + kl) * NB + 4 * (size_t)(NB + kl)) * sizeof(double); }
+size_t band_lu_blk_smem(int kl) {
+  return ((size_t)(NB + kl) * NB + kLuColWarps * (size_t)(NB + kl)) * sizeof(double);
+}
 
 // Narrow-band variant of k_band_inv (kl + ku <= 32 MR): each lane holds at
 // most MR rows of a factor column, and the column of step k + 1 is loaded
@@ -794,7 +798,10 @@ int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* rdiag
   // The kl + ku trailing columns of a panel are spread at about three per
   // warp: more blocks only add grid-barrier cost and take SMs from the work
   // that runs beside the coarse factorisation.
-  const int threads = 128;
+  // wide bands (the dense 3D slab complements): 16 warps, so the panel
+  // factorisation of block 0, which every other block waits for, has four
+  // times the threads; narrow bands (2D): 4 warps
+  const int threads = kl >= 256 ? 512 : 128;
   int grid = (int)std::min(std::min((int64_t)sm_count, n), std::max<int64_t>(8, ((int64_t)kl + ku + 11) / 12));
   if (grid < 1) grid = 1;
   void* args[] = {(void*)&n, (void*)&kl, (void*)&ku, (void*)&M, (void*)&piv, (void*)&rdiag, (void*)&status};
