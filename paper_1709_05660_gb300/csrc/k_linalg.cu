@@ -551,6 +551,41 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
 //     trailing column in shared memory: columns k0+nb .. k0+nb-1+kl+ku.
 constexpr int kLuColWarps = 4;   // warps per block in the trailing update of k_band_lu_blk
 
+// y[r] += a x[r] for r = base + lane, base + lane + 32, ... <= rhi (a warp-wide
+// update in shared memory): whole rounds of 128 rows (four per lane, all loads
+// issued before the stores: x and y are different columns, which the compiler
+// cannot prove), then the rest row by row.  The round count is warp-uniform, so
+// a short range (a narrow band) takes the plain loop only.
+__device__ __forceinline__ void axpy_rows(double* y, const double* x, double a, int base, int rhi) {
+  int r = base + threadIdx.x % kWarp;
+  const int rounds = (rhi - base + 1) / (4 * kWarp);
+  for (int q = 0; q < rounds; ++q, r += 4 * kWarp) {
+    const double x0 = x[r], x1 = x[r + kWarp], x2 = x[r + 2 * kWarp], x3 = x[r + 3 * kWarp];
+    const double y0 = y[r], y1 = y[r + kWarp], y2 = y[r + 2 * kWarp], y3 = y[r + 3 * kWarp];
+    y[r] = fma(a, x0, y0);
+    y[r + kWarp] = fma(a, x1, y1);
+    y[r + 2 * kWarp] = fma(a, x2, y2);
+    y[r + 3 * kWarp] = fma(a, x3, y3);
+  }
+  for (; r <= rhi; r += kWarp) y[r] = fma(a, x[r], y[r]);
+}
+
+// the same with x a column of the factor in global memory (y in shared memory)
+__device__ __forceinline__ void axpy_rows_g(double* y, const double* __restrict__ x, double a, int base, int rhi) {
+  int r = base + threadIdx.x % kWarp;
+  const int rounds = (rhi - base + 1) / (4 * kWarp);
+  for (int q = 0; q < rounds; ++q, r += 4 * kWarp) {
+    const double x0 = __ldg(x + r), x1 = __ldg(x + r + kWarp), x2 = __ldg(x + r + 2 * kWarp),
+                 x3 = __ldg(x + r + 3 * kWarp);
+    const double y0 = y[r], y1 = y[r + kWarp], y2 = y[r + 2 * kWarp], y3 = y[r + 3 * kWarp];
+    y[r] = fma(a, x0, y0);
+    y[r + kWarp] = fma(a, x1, y1);
+    y[r + 2 * kWarp] = fma(a, x2, y2);
+    y[r + 3 * kWarp] = fma(a, x3, y3);
+  }
+  for (; r <= rhi; r += kWarp) y[r] = fma(a, __ldg(x + r), y[r]);
+}
+
 template <int NB>
 __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, double* __restrict__ M,
                                                     int32_t* __restrict__ piv, double* __restrict__ rdiag,
@@ -606,8 +641,7 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
         // lanes over rows (the column's multiplier is warp-uniform)
         for (int c = j + 1 + wid; c < nb; c += nw) {
           const double pc = P[c * R + j];
-          if (pc != 0.0)
-            for (int r = j + 1 + lane; r <= rhi; r += kWarp) P[c * R + r] -= P[j * R + r] * pc;
+          if (pc != 0.0) axpy_rows(P + c * R, P + j * R, -pc, j + 1, rhi);
         }
         if (threadIdx.x == 0) s_piv[j] = pr;
         __syncthreads();
@@ -639,10 +673,7 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
           }
           __syncwarp();
           const double t = Sw[j];
-          if (t != 0.0) {
-            const int rhi = min(j + kl, nr - 1);
-            for (int r = j + 1 + lane; r <= rhi; r += kWarp) Sw[r] -= P[j * R + r] * t;
-          }
+          if (t != 0.0) axpy_rows(Sw, P + j * R, -t, j + 1, min(j + kl, nr - 1));
           __syncwarp();
         }
         for (int r = lane; r < nr; r += kWarp) Mc[r] = Sw[r];
@@ -770,8 +801,7 @@ __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, con
     const double xk = x[k];
     if (xk != 0.0) {
       const int64_t r_hi = min(n - 1, k + (int64_t)kl);
-      const double* Lk = M + k * n;
-      for (int64_t r = k + 1 + lane; r <= r_hi; r += kWarp) x[r] -= Lk[r] * xk;
+      axpy_rows_g(x + k, M + k * n + k, -xk, 1, (int)(r_hi - k));
     }
     __syncwarp();
   }
@@ -783,7 +813,7 @@ __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, con
     const double xk = x[k];
     if (xk != 0.0) {
       const int64_t r_lo = max((int64_t)0, k - w);
-      for (int64_t r = r_lo + lane; r < k; r += kWarp) x[r] -= Uk[r] * xk;
+      axpy_rows_g(x + r_lo, Uk + r_lo, -xk, 0, (int)(k - 1 - r_lo));
     }
     __syncwarp();
   }
