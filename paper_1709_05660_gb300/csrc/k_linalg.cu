@@ -549,7 +549,6 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
 //  B. every block stages the panel's multipliers and pivots, and each warp
 //     applies the panel's NB steps (swap, then the multiplier update) to one
 //     trailing column in shared memory: columns k0+nb .. k0+nb-1+kl+ku.
-constexpr int kLuColWarps = 4;   // warps per block in the trailing update of k_band_lu_blk
 
 // y[r] += a x[r] for r = base + lane, base + lane + 32, ... <= rhi (a warp-wide
 // update in shared memory): whole rounds of 128 rows (four per lane, all loads
@@ -589,7 +588,7 @@ __device__ __forceinline__ void axpy_rows_g(double* y, const double* __restrict_
 template <int NB>
 __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, double* __restrict__ M,
                                                     int32_t* __restrict__ piv, double* __restrict__ rdiag,
-                                                    int32_t* __restrict__ status) {
+                                                    int32_t* __restrict__ status, int col_warps) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int R = NB + kl;                                  // panel rows (at most)
@@ -599,9 +598,9 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
   __shared__ double sv[32];
   __shared__ int si[32];
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
-  // the trailing update of phase B uses kLuColWarps warps per block (one
+  // the trailing update of phase B uses col_warps warps per block (one
   // shared-memory column buffer each); all warps work in phase A
-  const int nwb = min(nw, kLuColWarps);
+  const int nwb = min(nw, col_warps);
   const int64_t wmax = (int64_t)kl + ku;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int nb = (int)min((int64_t)NB, n - k0);
@@ -685,8 +684,8 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
 }
 
 template <int NB>
-size_t band_lu_blk_smem(int kl) {
-  return ((size_t)(NB + kl) * NB + kLuColWarps * (size_t)(NB + kl)) * sizeof(double);
+size_t band_lu_blk_smem(int kl, int col_warps) {
+  return ((size_t)(NB + kl) * NB + (size_t)col_warps * (NB + kl)) * sizeof(double);
 }
 
 // Narrow-band variant of k_band_inv (kl + ku <= 32 MR): each lane holds at
@@ -834,7 +833,11 @@ int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* rdiag
   const int threads = kl >= 256 ? 512 : 128;
   int grid = (int)std::min(std::min((int64_t)sm_count, n), std::max<int64_t>(8, ((int64_t)kl + ku + 11) / 12));
   if (grid < 1) grid = 1;
-  void* args[] = {(void*)&n, (void*)&kl, (void*)&ku, (void*)&M, (void*)&piv, (void*)&rdiag, (void*)&status};
+  // trailing-update warps per block: 8 when their column buffers fit beside
+  // the panel (wide bands), else 4
+  int cw = threads >= 512 ? 8 : 4;
+  void* args[] = {(void*)&n,     (void*)&kl,     (void*)&ku, (void*)&M, (void*)&piv, (void*)&rdiag,
+                  (void*)&status, (void*)&cw};
   auto go = [&](auto kern, size_t smem) -> int {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -844,8 +847,10 @@ int launch_coarse_lu_inverse(int64_t n, int kl, int ku, double* M, double* rdiag
     return 0;
   };
   int rc;
-  if (band_lu_blk_smem<16>(kl) <= 200 * 1024) rc = go(k_band_lu_blk<16>, band_lu_blk_smem<16>(kl));
-  else if (band_lu_blk_smem<8>(kl) <= 200 * 1024) rc = go(k_band_lu_blk<8>, band_lu_blk_smem<8>(kl));
+  const size_t cap = 222 * 1024;   // dynamic shared memory per block (227 KB minus the static arrays)
+  if (band_lu_blk_smem<16>(kl, cw) > cap) cw = 4;
+  if (band_lu_blk_smem<16>(kl, cw) <= cap) rc = go(k_band_lu_blk<16>, band_lu_blk_smem<16>(kl, cw));
+  else if (band_lu_blk_smem<8>(kl, cw) <= cap) rc = go(k_band_lu_blk<8>, band_lu_blk_smem<8>(kl, cw));
   else return -3;
   if (rc != 0) return rc;
   // inverse columns: 4 warps (right-hand sides) per block, x in shared memory
