@@ -59,8 +59,12 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle-reason sampling during the timed region.
+    The sampler is started before the warm-up (nvidia-smi takes a while to
+    come up) and polls every 50 ms with a timestamp; begin() / end() mark the
+    timed region, and only samples whose timestamps fall inside it count
+    (the nearest one if none does)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -68,17 +72,25 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.f = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
     def stop(self):
+        import datetime
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
         if self.proc is None:
             return out
@@ -89,25 +101,30 @@ class ClockSampler:
             self.proc.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
         os.unlink(self.f.name)
-        if sm:
-            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                   "samples": len(sm)}
-        return out
+        if not rows:
+            return out
+        t0 = self.t0 if self.t0 is not None else rows[0][0]
+        t1 = self.t1 if self.t1 is not None else rows[-1][0]
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if not inside:   # region shorter than the polling interval: the sample nearest to it
+            mid = 0.5 * (t0 + t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        reasons = set().union(*(r[3] for r in inside))
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "poll_ms": 50}
 
 
 # ----------------------------------------------------------------------------
@@ -235,14 +252,15 @@ def _measure(args, prec, stream, barrier, dist, world, local):
         s.set_state(y0)
         return s.newton_step(dx)
 
+    clocks = ClockSampler(local)
+    clocks.start()                      # up and polling by the end of the warm-up
     for _ in range(args.warmup):
         rel, st = step()
     # headline: args.steps Newton steps timed with CUDA events, no per-kernel events
     launches0 = s.launch_count()
-    clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -253,6 +271,7 @@ def _measure(args, prec, stream, barrier, dist, world, local):
         rel_res.append(st.rel_res)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
