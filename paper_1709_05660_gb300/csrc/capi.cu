@@ -761,7 +761,7 @@ template <> struct VC<float> {
     if (c.coarse_slab) {
       const double by = coarse_slab_apply_bytes(c);
       Prof pr(c, FSI_K_TRANSFER, by + 4.0 * n0 * 8.0 + 2.0 * n0 * 4.0, by / 4.0, 4 + 8 * ((int)c.slab_off.size() - 1));
-      launch_axpby_f32_to_f64(c.dl[0].Ni, b, c.c_xb, c.stream);
+      launch_to_f64(c.dl[0].Ni, b, c.c_xb, c.stream);
       counted(c);
       coarse_apply_slab(c, c.c_xb, c.c_zb);   // both buffers are free again when it writes its result
       launch_to_f32(c.dl[0].Ni, c.c_zb, x, c.stream);
@@ -920,7 +920,7 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
         // (each widening is an FP64-pipe instruction, about 80 per entry
         // inside the block sparse product)
         Prof pr(c, FSI_K_SPMV, F.spmv_bytes + n * 4.0, F.spmv_flops, 2);   // no b; + widening
-        launch_axpby_f32_to_f64(n, zj, c.zd, c.stream);
+        launch_to_f64(n, zj, c.zd, c.stream);
         launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, c.zd, nullptr, c.w, c.stream);
         counted(c, 2);
       } else {
@@ -1502,7 +1502,7 @@ int fsi_apply_vcycle(fsi_ctx* c, const double* b, double* z) {
     if (c->mixed) {
       DevLevel& F = c->dl[L - 1];
       precondition(*c, c->bk, nullptr, F.x32);
-      launch_axpby_f32_to_f64(F.Ni, F.x32, c->xk, c->stream);
+      launch_to_f64(F.Ni, F.x32, c->xk, c->stream);
       counted(*c);
     } else {
       precondition(*c, c->bk, c->xk, nullptr);
@@ -1572,7 +1572,7 @@ int fsi_apply_smoother(fsi_ctx* c, int level, const double* b, const double* x, 
       launch_to_f32(D.Ni, D.b, D.b32, c->stream);
       launch_to_f32(D.Ni, D.x, D.x32, c->stream);
       smooth_step_t<float>(*c, level, D.b32, D.x32, false);
-      launch_axpby_f32_to_f64(D.Ni, D.x32, D.x, c->stream);
+      launch_to_f64(D.Ni, D.x32, D.x, c->stream);
       counted(*c, 3);
     } else {
       smooth_step_t<double>(*c, level, D.b, D.x, false);

@@ -252,7 +252,7 @@ void launch_to_f32(int64_t n, const double* in, float* out, cudaStream_t st) {
   k_convert<double, float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, out);
 }
 
-void launch_axpby_f32_to_f64(int64_t n, const float* in, double* out, cudaStream_t st) {
+void launch_to_f64(int64_t n, const float* in, double* out, cudaStream_t st) {
   k_convert<float, double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, out);
 }
 
@@ -305,24 +305,6 @@ __global__ void k_scale_by(int64_t n, const double* __restrict__ src, const doub
 
 void launch_scale_by(int64_t n, const double* src, const double* dev_scalar, double* dst, cudaStream_t st) {
   k_scale_by<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, src, dev_scalar, dst);
-}
-
-// partial[v * nblk + bx] = sum over block bx's chunk of V[v] . w
-__global__ void k_dots(int64_t n, const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
-                       double* __restrict__ partial) {
-  __shared__ double scratch[32];
-  const int v = blockIdx.y;
-  const double* Vv = V + (int64_t)v * ldv;
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += Vv[i] * w[i];
-  const double s = block_sum(acc, scratch);
-  if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = s;
-}
-
-void launch_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, double* partial, int nblk,
-                 cudaStream_t st) {
-  k_dots<<<dim3(nblk, nvec), 256, 0, st>>>(n, V, ldv, w, partial);
 }
 
 __global__ void k_norm_partial(int64_t n, const double* __restrict__ w, double* __restrict__ partial) {

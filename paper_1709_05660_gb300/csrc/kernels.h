@@ -51,8 +51,6 @@ void launch_csr_spmv(int64_t nrows, const int32_t* ptr, const int32_t* col, cons
 void launch_gather(int64_t n, const int32_t* map, const double* in, double* out, cudaStream_t st);
 void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
 void launch_scale_by(int64_t n, const double* src, const double* dev_scalar, double* dst, cudaStream_t st);
-void launch_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, double* partial, int nblk,
-                 cudaStream_t st);
 void launch_reduce(const double* partial, int nvec, int nblk, double* out, bool sqrt_out, cudaStream_t st);
 // fused Arnoldi passes (nvec <= 72; partial holds (nvec + 1) * nblk doubles)
 void launch_arnoldi_dots(int64_t n, const double* V, int64_t ldv, int nvec, const double* w, bool with_norm,
@@ -128,7 +126,7 @@ void launch_gemv_sub(int m, int nc, double alpha, const double* A, int64_t lda, 
 void launch_csr_spmv_f32(int64_t nrows, const int32_t* ptr, const int32_t* col, const float* val, const float* x,
                          float* y, bool add, cudaStream_t st);
 void launch_to_f32(int64_t n, const double* in, float* out, cudaStream_t st);
-void launch_axpby_f32_to_f64(int64_t n, const float* in, double* out, cudaStream_t st);
+void launch_to_f64(int64_t n, const float* in, double* out, cudaStream_t st);
 void launch_combo_mixed(int64_t n, const float* Z, int64_t ldz, int nvec, const double* coef, double* x,
                         cudaStream_t st);
 
