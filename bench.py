@@ -324,6 +324,45 @@ def _measure(args, prec, stream, barrier, dist, world, local):
     return out
 
 
+def _measure_config(name, prec, stream, steps=3, warmup=2):
+    """Newton steps of another configuration at its seeded state (as the
+    headline: set_state, assemble, Galerkin, factor, FGMRES, update), device
+    time with CUDA events over `steps` steps after `warmup` untimed ones."""
+    import torch
+    from dataclasses import replace
+    from paper_1709_05660_gb300 import fsi
+
+    prob, opts = CONFIGS[name]
+    opts = replace(opts, precision=prec)
+    s = fsi.FSI(prob, opts, stream=stream.cuda_stream)
+    N = int(s.N[-1])
+    y0 = torch.empty(N, dtype=torch.float64, device="cuda")
+    s.initial_state(torch.tensor(noise(N, 0), dtype=torch.float64, device="cuda"), y0)
+    dx = torch.empty(N, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        s.set_state(y0)
+        s.newton_step(dx)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters, rel_res = [], 0.0
+    for _ in range(steps):
+        s.set_state(y0)
+        _, st = s.newton_step(dx)
+        iters.append(st.iters)
+        rel_res = max(rel_res, st.rel_res)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"unknowns": N, "levels": prob.levels, "tile": list(opts.tile), "solves_per_s": steps / (ms / 1e3),
+           "ms_per_step": ms / steps, "fgmres_iters": iters, "max_true_rel_residual": rel_res,
+           "phase_ms": {"assemble": st.t_assemble_ms, "factor": st.t_factor_ms, "solve": st.t_solve_ms},
+           "launch_shapes": "autotuned" if s.tuning is not None else "built-in"}
+    s.close()
+    return out
+
+
 def _measure_full_newton(args, prec, stream, U=None, max_steps=20):
     """Config 2's nonlinear driver: Newton from d = 0, u = the boundary-condition
     lift, p = 0 (no noise) until ||dx|| <= 1e-8 ||y||, each step assembling
@@ -509,6 +548,14 @@ def run_gpu(args, rank, world):
             line["served"] = run_serve(args, n_requests=32, max_levels=4, quiet=True)
         if args.t3d_steps > 0 and world == 1:
             line["transient_3d"] = _measure_transient_3d(args, stream)
+        if not args.no_configs and world == 1:
+            cfg = {}
+            for name in ("c1_2d_l3", "c3_2d_l6"):
+                cfg[name] = {"mixed": _measure_config(name, 1, stream)}
+                if not args.mixed_only:
+                    cfg[name]["fp64"] = _measure_config(name, 0, stream, steps=2, warmup=1)
+                    cfg[name]["mixed_over_fp64"] = cfg[name]["mixed"]["solves_per_s"] / cfg[name]["fp64"]["solves_per_s"]
+            line["configs"] = cfg
         if not args.no_full_newton and world == 1:
             fn = {"start": "d = 0, u = boundary-condition lift, p = 0; stop at ||dx|| <= 1e-8 ||y||",
                   "note": "plain Newton (no damping or continuation); at the workload's mean inflow it diverges "
@@ -676,6 +723,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the small served run of the default line")
     ap.add_argument("--no-full-newton", action="store_true", help="skip the full Newton run to steady state")
+    ap.add_argument("--no-configs", action="store_true", help="skip the Newton-step timing of configs 1 and 3")
     ap.add_argument("--t3d-steps", type=int, default=2,
                     help="BDF time steps of the 3D transient workload in the default line (0: skip)")
     ap.add_argument("--serve-3d-frac", type=float, default=0.25, help="share of 3D instances in the request mix")
