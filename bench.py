@@ -233,6 +233,25 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, dist) -> float:
+    """Largest value of x over all ranks (x itself without a process group).
+    The reduction tensor lives where the backend needs it: on the GPU for
+    NCCL, on the host for gloo."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, seconds: float) -> float:
+    """Units per second of the whole job: every rank runs `steps` units and the
+    slowest rank's time counts."""
+    return world * steps / seconds
+
+
 def _measure(args, prec, stream, barrier, dist, world, local):
     """Times args.steps Newton steps of one precision; returns a result dict."""
     import torch
@@ -290,11 +309,8 @@ def _measure(args, prec, stream, barrier, dist, world, local):
     ms_prof = p0.elapsed_time(p1)
     kst = s.kernel_stats()
     s.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    out = {"N": N, "ms": ms, "per_step": ms / args.steps, "value": world * args.steps / (ms / 1e3),
+    ms = max_over_ranks(ms, dist)
+    out = {"N": N, "ms": ms, "per_step": ms / args.steps, "value": whole_job_rate(world, args.steps, ms / 1e3),
            "profiled_ms_per_step": ms_prof / args.steps,
            "iters": iters, "rel_res": max(rel_res), "rel_step": rel, "kst": kst, "launches": launches,
            "clocks": clk, "hbm_bytes": s.hbm_bytes, "tuned": s.tuning is not None,
@@ -314,11 +330,8 @@ def _measure(args, prec, stream, barrier, dist, world, local):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    out["e2e"] = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+    e2e_s = max_over_ranks(e2e_s, dist)
+    out["e2e"] = {"value": whole_job_rate(world, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * 8,
                   "d2h_bytes_per_step": N * 8}
     s.close()
     return out
