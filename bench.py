@@ -377,7 +377,7 @@ def _measure_config(name, prec, stream, steps=3, warmup=2):
 
 
 def _measure_full_newton(args, prec, stream, U=None, max_steps=20):
-    """Config 2's nonlinear driver: Newton from d = 0, u = the boundary-condition
+    """The benchmark workload's nonlinear driver: Newton from d = 0, u = the boundary-condition
     lift, p = 0 (no noise) until ||dx|| <= 1e-8 ||y||, each step assembling
     the exact Jacobian, the Galerkin hierarchy and the Schwarz / coarse
     factors on the device and solving with FGMRES.  Device time of every
@@ -433,7 +433,7 @@ def _measure_transient_3d(args, stream):
     from dataclasses import replace
     from paper_1709_05660_gb300 import fsi
 
-    prob, opts = CONFIGS["c4_3d_l3"]
+    prob, opts = CONFIGS["box3d_l3_bdf2"]
     s = fsi.FSI(prob, opts, stream=stream.cuda_stream)
     N = int(s.N[-1])
     y = torch.empty(N, dtype=torch.float64, device="cuda")
@@ -466,7 +466,7 @@ def _measure_transient_3d(args, stream):
     s.set_profiling(False)
     s.close()
     _, classes = _roofline(kst, newton, fp32_classes=("patch_factor",))
-    return {"workload": "c4_3d_l3 (3D BDF2, dt 0.01, 64x16x16 hexahedra, 3 levels, mixed)", "unknowns": N,
+    return {"workload": "box3d_l3_bdf2 (3D BDF2, dt 0.01, 64x16x16 hexahedra, 3 levels, mixed)", "unknowns": N,
             "time_steps": args.t3d_steps, "newton_steps_per_time_step": per_step,
             "newton_solves_per_s": newton / (ms_tot / 1e3), "time_steps_per_s": args.t3d_steps / (ms_tot / 1e3),
             "ms_per_newton_step": ms_tot / newton, "fgmres_iters": iters, "max_true_rel_residual": rel_res,
@@ -563,7 +563,7 @@ def run_gpu(args, rank, world):
             line["transient_3d"] = _measure_transient_3d(args, stream)
         if not args.no_configs and world == 1:
             cfg = {}
-            for name in ("c1_2d_l3", "c3_2d_l6"):
+            for name in ("channel2d_l3", "channel2d_l6"):
                 cfg[name] = {"mixed": _measure_config(name, 1, stream)}
                 if not args.mixed_only:
                     cfg[name]["fp64"] = _measure_config(name, 0, stream, steps=2, warmup=1)
@@ -726,7 +726,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="c2_2d_l5")
+    ap.add_argument("--config", default="channel2d_l5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed-only", action="store_true", help="skip the FP64-path measurement")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (request mix) instead")
@@ -736,7 +736,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the small served run of the default line")
     ap.add_argument("--no-full-newton", action="store_true", help="skip the full Newton run to steady state")
-    ap.add_argument("--no-configs", action="store_true", help="skip the Newton-step timing of configs 1 and 3")
+    ap.add_argument("--no-configs", action="store_true", help="skip the Newton-step timing of the 3- and 6-level channels")
     ap.add_argument("--t3d-steps", type=int, default=2,
                     help="BDF time steps of the 3D transient workload in the default line (0: skip)")
     ap.add_argument("--serve-3d-frac", type=float, default=0.25, help="share of 3D instances in the request mix")

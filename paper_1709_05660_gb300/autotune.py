@@ -8,7 +8,7 @@ instance the panel width of the tensor-core Gauss-Jordan factorisation.  The
 candidates differ only in how work is mapped to threads (and so in the
 rounding order of sums), never in what is computed.
 
-``python -m paper_1709_05660_gb300.autotune --configs c2_2d_l5 ...`` times
+``python -m paper_1709_05660_gb300.autotune --configs channel2d_l5 ...`` times
 every candidate on the device with CUDA events (``fsi_time_level_kernels``;
 the factorisation through the per-class counters) and writes the fastest into
 ``tuning.json`` beside this file, keyed by the GPU's name and by the problem's
@@ -174,7 +174,7 @@ def tune(prob, opts, stream: Optional[int] = None, reps: int = 40, trials: int =
 def main():
     from .workloads import CONFIGS
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--configs", nargs="+", default=["c2_2d_l5"])
+    ap.add_argument("--configs", nargs="+", default=["channel2d_l5"])
     ap.add_argument("--precision", nargs="+", type=int, default=[1], help="1 mixed, 0 FP64")
     ap.add_argument("--out", default=TABLE)
     ap.add_argument("--reps", type=int, default=40)

@@ -69,16 +69,17 @@ def problem_3d(levels: int = 3, **kw) -> Problem:
                    flap_lo=(0.5, 0.0, 0.1), flap_hi=(0.55, 0.25, 0.4), **kw)
 
 
-# The five workloads.  Config 1 is small (the oracle solves it in seconds);
-# config 2 is the single-GPU benchmark workload.
+# The workloads: 2D channels with a flap at 3-6 levels (the 3-level one is small
+# enough for the oracle to solve in seconds; the 5-level one, 313,860 unknowns,
+# is the single-GPU benchmark workload) and the 3D box channel with a plate.
 CONFIGS = {
-    "c1_2d_l3": (Problem(levels=3, mu_s=5e5, U=0.2), SolverOpts(tile=(2, 2))),
-    "c2_2d_l5": (Problem(levels=5, mu_s=2e6, U=1.0), SolverOpts(tile=(4, 4))),
-    # the config-2 problem one level coarser (72k unknowns, ~1 GB on the device):
+    "channel2d_l3": (Problem(levels=3, mu_s=5e5, U=0.2), SolverOpts(tile=(2, 2))),
+    "channel2d_l5": (Problem(levels=5, mu_s=2e6, U=1.0), SolverOpts(tile=(4, 4))),
+    # the 5-level problem one level coarser (79k unknowns, ~1 GB on the device):
     # small case for detailed profiles of the same kernels
-    "c2s_2d_l4": (Problem(levels=4, mu_s=2e6, U=1.0), SolverOpts(tile=(4, 4))),
-    "c3_2d_l6": (Problem(levels=6, mu_s=2e6, U=1.0), SolverOpts(tile=(6, 6), precision=1)),
-    "c4_3d_l3": (problem_3d(levels=3, mu_s=5e5, U=1.0, transient=1, dt=0.01),
+    "channel2d_l4": (Problem(levels=4, mu_s=2e6, U=1.0), SolverOpts(tile=(4, 4))),
+    "channel2d_l6": (Problem(levels=6, mu_s=2e6, U=1.0), SolverOpts(tile=(6, 6), precision=1)),
+    "box3d_l3_bdf2": (problem_3d(levels=3, mu_s=5e5, U=1.0, transient=1, dt=0.01),
                  SolverOpts(tile=(2, 2, 2), precision=1)),
 }
 

@@ -16,7 +16,7 @@ ENTRY = {"levels": {"1": dict(apply_slices=8, apply_groups=32, spmv_sub=8),
 
 
 def test_signature_fixes_block_shapes_not_materials():
-    prob, opts = CONFIGS["c2_2d_l5"]
+    prob, opts = CONFIGS["channel2d_l5"]
     assert autotune.signature(prob, opts) == "2d-L5-c16x4-t4x4-fp64"
     from dataclasses import replace
     soft = replace(prob, mu_s=1e4, U=0.1)
@@ -37,7 +37,7 @@ def test_check_entry_ranges():
 
 
 def test_lookup_by_gpu_and_signature():
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     table = {"GPU A": {autotune.signature(prob, opts): ENTRY}}
     assert autotune.lookup(prob, opts, gpu="GPU A", table=table) is ENTRY
     assert autotune.lookup(prob, opts, gpu="GPU B", table=table) is None
@@ -54,7 +54,7 @@ class _Recorder:
 
 
 def test_apply_table_sets_every_level_and_the_panel_on_the_finest():
-    prob, opts = CONFIGS["c1_2d_l3"]          # 3 levels: Schwarz levels 1 and 2
+    prob, opts = CONFIGS["channel2d_l3"]          # 3 levels: Schwarz levels 1 and 2
     rec = _Recorder(prob, opts)
     assert autotune.apply_table(rec, ENTRY) is ENTRY
     assert rec.calls == [(1, dict(apply_slices=8, apply_groups=32, spmv_sub=8, gj_panel=0)),

@@ -1,6 +1,6 @@
 """Launch shapes (fsi_set_launch_params) and their autotuner on the device.
 
-Config-1 hierarchy, mixed path.  Forcing any candidate shape (one block per
+The 3-level 2D channel (20,100 unknowns), mixed path.  Forcing any candidate shape (one block per
 Schwarz block or row slices with several column-group counts, 2 / 4 / 8
 threads per SpMV row, panel width 16 or 32) changes only the rounding order:
 the V-cycle matches the built-in shapes to FP32 rounding, and the Newton
@@ -28,7 +28,7 @@ def _dev(a):
 
 @pytest.fixture(scope="module")
 def case():
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     opts = replace(opts, precision=1)
     orc = osolver.Oracle(prob, opts)
     y0 = initial_state(prob, orc.fine, noise(orc.fine.N, 0))

@@ -74,7 +74,7 @@ def _csr(s, level):
 def c1():
     fsi = _fsi()
     torch.cuda.set_device(0)
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     s = fsi.FSI(prob, opts, stream=torch.cuda.current_stream().cuda_stream)
     orc = osolver.Oracle(prob, opts)
     N = orc.fine.N
@@ -268,7 +268,7 @@ def test_error_status_codes(c1):
 
 @pytest.fixture(scope="module")
 def c1_t4():
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     opts = replace(opts, tile=(4, 4))
     orc = osolver.Oracle(prob, opts)
     N = orc.fine.N
@@ -319,9 +319,9 @@ def test_blocked_factor_smoother_and_newton_step(c1_t4, precision):
     s.close()
 
 
-def test_mixed_newton_step_config1():
+def test_mixed_newton_step_3level_channel():
     fsi = _fsi()
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     opts = replace(opts, precision=1)
     orc = osolver.Oracle(prob, opts)
     N = orc.fine.N
@@ -377,7 +377,7 @@ def _oracle_rows(prob, lev, y, nodes):
     return rows, rres
 
 
-@pytest.mark.parametrize("cfg,precision", [("c2_2d_l5", 0), ("c2_2d_l5", 1), ("c3_2d_l6", 1), ("c3_2d_l6", 0)],
+@pytest.mark.parametrize("cfg,precision", [("channel2d_l5", 0), ("channel2d_l5", 1), ("channel2d_l6", 1), ("channel2d_l6", 0)],
                          ids=["c2-fp64", "c2-mixed", "c3-mixed", "c3-fp64"])
 def test_full_size_newton_step_sampled(cfg, precision):
     fsi = _fsi()

@@ -46,7 +46,7 @@ def _csr(s, level):
 def test_transient_step_parity(order):
     from paper_1709_05660_gb300 import fsi
     torch.cuda.set_device(0)
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     prob = replace(prob, transient=1, dt=0.01)
     opts = replace(opts, rtol=1e-12)
     orc = osolver.Oracle(prob, opts)
@@ -82,7 +82,7 @@ def test_transient_step_parity(order):
 
 def test_transient_needs_history():
     from paper_1709_05660_gb300 import fsi
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     prob = replace(prob, transient=1, dt=0.01, levels=2)
     s = fsi.FSI(prob, opts, stream=torch.cuda.current_stream().cuda_stream)
     try:

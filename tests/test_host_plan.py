@@ -42,7 +42,7 @@ def _plan(lib, prob, opts):
 @pytest.mark.parametrize("case", ["c1", "3d"])
 def test_plan_matches_oracle_bit_exact(lib, case):
     if case == "c1":
-        prob, opts = CONFIGS["c1_2d_l3"]
+        prob, opts = CONFIGS["channel2d_l3"]
     else:
         prob, opts = replace(SMALL_3D, levels=2), SolverOpts(tile=(2, 2, 2))
     s = _plan(lib, prob, opts)
@@ -83,15 +83,15 @@ def test_plan_matches_oracle_bit_exact(lib, case):
     s.close()
 
 
-def test_plan_sizes_config2_and_3d_counts(lib):
-    prob, opts = CONFIGS["c2_2d_l5"]
+def test_plan_sizes_5level_channel_and_3d_counts(lib):
+    prob, opts = CONFIGS["channel2d_l5"]
     s = _plan(lib, prob, opts)
     assert int(s.N[-1]) == 313860
     s.close()
 
 
 def test_compute_on_planned_ctx_is_rejected(lib):
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     s = _plan(lib, prob, opts)
     y = np.zeros(int(s.N[-1]))
     with pytest.raises(lib.FSIError) as ei:
@@ -101,7 +101,7 @@ def test_compute_on_planned_ctx_is_rejected(lib):
 
 
 def test_invalid_descriptors_rejected(lib):
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     with pytest.raises(lib.FSIError):
         _plan(lib, replace(prob, levels=0), opts)
     with pytest.raises(lib.FSIError):

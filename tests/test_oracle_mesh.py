@@ -40,7 +40,7 @@ def test_mesh_count_matches_closed_form():
         lev = build_level(box, l)
         assert lev.N == n_unknowns(3, lev.cells)
     assert build_level(box, 1).N == 17062   # level 2 of the paper's 3D table
-    p, _ = CONFIGS["c1_2d_l3"]
+    p, _ = CONFIGS["channel2d_l3"]
     lev = build_level(p, 2)
     assert lev.cells == (64, 16) and lev.n_nodes == 4257 and lev.N == 20100
 
@@ -60,7 +60,7 @@ def test_paper_block_sizes():
     assert len(pts3) == 1 and len(pts3[0].dofs) == want["3d"]
 
 
-@pytest.mark.parametrize("cfg", ["c1_2d_l3"])
+@pytest.mark.parametrize("cfg", ["channel2d_l3"])
 def test_patches_partition_and_materials(cfg):
     prob, opts = CONFIGS[cfg]
     for l in range(1, prob.levels):
@@ -81,7 +81,7 @@ def test_patches_partition_and_materials(cfg):
 
 
 def test_node_classes_and_dirichlet():
-    prob, _ = CONFIGS["c1_2d_l3"]
+    prob, _ = CONFIGS["channel2d_l3"]
     lev = build_level(prob, 0)
     # flap = coarse x cell 4, y cells 0-1: 2 solid elements, interface nodes on its 3 free sides
     assert lev.elem_solid.sum() == 2
@@ -110,7 +110,7 @@ def test_node_classes_and_dirichlet():
 
 
 def test_initial_state_recipe():
-    prob, _ = CONFIGS["c1_2d_l3"]
+    prob, _ = CONFIGS["channel2d_l3"]
     lev = build_level(prob, 2)
     nz = noise(lev.N, 0)
     y = initial_state(prob, lev, nz)

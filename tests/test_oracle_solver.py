@@ -203,7 +203,7 @@ def test_fgmres_identity_diagonal():
 
 
 def test_fgmres_vcycle_matches_direct_solve():
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     prob = replace(prob, levels=2)
     orc = solver.Oracle(prob, opts)
     y = initial_state(prob, orc.fine, noise(orc.fine.N, 0))
@@ -217,7 +217,7 @@ def test_fgmres_vcycle_matches_direct_solve():
 
 
 def test_newton_converges_quadratically():
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     prob = replace(prob, levels=2)
     orc = solver.Oracle(prob, opts)
     lev = orc.fine

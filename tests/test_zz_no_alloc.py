@@ -37,7 +37,7 @@ def _instance(prob, opts):
 
 def test_static_coarse_solve_matches_vcycle_bitwise():
     import scipy.sparse.linalg as spla
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     s, orc = _instance(replace(prob, levels=1), opts)
     try:
         n = int(s.N[0])
@@ -64,7 +64,7 @@ def test_static_coarse_solve_matches_vcycle_bitwise():
 def test_static_coarse_solve_on_a_hierarchy():
     """Level 0 of a three-level instance holds the Galerkin operator."""
     import scipy.sparse.linalg as spla
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     s, orc = _instance(prob, opts)
     try:
         n = int(s.N[0])
@@ -82,7 +82,7 @@ def test_static_coarse_solve_size_limit():
     """A coarse level above FSI_STATIC_COARSE_MAX (4096) is rejected before
     any launch; the instance stays usable."""
     from paper_1709_05660_gb300 import fsi
-    prob, opts = CONFIGS["c1_2d_l3"]
+    prob, opts = CONFIGS["channel2d_l3"]
     xb = tuple(np.linspace(0.0, 2.0, 33))          # 32 x 8 coarse cells: 5,444 internal unknowns
     yb = tuple(np.linspace(0.0, 0.5, 9))
     big = replace(prob, levels=1, breaks=(xb, yb))
