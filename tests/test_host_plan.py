@@ -12,7 +12,7 @@ import pytest
 from oracle import fem, solver
 from oracle.mesh import build_level, build_patches
 from paper_1709_05660_gb300.workloads import CONFIGS, SolverOpts
-from tests.oracle_cases import SMALL_3D
+from tests.oracle_cases import SMALL_3D, UNIT_FLUID
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -39,12 +39,25 @@ def _plan(lib, prob, opts):
     return lib.FSI(prob, opts, plan_only=True)
 
 
-@pytest.mark.parametrize("case", ["c1", "3d"])
+PLAN_CASES = {
+    "c1": lambda: CONFIGS["channel2d_l3"],
+    "3d": lambda: (replace(SMALL_3D, levels=2), SolverOpts(tile=(2, 2, 2))),
+    # ragged blocks: 3 x 3 tiles do not divide the 64 x 16 fine mesh, and they are split by material
+    "ragged_tile": lambda: (CONFIGS["channel2d_l3"][0], SolverOpts(tile=(3, 3))),
+    # a tile larger than the mesh: one block per material region
+    "tile_beyond_mesh": lambda: (replace(CONFIGS["channel2d_l3"][0], levels=2), SolverOpts(tile=(100, 100))),
+    # one level: coarse operator only, no Schwarz level
+    "one_level": lambda: (replace(CONFIGS["channel2d_l3"][0], levels=1), SolverOpts(tile=(2, 2))),
+    # no solid and no interface (the flap box lies outside the domain)
+    "all_fluid": lambda: (replace(UNIT_FLUID, levels=2), SolverOpts(tile=(2, 2))),
+    # ragged 3D blocks
+    "3d_ragged": lambda: (replace(SMALL_3D, levels=2), SolverOpts(tile=(3, 2, 3))),
+}
+
+
+@pytest.mark.parametrize("case", list(PLAN_CASES))
 def test_plan_matches_oracle_bit_exact(lib, case):
-    if case == "c1":
-        prob, opts = CONFIGS["channel2d_l3"]
-    else:
-        prob, opts = replace(SMALL_3D, levels=2), SolverOpts(tile=(2, 2, 2))
+    prob, opts = PLAN_CASES[case]()
     s = _plan(lib, prob, opts)
     for l in range(prob.levels):
         lev = build_level(prob, l)
