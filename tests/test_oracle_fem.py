@@ -324,3 +324,221 @@ def test_transient_kinematic_rows_vanish_for_consistent_velocity():
                     if not lev.dir_mask[node * nd + n + c]]
         scale = np.max(np.abs(y[n:lev.n_nodes * nd:nd])) * np.max(lev.elem_h) ** 2
         assert np.max(np.abs(r[kin_rows])) <= 1e-12 * scale
+
+
+# ----------------------------------------------------------------------------
+# fluid terms on a deformed mesh (F != I)
+# ----------------------------------------------------------------------------
+
+def _quad_map():
+    """A quadratic displacement d(x_hat) (exactly representable in Q2, so the
+    discrete mesh equals the exact one), its gradient and det F.  F = I +
+    grad_hat d is non-constant and non-symmetric."""
+    def d(xh):
+        x, y = xh[:, 0], xh[:, 1]
+        return np.stack([0.12 * x * y + 0.05 * y * y, 0.1 * x * x - 0.07 * x * y], axis=1)
+
+    def detF(xh):
+        x, y = xh[:, 0], xh[:, 1]
+        F = np.array([[1 + 0.12 * y, 0.12 * x + 0.1 * y], [0.2 * x - 0.07 * y, 1 - 0.07 * x]])
+        return F[0, 0] * F[1, 1] - F[0, 1] * F[1, 0]
+    return d, detF
+
+
+def test_mms_navier_stokes_deformed_mesh():
+    """Navier-Stokes on a fixed curved mesh x = x_hat + d(x_hat) (Sec. 2.1,
+    2.3): the manufactured solution is a smooth field of the physical
+    coordinates; every displacement unknown and every boundary velocity is a
+    Dirichlet value.  The ALE form maps gradients by F^{-T} and weights by J,
+    so a transposed F^{-1}, or J dropped from a term, converges to another
+    field and breaks the rates (at d = 0 these factors are the identity)."""
+    rho, mu = UNIT_FLUID.rho_f, UNIT_FLUID.mu_f
+    psi = sy.sin(sy.pi * X) * sy.sin(sy.pi * Y) * sy.Rational(1, 2)
+    u = [sy.diff(psi, Y), -sy.diff(psi, X)]
+    p = sy.cos(sy.pi * X) * sy.sin(sy.pi * Y)
+    grad = [[sy.diff(u[i], v) for v in (X, Y)] for i in range(2)]
+    f = [sy.simplify(sum(grad[i][j] * u[j] for j in range(2)) - mu / rho * sum(sy.diff(u[i], v, 2) for v in (X, Y))
+                     + sy.diff(p, (X, Y)[i]) / rho) for i in range(2)]
+    fm_phys, u_phys, p_phys = _lambdify_vec(f), _lambdify_vec(u), _lambdify_vec([p])
+    dmap, detF = _quad_map()
+    to_phys = lambda xh: xh + dmap(xh)
+    # the source callback integrates -(rho f, phi) over the reference element,
+    # so the physical body force carries the Jacobian of the map
+    src = lambda xh: (fm_phys(to_phys(xh)) * detF(xh)[:, None], np.zeros(len(xh)), None)
+    ex_d = dmap
+    ex_u = lambda xh: u_phys(to_phys(xh))
+    ex_p = lambda xh: p_phys(to_phys(xh))
+    errs = []
+    for l in (1, 2, 3):
+        lev = build_level(UNIT_FLUID, l)
+        nd = 4
+        xyz = lev.node_xyz
+        bnd = np.zeros(lev.n_nodes, dtype=bool)
+        for a in range(2):
+            bnd |= np.isclose(xyz[:, a], 0.0) | np.isclose(xyz[:, a], 1.0)
+        lev.dir_mask[:] = False
+        for c in range(2):
+            lev.dir_mask[np.arange(lev.n_nodes) * nd + c] = True            # the mesh is fixed
+            lev.dir_mask[np.nonzero(bnd)[0] * nd + 2 + c] = True             # velocity on all walls
+        dv, uv = ex_d(xyz), ex_u(xyz)
+        lev.dir_val[:] = 0.0
+        for c in range(2):
+            lev.dir_val[np.arange(lev.n_nodes) * nd + c] = dv[:, c]
+            lev.dir_val[np.arange(lev.n_nodes) * nd + 2 + c] = uv[:, c]
+        y = np.zeros(lev.N)
+        y[lev.dir_mask] = lev.dir_val[lev.dir_mask]
+        y = _newton_direct(UNIT_FLUID, lev, y, src, fix_pressure=True)
+        errs.append(_l2_errors(lev, y, ex_d, ex_u, ex_p))
+    ru = np.log2(errs[-2]["u"] / errs[-1]["u"])
+    rp = np.log2(errs[-2]["p"] / errs[-1]["p"])
+    assert errs[-1]["d"] < 1e-12
+    assert ru > 2.7, (errs, ru)
+    assert rp > 1.8, (errs, rp)
+
+
+# ----------------------------------------------------------------------------
+# transient terms: inertia with J, and the mesh velocity in the convection
+# ----------------------------------------------------------------------------
+
+SIMPSON = np.array([1.0, 4.0, 1.0]) / 6.0     # integrals of the 1D Q2 basis over a unit cell
+
+
+def _affine_state(lev, A, rng, p_amp=30.0):
+    """d = (A - I) x_hat at every node (F = A), random pressures."""
+    nd, n = 2 * lev.dim, lev.dim
+    y = np.zeros(lev.N)
+    dvals = lev.node_xyz @ (A - np.eye(n)).T
+    for c in range(n):
+        y[c:lev.n_nodes * nd:nd] = dvals[:, c]
+    y[lev.n_nodes * nd:] = p_amp * rng.standard_normal(lev.N - lev.n_nodes * nd)
+    return y
+
+
+def _basis_integrals(lev):
+    """(E, 3^dim): exact integral of each element's Q2 basis functions over
+    the (undeformed) element, by the product of 1D Simpson weights."""
+    nloc = 3 ** lev.dim
+    w = np.ones((lev.n_elem, nloc))
+    for a in range(nloc):
+        for d in range(lev.dim):
+            w[:, a] *= SIMPSON[(a // 3 ** d) % 3] * lev.elem_h[:, d]
+    return w
+
+
+_A2 = np.array([[1.45, 0.2], [-0.15, 0.92]])
+_A3 = np.array([[1.3, 0.1, -0.05], [0.08, 1.1, 0.12], [-0.1, 0.05, 0.95]])
+
+
+@pytest.mark.parametrize("prob,order", [(CHANNEL_2D, 1), (CHANNEL_2D, 2), (SMALL_3D, 2)],
+                         ids=["2d-bdf1", "2d-bdf2", "3d-bdf2"])
+def test_transient_inertia_closed_form(prob, order):
+    """Uniform acceleration on an affinely deformed mesh (F = A constant):
+    nodal velocities linear in time, u_t = c, grad u = 0, displacement
+    constant in time (w = 0).  The transient residual minus the steady one is
+    then the inertia term alone: rho J c_i times the integral of the test
+    function, with J = det A, fluid rows weighted by rho_f and solid rows by
+    rho_s (interface rows both); every other row is unchanged.  The basis
+    integrals come from Simpson's weights, not from the oracle's quadrature."""
+    prob = replace(prob, rho_s=700.0)
+    lev = build_level(prob, 0)
+    n, nd = lev.dim, 2 * lev.dim
+    A = _A2 if n == 2 else _A3
+    rng = np.random.default_rng(21)
+    y = _affine_state(lev, A, rng)
+    U0 = rng.standard_normal(n)
+    c = rng.standard_normal(n) * 3.0
+    dt = 0.02
+    hist = []
+    for k in (0, 1, 2):
+        yk = y.copy()
+        for i in range(n):
+            yk[n + i:lev.n_nodes * nd:nd] = U0[i] - k * c[i] * dt
+        hist.append(yk)
+    tr = dict(yn=hist[1], ynm1=hist[2], a=fem.bdf_coefficients(order), dt=dt, t=0.25)
+    r_tr = fem.residual_only(prob, lev, hist[0], tr=tr)
+    r_st = fem.residual_only(prob, lev, hist[0])
+    want = np.zeros(lev.N)
+    wint = _basis_integrals(lev)
+    detA = np.linalg.det(A)
+    for e in range(lev.n_elem):
+        solid = bool(lev.elem_solid[e])
+        for a, node in enumerate(lev.elem_nodes[e]):
+            cls = lev.node_class[node]
+            slot0 = 0 if (solid or cls == IFACE) else n      # momentum rows: d-rows of solid / interface nodes
+            rho = prob.rho_s if solid else prob.rho_f
+            for i in range(n):
+                want[node * nd + slot0 + i] += rho * detA * c[i] * wint[e, a]
+    free = ~lev.dir_mask
+    got = (r_tr - r_st)[free]
+    scale = np.max(np.abs(want))
+    assert scale > 0
+    assert np.max(np.abs(got - want[free])) <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("prob,order", [(CHANNEL_2D, 1), (CHANNEL_2D, 2), (SMALL_3D, 2)],
+                         ids=["2d-bdf1", "2d-bdf2", "3d-bdf2"])
+def test_transient_galilean_mesh_velocity(prob, order):
+    """Galilean invariance of the ALE form: translate an (affinely deformed)
+    state rigidly with constant velocity V, i.e. displacement d + V t and
+    velocity u + V at every node.  The BDF mesh velocity is then exactly
+    w = V and u_t = 0, so the convective velocity u + V - w, the solid
+    kinematic velocity u + V - d_t and every gradient are those of the
+    untranslated steady state: all free rows of the transient residual equal
+    the steady residual of (d, u, p).  A wrong sign of w, w missing from the
+    convection or d_t missing from the kinematic rows breaks the identity."""
+    lev = build_level(prob, 0)
+    n, nd = lev.dim, 2 * lev.dim
+    A = _A2 if n == 2 else _A3
+    rng = np.random.default_rng(22)
+    base = _affine_state(lev, A, rng)
+    for i in range(n):
+        base[n + i:lev.n_nodes * nd:nd] = 0.4 * rng.standard_normal(lev.n_nodes)
+    V = rng.standard_normal(n) * 0.7
+    dt, t1 = 0.03, 0.25
+    hist = []
+    for k in (0, 1, 2):
+        yk = base.copy()
+        for i in range(n):
+            yk[i:lev.n_nodes * nd:nd] += V[i] * (t1 - k * dt)
+            yk[n + i:lev.n_nodes * nd:nd] += V[i]
+        hist.append(yk)
+    tr = dict(yn=hist[1], ynm1=hist[2], a=fem.bdf_coefficients(order), dt=dt, t=t1)
+    r_tr = fem.residual_only(prob, lev, hist[0], tr=tr)
+    r_st = fem.residual_only(prob, lev, base)
+    free = ~lev.dir_mask
+    scale = np.max(np.abs(r_st[free]))
+    assert np.max(np.abs(r_tr[free] - r_st[free])) <= 1e-11 * scale
+    # the same translation without the mesh moving along (w = 0) is not invariant
+    for k in range(3):
+        for i in range(n):
+            hist[k][i:lev.n_nodes * nd:nd] -= V[i] * (t1 - k * dt)
+    r_fixed = fem.residual_only(prob, lev, hist[0], tr=dict(tr, yn=hist[1], ynm1=hist[2]))
+    assert np.max(np.abs(r_fixed[free] - r_st[free])) > 1e-6 * scale
+
+
+@pytest.mark.parametrize("prob", [CHANNEL_2D, SMALL_3D], ids=["2d", "3d"])
+def test_mass_rows_affine_closed_form(prob):
+    """Mass rows on an affinely deformed mesh (x = A x_hat, F = A) with a
+    velocity linear in the physical coordinates, u = B x + b (exactly a Q2
+    field).  A fluid element's rows are the integrals of div u times the
+    P1disc test functions over the deformed element: tr(B) |det A| |e| for
+    q = 1 and 0 for q = xi, eta(, zeta) (odd about the element centre); a
+    solid element's rows are the integrals of J - 1: (det A - 1) |e| and 0."""
+    lev = build_level(prob, 0)
+    n, nd = lev.dim, 2 * lev.dim
+    A = _A2 if n == 2 else _A3
+    rng = np.random.default_rng(23)
+    y = _affine_state(lev, A, rng)
+    Bm = rng.standard_normal((n, n))
+    bv = rng.standard_normal(n)
+    uval = (lev.node_xyz @ A.T) @ Bm.T + bv
+    for i in range(n):
+        y[n + i:lev.n_nodes * nd:nd] = uval[:, i]
+    r = fem.residual_only(prob, lev, y)
+    vol = np.prod(lev.elem_h, axis=1)
+    detA = np.linalg.det(A)
+    p0 = lev.n_nodes * nd
+    want = np.zeros((lev.n_elem, n + 1))
+    want[:, 0] = np.where(lev.elem_solid, (detA - 1.0) * vol, np.trace(Bm) * detA * vol)
+    got = r[p0:].reshape(lev.n_elem, n + 1)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
