@@ -8,8 +8,13 @@ as the paper obtains it by automatic differentiation, Sec. 3):
 
 Kinematics (Sec. 2.1): F = I + grad_hat d, J = det F, B = F F^T.
 
-Solid element (Lagrangian, Sec. 2.2 / 2.3), sigma = -p I + 2 C1 B, C1 = mu_s/2:
-    momentum  (J sigma F^{-T} : grad_hat phi)      = (( -p J F^{-T} + mu_s J F ) : grad_hat phi)
+Solid element (Lagrangian, Sec. 2.2 / 2.3), incompressible Neo-Hookean
+sigma = -p I + 2 C1 B or Mooney-Rivlin sigma = -p I + 2 C1 B - 2 C2 B^{-1}
+(Sec. 2.2), with C2 = ``mr_c2`` (0: Neo-Hookean) and C1 = mu_s/2 - C2, so
+that mu_s = 2 (C1 + C2) stays the shear modulus of the linearised law:
+    momentum  (J sigma F^{-T} : grad_hat phi)
+              = (( -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T} ) : grad_hat phi)
+              (B F^{-T} = F and B^{-1} F^{-T} = F^{-T} F^{-1} F^{-T})
     mass      ((J - 1) q)
     kinematic (u . psi)                              (steady: d/dt d = 0)
 Fluid element (ALE, integrals on the deformed element x = x_hat + d):
@@ -150,7 +155,9 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
     -(g, q) to the mass rows and -(g_ale, psi) to the ALE rows.
 
     ``tr = dict(yn=..., ynm1=..., a=(a0, a1, a2), dt=...)`` switches on the
-    transient (BDF) terms; ``None`` is the steady form.
+    transient (BDF) terms; ``tr = dict(scheme="cn", yn=..., dt=...)`` the
+    paper's Crank-Nicolson form (see ``cn_terms``); ``None`` is the steady
+    form.
     """
     dim = lev.dim
     n = dim
@@ -165,10 +172,15 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
     vol = np.prod(h, axis=1)
     kale = 1.0 / vol
     ye = y[lev.elem_dofs[elems]]                 # (E, m)
-    if tr is not None:
+    cn = tr is not None and tr.get("scheme") == "cn"
+    bdf = tr is not None and not cn
+    if bdf:
         a0, a1, a2 = tr["a"]
         idt = 1.0 / tr["dt"]
         yold = (a1 * tr["yn"] + a2 * tr["ynm1"])[lev.elem_dofs[elems]]   # constant part of q_t * dt
+    if cn:
+        idt = 1.0 / tr["dt"]
+        yne = tr["yn"][lev.elem_dofs[elems]]                            # state at t_n (constants)
     iface = lev.node_class[lev.elem_nodes[elems]] == IFACE   # (E, nloc)
 
     Rv = np.zeros((E, m))
@@ -188,9 +200,16 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
         g[:, cols] = psi[None, :]
         return Dual(ye[:, cols] @ psi, g)
 
+    def cfield(coef, comp):
+        """Value of the t_n state: sum_a coef[:, a] * y_n[a*nd + comp]."""
+        cols = np.arange(nloc) * nd + comp
+        return np.einsum("ea,ea->e", coef, yne[:, cols])
+
     def add_rows(rows, val: Dual, test):
         """R[rows] += val * test; rows (nloc,) or (E, nloc) with -1 = skip,
         test (E, nloc)."""
+        if not isinstance(val, Dual):
+            val = Dual(np.asarray(val), np.zeros((E, m)))
         tv = val.v[:, None] * test                            # (E, nloc)
         tg = val.g[:, None, :] * test[:, :, None]             # (E, nloc, m)
         if rows.ndim == 1:
@@ -213,7 +232,7 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
         gd = [[field(Gh[:, :, j], i) for j in range(n)] for i in range(n)]
         gu = [[field(Gh[:, :, j], n + i) for j in range(n)] for i in range(n)]
         u = [field(Nb, n + i) for i in range(n)]
-        if tr is not None:
+        if bdf:
             # nodal BDF time derivatives interpolated at the quadrature point
             ut = [(field(Nb, n + i) * a0 + np.einsum("ea,a->e", yold[:, np.arange(nloc) * nd + n + i], Nq)) * idt
                   for i in range(n)]
@@ -222,17 +241,31 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
         p = pfield(psi)
         F = [[gd[i][j] + (1.0 if i == j else 0.0) for j in range(n)] for i in range(n)]
         J, Finv = _det_inv(F)
+        if cn:
+            # the t_n state (constants) and the mesh velocity w = (d - d_n) / dt
+            gdn = [[cfield(Gh[:, :, j], i) for j in range(n)] for i in range(n)]
+            un = [cfield(Nb, n + i) for i in range(n)]
+            pn = yne[:, nd * nloc + np.arange(dim + 1)] @ psi
+            Fn = [[gdn[i][j] + (1.0 if i == j else 0.0) for j in range(n)] for i in range(n)]
+            Jn, Finvn = _det_inv(Fn)
+            w = [(field(Nb, i) - cfield(Nb, i)) * idt for i in range(n)]
+            gw = [[(gd[i][j] - gdn[i][j]) * idt for j in range(n)] for i in range(n)]
         if solid:
-            # P = J sigma F^{-T} = -p J F^{-T} + mu_s J F   (sigma = -pI + 2 C1 B)
-            pJ = p * J
-            muJ = J * prob.mu_s
-            T = [[-(pJ * Finv[j][i]) + muJ * F[i][j] for j in range(n)] for i in range(n)]
+            T = _solid_piola(prob, F, Finv, J, p, n)
+            if cn:
+                Tn = _solid_piola(prob, Fn, Finvn, Jn, pn, n)
             for c in range(n):
                 for j in range(n):
-                    add_rows(a_idx * nd + c, T[c][j] * wq, Gh[:, :, j])
-                kin = u[c] if tr is None else u[c] - dt_[c]
+                    Tc = T[c][j] if not cn else T[c][j] * 0.5 + Tn[c][j] * 0.5
+                    add_rows(a_idx * nd + c, Tc * wq, Gh[:, :, j])
+                if cn:
+                    # (rho J u)_{n+1} - (rho J u)_n over dt; kinematic -w + (u + u_n) / 2
+                    add_rows(a_idx * nd + c, (u[c] * J - un[c] * Jn) * (prob.rho_s * idt * wq), Nb)
+                    add_rows(a_idx * nd + n + c, ((u[c] + un[c]) * 0.5 - w[c]) * wq, Nb)
+                    continue
+                kin = u[c] if not bdf else u[c] - dt_[c]
                 add_rows(a_idx * nd + n + c, kin * wq, Nb)
-                if tr is not None:
+                if bdf:
                     add_rows(a_idx * nd + c, ut[c] * J * (prob.rho_s * wq), Nb)
             mass = J - 1.0
         else:
@@ -252,20 +285,53 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
                 sig[i][i] = sig[i][i] - p
             mom_rows = np.where(iface, a_idx[None, :] * nd, a_idx[None, :] * nd + n)
             ale_rows = np.where(iface, -1, a_idx[None, :] * nd)
-            adv = u if tr is None else [u[j] - dt_[j] for j in range(n)]   # u - w
+            if cn:
+                gun = [[cfield(Gh[:, :, j], n + i) for j in range(n)] for i in range(n)]
+                guxn = [[sum(gun[i][k] * Finvn[k][j] for k in range(n)) for j in range(n)] for i in range(n)]
+                sign = [[prob.mu_f * (guxn[i][j] + guxn[j][i]) - (pn if i == j else 0.0) for j in range(n)]
+                        for i in range(n)]
+                # div w on the two meshes (grad = grad_hat F^{-1})
+                divw1 = gw[0][0] * Finv[0][0]
+                divwn = gw[0][0] * Finvn[0][0]
+                for i in range(n):
+                    for k in range(n):
+                        if i == 0 and k == 0:
+                            continue
+                        divw1 = divw1 + gw[i][k] * Finv[k][i]
+                        divwn = divwn + gw[i][k] * Finvn[k][i]
+            adv = u if not bdf else [u[j] - dt_[j] for j in range(n)]   # u - w
             for c in range(n):
-                conv = gux[c][0] * adv[0]
-                for j in range(1, n):
-                    conv = conv + gux[c][j] * adv[j]
-                if tr is not None:
-                    conv = conv + ut[c]
                 rows_c = mom_rows + c
-                add_rows(rows_c, conv * J * (prob.rho_f * wq), Nb)
-                for k in range(n):
-                    Tk = sig[c][0] * Finv[k][0]
+                if cn:
+                    # conservative ALE form: (rho J u)_{n+1} - (rho J u)_n over dt,
+                    # -(div w) u and [(u - w) . grad] u averaged over t_{n+1}, t_n
+                    conv1 = gux[c][0] * (u[0] - w[0])
+                    convn = -(w[0] - un[0]) * guxn[c][0]
                     for j in range(1, n):
-                        Tk = Tk + sig[c][j] * Finv[k][j]
-                    add_rows(rows_c, Tk * J * wq, Gh[:, :, k])
+                        conv1 = conv1 + gux[c][j] * (u[j] - w[j])
+                        convn = convn + -(w[j] - un[j]) * guxn[c][j]
+                    val = ((u[c] * J - un[c] * Jn) * idt - divw1 * J * u[c] * 0.5 - divwn * (Jn * un[c]) * 0.5
+                           + conv1 * J * 0.5 + convn * Jn * 0.5)
+                    add_rows(rows_c, val * (prob.rho_f * wq), Nb)
+                    for k in range(n):
+                        Tk = sig[c][0] * Finv[k][0]
+                        Tkn = sign[c][0] * Finvn[k][0]
+                        for j in range(1, n):
+                            Tk = Tk + sig[c][j] * Finv[k][j]
+                            Tkn = Tkn + sign[c][j] * Finvn[k][j]
+                        add_rows(rows_c, (Tk * J * 0.5 + Tkn * Jn * 0.5) * wq, Gh[:, :, k])
+                else:
+                    conv = gux[c][0] * adv[0]
+                    for j in range(1, n):
+                        conv = conv + gux[c][j] * adv[j]
+                    if bdf:
+                        conv = conv + ut[c]
+                    add_rows(rows_c, conv * J * (prob.rho_f * wq), Nb)
+                    for k in range(n):
+                        Tk = sig[c][0] * Finv[k][0]
+                        for j in range(1, n):
+                            Tk = Tk + sig[c][j] * Finv[k][j]
+                        add_rows(rows_c, Tk * J * wq, Gh[:, :, k])
                 arow = np.where(ale_rows >= 0, ale_rows + c, -1)
                 for j in range(n):
                     if prob.ale_op == 0:
@@ -292,6 +358,33 @@ def element_system(prob, lev: Level, elems: np.ndarray, y: np.ndarray,
                     np.subtract.at(Rv, (np.nonzero(sel)[0], arow[sel]), contrib[sel])
             Rv[:, prow] -= (gm * wq)[:, None] * psi[None, :]
     return Rv, Rg
+
+
+def _solid_piola(prob, F, Finv, J, p, n):
+    """First Piola stress P = J sigma F^{-T} of the incompressible solid
+    (Sec. 2.2): -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T} with
+    2 C1 = mu_s - 2 C2 (C2 = 0: Neo-Hookean); entries are Duals or arrays."""
+    c2 = getattr(prob, "mr_c2", 0.0)
+    pJ = p * J
+    muJ = J * (prob.mu_s - 2.0 * c2)                # 2 C1 J
+    T = [[-(pJ * Finv[j][i]) + muJ * F[i][j] for j in range(n)] for i in range(n)]
+    if c2 != 0.0:
+        # Q = F^{-1} F^{-T} (Q_ab = sum_m Finv_am Finv_bm), (F^{-T} Q)_ij = sum_a Finv_ai Q_aj
+        Q = [[None] * n for _ in range(n)]
+        for a_ in range(n):
+            for b_ in range(n):
+                q_ = Finv[a_][0] * Finv[b_][0]
+                for m_ in range(1, n):
+                    q_ = q_ + Finv[a_][m_] * Finv[b_][m_]
+                Q[a_][b_] = q_
+        c2J = J * (2.0 * c2)
+        for i in range(n):
+            for j in range(n):
+                g_ = Finv[0][i] * Q[0][j]
+                for a_ in range(1, n):
+                    g_ = g_ + Finv[a_][i] * Q[a_][j]
+                T[i][j] = T[i][j] - c2J * g_
+    return T
 
 
 def fe_pattern(lev: Level) -> sp.csr_matrix:

@@ -44,7 +44,8 @@ class Problem:
     rho_f: float = 1000.0
     mu_f: float = 1.0
     rho_s: float = 1000.0
-    mu_s: float = 5e5                    # shear modulus; C1 = mu_s / 2
+    mu_s: float = 5e5                    # shear modulus; C1 = mu_s / 2 - mr_c2
+    mr_c2: float = 0.0                   # Mooney-Rivlin C2 (0: Neo-Hookean)
     U: float = 0.2                       # mean inflow velocity
     transient: int = 0
     dt: float = 0.01
@@ -62,6 +63,8 @@ class SolverOpts:
     rtol: float = 1e-10
     max_iters: int = 1000
     precision: int = 0                   # 0 = FP64, 1 = mixed
+    krylov: int = 0                      # 0 = FGMRES (right, true residual), 1 = GMRES (left, preconditioned residual)
+    gs_passes: int = 0                   # Gram-Schmidt passes (0: 2 for FGMRES, 1 for left GMRES)
 
 
 def problem_3d(levels: int = 3, **kw) -> Problem:

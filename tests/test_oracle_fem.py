@@ -120,7 +120,7 @@ X, Y = sy.symbols("x y")
 
 
 def _lambdify_vec(exprs):
-    fs = [sy.lambdify((X, Y), e, "numpy") for e in exprs]
+    fs = [sy.lambdify((X, Y), e, "numpy", cse=True) for e in exprs]
 
     def f(xy):
         out = np.zeros((xy.shape[0], len(fs)))
@@ -542,3 +542,266 @@ def test_mass_rows_affine_closed_form(prob):
     want[:, 0] = np.where(lev.elem_solid, (detA - 1.0) * vol, np.trace(Bm) * detA * vol)
     got = r[p0:].reshape(lev.n_elem, n + 1)
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+# ----------------------------------------------------------------------------
+# Mooney-Rivlin solid (Sec. 2.2): sigma = -p I + 2 C1 B - 2 C2 B^{-1}
+# ----------------------------------------------------------------------------
+
+def test_mms_mooney_rivlin_solid():
+    """Incompressible Mooney-Rivlin with C2 = 0.3, C1 = mu_s / 2 - C2:
+    -div(J sigma F^{-T}) = rho f, J - 1 = g.  A wrong sign or a transposed
+    factor of the B^{-1} term converges to another field and breaks the
+    rates."""
+    c2 = 0.3
+    prob = replace(UNIT_SOLID, mr_c2=c2)
+    mu = prob.mu_s
+    d = [sy.Rational(1, 20) * sy.sin(sy.pi * X) * sy.sin(sy.pi * Y),
+         sy.Rational(1, 10) * X * Y * (1 - X) * (1 + Y)]
+    p = sy.cos(sy.pi * X) * sy.cos(sy.pi * Y)
+    F = sy.Matrix([[1 + sy.diff(d[0], X), sy.diff(d[0], Y)], [sy.diff(d[1], X), 1 + sy.diff(d[1], Y)]])
+    J = F.det()
+    Bm = F * F.T
+    adj = lambda M: sy.Matrix([[M[1, 1], -M[0, 1]], [-M[1, 0], M[0, 0]]])   # det(B) = J^2
+    sigma = -p * sy.eye(2) + (mu - 2 * c2) * Bm - 2 * c2 * adj(Bm) / J ** 2
+    P = J * sigma * adj(F).T / J
+    f = [-(sy.diff(P[i, 0], X) + sy.diff(P[i, 1], Y)) / prob.rho_s for i in range(2)]
+    fm = _lambdify_vec(f)
+    gm = _lambdify_vec([J - 1])
+    src = lambda xq: (fm(xq), gm(xq)[:, 0], None)
+    ex = (_lambdify_vec(d), _lambdify_vec([sy.Integer(0), sy.Integer(0)]), _lambdify_vec([p]))
+    errs, rates = _rates(prob, ex, src, fix_pressure=True)
+    assert errs[-1]["u"] < 1e-12
+    assert rates["d"] > 2.7, (errs, rates)
+    assert rates["p"] > 1.8, (errs, rates)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mooney_rivlin_rigid_rotation_is_stress_free(dim):
+    """A rigid rotation d = (Q - I) x_hat has B = I, so with the element
+    pressures at 2 C1 - 2 C2 = mu_s - 4 C2 the Mooney-Rivlin stress vanishes:
+    every free row of an all-solid mesh is zero (momentum, J - 1 = 0, u = 0),
+    including the displacement rows of a traction-free face (x = max, its
+    displacements freed here).  A pressure balancing 2 C1 + 2 C2 instead (the
+    C2 term with the other sign) leaves a hydrostatic stress whose traction
+    on that face is nonzero."""
+    c2 = 0.21
+    if dim == 2:
+        prob = replace(UNIT_SOLID, mr_c2=c2)
+        th = 0.4
+        Q = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    else:
+        prob = replace(SMALL_3D, flap_lo=(-1.0, -1.0, -1.0), flap_hi=(2.0, 2.0, 2.0), mr_c2=c2 * 1e5)
+        a, b = 0.3, -0.5
+        Qx = np.array([[1, 0, 0], [0, np.cos(a), -np.sin(a)], [0, np.sin(a), np.cos(a)]])
+        Qz = np.array([[np.cos(b), -np.sin(b), 0], [np.sin(b), np.cos(b), 0], [0, 0, 1]])
+        Q = Qz @ Qx
+    lev = build_level(prob, 1 if dim == 2 else 0)
+    assert np.all(lev.elem_solid)
+    n, nd = lev.dim, 2 * lev.dim
+    right = np.nonzero(np.isclose(lev.node_xyz[:, 0], lev.node_xyz[:, 0].max()))[0]
+    for c in range(n):
+        lev.dir_mask[right * nd + c] = False
+    y = np.zeros(lev.N)
+    dv = lev.node_xyz @ (Q - np.eye(n)).T
+    for c in range(n):
+        y[c:lev.n_nodes * nd:nd] = dv[:, c]
+    p0 = lev.n_nodes * nd
+    y[p0::n + 1] = prob.mu_s - 4.0 * prob.mr_c2
+    r = fem.residual_only(prob, lev, y)
+    free = ~lev.dir_mask
+    scale = prob.mu_s * np.max(lev.elem_h) ** (dim - 1)
+    assert np.max(np.abs(r[free])) <= 1e-10 * scale
+    y[p0::n + 1] = prob.mu_s            # a pressure that balances 2 C1 + 2 C2 instead
+    r = fem.residual_only(prob, lev, y)
+    assert np.max(np.abs(r[free])) > 1e-3 * prob.mr_c2 * np.min(lev.elem_h) ** (dim - 1)
+
+
+@pytest.mark.parametrize("prob", [replace(CHANNEL_2D, mr_c2=8e4), replace(SMALL_3D, mr_c2=6e4)], ids=["2d", "3d"])
+def test_fd_jacobian_mooney_rivlin(prob):
+    _fd_check(prob, build_level(prob, 0), 31, ndir=2)
+
+
+# ----------------------------------------------------------------------------
+# Crank-Nicolson form of Sec. 2.5 (conservative ALE identity of Sec. 2.3)
+# ----------------------------------------------------------------------------
+
+def _cn(yn, dt, t=0.25):
+    return dict(scheme="cn", yn=yn, dt=dt, t=t)
+
+
+@pytest.mark.parametrize("prob", [replace(CHANNEL_2D, mr_c2=5e4), SMALL_3D], ids=["2d", "3d"])
+def test_fd_jacobian_crank_nicolson(prob):
+    lev = build_level(prob, 0)
+    y, yn, _ = _tr_state(lev, 17)
+    tr = _cn(yn, 0.02)
+    r, J = fem.assemble(prob, lev, y, tr=tr)
+    rng = np.random.default_rng(18)
+    h = 1e-6
+    for _ in range(2):
+        v = rng.standard_normal(lev.N)
+        fd = (fem.residual_only(prob, lev, y + h * v, tr=tr) - fem.residual_only(prob, lev, y - h * v, tr=tr)) / (2 * h)
+        jv = J @ v
+        assert np.linalg.norm(fd - jv) <= 1e-6 * np.linalg.norm(jv)
+
+
+@pytest.mark.parametrize("prob", [CHANNEL_2D, SMALL_3D], ids=["2d", "3d"])
+def test_cn_galilean_invariance(prob):
+    """Rigid translation with velocity V between t_n and t_{n+1} (d + V t,
+    u + V at both levels): the conservative inertia vanishes, div w = 0, the
+    convective velocity u + V - w and the kinematic velocity (u + V) - w are
+    those of the untranslated state, and both stress halves coincide, so every
+    free row equals the steady residual of (d, u, p)."""
+    lev = build_level(prob, 0)
+    n, nd = lev.dim, 2 * lev.dim
+    A = _A2 if n == 2 else _A3
+    rng = np.random.default_rng(24)
+    base = _affine_state(lev, A, rng)
+    for i in range(n):
+        base[n + i:lev.n_nodes * nd:nd] = 0.4 * rng.standard_normal(lev.n_nodes)
+    V = rng.standard_normal(n) * 0.7
+    dt, t1 = 0.03, 0.25
+    ys = []
+    for k in (0, 1):
+        yk = base.copy()
+        for i in range(n):
+            yk[i:lev.n_nodes * nd:nd] += V[i] * (t1 - k * dt)
+            yk[n + i:lev.n_nodes * nd:nd] += V[i]
+        ys.append(yk)
+    r_cn = fem.residual_only(prob, lev, ys[0], tr=_cn(ys[1], dt, t1))
+    r_st = fem.residual_only(prob, lev, base)
+    free = ~lev.dir_mask
+    scale = np.max(np.abs(r_st[free]))
+    assert np.max(np.abs(r_cn[free] - r_st[free])) <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("prob", [CHANNEL_2D, SMALL_3D], ids=["2d", "3d"])
+def test_cn_uniform_acceleration_closed_form(prob):
+    """Affinely deformed mesh at rest (w = 0, F = A), velocities uniform in
+    space with u_{n+1} - u_n = c dt, same pressures at both levels: relative
+    to the steady residual of the new state, the momentum rows gain
+    rho J c times the integral of the test function (rho_f on fluid, rho_s on
+    solid elements) and the solid kinematic rows, (u_{n+1} + u_n)/2 - w
+    instead of u_{n+1}, lose c dt / 2 times it; nothing else changes."""
+    prob = replace(prob, rho_s=700.0)
+    lev = build_level(prob, 0)
+    n, nd = lev.dim, 2 * lev.dim
+    A = _A2 if n == 2 else _A3
+    rng = np.random.default_rng(25)
+    y = _affine_state(lev, A, rng)
+    U0 = rng.standard_normal(n)
+    c = rng.standard_normal(n) * 3.0
+    dt = 0.02
+    y1, y0 = y.copy(), y.copy()
+    for i in range(n):
+        y1[n + i:lev.n_nodes * nd:nd] = U0[i]
+        y0[n + i:lev.n_nodes * nd:nd] = U0[i] - c[i] * dt
+    r_cn = fem.residual_only(prob, lev, y1, tr=_cn(y0, dt))
+    r_st = fem.residual_only(prob, lev, y1)
+    want = np.zeros(lev.N)
+    wint = _basis_integrals(lev)
+    detA = np.linalg.det(A)
+    for e in range(lev.n_elem):
+        solid = bool(lev.elem_solid[e])
+        for a, node in enumerate(lev.elem_nodes[e]):
+            cls = lev.node_class[node]
+            slot0 = 0 if (solid or cls == IFACE) else n
+            rho = prob.rho_s if solid else prob.rho_f
+            for i in range(n):
+                want[node * nd + slot0 + i] += rho * detA * c[i] * wint[e, a]
+                if solid:
+                    want[node * nd + n + i] += -0.5 * c[i] * dt * wint[e, a]
+    free = ~lev.dir_mask
+    got = (r_cn - r_st)[free]
+    assert np.max(np.abs(got - want[free])) <= 1e-11 * np.max(np.abs(want))
+
+
+def test_cn_geometric_conservation_2d():
+    """Discrete geometric conservation in 2D: a uniform velocity on a mesh
+    moving affinely (d = (A(t) - I) x_hat with A linear in t, so J is
+    quadratic and J div w linear in t) leaves every free fluid momentum row
+    at zero (p = 0): the conservative difference of J u over the step equals
+    the trapezoidal average of J (div w) u exactly.  A wrong sign or weight
+    of the -(div w) u terms breaks it."""
+    lev = build_level(UNIT_FLUID, 1)
+    n, nd = 2, 4
+    B = np.array([[0.8, -0.3], [0.5, 0.6]])
+    dt, t1 = 0.05, 0.4
+    U = np.array([0.7, -0.4])
+    ys = []
+    for t in (t1, t1 - dt):
+        yk = np.zeros(lev.N)
+        dv = lev.node_xyz @ (t * B).T
+        for i in range(n):
+            yk[i:lev.n_nodes * nd:nd] = dv[:, i]
+            yk[n + i:lev.n_nodes * nd:nd] = U[i]
+        ys.append(yk)
+    r = fem.residual_only(UNIT_FLUID, lev, ys[0], tr=_cn(ys[1], dt, 0.25))
+    rows = [node * nd + n + i for node in range(lev.n_nodes) for i in range(n) if not lev.dir_mask[node * nd + n + i]]
+    scale = UNIT_FLUID.rho_f * np.max(np.abs(U)) * np.max(lev.elem_h) ** 2 / dt
+    assert np.max(np.abs(r[rows])) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("scheme,rate", [("cn", 2.0), ("bdf1", 1.0), ("bdf2", 2.0)])
+def test_temporal_rate_solid_shear_oscillation(scheme, rate):
+    """A manufactured solution in time: an incompressible Neo-Hookean block in
+    homogeneous simple shear d = s(t) (y, 0), u = s'(t) (y, 0), p = mu_s
+    (stress constant in space, J = 1), driven by the body force
+    f = s''(t) (y, 0) with all boundary values prescribed.  The space
+    discretisation is exact, so the error at T is the time discretisation's:
+    second order for Crank-Nicolson (trapezoidal inertia and kinematics with
+    the averaged force) and BDF2 (BDF1 start), first order for BDF1."""
+    prob = UNIT_SOLID
+    om = 2.0 * np.pi
+    s = lambda t: 0.05 * np.sin(om * t)
+    s1 = lambda t: 0.05 * om * np.cos(om * t)
+    s2 = lambda t: -0.05 * om * om * np.sin(om * t)
+    T = 0.4
+    errs = []
+    for nsteps in (16, 32, 64):
+        lev = build_level(prob, 1)
+        nd = 4
+        dt = T / nsteps
+        yy = lev.node_xyz[:, 1]
+        p0 = lev.n_nodes * nd
+
+        def exact(t):
+            y = np.zeros(lev.N)
+            y[0:p0:nd] = s(t) * yy
+            y[2:p0:nd] = s1(t) * yy
+            y[p0::3] = prob.mu_s
+            return y
+
+        hist = [exact(0.0)]
+        for k in range(1, nsteps + 1):
+            t = k * dt
+            ex = exact(t)
+            lev.dir_val[:] = ex
+            if scheme == "cn":
+                tr = _cn(hist[-1], dt)
+                fsrc = lambda xq, t=t: 0.5 * (s2(t) + s2(t - dt)) * xq[:, 1]
+            else:
+                order = 1 if (scheme == "bdf1" or k == 1) else 2
+                tr = dict(yn=hist[-1], ynm1=hist[-2] if order == 2 else hist[-1],
+                          a=fem.bdf_coefficients(order), dt=dt, t=0.25)
+                fsrc = lambda xq, t=t: s2(t) * xq[:, 1]
+            src = lambda xq, f=fsrc: (np.stack([f(xq), np.zeros(len(xq))], axis=1), np.zeros(len(xq)), None)
+            y = hist[-1].copy()
+            y[lev.dir_mask] = ex[lev.dir_mask]
+            for _ in range(8):
+                r, J = fem.assemble(prob, lev, y, src, tr=tr)
+                J = J.tolil()
+                J.rows[p0] = [p0]
+                J.data[p0] = [1.0]
+                J = J.tocsr()
+                r[p0] = y[p0] - prob.mu_s
+                dy = direct_solve(J, -r)
+                y = y + dy
+                if np.linalg.norm(dy) < 1e-13 * np.linalg.norm(y):
+                    break
+            hist.append(y)
+        e = hist[-1] - exact(T)
+        errs.append(np.max(np.abs(e[0:lev.n_nodes * nd:nd])))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > rate - 0.15, (errs, rates)
+    assert rates[-1] < rate + 0.5, (errs, rates)

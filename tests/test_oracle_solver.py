@@ -230,3 +230,116 @@ def test_newton_converges_quadratically():
     # steps square the relative update up to a modest factor
     assert rels[-1] < 1e3 * rels[-2] ** 2
     assert rels[-2] < rels[-3] * 1e-1
+
+
+# ----------------------------------------------------------------------------
+# left-preconditioned GMRES(m) (Sec. 4.1)
+# ----------------------------------------------------------------------------
+
+def _krylov_min(A, P, b, x0, k):
+    """Brute force: x in x0 + K_k(P A, P r0) minimising ||P (b - A x)||, from
+    an orthonormal basis of the explicit Krylov vectors (numpy QR + lstsq)."""
+    r = P @ (b - A @ x0)
+    K = [r]
+    for _ in range(k - 1):
+        K.append(P @ (A @ K[-1]))
+    Q, _ = np.linalg.qr(np.array(K).T)
+    y, *_ = np.linalg.lstsq(P @ A @ Q, r, rcond=None)
+    return x0 + Q @ y
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_gmres_left_minimises_the_preconditioned_residual(passes):
+    """After k steps without restart the iterate minimises the left-
+    preconditioned residual over the Krylov space; with restart m the same
+    holds cycle by cycle, each cycle starting from the previous iterate."""
+    from oracle.solver import gmres_left
+    rng = np.random.default_rng(1)
+    n = 30
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.5
+    P = np.linalg.inv(np.eye(n) * 3 + np.triu(rng.standard_normal((n, n)) * 0.3))
+    b = rng.standard_normal(n)
+    x, st = gmres_left(A, b, lambda v: P @ v, restart=20, rtol=1e-30, max_iters=7, gs_passes=passes)
+    assert st.iters == 7
+    want = _krylov_min(A, P, b, np.zeros(n), 7)
+    assert np.linalg.norm(x - want) <= 1e-10 * np.linalg.norm(want)
+    x, st = gmres_left(A, b, lambda v: P @ v, restart=3, rtol=1e-30, max_iters=6, gs_passes=passes)
+    x1 = _krylov_min(A, P, b, np.zeros(n), 3)
+    want = _krylov_min(A, P, b, x1, 3)
+    assert np.linalg.norm(x - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_gmres_left_stopping_rule():
+    """It stops at the first step whose minimal left-preconditioned residual
+    is below rtol times the initial one (brute force over k), and reports
+    that ratio; identity preconditioning of a 5 x 5 diagonal system takes at
+    most 5 steps."""
+    from oracle.solver import gmres_left
+    rng = np.random.default_rng(2)
+    n = 25
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) * 0.4
+    P = np.diag(1.0 / np.diag(A))
+    b = rng.standard_normal(n)
+    x, st = gmres_left(A, b, lambda v: P @ v, restart=50, rtol=1e-6, max_iters=50)
+    r0 = np.linalg.norm(P @ b)
+    ks = [k for k in range(1, n + 1)
+          if np.linalg.norm(P @ (b - A @ _krylov_min(A, P, b, np.zeros(n), k))) < 1e-6 * r0]
+    assert st.iters == ks[0]
+    assert st.rel_res == pytest.approx(np.linalg.norm(P @ (b - A @ x)) / r0, rel=1e-8)
+    D = np.diag([1.0, 2.0, 3.0, 4.0, 5.0])
+    _, st = gmres_left(D, np.ones(5), lambda v: v, restart=10, rtol=1e-12)
+    assert st.iters <= 5 and st.rel_res < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# nested iteration (full multigrid) for the steady problem (Sec. 3)
+# ----------------------------------------------------------------------------
+
+def test_state_injection_keeps_boundary_data_and_coarse_fields():
+    """Injecting a coarse state whose node values are a global biquadratic
+    field (in every level's Q2 space) reproduces that field at every free
+    fine unknown - including the fine nodes next to the boundary, whose
+    coarse stencil holds boundary nodes, so boundary values are carried, not
+    dropped as in the correction prolongation - and sets every fine
+    Dirichlet unknown to its data."""
+    from oracle.mesh import build_level
+    from oracle.solver import inject_state, transfer_operators
+    from paper_1709_05660_gb300.workloads import Problem
+    prob = Problem(levels=2, U=0.3)
+    c, f = build_level(prob, 0), build_level(prob, 1)
+    nd = 4
+    q = lambda xy, s_: (0.3 + 0.7 * xy[:, 0] - 1.1 * xy[:, 1] ** 2 + 0.2 * xy[:, 0] * xy[:, 1]
+                        + 0.05 * xy[:, 0] ** 2 * xy[:, 1] ** 2) * (s_ + 1)
+    yc = np.zeros(c.N)
+    for s_ in range(nd):
+        yc[s_:c.n_nodes * nd:nd] = q(c.node_xyz, s_)
+    yf = inject_state(c, f, yc)
+    assert np.array_equal(yf[f.dir_mask], f.dir_val[f.dir_mask])
+    want = np.zeros(f.N)
+    for s_ in range(nd):
+        want[s_:f.n_nodes * nd:nd] = q(f.node_xyz, s_)
+    free = ~f.dir_mask
+    free[f.n_nodes * nd:] = False
+    assert np.max(np.abs(yf[free] - want[free])) <= 1e-13 * np.max(np.abs(want))
+    # the masked correction prolongation differs exactly where coarse boundary
+    # values enter free fine unknowns
+    P, _ = transfer_operators(c, f)
+    assert np.max(np.abs((P @ yc)[free] - want[free])) > 1e-3
+
+
+def test_fmg_reaches_the_steady_state_of_plain_newton():
+    """Nested iteration from the coarsest mesh ends at the same discrete
+    steady state as plain Newton on the finest mesh from the lift, with no
+    more finest-level Newton steps."""
+    from oracle.mesh import initial_state
+    from oracle.solver import Oracle, fmg_newton
+    from paper_1709_05660_gb300.workloads import Problem, SolverOpts
+    prob, opts = Problem(levels=3, mu_s=5e5, U=0.2), SolverOpts(tile=(2, 2))
+    y_fmg, hists = fmg_newton(prob, opts, tol=1e-10)
+    assert len(hists) == 3 and all(h[-1][0] < 1e-10 for h in hists)
+    orc = Oracle(prob, opts)
+    y_pl, hist_pl = orc.newton(initial_state(prob, orc.fine, np.zeros(orc.fine.N)), tol=1e-10, linear="direct")
+    assert np.linalg.norm(y_fmg - y_pl) <= 1e-9 * np.linalg.norm(y_pl)
+    assert len(hists[-1]) <= len(hist_pl)
+    r, _ = orc.assemble(y_fmg)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(orc.assemble(initial_state(prob, orc.fine, np.zeros(orc.fine.N)))[0])
