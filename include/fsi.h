@@ -57,7 +57,9 @@ enum {
 enum { FSI_FP64 = 0, FSI_MIXED = 1 };
 enum { FSI_MAX_BREAKS = 65 };
 
-/* Problem descriptor (Sec. 2, 4).  The coarse tensor grid is given by its
+/* Problem descriptor (Sec. 2, 4).  The solid is incompressible Neo-Hookean, or
+ * Mooney-Rivlin when mr_c2 != 0 (Sec. 2.2); mu_s = 2 (C1 + C2) is the shear
+ * modulus of the linearised law.  The coarse tensor grid is given by its
  * cell boundaries per axis; every finer level is one midpoint refinement
  * (Sec. 3.2).  Elements whose centroid lies inside [flap_lo, flap_hi] are
  * solid, the rest fluid.  Boundary conditions: d = 0 on the whole outer
@@ -75,6 +77,8 @@ typedef struct {
   int transient;                        /* 0: steady; 1: time step of the BDF form (Sec. 2) */
   double dt;                            /* time step (transient only, > 0) */
   int ale_op;                           /* 0: k(grad d + grad d^T), k = 1/V_el; 1: k grad d */
+  double mr_c2;                         /* Mooney-Rivlin C2 (Sec. 2.2): sigma = -p I + 2 C1 B - 2 C2 B^{-1}
+                                           with C1 = mu_s/2 - C2; 0 = Neo-Hookean */
 } fsi_problem_desc;
 
 /* Solver options (Sec. 3.3, 4.1). */
@@ -82,11 +86,17 @@ typedef struct {
   int tile[3];         /* Schwarz block = aligned tile of elements per axis */
   int n_pre, n_post;   /* Richardson smoothing steps before / after the coarse correction */
   double omega;        /* Richardson damping */
-  int restart;         /* FGMRES restart length (<= 64) */
-  double rtol;         /* stop when ||b - J x|| <= rtol ||b|| (true residual) */
-  int max_iters;       /* total FGMRES iterations */
-  int precision;       /* FSI_FP64 (FSI_MIXED is reserved) */
+  int restart;         /* Krylov restart length (<= 64) */
+  double rtol;         /* krylov 0: stop when ||b - J x|| <= rtol ||b|| (true residual);
+                          krylov 1: when ||P^{-1}(b - J x)|| < rtol ||P^{-1}(b - J x0)|| */
+  int max_iters;       /* total Krylov iterations */
+  int precision;       /* FSI_FP64, or FSI_MIXED: FP32 V-cycle and Schwarz inverses, FP64 elsewhere */
+  int krylov;          /* FSI_FGMRES (0): right-preconditioned flexible GMRES, true-residual test;
+                          FSI_GMRES_LEFT (1): left-preconditioned GMRES, the paper's setting (Sec. 4.1) */
+  int gs_passes;       /* classical Gram-Schmidt passes per Arnoldi step: 1 or 2 (0: 2 for FGMRES,
+                          1 for left GMRES, the paper's unmodified classical Gram-Schmidt) */
 } fsi_solver_opts;
+enum { FSI_FGMRES = 0, FSI_GMRES_LEFT = 1 };
 
 typedef struct {
   int iters;             /* FGMRES iterations (Arnoldi steps) */
@@ -94,6 +104,8 @@ typedef struct {
   double rel_res;        /* final true ||b - J x|| / ||b|| */
   double rho;            /* average convergence rate (rel_res)^(1/iters) (Sec. 4.2) */
   double t_assemble_ms, t_factor_ms, t_solve_ms;  /* device time of the last calls */
+  double prec_rel_res;   /* left GMRES: final ||P^{-1} r|| / ||P^{-1} r_0|| (the stopping test);
+                            FGMRES: equal to rel_res */
 } fsi_solve_stats;
 
 typedef struct fsi_ctx fsi_ctx;
@@ -101,7 +113,8 @@ typedef struct fsi_ctx fsi_ctx;
 /* Builds the mesh hierarchy, unknown numbering, block-sparse patterns, grid
  * transfers, Schwarz blocks and all device workspaces (Sec. 2.5, 3.2, 3.3).
  * `stream` is a cudaStream_t (NULL = legacy default stream).  On success
- * *out owns all device memory of the instance; free it with fsi_destroy. */
+ * *out owns all device memory of the instance; free it with fsi_destroy.
+ * Errors: FSI_E_INVALID (bad descriptor or options), FSI_E_OOM, FSI_E_CUDA. */
 int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opts,
                         void* stream, fsi_ctx** out);
 /* Host-only variant: builds the same hierarchy, numbering, patterns,
@@ -112,19 +125,33 @@ int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opt
  * size an instance before admitting it, and to check the numbering without
  * a device. */
 int fsi_plan_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opts, fsi_ctx** out);
+/* Waits for the ctx's stream and frees everything the ctx owns (the device
+ * data of the hierarchy of Sec. 3.2 and the factors of Sec. 3.3).  NULL is a
+ * no-op. */
 void fsi_destroy(fsi_ctx* ctx);
+/* Message of the last failed call on ctx (owned by ctx, valid until its next
+ * call). */
 const char* fsi_last_error(const fsi_ctx* ctx);
+/* Rebinds the ctx to another cudaStream_t of the same device: waits for the
+ * old stream, then orders all later work of the ctx on `stream`.  Lets a
+ * caller run consecutive Newton steps of one instance on whichever of its
+ * streams is free (the serving loop does).  No counterpart in the paper. */
+int fsi_set_stream(fsi_ctx* ctx, void* stream);
 
 /* Sizes: N (canonical unknowns) and scalar nnz of J per level (arrays of
  * `levels` entries, level 0 = coarse) and the device bytes held by ctx (for a
- * planned ctx: the bytes fsi_build_hierarchy would allocate). */
+ * planned ctx: the bytes fsi_build_hierarchy would allocate).  The counts are
+ * those of the Q2-P1disc spaces of Sec. 2.5 on each mesh of Sec. 3.2 (the
+ * unknown counts of the table in Sec. 4); any pointer may be NULL. */
 int fsi_get_sizes(const fsi_ctx* ctx, int64_t* n_per_level, int64_t* nnz_per_level,
                   int64_t* hbm_bytes);
 
 /* Benchmark linearisation state: d = 0, p = 0, u_x = inflow profile at every
  * fluid node whose u_x is free (0 at solid and interface nodes), Dirichlet
  * values at Dirichlet unknowns, then noise[i] added at every free
- * displacement unknown.  noise and y_out: N doubles (host or device). */
+ * displacement unknown.  noise and y_out: N doubles (host or device; a
+ * planned ctx takes host buffers).  With zero noise this is the
+ * boundary-condition lift that starts a nonlinear solve. */
 int fsi_initial_state(fsi_ctx* ctx, const double* noise, double* y_out);
 
 /* Sets the Newton state y (N doubles).  Steady problems ignore y_prev,
@@ -156,9 +183,13 @@ int fsi_assemble_jacobian(fsi_ctx* ctx, double* residual_out);
  * coarse part on the ctx's private stream).  FSI_E_SINGULAR on a zero pivot. */
 int fsi_factor_schwarz(fsi_ctx* ctx);
 
-/* Right-preconditioned FGMRES(restart) on J x = b with the multigrid V-cycle
- * as preconditioner (Sec. 3, 4.1).  x holds the initial guess on entry and
- * the solution on exit (N doubles each).  stats may be NULL. */
+/* Krylov solve of J x = b with the multigrid V-cycle P as preconditioner
+ * (Sec. 3, 4.1): right-preconditioned FGMRES(restart) with a true-residual
+ * test, or (opts.krylov = FSI_GMRES_LEFT) the paper's left-preconditioned
+ * GMRES(restart) with its test on the left-preconditioned residual.  x holds
+ * the initial guess on entry and the solution on exit (N doubles each).
+ * stats may be NULL; on FSI_E_NOT_CONVERGED they are filled and x holds the
+ * last iterate. */
 int fsi_solve(fsi_ctx* ctx, const double* b, double* x, fsi_solve_stats* stats);
 
 /* Newton update y += dx (Sec. 3.1, 4.1); *rel_step_out = ||dx|| / ||y_new||. */
@@ -168,27 +199,75 @@ int fsi_newton_update(fsi_ctx* ctx, const double* dx, double* rel_step_out);
  * J dx = -r, update.  dx_out (N doubles, may be NULL) receives dx. */
 int fsi_newton_step(fsi_ctx* ctx, double* dx_out, double* rel_step_out, fsi_solve_stats* stats);
 
+/* ---- nested iteration (full multigrid) for the steady problem ---------- */
+
+enum { FSI_FMG_MAX_LEVELS = 16 };
+typedef struct {
+  int levels;                                  /* mesh levels solved (= desc.levels) */
+  int newton_steps[FSI_FMG_MAX_LEVELS];        /* Newton steps on mesh level l (0 = coarsest) */
+  int krylov_iters[FSI_FMG_MAX_LEVELS];        /* Krylov iterations summed over those steps */
+  double last_rel_step[FSI_FMG_MAX_LEVELS];    /* ||dy|| / ||y|| of the level's last step */
+  double ms[FSI_FMG_MAX_LEVELS];               /* device time of the level's steps (assemble + factor + solve) */
+  int status;                                  /* FSI_OK or the first error */
+} fsi_fmg_stats;
+
+/* Steady nonlinear problem by nested iteration, the full-multigrid driver of
+ * Sec. 3: Newton (each step an fsi_newton_step: exact Jacobian, Galerkin
+ * hierarchy, Schwarz and coarse factors, Krylov solve) to ||dy|| < tol ||y||
+ * on the coarsest mesh from the boundary-condition lift (the state of
+ * fsi_initial_state without noise), then on every finer mesh up to
+ * desc->levels from the coarser solution carried over by the natural
+ * injection of the nested spaces (Sec. 3.2; every unknown including its
+ * boundary values, then the fine Dirichlet data).  Mesh level l is solved
+ * with its own multigrid hierarchy of levels 0..l, built and freed in turn.
+ * y_out receives the finest state (N doubles, host or device).  Steady
+ * problems only (FSI_E_INVALID otherwise); FSI_E_NOT_CONVERGED when a level
+ * needs more than max_steps steps; stats may be NULL. */
+int fsi_fmg_newton(const fsi_problem_desc* desc, const fsi_solver_opts* opts, void* stream, double tol,
+                   int max_steps, double* y_out, fsi_fmg_stats* stats);
+
 /* ---- parity / diagnostics ------------------------------------------- */
 
 /* J_level in canonical CSR (host buffers): rowptr[N+1], col[nnz], val[nnz];
- * columns ascending; the pattern is the full FE graph (explicit zeros kept). */
+ * columns ascending; the pattern is the full FE graph (explicit zeros kept),
+ * i.e. the block structure of the Jacobian of Sec. 3.1.  col or val may be
+ * NULL (pattern or values only; a planned ctx has no values). */
 int fsi_export_csr(fsi_ctx* ctx, int level, int64_t* rowptr, int32_t* col, double* val);
-/* node_class[n_nodes] (0 fluid, 1 solid, 2 interface), elem_solid[n_elem],
- * dirichlet[N] (0/1), dir_val[N]; any pointer may be NULL; host buffers. */
+/* Unknown classification of Sec. 3.1: node_class[n_nodes] (0 fluid, 1 solid,
+ * 2 interface), elem_solid[n_elem], dirichlet[N] (0/1) and dir_val[N] (the
+ * boundary data of Sec. 4); any pointer may be NULL; host buffers. */
 int fsi_export_dofmap(fsi_ctx* ctx, int level, uint8_t* node_class, uint8_t* elem_solid,
                       uint8_t* dirichlet, double* dir_val);
-/* Schwarz blocks of a level >= 1: n_patches (may be NULL); ptr[n_patches+1]
+/* Schwarz blocks of Sec. 3.3 on a level >= 1: the overlapping sets R^delta_k
+ * and the owned sets R^0_k.  n_patches (may be NULL); ptr[n_patches+1]
  * offsets into dofs / owned; dofs ascending canonical unknowns (R^delta_k);
  * owned[i] = 1 if dofs[i] is in R^0_k.  Pass ptr = NULL to query the total
  * length through *total_len. */
 int fsi_export_patches(fsi_ctx* ctx, int level, int* n_patches, int64_t* total_len,
                        int64_t* ptr, int32_t* dofs, uint8_t* owned);
-/* Grid transfer matrices between level and level-1 in canonical CSR (host
- * buffers): which = 0 prolongation P (N_level rows), which = 1 restriction R
+/* Grid transfer matrices of Sec. 3.2 (natural injection P and the
+ * interface-aware restriction R) between level and level-1 in canonical CSR
+ * (host buffers): which = 0 prolongation P (N_level rows), which = 1 restriction R
  * (N_{level-1} rows); rowptr[rows+1], col[nnz], val[nnz], columns ascending.
  * Pass col = NULL to query *nnz only. */
 int fsi_export_transfer(fsi_ctx* ctx, int level, int which, int64_t* nnz, int64_t* rowptr, int32_t* col,
                         double* val);
+/* Replaces the values of J_level (level's pattern, canonical CSR order of
+ * fsi_export_csr; val: nnz host doubles) until the next
+ * fsi_assemble_jacobian.  For tests of the later steps in isolation (Sec. 3.2,
+ * 3.3 on a given operator) and for injecting a defective operator, e.g. a
+ * zero column that makes a Schwarz block singular (FSI_E_SINGULAR from
+ * fsi_factor_schwarz).  The values are copied; on a mixed-precision instance
+ * the FP32 copy of a level >= 1 is refreshed too. */
+int fsi_import_csr(fsi_ctx* ctx, int level, const double* val);
+/* Iteration limit of the first bounded wait of each Schwarz-block
+ * factorisation on its tensor-core work (mixed precision).  When it runs out
+ * the block waits (with the full limit) for the work it has already issued,
+ * releases its tensor memory and reports FSI_E_TIMEOUT from
+ * fsi_factor_schwarz; the ctx stays usable.  iters < 0 restores the built-in
+ * limit (2^22).  A diagnostic of the time-out path; no counterpart in the
+ * paper. */
+int fsi_set_tc_wait_limit(fsi_ctx* ctx, long long iters);
 /* y = J_level x (level's canonical numbering). */
 int fsi_apply_operator(fsi_ctx* ctx, int level, const double* x, double* y);
 /* z = one V-cycle applied to b on the finest level (the preconditioner). */
@@ -212,9 +291,10 @@ enum { FSI_STATIC_COARSE_MAX = 4096, FSI_STATIC_PART_MAX = 1 << 19 };
 
 /* x = J_0^{-1} b on level 0 (canonical numbering, FP64; host or device
  * buffers) with the dense coarse inverse of fsi_factor_schwarz: the same
- * kernels and summation order as the coarse step of fsi_apply_vcycle, so the
- * result equals that of fsi_apply_vcycle on a one-level instance bit for
- * bit.  The GEMV partial sums live in a file-scope device array of
+ * kernels and summation order as the FP64 coarse step of fsi_apply_vcycle,
+ * so on an FP64 (precision FSI_FP64) one-level instance the result equals
+ * that of fsi_apply_vcycle bit for bit.  (A mixed-precision instance's
+ * V-cycle rounds its coarse input and output to FP32; this call does not.)  The GEMV partial sums live in a file-scope device array of
  * FSI_STATIC_PART_MAX doubles instead of instance scratch, and the call
  * allocates no device or pinned memory.  It is meant for callers that cannot
  * allocate at call time: a serving worker whose instances were admitted
@@ -222,7 +302,9 @@ enum { FSI_STATIC_COARSE_MAX = 4096, FSI_STATIC_PART_MAX = 1 << 19 };
  * several streams at once, for whom a cudaMalloc / cudaFree could
  * synchronise the device and stall the other streams.
  * Limits: FSI_E_INVALID when the level-0 internal length exceeds
- * FSI_STATIC_COARSE_MAX, and for 3D instances (slab-blocked coarse LU).
+ * FSI_STATIC_COARSE_MAX, for 3D instances (slab-blocked coarse LU), before
+ * the first fsi_factor_schwarz, and when the calling thread's current
+ * device is not the one the ctx was built on.
  * The array is shared by every instance on a device: calls that overlap in
  * time (two threads or two streams) race on it and must be serialised by the
  * caller.  The first call on a device resolves the array's address once
@@ -286,6 +368,10 @@ int fsi_get_launch_params(fsi_ctx* ctx, int level, fsi_launch_params* out);
 int fsi_time_level_kernels(fsi_ctx* ctx, int level, int reps, double* apply_ms, double* spmv_ms);
 
 /* ---- serving: continuous batching of Newton-step requests ---------------
+ *
+ * No counterpart in the paper (its solver runs one problem at a time, Sec.
+ * 4.1): a serving form of the Newton step of Sec. 3.1 for many independent
+ * instances on one GPU.
  *
  * A server owns `max_slots` worker threads, each with its own CUDA stream, and
  * a device-memory budget.  A request asks for one Newton step (assemble,

@@ -216,6 +216,7 @@ void build_device(Ctx& c) {
     if (l > 0) {
       D.P_ptr = upload(c, H.P_ptr); D.P_col = upload(c, H.P_col); D.P_val = upload(c, H.P_val);
       D.R_ptr = upload(c, H.R_ptr); D.R_col = upload(c, H.R_col); D.R_val = upload(c, H.R_val);
+      D.S_ptr = upload(c, H.S_ptr); D.S_col = upload(c, H.S_col); D.S_val = upload(c, H.S_val);
       D.n_patches = H.n_patches;
       D.max_n = H.max_n;
       D.max_nown = H.max_nown;
@@ -374,7 +375,7 @@ void assemble(Ctx& c, bool want_res) {
   const int L = (int)c.dl.size();
   const int B = c.B;
   DevLevel& F = c.dl[L - 1];
-  PhysParams pp{c.desc.rho_f, c.desc.mu_f, c.desc.rho_s, c.desc.mu_s, c.desc.ale_op};
+  PhysParams pp{c.desc.rho_f, c.desc.mu_f, c.desc.rho_s, c.desc.mu_s, c.desc.ale_op, c.desc.mr_c2};
   const bool transient = c.desc.transient != 0;
   if (transient) {
     if (!c.have_history) throw ApiError(FSI_E_INVALID, "transient problem: fsi_set_state needs y_prev first");
@@ -558,6 +559,7 @@ void schwarz_factor(Ctx& c) {
     float* ws = reinterpret_cast<float*>(c.dense_ws);
     GjLevels lv{};
     lv.nlev = 0;
+    lv.first_wait = c.tc_first_wait >= 0 ? c.tc_first_wait : kTcWaitIters;
     int first = 0, max_n = 0;
     double by = 0.0, fl = 0.0;
     int64_t off = 0;
@@ -879,6 +881,143 @@ void precondition(Ctx& c, const double* v, double* z64, float* z32) {
 }
 
 // ---------------------------------------------------------------------------
+// Arnoldi orthonormalisation of c.w against V[0..j] by classical Gram-Schmidt
+// with `passes` passes (each pass's j + 1 dot products in one sweep over the
+// basis), v_{j+1} = w / ||w||.  Returns the Hessenberg column h[0..j] and
+// ||w|| after / before orthogonalisation (host values).
+// ---------------------------------------------------------------------------
+void orthonormalize(Ctx& c, int j, int passes, double* h, double* hn, double* wn0) {
+  const int L = (int)c.dl.size();
+  const int64_t n = c.dl[L - 1].Ni;
+  const int nb = nblk_red(c);
+  double* sm = c.small;
+  double* hs = c.host_small;
+  Prof pr(c, FSI_K_KRYLOV, (2.0 * passes * (j + 1) + 8.0) * n * 8.0, (4.0 * passes * (j + 1) + 4.0) * n,
+          passes == 2 ? 8 : 5);
+  // pass 1: h1 = V^T w (with ||w||^2)
+  launch_arnoldi_dots(n, c.V, n, j + 1, c.w, true, c.partial, nb, c.stream);
+  launch_reduce(c.partial, j + 2, nb, sm, false, c.stream);             // h1 = sm[0..j], ||w||^2 = sm[j+1]
+  const double* hlast = sm;
+  if (passes == 2) {
+    launch_cgs_update(n, c.V, n, j + 1, sm, c.w, c.stream);
+    launch_arnoldi_dots(n, c.V, n, j + 1, c.w, false, c.partial, nb, c.stream);
+    launch_reduce(c.partial, j + 1, nb, sm + 128, false, c.stream);     // h2
+    hlast = sm + 128;
+  }
+  launch_arnoldi_update_norm(n, c.V, n, j + 1, hlast, c.w, c.partial, nb, c.stream);
+  launch_reduce(c.partial, 1, nb, sm + 257, true, c.stream);            // ||w|| after the passes
+  launch_scale_by(n, c.w, sm + 257, c.V + (size_t)(j + 1) * n, c.stream);
+  counted(c, passes == 2 ? 8 : 5);
+  ck(cudaMemcpyAsync(hs, sm, 260 * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "D2H");
+  sync(c);
+  for (int i = 0; i <= j; ++i) h[i] = hs[i] + (passes == 2 ? hs[128 + i] : 0.0);
+  *hn = hs[257];
+  *wn0 = std::sqrt(hs[j + 1]);
+}
+
+// out = M^{-1} in on the finest level, FP64 in and out (FP32 V-cycle inside on
+// the mixed path)
+void precondition64(Ctx& c, const double* in, double* out) {
+  const int L = (int)c.dl.size();
+  DevLevel& F = c.dl[L - 1];
+  if (c.mixed) {
+    precondition(c, in, nullptr, F.x32);
+    launch_to_f64(F.Ni, F.x32, out, c.stream);
+    counted(c);
+  } else {
+    precondition(c, in, out, nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GMRES(m), left preconditioned (Sec. 4.1): Arnoldi on P^{-1} J with
+// classical Gram-Schmidt, x += V y, convergence when the left-preconditioned
+// residual ||P^{-1}(b - J x_j)|| < rtol ||P^{-1}(b - J x_0)|| (the Givens
+// estimate inside a cycle, the recomputed value at every restart)
+// ---------------------------------------------------------------------------
+void gmres_left(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
+  const int L = (int)c.dl.size();
+  DevLevel& F = c.dl[L - 1];
+  const int64_t n = F.Ni;
+  const int m = c.opts.restart;
+  const int passes = c.opts.gs_passes > 0 ? c.opts.gs_passes : 1;
+  double* sm = c.small;
+  const double bnorm = dev_norm(c, n, b, sm + 300);
+  if (!std::isfinite(bnorm)) throw ApiError(FSI_E_NONFINITE, "non-finite right-hand side");
+  auto prec_residual = [&]() {   // c.w = P^{-1}(b - J x), returns its norm
+    launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, x, b, c.tmp, c.stream);
+    counted(c);
+    precondition64(c, c.tmp, c.w);
+    return dev_norm(c, n, c.w, sm + 301);
+  };
+  double beta = prec_residual();
+  const double r0 = beta;
+  int iters = 0, restarts = 0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yv(m), hcol(m + 1);
+  auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  while (r0 > 0.0) {
+    if (!std::isfinite(beta)) throw ApiError(FSI_E_NONFINITE, "non-finite residual in GMRES");
+    if (beta < c.opts.rtol * r0 || iters >= c.opts.max_iters) break;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    launch_scale_by(n, c.w, sm + 301, c.V, c.stream);
+    counted(c);
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      const double* vj = c.V + (size_t)j * n;
+      spmv(c, L - 1, vj, nullptr, c.tmp);     // t = J v_j (FP64)
+      precondition64(c, c.tmp, c.w);          // w = P^{-1} t
+      double hn = 0.0, wn0 = 0.0;
+      orthonormalize(c, j, passes, hcol.data(), &hn, &wn0);
+      if (!std::isfinite(hn)) throw ApiError(FSI_E_NONFINITE, "non-finite Krylov vector");
+      for (int i = 0; i <= j; ++i) Hc(i, j) = hcol[i];
+      Hc(j + 1, j) = hn;
+      const bool breakdown = hn <= 1e-14 * wn0;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+        Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+        Hc(i, j) = t;
+      }
+      const double den = std::hypot(Hc(j, j), Hc(j + 1, j));
+      cs[j] = Hc(j, j) / den;
+      sn[j] = Hc(j + 1, j) / den;
+      Hc(j, j) = den;
+      Hc(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++iters;
+      k = j + 1;
+      if (std::fabs(g[j + 1]) < c.opts.rtol * r0 || breakdown || iters >= c.opts.max_iters) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < k; ++q) s -= Hc(i, q) * yv[q];
+      yv[i] = s / Hc(i, i);
+    }
+    std::memcpy(c.host_small + 384, yv.data(), k * sizeof(double));
+    ck(cudaMemcpyAsync(sm + 384, c.host_small + 384, k * sizeof(double), cudaMemcpyHostToDevice, c.stream), "H2D");
+    launch_combo(n, c.V, n, k, sm + 384, x, c.stream);
+    counted(c);
+    beta = prec_residual();
+    ++restarts;
+  }
+  // true residual of the result, for the statistics
+  launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, x, b, c.tmp, c.stream);
+  counted(c);
+  const double rt = dev_norm(c, n, c.tmp, sm + 302);
+  const double prel = r0 > 0.0 ? beta / r0 : 0.0;
+  if (st) {
+    st->iters = iters;
+    st->restarts = restarts;
+    st->rel_res = bnorm > 0.0 ? rt / bnorm : 0.0;
+    st->prec_rel_res = prel;
+    st->rho = iters > 0 ? std::pow(prel, 1.0 / iters) : 0.0;
+  }
+  if (!(prel < c.opts.rtol) && r0 > 0.0) throw ApiError(FSI_E_NOT_CONVERGED, "GMRES reached max_iters");
+}
+
+// ---------------------------------------------------------------------------
 // FGMRES(m), right preconditioned, CGS2, true residual at restart / exit
 // ---------------------------------------------------------------------------
 void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
@@ -894,13 +1033,14 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
   double rel = 0.0;
   if (!std::isfinite(bnorm)) throw ApiError(FSI_E_NONFINITE, "non-finite right-hand side");
   if (bnorm == 0.0) {
-    if (st) { st->iters = 0; st->restarts = 0; st->rel_res = 0.0; st->rho = 0.0; }
+    if (st) { st->iters = 0; st->restarts = 0; st->rel_res = 0.0; st->prec_rel_res = 0.0; st->rho = 0.0; }
     return;
   }
   launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, x, b, c.w, c.stream);
   counted(c);
   double beta = dev_norm(c, n, c.w, sm + 301);
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yv(m);
+  const int passes = c.opts.gs_passes > 0 ? c.opts.gs_passes : 2;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yv(m), hcol(m + 1);
   auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   while (true) {
     if (!std::isfinite(beta)) throw ApiError(FSI_E_NONFINITE, "non-finite residual in FGMRES");
@@ -928,22 +1068,10 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
         precondition(c, vj, zj, nullptr);
         spmv(c, L - 1, zj, nullptr, c.w);
       }
-      // CGS2: h1 = V^T w (with ||w||^2), w -= V h1, h2 = V^T w, w -= V h2 (with
-      // ||w||^2), v_{j+1} = w / ||w||; every V^T w is one pass over V for all j + 1 dots
-      Prof pr(c, FSI_K_KRYLOV, (4.0 * (j + 1) + 8.0) * n * 8.0, (8.0 * (j + 1) + 4.0) * n, 8);
-      launch_arnoldi_dots(n, c.V, n, j + 1, c.w, true, c.partial, nb, c.stream);
-      launch_reduce(c.partial, j + 2, nb, sm, false, c.stream);             // h1 = sm[0..j], ||w||^2 = sm[j+1]
-      launch_cgs_update(n, c.V, n, j + 1, sm, c.w, c.stream);
-      launch_arnoldi_dots(n, c.V, n, j + 1, c.w, false, c.partial, nb, c.stream);
-      launch_reduce(c.partial, j + 1, nb, sm + 128, false, c.stream);       // h2
-      launch_arnoldi_update_norm(n, c.V, n, j + 1, sm + 128, c.w, c.partial, nb, c.stream);
-      launch_reduce(c.partial, 1, nb, sm + 257, true, c.stream);            // ||w|| after both passes
-      launch_scale_by(n, c.w, sm + 257, c.V + (size_t)(j + 1) * n, c.stream);
-      counted(c, 8);
-      ck(cudaMemcpyAsync(hs, sm, 260 * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "D2H");
-      sync(c);
-      for (int i = 0; i <= j; ++i) Hc(i, j) = hs[i] + hs[128 + i];
-      const double hn = hs[257], wn0 = std::sqrt(hs[j + 1]);
+      // CGS (two passes by default): h = V^T w, w -= V h per pass, v_{j+1} = w / ||w||
+      double hn = 0.0, wn0 = 0.0;
+      orthonormalize(c, j, passes, hcol.data(), &hn, &wn0);
+      for (int i = 0; i <= j; ++i) Hc(i, j) = hcol[i];
       if (!std::isfinite(hn)) throw ApiError(FSI_E_NONFINITE, "non-finite Krylov vector");
       Hc(j + 1, j) = hn;
       const bool breakdown = hn <= 1e-14 * wn0;
@@ -982,9 +1110,15 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
     st->iters = iters;
     st->restarts = restarts;
     st->rel_res = rel;
+    st->prec_rel_res = rel;
     st->rho = iters > 0 ? std::pow(rel, 1.0 / iters) : 0.0;
   }
   if (!(rel <= c.opts.rtol)) throw ApiError(FSI_E_NOT_CONVERGED, "FGMRES reached max_iters");
+}
+
+void krylov_solve(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
+  if (c.opts.krylov == FSI_GMRES_LEFT) gmres_left(c, b, x, st);
+  else fgmres(c, b, x, st);
 }
 
 float elapsed(Ctx& c) {
@@ -1050,7 +1184,8 @@ static int64_t estimate_device_bytes(const Ctx& c) {
     b += H.n_elem * (H.nloc * 4.0 + 1.0 + 2.0 * H.dim * 8.0 + (H.nloc + 1.0) * (H.nloc + 1.0) * 4.0 + 4.0);
     b += H.n_nodes + H.Ni * (1.0 + 8.0 + 4.0 + 4.0) + H.N * 4.0 + H.Ni * 3.0 * 8.0;
     if (l > 0) {
-      b += (H.P_ptr.size() + H.R_ptr.size()) * 4.0 + (H.P_col.size() + H.R_col.size()) * 12.0;
+      b += (H.P_ptr.size() + H.R_ptr.size() + H.S_ptr.size()) * 4.0 +
+           (H.P_col.size() + H.R_col.size() + H.S_col.size()) * 12.0;
       b += H.idx_total * 4.0 + H.own_total * 4.0 + H.n_patches * 8.0 * 8.0 + H.p_gmap.size() * 4.0 +
            H.p_padpos.size() * 4.0 + H.inv_total * fs + 2.0 * H.idx_total * fs;
       if (mixed) b += H.nnzb * B * B * 4.0 + (H.P_col.size() + H.R_col.size()) * 4.0 + H.Ni * 3.0 * 4.0;
@@ -1088,6 +1223,8 @@ static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts
   if (opts->restart < 1 || opts->restart > 64) throw ApiError(FSI_E_INVALID, "restart must be in [1, 64]");
   if (opts->n_pre < 0 || opts->n_post < 0 || opts->max_iters < 1 || !(opts->rtol > 0.0))
     throw ApiError(FSI_E_INVALID, "bad solver options");
+  if ((opts->krylov != FSI_FGMRES && opts->krylov != FSI_GMRES_LEFT) || opts->gs_passes < 0 || opts->gs_passes > 2)
+    throw ApiError(FSI_E_INVALID, "bad Krylov options (krylov 0 or 1, gs_passes 0..2)");
   std::string err;
   if (!build_host_hierarchy(*desc, *opts, c->hl, err)) throw ApiError(FSI_E_INVALID, err);
   c->dim = desc->dim;
@@ -1127,6 +1264,7 @@ int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opt
     c->mixed = opts->precision == FSI_MIXED;
     int dev = 0;
     ck(cudaGetDevice(&dev), "cudaGetDevice");
+    c->device = dev;
     ck(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev), "attr");
     int coop = 0;
     ck(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "attr");
@@ -1200,11 +1338,13 @@ int fsi_get_sizes(const fsi_ctx* c, int64_t* n_per_level, int64_t* nnz_per_level
 
 int fsi_initial_state(fsi_ctx* c, const double* noise, double* y_out) {
   return guard(c, [&] {
-    need_device(*c);
+    // a host computation: also answers on a planned ctx (host buffers)
     if (!noise || !y_out) throw ApiError(FSI_E_INVALID, "null pointer");
     const HostLevel& H = c->hl.back();
     std::vector<double> nz(H.N), y(H.N, 0.0);
-    ck(cudaMemcpy(nz.data(), noise, H.N * sizeof(double), cudaMemcpyDefault), "copy noise");
+    const bool dev_in = is_device_ptr(noise), dev_out = is_device_ptr(y_out);
+    if (dev_in) ck(cudaMemcpy(nz.data(), noise, H.N * sizeof(double), cudaMemcpyDeviceToHost), "copy noise");
+    else std::memcpy(nz.data(), noise, H.N * sizeof(double));
     const int dim = H.dim, B = H.B;
     const double Hy = c->desc.breaks[1][c->desc.n_breaks[1] - 1];
     const double Hz = dim == 3 ? c->desc.breaks[2][c->desc.n_breaks[2] - 1] : 1.0;
@@ -1228,7 +1368,8 @@ int fsi_initial_state(fsi_ctx* c, const double* noise, double* y_out) {
       if (H.dir[i]) y[cidx] = H.dir_val[i];
       else if (i < H.n_nodes * B && (i % B) < dim) y[cidx] += nz[cidx];
     }
-    ck(cudaMemcpy(y_out, y.data(), H.N * sizeof(double), cudaMemcpyDefault), "copy state");
+    if (dev_out) ck(cudaMemcpy(y_out, y.data(), H.N * sizeof(double), cudaMemcpyHostToDevice), "copy state");
+    else std::memcpy(y_out, y.data(), H.N * sizeof(double));
   });
 }
 
@@ -1302,7 +1443,7 @@ int fsi_solve(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
     int rc = FSI_OK;
     std::string msg;
     try {
-      fgmres(*c, c->bk, c->xk, st);
+      krylov_solve(*c, c->bk, c->xk, st);
     } catch (const ApiError& e) {
       if (e.code != FSI_E_NOT_CONVERGED) throw;
       rc = e.code;
@@ -1352,7 +1493,7 @@ int fsi_newton_step(fsi_ctx* c, double* dx_out, double* rel_step_out, fsi_solve_
     ck(cudaMemsetAsync(c->xk, 0, n * sizeof(double), c->stream), "memset");
     counted(*c);
     ck(cudaEventRecord(c->ev0, c->stream), "event");
-    fgmres(*c, c->bk, c->xk, st);
+    krylov_solve(*c, c->bk, c->xk, st);
     ck(cudaEventRecord(c->ev1, c->stream), "event");
     sync(*c);
     c->t_solve = elapsed(*c);
@@ -1481,6 +1622,52 @@ int fsi_export_transfer(fsi_ctx* c, int level, int which, int64_t* nnz, int64_t*
   });
 }
 
+int fsi_import_csr(fsi_ctx* c, int level, const double* val) {
+  return guard(c, [&] {
+    need_device(*c);
+    check_level(*c, level, false);
+    if (!val) throw ApiError(FSI_E_INVALID, "null values");
+    const HostLevel& H = c->hl[level];
+    DevLevel& D = c->dl[level];
+    const int B = H.B, np = H.dim + 1;
+    // BSR storage of the level, padding entries zero; canonical CSR order as
+    // in fsi_export_csr
+    std::vector<double> v((size_t)H.nnzb * B * B, 0.0);
+    int64_t pos = 0;
+    for (int64_t br = 0; br < H.nb; ++br) {
+      const int rows = br < H.n_nodes ? B : np;
+      for (int ci = 0; ci < rows; ++ci)
+        for (int32_t k = H.rowptr[br]; k < H.rowptr[br + 1]; ++k) {
+          const int cols = H.col[k] < H.n_nodes ? B : np;
+          for (int cj = 0; cj < cols; ++cj) v[(size_t)k * B * B + ci * B + cj] = val[pos++];
+        }
+    }
+    ck(cudaMemcpyAsync(D.val, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream), "H2D");
+    if (c->mixed && level >= 1) {
+      launch_to_f32((int64_t)v.size(), D.val, D.val32, c->stream);
+      counted(*c);
+    }
+    sync(*c);
+  });
+}
+
+int fsi_set_tc_wait_limit(fsi_ctx* c, long long iters) {
+  return guard(c, [&] {
+    need_device(*c);
+    c->tc_first_wait = iters < 0 ? -1 : iters;
+  });
+}
+
+int fsi_set_stream(fsi_ctx* c, void* stream) {
+  return guard(c, [&] {
+    need_device(*c);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (s == c->stream) return;
+    sync(*c);   // nothing of the ctx is in flight on the old stream
+    c->stream = s;
+  });
+}
+
 int fsi_apply_operator(fsi_ctx* c, int level, const double* x, double* y) {
   return guard(c, [&] {
     need_device(*c);
@@ -1510,6 +1697,86 @@ int fsi_apply_vcycle(fsi_ctx* c, const double* b, double* z) {
     to_canonical(*c, L - 1, c->xk, z);
     sync(*c);
   });
+}
+
+// ---------------------------------------------------------------------------
+// nested iteration (full multigrid) for the steady problem
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_set_dirichlet(const int32_t* __restrict__ list, int64_t n, const double* __restrict__ val,
+                                double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[list[i]] = val[list[i]];
+}
+}  // namespace
+
+int fsi_fmg_newton(const fsi_problem_desc* desc, const fsi_solver_opts* opts, void* stream, double tol,
+                   int max_steps, double* y_out, fsi_fmg_stats* stats) {
+  if (!desc || !opts || !y_out || desc->levels < 1 || desc->levels > FSI_FMG_MAX_LEVELS || !(tol > 0.0) ||
+      max_steps < 1 || desc->transient != 0)
+    return FSI_E_INVALID;
+  fsi_fmg_stats st{};
+  st.levels = desc->levels;
+  fsi_ctx* prev = nullptr;
+  int rc = FSI_OK;
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  for (int l = 1; l <= desc->levels && rc == FSI_OK; ++l) {
+    fsi_problem_desc dl = *desc;
+    dl.levels = l;
+    fsi_ctx* c = nullptr;
+    rc = fsi_build_hierarchy(&dl, opts, stream, &c);
+    if (rc != FSI_OK) break;
+    rc = guard(c, [&] {
+      DevLevel& F = c->dl.back();
+      if (!prev) {
+        // boundary-condition lift: fsi_initial_state without noise
+        const int64_t N = c->hl.back().N;
+        std::vector<double> zero(N, 0.0), y(N);
+        const int r0 = fsi_initial_state(c, zero.data(), y.data());
+        if (r0 != FSI_OK) throw ApiError(r0, c->err);
+        const int r1 = fsi_set_state(c, y.data(), nullptr, nullptr, 0.0);
+        if (r1 != FSI_OK) throw ApiError(r1, c->err);
+      } else {
+        // the coarser solution injected (every unknown, boundary values
+        // included), then the Dirichlet data
+        launch_csr_spmv(F.Ni, F.S_ptr, F.S_col, F.S_val, prev->y, c->y, false, cs);
+        counted(*c);
+        if (F.n_dir > 0) {
+          k_set_dirichlet<<<(unsigned)((F.n_dir + 255) / 256), 256, 0, cs>>>(F.dir_list, F.n_dir, F.dir_val, c->y);
+          counted(*c);
+        }
+        sync(*c);
+      }
+    });
+    if (prev) {
+      fsi_destroy(prev);
+      prev = nullptr;
+    }
+    prev = c;
+    if (rc != FSI_OK) break;
+    const int li = l - 1;
+    for (int k = 0; k < max_steps; ++k) {
+      fsi_solve_stats s{};
+      double rel = 0.0;
+      rc = fsi_newton_step(c, nullptr, &rel, &s);
+      if (rc != FSI_OK) break;
+      st.newton_steps[li] += 1;
+      st.krylov_iters[li] += s.iters;
+      st.last_rel_step[li] = rel;
+      st.ms[li] += s.t_assemble_ms + s.t_factor_ms + s.t_solve_ms;
+      if (rel < tol) break;
+    }
+    if (rc == FSI_OK && !(st.last_rel_step[li] < tol)) rc = FSI_E_NOT_CONVERGED;
+  }
+  if (prev) {
+    const int rg = fsi_get_state(prev, y_out);
+    if (rc == FSI_OK) rc = rg;
+    if (rc != FSI_OK) std::fprintf(stderr, "fsi_fmg_newton: %s\n", prev->err.c_str());
+    fsi_destroy(prev);
+  }
+  st.status = rc;
+  if (stats) *stats = st;
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1550,8 +1817,14 @@ int fsi_coarse_solve_static(fsi_ctx* c, const double* b, double* x) {
     if (need > FSI_STATIC_PART_MAX)
       throw ApiError(FSI_E_INVALID, "fsi_coarse_solve_static: level-0 internal length " + std::to_string(n0) +
                                         " exceeds the static scratch limit of " + std::to_string(FSI_STATIC_COARSE_MAX));
+    if (!c->factored) throw ApiError(FSI_E_INVALID, "fsi_coarse_solve_static: fsi_factor_schwarz first");
+    // the array's address is per device: it must be the one the ctx (and its
+    // stream) lives on, which must also be the calling thread's current device
     int dev = 0;
     ck(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != c->device)
+      throw ApiError(FSI_E_INVALID, "fsi_coarse_solve_static: the current device (" + std::to_string(dev) +
+                                        ") is not the device the ctx was built on (" + std::to_string(c->device) + ")");
     double* part = static_part(dev);
     to_internal(*c, 0, b, C.b);
     launch_gemv(n0, c->c_inv, C.b, C.x, part, c->stream);

@@ -46,6 +46,10 @@ struct HostLevel {
   std::vector<double> P_val;
   std::vector<int32_t> R_ptr, R_col;   // Ni(l-1) rows
   std::vector<double> R_val;
+  // unmasked natural injection of whole states (Dirichlet values included),
+  // for nested iteration: Ni rows
+  std::vector<int32_t> S_ptr, S_col;
+  std::vector<double> S_val;
   // Schwarz blocks (levels >= 1)
   int n_patches = 0;
   std::vector<int32_t> p_n, p_nown;            // per patch sizes (padded) / owned rows
@@ -101,6 +105,8 @@ struct DevLevel {
   std::vector<int32_t> color_ptr;  // host copy
   int32_t *P_ptr = nullptr, *P_col = nullptr, *R_ptr = nullptr, *R_col = nullptr;
   double *P_val = nullptr, *R_val = nullptr;
+  int32_t *S_ptr = nullptr, *S_col = nullptr;   // unmasked state injection from level - 1
+  double* S_val = nullptr;
   // patches
   int n_patches = 0, max_n = 0, max_nown = 0;
   // launch parameters (0 = built-in choice; set by fsi_set_launch_params)
@@ -137,6 +143,7 @@ struct Ctx {
   int64_t launches = 0;
   int dim = 2, B = 4, nloc = 9, ndofe = 39;
   int sm_count = 0;
+  int device = -1;                       // CUDA device the ctx was built on
   // finest-level state and vectors (internal layout)
   double *y = nullptr, *res = nullptr;
   double *V = nullptr, *Z = nullptr;     // Krylov bases
@@ -185,6 +192,7 @@ struct Ctx {
   // the coarse factorisation runs on this higher-priority stream beside the
   // Schwarz factorisation (fork / join events on the ctx stream)
   int gj_panel = 0;   // preferred Gauss-Jordan panel width on the tensor cores (0, 16, 32)
+  long long tc_first_wait = -1;   // first tensor-core wait limit (< 0: the built-in limit)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool aux_failed = false;

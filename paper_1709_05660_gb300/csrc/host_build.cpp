@@ -252,11 +252,12 @@ void to_csr(int64_t nrows, std::vector<std::pair<int64_t, std::pair<int32_t, dou
 void build_transfers(const HostLevel& C, HostLevel& F) {
   const int dim = F.dim, B = F.B;
   std::vector<Trip> S = node_prolongation(C, F);
-  std::vector<std::pair<int64_t, std::pair<int32_t, double>>> pe, re;
+  std::vector<std::pair<int64_t, std::pair<int32_t, double>>> pe, re, se;
   for (const Trip& t : S) {
     for (int s = 0; s < B; ++s) {
       const int64_t fr = t.f * B + s, cc = t.c * B + s;
       if (!F.dir[fr] && !C.dir[cc]) pe.push_back({fr, {(int32_t)cc, t.w}});
+      se.push_back({fr, {(int32_t)cc, t.w}});   // unmasked: states (nested iteration)
     }
     // restriction: same component, same equation kind, no Dirichlet rows
     for (int sc = 0; sc < B; ++sc) {
@@ -280,16 +281,20 @@ void build_transfers(const HostLevel& C, HostLevel& F) {
     const int64_t ec = fi[0] / 2 + (int64_t)C.cells[0] * (fi[1] / 2 + (int64_t)C.cells[1] * (fi[2] / 2));
     const int64_t fb = (F.n_nodes + ef) * B, cb = (C.n_nodes + ec) * B;
     pe.push_back({fb, {(int32_t)cb, 1.0}});
+    se.push_back({fb, {(int32_t)cb, 1.0}});
     re.push_back({cb, {(int32_t)fb, 1.0}});
     for (int a = 0; a < dim; ++a) {
       const double sig = 0.5 * (double)(2 * (fi[a] % 2) - 1);
       pe.push_back({fb, {(int32_t)(cb + 1 + a), sig}});
+      se.push_back({fb, {(int32_t)(cb + 1 + a), sig}});
       re.push_back({cb + 1 + a, {(int32_t)fb, sig}});
       pe.push_back({fb + 1 + a, {(int32_t)(cb + 1 + a), 0.5}});
+      se.push_back({fb + 1 + a, {(int32_t)(cb + 1 + a), 0.5}});
       re.push_back({cb + 1 + a, {(int32_t)(fb + 1 + a), 0.5}});
     }
   }
   to_csr(F.Ni, pe, F.P_ptr, F.P_col, F.P_val);
+  to_csr(F.Ni, se, F.S_ptr, F.S_col, F.S_val);
   to_csr(C.Ni, re, F.R_ptr, F.R_col, F.R_val);
 }
 

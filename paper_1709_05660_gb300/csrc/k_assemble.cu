@@ -206,13 +206,31 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
       Fi[1][0] = -F[1][0] / J; Fi[1][1] = F[0][0] / J;
       Dual out[kNO];
       if (SOLID) {
-        // P = J sigma F^{-T} = -p J F^{-T} + mu_s J F   (sigma = -p I + 2 C1 B, C1 = mu_s / 2)
+        // P = J sigma F^{-T} = -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T}
+        // (sigma = -p I + 2 C1 B - 2 C2 B^{-1}, 2 C1 = mu_s - 2 C2; C2 = 0: Neo-Hookean)
         const Dual pJ = p * J;
-        const Dual muJ = J * pp.mu_s;
+        const Dual muJ = J * (pp.mu_s - 2.0 * pp.mr_c2);
+        Dual G[2][2];   // F^{-T} F^{-1} F^{-T}
+        if (pp.mr_c2 != 0.0) {
+          Dual Q[2][2];   // F^{-1} F^{-T}
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) Q[a][b] = Fi[a][0] * Fi[b][0] + Fi[a][1] * Fi[b][1];
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) G[c][k] = (Fi[0][c] * Q[0][k] + Fi[1][c] * Q[1][k]) * J * (2.0 * pp.mr_c2);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) G[c][k] = mk(0.0, 0.0);
+        }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
 #pragma unroll
-          for (int k = 0; k < 2; ++k) out[2 * c + k] = (muJ * F[c][k] - pJ * Fi[k][c]) * wq;
+          for (int k = 0; k < 2; ++k) out[2 * c + k] = (muJ * F[c][k] - pJ * Fi[k][c] - G[c][k]) * wq;
           out[4 + c] = TRANS ? ut[c] * J * (pp.rho_s * wq) : mk(0.0, 0.0);
           out[6 + c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
         }
@@ -652,12 +670,31 @@ k_flux_3d(const int32_t* __restrict__ elems, const double* __restrict__ y, const
 #pragma unroll
     for (int o = 0; o < k3NO; ++o) out[o] = mk(0.0, 0.0);
     if (SOLID) {
+      // P = -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T}, 2 C1 = mu_s - 2 C2
       const Dual pJ = p * J;
-      const Dual muJ = J * pp.mu_s;
+      const Dual muJ = J * (pp.mu_s - 2.0 * pp.mr_c2);
+      Dual G[3][3];
+      if (pp.mr_c2 != 0.0) {
+        Dual Q[3][3];   // F^{-1} F^{-T}
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) Q[a][b] = Fi[a][0] * Fi[b][0] + Fi[a][1] * Fi[b][1] + Fi[a][2] * Fi[b][2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            G[c][k] = (Fi[0][c] * Q[0][k] + Fi[1][c] * Q[1][k] + Fi[2][c] * Q[2][k]) * J * (2.0 * pp.mr_c2);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) G[c][k] = mk(0.0, 0.0);
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) out[3 * c + k] = (muJ * F[c][k] - pJ * Fi[k][c]) * wq;
+        for (int k = 0; k < 3; ++k) out[3 * c + k] = (muJ * F[c][k] - pJ * Fi[k][c] - G[c][k]) * wq;
         if (TRANS) out[9 + c] = ut[c] * J * (pp.rho_s * wq);
         out[12 + c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
       }

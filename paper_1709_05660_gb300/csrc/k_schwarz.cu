@@ -885,11 +885,11 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
         if (threadIdx.x == 0) {
           tc::fence_after_sync();
           if (t + 1 < ntiles) issue(t + 1);   // its accumulator was drained in iteration t - 1
-          if (!tc::mbar_wait(&mbar2[b], (bphase >> b) & 1u, 1LL << 22)) {
-            // one more bounded wait for tile t and for tile t + 1 before the
-            // tensor memory is released
-            tc::mbar_wait(&mbar2[b], (bphase >> b) & 1u, 1LL << 22);
-            if (t + 1 < ntiles) tc::mbar_wait(&mbar2[b ^ 1], (bphase >> (b ^ 1)) & 1u, 1LL << 22);
+          if (!tc::mbar_wait(&mbar2[b], (bphase >> b) & 1u, lv.first_wait)) {
+            // one more bounded wait (full limit) for tile t and for tile t + 1
+            // before the tensor memory is released
+            tc::mbar_wait(&mbar2[b], (bphase >> b) & 1u, kTcWaitIters);
+            if (t + 1 < ntiles) tc::mbar_wait(&mbar2[b ^ 1], (bphase >> (b ^ 1)) & 1u, kTcWaitIters);
             s_abort = 1;
           }
         }
@@ -932,6 +932,10 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
     }
     __syncthreads();
   }
+  // qinv starts at 0 so that it stays a valid column even if a singular
+  // block repeated a pivot row (ST_SINGULAR is reported; the values are void)
+  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[k] = 0;
+  __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
   __syncthreads();
   {
@@ -1126,6 +1130,7 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
     float* o = reinterpret_cast<float*>(invT);
     GjLevels lv{};
     lv.nlev = 1;
+    lv.first_wait = kTcWaitIters;
     lv.l[0] = GjLevel{p_n, p_nown, dense_off, own_off, own, inv_off, d, o, 0};
     if (launch_patch_gj_tc_levels(lv, np, max_n, status, st)) return;
     if (try_gj_f32<32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
@@ -1244,6 +1249,8 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
   if (a.kind == 1) {
     const int threads = a.vps * a.groups;
     const size_t smem = ((size_t)((max_n + 3) & ~3) + (size_t)a.groups * a.vps * VecT<T>::W) * sizeof(T);
+    if (smem > 48 * 1024)   // large blocks (e.g. 16 x 16 elements): opt in to more shared memory
+      cudaFuncSetAttribute(k_patch_apply_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_patch_apply_rows<T><<<(unsigned)((int64_t)np * a.slices), threads, smem, st>>>(
         p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x, T(omega), dr, dc, a.slices, a.vps, a.groups);
     return;
@@ -1254,6 +1261,8 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
   if (vstride > 128) vstride = 128;
   const int threads = vstride * CG;
   const size_t smem = ((size_t)((max_n + 3) & ~3) + (size_t)CG * vstride * VecT<T>::W) * sizeof(T);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_patch_apply_t<T, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_patch_apply_t<T, CG><<<np, threads, smem, st>>>(p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x,
                                                     T(omega), dr, dc, vstride);
 }

@@ -12,6 +12,7 @@ namespace fsi {
 struct PhysParams {
   double rho_f, mu_f, rho_s, mu_s;
   int ale_op;
+  double mr_c2;         // Mooney-Rivlin C2 (0: Neo-Hookean); 2 C1 = mu_s - 2 C2
   // transient (BDF) terms: q_t = (a0 q + yold) * idt with yold = a1 q_n + a2 q_{n-1}
   int transient;
   double a0, idt;
@@ -79,8 +80,12 @@ struct GjLevel {
 };
 struct GjLevels {
   int nlev;
+  // iteration limit of the first bounded wait of each block on its tensor-core
+  // work (the drain waits before tensor memory is released keep their full limit)
+  long long first_wait;
   GjLevel l[kGjMaxLevels];
 };
+constexpr long long kTcWaitIters = 1LL << 22;
 // false when the blocks do not fit the tensor-core kernel (the caller then
 // factors level by level)
 // panel: preferred panel width (16 or 32; 0 = 32 when the blocks fit, else 16)

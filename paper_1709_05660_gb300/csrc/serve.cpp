@@ -23,10 +23,10 @@ using Clock = std::chrono::steady_clock;
 
 struct Instance {
   fsi_ctx* ctx = nullptr;
-  cudaStream_t stream = nullptr;   // stream the ctx was built on
   int64_t bytes = 0;
   bool busy = false;
   int64_t n = 0;
+  int failed = 0;                  // error of an earlier step that freed the instance
 };
 
 struct Ticket {
@@ -70,7 +70,9 @@ struct fsi_server {
       for (auto jt = queue.begin(); jt != it; ++jt)
         if ((*jt)->req.instance == t->req.instance) { earlier_same = true; break; }
       if (earlier_same) continue;
-      if (f == inst.end() && budget > 0 && resident + t->planned > budget) continue;   // admission
+      if ((f == inst.end() || (!f->second.ctx && !f->second.failed)) && budget > 0 &&
+          resident + t->planned > budget)
+        continue;   // admission
       queue.erase(it);
       return t;
     }
@@ -88,7 +90,7 @@ struct fsi_server {
         if (!t) break;
         auto& in = inst[t->req.instance];
         in.busy = true;
-        if (!in.ctx) resident += t->planned;   // reserve before building
+        if (!in.ctx && !in.failed) resident += t->planned;   // reserve before building
         t->state = 1;
         t->t_start = Clock::now();
         ++running;
@@ -99,10 +101,13 @@ struct fsi_server {
         in = &inst[t->req.instance];
       }
       int rc = FSI_OK;
-      if (!in->ctx) {
+      if (in->failed) {
+        // an earlier step of this instance failed and freed it: complete the
+        // request at once with that step's error instead of rebuilding it
+        rc = in->failed;
+      } else if (!in->ctx) {
         rc = fsi_build_hierarchy(&t->req.desc, &t->req.opts, stream, &in->ctx);
         if (rc == FSI_OK) {
-          in->stream = stream;
           int64_t nl[16], hb = 0;
           fsi_get_sizes(in->ctx, nl, nullptr, &hb);
           in->n = nl[t->req.desc.levels - 1];
@@ -113,6 +118,7 @@ struct fsi_server {
         }
         std::lock_guard<std::mutex> lk(mu);
         resident += (rc == FSI_OK ? in->bytes : 0) - t->planned;
+        t->planned = 0;
         if (rc != FSI_OK && in->ctx) {
           fsi_destroy(in->ctx);
           in->ctx = nullptr;
@@ -121,9 +127,12 @@ struct fsi_server {
       fsi_solve_stats st{};
       double rel = 0.0;
       if (rc == FSI_OK) {
-        // a ctx stays bound to the stream it was built on
+        // the step runs on this worker's stream, whichever worker built the
+        // instance, so instances served by different workers overlap on the
+        // device (the ctx is idle here: its previous step has completed)
+        rc = fsi_set_stream(in->ctx, stream);
         dxbuf.assign(t->req.keep_dx ? in->n : 0, 0.0);
-        rc = fsi_newton_step(in->ctx, t->req.keep_dx ? dxbuf.data() : nullptr, &rel, &st);
+        if (rc == FSI_OK) rc = fsi_newton_step(in->ctx, t->req.keep_dx ? dxbuf.data() : nullptr, &rel, &st);
       }
       {
         std::lock_guard<std::mutex> lk(mu);
@@ -139,14 +148,21 @@ struct fsi_server {
         if (t->req.keep_dx) t->dx.swap(dxbuf);
         t->noise.clear();
         // a step that did not converge leaves the instance (and its state) in
-        // place; other failures and the last request free it
+        // place; other failures free it and are remembered, so the instance's
+        // queued requests complete with the same error; the last request
+        // forgets the instance
         if (t->req.last || (rc != FSI_OK && rc != FSI_E_NOT_CONVERGED)) {
           if (in->ctx) {
             fsi_destroy(in->ctx);
             in->ctx = nullptr;
             resident -= in->bytes;
           }
-          inst.erase(t->req.instance);
+          if (t->req.last) {
+            inst.erase(t->req.instance);
+          } else {
+            in->failed = rc;
+            in->busy = false;
+          }
         } else {
           in->busy = false;
         }

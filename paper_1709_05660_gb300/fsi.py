@@ -34,7 +34,8 @@ SYMBOLS = (
     "fsi_launch_count", "fsi_plan_hierarchy", "fsi_export_transfer", "fsi_set_profiling",
     "fsi_kernel_stats", "fsi_server_create", "fsi_serve_submit", "fsi_serve_poll", "fsi_serve_drain",
     "fsi_server_resident_bytes", "fsi_server_destroy", "fsi_coarse_solve_static", "fsi_set_launch_params",
-    "fsi_get_launch_params", "fsi_time_level_kernels",
+    "fsi_get_launch_params", "fsi_time_level_kernels", "fsi_set_stream", "fsi_import_csr",
+    "fsi_set_tc_wait_limit", "fsi_fmg_newton",
 )
 
 # kernel classes for fsi_kernel_stats
@@ -49,6 +50,7 @@ class ProblemDesc(ctypes.Structure):
         ("flap_hi", ctypes.c_double * 3), ("rho_f", ctypes.c_double), ("mu_f", ctypes.c_double),
         ("rho_s", ctypes.c_double), ("mu_s", ctypes.c_double), ("U", ctypes.c_double),
         ("transient", ctypes.c_int), ("dt", ctypes.c_double), ("ale_op", ctypes.c_int),
+        ("mr_c2", ctypes.c_double),
     ]
 
 
@@ -61,7 +63,8 @@ class SolverOptsC(ctypes.Structure):
     _fields_ = [
         ("tile", ctypes.c_int * 3), ("n_pre", ctypes.c_int), ("n_post", ctypes.c_int),
         ("omega", ctypes.c_double), ("restart", ctypes.c_int), ("rtol", ctypes.c_double),
-        ("max_iters", ctypes.c_int), ("precision", ctypes.c_int),
+        ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
+        ("gs_passes", ctypes.c_int),
     ]
 
 
@@ -69,11 +72,26 @@ class SolveStats(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_res", ctypes.c_double),
         ("rho", ctypes.c_double), ("t_assemble_ms", ctypes.c_double), ("t_factor_ms", ctypes.c_double),
-        ("t_solve_ms", ctypes.c_double),
+        ("t_solve_ms", ctypes.c_double), ("prec_rel_res", ctypes.c_double),
     ]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FMG_MAX_LEVELS = 16
+
+
+class FmgStats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("newton_steps", ctypes.c_int * FMG_MAX_LEVELS),
+                ("krylov_iters", ctypes.c_int * FMG_MAX_LEVELS),
+                ("last_rel_step", ctypes.c_double * FMG_MAX_LEVELS), ("ms", ctypes.c_double * FMG_MAX_LEVELS),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        L = self.levels
+        return {"levels": L, "newton_steps": list(self.newton_steps[:L]), "krylov_iters": list(self.krylov_iters[:L]),
+                "last_rel_step": list(self.last_rel_step[:L]), "ms": list(self.ms[:L]), "status": self.status}
 
 
 class Request(ctypes.Structure):
@@ -130,6 +148,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fsi_apply_operator.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.fsi_apply_vcycle.argtypes = [vp, vp, vp]
     lib.fsi_coarse_solve_static.argtypes = [vp, vp, vp]
+    lib.fsi_set_stream.argtypes = [vp, vp]
+    lib.fsi_fmg_newton.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOptsC), vp, ctypes.c_double,
+                                   ctypes.c_int, vp, ctypes.POINTER(FmgStats)]
+    lib.fsi_import_csr.argtypes = [vp, ctypes.c_int, vp]
+    lib.fsi_set_tc_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.fsi_apply_smoother.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.fsi_restrict.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.fsi_prolong.argtypes = [vp, ctypes.c_int, vp, vp]
@@ -168,6 +191,7 @@ def make_desc(p: Problem) -> ProblemDesc:
         d.flap_hi[a] = p.flap_hi[a]
     d.rho_f, d.mu_f, d.rho_s, d.mu_s, d.U = p.rho_f, p.mu_f, p.rho_s, p.mu_s, p.U
     d.transient, d.dt, d.ale_op = p.transient, p.dt, p.ale_op
+    d.mr_c2 = p.mr_c2
     return d
 
 
@@ -177,6 +201,7 @@ def make_opts(o: SolverOpts) -> SolverOptsC:
         c.tile[a] = t
     c.n_pre, c.n_post, c.omega = o.n_pre, o.n_post, o.omega
     c.restart, c.rtol, c.max_iters, c.precision = o.restart, o.rtol, o.max_iters, o.precision
+    c.krylov, c.gs_passes = o.krylov, o.gs_passes
     return c
 
 
@@ -266,8 +291,14 @@ class FSI:
         self._check(self.lib.fsi_factor_schwarz(self.h))
 
     def solve(self, b, x) -> SolveStats:
+        """FGMRES solve; on FSI_E_NOT_CONVERGED the raised FSIError carries
+        the filled statistics as ``.stats``."""
         st = SolveStats()
-        self._check(self.lib.fsi_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(st)))
+        rc = self.lib.fsi_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(st))
+        if rc != FSI_OK:
+            err = FSIError(rc, self.lib.fsi_last_error(self.h).decode())
+            err.stats = st
+            raise err
         return st
 
     def newton_update(self, dx) -> float:
@@ -331,6 +362,20 @@ class FSI:
     def apply_vcycle(self, b, z):
         self._check(self.lib.fsi_apply_vcycle(self.h, _ptr(b), _ptr(z)))
 
+    def import_csr(self, level: int, val):
+        """Replaces J_level's values (canonical CSR order of export_csr)."""
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        assert val.shape == (int(self.nnz[level]),)
+        self._check(self.lib.fsi_import_csr(self.h, level, _ptr(val)))
+
+    def set_tc_wait_limit(self, iters: int):
+        """First tensor-core wait limit of the Schwarz factorisation (< 0: built-in)."""
+        self._check(self.lib.fsi_set_tc_wait_limit(self.h, int(iters)))
+
+    def set_stream(self, stream: int):
+        """Rebinds the instance to another CUDA stream (raw cudaStream_t)."""
+        self._check(self.lib.fsi_set_stream(self.h, ctypes.c_void_p(stream)))
+
     def coarse_solve_static(self, b, x):
         """x = J_0^{-1} b with the coarse solve's scratch in a fixed
         file-scope device array (the call allocates nothing)."""
@@ -379,6 +424,22 @@ class FSI:
         a, b = ctypes.c_double(), ctypes.c_double()
         self._check(self.lib.fsi_time_level_kernels(self.h, level, reps, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+
+def fmg_newton(prob: Problem, opts: SolverOpts, y_out, stream: Optional[int] = None, tol: float = 1e-8,
+               max_steps: int = 20) -> dict:
+    """Nested-iteration (full multigrid) Newton for the steady problem
+    (fsi_fmg_newton); y_out receives the finest state.  Raises FSIError
+    (with .stats) on failure."""
+    lib = load_library()
+    d, o, st = make_desc(prob), make_opts(opts), FmgStats()
+    rc = lib.fsi_fmg_newton(ctypes.byref(d), ctypes.byref(o), ctypes.c_void_p(stream or 0), float(tol),
+                            int(max_steps), _ptr(y_out), ctypes.byref(st))
+    if rc != FSI_OK:
+        err = FSIError(rc, "fsi_fmg_newton failed (see stderr)")
+        err.stats = st.as_dict()
+        raise err
+    return st.as_dict()
 
 
 class Server:

@@ -103,3 +103,18 @@ def test_roofline_picks_the_largest_class_and_divides_by_its_peak(dominant):
     else:
         assert roof["bound"] == "alu"
     assert classes[dominant]["ms_per_step"] == pytest.approx(10.0)
+
+
+def test_cpu_baseline_leg_serial_and_all_cores():
+    """The cpu_baseline child process (one BLAS / OpenMP thread) times the
+    oracle sample serially and spread over one process per core, and reports
+    both with their core counts."""
+    b = _bench()
+    leg = b.CpuBaseline("channel2d_l3", 0.05, 1)
+    out, why = leg.result(timeout=600)
+    assert out is not None, why
+    assert out["kind"] == "oracle" and out["cores"] == 1 and out["value"] > 0 and out["sample"]
+    assert out["detail"]["frac"] == 0.05
+    if b._cores() > 1:
+        a = out["all_cores"]
+        assert a["cores"] == b._cores() and a["value"] > 0

@@ -104,3 +104,86 @@ def test_admission_by_device_bytes():
     with pytest.raises(fsi.FSIError):
         srv.submit(3, replace(p, levels=5), o, noise=noise(313860, 3))
     srv.close()
+
+
+def test_rebound_streams_overlap():
+    """Two instances built on the same stream and then rebound to two streams
+    (fsi_set_stream) overlap on the device when driven from two threads: the
+    sum of their device times (CUDA events on each stream) exceeds the wall
+    time, and the concurrent run is faster than running them one after the
+    other.  Results are bit-identical to the sequential run."""
+    import threading
+    import time
+    fsi = _fsi()
+    torch.cuda.set_device(0)
+    s0 = torch.cuda.Stream()
+    p, o = Problem(levels=3, mu_s=5e5, U=0.2), SolverOpts(tile=(2, 2), precision=1)
+    inst = [fsi.FSI(p, o, stream=s0.cuda_stream) for _ in range(2)]
+    n = int(inst[0].N[-1])
+    y0 = []
+    for k, s in enumerate(inst):
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        s.initial_state(torch.tensor(noise(n, 40 + k), dtype=torch.float64, device="cuda"), y)
+        y0.append(y)
+    steps = 6
+
+    def run(k, out, stream=None):
+        s = inst[k]
+        dx = torch.empty(n, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = stream or s0
+        e0.record(st)
+        for _ in range(steps):
+            s.set_state(y0[k])
+            s.newton_step(dx)
+        e1.record(st)
+        e1.synchronize()
+        out[k] = (dx.cpu().numpy(), e0.elapsed_time(e1))
+
+    seq = {}
+    for k in range(2):
+        run(k, seq)                    # warm-up (records the V-cycle graphs)
+    t0 = time.perf_counter()
+    for k in range(2):
+        run(k, seq)
+    t_seq = time.perf_counter() - t0
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for k in range(2):
+        inst[k].set_stream(streams[k].cuda_stream)
+    par = {}
+    th = [threading.Thread(target=run, args=(k, par, streams[k])) for k in range(2)]
+    t0 = time.perf_counter()
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    t_par = time.perf_counter() - t0
+    for k in range(2):
+        assert np.array_equal(par[k][0], seq[k][0])
+    dev_sum_ms = par[0][1] + par[1][1]
+    assert dev_sum_ms > 1.1 * t_par * 1e3, (dev_sum_ms, t_par)
+    assert t_par < 0.9 * t_seq, (t_par, t_seq)
+    for s in inst:
+        s.close()
+
+
+def test_failed_instance_completes_its_queued_requests():
+    """An instance whose first step fails (a non-finite state) is freed; its
+    queued follow-up requests complete at once with the same error instead of
+    rebuilding the hierarchy, and nothing stays resident."""
+    fsi = _fsi()
+    p, o = Problem(levels=3, mu_s=5e5, U=0.2), SolverOpts(tile=(2, 2), precision=1)
+    n = _n(p)
+    bad = np.full(n, np.nan)
+    srv = fsi.Server(hbm_budget_bytes=0, max_slots=2)
+    tickets = [srv.submit(7, p, o, noise=bad if k == 0 else None, last=(k == 3)) for k in range(4)]
+    good = srv.submit(8, p, o, noise=noise(n, 8), last=True)
+    srv.drain()
+    res = [srv.poll(t) for t in tickets]
+    assert res[0]["status"] in (-6, -7), res[0]
+    for r in res[1:]:
+        assert r["status"] == res[0]["status"]
+        assert r["run_ms"] < 50.0, r
+    assert srv.poll(good)["status"] == 0
+    assert srv.resident_bytes() == 0
+    srv.close()

@@ -121,3 +121,21 @@ def test_invalid_descriptors_rejected(lib):
         _plan(lib, prob, replace(opts, restart=0))
     with pytest.raises(lib.FSIError):
         _plan(lib, replace(prob, breaks=((0.0, 1.0, 0.5), prob.breaks[1])), opts)
+
+
+def test_initial_state_on_a_planned_ctx_is_bit_exact():
+    """fsi_initial_state is a host computation: a planned ctx (no GPU) gives
+    the oracle's benchmark state bit for bit, and with zero noise the
+    boundary-condition lift that starts a nonlinear solve."""
+    from oracle.mesh import build_level, initial_state
+    from paper_1709_05660_gb300 import fsi
+    from paper_1709_05660_gb300.workloads import CONFIGS, noise, problem_3d
+    for prob, opts in (CONFIGS["channel2d_l3"], (problem_3d(levels=1), CONFIGS["box3d_l3_bdf2"][1])):
+        p = fsi.FSI(prob, opts, plan_only=True)
+        N = int(p.N[-1])
+        lev = build_level(prob, prob.levels - 1)
+        for nz in (noise(N, 0), np.zeros(N)):
+            y = np.empty(N)
+            p.initial_state(nz, y)
+            assert np.array_equal(y, initial_state(prob, lev, nz))
+        p.close()

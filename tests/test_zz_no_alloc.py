@@ -98,3 +98,21 @@ def test_static_coarse_solve_size_limit():
         s.initial_state(_dev(noise(n, 0)), y)
     finally:
         s.close()
+
+
+def test_static_coarse_solve_needs_factors():
+    """Before the first fsi_factor_schwarz the dense coarse inverse does not
+    exist yet: the call is rejected (FSI_E_INVALID) instead of applying an
+    uninitialised inverse."""
+    from paper_1709_05660_gb300 import fsi
+    prob, opts = CONFIGS["channel2d_l3"]
+    s = fsi.FSI(replace(prob, levels=1), opts, stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        n = int(s.N[0])
+        b = torch.ones(n, dtype=torch.float64, device="cuda")
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        with pytest.raises(fsi.FSIError) as ei:
+            s.coarse_solve_static(b, x)
+        assert ei.value.code == -1 and "factor" in str(ei.value)
+    finally:
+        s.close()
