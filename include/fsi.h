@@ -74,7 +74,8 @@ typedef struct {
   double flap_lo[3], flap_hi[3];        /* solid box */
   double rho_f, mu_f, rho_s, mu_s;      /* densities, viscosity, shear modulus (C1 = mu_s/2) */
   double U;                             /* mean inflow velocity */
-  int transient;                        /* 0: steady; 1: time step of the BDF form (Sec. 2) */
+  int transient;                        /* 0: steady; 1: time step of the BDF form; 2: time step of the
+                                           paper's Crank-Nicolson form (Sec. 2.5) */
   double dt;                            /* time step (transient only, > 0) */
   int ale_op;                           /* 0: k(grad d + grad d^T), k = 1/V_el; 1: k grad d */
   double mr_c2;                         /* Mooney-Rivlin C2 (Sec. 2.2): sigma = -p I + 2 C1 B - 2 C2 B^{-1}
@@ -155,12 +156,18 @@ int fsi_get_sizes(const fsi_ctx* ctx, int64_t* n_per_level, int64_t* nnz_per_lev
 int fsi_initial_state(fsi_ctx* ctx, const double* noise, double* y_out);
 
 /* Sets the Newton state y (N doubles).  Steady problems ignore y_prev,
- * y_prev2 and t.  Transient problems (desc.transient = 1) need the state of
- * the previous time step y_prev; with y_prev2 (the one before) the time
- * derivative is BDF2, q_t = (1.5 q - 2 q_n + 0.5 q_{n-1}) / dt, without it
- * BDF1, q_t = (q - q_n) / dt (start-up step).  t is the new time level: the
- * inflow data are scaled by alpha(t) = (1 + sin 2 pi t) / 2, so Dirichlet
- * residual rows read r_i = y_i - alpha(t) g_i.  Host or device buffers. */
+ * y_prev2 and t.  Transient problems need the state of the previous time
+ * step y_prev.  BDF form (desc.transient = 1): with y_prev2 (the one before)
+ * the time derivative is BDF2, q_t = (1.5 q - 2 q_n + 0.5 q_{n-1}) / dt,
+ * without it BDF1, q_t = (q - q_n) / dt (start-up step).  Crank-Nicolson form
+ * (desc.transient = 2, Sec. 2.5): y_prev is the state of t_n, y_prev2 is
+ * ignored; the fluid momentum uses the conservative ALE identity of Sec. 2.3
+ * ((rho J u)_{n+1} - (rho J u)_n over dt with the -(div w) u terms), the
+ * stresses, the convection and the solid kinematic velocity are averaged
+ * over t_{n+1} and t_n, with the mesh velocity w = (d - d_n) / dt.  t is the
+ * new time level: the inflow data are scaled by alpha(t) = (1 + sin 2 pi t)
+ * / 2, so Dirichlet residual rows read r_i = y_i - alpha(t) g_i.  Host or
+ * device buffers. */
 int fsi_set_state(fsi_ctx* ctx, const double* y, const double* y_prev,
                   const double* y_prev2, double t);
 int fsi_get_state(fsi_ctx* ctx, double* y_out);

@@ -379,7 +379,7 @@ void assemble(Ctx& c, bool want_res) {
   const bool transient = c.desc.transient != 0;
   if (transient) {
     if (!c.have_history) throw ApiError(FSI_E_INVALID, "transient problem: fsi_set_state needs y_prev first");
-    pp.transient = 1;
+    pp.transient = c.desc.transient == 2 ? 2 : 1;
     pp.a0 = c.bdf_a0;
     pp.idt = 1.0 / c.desc.dt;
     pp.yold = c.yold;
@@ -1219,6 +1219,7 @@ static int64_t estimate_device_bytes(const Ctx& c) {
 
 static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts* opts) {
   if (desc->transient != 0 && !(desc->dt > 0.0)) throw ApiError(FSI_E_INVALID, "transient problem needs dt > 0");
+  if (desc->transient < 0 || desc->transient > 2) throw ApiError(FSI_E_INVALID, "transient must be 0, 1 or 2");
   if (opts->precision != FSI_FP64 && opts->precision != FSI_MIXED) throw ApiError(FSI_E_INVALID, "bad precision");
   if (opts->restart < 1 || opts->restart > 64) throw ApiError(FSI_E_INVALID, "restart must be in [1, 64]");
   if (opts->n_pre < 0 || opts->n_post < 0 || opts->max_iters < 1 || !(opts->rtol > 0.0))
@@ -1379,7 +1380,13 @@ int fsi_set_state(fsi_ctx* c, const double* y, const double* y_prev, const doubl
     if (!y) throw ApiError(FSI_E_INVALID, "null state");
     const int L = (int)c->dl.size();
     to_internal(*c, L - 1, y, c->y);
-    if (c->desc.transient != 0) {
+    if (c->desc.transient == 2) {
+      // Crank-Nicolson: the state of t_n itself
+      if (!y_prev) throw ApiError(FSI_E_INVALID, "transient problem: y_prev is required");
+      to_internal(*c, L - 1, y_prev, c->yold);
+      c->inflow_alpha = 0.5 * (1.0 + std::sin(2.0 * M_PI * t));
+      c->have_history = true;
+    } else if (c->desc.transient != 0) {
       if (!y_prev) throw ApiError(FSI_E_INVALID, "transient problem: y_prev is required");
       // BDF2 with two history states, BDF1 (start-up step) with one
       const double a0 = y_prev2 ? 1.5 : 1.0, a1 = y_prev2 ? -2.0 : -1.0, a2 = 0.5;

@@ -74,6 +74,7 @@ namespace {
 constexpr int kQ = 9;            // Gauss points (3 x 3)
 constexpr int kNF = 13;          // differentiated fields
 constexpr int kNFV = 17;         // + BDF history values (u_old, d_old)
+constexpr int kNFVcn = 26;       // Crank-Nicolson: + the t_n fields (u_n, d_n, grad d_n, grad u_n, p_n)
 constexpr int kNO = 11;          // flux outputs per point
 // fields: 0,1 d_i | 2..5 dd_i/dx_k (2 + 2 i + k) | 6,7 u_i | 8..11 du_i/dx_k (8 + 2 i + k) | 12 p
 //         13,14 u-history | 15,16 d-history
@@ -81,17 +82,46 @@ constexpr int kNO = 11;          // flux outputs per point
 //          solid: 0..3 T_ck | 4,5 inertia_c | 6,7 kinematic_c | 10 mass
 // (every output carries its quadrature weight; T and A multiply a test gradient
 // in reference coordinates scaled by 2 / h, the others a test value)
-constexpr size_t kAsmElemDoubles = (size_t)kQ * kNFV + (size_t)kQ * kNF * kNO + (size_t)kQ * kNO;
+//         CN: 13,14 u_n | 15,16 d_n | 17..20 d d_n,i/dx_k (17 + 2 i + k) | 21..24 d u_n,i/dx_k | 25 p_n
+constexpr size_t asm_elem_doubles(int nfv) { return (size_t)kQ * nfv + (size_t)kQ * kNF * kNO + (size_t)kQ * kNO; }
+constexpr size_t kAsmElemDoubles = asm_elem_doubles(kNFV);
+
+// First Piola stress of the incompressible solid (Sec. 2.2):
+// P = -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T}, 2 C1 = mu_s - 2 C2
+__device__ __forceinline__ void piola_2d(const Dual (&F)[2][2], const Dual (&Fi)[2][2], Dual J, Dual p,
+                                         const PhysParams& pp, Dual (&P)[2][2]) {
+  const Dual pJ = p * J;
+  const Dual muJ = J * (pp.mu_s - 2.0 * pp.mr_c2);
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) P[c][k] = muJ * F[c][k] - pJ * Fi[k][c];
+  if (pp.mr_c2 != 0.0) {
+    Dual Q[2][2];   // F^{-1} F^{-T}
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) Q[a][b] = Fi[a][0] * Fi[b][0] + Fi[a][1] * Fi[b][1];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) P[c][k] = P[c][k] - (Fi[0][c] * Q[0][k] + Fi[1][c] * Q[1][k]) * J * (2.0 * pp.mr_c2);
+  }
+}
 }  // namespace
 
-template <bool SOLID, bool TRANS>
+// MODE: 0 steady, 1 BDF (yold = a1 y_n + a2 y_{n-1}), 2 Crank-Nicolson (yold = y_n)
+template <bool SOLID, int MODE>
 __global__ void __launch_bounds__(kEPB * kNdofe, 2)
 k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ y,
               const int32_t* __restrict__ elem_nodes, const uint8_t* __restrict__ node_class,
               const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp,
               double* __restrict__ Ke, double* __restrict__ Re, int32_t* __restrict__ status) {
+  constexpr bool TRANS = MODE != 0;
+  constexpr bool CN = MODE == 2;
+  constexpr int NFV = CN ? kNFVcn : kNFV;
   __shared__ double s_y[kEPB][kNdofe];
-  __shared__ double s_yo[kEPB][kNN];
+  __shared__ double s_yo[kEPB][kNdofe];
   __shared__ double s_geo[kEPB][2 * kDim];
   __shared__ unsigned s_iface[kEPB];
   __shared__ double s_N[kQ][kNloc], s_Dx[kQ][kNloc], s_Dy[kQ][kNloc];   // reference basis at the points
@@ -117,6 +147,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
       if (TRANS) s_yo[le][j] = pp.yold[gi];
     } else {
       s_y[le][j] = y[(n_nodes + e) * kB + (j - kNN)];
+      if (CN) s_yo[le][j] = pp.yold[(n_nodes + e) * kB + (j - kNN)];
     }
     if (j < 2 * kDim) s_geo[le][j] = elem_geo[(int64_t)e * 2 * kDim + j];
     if (j == 0) {
@@ -128,8 +159,8 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   }
   __syncthreads();
   const int le_c = le < kEPB ? le : 0;
-  double* Fv = reinterpret_cast<double*>(smem_raw) + (size_t)le_c * kAsmElemDoubles;   // [kQ][kNFV]
-  double* Dd = Fv + kQ * kNFV;                                                          // [kQ][kNF][kNO]
+  double* Fv = reinterpret_cast<double*>(smem_raw) + (size_t)le_c * asm_elem_doubles(NFV);   // [kQ][NFV]
+  double* Dd = Fv + kQ * NFV;                                                               // [kQ][kNF][kNO]
   double* Vo = Dd + kQ * kNF * kNO;                                                     // [kQ][kNO]
   const double* ye = s_y[le_c];
   const double* yo = s_yo[le_c];
@@ -140,11 +171,13 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
 
   // 1. field values at the points
   if (active) {
-    for (int it = j; it < kQ * kNFV; it += kNdofe) {
-      const int q = it / kNFV, f = it % kNFV;
+    for (int it = j; it < kQ * NFV; it += kNdofe) {
+      const int q = it / NFV, f = it % NFV;
       double v = 0.0;
       if (f == 12) {
         v = ye[kNN] + ye[kNN + 1] * gp(q % 3) + ye[kNN + 2] * gp(q / 3);
+      } else if (CN && f == 25) {
+        v = yo[kNN] + yo[kNN + 1] * gp(q % 3) + yo[kNN + 2] * gp(q / 3);
       } else if (f < 13 || TRANS) {
         // source component, basis kind (0 value, 1 d/dx, 2 d/dy), history flag
         int comp, kind;
@@ -154,7 +187,9 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         else if (f < 8) { comp = 2 + (f - 6); kind = 0; }
         else if (f < 12) { comp = 2 + (f - 8) / 2; kind = 1 + (f - 8) % 2; }
         else if (f < 15) { comp = 2 + (f - 13); kind = 0; src = yo; }
-        else { comp = f - 15; kind = 0; src = yo; }
+        else if (f < 17) { comp = f - 15; kind = 0; src = yo; }
+        else if (f < 21) { comp = (f - 17) / 2; kind = 1 + (f - 17) % 2; src = yo; }
+        else { comp = 2 + (f - 21) / 2; kind = 1 + (f - 21) % 2; src = yo; }
         const double* tb = kind == 0 ? s_N[q] : (kind == 1 ? s_Dx[q] : s_Dy[q]);
 #pragma unroll
         for (int a = 0; a < kNloc; ++a) v += src[a * kB + comp] * tb[a];
@@ -205,32 +240,91 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
       Fi[0][0] = F[1][1] / J; Fi[0][1] = -F[0][1] / J;
       Fi[1][0] = -F[1][0] / J; Fi[1][1] = F[0][0] / J;
       Dual out[kNO];
-      if (SOLID) {
+      if (CN) {
+        // Crank-Nicolson (Sec. 2.5): stresses and convection averaged over
+        // t_{n+1} and t_n, the conservative ALE inertia (rho J u)_{n+1} -
+        // (rho J u)_n over dt with -(div w) u averaged, w = (d - d_n) / dt;
+        // the t_n state enters as constants (zero derivative)
+        const double un[2] = {fv[13], fv[14]};
+        Dual Fn[2][2], Fin[2][2], gw[2][2], w[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          w[i] = (mk(fv[i], f == i ? 1.0 : 0.0) + (-fv[15 + i])) * pp.idt;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            Fn[i][k] = mk(fv[17 + 2 * i + k] + (i == k ? 1.0 : 0.0), 0.0);
+            gw[i][k] = (gd[i][k] + (-fv[17 + 2 * i + k])) * pp.idt;
+          }
+        }
+        const Dual Jn = Fn[0][0] * Fn[1][1] - Fn[0][1] * Fn[1][0];
+        if (!(Jn.v > 0.0)) tangled = true;
+        Fin[0][0] = Fn[1][1] / Jn; Fin[0][1] = -Fn[0][1] / Jn;
+        Fin[1][0] = -Fn[1][0] / Jn; Fin[1][1] = Fn[0][0] / Jn;
+        const Dual pn = mk(fv[25], 0.0);
+        if (SOLID) {
+          Dual P1[2][2], Pn[2][2];
+          piola_2d(F, Fi, J, p, pp, P1);
+          piola_2d(Fn, Fin, Jn, pn, pp, Pn);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) out[2 * c + k] = (P1[c][k] + Pn[c][k]) * (0.5 * wq);
+            out[4 + c] = (u[c] * J - Jn * un[c]) * (pp.rho_s * pp.idt * wq);
+            out[6 + c] = ((u[c] + un[c]) * 0.5 - w[c]) * wq;
+          }
+          out[8] = mk(0.0, 0.0);
+          out[9] = mk(0.0, 0.0);
+          out[10] = (J + (-1.0)) * wq;
+        } else {
+          Dual gx[2][2], gxn[2][2];
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              gx[i][k] = gu[i][0] * Fi[0][k] + gu[i][1] * Fi[1][k];
+              gxn[i][k] = Fin[0][k] * fv[21 + 2 * i] + Fin[1][k] * fv[21 + 2 * i + 1];
+            }
+          Dual sig[2][2], sgn[2][2];
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              sig[i][k] = (gx[i][k] + gx[k][i]) * pp.mu_f;
+              sgn[i][k] = (gxn[i][k] + gxn[k][i]) * pp.mu_f;
+            }
+          sig[0][0] = sig[0][0] - p;
+          sig[1][1] = sig[1][1] - p;
+          sgn[0][0] = sgn[0][0] - pn;
+          sgn[1][1] = sgn[1][1] - pn;
+          const Dual divw1 = gw[0][0] * Fi[0][0] + gw[0][1] * Fi[1][0] + gw[1][0] * Fi[0][1] + gw[1][1] * Fi[1][1];
+          const Dual divwn =
+              gw[0][0] * Fin[0][0] + gw[0][1] * Fin[1][0] + gw[1][0] * Fin[0][1] + gw[1][1] * Fin[1][1];
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+              out[2 * c + k] = ((sig[c][0] * Fi[k][0] + sig[c][1] * Fi[k][1]) * J +
+                                (sgn[c][0] * Fin[k][0] + sgn[c][1] * Fin[k][1]) * Jn) * (0.5 * wq);
+            const Dual conv1 = gx[c][0] * (u[0] - w[0]) + gx[c][1] * (u[1] - w[1]);
+            const Dual convn = gxn[c][0] * (-w[0] + un[0]) + gxn[c][1] * (-w[1] + un[1]);
+            const Dual val = (u[c] * J - Jn * un[c]) * pp.idt - divw1 * J * u[c] * 0.5 - divwn * Jn * (0.5 * un[c]) +
+                             conv1 * J * 0.5 + convn * Jn * 0.5;
+            out[4 + c] = val * (pp.rho_f * wq);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+              out[6 + 2 * c + k] = (pp.ale_op == 0 ? gd[c][k] + gd[k][c] : gd[c][k]) * (kale * wq);
+          }
+          out[10] = J * (gx[0][0] + gx[1][1]) * wq;
+        }
+      } else if (SOLID) {
         // P = J sigma F^{-T} = -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T}
         // (sigma = -p I + 2 C1 B - 2 C2 B^{-1}, 2 C1 = mu_s - 2 C2; C2 = 0: Neo-Hookean)
-        const Dual pJ = p * J;
-        const Dual muJ = J * (pp.mu_s - 2.0 * pp.mr_c2);
-        Dual G[2][2];   // F^{-T} F^{-1} F^{-T}
-        if (pp.mr_c2 != 0.0) {
-          Dual Q[2][2];   // F^{-1} F^{-T}
-#pragma unroll
-          for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) Q[a][b] = Fi[a][0] * Fi[b][0] + Fi[a][1] * Fi[b][1];
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int k = 0; k < 2; ++k) G[c][k] = (Fi[0][c] * Q[0][k] + Fi[1][c] * Q[1][k]) * J * (2.0 * pp.mr_c2);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int k = 0; k < 2; ++k) G[c][k] = mk(0.0, 0.0);
-        }
+        Dual P[2][2];
+        piola_2d(F, Fi, J, p, pp, P);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
 #pragma unroll
-          for (int k = 0; k < 2; ++k) out[2 * c + k] = (muJ * F[c][k] - pJ * Fi[k][c] - G[c][k]) * wq;
+          for (int k = 0; k < 2; ++k) out[2 * c + k] = P[c][k] * wq;
           out[4 + c] = TRANS ? ut[c] * J * (pp.rho_s * wq) : mk(0.0, 0.0);
           out[6 + c] = (TRANS ? u[c] - dt_[c] : u[c]) * wq;
         }
@@ -533,6 +627,7 @@ constexpr int k3Nloc = 27;
 constexpr int k3NN = k3B * k3Nloc;        // 162
 constexpr int k3Ndofe = k3NN + k3Dim + 1; // 166
 constexpr int k3Fields = 31;              // gd 9, gu 9, u 3, d 3, p 1, u_old 3, d_old 3
+constexpr int k3FieldsCN = 50;            // + (Crank-Nicolson) gd_n 31..39, gu_n 40..48, p_n 49
 __device__ __forceinline__ int row_kind3(int cls, int slot) {
   if (cls == kFluid) return slot < k3Dim ? 2 : 0;
   return slot < k3Dim ? 0 : 1;
@@ -564,15 +659,63 @@ size_t assemble_3d_scratch_doubles(int max_ne) {
   return (size_t)std::min(max_ne, k3Chunk) * k3FluxDoubles;
 }
 
+// First Piola stress of the incompressible solid (Sec. 2.2), 3D:
+// P = -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T}, 2 C1 = mu_s - 2 C2
+__device__ __forceinline__ void piola_3d(const Dual (&F)[3][3], const Dual (&Fi)[3][3], Dual J, Dual p,
+                                         const PhysParams& pp, Dual (&P)[3][3]) {
+  const Dual pJ = p * J;
+  const Dual muJ = J * (pp.mu_s - 2.0 * pp.mr_c2);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) P[c][k] = muJ * F[c][k] - pJ * Fi[k][c];
+  if (pp.mr_c2 != 0.0) {
+    Dual Q[3][3];   // F^{-1} F^{-T}
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Q[a][b] = Fi[a][0] * Fi[b][0] + Fi[a][1] * Fi[b][1] + Fi[a][2] * Fi[b][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        P[c][k] = P[c][k] - (Fi[0][c] * Q[0][k] + Fi[1][c] * Q[1][k] + Fi[2][c] * Q[2][k]) * J * (2.0 * pp.mr_c2);
+  }
+}
+
+// F^{-1} and det F of a 3 x 3 Dual matrix (cofactors)
+__device__ __forceinline__ Dual inv3(const Dual (&F)[3][3], Dual (&Fi)[3][3]) {
+  Dual C[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+      C[i][k] = F[i1][k1] * F[i2][k2] - F[i1][k2] * F[i2][k1];
+    }
+  const Dual J = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
+  const double iJ = 1.0 / J.v;
+  const Dual rJ = mk(iJ, -J.d * iJ * iJ);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fi[i][k] = C[k][i] * rJ;
+  return J;
+}
+
 // fields at the 27 points, then flux values and derivatives along each field
-template <bool SOLID, bool TRANS>
+// MODE: 0 steady, 1 BDF (yold = a1 y_n + a2 y_{n-1}), 2 Crank-Nicolson (yold = y_n)
+template <bool SOLID, int MODE>
 __global__ void __launch_bounds__(256)
 k_flux_3d(const int32_t* __restrict__ elems, const double* __restrict__ y, const int32_t* __restrict__ elem_nodes,
           const double* __restrict__ elem_geo, int64_t n_nodes, PhysParams pp, double* __restrict__ Dg,
           int32_t* __restrict__ status) {
-  __shared__ double ye[k3Ndofe], yo[k3NN];
+  constexpr bool TRANS = MODE != 0;
+  constexpr bool CN = MODE == 2;
+  constexpr int NFLD = CN ? k3FieldsCN : k3Fields;
+  __shared__ double ye[k3Ndofe], yo[k3Ndofe];
   __shared__ double bt[k3Q][k3Nloc][4];   // physical basis: N, d/dx, d/dy, d/dz
-  __shared__ double fvs[k3Q][k3Fields];
+  __shared__ double fvs[k3Q][NFLD];
   __shared__ double geo[2 * k3Dim];
   const int e = elems[blockIdx.x];
   for (int t = threadIdx.x; t < k3Ndofe; t += blockDim.x) {
@@ -582,6 +725,7 @@ k_flux_3d(const int32_t* __restrict__ elems, const double* __restrict__ y, const
       yo[t] = TRANS ? pp.yold[gi] : 0.0;
     } else {
       ye[t] = y[(n_nodes + e) * k3B + (t - k3NN)];
+      yo[t] = CN ? pp.yold[(n_nodes + e) * k3B + (t - k3NN)] : 0.0;
     }
   }
   if (threadIdx.x < 2 * k3Dim) geo[threadIdx.x] = elem_geo[(int64_t)e * 2 * k3Dim + threadIdx.x];
@@ -600,8 +744,8 @@ k_flux_3d(const int32_t* __restrict__ elems, const double* __restrict__ y, const
     bt[q][a][3] = lx * ly * dL1(ka, zeta) * (2.0 / hz);
   }
   __syncthreads();
-  for (int it = threadIdx.x; it < k3Q * k3Fields; it += blockDim.x) {
-    const int q = it / k3Fields, t = it % k3Fields;
+  for (int it = threadIdx.x; it < k3Q * NFLD; it += blockDim.x) {
+    const int q = it / NFLD, t = it % NFLD;
     double acc = 0.0;
     if (t < 18) {           // gd (t < 9) and gu: d_i / dx_k of d or u
       const int i = (t % 9) / 3, k = t % 3, off = t < 9 ? 0 : 3;
@@ -611,9 +755,14 @@ k_flux_3d(const int32_t* __restrict__ elems, const double* __restrict__ y, const
       for (int a = 0; a < k3Nloc; ++a) acc += ye[a * k3B + off + i] * bt[q][a][0];
     } else if (t == 24) {   // pressure
       acc = ye[k3NN] + ye[k3NN + 1] * gp(q % 3) + ye[k3NN + 2] * gp((q / 3) % 3) + ye[k3NN + 3] * gp(q / 9);
-    } else if (TRANS) {     // u_old (25..27), d_old (28..30)
+    } else if (TRANS && t < 31) {     // u_old (25..27), d_old (28..30)
       const int i = (t - 25) % 3, off = t < 28 ? 3 : 0;
       for (int a = 0; a < k3Nloc; ++a) acc += yo[a * k3B + off + i] * bt[q][a][0];
+    } else if (CN && t < 49) {        // t_n gradients: d (31..39), u (40..48)
+      const int tt = t - 31, i = (tt % 9) / 3, k = tt % 3, off = tt < 9 ? 0 : 3;
+      for (int a = 0; a < k3Nloc; ++a) acc += yo[a * k3B + off + i] * bt[q][a][1 + k];
+    } else if (CN) {                  // p_n
+      acc = yo[k3NN] + yo[k3NN + 1] * gp(q % 3) + yo[k3NN + 2] * gp((q / 3) % 3) + yo[k3NN + 3] * gp(q / 9);
     }
     fvs[q][t] = acc;
   }
@@ -669,7 +818,84 @@ k_flux_3d(const int32_t* __restrict__ elems, const double* __restrict__ y, const
     Dual out[k3NO];
 #pragma unroll
     for (int o = 0; o < k3NO; ++o) out[o] = mk(0.0, 0.0);
-    if (SOLID) {
+    if (CN) {
+      // Crank-Nicolson (Sec. 2.5), as in the 2D kernel: stresses and convection
+      // averaged over t_{n+1} and t_n, conservative ALE inertia, w = (d - d_n) / dt
+      Dual Fn[3][3], Fin[3][3], gw[3][3], w[3];
+      double un[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        un[i] = fv[25 + i];
+        w[i] = (mk(fv[21 + i], f == 21 + i ? 1.0 : 0.0) + (-fv[28 + i])) * pp.idt;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          Fn[i][k] = mk(fv[31 + 3 * i + k] + (i == k ? 1.0 : 0.0), 0.0);
+          gw[i][k] = (gd[i][k] + (-fv[31 + 3 * i + k])) * pp.idt;
+        }
+      }
+      const Dual Jn = inv3(Fn, Fin);
+      if (!(Jn.v > 0.0)) tangled = true;
+      const Dual pn = mk(fv[49], 0.0);
+      if (SOLID) {
+        Dual P1[3][3], Pn[3][3];
+        piola_3d(F, Fi, J, p, pp, P1);
+        piola_3d(Fn, Fin, Jn, pn, pp, Pn);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) out[3 * c + k] = (P1[c][k] + Pn[c][k]) * (0.5 * wq);
+          out[9 + c] = (u[c] * J - Jn * un[c]) * (pp.rho_s * pp.idt * wq);
+          out[12 + c] = ((u[c] + un[c]) * 0.5 - w[c]) * wq;
+        }
+        out[21] = (J + (-1.0)) * wq;
+      } else {
+        Dual gx[3][3], gxn[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const Dual gu0 = mk(fv[9 + i * 3 + 0], f == 9 + i * 3 + 0 ? 1.0 : 0.0);
+            const Dual gu1 = mk(fv[9 + i * 3 + 1], f == 9 + i * 3 + 1 ? 1.0 : 0.0);
+            const Dual gu2 = mk(fv[9 + i * 3 + 2], f == 9 + i * 3 + 2 ? 1.0 : 0.0);
+            gx[i][k] = gu0 * Fi[0][k] + gu1 * Fi[1][k] + gu2 * Fi[2][k];
+            gxn[i][k] = Fin[0][k] * fv[40 + 3 * i] + Fin[1][k] * fv[40 + 3 * i + 1] + Fin[2][k] * fv[40 + 3 * i + 2];
+          }
+        Dual divw1 = mk(0.0, 0.0), divwn = mk(0.0, 0.0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            divw1 = divw1 + gw[i][k] * Fi[k][i];
+            divwn = divwn + gw[i][k] * Fin[k][i];
+          }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Dual sig[3], sgn[3];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            sig[m] = (gx[c][m] + gx[m][c]) * pp.mu_f;
+            sgn[m] = (gxn[c][m] + gxn[m][c]) * pp.mu_f;
+            if (m == c) {
+              sig[m] = sig[m] - p;
+              sgn[m] = sgn[m] - pn;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            out[3 * c + k] = ((sig[0] * Fi[k][0] + sig[1] * Fi[k][1] + sig[2] * Fi[k][2]) * J +
+                              (sgn[0] * Fin[k][0] + sgn[1] * Fin[k][1] + sgn[2] * Fin[k][2]) * Jn) * (0.5 * wq);
+          const Dual conv1 = gx[c][0] * (u[0] - w[0]) + gx[c][1] * (u[1] - w[1]) + gx[c][2] * (u[2] - w[2]);
+          const Dual convn = gxn[c][0] * (-w[0] + un[0]) + gxn[c][1] * (-w[1] + un[1]) + gxn[c][2] * (-w[2] + un[2]);
+          const Dual val = (u[c] * J - Jn * un[c]) * pp.idt - divw1 * J * u[c] * 0.5 - divwn * Jn * (0.5 * un[c]) +
+                           conv1 * J * 0.5 + convn * Jn * 0.5;
+          out[9 + c] = val * (pp.rho_f * wq);
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            out[12 + 3 * c + k] = (pp.ale_op == 0 ? gd[c][k] + gd[k][c] : gd[c][k]) * (kale * wq);
+        }
+        out[21] = J * (gx[0][0] + gx[1][1] + gx[2][2]) * wq;
+      }
+    } else if (SOLID) {
       // P = -p J F^{-T} + 2 C1 J F - 2 C2 J F^{-T} F^{-1} F^{-T}, 2 C1 = mu_s - 2 C2
       const Dual pJ = p * J;
       const Dual muJ = J * (pp.mu_s - 2.0 * pp.mr_c2);
@@ -1030,16 +1256,21 @@ void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* 
   (void)scratch;
   if (ne <= 0) return;
   const int grid = (ne + kEPB - 1) / kEPB;
-  const size_t smem = (size_t)kEPB * kAsmElemDoubles * sizeof(double);
+  const size_t smem = (size_t)kEPB * asm_elem_doubles(pp.transient == 2 ? kNFVcn : kNFV) * sizeof(double);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, kEPB * kNdofe, smem, st>>>(elems, ne, y, elem_nodes, node_class, elem_geo, n_nodes, pp, Ke, Re,
                                            status);
   };
-  if (solid)
-    pp.transient ? go(k_assemble_2d<true, true>) : go(k_assemble_2d<true, false>);
-  else
-    pp.transient ? go(k_assemble_2d<false, true>) : go(k_assemble_2d<false, false>);
+  if (solid) {
+    if (pp.transient == 2) go(k_assemble_2d<true, 2>);
+    else if (pp.transient) go(k_assemble_2d<true, 1>);
+    else go(k_assemble_2d<true, 0>);
+  } else {
+    if (pp.transient == 2) go(k_assemble_2d<false, 2>);
+    else if (pp.transient) go(k_assemble_2d<false, 1>);
+    else go(k_assemble_2d<false, 0>);
+  }
 }
 
 void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
@@ -1080,11 +1311,15 @@ void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* 
       cols<<<nc, 192, smem, st>>>(elems + e0, elem_nodes, node_class, elem_geo, scratch, Ke, Re);
     }
   };
-  if (solid)
-    pp.transient ? go(k_flux_3d<true, true>, k_assemble_3d<true>) : go(k_flux_3d<true, false>, k_assemble_3d<true>);
-  else
-    pp.transient ? go(k_flux_3d<false, true>, k_assemble_3d<false>)
-                 : go(k_flux_3d<false, false>, k_assemble_3d<false>);
+  if (solid) {
+    if (pp.transient == 2) go(k_flux_3d<true, 2>, k_assemble_3d<true>);
+    else if (pp.transient) go(k_flux_3d<true, 1>, k_assemble_3d<true>);
+    else go(k_flux_3d<true, 0>, k_assemble_3d<true>);
+  } else {
+    if (pp.transient == 2) go(k_flux_3d<false, 2>, k_assemble_3d<false>);
+    else if (pp.transient) go(k_flux_3d<false, 1>, k_assemble_3d<false>);
+    else go(k_flux_3d<false, 0>, k_assemble_3d<false>);
+  }
 }
 
 int assemble_launches(int dim, int ne) { return dim == 2 || ne <= 0 ? (ne > 0) : 2 * ((ne + k3Chunk - 1) / k3Chunk); }
