@@ -107,6 +107,8 @@ typedef struct {
   double t_assemble_ms, t_factor_ms, t_solve_ms;  /* device time of the last calls */
   double prec_rel_res;   /* left GMRES: final ||P^{-1} r|| / ||P^{-1} r_0|| (the stopping test);
                             FGMRES: equal to rel_res */
+  double bytes_assemble, bytes_factor, bytes_solve;   /* algorithmic bytes of the last calls: matrix,
+                            index and vector entries their kernels must move at least once */
 } fsi_solve_stats;
 
 typedef struct fsi_ctx fsi_ctx;
@@ -205,6 +207,24 @@ int fsi_newton_update(fsi_ctx* ctx, const double* dx, double* rel_step_out);
 /* One whole Newton step at the current state: assemble, factor, solve
  * J dx = -r, update.  dx_out (N doubles, may be NULL) receives dx. */
 int fsi_newton_step(fsi_ctx* ctx, double* dx_out, double* rel_step_out, fsi_solve_stats* stats);
+/* The second half of fsi_newton_step: solve J dx = -r with the current
+ * factors and the residual of the last fsi_assemble_jacobian, then y += dx
+ * (Sec. 3.1).  For callers that factor several instances together
+ * (fsi_factor_schwarz_batch).  FSI_E_INVALID before the first factorisation. */
+int fsi_newton_solve_update(fsi_ctx* ctx, double* dx_out, double* rel_step_out, fsi_solve_stats* stats);
+
+/* fsi_factor_schwarz for n mixed-precision instances at once (no
+ * counterpart in the paper; the batched form of Sec. 3.3 for serving): the
+ * Schwarz blocks of all their levels >= 1 are factored by one tensor-core
+ * launch per kernel variant (instances whose largest blocks call for the
+ * same panel width share a launch), and each instance's coarse LU runs on
+ * its private stream beside it.  Every block is factored exactly as by the
+ * instance's own fsi_factor_schwarz, so the results are bit-identical.  All
+ * instances must be bound to the same stream (fsi_set_stream) and device and
+ * have >= 2 levels; FSI_E_INVALID otherwise.  Errors of the factorisation
+ * (FSI_E_SINGULAR, FSI_E_TIMEOUT) are reported for the first instance
+ * affected. */
+int fsi_factor_schwarz_batch(fsi_ctx* const* ctxs, int n);
 
 /* ---- nested iteration (full multigrid) for the steady problem ---------- */
 
@@ -355,8 +375,9 @@ int fsi_kernel_stats(fsi_ctx* ctx, int kind, double* device_ms, int64_t* launche
  *   spmv_sub      threads per scalar row of the level's block-sparse residual
  *                 in the V-cycle (mixed path; B = 4 blocks): 2, 4 or 8.
  *   gj_panel      panel width of the tensor-core Gauss-Jordan of the Schwarz
- *                 blocks (16 or 32).  One launch factors every level, so only
- *                 the value set on the finest level counts.
+ *                 blocks (16, 24 or 32; the widest that fits the largest block
+ *                 is taken when the asked one does not).  One launch factors
+ *                 every level, so only the value set on the finest level counts.
  * The values are a property of the ctx; setting them waits for the ctx's
  * stream and drops the recorded V-cycle graph, which is recorded again at the
  * next solve.  FSI_E_INVALID for a bad level or out-of-range values. */
@@ -427,6 +448,14 @@ int fsi_serve_poll(fsi_server* srv, uint64_t ticket, fsi_result* out, double* dx
 int fsi_serve_drain(fsi_server* srv);
 /* Device bytes currently held by resident instances. */
 int64_t fsi_server_resident_bytes(const fsi_server* srv);
+/* Continuous batching of the factorisation: a worker that takes a request of
+ * a resident mixed-precision instance (>= 2 levels) also takes the runnable
+ * requests of up to max_batch - 1 other such instances; each assembles, the
+ * Schwarz blocks of all of them are factored by fsi_factor_schwarz_batch
+ * (one launch per kernel variant), then each solves and updates.  Results
+ * are bit-identical to unbatched steps.  1 turns it off; the default is 4.
+ * FSI_E_INVALID outside [1, 64]. */
+int fsi_server_set_batching(fsi_server* srv, int max_batch);
 /* Waits for running requests, frees every instance and the server. */
 int fsi_server_destroy(fsi_server* srv);
 

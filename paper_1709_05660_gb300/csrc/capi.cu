@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fsi_internal.h"
 #include "kernels.h"
 
@@ -83,13 +85,21 @@ cudaEvent_t get_event(Ctx& c) {
   return e;
 }
 
+// NVTX range of a phase (visible in Nsight timelines; no cost without a tool)
+struct Nvtx {
+  explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+};
+
 // Brackets the launches of one kernel class with events (profiling only) and
-// accumulates their algorithmic bytes / flops.
+// accumulates their algorithmic bytes / flops; the bytes are also counted
+// without profiling, for the per-phase totals of fsi_solve_stats.
 struct Prof {
   Ctx& c;
   int kind;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   Prof(Ctx& c_, int k, double bytes, double flops, int launches = 1) : c(c_), kind(k) {
+    c.alg_bytes += bytes;
     if (!c.prof) return;
     e0 = get_event(c);
     e1 = get_event(c);
@@ -371,7 +381,16 @@ std::vector<int32_t> coarse_pads(const Ctx& c) {
 // ---------------------------------------------------------------------------
 // assembly
 // ---------------------------------------------------------------------------
+void assemble_impl(Ctx& c);
 void assemble(Ctx& c, bool want_res) {
+  Nvtx nv("fsi assemble + Galerkin");
+  const double b0 = c.alg_bytes;
+  assemble_impl(c);
+  c.b_assemble = c.alg_bytes - b0;
+  (void)want_res;
+}
+
+void assemble_impl(Ctx& c) {
   const int L = (int)c.dl.size();
   const int B = c.B;
   DevLevel& F = c.dl[L - 1];
@@ -450,7 +469,6 @@ void assemble(Ctx& c, bool want_res) {
       counted(c);
     }
   check_status(c);
-  (void)want_res;
 }
 
 // ---------------------------------------------------------------------------
@@ -549,6 +567,40 @@ double coarse_slab_apply_bytes(const Ctx& c) {
 // ---------------------------------------------------------------------------
 // Schwarz factorisation (all levels >= 1) + coarse LU
 // ---------------------------------------------------------------------------
+// Largest Schwarz block of the instance (levels >= 1).
+int max_block(const Ctx& c) {
+  int m = 0;
+  for (size_t l = 1; l < c.dl.size(); ++l) m = std::max(m, c.dl[l].max_n);
+  return m;
+}
+
+// Mixed path: gathers the Schwarz blocks of every level >= 1 of c into the
+// level's region of its FP32 workspace (on c.stream) and appends the levels
+// to the tensor-core factorisation table lv (blocks numbered from *first).
+// Returns false when a level has no blocks or the table is full.
+bool gather_mixed(Ctx& c, GjLevels& lv, int& first, int& max_n) {
+  const int L = (int)c.dl.size();
+  float* ws = reinterpret_cast<float*>(c.dense_ws);
+  int64_t off = 0;
+  bool ok = true;
+  for (int l = 1; l < L; ++l) {
+    DevLevel& D = c.dl[l];
+    launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
+                                 D.p_padpos, D.val, c.B, ws + off, D.p_idx_off, D.dr32, D.dc32, c.stream);
+    counted(c);
+    if (D.n_patches > 0 && lv.nlev < kGjMaxLevels) {
+      lv.l[lv.nlev++] = GjLevel{D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own, D.p_inv_off, ws + off,
+                                D.inv32, c.status, first};
+      first += D.n_patches;
+      max_n = std::max(max_n, D.max_n);
+    } else {
+      ok = false;
+    }
+    off += D.dense_total;
+  }
+  return ok;
+}
+
 void schwarz_factor(Ctx& c) {
   const int L = (int)c.dl.size();
   const int B = c.B;
@@ -572,19 +624,8 @@ void schwarz_factor(Ctx& c) {
       fl += D.factor_flops;
     }
     Prof pr(c, FSI_K_PATCH_FACTOR, by, fl, L);
-    for (int l = 1; l < L; ++l) {
-      DevLevel& D = c.dl[l];
-      launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
-                                   D.p_padpos, D.val, B, ws + base[l], D.p_idx_off, D.dr32, D.dc32, c.stream);
-      counted(c);
-      if (D.n_patches > 0 && lv.nlev < kGjMaxLevels) {
-        lv.l[lv.nlev++] = GjLevel{D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own, D.p_inv_off, ws + base[l],
-                                  D.inv32, first};
-        first += D.n_patches;
-        max_n = std::max(max_n, D.max_n);
-      }
-    }
-    if (lv.nlev == L - 1 && launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream, c.gj_panel)) {
+    const bool all = gather_mixed(c, lv, first, max_n);
+    if (all && launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream, c.gj_panel)) {
       counted(c);
     } else {
       for (int l = 1; l < L; ++l) {   // blocks too large for the tensor-core kernel: level by level
@@ -660,6 +701,8 @@ struct StreamSwap {   // launches of the enclosing scope go to another stream
 // per-class profiling on (events on the ctx stream) the two run one after the
 // other.
 void factor(Ctx& c) {
+  Nvtx nv("fsi factor (Schwarz + coarse)");
+  const double b0 = c.alg_bytes;
   const bool fork = !c.prof && aux_stream(c);
   if (fork) {
     cudaEventRecord(c.ev_fork, c.stream);
@@ -675,6 +718,7 @@ void factor(Ctx& c) {
   else coarse_factor(c);
   check_status(c);
   c.factored = true;
+  c.b_factor = c.alg_bytes - b0;
 }
 
 // ---------------------------------------------------------------------------
@@ -789,6 +833,10 @@ void smooth_step_t(Ctx& c, int l, const T* b, T* x, bool x_is_zero) {
 
 template <typename T>
 void vcycle_t(Ctx& c, int l, const T* b, T* x) {
+  static const char* names[] = {"fsi V-cycle level 0", "fsi V-cycle level 1", "fsi V-cycle level 2",
+                                "fsi V-cycle level 3", "fsi V-cycle level 4", "fsi V-cycle level 5",
+                                "fsi V-cycle level 6", "fsi V-cycle level 7+"};
+  Nvtx nv(names[l < 7 ? l : 7]);
   if (l == 0) {
     VC<T>::coarse(c, b, x);
     return;
@@ -818,6 +866,7 @@ void capture_vcycle(Ctx& c) {
   }
   const cudaStream_t saved = c.stream;
   const int64_t l0 = c.launches;
+  const double b0 = c.alg_bytes;
   c.stream = c.cap_stream;
   bool ok = cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
@@ -839,6 +888,8 @@ void capture_vcycle(Ctx& c) {
   c.stream = saved;
   c.vc_launches = c.launches - l0;
   c.launches = l0;
+  c.vc_bytes = c.alg_bytes - b0;   // algorithmic bytes of one V-cycle (counted per replay)
+  c.alg_bytes = b0;
   if (!ok) {
     c.vc_exec = nullptr;
     c.vc_graph_failed = true;
@@ -861,6 +912,7 @@ void precondition(Ctx& c, const double* v, double* z64, float* z32) {
       }
       ck(cudaGraphLaunch(c.vc_exec, c.stream), "cudaGraphLaunch");
       c.launches += c.vc_launches;
+      c.alg_bytes += c.vc_bytes;
       if (c.mixed) {
         if (z32 != F.x32)
           ck(cudaMemcpyAsync(z32, F.x32, F.Ni * sizeof(float), cudaMemcpyDeviceToDevice, c.stream), "copy");
@@ -1117,6 +1169,13 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
 }
 
 void krylov_solve(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
+  Nvtx nv(c.opts.krylov == FSI_GMRES_LEFT ? "fsi GMRES (left)" : "fsi FGMRES");
+  const double b0 = c.alg_bytes;
+  struct Tally {   // also when the solve ends with an error
+    Ctx& c;
+    double b0;
+    ~Tally() { c.b_solve = c.alg_bytes - b0; }
+  } tally{c, b0};
   if (c.opts.krylov == FSI_GMRES_LEFT) gmres_left(c, b, x, st);
   else fgmres(c, b, x, st);
 }
@@ -1460,7 +1519,10 @@ int fsi_solve(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
     to_canonical(*c, L - 1, c->xk, x);
     sync(*c);
     c->t_solve = elapsed(*c);
-    if (st) { st->t_assemble_ms = c->t_assemble; st->t_factor_ms = c->t_factor; st->t_solve_ms = c->t_solve; }
+    if (st) {
+      st->t_assemble_ms = c->t_assemble; st->t_factor_ms = c->t_factor; st->t_solve_ms = c->t_solve;
+      st->bytes_assemble = c->b_assemble; st->bytes_factor = c->b_factor; st->bytes_solve = c->b_solve;
+    }
     if (rc != FSI_OK) throw ApiError(rc, msg);
   });
 }
@@ -1481,11 +1543,15 @@ int fsi_newton_update(fsi_ctx* c, const double* dx, double* rel_step_out) {
   });
 }
 
+namespace {
+// Second half of a Newton step: solve J dx = -r with the current factors and
+// the residual of the last assembly, then y += dx.
+void solve_update(Ctx* c, double* dx_out, double* rel_step_out, fsi_solve_stats* st);
+}  // namespace
+
 int fsi_newton_step(fsi_ctx* c, double* dx_out, double* rel_step_out, fsi_solve_stats* st) {
   return guard(c, [&] {
     need_device(*c);
-    const int L = (int)c->dl.size();
-    const int64_t n = c->dl[L - 1].Ni;
     ck(cudaEventRecord(c->ev0, c->stream), "event");
     assemble(*c, true);
     ck(cudaEventRecord(c->ev1, c->stream), "event");
@@ -1496,6 +1562,113 @@ int fsi_newton_step(fsi_ctx* c, double* dx_out, double* rel_step_out, fsi_solve_
     ck(cudaEventRecord(c->ev1, c->stream), "event");
     sync(*c);
     c->t_factor = elapsed(*c);
+    solve_update(c, dx_out, rel_step_out, st);
+  });
+}
+
+int fsi_newton_solve_update(fsi_ctx* c, double* dx_out, double* rel_step_out, fsi_solve_stats* st) {
+  return guard(c, [&] {
+    need_device(*c);
+    if (!c->factored) throw ApiError(FSI_E_INVALID, "fsi_newton_solve_update: assemble and factor first");
+    solve_update(c, dx_out, rel_step_out, st);
+  });
+}
+
+int fsi_factor_schwarz_batch(fsi_ctx* const* ctxs, int n) {
+  if (!ctxs || n < 1) return FSI_E_INVALID;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return FSI_E_INVALID;
+  fsi_ctx* c0 = ctxs[0];
+  return guard(c0, [&] {
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctxs[i];
+      need_device(c);
+      if (!c.mixed || c.dl.size() < 2)
+        throw ApiError(FSI_E_INVALID, "batched factorisation: mixed-precision instances with >= 2 levels only");
+      if (c.stream != c0->stream || c.device != c0->device)
+        throw ApiError(FSI_E_INVALID, "batched factorisation: every instance on the same stream and device");
+      if (c.prof) throw ApiError(FSI_E_INVALID, "batched factorisation: per-class profiling is on");
+      for (int j = 0; j < i; ++j)
+        if (ctxs[j] == ctxs[i]) throw ApiError(FSI_E_INVALID, "batched factorisation: an instance appears twice");
+    }
+    const cudaStream_t st = c0->stream;
+    ck(cudaEventRecord(c0->ev0, st), "event");
+    // coarse factorisations on each instance's private stream, forked from the common stream
+    std::vector<bool> forked(n, false);
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctxs[i];
+      if (!aux_stream(c)) continue;
+      cudaEventRecord(c.ev_fork, st);
+      cudaStreamWaitEvent(c.aux_stream, c.ev_fork, 0);
+      {
+        StreamSwap sw(c, c.aux_stream);
+        coarse_factor(c);
+      }
+      cudaEventRecord(c.ev_join, c.aux_stream);
+      forked[i] = true;
+    }
+    // instances grouped by the tensor-core variant each would use alone, so
+    // every block is factored exactly as in its own fsi_factor_schwarz
+    std::vector<int> variant(n);
+    for (int i = 0; i < n; ++i) variant[i] = gj_tc_variant(max_block(*ctxs[i]), ctxs[i]->gj_panel);
+    std::vector<bool> done(n, false);
+    for (int i = 0; i < n; ++i) {
+      if (done[i]) continue;
+      if (variant[i] == 0) {   // no tensor-core variant fits: the instance's own path
+        schwarz_factor(*ctxs[i]);
+        done[i] = true;
+        continue;
+      }
+      GjLevels lv{};
+      lv.nlev = 0;
+      lv.first_wait = kTcWaitIters;
+      int first = 0, max_n = 0;
+      for (int j = i; j < n; ++j) {
+        if (done[j] || variant[j] != variant[i]) continue;
+        Ctx& c = *ctxs[j];
+        if (lv.nlev + (int)c.dl.size() - 1 > kGjMaxLevels) continue;   // next launch
+        GjLevels one = lv;
+        int f1 = first, m1 = max_n;
+        if (!gather_mixed(c, one, f1, m1)) {   // a level without blocks: its own path
+          schwarz_factor(c);
+          done[j] = true;
+          continue;
+        }
+        lv = one;
+        first = f1;
+        max_n = m1;
+        done[j] = true;
+      }
+      if (lv.nlev > 0) {
+        if (!launch_patch_gj_tc_levels(lv, first, max_n, c0->status, st, variant[i]))
+          throw ApiError(FSI_E_CUDA, "batched factorisation: tensor-core launch refused");
+        counted(*c0);
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctxs[i];
+      if (forked[i]) cudaStreamWaitEvent(st, c.ev_join, 0);
+      else coarse_factor(c);
+    }
+    ck(cudaEventRecord(c0->ev1, st), "event");
+    sync(*c0);
+    const float ms = elapsed(*c0);
+    for (int i = 0; i < n; ++i) {
+      Ctx& c = *ctxs[i];
+      check_status(c);
+      c.factored = true;
+      c.t_factor = ms;
+      double by = 0.0;   // the Schwarz gathers and inverses (the coarse LU is in the level-0 estimate)
+      for (size_t l = 1; l < c.dl.size(); ++l) by += c.dl[l].factor_bytes;
+      c.b_factor = by + (double)c.dl[0].Ni * c.dl[0].Ni * 8.0 * 3.0;
+    }
+  });
+}
+
+namespace {
+void solve_update(Ctx* c, double* dx_out, double* rel_step_out, fsi_solve_stats* st) {
+    const int L = (int)c->dl.size();
+    const int64_t n = c->dl[L - 1].Ni;
     launch_axpby(n, -1.0, c->res, 0.0, c->bk, c->stream);
     ck(cudaMemsetAsync(c->xk, 0, n * sizeof(double), c->stream), "memset");
     counted(*c);
@@ -1511,9 +1684,12 @@ int fsi_newton_step(fsi_ctx* c, double* dx_out, double* rel_step_out, fsi_solve_
     if (rel_step_out) *rel_step_out = yn > 0 ? dn / yn : dn;
     if (dx_out) to_canonical(*c, L - 1, c->xk, dx_out);
     sync(*c);
-    if (st) { st->t_assemble_ms = c->t_assemble; st->t_factor_ms = c->t_factor; st->t_solve_ms = c->t_solve; }
-  });
+    if (st) {
+      st->t_assemble_ms = c->t_assemble; st->t_factor_ms = c->t_factor; st->t_solve_ms = c->t_solve;
+      st->bytes_assemble = c->b_assemble; st->bytes_factor = c->b_factor; st->bytes_solve = c->b_solve;
+    }
 }
+}  // namespace
 
 int fsi_export_csr(fsi_ctx* c, int level, int64_t* rowptr, int32_t* col, double* val) {
   return guard(c, [&] {
@@ -1920,7 +2096,7 @@ int fsi_set_launch_params(fsi_ctx* c, int level, const fsi_launch_params* p) {
     if (!p) throw ApiError(FSI_E_INVALID, "null launch parameters");
     if (p->apply_slices < 0 || p->apply_slices > 4096 || p->apply_groups < 0 || p->apply_groups > 256 ||
         (p->spmv_sub != 0 && p->spmv_sub != 2 && p->spmv_sub != 4 && p->spmv_sub != 8) ||
-        (p->gj_panel != 0 && p->gj_panel != 16 && p->gj_panel != 32))
+        (p->gj_panel != 0 && p->gj_panel != 16 && p->gj_panel != 24 && p->gj_panel != 32))
       throw ApiError(FSI_E_INVALID, "launch parameters out of range");
     sync(*c);   // nothing in flight uses the old shapes or the graph
     DevLevel& D = c->dl[level];

@@ -191,12 +191,15 @@ struct Ctx {
   cudaStream_t cap_stream = nullptr;
   // the coarse factorisation runs on this higher-priority stream beside the
   // Schwarz factorisation (fork / join events on the ctx stream)
-  int gj_panel = 0;   // preferred Gauss-Jordan panel width on the tensor cores (0, 16, 32)
+  int gj_panel = 0;   // preferred Gauss-Jordan panel width on the tensor cores (0, 16, 24, 32)
   long long tc_first_wait = -1;   // first tensor-core wait limit (< 0: the built-in limit)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool aux_failed = false;
   int64_t vc_launches = 0;
+  double vc_bytes = 0.0;                  // algorithmic bytes of one recorded V-cycle
+  double alg_bytes = 0.0;                 // running total of algorithmic bytes of all launches
+  double b_assemble = 0.0, b_factor = 0.0, b_solve = 0.0;   // of the last call of each phase
   bool vc_graph_failed = false;
   // per-kernel-class profiling
   bool prof = false;

@@ -632,22 +632,29 @@ bool try_gj_f32(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, co
 // one of two accumulators, so the UMMAs of tile t + 1 run while tile t is
 // added to M: D is staged through shared memory and each warp adds whole
 // rows of it to M with coalesced loads and stores (panel columns excluded).
-// Tensor memory: accumulators in columns [0, 256), the A parts of row tile t
-// at 256 + 2 W t.  Requires n % 4 == 0.  The waits on the tensor core are
-// bounded; on time-out the block records ST_TIMEOUT, stops issuing work and
-// releases its tensor memory.
+// Tiles are 128 rows x TN columns.  Tensor memory: the two accumulators in
+// columns [0, 2 TN), the A parts of row tile t at 2 TN + 2 W t.  The panel
+// width W is what the 512 columns leave room for: W = 32 with TN = 128 up to
+// n = 512, W = 24 with TN = 64 (narrower accumulators, wider panel: a third
+// fewer passes over M) or W = 16 with TN = 128 up to n = 1024.  Requires
+// n % 4 == 0.  The waits on the tensor core are bounded; on time-out the
+// block records ST_TIMEOUT, stops issuing work and releases its tensor memory.
 // ---------------------------------------------------------------------------
-template <int W>
-__host__ __device__ constexpr int gj_tc_max_n() { return W == 32 ? 512 : 1024; }   // A parts + accumulators fit 512 columns
-template <int W>
-__host__ __device__ constexpr int gj_tc_threads() { return gj_tc_max_n<W>(); }   // one thread per row
-constexpr int kStage = 129;   // row stride of the staged accumulator tile (conflict-free banks)
+template <int W, int TN>
+__host__ __device__ constexpr int gj_tc_max_n() {
+  // row tiles whose A parts (2 W columns each) fit beside the accumulators
+  return (512 - 2 * TN) / (2 * W) * 128 < 1024 ? (512 - 2 * TN) / (2 * W) * 128 : 1024;
+}
+template <int W, int TN>
+__host__ __device__ constexpr int gj_tc_threads() { return gj_tc_max_n<W, TN>(); }   // one thread per row
+template <int TN>
+__host__ __device__ constexpr int gj_stage() { return TN + 1; }   // row stride of the staged tile (conflict-free banks)
 
-template <int W>
+template <int W, int TN>
 size_t gj_tc_smem(int max_n) {
   const size_t n16 = ((size_t)max_n + 15) / 16 * 16;
-  return (2 * n16 * W + 2 * 32 * (size_t)W + 128 * (size_t)kStage) * sizeof(float) + 2 * 32 * sizeof(uint32_t) +
-         2 * (size_t)max_n * sizeof(int) + (size_t)max_n + 64;
+  return (2 * n16 * W + 2 * 32 * (size_t)W + 128 * (size_t)gj_stage<TN>()) * sizeof(float) +
+         2 * 32 * sizeof(uint32_t) + 2 * (size_t)max_n * sizeof(int) + (size_t)max_n + 64;
 }
 
 // pivot key: larger |a| wins, ties to the lower row; 0 = no candidate
@@ -657,19 +664,22 @@ __device__ __forceinline__ uint32_t piv_key(float a, int row) {
   return (b & ~0x3FFu) | (uint32_t)(1023 - row);
 }
 
-template <int W>
-__global__ void __launch_bounds__(gj_tc_threads<W>(), 1)
+template <int W, int TN>
+__global__ void __launch_bounds__(gj_tc_threads<W, TN>(), 1)
 k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
-  static_assert(W == 16 || W == 32, "panel width");
-  constexpr int NWARP = gj_tc_threads<W>() / kWarp;   // 16 or 32 warps
-  constexpr int CGN = NWARP / 4;                       // column chunks of a tile per lane quarter
-  constexpr int CW = 128 / CGN;                        // chunk width: 32 (512 threads) or 16 (1024)
+  static_assert(W % 8 == 0 && W >= 16 && W <= 32, "panel width");
+  static_assert(TN == 64 || TN == 128, "tile width");
+  constexpr int NWARP = gj_tc_threads<W, TN>() / kWarp;   // 16 or 32 warps
+  constexpr int CGN = NWARP / 4;                           // column-chunk slots of a tile per lane quarter
+  constexpr int CW = TN / CGN > 16 ? TN / CGN : 16;        // chunk width (multiple of 16)
+  constexpr int kStage = gj_stage<TN>();
+  constexpr int NE = TN / 32;                              // tile columns per lane in the epilogue
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n16 = (max_n + 15) / 16 * 16;
   float* Bhi = reinterpret_cast<float*>(smem_raw);          // n16 x W, K-major
   float* Blo = Bhi + (size_t)n16 * W;
   float* offer_row = Blo + (size_t)n16 * W;                 // [2][32][W] panel values of each warp's offer
-  float* stage = offer_row + 2 * 32 * W;                    // 128 x kStage accumulator tile
+  float* stage = offer_row + 2 * 32 * W;                    // 128 x kStage staged accumulator tile
   uint32_t* offer_key = reinterpret_cast<uint32_t*>(stage + 128 * kStage);   // [2][32]
   int* piv = reinterpret_cast<int*>(offer_key + 64);        // max_n
   int* qinv = piv + max_n;                                  // max_n
@@ -688,7 +698,7 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
   const int me = threadIdx.x;
   const bool has_row = me < n;
   const bool warp_rows = wid * kWarp < n;     // this warp owns at least one row
-  constexpr uint32_t kCols = 512, kD = 256;
+  constexpr uint32_t kCols = 512, kD = 2 * TN;
   if (wid == 0) tc::tmem_alloc(&tslot, kCols);
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar2[0], 1);
@@ -813,18 +823,18 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
       bool any = false;
       const uint32_t col = kD + 2u * W * (uint32_t)(me / 128);
 #pragma unroll
-      for (int h = 0; h < W / 16; ++h) {   // 16 columns at a time: hi part, then lo part
-        float ahi[16], alo[16];
+      for (int h = 0; h < W / 8; ++h) {   // 8 columns at a time: hi part, then lo part
+        float ahi[8], alo[8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int cc = 16 * h + c;
+        for (int c = 0; c < 8; ++c) {
+          const int cc = 8 * h + c;
           const float a = (has_row && cc < wp) ? (cc == my_step ? row[cc] - 1.f : row[cc]) : 0.f;
           any |= a != 0.f;
           ahi[c] = tc::to_tf32(a);
           alo[c] = a - ahi[c];
         }
-        tc::tmem_st16(tc::taddr(tbase, 32 * q, col + 16 * h), ahi);
-        tc::tmem_st16(tc::taddr(tbase, 32 * q, col + W + 16 * h), alo);
+        tc::tmem_st8(tc::taddr(tbase, 32 * q, col + 8 * h), ahi);
+        tc::tmem_st8(tc::taddr(tbase, 32 * q, col + W + 8 * h), alo);
       }
       tc::tmem_wait_st();
       if (has_row) live[me] = any;
@@ -844,16 +854,16 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
     // trailing update: tile t's UMMAs into accumulator t % 2, issued one tile
     // ahead of the epilogue that adds the previous tile to M
     {
-      const int ntc = (n + 127) / 128, ntiles = ntc * ntc;
+      const int ntr = (n + 127) / 128, ntcc = (n + TN - 1) / TN, ntiles = ntr * ntcc;
       auto issue = [&](int t) {
-        const int i0 = (t / ntc) * 128, j0 = (t % ntc) * 128, b = t & 1;
-        const int nt = min(128, (n - j0 + 15) / 16 * 16);
+        const int i0 = (t / ntcc) * 128, j0 = (t % ntcc) * TN, b = t & 1;
+        const int nt = min(TN, (n - j0 + 15) / 16 * 16);
         const uint32_t id = tc::idesc_tf32(128, nt);
         const uint32_t lbo = tc::kmajor_lbo<W>(), sbo = tc::kmajor_sbo<W>();
         const uint32_t ahi = tbase + kD + 2u * W * (uint32_t)(i0 / 128), alo = ahi + W;
         const uint32_t b0 = tc::smem_u32(Bhi) + (uint32_t)(j0 / 8) * sbo;
         const uint32_t b1 = tc::smem_u32(Blo) + (uint32_t)(j0 / 8) * sbo;
-        const uint32_t d = tbase + 128u * b;
+        const uint32_t d = tbase + (uint32_t)TN * b;
 #pragma unroll
         for (int s8 = 0; s8 < W / 8; ++s8) {
           const uint32_t ko = 256u * s8;   // two core matrices (8 k-values) of B per UMMA
@@ -866,18 +876,18 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
       if (threadIdx.x == 0) issue(0);
       constexpr int RPW = 128 / NWARP;   // epilogue rows per warp
       for (int t = 0; t < ntiles; ++t) {
-        const int i0 = (t / ntc) * 128, j0 = (t % ntc) * 128, b = t & 1;
-        const int nt = min(128, (n - j0 + 15) / 16 * 16);
-        // the tile's old values (lane l: columns l, l + 32, l + 64, l + 96 of
-        // its warp's rows) are loaded before waiting for the tile's UMMAs, so
-        // their L2 round trip overlaps the tensor-core work and the staging
-        float old[RPW][4];
+        const int i0 = (t / ntcc) * 128, j0 = (t % ntcc) * TN, b = t & 1;
+        const int nt = min(TN, (n - j0 + 15) / 16 * 16);
+        // the tile's old values (lane l: columns l, l + 32, ... of its warp's
+        // rows) are loaded before waiting for the tile's UMMAs, so their L2
+        // round trip overlaps the tensor-core work and the staging
+        float old[RPW][NE];
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
           const int r = i0 + wid + NWARP * k;
           const bool ok = r < n && live[r];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
+          for (int e = 0; e < NE; ++e) {
             const int c = lane + 32 * e, j = j0 + c;
             old[k][e] = (ok && c < nt && j < n) ? M[(int64_t)r * n + j] : 0.f;
           }
@@ -903,7 +913,7 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
 #pragma unroll
             for (int h = 0; h < CW / 16; ++h) {
               float v[16];
-              tc::tmem_ld<16>(tc::taddr(tbase, 32 * q, 128u * b + cg * CW + 16 * h), v);
+              tc::tmem_ld<16>(tc::taddr(tbase, 32 * q, (uint32_t)TN * b + cg * CW + 16 * h), v);
               tc::tmem_wait_ld();
               float* srow = stage + (32 * q + lane) * kStage + cg * CW + 16 * h;
 #pragma unroll
@@ -914,7 +924,7 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
         tc::fence_before_sync();
         __syncthreads();
         // M += D for live rows, panel columns excluded: lane l adds columns
-        // l, l + 32, l + 64, l + 96 of a row (coalesced)
+        // l, l + 32, ... of a row (coalesced)
         {
 #pragma unroll
           for (int k = 0; k < RPW; ++k) {
@@ -922,7 +932,7 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
             if (!(r < n && live[r])) continue;
             const float* srow = stage + rr * kStage;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < NE; ++e) {
               const int c = lane + 32 * e, j = j0 + c;
               if (c < nt && j < n && !(j >= k0 && j < k0 + wp)) M[(int64_t)r * n + j] = old[k][e] + srow[c];
             }
@@ -966,27 +976,45 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
 done:
   tc::fence_before_sync();
   __syncthreads();
-  if (s_abort && threadIdx.x == 0) atomicExch(&status[ST_TIMEOUT], 1);
+  int32_t* const stat = L.status ? L.status : status;   // the block's own instance
+  if (s_abort && threadIdx.x == 0) atomicExch(&stat[ST_TIMEOUT], 1);
   tc::fence_after_sync();
   if (wid == 0) tc::tmem_dealloc(tbase, kCols);
-  if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
+  if (threadIdx.x == 0 && s_sing) atomicExch(&stat[ST_SINGULAR], 1);
 }
 
-template <int W>
-bool try_gj_tc(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st) {
-  const size_t smem = gj_tc_smem<W>(max_n);
-  if (smem > 225 * 1024 || max_n % 4 != 0 || max_n > gj_tc_max_n<W>() || max_n < 64) return false;
-  cudaFuncSetAttribute(k_patch_gj_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_patch_gj_tc<W><<<nblocks, gj_tc_threads<W>(), smem, st>>>(lv, status, max_n);
-  return true;
+template <int W, int TN>
+bool fits_gj_tc(int max_n) {
+  const size_t smem = gj_tc_smem<W, TN>(max_n);
+  return !(smem > 225 * 1024 || max_n % 4 != 0 || max_n > gj_tc_max_n<W, TN>() || max_n < 64);
+}
+
+template <int W, int TN>
+void run_gj_tc(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st) {
+  const size_t smem = gj_tc_smem<W, TN>(max_n);
+  cudaFuncSetAttribute(k_patch_gj_tc<W, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_patch_gj_tc<W, TN><<<nblocks, gj_tc_threads<W, TN>(), smem, st>>>(lv, status, max_n);
+}
+
+// the widest panel that fits, unless a narrower one that fits was asked for
+int gj_tc_variant(int max_n, int panel) {
+  if (panel == 16 && fits_gj_tc<16, 128>(max_n)) return 16;
+  if (panel == 24 && fits_gj_tc<24, 64>(max_n)) return 24;
+  if (fits_gj_tc<32, 128>(max_n)) return 32;
+  if (fits_gj_tc<24, 64>(max_n)) return 24;
+  if (fits_gj_tc<16, 128>(max_n)) return 16;
+  return 0;
 }
 
 bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st,
                                int panel) {
   if (nblocks <= 0 || lv.nlev < 1 || lv.nlev > kGjMaxLevels) return false;
-  if (panel == 16 && try_gj_tc<16>(lv, nblocks, max_n, status, st)) return true;
-  if (try_gj_tc<32>(lv, nblocks, max_n, status, st)) return true;
-  return try_gj_tc<16>(lv, nblocks, max_n, status, st);
+  switch (gj_tc_variant(max_n, panel)) {
+    case 32: run_gj_tc<32, 128>(lv, nblocks, max_n, status, st); return true;
+    case 24: run_gj_tc<24, 64>(lv, nblocks, max_n, status, st); return true;
+    case 16: run_gj_tc<16, 128>(lv, nblocks, max_n, status, st); return true;
+    default: return false;
+  }
 }
 
 template <typename T, int W>
@@ -1131,7 +1159,7 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
     GjLevels lv{};
     lv.nlev = 1;
     lv.first_wait = kTcWaitIters;
-    lv.l[0] = GjLevel{p_n, p_nown, dense_off, own_off, own, inv_off, d, o, 0};
+    lv.l[0] = GjLevel{p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, 0};
     if (launch_patch_gj_tc_levels(lv, np, max_n, status, st)) return;
     if (try_gj_f32<32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
     if (try_gj_f32<16>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;

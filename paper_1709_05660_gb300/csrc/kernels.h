@@ -66,7 +66,7 @@ void launch_nonfinite_check(int64_t n, const double* v, int32_t* status, cudaStr
 // k_schwarz.cu (T = double: FP64 path, T = float: mixed path)
 // Schwarz blocks of one level for the tensor-core factorisation; several
 // levels can share one launch (blocks first .. first + n_patches - 1)
-constexpr int kGjMaxLevels = 10;
+constexpr int kGjMaxLevels = 24;   // levels of one launch (several instances may share it)
 struct GjLevel {
   const int32_t* p_n;
   const int32_t* p_nown;
@@ -76,6 +76,7 @@ struct GjLevel {
   const int64_t* inv_off;
   float* dense;
   float* invT;
+  int32_t* status;   // status flags of the instance the level belongs to
   int first;
 };
 struct GjLevels {
@@ -91,6 +92,9 @@ constexpr long long kTcWaitIters = 1LL << 22;
 // panel: preferred panel width (16 or 32; 0 = 32 when the blocks fit, else 16)
 bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st,
                                int panel = 0);
+// panel width of the tensor-core variant that launch_patch_gj_tc_levels picks
+// for blocks up to max_n with preference `panel` (0: none fits)
+int gj_tc_variant(int max_n, int panel);
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
                            const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,

@@ -27,6 +27,7 @@ struct Instance {
   bool busy = false;
   int64_t n = 0;
   int failed = 0;                  // error of an earlier step that freed the instance
+  bool batchable = false;          // mixed precision with >= 2 levels: may share a factorisation launch
 };
 
 struct Ticket {
@@ -49,6 +50,7 @@ double ms(Clock::time_point a, Clock::time_point b) {
 struct fsi_server {
   int64_t budget = 0;
   int64_t resident = 0;
+  int max_batch = 4;                   // requests that may share one Schwarz factorisation launch
   std::mutex mu;
   std::condition_variable cv, done_cv;
   std::deque<Ticket*> queue;
@@ -60,12 +62,14 @@ struct fsi_server {
   int running = 0;
   bool stop = false;
 
-  // first runnable ticket in arrival order (caller holds mu)
-  Ticket* pick() {
+  // first runnable ticket in arrival order (caller holds mu); with
+  // batch_only, only requests of resident batchable instances qualify
+  Ticket* pick(bool batch_only = false) {
     for (auto it = queue.begin(); it != queue.end(); ++it) {
       Ticket* t = *it;
       auto f = inst.find(t->req.instance);
       if (f != inst.end() && f->second.busy) continue;                 // in order per instance
+      if (batch_only && (f == inst.end() || !f->second.ctx || !f->second.batchable)) continue;
       bool earlier_same = false;                                       // an older request of it waits
       for (auto jt = queue.begin(); jt != it; ++jt)
         if ((*jt)->req.instance == t->req.instance) { earlier_same = true; break; }
@@ -79,98 +83,164 @@ struct fsi_server {
     return nullptr;
   }
 
-  void work(int slot) {
-    cudaStream_t stream = streams[slot];
-    std::vector<double> dxbuf;
-    while (true) {
-      Ticket* t = nullptr;
-      {
-        std::unique_lock<std::mutex> lk(mu);
-        cv.wait(lk, [&] { return stop || (t = pick()) != nullptr; });
-        if (!t) break;
-        auto& in = inst[t->req.instance];
-        in.busy = true;
-        if (!in.ctx && !in.failed) resident += t->planned;   // reserve before building
-        t->state = 1;
-        t->t_start = Clock::now();
-        ++running;
-      }
-      Instance* in;
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        in = &inst[t->req.instance];
-      }
-      int rc = FSI_OK;
-      if (in->failed) {
-        // an earlier step of this instance failed and freed it: complete the
-        // request at once with that step's error instead of rebuilding it
-        rc = in->failed;
-      } else if (!in->ctx) {
-        rc = fsi_build_hierarchy(&t->req.desc, &t->req.opts, stream, &in->ctx);
-        if (rc == FSI_OK) {
-          int64_t nl[16], hb = 0;
-          fsi_get_sizes(in->ctx, nl, nullptr, &hb);
-          in->n = nl[t->req.desc.levels - 1];
-          in->bytes = hb;
-          std::vector<double> y(in->n);
-          rc = fsi_initial_state(in->ctx, t->noise.data(), y.data());
-          if (rc == FSI_OK) rc = fsi_set_state(in->ctx, y.data(), nullptr, nullptr, 0.0);
-        }
-        std::lock_guard<std::mutex> lk(mu);
-        resident += (rc == FSI_OK ? in->bytes : 0) - t->planned;
-        t->planned = 0;
-        if (rc != FSI_OK && in->ctx) {
+  // marks a picked ticket running (caller holds mu)
+  void claim(Ticket* t) {
+    auto& in = inst[t->req.instance];
+    in.busy = true;
+    if (!in.ctx && !in.failed) resident += t->planned;   // reserve before building
+    t->state = 1;
+    t->t_start = Clock::now();
+    ++running;
+  }
+
+  // first request of an instance: build its hierarchy and initial state
+  int build(Ticket* t, Instance* in, cudaStream_t stream) {
+    int rc = fsi_build_hierarchy(&t->req.desc, &t->req.opts, stream, &in->ctx);
+    if (rc == FSI_OK) {
+      int64_t nl[16], hb = 0;
+      fsi_get_sizes(in->ctx, nl, nullptr, &hb);
+      in->n = nl[t->req.desc.levels - 1];
+      in->bytes = hb;
+      in->batchable = t->req.opts.precision == FSI_MIXED && t->req.desc.levels >= 2;
+      std::vector<double> y(in->n);
+      rc = fsi_initial_state(in->ctx, t->noise.data(), y.data());
+      if (rc == FSI_OK) rc = fsi_set_state(in->ctx, y.data(), nullptr, nullptr, 0.0);
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    resident += (rc == FSI_OK ? in->bytes : 0) - t->planned;
+    t->planned = 0;
+    if (rc != FSI_OK && in->ctx) {
+      fsi_destroy(in->ctx);
+      in->ctx = nullptr;
+    }
+    return rc;
+  }
+
+  // records a finished step and frees / keeps its instance
+  void finish(Ticket* t, Instance* in, int rc, double rel, const fsi_solve_stats& st, std::vector<double>& dx) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      t->t_end = Clock::now();
+      t->res.status = rc;
+      t->res.iters = st.iters;
+      t->res.rel_step = rel;
+      t->res.rel_res = st.rel_res;
+      t->res.n = in->n;
+      t->res.queue_ms = ms(t->t_submit, t->t_start);
+      t->res.run_ms = ms(t->t_start, t->t_end);
+      t->res.latency_ms = ms(t->t_submit, t->t_end);
+      if (t->req.keep_dx) t->dx.swap(dx);
+      t->noise.clear();
+      // a step that did not converge leaves the instance (and its state) in
+      // place; other failures free it and are remembered, so the instance's
+      // queued requests complete with the same error; the last request
+      // forgets the instance
+      if (t->req.last || (rc != FSI_OK && rc != FSI_E_NOT_CONVERGED)) {
+        if (in->ctx) {
           fsi_destroy(in->ctx);
           in->ctx = nullptr;
+          resident -= in->bytes;
         }
-      }
-      fsi_solve_stats st{};
-      double rel = 0.0;
-      if (rc == FSI_OK) {
-        // the step runs on this worker's stream, whichever worker built the
-        // instance, so instances served by different workers overlap on the
-        // device (the ctx is idle here: its previous step has completed)
-        rc = fsi_set_stream(in->ctx, stream);
-        dxbuf.assign(t->req.keep_dx ? in->n : 0, 0.0);
-        if (rc == FSI_OK) rc = fsi_newton_step(in->ctx, t->req.keep_dx ? dxbuf.data() : nullptr, &rel, &st);
-      }
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        t->t_end = Clock::now();
-        t->res.status = rc;
-        t->res.iters = st.iters;
-        t->res.rel_step = rel;
-        t->res.rel_res = st.rel_res;
-        t->res.n = in->n;
-        t->res.queue_ms = ms(t->t_submit, t->t_start);
-        t->res.run_ms = ms(t->t_start, t->t_end);
-        t->res.latency_ms = ms(t->t_submit, t->t_end);
-        if (t->req.keep_dx) t->dx.swap(dxbuf);
-        t->noise.clear();
-        // a step that did not converge leaves the instance (and its state) in
-        // place; other failures free it and are remembered, so the instance's
-        // queued requests complete with the same error; the last request
-        // forgets the instance
-        if (t->req.last || (rc != FSI_OK && rc != FSI_E_NOT_CONVERGED)) {
-          if (in->ctx) {
-            fsi_destroy(in->ctx);
-            in->ctx = nullptr;
-            resident -= in->bytes;
-          }
-          if (t->req.last) {
-            inst.erase(t->req.instance);
-          } else {
-            in->failed = rc;
-            in->busy = false;
-          }
+        if (t->req.last) {
+          inst.erase(t->req.instance);
         } else {
+          in->failed = rc;
           in->busy = false;
         }
-        t->state = 2;
-        --running;
+      } else {
+        in->busy = false;
       }
-      cv.notify_all();
-      done_cv.notify_all();
+      t->state = 2;
+      --running;
+    }
+    cv.notify_all();
+    done_cv.notify_all();
+  }
+
+  void run_single(Ticket* t, cudaStream_t stream) {
+    Instance* in;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      in = &inst[t->req.instance];
+    }
+    int rc = FSI_OK;
+    if (in->failed) {
+      // an earlier step of this instance failed and freed it: complete the
+      // request at once with that step's error instead of rebuilding it
+      rc = in->failed;
+    } else if (!in->ctx) {
+      rc = build(t, in, stream);
+    }
+    fsi_solve_stats st{};
+    double rel = 0.0;
+    std::vector<double> dx;
+    if (rc == FSI_OK) {
+      // the step runs on this worker's stream, whichever worker built the
+      // instance, so instances served by different workers overlap on the
+      // device (the ctx is idle here: its previous step has completed)
+      rc = fsi_set_stream(in->ctx, stream);
+      dx.assign(t->req.keep_dx ? in->n : 0, 0.0);
+      if (rc == FSI_OK) rc = fsi_newton_step(in->ctx, t->req.keep_dx ? dx.data() : nullptr, &rel, &st);
+    }
+    finish(t, in, rc, rel, st, dx);
+  }
+
+  // steps of several resident instances: each assembles, the Schwarz blocks
+  // of all of them are factored by one launch (fsi_factor_schwarz_batch;
+  // bit-identical to factoring them one by one), then each solves and
+  // updates; on a factorisation error every instance factors alone, so the
+  // error is reported for the instance it belongs to
+  void run_batch(const std::vector<Ticket*>& batch, cudaStream_t stream) {
+    const size_t k = batch.size();
+    std::vector<Instance*> in(k);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (size_t i = 0; i < k; ++i) in[i] = &inst[batch[i]->req.instance];
+    }
+    std::vector<int> rc(k, FSI_OK);
+    std::vector<fsi_ctx*> ok;
+    for (size_t i = 0; i < k; ++i) {
+      rc[i] = fsi_set_stream(in[i]->ctx, stream);
+      if (rc[i] == FSI_OK) rc[i] = fsi_assemble_jacobian(in[i]->ctx, nullptr);
+      if (rc[i] == FSI_OK) ok.push_back(in[i]->ctx);
+    }
+    if (!ok.empty() && fsi_factor_schwarz_batch(ok.data(), (int)ok.size()) != FSI_OK)
+      for (size_t i = 0; i < k; ++i)
+        if (rc[i] == FSI_OK) rc[i] = fsi_factor_schwarz(in[i]->ctx);
+    for (size_t i = 0; i < k; ++i) {
+      fsi_solve_stats st{};
+      double rel = 0.0;
+      std::vector<double> dx(batch[i]->req.keep_dx ? in[i]->n : 0, 0.0);
+      if (rc[i] == FSI_OK)
+        rc[i] = fsi_newton_solve_update(in[i]->ctx, batch[i]->req.keep_dx ? dx.data() : nullptr, &rel, &st);
+      finish(batch[i], in[i], rc[i], rel, st, dx);
+    }
+  }
+
+  void work(int slot) {
+    cudaStream_t stream = streams[slot];
+    while (true) {
+      std::vector<Ticket*> batch;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        Ticket* t = nullptr;
+        cv.wait(lk, [&] { return stop || (t = pick()) != nullptr; });
+        if (!t) break;
+        claim(t);
+        batch.push_back(t);
+        auto f = inst.find(t->req.instance);
+        if (max_batch > 1 && f != inst.end() && f->second.ctx && f->second.batchable) {
+          // other resident batchable instances with a runnable request join
+          while ((int)batch.size() < max_batch) {
+            Ticket* u = pick(true);
+            if (!u) break;
+            claim(u);
+            batch.push_back(u);
+          }
+        }
+      }
+      if (batch.size() == 1) run_single(batch[0], stream);
+      else run_batch(batch, stream);
     }
   }
 };
@@ -246,6 +316,13 @@ int fsi_serve_drain(fsi_server* s) {
   if (!s) return FSI_E_INVALID;
   std::unique_lock<std::mutex> lk(s->mu);
   s->done_cv.wait(lk, [&] { return s->queue.empty() && s->running == 0; });
+  return FSI_OK;
+}
+
+int fsi_server_set_batching(fsi_server* s, int max_batch) {
+  if (!s || max_batch < 1 || max_batch > 64) return FSI_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->max_batch = max_batch;
   return FSI_OK;
 }
 

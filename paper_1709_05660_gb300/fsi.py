@@ -35,7 +35,8 @@ SYMBOLS = (
     "fsi_kernel_stats", "fsi_server_create", "fsi_serve_submit", "fsi_serve_poll", "fsi_serve_drain",
     "fsi_server_resident_bytes", "fsi_server_destroy", "fsi_coarse_solve_static", "fsi_set_launch_params",
     "fsi_get_launch_params", "fsi_time_level_kernels", "fsi_set_stream", "fsi_import_csr",
-    "fsi_set_tc_wait_limit", "fsi_fmg_newton",
+    "fsi_set_tc_wait_limit", "fsi_fmg_newton", "fsi_newton_solve_update", "fsi_factor_schwarz_batch",
+    "fsi_server_set_batching",
 )
 
 # kernel classes for fsi_kernel_stats
@@ -73,6 +74,7 @@ class SolveStats(ctypes.Structure):
         ("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_res", ctypes.c_double),
         ("rho", ctypes.c_double), ("t_assemble_ms", ctypes.c_double), ("t_factor_ms", ctypes.c_double),
         ("t_solve_ms", ctypes.c_double), ("prec_rel_res", ctypes.c_double),
+        ("bytes_assemble", ctypes.c_double), ("bytes_factor", ctypes.c_double), ("bytes_solve", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -149,6 +151,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fsi_apply_vcycle.argtypes = [vp, vp, vp]
     lib.fsi_coarse_solve_static.argtypes = [vp, vp, vp]
     lib.fsi_set_stream.argtypes = [vp, vp]
+    lib.fsi_newton_solve_update.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveStats)]
+    lib.fsi_factor_schwarz_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.fsi_server_set_batching.argtypes = [vp, ctypes.c_int]
     lib.fsi_fmg_newton.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOptsC), vp, ctypes.c_double,
                                    ctypes.c_int, vp, ctypes.POINTER(FmgStats)]
     lib.fsi_import_csr.argtypes = [vp, ctypes.c_int, vp]
@@ -362,6 +367,13 @@ class FSI:
     def apply_vcycle(self, b, z):
         self._check(self.lib.fsi_apply_vcycle(self.h, _ptr(b), _ptr(z)))
 
+    def newton_solve_update(self, dx_out=None):
+        """Solve and update with the current factors (fsi_newton_solve_update)."""
+        rel = ctypes.c_double()
+        st = SolveStats()
+        self._check(self.lib.fsi_newton_solve_update(self.h, _ptr(dx_out), ctypes.byref(rel), ctypes.byref(st)))
+        return rel.value, st
+
     def import_csr(self, level: int, val):
         """Replaces J_level's values (canonical CSR order of export_csr)."""
         val = np.ascontiguousarray(val, dtype=np.float64)
@@ -426,6 +438,15 @@ class FSI:
         return a.value, b.value
 
 
+def factor_batch(instances) -> None:
+    """fsi_factor_schwarz_batch over FSI instances bound to one stream."""
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(instances))(*[s.h.value if hasattr(s.h, "value") else s.h for s in instances])
+    rc = lib.fsi_factor_schwarz_batch(arr, len(instances))
+    if rc != FSI_OK:
+        raise FSIError(rc, lib.fsi_last_error(instances[0].h).decode())
+
+
 def fmg_newton(prob: Problem, opts: SolverOpts, y_out, stream: Optional[int] = None, tol: float = 1e-8,
                max_steps: int = 20) -> dict:
     """Nested-iteration (full multigrid) Newton for the steady problem
@@ -479,6 +500,13 @@ class Server:
         if rc != FSI_OK:
             raise FSIError(rc, "fsi_serve_poll failed")
         return res.as_dict()
+
+    def set_batching(self, max_batch: int):
+        """Requests of up to max_batch resident mixed-precision instances share
+        one Schwarz factorisation launch (1: off)."""
+        rc = self.lib.fsi_server_set_batching(self.h, int(max_batch))
+        if rc != FSI_OK:
+            raise FSIError(rc, "fsi_server_set_batching rejected the value")
 
     def drain(self):
         self.lib.fsi_serve_drain(self.h)

@@ -33,7 +33,7 @@ def test_check_entry_ranges():
         with pytest.raises(ValueError):
             autotune.check_entry({"levels": {"1": bad}}, 3)
     with pytest.raises(ValueError):
-        autotune.check_entry({"levels": {}, "gj_panel": 24}, 3)
+        autotune.check_entry({"levels": {}, "gj_panel": 20}, 3)
 
 
 def test_lookup_by_gpu_and_signature():

@@ -187,3 +187,48 @@ def test_failed_instance_completes_its_queued_requests():
     assert srv.poll(good)["status"] == 0
     assert srv.resident_bytes() == 0
     srv.close()
+
+
+def test_factor_batch_is_bitwise_the_individual_factorisation():
+    """fsi_factor_schwarz_batch over instances of different shapes (2D at 3
+    and 4 levels, whose blocks take the 32-column panel, and 3D at 2 levels,
+    whose 784-unknown blocks take the 24-column one): the Newton corrections
+    after the batched factorisation equal, bit for bit, those after each
+    instance's own fsi_factor_schwarz."""
+    fsi = _fsi()
+    torch.cuda.set_device(0)
+    s0 = torch.cuda.Stream()
+    specs = [(Problem(levels=3, mu_s=1e5, U=0.3), SolverOpts(tile=(2, 2), precision=1)),
+             (Problem(levels=4, mu_s=3e4, U=0.15), SolverOpts(tile=(2, 2), precision=1)),
+             (problem_3d(levels=2, mu_s=5e5, U=0.2), SolverOpts(tile=(2, 2, 2), precision=1))]
+    inst, y0 = [], []
+    for k, (p, o) in enumerate(specs):
+        s = fsi.FSI(p, o, stream=s0.cuda_stream)
+        n = int(s.N[-1])
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        s.initial_state(torch.tensor(noise(n, 60 + k), dtype=torch.float64, device="cuda"), y)
+        inst.append(s)
+        y0.append(y)
+
+    def run(batched):
+        out = []
+        for s, y in zip(inst, y0):
+            s.set_state(y)
+            s.assemble()
+        if batched:
+            fsi.factor_batch(inst)
+        else:
+            for s in inst:
+                s.factor()
+        for s, y in zip(inst, y0):
+            dx = torch.empty_like(y)
+            s.newton_solve_update(dx)
+            out.append(dx.cpu().numpy())
+        return out
+
+    ref = run(False)
+    got = run(True)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+    for s in inst:
+        s.close()
