@@ -96,6 +96,10 @@ typedef struct {
                           FSI_GMRES_LEFT (1): left-preconditioned GMRES, the paper's setting (Sec. 4.1) */
   int gs_passes;       /* classical Gram-Schmidt passes per Arnoldi step: 1 or 2 (0: 2 for FGMRES,
                           1 for left GMRES, the paper's unmodified classical Gram-Schmidt) */
+  int local_solver;    /* Schwarz blocks (Sec. 3.3, 4.1): 0 = exact LU of every block; 1 = ILU(0) of
+                          the fluid blocks (pattern: their node / element block pairs and the diagonal;
+                          blocks of at most 1024 unknowns) and exact LU of the solid ones; mixed
+                          precision only */
 } fsi_solver_opts;
 enum { FSI_FGMRES = 0, FSI_GMRES_LEFT = 1 };
 
@@ -352,10 +356,11 @@ enum {
   FSI_K_PATCH_FACTOR = 3,  /* Schwarz block gather + Gauss-Jordan inversion */
   FSI_K_COARSE_FACTOR = 4, /* coarse dense gather + cooperative Gauss-Jordan */
   FSI_K_PATCH_APPLY = 5,   /* restricted Schwarz update (owned inverse rows x residual) */
-  FSI_K_SPMV = 6,          /* block-sparse residual / product */
+  FSI_K_SPMV = 6,          /* block-sparse residual of the V-cycle (FP32 on the mixed path) */
   FSI_K_TRANSFER = 7,      /* restriction / prolongation / coarse apply */
   FSI_K_KRYLOV = 8,        /* dots, Gram-Schmidt updates, norms, combinations */
-  FSI_K_COUNT = 9
+  FSI_K_OPERATOR = 9,      /* the Krylov method's FP64 product J v (FP64 pipe: 16 FMAs per 4 x 4 block) */
+  FSI_K_COUNT = 10
 };
 int fsi_set_profiling(fsi_ctx* ctx, int on);
 int fsi_kernel_stats(fsi_ctx* ctx, int kind, double* device_ms, int64_t* launches, double* alg_bytes,

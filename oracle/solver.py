@@ -184,19 +184,65 @@ class LevelOps:
     coarse_lu: object = None
 
 
-def factor_patches(ops: LevelOps) -> None:
+def ilu0(B: np.ndarray, mask: np.ndarray):
+    """Incomplete LU factorisation with zero fill (Sec. 3.3, 4.1: the
+    approximate local solver of the fluid subdomains): Gaussian elimination
+    without pivoting in which every entry outside the sparsity pattern
+    `mask` (which must hold the diagonal) stays zero.  Row by row (i), each
+    earlier row k of the pattern first scales the entry (i, k) by 1 / u_kk,
+    then subtracts l_ik u_kj from the pattern entries (i, j), j > k.
+    Returns (L, U): L unit lower triangular, U upper triangular, both
+    supported on the pattern, with (L U)_ij = B_ij on the pattern."""
+    A = np.array(B, dtype=np.float64)
+    n = A.shape[0]
+    assert np.all(np.diag(mask))
+    A[~mask] = 0.0
+    for i in range(1, n):
+        for k in np.nonzero(mask[i, :i])[0]:
+            A[i, k] /= A[k, k]
+            A[i, k + 1:] -= A[i, k] * A[k, k + 1:] * mask[i, k + 1:]
+    L = np.tril(A, -1) + np.eye(n)
+    U = np.triu(A)
+    return L, U
+
+
+def patch_pattern(ops: LevelOps, pt) -> np.ndarray:
+    """Sparsity pattern of a Schwarz block: the FE pattern of the level
+    (Sec. 3.1 blocks) restricted to R^delta_k, with the diagonal added (the
+    element pressure rows have no pressure-pressure entries)."""
+    P = fem.fe_pattern(ops.lev)
+    Pk = P[pt.dofs][:, pt.dofs]
+    mask = np.zeros((len(pt.dofs), len(pt.dofs)), dtype=bool)
+    coo = Pk.tocoo()
+    mask[coo.row, coo.col] = True
+    np.fill_diagonal(mask, True)
+    return mask
+
+
+def factor_patches(ops: LevelOps, fluid_ilu: bool = False) -> None:
+    """Local solvers of the Schwarz blocks: partial-pivot LU of every block,
+    or (fluid_ilu) ILU(0) of the fluid blocks and LU of the solid ones, the
+    setting of Sec. 3.3 and 4.1."""
     Jd = ops.J.tocsr()
     ops.lu = []
     for pt in ops.patches:
         B = Jd[pt.dofs][:, pt.dofs].toarray()
-        ops.lu.append(sla.lu_factor(B, check_finite=True))
+        if fluid_ilu and not pt.solid:
+            ops.lu.append(("ilu",) + ilu0(B, patch_pattern(ops, pt)))
+        else:
+            ops.lu.append(sla.lu_factor(B, check_finite=True))
 
 
 def ras_apply(ops: LevelOps, r: np.ndarray) -> np.ndarray:
-    """sum_k (R^0_k)^T B_k^{-1} R^delta_k r  (restricted additive Schwarz)."""
+    """sum_k (R^0_k)^T B_k^{-1} R^delta_k r  (restricted additive Schwarz);
+    an ILU(0) block applies U^{-1} L^{-1} in place of B_k^{-1}."""
     out = np.zeros_like(r)
     for pt, lu in zip(ops.patches, ops.lu):
-        z = sla.lu_solve(lu, r[pt.dofs])
+        if isinstance(lu, tuple) and lu and isinstance(lu[0], str):
+            _, L, U = lu
+            z = sla.solve_triangular(U, sla.solve_triangular(L, r[pt.dofs], lower=True, unit_diagonal=True))
+        else:
+            z = sla.lu_solve(lu, r[pt.dofs])
         out[pt.dofs[pt.owned]] += z[pt.owned]
     return out
 
@@ -452,11 +498,12 @@ class Oracle:
         return r, J
 
     def factor(self):
+        fluid_ilu = getattr(self.opts, "local_solver", 0) == 1
         for l, op in enumerate(self.ops):
             if l == 0:
                 op.coarse_lu = sla.lu_factor(op.J.toarray())
             else:
-                factor_patches(op)
+                factor_patches(op, fluid_ilu)
 
     def precond(self, v: np.ndarray) -> np.ndarray:
         return vcycle(self.ops, len(self.ops) - 1, v, self.opts)

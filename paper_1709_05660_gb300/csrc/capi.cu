@@ -252,6 +252,18 @@ void build_device(Ctx& c) {
         D.inv = dalloc<double>(c, (size_t)H.inv_total);
       }
       max_dense = std::max(max_dense, H.dense_total);
+      if (c.opts.local_solver == 1) {
+        // fluid blocks (material of the block's elements) up to the ILU size limit
+        std::vector<int32_t> lu, ilu;
+        for (int p = 0; p < H.n_patches; ++p) {
+          const bool solid = H.elem_solid[H.p_elems[H.p_elem_off[p]]] != 0;
+          (!solid && H.p_n[p] <= kIluMaxRows ? ilu : lu).push_back(p);
+        }
+        D.n_lu = (int)lu.size();
+        D.n_ilu = (int)ilu.size();
+        D.sel_lu = upload(c, lu);
+        D.sel_ilu = upload(c, ilu);
+      }
       for (int p = 0; p < H.n_patches; ++p) {
         const double n = H.p_n[p], no = H.p_nown[p];
         // inverse rows, residual gather + index + row scale, owned index + column scale + x read/write
@@ -588,17 +600,32 @@ bool gather_mixed(Ctx& c, GjLevels& lv, int& first, int& max_n) {
     launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
                                  D.p_padpos, D.val, c.B, ws + off, D.p_idx_off, D.dr32, D.dc32, c.stream);
     counted(c);
-    if (D.n_patches > 0 && lv.nlev < kGjMaxLevels) {
+    const bool ilu = c.opts.local_solver == 1;
+    const int nsel = ilu ? D.n_lu : D.n_patches;
+    if (ilu) {   // the fluid blocks: ILU(0) in place in the workspace
+      launch_patch_ilu0(D.n_ilu, D.sel_ilu, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, c.B, ws + off, c.status,
+                        c.stream);
+      if (D.n_ilu > 0) counted(c);
+    }
+    if (nsel > 0 && lv.nlev < kGjMaxLevels) {
       lv.l[lv.nlev++] = GjLevel{D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own, D.p_inv_off, ws + off,
-                                D.inv32, c.status, first};
-      first += D.n_patches;
+                                D.inv32, c.status, ilu ? D.sel_lu : nullptr, first};
+      first += nsel;
       max_n = std::max(max_n, D.max_n);
-    } else {
+    } else if (nsel > 0 || !ilu) {
       ok = false;
     }
     off += D.dense_total;
   }
   return ok;
+}
+
+// FP32 workspace region of level l (the mixed path keeps every level's
+// gathered blocks, which the ILU(0) blocks are applied from)
+float* level_ws(Ctx& c, int l) {
+  int64_t off = 0;
+  for (int k = 1; k < l; ++k) off += c.dl[k].dense_total;
+  return reinterpret_cast<float*>(c.dense_ws) + off;
 }
 
 void schwarz_factor(Ctx& c) {
@@ -625,8 +652,10 @@ void schwarz_factor(Ctx& c) {
     }
     Prof pr(c, FSI_K_PATCH_FACTOR, by, fl, L);
     const bool all = gather_mixed(c, lv, first, max_n);
-    if (all && launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream, c.gj_panel)) {
-      counted(c);
+    if (all && (lv.nlev == 0 || launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream, c.gj_panel))) {
+      if (lv.nlev > 0) counted(c);
+    } else if (c.opts.local_solver == 1) {
+      throw ApiError(FSI_E_INVALID, "ILU(0) fluid blocks: the exact blocks do not fit the tensor-core factorisation");
     } else {
       for (int l = 1; l < L; ++l) {   // blocks too large for the tensor-core kernel: level by level
         DevLevel& D = c.dl[l];
@@ -724,9 +753,9 @@ void factor(Ctx& c) {
 // ---------------------------------------------------------------------------
 // multigrid V-cycle (Sec. 3, 3.3): internal vectors of level l
 // ---------------------------------------------------------------------------
-void spmv(Ctx& c, int l, const double* x, const double* b, double* y) {
+void spmv(Ctx& c, int l, const double* x, const double* b, double* y, int kind = FSI_K_SPMV) {
   DevLevel& D = c.dl[l];
-  Prof pr(c, FSI_K_SPMV, D.spmv_bytes - (b ? 0.0 : D.Ni * 8.0), D.spmv_flops);
+  Prof pr(c, kind, D.spmv_bytes - (b ? 0.0 : D.Ni * 8.0), D.spmv_flops);
   launch_bsr_residual(c.B, D.nb, D.rowptr, D.col, D.val, x, b, y, c.stream);
   counted(c);
 }
@@ -784,6 +813,16 @@ template <> struct VC<float> {
   static void apply(Ctx& c, int l, const float* r, float* x) {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes32, D.apply_flops);
+    if (c.opts.local_solver == 1) {   // exact inverses of the solid blocks, ILU(0) solves of the fluid ones
+      launch_patch_apply_t<float>(D.n_lu, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off,
+                                  D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32, c.sm_count,
+                                  D.apply_slices, D.apply_groups, c.stream, D.sel_lu);
+      launch_patch_apply_ilu(D.n_ilu, D.sel_ilu, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off, D.p_own,
+                             D.p_dense_off, D.p_gmap_off, D.p_gmap, c.B, level_ws(c, l), r, x, c.opts.omega,
+                             D.dr32, D.dc32, c.stream);
+      counted(c, (D.n_lu > 0) + (D.n_ilu > 0));
+      return;
+    }
     launch_patch_apply_t<float>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
                                 D.p_own_off, D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32,
                                 c.sm_count, D.apply_slices, D.apply_groups, c.stream);
@@ -1018,7 +1057,7 @@ void gmres_left(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
     int k = 0;
     for (int j = 0; j < m; ++j) {
       const double* vj = c.V + (size_t)j * n;
-      spmv(c, L - 1, vj, nullptr, c.tmp);     // t = J v_j (FP64)
+      spmv(c, L - 1, vj, nullptr, c.tmp, FSI_K_OPERATOR);     // t = J v_j (FP64)
       precondition64(c, c.tmp, c.w);          // w = P^{-1} t
       double hn = 0.0, wn0 = 0.0;
       orthonormalize(c, j, passes, hcol.data(), &hn, &wn0);
@@ -1111,14 +1150,14 @@ void fgmres(Ctx& c, const double* b, double* x, fsi_solve_stats* st) {
         // A z_j in FP64: z_j widened once, not once per block that reads it
         // (each widening is an FP64-pipe instruction, about 80 per entry
         // inside the block sparse product)
-        Prof pr(c, FSI_K_SPMV, F.spmv_bytes + n * 4.0, F.spmv_flops, 2);   // no b; + widening
+        Prof pr(c, FSI_K_OPERATOR, F.spmv_bytes + n * 4.0, F.spmv_flops, 2);   // no b; + widening
         launch_to_f64(n, zj, c.zd, c.stream);
         launch_bsr_residual(c.B, F.nb, F.rowptr, F.col, F.val, c.zd, nullptr, c.w, c.stream);
         counted(c, 2);
       } else {
         double* zj = c.Z + (size_t)j * n;
         precondition(c, vj, zj, nullptr);
-        spmv(c, L - 1, zj, nullptr, c.w);
+        spmv(c, L - 1, zj, nullptr, c.w, FSI_K_OPERATOR);
       }
       // CGS (two passes by default): h = V^T w, w -= V h per pass, v_{j+1} = w / ||w||
       double hn = 0.0, wn0 = 0.0;
@@ -1285,6 +1324,10 @@ static void plan(fsi_ctx* c, const fsi_problem_desc* desc, const fsi_solver_opts
     throw ApiError(FSI_E_INVALID, "bad solver options");
   if ((opts->krylov != FSI_FGMRES && opts->krylov != FSI_GMRES_LEFT) || opts->gs_passes < 0 || opts->gs_passes > 2)
     throw ApiError(FSI_E_INVALID, "bad Krylov options (krylov 0 or 1, gs_passes 0..2)");
+  if (opts->local_solver != 0 && opts->local_solver != 1)
+    throw ApiError(FSI_E_INVALID, "local_solver must be 0 (LU) or 1 (ILU(0) for fluid blocks)");
+  if (opts->local_solver == 1 && opts->precision != FSI_MIXED)
+    throw ApiError(FSI_E_INVALID, "ILU(0) fluid blocks are built on the mixed-precision path");
   std::string err;
   if (!build_host_hierarchy(*desc, *opts, c->hl, err)) throw ApiError(FSI_E_INVALID, err);
   c->dim = desc->dim;
@@ -1610,7 +1653,8 @@ int fsi_factor_schwarz_batch(fsi_ctx* const* ctxs, int n) {
     // instances grouped by the tensor-core variant each would use alone, so
     // every block is factored exactly as in its own fsi_factor_schwarz
     std::vector<int> variant(n);
-    for (int i = 0; i < n; ++i) variant[i] = gj_tc_variant(max_block(*ctxs[i]), ctxs[i]->gj_panel);
+    for (int i = 0; i < n; ++i)
+      variant[i] = ctxs[i]->opts.local_solver == 1 ? 0 : gj_tc_variant(max_block(*ctxs[i]), ctxs[i]->gj_panel);
     std::vector<bool> done(n, false);
     for (int i = 0; i < n; ++i) {
       if (done[i]) continue;

@@ -109,6 +109,10 @@ struct DevLevel {
   double* S_val = nullptr;
   // patches
   int n_patches = 0, max_n = 0, max_nown = 0;
+  // local solvers (fsi_solver_opts.local_solver = 1): blocks with an exact
+  // inverse (solid, or too large for ILU) and ILU(0) blocks (fluid)
+  int32_t *sel_lu = nullptr, *sel_ilu = nullptr;
+  int n_lu = 0, n_ilu = 0;
   // launch parameters (0 = built-in choice; set by fsi_set_launch_params)
   int apply_slices = 0, apply_groups = 0, spmv_sub = 0;
   int32_t *p_n = nullptr, *p_nown = nullptr;

@@ -196,7 +196,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         if (kind == 1) v *= sx;
         if (kind == 2) v *= sy;
       }
-      Fv[q * kNFV + f] = v;
+      Fv[q * NFV + f] = v;
     }
   }
   __syncthreads();
@@ -207,7 +207,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
 #pragma unroll 1
     for (int it = j; it < kQ * kNF; it += kNdofe) {
       const int q = it / kNF, f = it % kNF;
-      const double* fv = Fv + q * kNFV;
+      const double* fv = Fv + q * NFV;
       double* dout = Dd + (q * kNF + f) * kNO;
       if (!TRANS && f < 2) {   // d itself enters only the BDF terms
 #pragma unroll

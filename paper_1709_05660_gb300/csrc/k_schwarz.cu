@@ -635,8 +635,8 @@ bool try_gj_f32(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, co
 // Tiles are 128 rows x TN columns.  Tensor memory: the two accumulators in
 // columns [0, 2 TN), the A parts of row tile t at 2 TN + 2 W t.  The panel
 // width W is what the 512 columns leave room for: W = 32 with TN = 128 up to
-// n = 512, W = 24 with TN = 64 (narrower accumulators, wider panel: a third
-// fewer passes over M) or W = 16 with TN = 128 up to n = 1024.  Requires
+// n = 512, W = 16 with TN = 128 or W = 24 with TN = 64 (a third fewer passes
+// over M, but half the loads in flight per tile) up to n = 1024.  Requires
 // n % 4 == 0.  The waits on the tensor core are bounded; on time-out the
 // block records ST_TIMEOUT, stops issuing work and releases its tensor memory.
 // ---------------------------------------------------------------------------
@@ -691,7 +691,7 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
   int lvl = 0;
   while (lvl + 1 < lv.nlev && (int)blockIdx.x >= lv.l[lvl + 1].first) ++lvl;
   const GjLevel& L = lv.l[lvl];
-  const int p = (int)blockIdx.x - L.first;
+  const int p = L.sel ? L.sel[(int)blockIdx.x - L.first] : (int)blockIdx.x - L.first;
   const int n = L.p_n[p];
   float* M = L.dense + L.dense_off[p];
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
@@ -996,13 +996,17 @@ void run_gj_tc(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cuda
   k_patch_gj_tc<W, TN><<<nblocks, gj_tc_threads<W, TN>(), smem, st>>>(lv, status, max_n);
 }
 
-// the widest panel that fits, unless a narrower one that fits was asked for
+// 32-column panels where they fit (n <= 512), else 16-column ones on
+// 128-column tiles; the 24-column panel on 64-column tiles only when asked
+// for: measured on GB300 it is slower (146 against 132 ms for the 6-level
+// channel's blocks of 784 unknowns), as the narrower tiles halve the loads
+// in flight of the tile epilogue that bounds this kernel
 int gj_tc_variant(int max_n, int panel) {
   if (panel == 16 && fits_gj_tc<16, 128>(max_n)) return 16;
   if (panel == 24 && fits_gj_tc<24, 64>(max_n)) return 24;
   if (fits_gj_tc<32, 128>(max_n)) return 32;
-  if (fits_gj_tc<24, 64>(max_n)) return 24;
   if (fits_gj_tc<16, 128>(max_n)) return 16;
+  if (fits_gj_tc<24, 64>(max_n)) return 24;
   return 0;
 }
 
@@ -1049,11 +1053,12 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
                 const int64_t* __restrict__ idx_off, const int32_t* __restrict__ idx,
                 const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
                 const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
-                T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc, int vstride) {
+                T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc, int vstride,
+                const int32_t* __restrict__ sel) {
   using VT = VecT<T>;
   constexpr int W = VT::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int p = blockIdx.x;
+  const int p = sel ? sel[blockIdx.x] : (int)blockIdx.x;
   const int n = p_n[p];
   T* rs = reinterpret_cast<T*>(smem_raw);              // n (padded to 4)
   const int32_t* id = idx + idx_off[p];
@@ -1159,7 +1164,7 @@ void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_n
     GjLevels lv{};
     lv.nlev = 1;
     lv.first_wait = kTcWaitIters;
-    lv.l[0] = GjLevel{p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, 0};
+    lv.l[0] = GjLevel{p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, nullptr, 0};
     if (launch_patch_gj_tc_levels(lv, np, max_n, status, st)) return;
     if (try_gj_f32<32>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
     if (try_gj_f32<16>(np, max_n, p_n, p_nown, dense_off, own_off, own, inv_off, d, o, status, st)) return;
@@ -1186,11 +1191,11 @@ k_patch_apply_rows(const int32_t* __restrict__ p_n, const int32_t* __restrict__ 
                    const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
                    const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
                    T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc, int S, int vps,
-                   int cg) {
+                   int cg, const int32_t* __restrict__ sel) {
   using VT = VecT<T>;
   constexpr int W = VT::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int p = blockIdx.x / S, s = blockIdx.x % S;
+  const int p = sel ? sel[blockIdx.x / S] : (int)(blockIdx.x / S), s = blockIdx.x % S;
   const int nown = p_nown[p];
   const int nvec = own_pad(nown) / W;
   const int v_lo = s * vps;
@@ -1271,7 +1276,8 @@ template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
-                          const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st) {
+                          const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st,
+                          const int32_t* sel) {
   if (np <= 0) return;
   const ApplyShape a = apply_shape(np, max_nown, VecT<T>::W, sm_count, want_slices, want_groups);
   if (a.kind == 1) {
@@ -1280,7 +1286,8 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
     if (smem > 48 * 1024)   // large blocks (e.g. 16 x 16 elements): opt in to more shared memory
       cudaFuncSetAttribute(k_patch_apply_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_patch_apply_rows<T><<<(unsigned)((int64_t)np * a.slices), threads, smem, st>>>(
-        p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x, T(omega), dr, dc, a.slices, a.vps, a.groups);
+        p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x, T(omega), dr, dc, a.slices, a.vps, a.groups,
+        sel);
     return;
   }
   constexpr int CG = 4;                       // column groups per block
@@ -1292,7 +1299,187 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_patch_apply_t<T, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_patch_apply_t<T, CG><<<np, threads, smem, st>>>(p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x,
-                                                    T(omega), dr, dc, vstride);
+                                                    T(omega), dr, dc, vstride, sel);
+}
+
+// ---------------------------------------------------------------------------
+// ILU(0) of the fluid Schwarz blocks (Sec. 3.3, 4.1: the approximate local
+// solver that suffices for fluid subdomains).  The pattern of a block is its
+// node / element block pairs (the block-sparse entries gathered from the
+// level's Jacobian) plus the diagonal; elimination without pivoting keeps
+// every entry outside it at zero.  The gathered block is equilibrated by
+// power-of-two row and column scales; ILU(0) commutes with them, so
+// B^{-1} r is applied as D_c U~^{-1} L~^{-1} D_r r as for the exact inverses.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kIluMaxNb = 256;   // block rows of a block: 1024 / 4 (2D) or ceil(1024 / 6) (3D)
+constexpr int kIluWords = kIluMaxNb / 32;
+
+// pattern bits of block pairs (local block row, local block column)
+__device__ __forceinline__ bool ilu_bit(const uint32_t* bm, int bi, int bj) {
+  return (bm[bi * kIluWords + (bj >> 5)] >> (bj & 31)) & 1u;
+}
+
+__device__ void ilu_mask(uint32_t* bm, int nb, int64_t g0, int64_t g1, const int32_t* __restrict__ gmap) {
+  for (int t = threadIdx.x; t < nb * kIluWords; t += blockDim.x) bm[t] = 0u;
+  __syncthreads();
+  for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const int lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
+    atomicOr(&bm[lr * kIluWords + (lc >> 5)], 1u << (lc & 31));
+  }
+  __syncthreads();
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256)
+k_patch_ilu0(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n, const int64_t* __restrict__ dense_off,
+             const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap, int B, float* __restrict__ dense,
+             int32_t* __restrict__ status) {
+  __shared__ uint32_t bm[kIluMaxNb * kIluWords];
+  __shared__ int16_t rb[kIluMaxNb], cb[kIluMaxNb];   // block rows / columns touching block bk
+  __shared__ int nrb, ncb, s_sing;
+  const int p = sel[blockIdx.x];
+  const int n = p_n[p], nb = (n + B - 1) / B;
+  float* D = dense + dense_off[p];
+  if (threadIdx.x == 0) s_sing = 0;
+  ilu_mask(bm, nb, gmap_off[p], gmap_off[p + 1], gmap);
+  for (int k = 0; k < n; ++k) {
+    const int bk = k / B;
+    if (k % B == 0) {
+      // candidate block rows (i > k) and columns (j > k): bk itself and the
+      // blocks coupled to it in the pattern
+      if (threadIdx.x == 0) {
+        int a = 0, c = 0;
+        rb[a++] = (int16_t)bk;
+        cb[c++] = (int16_t)bk;
+        for (int b = bk + 1; b < nb; ++b) {
+          if (ilu_bit(bm, b, bk)) rb[a++] = (int16_t)b;
+          if (ilu_bit(bm, bk, b)) cb[c++] = (int16_t)b;
+        }
+        nrb = a;
+        ncb = c;
+      }
+      __syncthreads();
+    }
+    const bool self = ilu_bit(bm, bk, bk);   // a full diagonal block (node block)
+    float* Dk = D + (int64_t)k * n;
+    float akk = Dk[k];
+    if (!(fabsf(akk) > 0.f) || !isfinite(akk)) {
+      if (threadIdx.x == 0) s_sing = 1;
+      akk = 1.f;
+    }
+    const float rk = 1.f / akk;
+    // l_ik = a_ik / u_kk
+    const int nr = nrb * B, nc = ncb * B;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const int bi = rb[t / B], i = bi * B + t % B;
+      if (i <= k || i >= n || (bi == bk && !self)) continue;
+      D[(int64_t)i * n + k] *= rk;
+    }
+    __syncthreads();
+    // a_ij -= l_ik u_kj on the pattern
+    for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) {
+      const int ri = t / nc, ci = t % nc;
+      const int bi = rb[ri / B], i = bi * B + ri % B;
+      const int bj = cb[ci / B], j = bj * B + ci % B;
+      if (i <= k || j <= k || i >= n || j >= n) continue;
+      if ((bi == bk || bj == bk) && !self) continue;
+      if (!(ilu_bit(bm, bi, bj) || i == j)) continue;
+      D[(int64_t)i * n + j] -= D[(int64_t)i * n + k] * Dk[j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
+}
+
+// One warp per block: y = D_r r, forward sweep with the unit lower factor and
+// backward sweep with the upper one, block row by block row (the lanes take
+// the off-diagonal blocks of the row, lane 0 the diagonal block), then the
+// owned rows: x += omega D_c y.
+__global__ void __launch_bounds__(32)
+k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n,
+                  const int32_t* __restrict__ p_nown, const int64_t* __restrict__ idx_off,
+                  const int32_t* __restrict__ idx, const int64_t* __restrict__ own_off,
+                  const int32_t* __restrict__ own, const int64_t* __restrict__ dense_off,
+                  const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap, int B,
+                  const float* __restrict__ dense, const float* __restrict__ r, float* __restrict__ x, float omega,
+                  const float* __restrict__ dr, const float* __restrict__ dc) {
+  __shared__ uint32_t bm[kIluMaxNb * kIluWords];
+  __shared__ float y[kIluMaxRows];
+  const int p = sel[blockIdx.x];
+  const int lane = threadIdx.x;
+  const int n = p_n[p], nb = (n + B - 1) / B;
+  const float* D = dense + dense_off[p];
+  const int32_t* id = idx + idx_off[p];
+  const float* Dr = dr + idx_off[p];
+  const float* Dc = dc + idx_off[p];
+  ilu_mask(bm, nb, gmap_off[p], gmap_off[p + 1], gmap);
+  for (int i = lane; i < n; i += 32) y[i] = id[i] >= 0 ? Dr[i] * r[id[i]] : 0.f;
+  __syncwarp();
+  for (int dir = 0; dir < 2; ++dir) {   // 0: L (forward), 1: U (backward)
+    for (int s = 0; s < nb; ++s) {
+      const int bi = dir == 0 ? s : nb - 1 - s;
+      float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const int lo = dir == 0 ? 0 : bi + 1, hi = dir == 0 ? bi : nb;
+      for (int bk = lo + lane; bk < hi; bk += 32) {
+        if (!ilu_bit(bm, bi, bk)) continue;
+        for (int rr = 0; rr < B; ++rr) {
+          const int i = bi * B + rr;
+          if (i >= n) break;
+          const float* Di = D + (int64_t)i * n + bk * B;
+          float a = 0.f;
+          for (int c = 0; c < B && bk * B + c < n; ++c) a += Di[c] * y[bk * B + c];
+          acc[rr] += a;
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 6; ++rr)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], o);
+      if (lane == 0) {
+        const bool self = ilu_bit(bm, bi, bi);
+        for (int q = 0; q < B; ++q) {
+          const int rr = dir == 0 ? q : B - 1 - q;
+          const int i = bi * B + rr;
+          if (i >= n) continue;
+          const float* Di = D + (int64_t)i * n + bi * B;
+          float v = y[i] - acc[rr];
+          if (self) {
+            if (dir == 0) {
+              for (int c = 0; c < rr; ++c) v -= Di[c] * y[bi * B + c];
+            } else {
+              for (int c = rr + 1; c < B && bi * B + c < n; ++c) v -= Di[c] * y[bi * B + c];
+            }
+          }
+          y[i] = dir == 0 ? v : v / Di[rr];
+        }
+      }
+      __syncwarp();
+    }
+  }
+  const int nown = p_nown[p];
+  const int32_t* ow = own + own_off[p];
+  for (int o = lane; o < nown; o += 32) {
+    const int row = ow[o];
+    if (id[row] >= 0) x[id[row]] += omega * (Dc[row] * y[row]);
+  }
+}
+
+void launch_patch_ilu0(int nsel, const int32_t* sel, const int32_t* p_n, const int64_t* dense_off,
+                       const int64_t* gmap_off, const int32_t* gmap, int B, float* dense, int32_t* status,
+                       cudaStream_t st) {
+  if (nsel <= 0) return;
+  k_patch_ilu0<<<nsel, 256, 0, st>>>(sel, p_n, dense_off, gmap_off, gmap, B, dense, status);
+}
+
+void launch_patch_apply_ilu(int nsel, const int32_t* sel, const int32_t* p_n, const int32_t* p_nown,
+                            const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
+                            const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap, int B,
+                            const float* dense, const float* r, float* x, double omega, const float* dr,
+                            const float* dc, cudaStream_t st) {
+  if (nsel <= 0) return;
+  k_patch_apply_ilu<<<nsel, 32, 0, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off, gmap, B,
+                                         dense, r, x, (float)omega, dr, dc);
 }
 
 #define FSI_INST(T)                                                                                              \
@@ -1304,7 +1491,7 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
   template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \
                                         const int32_t*, const int64_t*, const int32_t*, const int64_t*,        \
                                         const T*, const T*, T*, double, const T*, const T*, int, int, int,     \
-                                        cudaStream_t);
+                                        cudaStream_t, const int32_t*);
 FSI_INST(double)
 FSI_INST(float)
 #undef FSI_INST

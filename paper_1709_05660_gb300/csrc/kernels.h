@@ -77,6 +77,7 @@ struct GjLevel {
   float* dense;
   float* invT;
   int32_t* status;   // status flags of the instance the level belongs to
+  const int32_t* sel; // blocks of the level to factor (nullptr: all of them)
   int first;
 };
 struct GjLevels {
@@ -104,11 +105,26 @@ template <typename T>
 void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
                        const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
                        int32_t* status, bool n_mult4, cudaStream_t st);
+// sel: the np blocks to apply (nullptr: blocks 0 .. np - 1)
 template <typename T>
 void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
-                          const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st);
+                          const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st,
+                          const int32_t* sel = nullptr);
+// ILU(0) of the fluid Schwarz blocks listed in sel (Sec. 3.3, 4.1), in place
+// on their gathered, equilibrated dense blocks; blocks of at most
+// kIluMaxRows unknowns
+constexpr int kIluMaxRows = 1024;
+void launch_patch_ilu0(int nsel, const int32_t* sel, const int32_t* p_n, const int64_t* dense_off,
+                       const int64_t* gmap_off, const int32_t* gmap, int B, float* dense, int32_t* status,
+                       cudaStream_t st);
+// x[own] += omega (R^0)^T U^{-1} L^{-1} R^delta r for the ILU(0) blocks in sel
+void launch_patch_apply_ilu(int nsel, const int32_t* sel, const int32_t* p_n, const int32_t* p_nown,
+                            const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
+                            const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap, int B,
+                            const float* dense, const float* r, float* x, double omega, const float* dr,
+                            const float* dc, cudaStream_t st);
 // Launch shape of one level's Schwarz apply: kind 0 = one block per patch
 // (k_patch_apply_t), kind 1 = `slices` row slices per patch of `vps` owned-row
 // vectors, `groups` column groups per block (k_patch_apply_rows).

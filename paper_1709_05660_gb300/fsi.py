@@ -41,7 +41,7 @@ SYMBOLS = (
 
 # kernel classes for fsi_kernel_stats
 KERNEL_CLASSES = ("assemble", "galerkin", "scatter", "patch_factor", "coarse_factor", "patch_apply",
-                  "spmv", "transfer", "krylov")
+                  "spmv", "transfer", "krylov", "operator")
 
 
 class ProblemDesc(ctypes.Structure):
@@ -65,7 +65,7 @@ class SolverOptsC(ctypes.Structure):
         ("tile", ctypes.c_int * 3), ("n_pre", ctypes.c_int), ("n_post", ctypes.c_int),
         ("omega", ctypes.c_double), ("restart", ctypes.c_int), ("rtol", ctypes.c_double),
         ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
-        ("gs_passes", ctypes.c_int),
+        ("gs_passes", ctypes.c_int), ("local_solver", ctypes.c_int),
     ]
 
 
@@ -206,7 +206,7 @@ def make_opts(o: SolverOpts) -> SolverOptsC:
         c.tile[a] = t
     c.n_pre, c.n_post, c.omega = o.n_pre, o.n_post, o.omega
     c.restart, c.rtol, c.max_iters, c.precision = o.restart, o.rtol, o.max_iters, o.precision
-    c.krylov, c.gs_passes = o.krylov, o.gs_passes
+    c.krylov, c.gs_passes, c.local_solver = o.krylov, o.gs_passes, o.local_solver
     return c
 
 

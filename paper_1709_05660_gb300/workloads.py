@@ -65,6 +65,7 @@ class SolverOpts:
     precision: int = 0                   # 0 = FP64, 1 = mixed
     krylov: int = 0                      # 0 = FGMRES (right, true residual), 1 = GMRES (left, preconditioned residual)
     gs_passes: int = 0                   # Gram-Schmidt passes (0: 2 for FGMRES, 1 for left GMRES)
+    local_solver: int = 0                # Schwarz blocks: 0 = LU for all, 1 = ILU(0) for fluid blocks, LU for solid
 
 
 def problem_3d(levels: int = 3, **kw) -> Problem:

@@ -343,3 +343,74 @@ def test_fmg_reaches_the_steady_state_of_plain_newton():
     assert len(hists[-1]) <= len(hist_pl)
     r, _ = orc.assemble(y_fmg)
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(orc.assemble(initial_state(prob, orc.fine, np.zeros(orc.fine.N)))[0])
+
+
+# ----------------------------------------------------------------------------
+# ILU(0) local solver of the fluid blocks (Sec. 3.3, 4.1)
+# ----------------------------------------------------------------------------
+
+def test_ilu0_defining_property_on_a_block_pattern():
+    """On a random block-sparse pattern (with the diagonal): L is unit lower
+    and U upper triangular, both zero outside the pattern, and L U equals B at
+    every pattern entry (the entries outside hold the dropped fill)."""
+    from oracle.solver import ilu0
+    rng = np.random.default_rng(5)
+    nb, b = 12, 4
+    bm = rng.uniform(size=(nb, nb)) < 0.35
+    bm |= bm.T
+    np.fill_diagonal(bm, True)
+    mask = np.kron(bm, np.ones((b, b), dtype=bool))
+    n = nb * b
+    B = rng.standard_normal((n, n)) * mask + np.eye(n) * 8.0
+    L, U = ilu0(B, mask)
+    assert np.allclose(np.triu(L, 1), 0.0) and np.allclose(np.diag(L), 1.0)
+    assert np.allclose(np.tril(U, -1), 0.0)
+    assert np.all(L[~mask] == 0.0) and np.all(U[~mask] == 0.0)
+    LU = L @ U
+    assert np.max(np.abs(LU[mask] - B[mask])) <= 1e-12 * np.max(np.abs(B))
+    assert np.max(np.abs(LU[~mask])) > 1e-6          # fill was dropped somewhere
+
+
+def test_ilu0_special_cases():
+    """A full pattern gives the LU factorisation without pivoting (diagonally
+    dominant, so partial pivoting keeps the diagonal: scipy's LU with P = I);
+    a tridiagonal pattern has no fill, so ILU(0) solves exactly."""
+    from oracle.solver import ilu0
+    rng = np.random.default_rng(6)
+    n = 20
+    B = rng.standard_normal((n, n)) + np.eye(n) * 3 * n
+    L, U = ilu0(B, np.ones((n, n), dtype=bool))
+    P, L2, U2 = sla.lu(B)
+    assert np.array_equal(P, np.eye(n))
+    assert np.allclose(L, L2, atol=1e-13) and np.allclose(U, U2, rtol=1e-12, atol=1e-12)
+    T = np.diag(rng.uniform(2, 3, n)) + np.diag(rng.standard_normal(n - 1), 1) + np.diag(rng.standard_normal(n - 1), -1)
+    mask = T != 0.0
+    L, U = ilu0(T, mask)
+    rhs = rng.standard_normal(n)
+    x = sla.solve_triangular(U, sla.solve_triangular(L, rhs, lower=True, unit_diagonal=True))
+    band = np.zeros((3, n))
+    band[0, 1:] = np.diag(T, 1)
+    band[1] = np.diag(T)
+    band[2, :-1] = np.diag(T, -1)
+    assert np.allclose(x, sla.solve_banded((1, 1), band, rhs), rtol=1e-12)
+
+
+def test_fluid_ilu_vcycle_solves_with_fgmres():
+    """With ILU(0) fluid blocks (LU for solid ones) the V-cycle is still a
+    preconditioner under which FGMRES reaches the direct solution; the solid
+    blocks keep their exact LU."""
+    from dataclasses import replace as _r
+    from oracle.mesh import initial_state
+    from oracle.solver import Oracle, direct_solve
+    from paper_1709_05660_gb300.workloads import CONFIGS, noise
+    prob, opts = CONFIGS["channel2d_l3"]
+    orc = Oracle(_r(prob, levels=2), _r(opts, local_solver=1))
+    y0 = initial_state(orc.prob, orc.fine, noise(orc.fine.N, 0))
+    r, J = orc.assemble(y0)
+    orc.factor()
+    kinds = [isinstance(lu, tuple) and isinstance(lu[0], str) for lu in orc.ops[1].lu]
+    solid = [pt.solid for pt in orc.ops[1].patches]
+    assert kinds == [not s for s in solid] and any(solid) and not all(solid)
+    x, st = orc.solve(-r)
+    xs = direct_solve(J, -r)
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
