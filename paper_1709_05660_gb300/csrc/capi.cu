@@ -252,12 +252,14 @@ void build_device(Ctx& c) {
         D.inv = dalloc<double>(c, (size_t)H.inv_total);
       }
       max_dense = std::max(max_dense, H.dense_total);
+      std::vector<char> is_ilu(H.n_patches, 0);
       if (c.opts.local_solver == 1) {
         // fluid blocks (material of the block's elements) up to the ILU size limit
         std::vector<int32_t> lu, ilu;
         for (int p = 0; p < H.n_patches; ++p) {
           const bool solid = H.elem_solid[H.p_elems[H.p_elem_off[p]]] != 0;
-          (!solid && H.p_n[p] <= kIluMaxRows ? ilu : lu).push_back(p);
+          is_ilu[p] = !solid && H.p_n[p] <= kIluMaxRows;
+          (is_ilu[p] ? ilu : lu).push_back(p);
         }
         D.n_lu = (int)lu.size();
         D.n_ilu = (int)ilu.size();
@@ -266,10 +268,18 @@ void build_device(Ctx& c) {
       }
       for (int p = 0; p < H.n_patches; ++p) {
         const double n = H.p_n[p], no = H.p_nown[p];
-        // inverse rows, residual gather + index + row scale, owned index + column scale + x read/write
-        D.apply_bytes += no * n * 8.0 + n * 20.0 + no * 28.0;
-        D.apply_bytes32 += no * n * 4.0 + n * 12.0 + no * 16.0;
-        D.apply_flops += 2.0 * no * n;
+        if (is_ilu[p]) {
+          // the pattern's B x B blocks of L and U (FP32) and their map entries, residual gather + index + row
+          // scale, owned index + column scale + x read/write
+          const double nz = (double)(H.p_gmap_off[p + 1] - H.p_gmap_off[p]);
+          D.apply_bytes32 += nz * (B * B * 4.0 + 12.0) + n * 12.0 + no * 16.0;
+          D.apply_flops += 2.0 * nz * B * B;
+        } else {
+          // inverse rows, residual gather + index + row scale, owned index + column scale + x read/write
+          D.apply_bytes += no * n * 8.0 + n * 20.0 + no * 28.0;
+          D.apply_bytes32 += no * n * 4.0 + n * 12.0 + no * 16.0;
+          D.apply_flops += 2.0 * no * n;
+        }
         D.factor_flops += 2.0 * n * n * n;
         D.factor_bytes += n * n * 8.0 + no * n * 8.0;
       }
