@@ -82,7 +82,11 @@ CONFIGS = {
     # the 5-level problem one level coarser (79k unknowns, ~1 GB on the device):
     # small case for detailed profiles of the same kernels
     "channel2d_l4": (Problem(levels=4, mu_s=2e6, U=1.0), SolverOpts(tile=(4, 4))),
-    "channel2d_l6": (Problem(levels=6, mu_s=2e6, U=1.0), SolverOpts(tile=(6, 6), precision=1)),
+    # 4 x 4-element Schwarz blocks (up to 372 unknowns): measured on GB300 the
+    # fastest of the 4 x 4, 5 x 5 and 6 x 6 blocks (200-900 unknowns) at the
+    # 1e-8 error bar - larger blocks save one or two FGMRES iterations but cost
+    # n^3 to factor
+    "channel2d_l6": (Problem(levels=6, mu_s=2e6, U=1.0), SolverOpts(tile=(4, 4), precision=1)),
     # 3D plate with the shear modulus of the 2D channels: softer plates (5e5)
     # deflect by more than the fluid element next to them within a few
     # steps at this inflow and tangle the mesh

@@ -89,19 +89,20 @@ def test_roofline_picks_the_largest_class_and_divides_by_its_peak(dominant):
            "assemble": _kst(3.0, flops=3.0 * 5.0e8)}
     scale = 20.0 / kst[dominant]["ms"]   # make it the largest class at the same rate
     kst[dominant] = {k: (v * scale if k in ("ms", "bytes", "flops") else v) for k, v in kst[dominant].items()}
-    roof, classes = b._roofline(kst, steps=2, fp32_classes=("patch_factor",))
+    key = "channel2d_l6 mixed"
+    roof, classes = b._roofline(kst, steps=2, fp32_classes=("patch_factor",), traffic_key=key)
     assert roof["kernel"] == dominant
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
     assert roof["avg_launch_ms"] == pytest.approx(20.0 / 10)
     if dominant == "patch_apply":
         assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
         assert roof["achieved"] == pytest.approx(4.0e6 / 1e-3 / 1e9)     # bytes per ms -> GB/s
-        assert roof["traffic"] == json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["patch_apply"]
     elif dominant == "patch_factor":
         assert roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
         assert roof["achieved"] == pytest.approx(1.0e10 / 1e-3 / 1e12)
     else:
         assert roof["bound"] == "alu"
+    assert roof["traffic"] == json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(key, {}).get(dominant)
     assert classes[dominant]["ms_per_step"] == pytest.approx(10.0)
 
 
