@@ -9,8 +9,9 @@ displacements, seed 0) this computes, with the CPU oracle only:
   refinement) where it fits in memory and time, else the oracle's own
   FGMRES with the V-cycle driven to a true relative residual of 1e-13
   (the plain definition of the Newton-step solve, Sec. 3.1);
-* the oracle FGMRES(30) iteration count at the workload's tolerance
-  (Sec. 4.1 with this build's FGMRES reading), for iteration-count parity;
+* the oracle FGMRES(30) iteration counts at the workload's tolerance and at
+  a ten times tighter one (Sec. 4.1 with this build's FGMRES reading), for
+  iteration-count parity of the mixed and the FP64 path;
 * a seeded sample of rows of every Galerkin level J_l, l < L-1, as
   (row, column, value) triples, for sampled parity of the coarse operators.
 
@@ -51,6 +52,8 @@ def make(name: str) -> str:
     x_it, st = orc.solve(-r, rtol=opts.rtol)
     iters, rel_it = st.iters, st.rel_res
     print(f"{name}: oracle FGMRES {iters} iterations to {rel_it:.2e} in {time.time() - t0:.0f} s", flush=True)
+    _, st_t = orc.solve(-r, rtol=opts.rtol / 10)
+    print(f"{name}: oracle FGMRES {st_t.iters} iterations to {st_t.rel_res:.2e} (rtol {opts.rtol / 10:g})", flush=True)
     t0 = time.time()
     if lev.N <= DIRECT_MAX_N:
         xs = osolver.direct_solve(J, -r)
@@ -75,6 +78,8 @@ def make(name: str) -> str:
     out = os.path.join(HERE, f"xstar_{name}.npz")
     np.savez_compressed(
         out, xstar=xs, oracle_iters=np.int64(iters), oracle_rel_res=np.float64(rel_it),
+        oracle_rtol=np.float64(opts.rtol), oracle_iters_tight=np.int64(st_t.iters),
+        oracle_rtol_tight=np.float64(opts.rtol / 10),
         xstar_rel_res=np.float64(res), rnorm=np.float64(np.linalg.norm(r)), N=np.int64(lev.N),
         y0_checksum=np.float64(np.sum(y0 * np.arange(1, lev.N + 1) / lev.N)),
         how=np.array(how), galerkin_level=np.concatenate(s_lv), galerkin_row=np.concatenate(s_row),
