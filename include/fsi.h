@@ -379,9 +379,12 @@ int fsi_kernel_stats(fsi_ctx* ctx, int kind, double* device_ms, int64_t* launche
  *                 capped so a block has at most 256 threads).
  *   spmv_sub      threads per scalar row of the level's block-sparse residual
  *                 in the V-cycle (mixed path; B = 4 blocks): 2, 4 or 8.
- *   gj_panel      panel width of the tensor-core Gauss-Jordan of the Schwarz
- *                 blocks (16, 24 or 32; the widest that fits the largest block
- *                 is taken when the asked one does not).  One launch factors
+ *   gj_panel      variant of the tensor-core Gauss-Jordan of the Schwarz
+ *                 blocks: the panel width 16, 24 or 32 (one thread block per
+ *                 SM), or 216: 16-column panels with half the tensor memory,
+ *                 so that two thread blocks share an SM (blocks of at most 512
+ *                 unknowns).  When the asked variant does not fit the largest
+ *                 block, the widest that fits is taken.  One launch factors
  *                 every level, so only the value set on the finest level counts.
  * The values are a property of the ctx; setting them waits for the ctx's
  * stream and drops the recorded V-cycle graph, which is recorded again at the

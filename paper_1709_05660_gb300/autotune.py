@@ -30,7 +30,9 @@ TABLE = os.path.join(HERE, "tuning.json")
 # apply shapes tried per level: (slices, column groups); slices 1 = one block per Schwarz block
 APPLY_CANDIDATES = [(1, 4)] + [(s, g) for s in (2, 3, 4, 6, 8, 12, 16, 24, 32) for g in (4, 8, 16, 32)]
 SPMV_CANDIDATES = (2, 4, 8)
-PANEL_CANDIDATES = (16, 24, 32)
+# Gauss-Jordan variants: panel width 16, 24 or 32 (one thread block per SM), 216 = 16-column
+# panels with half the tensor memory, two thread blocks per SM
+PANEL_CANDIDATES = (16, 24, 32, 216)
 
 
 def signature(prob, opts) -> str:

@@ -2150,7 +2150,8 @@ int fsi_set_launch_params(fsi_ctx* c, int level, const fsi_launch_params* p) {
     if (!p) throw ApiError(FSI_E_INVALID, "null launch parameters");
     if (p->apply_slices < 0 || p->apply_slices > 4096 || p->apply_groups < 0 || p->apply_groups > 256 ||
         (p->spmv_sub != 0 && p->spmv_sub != 2 && p->spmv_sub != 4 && p->spmv_sub != 8) ||
-        (p->gj_panel != 0 && p->gj_panel != 16 && p->gj_panel != 24 && p->gj_panel != 32))
+        (p->gj_panel != 0 && p->gj_panel != 16 && p->gj_panel != 24 && p->gj_panel != 32 &&
+         p->gj_panel != kGjPanelPair))
       throw ApiError(FSI_E_INVALID, "launch parameters out of range");
     sync(*c);   // nothing in flight uses the old shapes or the graph
     DevLevel& D = c->dl[level];

@@ -195,7 +195,7 @@ struct Ctx {
   cudaStream_t cap_stream = nullptr;
   // the coarse factorisation runs on this higher-priority stream beside the
   // Schwarz factorisation (fork / join events on the ctx stream)
-  int gj_panel = 0;   // preferred Gauss-Jordan panel width on the tensor cores (0, 16, 24, 32)
+  int gj_panel = 0;   // preferred Gauss-Jordan variant on the tensor cores (0, 16, 24, 32, 216)
   long long tc_first_wait = -1;   // first tensor-core wait limit (< 0: the built-in limit)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

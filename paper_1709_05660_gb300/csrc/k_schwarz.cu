@@ -640,17 +640,18 @@ bool try_gj_f32(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, co
 // n % 4 == 0.  The waits on the tensor core are bounded; on time-out the
 // block records ST_TIMEOUT, stops issuing work and releases its tensor memory.
 // ---------------------------------------------------------------------------
-template <int W, int TN>
+// NC: tensor-memory columns of a block (512: one block per SM; 256: two)
+template <int W, int TN, int NC = 512>
 __host__ __device__ constexpr int gj_tc_max_n() {
   // row tiles whose A parts (2 W columns each) fit beside the accumulators
-  return (512 - 2 * TN) / (2 * W) * 128 < 1024 ? (512 - 2 * TN) / (2 * W) * 128 : 1024;
+  return (NC - 2 * TN) / (2 * W) * 128 < 1024 ? (NC - 2 * TN) / (2 * W) * 128 : 1024;
 }
-template <int W, int TN>
-__host__ __device__ constexpr int gj_tc_threads() { return gj_tc_max_n<W, TN>(); }   // one thread per row
+template <int W, int TN, int NC = 512>
+__host__ __device__ constexpr int gj_tc_threads() { return gj_tc_max_n<W, TN, NC>(); }   // one thread per row
 template <int TN>
 __host__ __device__ constexpr int gj_stage() { return TN + 1; }   // row stride of the staged tile (conflict-free banks)
 
-template <int W, int TN>
+template <int W, int TN, int NC = 512>
 size_t gj_tc_smem(int max_n) {
   const size_t n16 = ((size_t)max_n + 15) / 16 * 16;
   return (2 * n16 * W + 2 * 32 * (size_t)W + 128 * (size_t)gj_stage<TN>()) * sizeof(float) +
@@ -664,12 +665,13 @@ __device__ __forceinline__ uint32_t piv_key(float a, int row) {
   return (b & ~0x3FFu) | (uint32_t)(1023 - row);
 }
 
-template <int W, int TN>
-__global__ void __launch_bounds__(gj_tc_threads<W, TN>(), 1)
+template <int W, int TN, int NC>
+__global__ void __launch_bounds__(gj_tc_threads<W, TN, NC>(), 512 / NC)
 k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
   static_assert(W % 8 == 0 && W >= 16 && W <= 32, "panel width");
   static_assert(TN == 64 || TN == 128, "tile width");
-  constexpr int NWARP = gj_tc_threads<W, TN>() / kWarp;   // 16 or 32 warps
+  static_assert(NC == 512 || NC == 256, "tensor-memory columns");
+  constexpr int NWARP = gj_tc_threads<W, TN, NC>() / kWarp;   // 16 or 32 warps
   constexpr int CGN = NWARP / 4;                           // column-chunk slots of a tile per lane quarter
   constexpr int CW = TN / CGN > 16 ? TN / CGN : 16;        // chunk width (multiple of 16)
   constexpr int kStage = gj_stage<TN>();
@@ -698,7 +700,7 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
   const int me = threadIdx.x;
   const bool has_row = me < n;
   const bool warp_rows = wid * kWarp < n;     // this warp owns at least one row
-  constexpr uint32_t kCols = 512, kD = 2 * TN;
+  constexpr uint32_t kCols = NC, kD = 2 * TN;
   if (wid == 0) tc::tmem_alloc(&tslot, kCols);
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar2[0], 1);
@@ -983,17 +985,18 @@ done:
   if (threadIdx.x == 0 && s_sing) atomicExch(&stat[ST_SINGULAR], 1);
 }
 
-template <int W, int TN>
+template <int W, int TN, int NC = 512>
 bool fits_gj_tc(int max_n) {
-  const size_t smem = gj_tc_smem<W, TN>(max_n);
-  return !(smem > 225 * 1024 || max_n % 4 != 0 || max_n > gj_tc_max_n<W, TN>() || max_n < 64);
+  // two blocks per SM (NC = 256) share the SM's 228 KB of shared memory
+  const size_t smem = gj_tc_smem<W, TN, NC>(max_n), cap = NC == 512 ? 225 * 1024 : 112 * 1024;
+  return !(smem > cap || max_n % 4 != 0 || max_n > gj_tc_max_n<W, TN, NC>() || max_n < 64);
 }
 
-template <int W, int TN>
+template <int W, int TN, int NC = 512>
 void run_gj_tc(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cudaStream_t st) {
-  const size_t smem = gj_tc_smem<W, TN>(max_n);
-  cudaFuncSetAttribute(k_patch_gj_tc<W, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_patch_gj_tc<W, TN><<<nblocks, gj_tc_threads<W, TN>(), smem, st>>>(lv, status, max_n);
+  const size_t smem = gj_tc_smem<W, TN, NC>(max_n);
+  cudaFuncSetAttribute(k_patch_gj_tc<W, TN, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_patch_gj_tc<W, TN, NC><<<nblocks, gj_tc_threads<W, TN, NC>(), smem, st>>>(lv, status, max_n);
 }
 
 // 32-column panels where they fit (n <= 512), else 16-column ones on
@@ -1002,6 +1005,7 @@ void run_gj_tc(const GjLevels& lv, int nblocks, int max_n, int32_t* status, cuda
 // channel's blocks of 784 unknowns), as the narrower tiles halve the loads
 // in flight of the tile epilogue that bounds this kernel
 int gj_tc_variant(int max_n, int panel) {
+  if (panel == kGjPanelPair && fits_gj_tc<16, 64, 256>(max_n)) return kGjPanelPair;
   if (panel == 16 && fits_gj_tc<16, 128>(max_n)) return 16;
   if (panel == 24 && fits_gj_tc<24, 64>(max_n)) return 24;
   if (fits_gj_tc<32, 128>(max_n)) return 32;
@@ -1017,6 +1021,7 @@ bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32
     case 32: run_gj_tc<32, 128>(lv, nblocks, max_n, status, st); return true;
     case 24: run_gj_tc<24, 64>(lv, nblocks, max_n, status, st); return true;
     case 16: run_gj_tc<16, 128>(lv, nblocks, max_n, status, st); return true;
+    case kGjPanelPair: run_gj_tc<16, 64, 256>(lv, nblocks, max_n, status, st); return true;
     default: return false;
   }
 }

@@ -88,6 +88,9 @@ struct GjLevels {
   GjLevel l[kGjMaxLevels];
 };
 constexpr long long kTcWaitIters = 1LL << 22;
+// Gauss-Jordan variant code: 16-column panels on 64-column tiles with 256
+// tensor-memory columns, so that two blocks share an SM (blocks <= 512 unknowns)
+constexpr int kGjPanelPair = 216;
 // false when the blocks do not fit the tensor-core kernel (the caller then
 // factors level by level)
 // panel: preferred panel width (16 or 32; 0 = 32 when the blocks fit, else 16)

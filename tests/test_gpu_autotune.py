@@ -89,7 +89,7 @@ def test_forced_shapes_change_rounding_only(case, shape):
         s.close()
 
 
-@pytest.mark.parametrize("panel", [16, 32])
+@pytest.mark.parametrize("panel", [16, 32, 216])
 def test_panel_width(case, panel):
     s = _instance(case)
     try:
@@ -107,7 +107,7 @@ def test_tuner_entry_is_valid_and_solves(case):
     entry = autotune.tune(case["prob"], case["opts"], stream=torch.cuda.current_stream().cuda_stream, reps=5,
                           trials=1, log=lambda m: None)
     autotune.check_entry(entry, case["prob"].levels)
-    assert entry["gj_panel"] in (16, 24, 32)
+    assert entry["gj_panel"] in (16, 24, 32, 216)
     s = fsi.FSI(case["prob"], case["opts"], stream=torch.cuda.current_stream().cuda_stream, tuned=False)
     try:
         assert autotune.apply_table(s, entry) is entry
