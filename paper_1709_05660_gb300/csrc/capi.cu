@@ -236,6 +236,7 @@ void build_device(Ctx& c) {
       D.p_gmap_off = upload(c, H.p_gmap_off); D.p_pad_off = upload(c, H.p_pad_off);
       D.p_idx = upload(c, H.p_idx); D.p_own = upload(c, H.p_own);
       D.p_gmap = upload(c, H.p_gmap); D.p_padpos = upload(c, H.p_padpos);
+      D.p_boff = upload(c, H.p_boff); D.p_boff_off = upload(c, H.p_boff_off);
       D.inv_total = H.inv_total;
       D.dense_total = H.dense_total;
       if (c.mixed) {
@@ -607,14 +608,14 @@ bool gather_mixed(Ctx& c, GjLevels& lv, int& first, int& max_n) {
   bool ok = true;
   for (int l = 1; l < L; ++l) {
     DevLevel& D = c.dl[l];
-    launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
-                                 D.p_padpos, D.val, c.B, ws + off, D.p_idx_off, D.dr32, D.dc32, c.stream);
+    launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff,
+                                 D.p_pad_off, D.p_padpos, D.val, c.B, ws + off, D.p_idx_off, D.dr32, D.dc32, c.stream);
     counted(c);
     const bool ilu = c.opts.local_solver == 1;
     const int nsel = ilu ? D.n_lu : D.n_patches;
     if (ilu) {   // the fluid blocks: ILU(0) in place in the workspace
-      launch_patch_ilu0(D.n_ilu, D.sel_ilu, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, c.B, ws + off, c.status,
-                        c.stream);
+      launch_patch_ilu0(D.n_ilu, D.sel_ilu, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff, c.B,
+                        ws + off, c.status, c.stream);
       if (D.n_ilu > 0) counted(c);
     }
     if (nsel > 0 && lv.nlev < kGjMaxLevels) {
@@ -678,8 +679,9 @@ void schwarz_factor(Ctx& c) {
   for (int l = 1; l < L && !c.mixed; ++l) {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_FACTOR, D.factor_bytes, D.factor_flops, 2);
-    launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_pad_off,
-                                  D.p_padpos, D.val, B, c.dense_ws, D.p_idx_off, D.dr, D.dc, c.stream);
+    launch_patch_gather_t<double>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off,
+                                  D.p_boff, D.p_pad_off, D.p_padpos, D.val, B, c.dense_ws, D.p_idx_off, D.dr, D.dc,
+                                  c.stream);
     launch_patch_gj_t<double>(D.n_patches, D.max_n, D.p_n, D.p_nown, D.p_dense_off, D.p_own_off, D.p_own,
                               D.p_inv_off, c.dense_ws, D.inv, c.status, true, c.stream);
     counted(c, 2);
@@ -828,8 +830,8 @@ template <> struct VC<float> {
                                   D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32, c.sm_count,
                                   D.apply_slices, D.apply_groups, c.stream, D.sel_lu);
       launch_patch_apply_ilu(D.n_ilu, D.sel_ilu, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off, D.p_own,
-                             D.p_dense_off, D.p_gmap_off, D.p_gmap, c.B, level_ws(c, l), r, x, c.opts.omega,
-                             D.dr32, D.dc32, c.stream);
+                             D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff, c.B, level_ws(c, l), r,
+                             x, c.opts.omega, D.dr32, D.dc32, c.stream);
       counted(c, (D.n_lu > 0) + (D.n_ilu > 0));
       return;
     }
@@ -1294,8 +1296,8 @@ static int64_t estimate_device_bytes(const Ctx& c) {
     if (l > 0) {
       b += (H.P_ptr.size() + H.R_ptr.size() + H.S_ptr.size()) * 4.0 +
            (H.P_col.size() + H.R_col.size() + H.S_col.size()) * 12.0;
-      b += H.idx_total * 4.0 + H.own_total * 4.0 + H.n_patches * 8.0 * 8.0 + H.p_gmap.size() * 4.0 +
-           H.p_padpos.size() * 4.0 + H.inv_total * fs + 2.0 * H.idx_total * fs;
+      b += H.idx_total * 4.0 + H.own_total * 4.0 + H.n_patches * 9.0 * 8.0 + H.p_gmap.size() * 4.0 +
+           H.p_padpos.size() * 4.0 + H.p_boff.size() * 4.0 + H.inv_total * fs + 2.0 * H.idx_total * fs;
       if (mixed) b += H.nnzb * B * B * 4.0 + (H.P_col.size() + H.R_col.size()) * 4.0 + H.Ni * 3.0 * 4.0;
       max_dense = std::max(max_dense, (double)H.dense_total);
     }

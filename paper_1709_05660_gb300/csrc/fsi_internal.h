@@ -62,6 +62,8 @@ struct HostLevel {
   std::vector<int32_t> p_own;                  // patch-local row of each owned row
   std::vector<int32_t> p_gmap;                 // (bsr block, local block row, local block col)
   std::vector<int32_t> p_padpos;               // patch-local pad positions (identity diag), flat
+  std::vector<int32_t> p_boff;                 // per local block: dense offset * 8 + width (B or dim + 1)
+  std::vector<int64_t> p_boff_off;             // into p_boff
   std::vector<int64_t> p_pad_off;
   std::vector<int32_t> p_elems;                // elements of each patch (for export)
   std::vector<int64_t> p_elem_off;
@@ -118,7 +120,8 @@ struct DevLevel {
   int32_t *p_n = nullptr, *p_nown = nullptr;
   int64_t *p_idx_off = nullptr, *p_own_off = nullptr, *p_dense_off = nullptr, *p_inv_off = nullptr,
           *p_gmap_off = nullptr, *p_pad_off = nullptr;
-  int32_t *p_idx = nullptr, *p_own = nullptr, *p_gmap = nullptr, *p_padpos = nullptr;
+  int32_t *p_idx = nullptr, *p_own = nullptr, *p_gmap = nullptr, *p_padpos = nullptr, *p_boff = nullptr;
+  int64_t* p_boff_off = nullptr;
   double* inv = nullptr;          // owned rows of B~_k^{-1} (equilibrated block)
   double *dr = nullptr, *dc = nullptr;     // row / column scales of each block (FP64 path)
   float *dr32 = nullptr, *dc32 = nullptr;  // (mixed path)

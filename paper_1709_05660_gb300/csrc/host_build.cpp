@@ -337,8 +337,8 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
   L.p_n.assign(np, 0); L.p_nown.assign(np, 0);
   L.p_idx_off.assign(np + 1, 0); L.p_own_off.assign(np + 1, 0); L.p_dense_off.assign(np + 1, 0);
   L.p_inv_off.assign(np + 1, 0); L.p_gmap_off.assign(np + 1, 0); L.p_pad_off.assign(np + 1, 0);
-  L.p_elem_off.assign(np + 1, 0);
-  L.p_idx.clear(); L.p_own.clear(); L.p_gmap.clear(); L.p_padpos.clear(); L.p_elems.clear();
+  L.p_elem_off.assign(np + 1, 0); L.p_boff_off.assign(np + 1, 0);
+  L.p_idx.clear(); L.p_own.clear(); L.p_gmap.clear(); L.p_padpos.clear(); L.p_elems.clear(); L.p_boff.clear();
   L.max_n = 0;
   L.max_nown = 0;
   for (int p = 0; p < np; ++p) {
@@ -350,11 +350,20 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
     std::vector<int32_t> blocks(nodes);
     for (int32_t e : pel[p]) blocks.push_back((int32_t)(L.n_nodes + e));   // elements ascending
     const int nbk = (int)blocks.size();
-    // block sizes are padded to a multiple of 4 (the FP32 factorisation
-    // kernels move rows as float4): the extra positions are identity rows /
-    // columns whose index is an element padding slot (its vector entries are
-    // always zero), never owned
-    const int n_blk = nbk * B;
+    // dense layout: the B unknowns of each node block, then the dim + 1
+    // pressures of each element block (its padding slots are left out), at
+    // the offsets kept in p_boff; the size is padded to a multiple of 4 (the
+    // FP32 factorisation kernels move rows as float4) by identity rows /
+    // columns at the end whose index is an element padding slot (its vector
+    // entries are always zero), never owned
+    std::vector<int32_t> boff(nbk);
+    int n_blk = 0;
+    for (int lb = 0; lb < nbk; ++lb) {
+      const int w = blocks[lb] < L.n_nodes ? B : dim + 1;
+      boff[lb] = n_blk;
+      L.p_boff.push_back(n_blk * 8 + w);
+      n_blk += w;
+    }
     const int n = (n_blk + 3) & ~3;
     L.p_n[p] = n;
     L.max_n = std::max(L.max_n, n);
@@ -362,12 +371,10 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
     for (int lb = 0; lb < nbk; ++lb) {
       const int32_t blk = blocks[lb];
       const bool is_node = blk < L.n_nodes;
-      for (int c = 0; c < B; ++c) {
+      for (int c = 0; c < (is_node ? B : dim + 1); ++c) {
         L.p_idx.push_back(blk * B + c);
-        const bool pad = !is_node && c > dim;
-        if (pad) L.p_padpos.push_back(lb * B + c);
-        const bool own = is_node ? (patch_of[owner[blk]] == p) : !pad;
-        if (own) { L.p_own.push_back(lb * B + c); ++nown; }
+        const bool own = is_node ? (patch_of[owner[blk]] == p) : true;
+        if (own) { L.p_own.push_back(boff[lb] + c); ++nown; }
       }
     }
     for (int q = n_blk; q < n; ++q) {
@@ -395,6 +402,7 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
     L.p_gmap_off[p + 1] = (int64_t)L.p_gmap.size() / 3;
     L.p_pad_off[p + 1] = (int64_t)L.p_padpos.size();
     L.p_elem_off[p + 1] = (int64_t)L.p_elems.size();
+    L.p_boff_off[p + 1] = (int64_t)L.p_boff.size();
   }
   L.dense_total = L.p_dense_off[np];
   L.inv_total = L.p_inv_off[np];

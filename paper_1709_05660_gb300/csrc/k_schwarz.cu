@@ -68,15 +68,29 @@ __device__ __forceinline__ double pow2_inv(double m) {
 // Gather B_k and equilibrate it: B~ = D_r B D_c with power-of-two row scales
 // (row maxima -> [1, 2)) and then column scales.  The scales are stored so
 // that B^{-1} r = D_c B~^{-1} (D_r r).
+// Entry e of the B x B matrix block of gmap entry g: its dense row i and
+// column j, or false for a padding component of an element block (left out
+// of the dense block).
+__device__ __forceinline__ bool gather_pos(const int32_t* __restrict__ gmap, const int32_t* __restrict__ bo,
+                                           int64_t g, int e, int B, int& i, int& j) {
+  const int ci = e / B, cj = e % B;
+  const int32_t r = __ldg(bo + gmap[3 * g + 1]), c = __ldg(bo + gmap[3 * g + 2]);
+  i = (r >> 3) + ci;
+  j = (c >> 3) + cj;
+  return ci < (r & 7) && cj < (c & 7);
+}
+
 template <typename T>
 __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t* __restrict__ dense_off,
                                  const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
+                                 const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff,
                                  const int64_t* __restrict__ pad_off, const int32_t* __restrict__ padpos,
                                  const double* __restrict__ bsr_val, int B, T* __restrict__ dense,
                                  const int64_t* __restrict__ idx_off, T* __restrict__ dr, T* __restrict__ dc) {
   const int p = blockIdx.x;
   const int n = p_n[p];
   T* D = dense + dense_off[p];
+  const int32_t* bo = boff + boff_off[p];
   for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) D[t] = T(0);
   __syncthreads();
   const int BB = B * B;
@@ -91,10 +105,11 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
     __syncthreads();
     for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
       const int64_t g = g0 + t / BB;
-      const int e = (int)(t % BB), ci = e / B;
-      const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1];
-      const double a = fabs((double)T(bsr_val[(int64_t)blk * BB + e]));
-      atomicMax(&rmx[lr * B + ci], (unsigned long long)__double_as_longlong(a));
+      const int e = (int)(t % BB);
+      int i, j;
+      if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
+      const double a = fabs((double)T(bsr_val[(int64_t)gmap[3 * g] * BB + e]));
+      atomicMax(&rmx[i], (unsigned long long)__double_as_longlong(a));
     }
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x)
       atomicMax(&rmx[padpos[t]], (unsigned long long)__double_as_longlong(1.0));
@@ -103,10 +118,11 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
     __syncthreads();
     for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
       const int64_t g = g0 + t / BB;
-      const int e = (int)(t % BB), ci = e / B, cj = e % B;
-      const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
-      const double a = fabs((double)(T(bsr_val[(int64_t)blk * BB + e]) * srw[lr * B + ci]));
-      atomicMax(&cmx[lc * B + cj], (unsigned long long)__double_as_longlong(a));
+      const int e = (int)(t % BB);
+      int i, j;
+      if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
+      const double a = fabs((double)(T(bsr_val[(int64_t)gmap[3 * g] * BB + e]) * srw[i]));
+      atomicMax(&cmx[j], (unsigned long long)__double_as_longlong(a));
     }
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
       const int q = padpos[t];
@@ -123,10 +139,10 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
     __syncthreads();
     for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
       const int64_t g = g0 + t / BB;
-      const int e = (int)(t % BB), ci = e / B, cj = e % B;
-      const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
-      const int i = lr * B + ci, j = lc * B + cj;
-      D[(int64_t)i * n + j] = T(T(bsr_val[(int64_t)blk * BB + e]) * srw[i]) * scl[j];
+      const int e = (int)(t % BB);
+      int i, j;
+      if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
+      D[(int64_t)i * n + j] = T(T(bsr_val[(int64_t)gmap[3 * g] * BB + e]) * srw[i]) * scl[j];
     }
     __syncthreads();   // padding rows / columns of the block matrix hold zeros: the diagonal goes last
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
@@ -137,9 +153,10 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
   }
   for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
     const int64_t g = g0 + t / BB;
-    const int e = (int)(t % BB), ci = e / B, cj = e % B;
-    const int32_t blk = gmap[3 * g], lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
-    D[(int64_t)(lr * B + ci) * n + lc * B + cj] = T(bsr_val[(int64_t)blk * BB + e]);
+    const int e = (int)(t % BB);
+    int i, j;
+    if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
+    D[(int64_t)i * n + j] = T(bsr_val[(int64_t)gmap[3 * g] * BB + e]);
   }
   __syncthreads();
   for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
@@ -1128,12 +1145,12 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
-                           const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
-                           const double* bsr_val, int B, T* dense, const int64_t* idx_off, T* dr, T* dc,
-                           cudaStream_t st) {
+                           const int32_t* gmap, const int64_t* boff_off, const int32_t* boff, const int64_t* pad_off,
+                           const int32_t* padpos, const double* bsr_val, int B, T* dense, const int64_t* idx_off,
+                           T* dr, T* dc, cudaStream_t st) {
   if (np <= 0) return;
-  k_patch_gather_t<T><<<np, 512, 0, st>>>(p_n, dense_off, gmap_off, gmap, pad_off, padpos, bsr_val, B, dense,
-                                          idx_off, dr, dc);
+  k_patch_gather_t<T><<<np, 512, 0, st>>>(p_n, dense_off, gmap_off, gmap, boff_off, boff, pad_off, padpos, bsr_val,
+                                          B, dense, idx_off, dr, dc);
 }
 
 template <typename T, int W>
@@ -1317,7 +1334,7 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
 // B^{-1} r is applied as D_c U~^{-1} L~^{-1} D_r r as for the exact inverses.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kIluMaxNb = 256;   // block rows of a block: 1024 / 4 (2D) or ceil(1024 / 6) (3D)
+constexpr int kIluMaxNb = 352;   // node / element blocks of a Schwarz block: <= 1024 / 3
 constexpr int kIluWords = kIluMaxNb / 32;
 
 // pattern bits of block pairs (local block row, local block column)
@@ -1336,104 +1353,124 @@ __device__ void ilu_mask(uint32_t* bm, int nb, int64_t g0, int64_t g1, const int
 }
 }  // namespace
 
+// the dense offsets and widths of a Schwarz block's node / element blocks
+__device__ void ilu_blocks(int16_t* off, int8_t* w, int nb, const int32_t* __restrict__ bo) {
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int32_t v = bo[b];
+    off[b] = (int16_t)(v >> 3);
+    w[b] = (int8_t)(v & 7);
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256)
 k_patch_ilu0(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n, const int64_t* __restrict__ dense_off,
-             const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap, int B, float* __restrict__ dense,
-             int32_t* __restrict__ status) {
+             const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
+             const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff, int B,
+             float* __restrict__ dense, int32_t* __restrict__ status) {
   __shared__ uint32_t bm[kIluMaxNb * kIluWords];
   __shared__ int16_t rb[kIluMaxNb], cb[kIluMaxNb];   // block rows / columns touching block bk
+  __shared__ int16_t s_off[kIluMaxNb];
+  __shared__ int8_t s_w[kIluMaxNb];
   __shared__ int nrb, ncb, s_sing;
   const int p = sel[blockIdx.x];
-  const int n = p_n[p], nb = (n + B - 1) / B;
+  const int n = p_n[p], nb = (int)(boff_off[p + 1] - boff_off[p]);
   float* D = dense + dense_off[p];
   if (threadIdx.x == 0) s_sing = 0;
   ilu_mask(bm, nb, gmap_off[p], gmap_off[p + 1], gmap);
-  for (int k = 0; k < n; ++k) {
-    const int bk = k / B;
-    if (k % B == 0) {
-      // candidate block rows (i > k) and columns (j > k): bk itself and the
-      // blocks coupled to it in the pattern
-      if (threadIdx.x == 0) {
-        int a = 0, c = 0;
-        rb[a++] = (int16_t)bk;
-        cb[c++] = (int16_t)bk;
-        for (int b = bk + 1; b < nb; ++b) {
-          if (ilu_bit(bm, b, bk)) rb[a++] = (int16_t)b;
-          if (ilu_bit(bm, bk, b)) cb[c++] = (int16_t)b;
-        }
-        nrb = a;
-        ncb = c;
+  ilu_blocks(s_off, s_w, nb, boff + boff_off[p]);
+  for (int bk = 0; bk < nb; ++bk) {
+    // candidate block rows (i > k) and columns (j > k): bk itself and the
+    // blocks coupled to it in the pattern
+    if (threadIdx.x == 0) {
+      int a = 0, c = 0;
+      rb[a++] = (int16_t)bk;
+      cb[c++] = (int16_t)bk;
+      for (int b = bk + 1; b < nb; ++b) {
+        if (ilu_bit(bm, b, bk)) rb[a++] = (int16_t)b;
+        if (ilu_bit(bm, bk, b)) cb[c++] = (int16_t)b;
+      }
+      nrb = a;
+      ncb = c;
+    }
+    __syncthreads();
+    const bool self = ilu_bit(bm, bk, bk);   // a full diagonal block (node block)
+    const int nr = nrb * B, nc = ncb * B;
+    for (int kk = 0; kk < s_w[bk]; ++kk) {
+      const int k = s_off[bk] + kk;
+      float* Dk = D + (int64_t)k * n;
+      float akk = Dk[k];
+      if (!(fabsf(akk) > 0.f) || !isfinite(akk)) {
+        if (threadIdx.x == 0) s_sing = 1;
+        akk = 1.f;
+      }
+      const float rk = 1.f / akk;
+      // l_ik = a_ik / u_kk
+      for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        const int bi = rb[t / B], cr = t % B;
+        if (cr >= s_w[bi]) continue;
+        const int i = s_off[bi] + cr;
+        if (i <= k || (bi == bk && !self)) continue;
+        D[(int64_t)i * n + k] *= rk;
+      }
+      __syncthreads();
+      // a_ij -= l_ik u_kj on the pattern
+      for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) {
+        const int ri = t / nc, ci = t % nc;
+        const int bi = rb[ri / B], cr = ri % B, bj = cb[ci / B], cc = ci % B;
+        if (cr >= s_w[bi] || cc >= s_w[bj]) continue;
+        const int i = s_off[bi] + cr, j = s_off[bj] + cc;
+        if (i <= k || j <= k) continue;
+        if ((bi == bk || bj == bk) && !self) continue;
+        if (!(ilu_bit(bm, bi, bj) || i == j)) continue;
+        D[(int64_t)i * n + j] -= D[(int64_t)i * n + k] * Dk[j];
       }
       __syncthreads();
     }
-    const bool self = ilu_bit(bm, bk, bk);   // a full diagonal block (node block)
-    float* Dk = D + (int64_t)k * n;
-    float akk = Dk[k];
-    if (!(fabsf(akk) > 0.f) || !isfinite(akk)) {
-      if (threadIdx.x == 0) s_sing = 1;
-      akk = 1.f;
-    }
-    const float rk = 1.f / akk;
-    // l_ik = a_ik / u_kk
-    const int nr = nrb * B, nc = ncb * B;
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-      const int bi = rb[t / B], i = bi * B + t % B;
-      if (i <= k || i >= n || (bi == bk && !self)) continue;
-      D[(int64_t)i * n + k] *= rk;
-    }
-    __syncthreads();
-    // a_ij -= l_ik u_kj on the pattern
-    for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) {
-      const int ri = t / nc, ci = t % nc;
-      const int bi = rb[ri / B], i = bi * B + ri % B;
-      const int bj = cb[ci / B], j = bj * B + ci % B;
-      if (i <= k || j <= k || i >= n || j >= n) continue;
-      if ((bi == bk || bj == bk) && !self) continue;
-      if (!(ilu_bit(bm, bi, bj) || i == j)) continue;
-      D[(int64_t)i * n + j] -= D[(int64_t)i * n + k] * Dk[j];
-    }
-    __syncthreads();
   }
   if (threadIdx.x == 0 && s_sing) atomicExch(&status[ST_SINGULAR], 1);
 }
 
 // One warp per block: y = D_r r, forward sweep with the unit lower factor and
-// backward sweep with the upper one, block row by block row (the lanes take
-// the off-diagonal blocks of the row, lane 0 the diagonal block), then the
-// owned rows: x += omega D_c y.
+// backward sweep with the upper factor over node / element block rows (the
+// pattern's blocks only), x[own] += omega D_c y.
 __global__ void __launch_bounds__(32)
 k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n,
                   const int32_t* __restrict__ p_nown, const int64_t* __restrict__ idx_off,
                   const int32_t* __restrict__ idx, const int64_t* __restrict__ own_off,
                   const int32_t* __restrict__ own, const int64_t* __restrict__ dense_off,
-                  const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap, int B,
+                  const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
+                  const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff, int B,
                   const float* __restrict__ dense, const float* __restrict__ r, float* __restrict__ x, float omega,
                   const float* __restrict__ dr, const float* __restrict__ dc) {
   __shared__ uint32_t bm[kIluMaxNb * kIluWords];
   __shared__ float y[kIluMaxRows];
+  __shared__ int16_t s_off[kIluMaxNb];
+  __shared__ int8_t s_w[kIluMaxNb];
   const int p = sel[blockIdx.x];
   const int lane = threadIdx.x;
-  const int n = p_n[p], nb = (n + B - 1) / B;
+  const int n = p_n[p], nb = (int)(boff_off[p + 1] - boff_off[p]);
   const float* D = dense + dense_off[p];
   const int32_t* id = idx + idx_off[p];
   const float* Dr = dr + idx_off[p];
   const float* Dc = dc + idx_off[p];
   ilu_mask(bm, nb, gmap_off[p], gmap_off[p + 1], gmap);
+  ilu_blocks(s_off, s_w, nb, boff + boff_off[p]);
   for (int i = lane; i < n; i += 32) y[i] = id[i] >= 0 ? Dr[i] * r[id[i]] : 0.f;
   __syncwarp();
   for (int dir = 0; dir < 2; ++dir) {   // 0: L (forward), 1: U (backward)
     for (int s = 0; s < nb; ++s) {
       const int bi = dir == 0 ? s : nb - 1 - s;
+      const int oi = s_off[bi], wi = s_w[bi];
       float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int lo = dir == 0 ? 0 : bi + 1, hi = dir == 0 ? bi : nb;
       for (int bk = lo + lane; bk < hi; bk += 32) {
         if (!ilu_bit(bm, bi, bk)) continue;
-        for (int rr = 0; rr < B; ++rr) {
-          const int i = bi * B + rr;
-          if (i >= n) break;
-          const float* Di = D + (int64_t)i * n + bk * B;
+        const int ok = s_off[bk], wk = s_w[bk];
+        for (int rr = 0; rr < wi; ++rr) {
+          const float* Di = D + (int64_t)(oi + rr) * n + ok;
           float a = 0.f;
-          for (int c = 0; c < B && bk * B + c < n; ++c) a += Di[c] * y[bk * B + c];
+          for (int c = 0; c < wk; ++c) a += Di[c] * y[ok + c];
           acc[rr] += a;
         }
       }
@@ -1443,17 +1480,16 @@ k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p
         for (int o = 16; o > 0; o >>= 1) acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], o);
       if (lane == 0) {
         const bool self = ilu_bit(bm, bi, bi);
-        for (int q = 0; q < B; ++q) {
-          const int rr = dir == 0 ? q : B - 1 - q;
-          const int i = bi * B + rr;
-          if (i >= n) continue;
-          const float* Di = D + (int64_t)i * n + bi * B;
+        for (int q = 0; q < wi; ++q) {
+          const int rr = dir == 0 ? q : wi - 1 - q;
+          const int i = oi + rr;
+          const float* Di = D + (int64_t)i * n + oi;
           float v = y[i] - acc[rr];
           if (self) {
             if (dir == 0) {
-              for (int c = 0; c < rr; ++c) v -= Di[c] * y[bi * B + c];
+              for (int c = 0; c < rr; ++c) v -= Di[c] * y[oi + c];
             } else {
-              for (int c = rr + 1; c < B && bi * B + c < n; ++c) v -= Di[c] * y[bi * B + c];
+              for (int c = rr + 1; c < wi; ++c) v -= Di[c] * y[oi + c];
             }
           }
           y[i] = dir == 0 ? v : v / Di[rr];
@@ -1471,26 +1507,26 @@ k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p
 }
 
 void launch_patch_ilu0(int nsel, const int32_t* sel, const int32_t* p_n, const int64_t* dense_off,
-                       const int64_t* gmap_off, const int32_t* gmap, int B, float* dense, int32_t* status,
-                       cudaStream_t st) {
+                       const int64_t* gmap_off, const int32_t* gmap, const int64_t* boff_off, const int32_t* boff,
+                       int B, float* dense, int32_t* status, cudaStream_t st) {
   if (nsel <= 0) return;
-  k_patch_ilu0<<<nsel, 256, 0, st>>>(sel, p_n, dense_off, gmap_off, gmap, B, dense, status);
+  k_patch_ilu0<<<nsel, 256, 0, st>>>(sel, p_n, dense_off, gmap_off, gmap, boff_off, boff, B, dense, status);
 }
 
 void launch_patch_apply_ilu(int nsel, const int32_t* sel, const int32_t* p_n, const int32_t* p_nown,
                             const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
-                            const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap, int B,
-                            const float* dense, const float* r, float* x, double omega, const float* dr,
-                            const float* dc, cudaStream_t st) {
+                            const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap,
+                            const int64_t* boff_off, const int32_t* boff, int B, const float* dense, const float* r,
+                            float* x, double omega, const float* dr, const float* dc, cudaStream_t st) {
   if (nsel <= 0) return;
-  k_patch_apply_ilu<<<nsel, 32, 0, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off, gmap, B,
-                                         dense, r, x, (float)omega, dr, dc);
+  k_patch_apply_ilu<<<nsel, 32, 0, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off, gmap,
+                                         boff_off, boff, B, dense, r, x, (float)omega, dr, dc);
 }
 
 #define FSI_INST(T)                                                                                              \
   template void launch_patch_gather_t<T>(int, const int32_t*, const int64_t*, const int64_t*, const int32_t*,  \
-                                         const int64_t*, const int32_t*, const double*, int, T*,                \
-                                         const int64_t*, T*, T*, cudaStream_t);                                 \
+                                         const int64_t*, const int32_t*, const int64_t*, const int32_t*,        \
+                                         const double*, int, T*, const int64_t*, T*, T*, cudaStream_t);         \
   template void launch_patch_gj_t<T>(int, int, const int32_t*, const int32_t*, const int64_t*, const int64_t*, \
                                      const int32_t*, const int64_t*, T*, T*, int32_t*, bool, cudaStream_t);     \
   template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \

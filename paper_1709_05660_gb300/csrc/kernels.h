@@ -99,11 +99,12 @@ bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32
 // panel width of the tensor-core variant that launch_patch_gj_tc_levels picks
 // for blocks up to max_n with preference `panel` (0: none fits)
 int gj_tc_variant(int max_n, int panel);
+// boff / boff_off: per local block of a Schwarz block its dense offset * 8 + width
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
-                           const int32_t* gmap, const int64_t* pad_off, const int32_t* padpos,
-                           const double* bsr_val, int B, T* dense, const int64_t* idx_off, T* dr, T* dc,
-                           cudaStream_t st);
+                           const int32_t* gmap, const int64_t* boff_off, const int32_t* boff, const int64_t* pad_off,
+                           const int32_t* padpos, const double* bsr_val, int B, T* dense, const int64_t* idx_off,
+                           T* dr, T* dc, cudaStream_t st);
 template <typename T>
 void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
                        const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
@@ -120,14 +121,14 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
 // kIluMaxRows unknowns
 constexpr int kIluMaxRows = 1024;
 void launch_patch_ilu0(int nsel, const int32_t* sel, const int32_t* p_n, const int64_t* dense_off,
-                       const int64_t* gmap_off, const int32_t* gmap, int B, float* dense, int32_t* status,
-                       cudaStream_t st);
+                       const int64_t* gmap_off, const int32_t* gmap, const int64_t* boff_off, const int32_t* boff,
+                       int B, float* dense, int32_t* status, cudaStream_t st);
 // x[own] += omega (R^0)^T U^{-1} L^{-1} R^delta r for the ILU(0) blocks in sel
 void launch_patch_apply_ilu(int nsel, const int32_t* sel, const int32_t* p_n, const int32_t* p_nown,
                             const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
-                            const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap, int B,
-                            const float* dense, const float* r, float* x, double omega, const float* dr,
-                            const float* dc, cudaStream_t st);
+                            const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap,
+                            const int64_t* boff_off, const int32_t* boff, int B, const float* dense, const float* r,
+                            float* x, double omega, const float* dr, const float* dc, cudaStream_t st);
 // Launch shape of one level's Schwarz apply: kind 0 = one block per patch
 // (k_patch_apply_t), kind 1 = `slices` row slices per patch of `vps` owned-row
 // vectors, `groups` column groups per block (k_patch_apply_rows).
