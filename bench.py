@@ -716,11 +716,13 @@ def _roofline(kst, steps, fp32_classes=(), traffic_key=None):
                    "hbm_frac": (v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm_peak) if v["ms"] > 0 else None,
                    "GFLOPs": (v["flops"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
                for k, v in kst.items()}
-    # the FP64 Krylov product runs 16 FMAs per 4 x 4 block on the FP64 pipe:
-    # its fraction of the derived FP64 ALU peak
-    op = classes.get("operator")
-    if op and op["GFLOPs"]:
-        op["fp64_frac"] = op["GFLOPs"] / FP64_ALU_PEAK_GFLOPS
+    # FP64-pipe-bound classes: the Krylov product (16 FMAs per 4 x 4 block) and
+    # the element and Galerkin kernels (executed FP64 operations, counted with
+    # ncu per element): their fraction of the derived FP64 ALU peak
+    for name in ("operator", "assemble", "galerkin"):
+        op = classes.get(name)
+        if op and op["GFLOPs"]:
+            op["fp64_frac"] = op["GFLOPs"] / FP64_ALU_PEAK_GFLOPS
     return roof, classes
 
 
@@ -1036,14 +1038,35 @@ def run_sweep(args):
 def run_profile_case(args):
     """A small case of one kernel for ncu captures (a few GB on the device):
     `gj` factors the 6-level channel's Schwarz blocks on the 4-level mesh
-    (the same block sizes, 188 blocks in one launch) twice; `spmv` runs two
+    (the same block sizes, 337 blocks in one launch) twice; `spmv` runs two
     V-cycles of the 5-level channel (residual vectors and matrices larger than
-    L2).  Prints the unknowns and the device bytes held."""
+    L2); `asm` assembles small 2D and 3D problems once in each time
+    discretisation.  Prints the unknowns and the device bytes held."""
     import torch
     from dataclasses import replace
     from paper_1709_05660_gb300 import fsi
 
     torch.cuda.set_device(0)
+    if args.profile_case == "asm":
+        # one assembly (element matrices, scatter, Galerkin hierarchy) per
+        # problem kind: 2D and 3D, steady, BDF and Crank-Nicolson
+        from paper_1709_05660_gb300.workloads import Problem, SolverOpts, problem_3d
+        out = []
+        for prob, opts in [(Problem(levels=3, mu_s=5e5, U=0.2, transient=t), SolverOpts(tile=(2, 2), precision=1))
+                           for t in (0, 1, 2)] + \
+                          [(problem_3d(levels=2, mu_s=2e6, U=0.2, transient=t), SolverOpts(tile=(2, 2, 2), precision=1))
+                           for t in (0, 1, 2)]:
+            s = fsi.FSI(prob, opts, stream=torch.cuda.current_stream().cuda_stream)
+            N = int(s.N[-1])
+            y = torch.empty(N, dtype=torch.float64, device="cuda")
+            s.initial_state(torch.tensor(noise(N, 0), dtype=torch.float64, device="cuda"), y)
+            s.set_state(y, y if prob.transient else None, y if prob.transient else None)
+            s.assemble()
+            torch.cuda.synchronize()
+            out.append({"dim": prob.dim, "transient": prob.transient, "unknowns": N})
+            s.close()
+        print(json.dumps({"profile_case": "asm", "problems": out}))
+        return
     prob, opts = CONFIGS[args.config]
     prob = replace(prob, levels=4 if args.profile_case == "gj" else 5)
     s = fsi.FSI(prob, replace(opts, precision=1), stream=torch.cuda.current_stream().cuda_stream)
@@ -1113,7 +1136,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="paper-settings parameter studies instead")
     ap.add_argument("--sweep-config", default="channel2d_l5")
     ap.add_argument("--sweep-precision", type=int, default=1)
-    ap.add_argument("--profile-case", choices=["gj", "spmv"], default=None,
+    ap.add_argument("--profile-case", choices=["gj", "spmv", "asm"], default=None,
                     help="run one small case of a kernel for an ncu capture instead")
     ap.add_argument("--_cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_out", default=None, help=argparse.SUPPRESS)

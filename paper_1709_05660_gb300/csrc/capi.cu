@@ -222,6 +222,8 @@ void build_device(Ctx& c) {
     D.int_of_canon = upload(c, ioc);
     D.elem_map = upload(c, H.elem_map);
     D.color_list = upload(c, H.color_list);
+    D.mat_list = upload(c, H.mat_list);
+    D.n_fluid_elem = H.n_fluid_elem;
     D.color_ptr = H.color_ptr;
     if (l > 0) {
       D.P_ptr = upload(c, H.P_ptr); D.P_col = upload(c, H.P_col); D.P_val = upload(c, H.P_val);
@@ -264,6 +266,10 @@ void build_device(Ctx& c) {
         }
         D.n_lu = (int)lu.size();
         D.n_ilu = (int)ilu.size();
+        for (int32_t q : ilu) {
+          D.ilu_max_n = std::max(D.ilu_max_n, (int)H.p_n[q]);
+          D.ilu_max_nb = std::max(D.ilu_max_nb, (int)(H.p_boff_off[q + 1] - H.p_boff_off[q]));
+        }
         D.sel_lu = upload(c, lu);
         D.sel_ilu = upload(c, ilu);
       }
@@ -405,6 +411,7 @@ std::vector<int32_t> coarse_pads(const Ctx& c) {
 // assembly
 // ---------------------------------------------------------------------------
 void assemble_impl(Ctx& c);
+bool aux_stream(Ctx& c);
 void assemble(Ctx& c, bool want_res) {
   Nvtx nv("fsi assemble + Galerkin");
   const double b0 = c.alg_bytes;
@@ -432,15 +439,32 @@ void assemble_impl(Ctx& c) {
   ck(cudaMemsetAsync(c.res, 0, F.Ni * sizeof(double), c.stream), "memset");
   const int ngroups = (int)F.color_ptr.size() - 1;
   {
-    // bytes: element state in, element matrix + residual out
-    Prof pr(c, FSI_K_ASSEMBLE, (double)F.n_elem * (nd * 8.0 + nd * nd * 8.0 + nd * 8.0), 0.0, ngroups);
-    for (int g = 0; g < ngroups; ++g) {
-      const int ne = F.color_ptr[g + 1] - F.color_ptr[g];
-      (c.dim == 2 ? launch_assemble_2d : launch_assemble_3d)((g & 1) == 1, F.color_list + F.color_ptr[g], ne, c.y,
-                                                              F.elem_nodes, F.node_class, F.elem_geo, F.n_nodes, pp,
-                                                              F.Ke, Re, c.status, c.asm_scratch, c.stream);
+    // element matrices: one pass over the fluid elements and one over the
+    // solid ones (in 2D the small solid pass runs on the private stream beside
+    // the fluid one; in 3D both share the flux scratch, so they run in turn)
+    const int nf = (int)F.n_fluid_elem, ns = (int)(F.n_elem - F.n_fluid_elem);
+    // bytes: element state in, element matrix + residual out; flops: executed FP64 operations
+    Prof pr(c, FSI_K_ASSEMBLE, (double)F.n_elem * (nd * 8.0 + nd * nd * 8.0 + nd * 8.0),
+            nf * assemble_flops_per_element(c.dim, false, pp.transient) +
+                ns * assemble_flops_per_element(c.dim, true, pp.transient),
+            (nf > 0) + (ns > 0));
+    auto run = [&](bool solid, const int32_t* list, int ne, cudaStream_t st) {
+      if (!(c.dim == 2 ? launch_assemble_2d : launch_assemble_3d)(solid, list, ne, c.y, F.elem_nodes, F.node_class,
+                                                                   F.elem_geo, F.n_nodes, pp, F.Ke, Re, c.status,
+                                                                   c.asm_scratch, c.asm_scratch_ne, st))
+        throw ApiError(FSI_E_CUDA, "assembly: element pass larger than the flux scratch");
       counted(c, assemble_launches(c.dim, ne));
+    };
+    const bool fork = c.dim == 2 && nf > 0 && ns > 0 && !c.prof && aux_stream(c);
+    if (fork) {
+      cudaEventRecord(c.ev_fork, c.stream);
+      cudaStreamWaitEvent(c.aux_stream, c.ev_fork, 0);
+      run(true, F.mat_list + nf, ns, c.aux_stream);
+      cudaEventRecord(c.ev_join, c.aux_stream);
     }
+    run(false, F.mat_list, nf, c.stream);
+    if (fork) cudaStreamWaitEvent(c.stream, c.ev_join, 0);
+    else run(true, F.mat_list + nf, ns, c.stream);
   }
   {
     Prof pr(c, FSI_K_SCATTER, (double)F.n_elem * nd * nd * 8.0 + (double)F.nnzb * B * B * 16.0, 0.0, ngroups + 1);
@@ -461,7 +485,8 @@ void assemble_impl(Ctx& c) {
     DevLevel& Fi = c.dl[l];
     DevLevel& Co = c.dl[l - 1];
     {
-      Prof pr(c, FSI_K_GALERKIN, (double)Fi.n_elem * nd * nd * 8.0 + (double)Co.n_elem * nd * nd * 8.0, 0.0);
+      Prof pr(c, FSI_K_GALERKIN, (double)Fi.n_elem * nd * nd * 8.0 + (double)Co.n_elem * nd * nd * 8.0,
+              (double)Co.n_elem * galerkin_flops_per_coarse_element(c.dim));
       if (c.dim == 2)
         launch_galerkin_2d(Co.cells[0], Co.cells[1], Fi.Ke, Fi.elem_nodes, Fi.node_class, Fi.dir, Co.elem_nodes,
                            Co.node_class, Co.dir, Co.Ke, c.stream);
@@ -829,9 +854,9 @@ template <> struct VC<float> {
       launch_patch_apply_t<float>(D.n_lu, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off,
                                   D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32, c.sm_count,
                                   D.apply_slices, D.apply_groups, c.stream, D.sel_lu);
-      launch_patch_apply_ilu(D.n_ilu, D.sel_ilu, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off, D.p_own,
-                             D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff, c.B, level_ws(c, l), r,
-                             x, c.opts.omega, D.dr32, D.dc32, c.stream);
+      launch_patch_apply_ilu(D.n_ilu, D.ilu_max_n, D.ilu_max_nb, D.sel_ilu, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
+                             D.p_own_off, D.p_own, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff, c.B,
+                             level_ws(c, l), r, x, c.opts.omega, D.dr32, D.dc32, c.stream);
       counted(c, (D.n_lu > 0) + (D.n_ilu > 0));
       return;
     }
@@ -1275,11 +1300,11 @@ extern "C" {
 // Device bytes fsi_build_hierarchy will allocate for this plan (same sizes as
 // build_device), used for admission by device memory.
 // largest element count of one colour / material group of the finest level
-static int max_color_group(const Ctx& c) {
+// elements of the largest launch_assemble_* call: all fluid or all solid
+// elements of the finest level (the 3D flux scratch holds min(this, chunk))
+static int max_assembly_batch(const Ctx& c) {
   const HostLevel& F = c.hl.back();
-  int m = 0;
-  for (size_t g = 0; g + 1 < F.color_ptr.size(); ++g) m = std::max(m, (int)(F.color_ptr[g + 1] - F.color_ptr[g]));
-  return m;
+  return (int)std::max(F.n_fluid_elem, F.n_elem - F.n_fluid_elem);
 }
 
 static int64_t estimate_device_bytes(const Ctx& c) {
@@ -1307,7 +1332,7 @@ static int64_t estimate_device_bytes(const Ctx& c) {
   b += F.Ni * 8.0 * 2 + (m + 1.0) * F.Ni * 8.0 + m * (double)F.Ni * fs + F.Ni * 8.0 * 4 + F.N * 8.0 * 2;
   if (mixed) b += F.Ni * 8.0;   // the widened preconditioned vector
   if (c.desc.transient != 0) b += F.Ni * 8.0;
-  if (c.dim == 3) b += (double)assemble_3d_scratch_doubles(max_color_group(c)) * 8.0;
+  if (c.dim == 3) b += (double)assemble_3d_scratch_doubles(max_assembly_batch(c)) * 8.0;
   double sum_dense = 0.0;
   for (size_t l = 1; l < L; ++l) sum_dense += (double)c.hl[l].dense_total;
   b += (mixed ? sum_dense : max_dense) * fs + F.n_elem * (double)nd * 8.0 + 1e6;
@@ -1386,7 +1411,10 @@ int fsi_build_hierarchy(const fsi_problem_desc* desc, const fsi_solver_opts* opt
     if (!coop) throw ApiError(FSI_E_CUDA, "device lacks cooperative launch");
     build_device(*c);
     c->tmp_re = dalloc<double>(*c, (size_t)c->hl.back().n_elem * c->ndofe);
-    if (c->dim == 3) c->asm_scratch = dalloc<double>(*c, assemble_3d_scratch_doubles(max_color_group(*c)));
+    if (c->dim == 3) {
+      c->asm_scratch_ne = max_assembly_batch(*c);
+      c->asm_scratch = dalloc<double>(*c, assemble_3d_scratch_doubles(c->asm_scratch_ne));
+    }
     std::vector<int32_t> pads = coarse_pads(*c);
     c->coarse_pad_list = upload(*c, pads);
     c->n_coarse_pads = (int)pads.size();

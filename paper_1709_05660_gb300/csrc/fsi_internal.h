@@ -41,6 +41,8 @@ struct HostLevel {
   std::vector<int32_t> elem_map;       // n_elem * (nloc+1)^2 block index or -1
   std::vector<int32_t> color_list;     // elements ordered by (color, material)
   std::vector<int32_t> color_ptr;      // (2^dim * 2) + 1 offsets into color_list
+  std::vector<int32_t> mat_list;       // elements: the fluid ones ascending, then the solid ones
+  int64_t n_fluid_elem = 0;
   // grid transfers from level-1 into this level (scalar CSR, internal indices)
   std::vector<int32_t> P_ptr, P_col;   // Ni rows
   std::vector<double> P_val;
@@ -104,6 +106,8 @@ struct DevLevel {
   int32_t* int_of_canon = nullptr;
   int32_t* elem_map = nullptr;
   int32_t* color_list = nullptr;
+  int32_t* mat_list = nullptr;
+  int64_t n_fluid_elem = 0;
   std::vector<int32_t> color_ptr;  // host copy
   int32_t *P_ptr = nullptr, *P_col = nullptr, *R_ptr = nullptr, *R_col = nullptr;
   double *P_val = nullptr, *R_val = nullptr;
@@ -115,6 +119,7 @@ struct DevLevel {
   // inverse (solid, or too large for ILU) and ILU(0) blocks (fluid)
   int32_t *sel_lu = nullptr, *sel_ilu = nullptr;
   int n_lu = 0, n_ilu = 0;
+  int ilu_max_n = 0, ilu_max_nb = 0;   // largest ILU(0) block: unknowns, node / element blocks
   // launch parameters (0 = built-in choice; set by fsi_set_launch_params)
   int apply_slices = 0, apply_groups = 0, spmv_sub = 0;
   int32_t *p_n = nullptr, *p_nown = nullptr;
@@ -157,6 +162,7 @@ struct Ctx {
   float* Z32 = nullptr;                  // preconditioned vectors (mixed path)
   double* zd = nullptr;                  // one of them widened to FP64 for the operator product
   double* asm_scratch = nullptr;         // 3D assembly: flux derivatives of one chunk of elements
+  int asm_scratch_ne = 0;                // elements of the largest pass the scratch was sized for
   bool mixed = false;
   double *w = nullptr, *xk = nullptr, *bk = nullptr, *tmp = nullptr;
   double* partial = nullptr;              // reduction partials

@@ -198,6 +198,13 @@ void build_pattern(HostLevel& L) {
     for (int32_t e : groups[g]) L.color_list.push_back(e);
     L.color_ptr[g + 1] = (int32_t)L.color_list.size();
   }
+  // element matrices need no colouring: fluid elements, then solid ones
+  L.mat_list.clear();
+  for (int pass = 0; pass < 2; ++pass)
+    for (int64_t e = 0; e < L.n_elem; ++e)
+      if ((L.elem_solid[e] != 0) == (pass == 1)) L.mat_list.push_back((int32_t)e);
+  L.n_fluid_elem = 0;
+  for (int64_t e = 0; e < L.n_elem; ++e) L.n_fluid_elem += L.elem_solid[e] == 0;
 }
 
 // Scalar node prolongation entries (fine node, coarse node, weight):

@@ -1250,11 +1250,12 @@ k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const in
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+bool launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st) {
+                        double* Ke, double* Re, int32_t* status, double* scratch, int scratch_ne, cudaStream_t st) {
   (void)scratch;
-  if (ne <= 0) return;
+  (void)scratch_ne;
+  if (ne <= 0) return true;
   const int grid = (ne + kEPB - 1) / kEPB;
   const size_t smem = (size_t)kEPB * asm_elem_doubles(pp.transient == 2 ? kNFVcn : kNFV) * sizeof(double);
   auto go = [&](auto kern) {
@@ -1271,6 +1272,7 @@ void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* 
     else if (pp.transient) go(k_assemble_2d<false, 1>);
     else go(k_assemble_2d<false, 0>);
   }
+  return true;
 }
 
 void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
@@ -1298,10 +1300,11 @@ void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nod
 
 namespace fsi {
 
-void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+bool launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st) {
-  if (ne <= 0) return;
+                        double* Ke, double* Re, int32_t* status, double* scratch, int scratch_ne, cudaStream_t st) {
+  if (ne <= 0) return true;
+  if (std::min(ne, k3Chunk) > scratch_ne) return false;   // the flux scratch holds scratch_ne elements
   const size_t smem = assemble_3d_smem();
   auto go = [&](auto flux, auto cols) {
     cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1320,7 +1323,24 @@ void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* 
     else if (pp.transient) go(k_flux_3d<false, 1>, k_assemble_3d<false>);
     else go(k_flux_3d<false, 0>, k_assemble_3d<false>);
   }
+  return true;
 }
+
+// FP64 operations executed per element (2 per DFMA, 1 per DMUL / DADD) by the
+// element-matrix kernels, counted with ncu on GB300 (sm_103a build of these
+// kernels) for each dimension, material and time discretisation (0 steady,
+// 1 BDF, 2 Crank-Nicolson; Mooney-Rivlin adds a few percent in the solid);
+// used for the FP64-ALU fraction of the assembly in the per-class timings.
+double assemble_flops_per_element(int dim, bool solid, int mode) {
+  static const double f2[2][3] = {{115524.0, 123226.0, 157692.0}, {87338.0, 94222.0, 106269.0}};
+  // 3D: flux derivatives + columns
+  static const double f3[2][3] = {{437386.0 + 5908383.0, 539270.0 + 5908383.0, 1057103.0 + 5908383.0},
+                                  {242394.0 + 4286875.0, 313563.0 + 4286875.0, 502750.0 + 4286875.0}};
+  mode = mode < 0 ? 0 : (mode > 2 ? 2 : mode);
+  return dim == 2 ? f2[solid][mode] : f3[solid][mode];
+}
+// the same count for the Galerkin kernels, per coarse element
+double galerkin_flops_per_coarse_element(int dim) { return dim == 2 ? 78133.0 : 3030039.0; }
 
 int assemble_launches(int dim, int ne) { return dim == 2 || ne <= 0 ? (ne > 0) : 2 * ((ne + k3Chunk - 1) / k3Chunk); }
 

@@ -97,52 +97,85 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
   const int64_t g0 = gmap_off[p], g1 = gmap_off[p + 1];
   if (n <= kGatherMaxN) {
     // scales from the block-sparse entries (row and column maxima by integer
-    // max on the bits of non-negative doubles), then one scattered write of
-    // the equilibrated entries: the dense block is written once
-    __shared__ unsigned long long rmx[kGatherMaxN], cmx[kGatherMaxN];
+    // max on the bits of non-negative values, 32-bit for FP32 blocks), then one
+    // scattered write of the equilibrated entries: the dense block is written
+    // once.  Each pass takes kU entries per thread at a time, their loads
+    // issued together (the passes are bound by the latency of these loads).
+    using Key = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
+    auto key = [](T a) -> Key {
+      if constexpr (sizeof(T) == 4) return __float_as_uint(fabsf(a));
+      else return (Key)__double_as_longlong(fabs(a));
+    };
+    auto val = [](Key k) -> double {
+      if constexpr (sizeof(T) == 4) return (double)__uint_as_float(k);
+      else return __longlong_as_double((long long)k);
+    };
+    __shared__ Key rmx[kGatherMaxN], cmx[kGatherMaxN];
     __shared__ T srw[kGatherMaxN], scl[kGatherMaxN];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) { rmx[i] = 0ull; cmx[i] = 0ull; }
+    constexpr int kU = 8;
+    const int64_t tot = (g1 - g0) * BB;
+    // entries t0, t0 + blockDim, ... (kU of them): value, dense position, kept?
+    auto fetch = [&](int64_t t0, T (&v)[kU], int (&ii)[kU], int (&jj)[kU], bool (&ok)[kU]) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t t = t0 + (int64_t)u * blockDim.x;
+        ok[u] = false;
+        v[u] = T(0);
+        ii[u] = jj[u] = 0;
+        if (t < tot) {
+          const int64_t g = g0 + t / BB;
+          const int e = (int)(t % BB);
+          ok[u] = gather_pos(gmap, bo, g, e, B, ii[u], jj[u]);
+          v[u] = T(bsr_val[(int64_t)gmap[3 * g] * BB + e]);
+        }
+      }
+    };
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { rmx[i] = 0; cmx[i] = 0; }
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
-      const int64_t g = g0 + t / BB;
-      const int e = (int)(t % BB);
-      int i, j;
-      if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
-      const double a = fabs((double)T(bsr_val[(int64_t)gmap[3 * g] * BB + e]));
-      atomicMax(&rmx[i], (unsigned long long)__double_as_longlong(a));
+    for (int64_t t0 = threadIdx.x; t0 < tot; t0 += (int64_t)kU * blockDim.x) {
+      T v[kU];
+      int ii[kU], jj[kU];
+      bool ok[kU];
+      fetch(t0, v, ii, jj, ok);
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (ok[u]) atomicMax(&rmx[ii[u]], key(v[u]));
     }
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x)
-      atomicMax(&rmx[padpos[t]], (unsigned long long)__double_as_longlong(1.0));
+      atomicMax(&rmx[padpos[t]], key(T(1)));
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) srw[i] = T(pow2_inv(__longlong_as_double((long long)rmx[i])));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) srw[i] = T(pow2_inv(val(rmx[i])));
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
-      const int64_t g = g0 + t / BB;
-      const int e = (int)(t % BB);
-      int i, j;
-      if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
-      const double a = fabs((double)(T(bsr_val[(int64_t)gmap[3 * g] * BB + e]) * srw[i]));
-      atomicMax(&cmx[j], (unsigned long long)__double_as_longlong(a));
+    for (int64_t t0 = threadIdx.x; t0 < tot; t0 += (int64_t)kU * blockDim.x) {
+      T v[kU];
+      int ii[kU], jj[kU];
+      bool ok[kU];
+      fetch(t0, v, ii, jj, ok);
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (ok[u]) atomicMax(&cmx[jj[u]], key(T(v[u] * srw[ii[u]])));
     }
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
       const int q = padpos[t];
-      atomicMax(&cmx[q], (unsigned long long)__double_as_longlong(fabs((double)(T(1) * srw[q]))));
+      atomicMax(&cmx[q], key(T(T(1) * srw[q])));
     }
     __syncthreads();
     T* Dr = dr + idx_off[p];
     T* Dc = dc + idx_off[p];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      scl[i] = T(pow2_inv(__longlong_as_double((long long)cmx[i])));
+      scl[i] = T(pow2_inv(val(cmx[i])));
       Dr[i] = srw[i];
       Dc[i] = scl[i];
     }
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < (g1 - g0) * BB; t += blockDim.x) {
-      const int64_t g = g0 + t / BB;
-      const int e = (int)(t % BB);
-      int i, j;
-      if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
-      D[(int64_t)i * n + j] = T(T(bsr_val[(int64_t)gmap[3 * g] * BB + e]) * srw[i]) * scl[j];
+    for (int64_t t0 = threadIdx.x; t0 < tot; t0 += (int64_t)kU * blockDim.x) {
+      T v[kU];
+      int ii[kU], jj[kU];
+      bool ok[kU];
+      fetch(t0, v, ii, jj, ok);
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (ok[u]) D[(int64_t)ii[u] * n + jj[u]] = T(v[u] * srw[ii[u]]) * scl[jj[u]];
     }
     __syncthreads();   // padding rows / columns of the block matrix hold zeros: the diagonal goes last
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
@@ -1433,39 +1466,58 @@ k_patch_ilu0(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n, c
 
 // One warp per block: y = D_r r, forward sweep with the unit lower factor and
 // backward sweep with the upper factor over node / element block rows (the
-// pattern's blocks only), x[own] += omega D_c y.
+// pattern's blocks only), x[own] += omega D_c y.  Per block row the lanes
+// share the products with the coupled blocks and stage the diagonal block in
+// shared memory; lane 0 then solves the (at most 6 x 6) diagonal block.
+// Shared memory is sized for the level's largest ILU block, so that many
+// blocks (warps) keep an SM busy: the sweeps are latency-bound.
 __global__ void __launch_bounds__(32)
 k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n,
                   const int32_t* __restrict__ p_nown, const int64_t* __restrict__ idx_off,
                   const int32_t* __restrict__ idx, const int64_t* __restrict__ own_off,
                   const int32_t* __restrict__ own, const int64_t* __restrict__ dense_off,
                   const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
-                  const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff, int B,
+                  const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff, int B, int max_n, int kw,
                   const float* __restrict__ dense, const float* __restrict__ r, float* __restrict__ x, float omega,
                   const float* __restrict__ dr, const float* __restrict__ dc) {
-  __shared__ uint32_t bm[kIluMaxNb * kIluWords];
-  __shared__ float y[kIluMaxRows];
-  __shared__ int16_t s_off[kIluMaxNb];
-  __shared__ int8_t s_w[kIluMaxNb];
+  extern __shared__ __align__(16) unsigned char ilu_smem[];
   const int p = sel[blockIdx.x];
   const int lane = threadIdx.x;
   const int n = p_n[p], nb = (int)(boff_off[p + 1] - boff_off[p]);
+  float* y = reinterpret_cast<float*>(ilu_smem);             // max_n
+  float* dg = y + max_n;                                      // 36: the diagonal block
+  uint32_t* bm = reinterpret_cast<uint32_t*>(dg + 36);        // nb x kw pattern bits
+  int16_t* s_off = reinterpret_cast<int16_t*>(bm + (size_t)nb * kw);
+  int8_t* s_w = reinterpret_cast<int8_t*>(s_off + nb);
   const float* D = dense + dense_off[p];
   const int32_t* id = idx + idx_off[p];
   const float* Dr = dr + idx_off[p];
   const float* Dc = dc + idx_off[p];
-  ilu_mask(bm, nb, gmap_off[p], gmap_off[p + 1], gmap);
-  ilu_blocks(s_off, s_w, nb, boff + boff_off[p]);
+  for (int t = lane; t < nb * kw; t += 32) bm[t] = 0u;
+  __syncwarp();
+  for (int64_t g = gmap_off[p] + lane; g < gmap_off[p + 1]; g += 32) {
+    const int lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
+    atomicOr(&bm[lr * kw + (lc >> 5)], 1u << (lc & 31));
+  }
+  const int32_t* bo = boff + boff_off[p];
+  for (int b = lane; b < nb; b += 32) {
+    const int32_t v = bo[b];
+    s_off[b] = (int16_t)(v >> 3);
+    s_w[b] = (int8_t)(v & 7);
+  }
   for (int i = lane; i < n; i += 32) y[i] = id[i] >= 0 ? Dr[i] * r[id[i]] : 0.f;
   __syncwarp();
+  auto bit = [&](int bi, int bj) { return (bm[bi * kw + (bj >> 5)] >> (bj & 31)) & 1u; };
   for (int dir = 0; dir < 2; ++dir) {   // 0: L (forward), 1: U (backward)
     for (int s = 0; s < nb; ++s) {
       const int bi = dir == 0 ? s : nb - 1 - s;
       const int oi = s_off[bi], wi = s_w[bi];
+      // the diagonal block (pattern: a node block is full, an element block diagonal)
+      for (int t = lane; t < wi * wi; t += 32) dg[t] = D[(int64_t)(oi + t / wi) * n + oi + t % wi];
       float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int lo = dir == 0 ? 0 : bi + 1, hi = dir == 0 ? bi : nb;
       for (int bk = lo + lane; bk < hi; bk += 32) {
-        if (!ilu_bit(bm, bi, bk)) continue;
+        if (!bit(bi, bk)) continue;
         const int ok = s_off[bk], wk = s_w[bk];
         for (int rr = 0; rr < wi; ++rr) {
           const float* Di = D + (int64_t)(oi + rr) * n + ok;
@@ -1478,21 +1530,21 @@ k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p
       for (int rr = 0; rr < 6; ++rr)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], o);
+      __syncwarp();
       if (lane == 0) {
-        const bool self = ilu_bit(bm, bi, bi);
+        const bool self = bit(bi, bi);
         for (int q = 0; q < wi; ++q) {
           const int rr = dir == 0 ? q : wi - 1 - q;
           const int i = oi + rr;
-          const float* Di = D + (int64_t)i * n + oi;
           float v = y[i] - acc[rr];
           if (self) {
             if (dir == 0) {
-              for (int c = 0; c < rr; ++c) v -= Di[c] * y[oi + c];
+              for (int c = 0; c < rr; ++c) v -= dg[rr * wi + c] * y[oi + c];
             } else {
-              for (int c = rr + 1; c < wi; ++c) v -= Di[c] * y[oi + c];
+              for (int c = rr + 1; c < wi; ++c) v -= dg[rr * wi + c] * y[oi + c];
             }
           }
-          y[i] = dir == 0 ? v : v / Di[rr];
+          y[i] = dir == 0 ? v : v / dg[rr * wi + rr];
         }
       }
       __syncwarp();
@@ -1513,14 +1565,18 @@ void launch_patch_ilu0(int nsel, const int32_t* sel, const int32_t* p_n, const i
   k_patch_ilu0<<<nsel, 256, 0, st>>>(sel, p_n, dense_off, gmap_off, gmap, boff_off, boff, B, dense, status);
 }
 
-void launch_patch_apply_ilu(int nsel, const int32_t* sel, const int32_t* p_n, const int32_t* p_nown,
-                            const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
-                            const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap,
-                            const int64_t* boff_off, const int32_t* boff, int B, const float* dense, const float* r,
-                            float* x, double omega, const float* dr, const float* dc, cudaStream_t st) {
+void launch_patch_apply_ilu(int nsel, int max_n, int max_nb, const int32_t* sel, const int32_t* p_n,
+                            const int32_t* p_nown, const int64_t* idx_off, const int32_t* idx, const int64_t* own_off,
+                            const int32_t* own, const int64_t* dense_off, const int64_t* gmap_off,
+                            const int32_t* gmap, const int64_t* boff_off, const int32_t* boff, int B,
+                            const float* dense, const float* r, float* x, double omega, const float* dr,
+                            const float* dc, cudaStream_t st) {
   if (nsel <= 0) return;
-  k_patch_apply_ilu<<<nsel, 32, 0, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off, gmap,
-                                         boff_off, boff, B, dense, r, x, (float)omega, dr, dc);
+  const int kw = (max_nb + 31) / 32;
+  const size_t smem = (size_t)(max_n + 36) * sizeof(float) + (size_t)max_nb * kw * sizeof(uint32_t) +
+                      (size_t)max_nb * (sizeof(int16_t) + sizeof(int8_t)) + 16;
+  k_patch_apply_ilu<<<nsel, 32, smem, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off, gmap,
+                                            boff_off, boff, B, max_n, kw, dense, r, x, (float)omega, dr, dc);
 }
 
 #define FSI_INST(T)                                                                                              \

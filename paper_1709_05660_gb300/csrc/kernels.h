@@ -20,15 +20,18 @@ struct PhysParams {
 };
 
 // k_assemble.cu
-// scratch: 3D only, assemble_3d_scratch_doubles(largest ne of one launch) doubles (2D: unused)
-void launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+// scratch: 3D only, assemble_3d_scratch_doubles(scratch_ne) doubles (2D: unused); false (nothing
+// launched) when one pass of ne elements needs more scratch than that
+bool launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st);
-void launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
+                        double* Ke, double* Re, int32_t* status, double* scratch, int scratch_ne, cudaStream_t st);
+bool launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* y, const int32_t* elem_nodes,
                         const uint8_t* node_class, const double* elem_geo, int64_t n_nodes, PhysParams pp,
-                        double* Ke, double* Re, int32_t* status, double* scratch, cudaStream_t st);
+                        double* Ke, double* Re, int32_t* status, double* scratch, int scratch_ne, cudaStream_t st);
 size_t assemble_3d_scratch_doubles(int max_ne);
 int assemble_launches(int dim, int ne);   // kernel launches of one launch_assemble_* call
+double assemble_flops_per_element(int dim, bool solid, int mode);   // executed FP64 flops (ncu count)
+double galerkin_flops_per_coarse_element(int dim);
 void launch_scatter_3d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
                        const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st);
 void launch_galerkin_3d(int ncx, int ncy, int ncz, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
@@ -123,8 +126,10 @@ constexpr int kIluMaxRows = 1024;
 void launch_patch_ilu0(int nsel, const int32_t* sel, const int32_t* p_n, const int64_t* dense_off,
                        const int64_t* gmap_off, const int32_t* gmap, const int64_t* boff_off, const int32_t* boff,
                        int B, float* dense, int32_t* status, cudaStream_t st);
-// x[own] += omega (R^0)^T U^{-1} L^{-1} R^delta r for the ILU(0) blocks in sel
-void launch_patch_apply_ilu(int nsel, const int32_t* sel, const int32_t* p_n, const int32_t* p_nown,
+// x[own] += omega (R^0)^T U^{-1} L^{-1} R^delta r for the ILU(0) blocks in sel (at most max_n
+// unknowns and max_nb node / element blocks each)
+void launch_patch_apply_ilu(int nsel, int max_n, int max_nb, const int32_t* sel, const int32_t* p_n,
+                            const int32_t* p_nown,
                             const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                             const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap,
                             const int64_t* boff_off, const int32_t* boff, int B, const float* dense, const float* r,
