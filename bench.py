@@ -1040,7 +1040,8 @@ def run_profile_case(args):
     `gj` factors the 6-level channel's Schwarz blocks on the 4-level mesh
     (the same block sizes, 337 blocks in one launch) twice; `spmv` runs two
     V-cycles of the 5-level channel (residual vectors and matrices larger than
-    L2); `asm` assembles small 2D and 3D problems once in each time
+    L2); `ilu` does the same with ILU(0) fluid blocks at mean inflow 0.2;
+    `asm` assembles small 2D and 3D problems once in each time
     discretisation.  Prints the unknowns and the device bytes held."""
     import torch
     from dataclasses import replace
@@ -1069,6 +1070,8 @@ def run_profile_case(args):
         return
     prob, opts = CONFIGS[args.config]
     prob = replace(prob, levels=4 if args.profile_case == "gj" else 5)
+    if args.profile_case == "ilu":   # ILU(0) fluid blocks at the inflow where they converge
+        prob, opts = replace(prob, U=0.2), replace(opts, local_solver=1)
     s = fsi.FSI(prob, replace(opts, precision=1), stream=torch.cuda.current_stream().cuda_stream)
     N = int(s.N[-1])
     y = torch.empty(N, dtype=torch.float64, device="cuda")
@@ -1077,7 +1080,7 @@ def run_profile_case(args):
     s.assemble()
     for _ in range(2):
         s.factor()
-    if args.profile_case == "spmv":
+    if args.profile_case in ("spmv", "ilu"):
         z = torch.empty(N, dtype=torch.float64, device="cuda")
         b = torch.randn(N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
         for _ in range(2):
@@ -1136,7 +1139,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="paper-settings parameter studies instead")
     ap.add_argument("--sweep-config", default="channel2d_l5")
     ap.add_argument("--sweep-precision", type=int, default=1)
-    ap.add_argument("--profile-case", choices=["gj", "spmv", "asm"], default=None,
+    ap.add_argument("--profile-case", choices=["gj", "spmv", "asm", "ilu"], default=None,
                     help="run one small case of a kernel for an ncu capture instead")
     ap.add_argument("--_cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_out", default=None, help=argparse.SUPPRESS)

@@ -238,7 +238,7 @@ void build_device(Ctx& c) {
       D.p_gmap_off = upload(c, H.p_gmap_off); D.p_pad_off = upload(c, H.p_pad_off);
       D.p_idx = upload(c, H.p_idx); D.p_own = upload(c, H.p_own);
       D.p_gmap = upload(c, H.p_gmap); D.p_padpos = upload(c, H.p_padpos);
-      D.p_boff = upload(c, H.p_boff); D.p_boff_off = upload(c, H.p_boff_off);
+      D.p_boff = upload(c, H.p_boff); D.p_boff_off = upload(c, H.p_boff_off); D.p_gptr = upload(c, H.p_gptr);
       D.inv_total = H.inv_total;
       D.dense_total = H.dense_total;
       if (c.mixed) {
@@ -855,8 +855,8 @@ template <> struct VC<float> {
                                   D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32, c.sm_count,
                                   D.apply_slices, D.apply_groups, c.stream, D.sel_lu);
       launch_patch_apply_ilu(D.n_ilu, D.ilu_max_n, D.ilu_max_nb, D.sel_ilu, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
-                             D.p_own_off, D.p_own, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff, c.B,
-                             level_ws(c, l), r, x, c.opts.omega, D.dr32, D.dc32, c.stream);
+                             D.p_own_off, D.p_own, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff,
+                             D.p_gptr, c.B, level_ws(c, l), r, x, c.opts.omega, D.dr32, D.dc32, c.stream);
       counted(c, (D.n_lu > 0) + (D.n_ilu > 0));
       return;
     }
@@ -1322,7 +1322,8 @@ static int64_t estimate_device_bytes(const Ctx& c) {
       b += (H.P_ptr.size() + H.R_ptr.size() + H.S_ptr.size()) * 4.0 +
            (H.P_col.size() + H.R_col.size() + H.S_col.size()) * 12.0;
       b += H.idx_total * 4.0 + H.own_total * 4.0 + H.n_patches * 9.0 * 8.0 + H.p_gmap.size() * 4.0 +
-           H.p_padpos.size() * 4.0 + H.p_boff.size() * 4.0 + H.inv_total * fs + 2.0 * H.idx_total * fs;
+           H.p_padpos.size() * 4.0 + (H.p_boff.size() + H.p_gptr.size()) * 4.0 + H.inv_total * fs +
+           2.0 * H.idx_total * fs;
       if (mixed) b += H.nnzb * B * B * 4.0 + (H.P_col.size() + H.R_col.size()) * 4.0 + H.Ni * 3.0 * 4.0;
       max_dense = std::max(max_dense, (double)H.dense_total);
     }

@@ -66,6 +66,10 @@ struct HostLevel {
   std::vector<int32_t> p_padpos;               // patch-local pad positions (identity diag), flat
   std::vector<int32_t> p_boff;                 // per local block: dense offset * 8 + width (B or dim + 1)
   std::vector<int64_t> p_boff_off;             // into p_boff
+  // per local block row: first p_gmap entry of the row, relative to the
+  // block's first entry, plus one end entry per block (at p_boff_off[p] + p);
+  // a row's entries are in ascending local column order
+  std::vector<int32_t> p_gptr;
   std::vector<int64_t> p_pad_off;
   std::vector<int32_t> p_elems;                // elements of each patch (for export)
   std::vector<int64_t> p_elem_off;
@@ -127,6 +131,7 @@ struct DevLevel {
           *p_gmap_off = nullptr, *p_pad_off = nullptr;
   int32_t *p_idx = nullptr, *p_own = nullptr, *p_gmap = nullptr, *p_padpos = nullptr, *p_boff = nullptr;
   int64_t* p_boff_off = nullptr;
+  int32_t* p_gptr = nullptr;
   double* inv = nullptr;          // owned rows of B~_k^{-1} (equilibrated block)
   double *dr = nullptr, *dc = nullptr;     // row / column scales of each block (FP64 path)
   float *dr32 = nullptr, *dc32 = nullptr;  // (mixed path)

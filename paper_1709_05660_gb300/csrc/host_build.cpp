@@ -346,6 +346,7 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
   L.p_inv_off.assign(np + 1, 0); L.p_gmap_off.assign(np + 1, 0); L.p_pad_off.assign(np + 1, 0);
   L.p_elem_off.assign(np + 1, 0); L.p_boff_off.assign(np + 1, 0);
   L.p_idx.clear(); L.p_own.clear(); L.p_gmap.clear(); L.p_padpos.clear(); L.p_elems.clear(); L.p_boff.clear();
+  L.p_gptr.clear();
   L.max_n = 0;
   L.max_nown = 0;
   for (int p = 0; p < np; ++p) {
@@ -390,8 +391,10 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
     }
     L.p_nown[p] = nown;
     L.max_nown = std::max(L.max_nown, nown);
+    const int64_t g_first = (int64_t)L.p_gmap.size() / 3;
     for (int lb = 0; lb < nbk; ++lb) {
       const int32_t br = blocks[lb];
+      L.p_gptr.push_back((int32_t)((int64_t)L.p_gmap.size() / 3 - g_first));
       for (int32_t k = L.rowptr[br]; k < L.rowptr[br + 1]; ++k) {
         auto it = std::lower_bound(blocks.begin(), blocks.end(), L.col[k]);
         if (it != blocks.end() && *it == L.col[k]) {
@@ -410,6 +413,7 @@ void build_patches(const fsi_solver_opts& o, HostLevel& L) {
     L.p_pad_off[p + 1] = (int64_t)L.p_padpos.size();
     L.p_elem_off[p + 1] = (int64_t)L.p_elems.size();
     L.p_boff_off[p + 1] = (int64_t)L.p_boff.size();
+    L.p_gptr.push_back((int32_t)((int64_t)L.p_gmap.size() / 3 - g_first));   // row pointers end
   }
   L.dense_total = L.p_dense_off[np];
   L.inv_total = L.p_inv_off[np];

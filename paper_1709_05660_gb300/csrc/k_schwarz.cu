@@ -1465,40 +1465,38 @@ k_patch_ilu0(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n, c
 }
 
 // One warp per block: y = D_r r, forward sweep with the unit lower factor and
-// backward sweep with the upper factor over node / element block rows (the
-// pattern's blocks only), x[own] += omega D_c y.  Per block row the lanes
-// share the products with the coupled blocks and stage the diagonal block in
-// shared memory; lane 0 then solves the (at most 6 x 6) diagonal block.
-// Shared memory is sized for the level's largest ILU block, so that many
-// blocks (warps) keep an SM busy: the sweeps are latency-bound.
+// backward sweep with the upper factor over node / element block rows, then
+// x[own] += omega D_c y.  A block row's entries come from the block's pattern
+// (row pointers built on the host, columns ascending): the lower part is the
+// entries left of the diagonal block, the upper part those right of it.  The
+// factor entries of the next block row (its first 32 coupled blocks, one per
+// lane, and its diagonal block) are loaded while the current row is reduced
+// and solved, so a row waits on shared memory rather than on a fresh load.
+template <int B>
 __global__ void __launch_bounds__(32)
 k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n,
                   const int32_t* __restrict__ p_nown, const int64_t* __restrict__ idx_off,
                   const int32_t* __restrict__ idx, const int64_t* __restrict__ own_off,
                   const int32_t* __restrict__ own, const int64_t* __restrict__ dense_off,
                   const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
-                  const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff, int B, int max_n, int kw,
-                  const float* __restrict__ dense, const float* __restrict__ r, float* __restrict__ x, float omega,
-                  const float* __restrict__ dr, const float* __restrict__ dc) {
+                  const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff,
+                  const int32_t* __restrict__ gptr, int max_n, const float* __restrict__ dense,
+                  const float* __restrict__ r, float* __restrict__ x, float omega, const float* __restrict__ dr,
+                  const float* __restrict__ dc) {
   extern __shared__ __align__(16) unsigned char ilu_smem[];
   const int p = sel[blockIdx.x];
   const int lane = threadIdx.x;
   const int n = p_n[p], nb = (int)(boff_off[p + 1] - boff_off[p]);
-  float* y = reinterpret_cast<float*>(ilu_smem);             // max_n
-  float* dg = y + max_n;                                      // 36: the diagonal block
-  uint32_t* bm = reinterpret_cast<uint32_t*>(dg + 36);        // nb x kw pattern bits
-  int16_t* s_off = reinterpret_cast<int16_t*>(bm + (size_t)nb * kw);
+  float* y = reinterpret_cast<float*>(ilu_smem);              // max_n
+  float* dg = y + max_n;                                       // B x B: the diagonal block
+  int16_t* s_off = reinterpret_cast<int16_t*>(dg + B * B);
   int8_t* s_w = reinterpret_cast<int8_t*>(s_off + nb);
   const float* D = dense + dense_off[p];
   const int32_t* id = idx + idx_off[p];
   const float* Dr = dr + idx_off[p];
   const float* Dc = dc + idx_off[p];
-  for (int t = lane; t < nb * kw; t += 32) bm[t] = 0u;
-  __syncwarp();
-  for (int64_t g = gmap_off[p] + lane; g < gmap_off[p + 1]; g += 32) {
-    const int lr = gmap[3 * g + 1], lc = gmap[3 * g + 2];
-    atomicOr(&bm[lr * kw + (lc >> 5)], 1u << (lc & 31));
-  }
+  const int32_t* gp = gptr + boff_off[p] + p;                  // nb + 1 row pointers
+  const int32_t* gm = gmap + 3 * gmap_off[p];
   const int32_t* bo = boff + boff_off[p];
   for (int b = lane; b < nb; b += 32) {
     const int32_t v = bo[b];
@@ -1507,44 +1505,105 @@ k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p
   }
   for (int i = lane; i < n; i += 32) y[i] = id[i] >= 0 ? Dr[i] * r[id[i]] : 0.f;
   __syncwarp();
-  auto bit = [&](int bi, int bj) { return (bm[bi * kw + (bj >> 5)] >> (bj & 31)) & 1u; };
+  // entry t of block row bi on the given side of the diagonal: its column
+  // block (-1: none) and factor values (row-major wi x wk, zero-padded to B x B)
+  auto fetch = [&](int bi, int t, bool lower, int& bk, bool& diag, float (&v)[B * B]) {
+    bk = -1;
+    diag = false;
+    const int e0 = gp[bi], e1 = gp[bi + 1];
+    if (e0 + t < e1) {
+      const int c = gm[3 * (e0 + t) + 2];
+      if (lower ? c < bi : c > bi) bk = c;
+      diag = c == bi;
+    }
+    const int oi = s_off[bi], wi = s_w[bi];
+    const int ok = bk >= 0 ? s_off[bk] : 0, wk = bk >= 0 ? s_w[bk] : 0;
+#pragma unroll
+    for (int rr = 0; rr < B; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < B; ++cc)
+        v[rr * B + cc] = (bk >= 0 && rr < wi && cc < wk) ? D[(int64_t)(oi + rr) * n + ok + cc] : 0.f;
+  };
+  // entries lane and lane + 32 (< wi * wi <= 36) of block row bi's diagonal block
+  auto fetch_diag = [&](int bi, float& d0, float& d1) {
+    const int oi = s_off[bi], wi = s_w[bi];
+    const int q1 = lane + 32;
+    d0 = lane < wi * wi ? D[(int64_t)(oi + lane / wi) * n + oi + lane % wi] : 0.f;
+    d1 = q1 < wi * wi ? D[(int64_t)(oi + q1 / wi) * n + oi + q1 % wi] : 0.f;
+  };
   for (int dir = 0; dir < 2; ++dir) {   // 0: L (forward), 1: U (backward)
+    const bool lower = dir == 0;
+    int bk_n;
+    bool dd_n;
+    float v_n[B * B];
+    float dg_n = 0.f, dg_n1 = 0.f;
+    if (nb > 0) {
+      const int b0 = lower ? 0 : nb - 1;
+      fetch(b0, lane, lower, bk_n, dd_n, v_n);
+      fetch_diag(b0, dg_n, dg_n1);
+    }
     for (int s = 0; s < nb; ++s) {
-      const int bi = dir == 0 ? s : nb - 1 - s;
+      const int bi = lower ? s : nb - 1 - s;
       const int oi = s_off[bi], wi = s_w[bi];
-      // the diagonal block (pattern: a node block is full, an element block diagonal)
-      for (int t = lane; t < wi * wi; t += 32) dg[t] = D[(int64_t)(oi + t / wi) * n + oi + t % wi];
-      float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const int lo = dir == 0 ? 0 : bi + 1, hi = dir == 0 ? bi : nb;
-      for (int bk = lo + lane; bk < hi; bk += 32) {
-        if (!bit(bi, bk)) continue;
-        const int ok = s_off[bk], wk = s_w[bk];
-        for (int rr = 0; rr < wi; ++rr) {
-          const float* Di = D + (int64_t)(oi + rr) * n + ok;
-          float a = 0.f;
-          for (int c = 0; c < wk; ++c) a += Di[c] * y[ok + c];
-          acc[rr] += a;
+      const int bk = bk_n;
+      bool has_diag = dd_n;   // the pattern holds block row bi's diagonal block (node blocks)
+      float v[B * B];
+#pragma unroll
+      for (int q = 0; q < B * B; ++q) v[q] = v_n[q];
+      if (lane < wi * wi) dg[lane] = dg_n;
+      if (lane + 32 < wi * wi) dg[lane + 32] = dg_n1;
+      float acc[B];
+#pragma unroll
+      for (int rr = 0; rr < B; ++rr) acc[rr] = 0.f;
+      if (bk >= 0) {
+        const int ok = s_off[bk];
+#pragma unroll
+        for (int rr = 0; rr < B; ++rr)
+#pragma unroll
+          for (int cc = 0; cc < B; ++cc) acc[rr] += v[rr * B + cc] * (cc < s_w[bk] ? y[ok + cc] : 0.f);
+      }
+      // coupled blocks beyond the first 32 (3D), loaded now
+      for (int t = 32 + lane; t < gp[bi + 1] - gp[bi]; t += 32) {
+        int b2;
+        bool d2;
+        float w2[B * B];
+        fetch(bi, t, lower, b2, d2, w2);
+        has_diag |= d2;
+        if (b2 >= 0) {
+          const int o2 = s_off[b2], k2 = s_w[b2];
+#pragma unroll
+          for (int rr = 0; rr < B; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < B; ++cc) acc[rr] += w2[rr * B + cc] * (cc < k2 ? y[o2 + cc] : 0.f);
         }
       }
+      // the next block row's entries, loaded during the reduction and solve below
+      if (s + 1 < nb) {
+        const int bn = lower ? bi + 1 : bi - 1;
+        fetch(bn, lane, lower, bk_n, dd_n, v_n);
+        fetch_diag(bn, dg_n, dg_n1);
+      }
+      const bool self = __any_sync(0xffffffffu, has_diag);
 #pragma unroll
-      for (int rr = 0; rr < 6; ++rr)
+      for (int rr = 0; rr < B; ++rr)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], o);
       __syncwarp();
       if (lane == 0) {
-        const bool self = bit(bi, bi);
+        // a block in the pattern with itself (node blocks) is a full diagonal
+        // block; otherwise only its diagonal is kept (element blocks)
         for (int q = 0; q < wi; ++q) {
-          const int rr = dir == 0 ? q : wi - 1 - q;
+          const int rr = lower ? q : wi - 1 - q;
           const int i = oi + rr;
-          float v = y[i] - acc[rr];
+          float vv = y[i] - acc[rr];
           if (self) {
-            if (dir == 0) {
-              for (int c = 0; c < rr; ++c) v -= dg[rr * wi + c] * y[oi + c];
+            if (lower) {
+              for (int c = 0; c < rr; ++c) vv -= dg[rr * wi + c] * y[oi + c];
             } else {
-              for (int c = rr + 1; c < wi; ++c) v -= dg[rr * wi + c] * y[oi + c];
+              for (int c = rr + 1; c < wi; ++c) vv -= dg[rr * wi + c] * y[oi + c];
             }
           }
-          y[i] = dir == 0 ? v : v / dg[rr * wi + rr];
+          y[i] = lower ? vv : vv / dg[rr * wi + rr];
         }
       }
       __syncwarp();
@@ -1568,15 +1627,17 @@ void launch_patch_ilu0(int nsel, const int32_t* sel, const int32_t* p_n, const i
 void launch_patch_apply_ilu(int nsel, int max_n, int max_nb, const int32_t* sel, const int32_t* p_n,
                             const int32_t* p_nown, const int64_t* idx_off, const int32_t* idx, const int64_t* own_off,
                             const int32_t* own, const int64_t* dense_off, const int64_t* gmap_off,
-                            const int32_t* gmap, const int64_t* boff_off, const int32_t* boff, int B,
-                            const float* dense, const float* r, float* x, double omega, const float* dr,
+                            const int32_t* gmap, const int64_t* boff_off, const int32_t* boff, const int32_t* gptr,
+                            int B, const float* dense, const float* r, float* x, double omega, const float* dr,
                             const float* dc, cudaStream_t st) {
   if (nsel <= 0) return;
-  const int kw = (max_nb + 31) / 32;
-  const size_t smem = (size_t)(max_n + 36) * sizeof(float) + (size_t)max_nb * kw * sizeof(uint32_t) +
-                      (size_t)max_nb * (sizeof(int16_t) + sizeof(int8_t)) + 16;
-  k_patch_apply_ilu<<<nsel, 32, smem, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off, gmap,
-                                            boff_off, boff, B, max_n, kw, dense, r, x, (float)omega, dr, dc);
+  const size_t smem = (size_t)(max_n + 36) * sizeof(float) + (size_t)max_nb * (sizeof(int16_t) + sizeof(int8_t)) + 16;
+  if (B == 4)
+    k_patch_apply_ilu<4><<<nsel, 32, smem, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off,
+                                                 gmap, boff_off, boff, gptr, max_n, dense, r, x, (float)omega, dr, dc);
+  else
+    k_patch_apply_ilu<6><<<nsel, 32, smem, st>>>(sel, p_n, p_nown, idx_off, idx, own_off, own, dense_off, gmap_off,
+                                                 gmap, boff_off, boff, gptr, max_n, dense, r, x, (float)omega, dr, dc);
 }
 
 #define FSI_INST(T)                                                                                              \

@@ -132,8 +132,9 @@ void launch_patch_apply_ilu(int nsel, int max_n, int max_nb, const int32_t* sel,
                             const int32_t* p_nown,
                             const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                             const int64_t* dense_off, const int64_t* gmap_off, const int32_t* gmap,
-                            const int64_t* boff_off, const int32_t* boff, int B, const float* dense, const float* r,
-                            float* x, double omega, const float* dr, const float* dc, cudaStream_t st);
+                            const int64_t* boff_off, const int32_t* boff, const int32_t* gptr, int B,
+                            const float* dense, const float* r, float* x, double omega, const float* dr,
+                            const float* dc, cudaStream_t st);
 // Launch shape of one level's Schwarz apply: kind 0 = one block per patch
 // (k_patch_apply_t), kind 1 = `slices` row slices per patch of `vps` owned-row
 // vectors, `groups` column groups per block (k_patch_apply_rows).
