@@ -172,6 +172,10 @@ void check_status(Ctx& c) {
   ck(cudaMemcpyAsync(st, c.status, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "D2H status");
   sync(c);
   ck(cudaMemsetAsync(c.status, 0, sizeof(st), c.stream), "memset");
+#ifdef FSI_BOUNDS_CHECK
+  for (int site : {bounds_site_schwarz(), bounds_site_linalg()})
+    if (site) throw ApiError(FSI_E_CUDA, "index out of range at bounds-check site " + std::to_string(site));
+#endif
   if (st[ST_TIMEOUT]) throw ApiError(FSI_E_TIMEOUT, "a bounded wait on the tensor core gave up");
   if (st[ST_TANGLED]) throw ApiError(FSI_E_MESH_TANGLED, "det F <= 0 at a quadrature point");
   if (st[ST_NONFINITE]) throw ApiError(FSI_E_NONFINITE, "non-finite values");
@@ -807,7 +811,7 @@ template <> struct VC<double> {
   static void apply(Ctx& c, int l, const double* r, double* x) {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes, D.apply_flops);
-    launch_patch_apply_t<double>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
+    launch_patch_apply_t<double>(D.n_patches, D.Ni, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
                                  D.p_own_off, D.p_own, D.p_inv_off, D.inv, r, x, c.opts.omega, D.dr, D.dc,
                                  c.sm_count, D.apply_slices, D.apply_groups, c.stream);
     counted(c);
@@ -851,7 +855,7 @@ template <> struct VC<float> {
     DevLevel& D = c.dl[l];
     Prof pr(c, FSI_K_PATCH_APPLY, D.apply_bytes32, D.apply_flops);
     if (c.opts.local_solver == 1) {   // exact inverses of the solid blocks, ILU(0) solves of the fluid ones
-      launch_patch_apply_t<float>(D.n_lu, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off,
+      launch_patch_apply_t<float>(D.n_lu, D.Ni, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx, D.p_own_off,
                                   D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32, c.sm_count,
                                   D.apply_slices, D.apply_groups, c.stream, D.sel_lu);
       launch_patch_apply_ilu(D.n_ilu, D.ilu_max_n, D.ilu_max_nb, D.sel_ilu, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
@@ -860,7 +864,7 @@ template <> struct VC<float> {
       counted(c, (D.n_lu > 0) + (D.n_ilu > 0));
       return;
     }
-    launch_patch_apply_t<float>(D.n_patches, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
+    launch_patch_apply_t<float>(D.n_patches, D.Ni, D.max_n, D.max_nown, D.p_n, D.p_nown, D.p_idx_off, D.p_idx,
                                 D.p_own_off, D.p_own, D.p_inv_off, D.inv32, r, x, c.opts.omega, D.dr32, D.dc32,
                                 c.sm_count, D.apply_slices, D.apply_groups, c.stream);
     counted(c);

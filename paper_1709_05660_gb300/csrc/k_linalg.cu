@@ -11,6 +11,7 @@
 
 #include <cmath>
 
+#include "bounds.cuh"
 #include "kernels.h"
 
 namespace cg = cooperative_groups;
@@ -100,10 +101,12 @@ __global__ void k_bsr_residual(int64_t nb, const int32_t* __restrict__ rowptr, c
   int32_t k = rowptr[br];
   for (; k + 1 < k1; k += 2) {
     const int64_t c0 = __ldg(col + k), c1 = __ldg(col + k + 1);
-    acc0 += block_row_dot<B, TV, TX, TY>(val + (int64_t)k * B * B + ci * B, x + c0 * B);
-    acc1 += block_row_dot<B, TV, TX, TY>(val + (int64_t)(k + 1) * B * B + ci * B, x + c1 * B);
+    if (FSI_IN(c0, nb, FSI_SITE(2))) acc0 += block_row_dot<B, TV, TX, TY>(val + (int64_t)k * B * B + ci * B, x + c0 * B);
+    if (FSI_IN(c1, nb, FSI_SITE(2)))
+      acc1 += block_row_dot<B, TV, TX, TY>(val + (int64_t)(k + 1) * B * B + ci * B, x + c1 * B);
   }
-  if (k < k1) acc0 += block_row_dot<B, TV, TX, TY>(val + (int64_t)k * B * B + ci * B, x + (int64_t)__ldg(col + k) * B);
+  if (k < k1 && FSI_IN(__ldg(col + k), nb, FSI_SITE(2)))
+    acc0 += block_row_dot<B, TV, TX, TY>(val + (int64_t)k * B * B + ci * B, x + (int64_t)__ldg(col + k) * B);
   const TY acc = acc0 + acc1;
   y[i] = b ? b[i] - acc : acc;
 }
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(256, 8) k_bsr4_residual_sub(int64_t nb, const 
       for (int u = 0; u < R; ++u) {
         const int32_t k = kb + u * SUB;
         c[u] = k < k1 ? __ldg(col + k) : -1;
+        if (c[u] >= 0 && !FSI_IN(c[u], nb, FSI_SITE(2))) c[u] = -1;
         if (k < k1) v[u].load(val + (int64_t)k * B * B + ci * B);
         else v[u].zero();
       }
@@ -497,8 +501,9 @@ __global__ void k_dense_gather(int B, int64_t nb, const int32_t* __restrict__ ro
   for (int32_t k = rowptr[br]; k < rowptr[br + 1]; ++k)
     for (int e = threadIdx.x; e < BB; e += blockDim.x) {
       const int ci = e / B, cj = e % B;
+      if (!FSI_IN(col[k], nb, FSI_SITE(2))) continue;
       const int64_t r = perm[br * B + ci], c = perm[(int64_t)col[k] * B + cj];
-      A[c * n + r] = val[(int64_t)k * BB + e];
+      if (FSI_IN(r, n, FSI_SITE(2)) && FSI_IN(c, n, FSI_SITE(2))) A[c * n + r] = val[(int64_t)k * BB + e];
     }
 }
 
@@ -507,7 +512,7 @@ __global__ void k_set_diag(const int32_t* __restrict__ list, int cnt, const int3
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < cnt) {
     const int64_t q = perm[list[t]];
-    A[q * n + q] = 1.0;
+    if (FSI_IN(q, n, FSI_SITE(2))) A[q * n + q] = 1.0;
   }
 }
 
@@ -1009,5 +1014,8 @@ void launch_gemv_sub(int m, int nc, double alpha, const double* A, int64_t lda, 
     k_gemv_sub_part<<<dim3((unsigned)((m + 255) / 256), (unsigned)nchunk), 256, 0, st>>>(m, nc, A, lda, x, part);
   k_gemv_sub_sum<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, nchunk, part, alpha, beta, y);
 }
+
+// the bounds-check build's recorded site of this translation unit (0: none)
+FSI_BOUNDS_READER(bounds_site_linalg)
 
 }  // namespace fsi

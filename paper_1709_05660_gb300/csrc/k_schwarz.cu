@@ -16,6 +16,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "bounds.cuh"
 #include "kernels.h"
 #include "tc_util.cuh"
 
@@ -126,6 +127,7 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
           const int64_t g = g0 + t / BB;
           const int e = (int)(t % BB);
           ok[u] = gather_pos(gmap, bo, g, e, B, ii[u], jj[u]);
+          ok[u] = ok[u] && FSI_IN(ii[u], n, FSI_SITE(1)) && FSI_IN(jj[u], n, FSI_SITE(1));
           v[u] = T(bsr_val[(int64_t)gmap[3 * g] * BB + e]);
         }
       }
@@ -142,7 +144,7 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
         if (ok[u]) atomicMax(&rmx[ii[u]], key(v[u]));
     }
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x)
-      atomicMax(&rmx[padpos[t]], key(T(1)));
+      if (FSI_IN(padpos[t], n, FSI_SITE(1))) atomicMax(&rmx[padpos[t]], key(T(1)));
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) srw[i] = T(pow2_inv(val(rmx[i])));
     __syncthreads();
@@ -157,7 +159,7 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
     }
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
       const int q = padpos[t];
-      atomicMax(&cmx[q], key(T(T(1) * srw[q])));
+      if (FSI_IN(q, n, FSI_SITE(1))) atomicMax(&cmx[q], key(T(T(1) * srw[q])));
     }
     __syncthreads();
     T* Dr = dr + idx_off[p];
@@ -180,7 +182,7 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
     __syncthreads();   // padding rows / columns of the block matrix hold zeros: the diagonal goes last
     for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
       const int q = padpos[t];
-      D[(int64_t)q * n + q] = T(T(1) * srw[q]) * scl[q];
+      if (FSI_IN(q, n, FSI_SITE(1))) D[(int64_t)q * n + q] = T(T(1) * srw[q]) * scl[q];
     }
     return;
   }
@@ -189,12 +191,13 @@ __global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t*
     const int e = (int)(t % BB);
     int i, j;
     if (!gather_pos(gmap, bo, g, e, B, i, j)) continue;
+    if (!FSI_IN(i, n, FSI_SITE(1)) || !FSI_IN(j, n, FSI_SITE(1))) continue;
     D[(int64_t)i * n + j] = T(bsr_val[(int64_t)gmap[3 * g] * BB + e]);
   }
   __syncthreads();
   for (int64_t t = pad_off[p] + threadIdx.x; t < pad_off[p + 1]; t += blockDim.x) {
     const int q = padpos[t];
-    D[(int64_t)q * n + q] = T(1);
+    if (FSI_IN(q, n, FSI_SITE(1))) D[(int64_t)q * n + q] = T(1);
   }
   __syncthreads();
   T* Dr = dr + idx_off[p];
@@ -298,7 +301,8 @@ k_patch_gj_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (FSI_IN(piv[k], n, FSI_SITE(1))) qinv[piv[k]] = k;
   __syncthreads();
   // owned rows of the inverse, written transposed through a shared tile
   const int nown = p_nown[p];
@@ -309,7 +313,7 @@ k_patch_gj_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_nown
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int oo = t / 32, cc = t % 32;
         const int o = o0 + oo, c = c0 + cc;
-        if (o < nown && c < n) tile[oo][cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
+        if (o < nown && c < n && FSI_IN(ow[o], n, FSI_SITE(1))) tile[oo][cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
       }
       __syncthreads();
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
@@ -439,7 +443,8 @@ k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (FSI_IN(piv[k], n, FSI_SITE(1))) qinv[piv[k]] = k;
   __syncthreads();
   // owned rows of the inverse, transposed through a shared tile (reuses G)
   T* tile = G;   // 32 x 33
@@ -451,7 +456,8 @@ k_patch_gj_blk(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int oo = t / 32, cc = t % 32;
         const int o = o0 + oo, c = c0 + cc;
-        if (o < nown && c < n) tile[oo * 33 + cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
+        if (o < nown && c < n && FSI_IN(ow[o], n, FSI_SITE(1)))
+          tile[oo * 33 + cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
       }
       __syncthreads();
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
@@ -622,7 +628,8 @@ k_patch_gj_f32(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (FSI_IN(piv[k], n, FSI_SITE(1))) qinv[piv[k]] = k;
   __syncthreads();
   float* tile = Gbuf0;   // 32 x 33
   const int nown = p_nown[p];
@@ -633,7 +640,8 @@ k_patch_gj_f32(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_no
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int oo = t / 32, cc = t % 32;
         const int o = o0 + oo, c = c0 + cc;
-        if (o < nown && c < n) tile[oo * 33 + cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
+        if (o < nown && c < n && FSI_IN(ow[o], n, FSI_SITE(1)))
+          tile[oo * 33 + cc] = M[(int64_t)piv[ow[o]] * n + qinv[c]];
       }
       __syncthreads();
       for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
@@ -998,7 +1006,8 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
   // block repeated a pivot row (ST_SINGULAR is reported; the values are void)
   for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[k] = 0;
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) qinv[piv[k]] = k;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (FSI_IN(piv[k], n, FSI_SITE(1))) qinv[piv[k]] = k;
   __syncthreads();
   {
     // owned rows of the inverse, transposed: out[c][o] = Binv[own[o]][c]; o is
@@ -1007,7 +1016,8 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
     const int32_t* ow = L.own + L.own_off[p];
     float* out = L.invT + L.inv_off[p];
     int* roff = reinterpret_cast<int*>(stage);   // row offset of B^{-1} row own[o] in M
-    for (int o = threadIdx.x; o < nown; o += blockDim.x) roff[o] = piv[ow[o]] * n;
+    for (int o = threadIdx.x; o < nown; o += blockDim.x)
+      roff[o] = FSI_IN(ow[o], n, FSI_SITE(1)) ? piv[ow[o]] * n : 0;
     __syncthreads();
     const int tot = n * opad;
     for (int t0 = threadIdx.x; t0 < tot; t0 += 4 * (int)blockDim.x) {
@@ -1109,7 +1119,7 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
                 const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
                 const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
                 T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc, int vstride,
-                const int32_t* __restrict__ sel) {
+                const int32_t* __restrict__ sel, int64_t nv) {
   using VT = VecT<T>;
   constexpr int W = VT::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1119,7 +1129,8 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
   const int32_t* id = idx + idx_off[p];
   const T* Dr = dr + idx_off[p];
   const T* Dc = dc + idx_off[p];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]] * Dr[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    rs[i] = FSI_IN(id[i], nv, FSI_SITE(1)) ? r[id[i]] * Dr[i] : T(0);
   const int nown = p_nown[p];
   const int nvec = own_pad(nown) / W;
   const int32_t* ow = own + own_off[p];
@@ -1168,7 +1179,7 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
 #pragma unroll
         for (int gg = 0; gg < CG; ++gg) sum += partial[gg * vstride * W + t];
         const int k = ow[o];
-        x[id[k]] += omega * Dc[k] * sum;
+        if (FSI_IN(k, n, FSI_SITE(1)) && FSI_IN(id[k], nv, FSI_SITE(1))) x[id[k]] += omega * Dc[k] * sum;
       }
     }
     __syncthreads();
@@ -1246,7 +1257,7 @@ k_patch_apply_rows(const int32_t* __restrict__ p_n, const int32_t* __restrict__ 
                    const int64_t* __restrict__ own_off, const int32_t* __restrict__ own,
                    const int64_t* __restrict__ inv_off, const T* __restrict__ invT, const T* __restrict__ r,
                    T* __restrict__ x, T omega, const T* __restrict__ dr, const T* __restrict__ dc, int S, int vps,
-                   int cg, const int32_t* __restrict__ sel) {
+                   int cg, const int32_t* __restrict__ sel, int64_t nv) {
   using VT = VecT<T>;
   constexpr int W = VT::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1261,7 +1272,8 @@ k_patch_apply_rows(const int32_t* __restrict__ p_n, const int32_t* __restrict__ 
   const int32_t* id = idx + idx_off[p];
   const T* Dr = dr + idx_off[p];
   const T* Dc = dc + idx_off[p];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rs[i] = r[id[i]] * Dr[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    rs[i] = FSI_IN(id[i], nv, FSI_SITE(1)) ? r[id[i]] * Dr[i] : T(0);
   const int32_t* ow = own + own_off[p];
   const typename VT::V* Bi = reinterpret_cast<const typename VT::V*>(invT + inv_off[p]);
   T* partial = rs + ((n + 3) & ~3);                    // cg * vps * W partial sums
@@ -1298,7 +1310,7 @@ k_patch_apply_rows(const int32_t* __restrict__ p_n, const int32_t* __restrict__ 
       T sum = T(0);
       for (int gg = 0; gg < cg; ++gg) sum += partial[gg * vps * W + t];
       const int k = ow[o];
-      x[id[k]] += omega * Dc[k] * sum;
+      if (FSI_IN(k, n, FSI_SITE(1)) && FSI_IN(id[k], nv, FSI_SITE(1))) x[id[k]] += omega * Dc[k] * sum;
     }
   }
 }
@@ -1328,7 +1340,7 @@ ApplyShape apply_shape(int np, int max_nown, int vec_width, int sm_count, int wa
 }
 
 template <typename T>
-void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
+void launch_patch_apply_t(int np, int64_t nv, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
                           const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st,
@@ -1342,7 +1354,7 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
       cudaFuncSetAttribute(k_patch_apply_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_patch_apply_rows<T><<<(unsigned)((int64_t)np * a.slices), threads, smem, st>>>(
         p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x, T(omega), dr, dc, a.slices, a.vps, a.groups,
-        sel);
+        sel, nv);
     return;
   }
   constexpr int CG = 4;                       // column groups per block
@@ -1354,7 +1366,7 @@ void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, c
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_patch_apply_t<T, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_patch_apply_t<T, CG><<<np, threads, smem, st>>>(p_n, p_nown, idx_off, idx, own_off, own, inv_off, invT, r, x,
-                                                    T(omega), dr, dc, vstride, sel);
+                                                    T(omega), dr, dc, vstride, sel, nv);
 }
 
 // ---------------------------------------------------------------------------
@@ -1387,11 +1399,12 @@ __device__ void ilu_mask(uint32_t* bm, int nb, int64_t g0, int64_t g1, const int
 }  // namespace
 
 // the dense offsets and widths of a Schwarz block's node / element blocks
-__device__ void ilu_blocks(int16_t* off, int8_t* w, int nb, const int32_t* __restrict__ bo) {
+__device__ void ilu_blocks(int16_t* off, int8_t* w, int nb, const int32_t* __restrict__ bo, int n) {
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const int32_t v = bo[b];
-    off[b] = (int16_t)(v >> 3);
-    w[b] = (int8_t)(v & 7);
+    const bool ok = FSI_IN((v >> 3) + (v & 7) - 1, n, FSI_SITE(1));
+    off[b] = (int16_t)(ok ? v >> 3 : 0);
+    w[b] = (int8_t)(ok ? v & 7 : 0);
   }
   __syncthreads();
 }
@@ -1411,7 +1424,7 @@ k_patch_ilu0(const int32_t* __restrict__ sel, const int32_t* __restrict__ p_n, c
   float* D = dense + dense_off[p];
   if (threadIdx.x == 0) s_sing = 0;
   ilu_mask(bm, nb, gmap_off[p], gmap_off[p + 1], gmap);
-  ilu_blocks(s_off, s_w, nb, boff + boff_off[p]);
+  ilu_blocks(s_off, s_w, nb, boff + boff_off[p], n);
   for (int bk = 0; bk < nb; ++bk) {
     // candidate block rows (i > k) and columns (j > k): bk itself and the
     // blocks coupled to it in the pattern
@@ -1500,8 +1513,9 @@ k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p
   const int32_t* bo = boff + boff_off[p];
   for (int b = lane; b < nb; b += 32) {
     const int32_t v = bo[b];
-    s_off[b] = (int16_t)(v >> 3);
-    s_w[b] = (int8_t)(v & 7);
+    const bool ok = FSI_IN((v >> 3) + (v & 7) - 1, n, FSI_SITE(1));
+    s_off[b] = (int16_t)(ok ? v >> 3 : 0);
+    s_w[b] = (int8_t)(ok ? v & 7 : 0);
   }
   for (int i = lane; i < n; i += 32) y[i] = id[i] >= 0 ? Dr[i] * r[id[i]] : 0.f;
   __syncwarp();
@@ -1513,8 +1527,10 @@ k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p
     const int e0 = gp[bi], e1 = gp[bi + 1];
     if (e0 + t < e1) {
       const int c = gm[3 * (e0 + t) + 2];
-      if (lower ? c < bi : c > bi) bk = c;
-      diag = c == bi;
+      if (FSI_IN(c, nb, FSI_SITE(1))) {
+        if (lower ? c < bi : c > bi) bk = c;
+        diag = c == bi;
+      }
     }
     const int oi = s_off[bi], wi = s_w[bi];
     const int ok = bk >= 0 ? s_off[bk] : 0, wk = bk >= 0 ? s_w[bk] : 0;
@@ -1613,7 +1629,7 @@ k_patch_apply_ilu(const int32_t* __restrict__ sel, const int32_t* __restrict__ p
   const int32_t* ow = own + own_off[p];
   for (int o = lane; o < nown; o += 32) {
     const int row = ow[o];
-    if (id[row] >= 0) x[id[row]] += omega * (Dc[row] * y[row]);
+    if (FSI_IN(row, n, FSI_SITE(1)) && id[row] >= 0) x[id[row]] += omega * (Dc[row] * y[row]);
   }
 }
 
@@ -1646,12 +1662,15 @@ void launch_patch_apply_ilu(int nsel, int max_n, int max_nb, const int32_t* sel,
                                          const double*, int, T*, const int64_t*, T*, T*, cudaStream_t);         \
   template void launch_patch_gj_t<T>(int, int, const int32_t*, const int32_t*, const int64_t*, const int64_t*, \
                                      const int32_t*, const int64_t*, T*, T*, int32_t*, bool, cudaStream_t);     \
-  template void launch_patch_apply_t<T>(int, int, int, const int32_t*, const int32_t*, const int64_t*,         \
+  template void launch_patch_apply_t<T>(int, int64_t, int, int, const int32_t*, const int32_t*, const int64_t*,\
                                         const int32_t*, const int64_t*, const int32_t*, const int64_t*,        \
                                         const T*, const T*, T*, double, const T*, const T*, int, int, int,     \
                                         cudaStream_t, const int32_t*);
 FSI_INST(double)
 FSI_INST(float)
 #undef FSI_INST
+
+// the bounds-check build's recorded site of this translation unit (0: none)
+FSI_BOUNDS_READER(bounds_site_schwarz)
 
 }  // namespace fsi

@@ -19,6 +19,12 @@ struct PhysParams {
   const double* yold;   // internal layout, finest level (nullptr when steady)
 };
 
+// bounds-check build (-DFSI_BOUNDS_CHECK): the first failed index check of
+// each translation unit's kernels since the last call (FSI_SITE code: unit *
+// 100000 + line; 0: none), cleared by the read; always 0 in the normal build
+int bounds_site_schwarz();
+int bounds_site_linalg();
+
 // k_assemble.cu
 // scratch: 3D only, assemble_3d_scratch_doubles(scratch_ne) doubles (2D: unused); false (nothing
 // launched) when one pass of ne elements needs more scratch than that
@@ -112,9 +118,9 @@ template <typename T>
 void launch_patch_gj_t(int np, int max_n, const int32_t* p_n, const int32_t* p_nown, const int64_t* dense_off,
                        const int64_t* own_off, const int32_t* own, const int64_t* inv_off, T* dense, T* invT,
                        int32_t* status, bool n_mult4, cudaStream_t st);
-// sel: the np blocks to apply (nullptr: blocks 0 .. np - 1)
+// sel: the np blocks to apply (nullptr: blocks 0 .. np - 1); nv: length of r and x
 template <typename T>
-void launch_patch_apply_t(int np, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
+void launch_patch_apply_t(int np, int64_t nv, int max_n, int max_nown, const int32_t* p_n, const int32_t* p_nown,
                           const int64_t* idx_off, const int32_t* idx, const int64_t* own_off, const int32_t* own,
                           const int64_t* inv_off, const T* invT, const T* r, T* x, double omega, const T* dr,
                           const T* dc, int sm_count, int want_slices, int want_groups, cudaStream_t st,
