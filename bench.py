@@ -924,6 +924,7 @@ def _serve_once(insts, order, prec, slots, budget, arrivals=None):
     srv.drain()
     wall = time.perf_counter() - t0
     res = [(iid, k, srv.poll(t)) for iid, k, t in tickets]
+    evictions = srv.evictions()
     srv.close()
     good = [r for _, _, r in res if r["status"] == 0]
     lat = np.array([r["latency_ms"] for r in good]) if good else np.zeros(1)
@@ -933,7 +934,7 @@ def _serve_once(insts, order, prec, slots, budget, arrivals=None):
     failed = sorted({iid for iid, _, r in res if r["status"] != 0})
     return {"solves_per_s": len(good) / wall, "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "requests": len(order), "completed": len(good),
-            "statuses": statuses, "rejected": len(rejected),
+            "statuses": statuses, "rejected": len(rejected), "evictions": evictions,
             "failed_instances": [(i, spec[i][1].dim, spec[i][1].levels, spec[i][1].mu_s, spec[i][1].U) for i in failed],
             "max_true_rel_residual": max([r["rel_res"] for r in good] or [0.0])}
 

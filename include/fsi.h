@@ -51,6 +51,7 @@ enum {
   FSI_E_NONFINITE = -6,     /* NaN / Inf in the state, residual or Krylov data */
   FSI_E_MESH_TANGLED = -7,  /* det F <= 0 at a quadrature point */
   FSI_E_TIMEOUT = -8,       /* a bounded device wait gave up */
+  FSI_E_CANCELLED = -9,     /* serving: the request was cancelled before it ran */
   FSI_PENDING = 1           /* serving poll: not finished yet */
 };
 
@@ -454,6 +455,15 @@ int fsi_serve_submit(fsi_server* srv, const fsi_request* req, uint64_t* ticket);
 int fsi_serve_poll(fsi_server* srv, uint64_t ticket, fsi_result* out, double* dx_out);
 /* Blocks until every queued request has finished (results stay pollable). */
 int fsi_serve_drain(fsi_server* srv);
+/* Cancels a request that has not started: it completes at once with status
+ * FSI_E_CANCELLED (poll it as usual; no dx) and the instance's state does not
+ * advance.  A cancelled first request hands its noise to the instance's next
+ * queued request, which then builds the instance.  A cancelled `last` request
+ * moves the end of the instance to its latest queued request, else to the end
+ * of the step that runs now, else frees the instance at once.  Returns
+ * FSI_PENDING if the request is already running or done (it is not
+ * cancelled), FSI_E_INVALID for an unknown or already polled ticket. */
+int fsi_serve_cancel(fsi_server* srv, uint64_t ticket);
 /* Device bytes currently held by resident instances. */
 int64_t fsi_server_resident_bytes(const fsi_server* srv);
 /* Continuous batching of the factorisation: a worker that takes a request of
@@ -464,6 +474,17 @@ int64_t fsi_server_resident_bytes(const fsi_server* srv);
  * are bit-identical to unbatched steps.  1 turns it off; the default is 4.
  * FSI_E_INVALID outside [1, 64]. */
 int fsi_server_set_batching(fsi_server* srv, int max_batch);
+/* Eviction under memory pressure (on by default): when the oldest waiting
+ * request does not fit in the budget, idle steady instances without queued
+ * requests are evicted, least recently used first - the Newton state y is
+ * copied to the host (fsi_get_state) and the hierarchy freed - and an evicted
+ * instance is rebuilt from its descriptor and saved state (fsi_set_state)
+ * when its next request is admitted.  Results do not change: every step
+ * re-assembles and re-factors from the state.  0 turns it off (a request that
+ * does not fit then waits for instances to finish). */
+int fsi_server_set_eviction(fsi_server* srv, int on);
+/* Instances evicted so far. */
+int64_t fsi_server_evictions(fsi_server* srv);
 /* Waits for running requests, frees every instance and the server. */
 int fsi_server_destroy(fsi_server* srv);
 

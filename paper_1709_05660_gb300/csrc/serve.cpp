@@ -1,8 +1,9 @@
 // Continuous-batching server for Newton-step requests (the serving form of
 // the solver): worker threads with their own CUDA streams pick the oldest
 // runnable request - an instance not already running, admitted by planned
-// device bytes against the budget - and run one fsi_newton_step on that
-// instance's resident hierarchy.
+// device bytes against the budget (evicting idle instances to the host when
+// the oldest waiting request does not fit) - and run one fsi_newton_step on
+// that instance's resident hierarchy.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -28,6 +29,16 @@ struct Instance {
   int64_t n = 0;
   int failed = 0;                  // error of an earlier step that freed the instance
   bool batchable = false;          // mixed precision with >= 2 levels: may share a factorisation launch
+  // eviction under memory pressure: a steady instance that is idle and has no
+  // queued request may be evicted (state kept on the host, hierarchy freed)
+  // and is rebuilt from that state when its next request is admitted
+  bool steady = false;
+  bool evicted = false;
+  std::vector<double> saved_y;
+  fsi_problem_desc desc{};
+  fsi_solver_opts opts{};
+  uint64_t last_use = 0;
+  bool free_after = false;         // its last request was cancelled while a step ran
 };
 
 struct Ticket {
@@ -39,6 +50,7 @@ struct Ticket {
   Clock::time_point t_submit, t_start, t_end;
   int state = 0;                   // 0 queued, 1 running, 2 done
   int64_t planned = 0;             // planned bytes when the request creates the instance
+  int64_t reserved = 0;            // bytes reserved at admission (new or evicted instance)
 };
 
 double ms(Clock::time_point a, Clock::time_point b) {
@@ -59,8 +71,48 @@ struct fsi_server {
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;   // one per worker; destroyed after the instances
   uint64_t next = 1;
+  uint64_t use_clock = 0;
+  int64_t evictions = 0;
+  bool evict = true;                   // evict idle instances when a request does not fit
   int running = 0;
   bool stop = false;
+
+  // device bytes a ticket needs to be admitted: the planned size of a new
+  // instance, the size of an evicted one, nothing for a resident one
+  int64_t need(const Ticket* t, std::map<uint64_t, Instance>::iterator f) {
+    if (f == inst.end()) return t->planned;
+    const Instance& in = f->second;
+    if (in.ctx || in.failed) return 0;
+    return in.evicted ? in.bytes : t->planned;
+  }
+
+  bool has_queued(uint64_t id) {
+    for (Ticket* q : queue)
+      if (q->req.instance == id) return true;
+    return false;
+  }
+
+  // evicts least recently used idle steady instances without queued requests
+  // until `bytes` more fit in the budget (caller holds mu); false if not
+  bool make_room(int64_t bytes) {
+    while (budget > 0 && resident + bytes > budget) {
+      Instance* lru = nullptr;
+      for (auto& kv : inst) {
+        Instance& in = kv.second;
+        if (!in.ctx || in.busy || !in.steady || has_queued(kv.first)) continue;
+        if (!lru || in.last_use < lru->last_use) lru = &in;
+      }
+      if (!lru) return false;
+      lru->saved_y.assign(lru->n, 0.0);
+      if (fsi_get_state(lru->ctx, lru->saved_y.data()) != FSI_OK) return false;
+      fsi_destroy(lru->ctx);
+      lru->ctx = nullptr;
+      lru->evicted = true;
+      resident -= lru->bytes;
+      ++evictions;
+    }
+    return true;
+  }
 
   // first runnable ticket in arrival order (caller holds mu); with
   // batch_only, only requests of resident batchable instances qualify
@@ -74,9 +126,12 @@ struct fsi_server {
       for (auto jt = queue.begin(); jt != it; ++jt)
         if ((*jt)->req.instance == t->req.instance) { earlier_same = true; break; }
       if (earlier_same) continue;
-      if ((f == inst.end() || (!f->second.ctx && !f->second.failed)) && budget > 0 &&
-          resident + t->planned > budget)
-        continue;   // admission
+      const int64_t nb = need(t, f);
+      if (nb > 0 && budget > 0 && resident + nb > budget) {   // admission
+        // evict only on behalf of the oldest waiting request, so that later
+        // small requests cannot evict instances ahead of it
+        if (!evict || it != queue.begin() || !make_room(nb)) continue;
+      }
       queue.erase(it);
       return t;
     }
@@ -85,30 +140,48 @@ struct fsi_server {
 
   // marks a picked ticket running (caller holds mu)
   void claim(Ticket* t) {
+    auto f = inst.find(t->req.instance);
+    t->reserved = need(t, f);
     auto& in = inst[t->req.instance];
     in.busy = true;
-    if (!in.ctx && !in.failed) resident += t->planned;   // reserve before building
+    resident += t->reserved;   // reserve before building
     t->state = 1;
     t->t_start = Clock::now();
     ++running;
   }
 
   // first request of an instance: build its hierarchy and initial state
+  // an evicted instance: rebuilt from its descriptor and saved state
   int build(Ticket* t, Instance* in, cudaStream_t stream) {
-    int rc = fsi_build_hierarchy(&t->req.desc, &t->req.opts, stream, &in->ctx);
+    const bool again = in->evicted;
+    if (!again) {
+      in->desc = t->req.desc;
+      in->opts = t->req.opts;
+    }
+    int rc = fsi_build_hierarchy(&in->desc, &in->opts, stream, &in->ctx);
     if (rc == FSI_OK) {
       int64_t nl[16], hb = 0;
       fsi_get_sizes(in->ctx, nl, nullptr, &hb);
-      in->n = nl[t->req.desc.levels - 1];
+      in->n = nl[in->desc.levels - 1];
       in->bytes = hb;
-      in->batchable = t->req.opts.precision == FSI_MIXED && t->req.desc.levels >= 2;
-      std::vector<double> y(in->n);
-      rc = fsi_initial_state(in->ctx, t->noise.data(), y.data());
-      if (rc == FSI_OK) rc = fsi_set_state(in->ctx, y.data(), nullptr, nullptr, 0.0);
+      in->batchable = in->opts.precision == FSI_MIXED && in->desc.levels >= 2;
+      in->steady = in->desc.transient == 0;
+      if (again) {
+        rc = fsi_set_state(in->ctx, in->saved_y.data(), nullptr, nullptr, 0.0);
+      } else {
+        std::vector<double> y(in->n);
+        rc = fsi_initial_state(in->ctx, t->noise.data(), y.data());
+        if (rc == FSI_OK) rc = fsi_set_state(in->ctx, y.data(), nullptr, nullptr, 0.0);
+      }
     }
     std::lock_guard<std::mutex> lk(mu);
-    resident += (rc == FSI_OK ? in->bytes : 0) - t->planned;
+    resident += (rc == FSI_OK ? in->bytes : 0) - t->reserved;
+    t->reserved = 0;
     t->planned = 0;
+    if (rc == FSI_OK) {
+      in->evicted = false;
+      in->saved_y.clear();
+    }
     if (rc != FSI_OK && in->ctx) {
       fsi_destroy(in->ctx);
       in->ctx = nullptr;
@@ -131,17 +204,18 @@ struct fsi_server {
       t->res.latency_ms = ms(t->t_submit, t->t_end);
       if (t->req.keep_dx) t->dx.swap(dx);
       t->noise.clear();
+      in->last_use = ++use_clock;
       // a step that did not converge leaves the instance (and its state) in
       // place; other failures free it and are remembered, so the instance's
       // queued requests complete with the same error; the last request
       // forgets the instance
-      if (t->req.last || (rc != FSI_OK && rc != FSI_E_NOT_CONVERGED)) {
+      if (t->req.last || in->free_after || (rc != FSI_OK && rc != FSI_E_NOT_CONVERGED)) {
         if (in->ctx) {
           fsi_destroy(in->ctx);
           in->ctx = nullptr;
           resident -= in->bytes;
         }
-        if (t->req.last) {
+        if (t->req.last || in->free_after) {
           inst.erase(t->req.instance);
         } else {
           in->failed = rc;
@@ -319,6 +393,67 @@ int fsi_serve_drain(fsi_server* s) {
   return FSI_OK;
 }
 
+int fsi_serve_cancel(fsi_server* s, uint64_t ticket) {
+  if (!s) return FSI_E_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return FSI_E_INVALID;
+    Ticket* t = it->second.get();
+    if (t->state != 0) return FSI_PENDING;   // running or done: not cancelled
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+      if (*q == t) {
+        s->queue.erase(q);
+        break;
+      }
+    // the instance's other queued requests, in arrival order
+    Ticket* first = nullptr;
+    Ticket* final_ = nullptr;
+    for (Ticket* q : s->queue)
+      if (q->req.instance == t->req.instance) {
+        if (!first) first = q;
+        final_ = q;
+      }
+    // a cancelled first request hands the noise of the initial state (and
+    // the planned size) to the next one, which then builds the instance
+    if (!t->noise.empty() && first) {
+      first->noise.swap(t->noise);
+      first->planned = t->planned;
+    }
+    // a cancelled last request: the instance ends after its latest queued
+    // request, else after the step that runs now, else at once
+    if (t->req.last) {
+      if (final_) {
+        final_->req.last = 1;
+      } else {
+        auto f = s->inst.find(t->req.instance);
+        if (f != s->inst.end()) {
+          Instance& in = f->second;
+          if (in.busy) {
+            in.free_after = true;
+          } else {
+            if (in.ctx) {
+              fsi_destroy(in.ctx);
+              s->resident -= in.bytes;
+            }
+            s->inst.erase(f);
+          }
+        }
+      }
+    }
+    t->state = 2;
+    t->t_start = t->t_end = Clock::now();
+    t->res = fsi_result{};
+    t->res.status = FSI_E_CANCELLED;
+    t->res.queue_ms = ms(t->t_submit, t->t_end);
+    t->res.latency_ms = t->res.queue_ms;
+    t->noise.clear();
+  }
+  s->cv.notify_all();
+  s->done_cv.notify_all();
+  return FSI_OK;
+}
+
 int fsi_server_set_batching(fsi_server* s, int max_batch) {
   if (!s || max_batch < 1 || max_batch > 64) return FSI_E_INVALID;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -327,6 +462,19 @@ int fsi_server_set_batching(fsi_server* s, int max_batch) {
 }
 
 int64_t fsi_server_resident_bytes(const fsi_server* s) { return s ? s->resident : 0; }
+
+int fsi_server_set_eviction(fsi_server* s, int on) {
+  if (!s) return FSI_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->evict = on != 0;
+  return FSI_OK;
+}
+
+int64_t fsi_server_evictions(fsi_server* s) {
+  if (!s) return 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  return s->evictions;
+}
 
 int fsi_server_destroy(fsi_server* s) {
   if (!s) return FSI_E_INVALID;

@@ -21,7 +21,7 @@ FSI_OK = 0
 ERRORS = {
     -1: "FSI_E_INVALID", -2: "FSI_E_OOM", -3: "FSI_E_CUDA", -4: "FSI_E_SINGULAR",
     -5: "FSI_E_NOT_CONVERGED", -6: "FSI_E_NONFINITE", -7: "FSI_E_MESH_TANGLED",
-    -8: "FSI_E_TIMEOUT", 1: "FSI_PENDING",
+    -8: "FSI_E_TIMEOUT", -9: "FSI_E_CANCELLED", 1: "FSI_PENDING",
 }
 MAX_BREAKS = 65
 
@@ -36,7 +36,7 @@ SYMBOLS = (
     "fsi_server_resident_bytes", "fsi_server_destroy", "fsi_coarse_solve_static", "fsi_set_launch_params",
     "fsi_get_launch_params", "fsi_time_level_kernels", "fsi_set_stream", "fsi_import_csr",
     "fsi_set_tc_wait_limit", "fsi_fmg_newton", "fsi_newton_solve_update", "fsi_factor_schwarz_batch",
-    "fsi_server_set_batching",
+    "fsi_server_set_batching", "fsi_server_set_eviction", "fsi_server_evictions", "fsi_serve_cancel",
 )
 
 # kernel classes for fsi_kernel_stats
@@ -154,6 +154,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fsi_newton_solve_update.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveStats)]
     lib.fsi_factor_schwarz_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
     lib.fsi_server_set_batching.argtypes = [vp, ctypes.c_int]
+    lib.fsi_server_set_eviction.argtypes = [vp, ctypes.c_int]
+    lib.fsi_serve_cancel.argtypes = [vp, ctypes.c_uint64]
+    lib.fsi_server_evictions.argtypes = [vp]
+    lib.fsi_server_evictions.restype = ctypes.c_int64
     lib.fsi_fmg_newton.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOptsC), vp, ctypes.c_double,
                                    ctypes.c_int, vp, ctypes.POINTER(FmgStats)]
     lib.fsi_import_csr.argtypes = [vp, ctypes.c_int, vp]
@@ -507,6 +511,27 @@ class Server:
         rc = self.lib.fsi_server_set_batching(self.h, int(max_batch))
         if rc != FSI_OK:
             raise FSIError(rc, "fsi_server_set_batching rejected the value")
+
+    def cancel(self, ticket: int) -> bool:
+        """Cancels a request that has not started (True); False if it is
+        already running or done."""
+        rc = self.lib.fsi_serve_cancel(self.h, ctypes.c_uint64(ticket))
+        if rc == 1:
+            return False
+        self._check(rc)
+        return True
+
+    def set_eviction(self, on: bool):
+        """Evict idle steady instances to the host when the oldest waiting
+        request does not fit in the budget (on by default)."""
+        self._check(self.lib.fsi_server_set_eviction(self.h, 1 if on else 0))
+
+    def evictions(self) -> int:
+        return int(self.lib.fsi_server_evictions(self.h))
+
+    def _check(self, rc):
+        if rc != FSI_OK:
+            raise FSIError(rc, "server call failed")
 
     def drain(self):
         self.lib.fsi_serve_drain(self.h)

@@ -5,7 +5,11 @@
   with fixed reduction orders);
 * admission by device bytes: with a budget that holds one instance, a second
   instance waits until the first one is freed, and both finish;
-* an instance larger than the whole budget is rejected at submit.
+* an instance larger than the whole budget is rejected at submit;
+* eviction under memory pressure: an idle instance is evicted to the host and
+  rebuilt from its saved state, and its results do not change;
+* cancellation: a cancelled request completes with FSI_E_CANCELLED without
+  advancing its instance, and the instance's other results do not change.
 """
 from dataclasses import replace
 
@@ -232,3 +236,97 @@ def test_factor_batch_is_bitwise_the_individual_factorisation():
         assert np.array_equal(a, b)
     for s in inst:
         s.close()
+
+
+def _wait(srv, tickets, n, deadline_s=600.0):
+    """Polls the tickets until all are done (a stuck request fails the test
+    instead of blocking it)."""
+    import time
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for k, t in tickets.items():
+            if k in out:
+                continue
+            dx = np.empty(n)
+            r = srv.poll(t, dx)
+            if r is not None:
+                out[k] = (dx, r)
+        assert time.time() - t0 < deadline_s, f"requests still pending: {sorted(set(tickets) - set(out))}"
+        time.sleep(0.01)
+    return out
+
+
+def test_eviction_and_readmission_keep_results():
+    """A budget that holds one instance, two instances with two steps each,
+    the second submitted while the first is resident and idle: the first is
+    evicted (state to the host, hierarchy freed), the second runs; the first's
+    next (last) request evicts the second and rebuilds the first from its
+    saved state; the second's next request then rebuilds the second, which
+    fits once the first has ended.  Every correction equals, bit for bit, that
+    of the instance served alone."""
+    fsi = _fsi()
+    p, o = Problem(levels=3, mu_s=1e5, U=0.3), SolverOpts(tile=(2, 2), precision=1)
+    plan = fsi.FSI(p, o, plan_only=True)
+    one, n = plan.hbm_bytes, int(plan.N[-1])
+    plan.close()
+    ref = {}
+    for iid in (1, 2):
+        srv = fsi.Server(hbm_budget_bytes=0, max_slots=1)
+        ts = {(iid, 0): srv.submit(iid, p, o, noise=noise(n, iid), keep_dx=True),
+              (iid, 1): srv.submit(iid, p, o, last=True, keep_dx=True)}
+        ref.update(_wait(srv, ts, n))
+        srv.close()
+    srv = fsi.Server(hbm_budget_bytes=int(one * 1.5), max_slots=2)
+    got = _wait(srv, {(1, 0): srv.submit(1, p, o, noise=noise(n, 1), keep_dx=True)}, n)
+    got.update(_wait(srv, {(2, 0): srv.submit(2, p, o, noise=noise(n, 2), keep_dx=True)}, n))
+    assert srv.evictions() == 1
+    got.update(_wait(srv, {(1, 1): srv.submit(1, p, o, last=True, keep_dx=True)}, n))
+    assert srv.evictions() == 2
+    got.update(_wait(srv, {(2, 1): srv.submit(2, p, o, last=True, keep_dx=True)}, n))
+    assert srv.evictions() == 2
+    for key, (dx, r) in got.items():
+        assert r["status"] == 0, (key, r)
+        assert np.array_equal(dx, ref[key][0]), (key, np.max(np.abs(dx - ref[key][0])))
+    assert srv.resident_bytes() == 0
+    srv.close()
+
+
+def test_cancelled_requests_leave_the_other_results_unchanged():
+    """One worker, instance 1 with three queued steps and instance 2 with
+    three: cancelling instance 1's last step ends it after its second (nothing
+    stays resident), cancelling instance 2's first step hands the initial-state
+    noise to its second, which builds it.  The cancelled requests complete with
+    FSI_E_CANCELLED; every other correction equals, bit for bit, the
+    corresponding step of the instance served alone."""
+    fsi = _fsi()
+    p, o = Problem(levels=3, mu_s=1e5, U=0.3), SolverOpts(tile=(2, 2), precision=1)
+    n = _n(p)
+    ref = {}
+    for iid in (1, 2):
+        srv = fsi.Server(hbm_budget_bytes=0, max_slots=1)
+        ts = {(iid, 0): srv.submit(iid, p, o, noise=noise(n, iid), keep_dx=True),
+              (iid, 1): srv.submit(iid, p, o, last=True, keep_dx=True)}
+        ref.update(_wait(srv, ts, n))
+        srv.close()
+    srv = fsi.Server(hbm_budget_bytes=0, max_slots=1)
+    ts = {}
+    for iid in (1, 2):
+        for k in range(3):
+            ts[(iid, k)] = srv.submit(iid, p, o, noise=noise(n, iid) if k == 0 else None, last=(k == 2),
+                                      keep_dx=True)
+    # the single worker is still building instance 1 for its first step
+    assert srv.cancel(ts[(1, 2)]) and srv.cancel(ts[(2, 0)])
+    srv.drain()
+    assert srv.cancel(ts[(1, 0)]) is False
+    got = _wait(srv, ts, n)
+    for key in ((1, 2), (2, 0)):
+        assert got[key][1]["status"] == -9, got[key][1]
+    for key, refkey in (((1, 0), (1, 0)), ((1, 1), (1, 1)), ((2, 1), (2, 0)), ((2, 2), (2, 1))):
+        dx, r = got[key]
+        assert r["status"] == 0, (key, r)
+        assert np.array_equal(dx, ref[refkey][0]), key
+    assert srv.resident_bytes() == 0
+    with pytest.raises(fsi.FSIError):
+        srv.cancel(ts[(1, 0)])
+    srv.close()
