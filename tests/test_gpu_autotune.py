@@ -107,7 +107,7 @@ def test_tuner_entry_is_valid_and_solves(case):
     entry = autotune.tune(case["prob"], case["opts"], stream=torch.cuda.current_stream().cuda_stream, reps=5,
                           trials=1, log=lambda m: None)
     autotune.check_entry(entry, case["prob"].levels)
-    assert entry["gj_panel"] in (16, 24, 32, 216)
+    assert entry["gj_panel"] in autotune.PANEL_CANDIDATES
     s = fsi.FSI(case["prob"], case["opts"], stream=torch.cuda.current_stream().cuda_stream, tuned=False)
     try:
         assert autotune.apply_table(s, entry) is entry
