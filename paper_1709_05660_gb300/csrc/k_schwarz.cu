@@ -707,7 +707,10 @@ __host__ __device__ constexpr int gj_tc_max_n() {
 template <int W, int TN, int NC = 512>
 __host__ __device__ constexpr int gj_tc_threads() { return gj_tc_max_n<W, TN, NC>(); }   // one thread per row
 template <int TN>
-__host__ __device__ constexpr int gj_stage() { return TN + 1; }   // row stride of the staged tile (conflict-free banks)
+__host__ __device__ constexpr int gj_stage() { return TN + 4; }   // row stride of the staged tile
+// (rows 16-byte aligned for 4-wide accesses; eight consecutive rows start in
+// distinct groups of four banks, so a quarter-warp's 4-wide stores of eight
+// rows do not conflict)
 
 template <int W, int TN, int NC = 512>
 size_t gj_tc_smem(int max_n) {
@@ -733,7 +736,8 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
   constexpr int CGN = NWARP / 4;                           // column-chunk slots of a tile per lane quarter
   constexpr int CW = TN / CGN > 16 ? TN / CGN : 16;        // chunk width (multiple of 16)
   constexpr int kStage = gj_stage<TN>();
-  constexpr int NE = TN / 32;                              // tile columns per lane in the epilogue
+  constexpr int LPR = TN / 4;                              // epilogue lanes per tile row (4 columns each)
+  constexpr int RPI = kWarp / LPR;                         // tile rows per warp instruction (1 or 2)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n16 = (max_n + 15) / 16 * 16;
   float* Bhi = reinterpret_cast<float*>(smem_raw);          // n16 x W, K-major
@@ -935,22 +939,25 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
       };
       if (threadIdx.x == 0) issue(0);
       constexpr int RPW = 128 / NWARP;   // epilogue rows per warp
+      constexpr int NK = RPW / RPI;      // 4-wide accesses per lane and tile
+      static_assert(RPW % RPI == 0, "epilogue rows per warp");
+      const int c4 = lane % LPR, rsub = lane / LPR;   // the lane's 4 columns and row of an instruction
       for (int t = 0; t < ntiles; ++t) {
         const int i0 = (t / ntcc) * 128, j0 = (t % ntcc) * TN, b = t & 1;
         const int nt = min(TN, (n - j0 + 15) / 16 * 16);
-        // the tile's old values (lane l: columns l, l + 32, ... of its warp's
-        // rows) are loaded before waiting for the tile's UMMAs, so their L2
-        // round trip overlaps the tensor-core work and the staging
-        float old[RPW][NE];
+        // the tile's old values (lane l: columns 4 (l % LPR) .. + 3 of a row
+        // of its warp) are loaded before waiting for the tile's UMMAs, so
+        // their L2 round trip overlaps the tensor-core work and the staging;
+        // n, j0 and the panel bounds are multiples of 4, so a 4-wide chunk is
+        // wholly inside or outside the matrix and the panel
+        const int jc = j0 + 4 * c4;
+        const bool col_ok = 4 * c4 < nt && jc < n && !(jc >= k0 && jc < k0 + wp);
+        float4 old[NK];
 #pragma unroll
-        for (int k = 0; k < RPW; ++k) {
-          const int r = i0 + wid + NWARP * k;
-          const bool ok = r < n && live[r];
-#pragma unroll
-          for (int e = 0; e < NE; ++e) {
-            const int c = lane + 32 * e, j = j0 + c;
-            old[k][e] = (ok && c < nt && j < n) ? M[(int64_t)r * n + j] : 0.f;
-          }
+        for (int k = 0; k < NK; ++k) {
+          const int r = i0 + wid + NWARP * (RPI * k + rsub);
+          const bool ok = col_ok && r < n && live[r];
+          old[k] = ok ? *reinterpret_cast<const float4*>(M + (int64_t)r * n + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (threadIdx.x == 0) {
           tc::fence_after_sync();
@@ -975,27 +982,24 @@ k_patch_gj_tc(const GjLevels lv, int32_t* __restrict__ status, int max_n) {
               float v[16];
               tc::tmem_ld<16>(tc::taddr(tbase, 32 * q, (uint32_t)TN * b + cg * CW + 16 * h), v);
               tc::tmem_wait_ld();
-              float* srow = stage + (32 * q + lane) * kStage + cg * CW + 16 * h;
+              float4* srow = reinterpret_cast<float4*>(stage + (32 * q + lane) * kStage + cg * CW + 16 * h);
 #pragma unroll
-              for (int c = 0; c < 16; ++c) srow[c] = v[c];
+              for (int c = 0; c < 4; ++c) srow[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
             }
           }
         }
         tc::fence_before_sync();
         __syncthreads();
-        // M += D for live rows, panel columns excluded: lane l adds columns
-        // l, l + 32, ... of a row (coalesced)
-        {
+        // M += D for live rows, panel columns excluded: 4-wide, a warp
+        // instruction covers whole rows (coalesced)
+        if (col_ok) {
 #pragma unroll
-          for (int k = 0; k < RPW; ++k) {
-            const int rr = wid + NWARP * k, r = i0 + rr;
+          for (int k = 0; k < NK; ++k) {
+            const int rr = wid + NWARP * (RPI * k + rsub), r = i0 + rr;
             if (!(r < n && live[r])) continue;
-            const float* srow = stage + rr * kStage;
-#pragma unroll
-            for (int e = 0; e < NE; ++e) {
-              const int c = lane + 32 * e, j = j0 + c;
-              if (c < nt && j < n && !(j >= k0 && j < k0 + wp)) M[(int64_t)r * n + j] = old[k][e] + srow[c];
-            }
+            const float4 d = *reinterpret_cast<const float4*>(stage + rr * kStage + 4 * c4);
+            *reinterpret_cast<float4*>(M + (int64_t)r * n + jc) =
+                make_float4(old[k].x + d.x, old[k].y + d.y, old[k].z + d.z, old[k].w + d.w);
           }
         }
       }
