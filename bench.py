@@ -1042,8 +1042,10 @@ def run_profile_case(args):
     (the same block sizes, 337 blocks in one launch) twice; `spmv` runs two
     V-cycles of the 5-level channel (residual vectors and matrices larger than
     L2); `ilu` does the same with ILU(0) fluid blocks at mean inflow 0.2;
-    `asm` assembles small 2D and 3D problems once in each time
-    discretisation.  Prints the unknowns and the device bytes held."""
+    `krylov` solves one Newton step of the 5-level channel with FGMRES
+    (Arnoldi kernels, FP64 operator products, V-cycles); `asm` assembles
+    small 2D and 3D problems once in each time discretisation.  Prints the
+    unknowns and the device bytes held."""
     import torch
     from dataclasses import replace
     from paper_1709_05660_gb300 import fsi
@@ -1086,6 +1088,9 @@ def run_profile_case(args):
         b = torch.randn(N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
         for _ in range(2):
             s.apply_vcycle(b, z)
+    if args.profile_case == "krylov":
+        dx = torch.empty(N, dtype=torch.float64, device="cuda")
+        s.newton_solve_update(dx)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "workload": args.config, "levels": prob.levels,
                       "unknowns": N, "device_bytes": int(s.hbm_bytes)}))
@@ -1140,7 +1145,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="paper-settings parameter studies instead")
     ap.add_argument("--sweep-config", default="channel2d_l5")
     ap.add_argument("--sweep-precision", type=int, default=1)
-    ap.add_argument("--profile-case", choices=["gj", "spmv", "asm", "ilu"], default=None,
+    ap.add_argument("--profile-case", choices=["gj", "spmv", "asm", "ilu", "krylov"], default=None,
                     help="run one small case of a kernel for an ncu capture instead")
     ap.add_argument("--_cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_out", default=None, help=argparse.SUPPRESS)

@@ -180,7 +180,7 @@ int fsi_set_state(fsi_ctx* ctx, const double* y, const double* y_prev,
 int fsi_get_state(fsi_ctx* ctx, double* y_out);
 
 /* Residual r(y) and exact Jacobian J(y) on the finest level (element-batched
- * forward-mode dual numbers, coloured scatter into block-sparse storage),
+ * forward-mode dual numbers, element contributions gathered into block-sparse storage),
  * Dirichlet rows replaced by identity rows with r_i = y_i - g_i, then the
  * Galerkin operators J_{l-1} = R J_l P of every coarser level (Sec. 3.2).
  * Transient problems add the BDF inertia terms, the mesh velocity in the
@@ -353,7 +353,7 @@ int fsi_coarse_solve_static(fsi_ctx* ctx, const double* b, double* x);
 enum {
   FSI_K_ASSEMBLE = 0,      /* element residual + Jacobian (dual numbers) */
   FSI_K_GALERKIN = 1,      /* element-wise Galerkin coarse matrices */
-  FSI_K_SCATTER = 2,       /* coloured scatter of element matrices, Dirichlet rows */
+  FSI_K_SCATTER = 2,       /* gather of element matrices into blocks, Dirichlet rows */
   FSI_K_PATCH_FACTOR = 3,  /* Schwarz block gather + Gauss-Jordan inversion */
   FSI_K_COARSE_FACTOR = 4, /* coarse dense gather + cooperative Gauss-Jordan */
   FSI_K_PATCH_APPLY = 5,   /* restricted Schwarz update (owned inverse rows x residual) */

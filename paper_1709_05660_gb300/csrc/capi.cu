@@ -224,11 +224,12 @@ void build_device(Ctx& c) {
     for (int64_t i = 0; i < H.Ni; ++i)
       if (H.canon_of_int[i] >= 0) ioc[H.canon_of_int[i]] = (int32_t)i;
     D.int_of_canon = upload(c, ioc);
-    D.elem_map = upload(c, H.elem_map);
-    D.color_list = upload(c, H.color_list);
     D.mat_list = upload(c, H.mat_list);
     D.n_fluid_elem = H.n_fluid_elem;
-    D.color_ptr = H.color_ptr;
+    D.blk_ptr = upload(c, H.blk_ptr); D.blk_src = upload(c, H.blk_src);
+    D.res_ptr = upload(c, H.res_ptr); D.res_src = upload(c, H.res_src);
+    D.n_blk_src = (int64_t)H.blk_src.size();
+    D.n_contrib = (int64_t)(H.blk_src.size() + H.res_src.size());
     if (l > 0) {
       D.P_ptr = upload(c, H.P_ptr); D.P_col = upload(c, H.P_col); D.P_val = upload(c, H.P_val);
       D.R_ptr = upload(c, H.R_ptr); D.R_col = upload(c, H.R_col); D.R_val = upload(c, H.R_val);
@@ -439,9 +440,6 @@ void assemble_impl(Ctx& c) {
   }
   double* Re = c.tmp_re;
   const double nd = c.ndofe;
-  ck(cudaMemsetAsync(F.val, 0, (size_t)F.nnzb * B * B * sizeof(double), c.stream), "memset");
-  ck(cudaMemsetAsync(c.res, 0, F.Ni * sizeof(double), c.stream), "memset");
-  const int ngroups = (int)F.color_ptr.size() - 1;
   {
     // element matrices: one pass over the fluid elements and one over the
     // solid ones (in 2D the small solid pass runs on the private stream beside
@@ -471,14 +469,14 @@ void assemble_impl(Ctx& c) {
     else run(true, F.mat_list + nf, ns, c.stream);
   }
   {
-    Prof pr(c, FSI_K_SCATTER, (double)F.n_elem * nd * nd * 8.0 + (double)F.nnzb * B * B * 16.0, 0.0, ngroups + 1);
-    for (int g = 0; g < ngroups; ++g) {
-      const int ne = F.color_ptr[g + 1] - F.color_ptr[g];
-      (c.dim == 2 ? launch_scatter_2d : launch_scatter_3d)(F.color_list + F.color_ptr[g], ne, F.Ke, Re,
-                                                            F.elem_nodes, F.elem_map, F.n_nodes, F.val, c.res,
-                                                            c.stream);
-      if (ne > 0) counted(c);
-    }
+    // element matrices in, block values out, gather lists; residual likewise
+    Prof pr(c, FSI_K_SCATTER,
+            (double)F.n_elem * nd * (nd + 1.0) * 8.0 + (double)F.nnzb * B * B * 8.0 + (double)F.Ni * 8.0 +
+                (double)(F.nnzb + F.nb + F.n_contrib) * 4.0,
+            0.0, 3);
+    launch_gather_elements(c.dim, F.nnzb, F.blk_ptr, F.blk_src, F.Ke, F.val, F.nb, F.res_ptr, F.res_src, Re, c.res,
+                           c.stream);
+    counted(c, 2);
     launch_dirichlet(F.dir_list, F.n_dir, F.rowptr, F.col, F.val, B, c.y, F.dir_val, transient ? c.inflow_alpha : 1.0,
                      c.res, c.stream);
     counted(c);
@@ -499,16 +497,13 @@ void assemble_impl(Ctx& c) {
                            Co.elem_nodes, Co.node_class, Co.dir, Co.Ke, c.stream);
       counted(c);
     }
-    ck(cudaMemsetAsync(Co.val, 0, (size_t)Co.nnzb * B * B * sizeof(double), c.stream), "memset");
-    const int ng = (int)Co.color_ptr.size() - 1;
-    Prof pr(c, FSI_K_SCATTER, (double)Co.n_elem * nd * nd * 8.0 + (double)Co.nnzb * B * B * 16.0, 0.0, ng + 1);
-    for (int g = 0; g < ng; ++g) {
-      const int ne = Co.color_ptr[g + 1] - Co.color_ptr[g];
-      (c.dim == 2 ? launch_scatter_2d : launch_scatter_3d)(Co.color_list + Co.color_ptr[g], ne, Co.Ke, nullptr,
-                                                            Co.elem_nodes, Co.elem_map, Co.n_nodes, Co.val, nullptr,
-                                                            c.stream);
-      if (ne > 0) counted(c);
-    }
+    Prof pr(c, FSI_K_SCATTER,
+            (double)Co.n_elem * nd * nd * 8.0 + (double)Co.nnzb * B * B * 8.0 + (double)Co.nnzb * 4.0 +
+                (double)Co.n_blk_src * 4.0,
+            0.0, 2);
+    launch_gather_elements(c.dim, Co.nnzb, Co.blk_ptr, Co.blk_src, Co.Ke, Co.val, 0, nullptr, nullptr, nullptr,
+                           nullptr, c.stream);
+    counted(c);
     launch_dirichlet(Co.dir_list, Co.n_dir, Co.rowptr, Co.col, Co.val, B, nullptr, nullptr, 1.0, nullptr, c.stream);
     counted(c);
   }
@@ -1320,7 +1315,8 @@ static int64_t estimate_device_bytes(const Ctx& c) {
   for (size_t l = 0; l < L; ++l) {
     const HostLevel& H = c.hl[l];
     b += (H.nb + 1) * 4.0 + H.nnzb * 4.0 + H.nnzb * B * B * 8.0 + H.n_elem * (double)nd * nd * 8.0;
-    b += H.n_elem * (H.nloc * 4.0 + 1.0 + 2.0 * H.dim * 8.0 + (H.nloc + 1.0) * (H.nloc + 1.0) * 4.0 + 4.0);
+    b += H.n_elem * (H.nloc * 4.0 + 1.0 + 2.0 * H.dim * 8.0 + 4.0);
+    b += (H.blk_ptr.size() + H.blk_src.size() + H.res_ptr.size() + H.res_src.size()) * 4.0;
     b += H.n_nodes + H.Ni * (1.0 + 8.0 + 4.0 + 4.0) + H.N * 4.0 + H.Ni * 3.0 * 8.0;
     if (l > 0) {
       b += (H.P_ptr.size() + H.R_ptr.size() + H.S_ptr.size()) * 4.0 +

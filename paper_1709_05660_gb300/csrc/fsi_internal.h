@@ -43,6 +43,12 @@ struct HostLevel {
   std::vector<int32_t> color_ptr;      // (2^dim * 2) + 1 offsets into color_list
   std::vector<int32_t> mat_list;       // elements: the fluid ones ascending, then the solid ones
   int64_t n_fluid_elem = 0;
+  // element contributions of each matrix block (nnzb + 1 offsets; entries
+  // e (nloc+1)^2 + a (nloc+1) + b for local block (a, b) of element e) and of
+  // each block row of the residual (nb + 1 offsets; entries e (nloc+1) + a),
+  // both in the order of color_list, so that summing them in list order adds
+  // the element values in the order of a coloured scatter
+  std::vector<int32_t> blk_ptr, blk_src, res_ptr, res_src;
   // grid transfers from level-1 into this level (scalar CSR, internal indices)
   std::vector<int32_t> P_ptr, P_col;   // Ni rows
   std::vector<double> P_val;
@@ -108,11 +114,10 @@ struct DevLevel {
   int64_t n_dir = 0;
   int32_t* canon_of_int = nullptr;
   int32_t* int_of_canon = nullptr;
-  int32_t* elem_map = nullptr;
-  int32_t* color_list = nullptr;
   int32_t* mat_list = nullptr;
   int64_t n_fluid_elem = 0;
-  std::vector<int32_t> color_ptr;  // host copy
+  int32_t *blk_ptr = nullptr, *blk_src = nullptr, *res_ptr = nullptr, *res_src = nullptr;
+  int64_t n_blk_src = 0, n_contrib = 0;   // entries of blk_src; of blk_src and res_src
   int32_t *P_ptr = nullptr, *P_col = nullptr, *R_ptr = nullptr, *R_col = nullptr;
   double *P_val = nullptr, *R_val = nullptr;
   int32_t *S_ptr = nullptr, *S_col = nullptr;   // unmasked state injection from level - 1

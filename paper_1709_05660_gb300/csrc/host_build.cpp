@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <numeric>
+#include <stdexcept>
 
 #include "fsi_internal.h"
 
@@ -197,6 +198,33 @@ void build_pattern(HostLevel& L) {
   for (int g = 0; g < ncol * 2; ++g) {
     for (int32_t e : groups[g]) L.color_list.push_back(e);
     L.color_ptr[g + 1] = (int32_t)L.color_list.size();
+  }
+  // gather lists of the element contributions, in colour-group order
+  if ((double)L.n_elem * nl1 * nl1 >= 2147483647.0) throw std::runtime_error("too many elements for the gather lists");
+  L.blk_ptr.assign(L.nnzb + 1, 0);
+  L.res_ptr.assign(L.nb + 1, 0);
+  for (int64_t e = 0; e < L.n_elem; ++e) {
+    for (int ab = 0; ab < nl1 * nl1; ++ab) {
+      const int32_t v = L.elem_map[e * nl1 * nl1 + ab];
+      if (v >= 0) ++L.blk_ptr[v + 1];
+    }
+    for (int a = 0; a < nloc; ++a) ++L.res_ptr[L.elem_nodes[e * nloc + a] + 1];
+    ++L.res_ptr[L.n_nodes + e + 1];
+  }
+  for (int64_t i = 0; i < L.nnzb; ++i) L.blk_ptr[i + 1] += L.blk_ptr[i];
+  for (int64_t i = 0; i < L.nb; ++i) L.res_ptr[i + 1] += L.res_ptr[i];
+  L.blk_src.assign(L.blk_ptr[L.nnzb], 0);
+  L.res_src.assign(L.res_ptr[L.nb], 0);
+  {
+    std::vector<int32_t> bp(L.blk_ptr.begin(), L.blk_ptr.end() - 1), rp(L.res_ptr.begin(), L.res_ptr.end() - 1);
+    for (int32_t e : L.color_list) {
+      for (int ab = 0; ab < nl1 * nl1; ++ab) {
+        const int32_t v = L.elem_map[(int64_t)e * nl1 * nl1 + ab];
+        if (v >= 0) L.blk_src[bp[v]++] = e * nl1 * nl1 + ab;
+      }
+      for (int a = 0; a < nloc; ++a) L.res_src[rp[L.elem_nodes[(int64_t)e * nloc + a]]++] = e * nl1 + a;
+      L.res_src[rp[L.n_nodes + e]++] = e * nl1 + nloc;
+    }
   }
   // element matrices need no colouring: fluid elements, then solid ones
   L.mat_list.clear();

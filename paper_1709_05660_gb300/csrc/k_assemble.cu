@@ -454,29 +454,6 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   Re[(int64_t)e * kNdofe + j] = vj;
 }
 
-__global__ void k_scatter_2d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ Ke,
-                             const double* __restrict__ Re, const int32_t* __restrict__ elem_nodes,
-                             const int32_t* __restrict__ elem_map, int64_t n_nodes, double* __restrict__ val,
-                             double* __restrict__ res) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t per = (int64_t)kNdofe * kNdofe;
-  if (t >= (int64_t)ne * per) return;
-  const int el = (int)(t / per);
-  const int ij = (int)(t % per);
-  const int i = ij / kNdofe, j = ij % kNdofe;
-  if (i >= kNN && j >= kNN) return;
-  const int e = elems[el];
-  const int lr = i < kNN ? i / kB : kNloc, ci = i < kNN ? i % kB : i - kNN;
-  const int lc = j < kNN ? j / kB : kNloc, cj = j < kNN ? j % kB : j - kNN;
-  const int32_t blk = elem_map[((int64_t)e * (kNloc + 1) + lr) * (kNloc + 1) + lc];
-  val[(int64_t)blk * kB * kB + ci * kB + cj] += Ke[(int64_t)e * per + ij];
-  if (res != nullptr && j == 0) {
-    const int64_t row = i < kNN ? (int64_t)elem_nodes[(int64_t)e * kNloc + lr] * kB + ci
-                                : (n_nodes + e) * kB + ci;
-    res[row] += Re[(int64_t)e * kNdofe + i];
-  }
-}
-
 // Dirichlet rows -> identity rows; residual r_i = y_i - g_i
 __global__ void k_dirichlet(const int32_t* __restrict__ dir_list, int64_t n_dir, const int32_t* __restrict__ rowptr,
                             const int32_t* __restrict__ col, double* __restrict__ val, int B,
@@ -1085,30 +1062,6 @@ k_assemble_3d(const int32_t* __restrict__ elems, const int32_t* __restrict__ ele
   if (act) Re[(int64_t)e * k3Ndofe + j] = vj;
 }
 
-// coloured scatter of 3D element matrices (B = 6)
-__global__ void k_scatter_3d(const int32_t* __restrict__ elems, int ne, const double* __restrict__ Ke,
-                             const double* __restrict__ Re, const int32_t* __restrict__ elem_nodes,
-                             const int32_t* __restrict__ elem_map, int64_t n_nodes, double* __restrict__ val,
-                             double* __restrict__ res) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t per = (int64_t)k3Ndofe * k3Ndofe;
-  if (t >= (int64_t)ne * per) return;
-  const int el = (int)(t / per);
-  const int ij = (int)(t % per);
-  const int i = ij / k3Ndofe, jj = ij % k3Ndofe;
-  if (i >= k3NN && jj >= k3NN) return;
-  const int e = elems[el];
-  const int lr = i < k3NN ? i / k3B : k3Nloc, ci = i < k3NN ? i % k3B : i - k3NN;
-  const int lc = jj < k3NN ? jj / k3B : k3Nloc, cj = jj < k3NN ? jj % k3B : jj - k3NN;
-  const int32_t blk = elem_map[((int64_t)e * (k3Nloc + 1) + lr) * (k3Nloc + 1) + lc];
-  val[(int64_t)blk * k3B * k3B + ci * k3B + cj] += Ke[(int64_t)e * per + ij];
-  if (res != nullptr && jj == 0) {
-    const int64_t row = i < k3NN ? (int64_t)elem_nodes[(int64_t)e * k3Nloc + lr] * k3B + ci
-                                 : (n_nodes + e) * k3B + ci;
-    res[row] += Re[(int64_t)e * k3Ndofe + i];
-  }
-}
-
 // Element-wise Galerkin coarsening in 3D.  Per child: T = A_c P_c is formed
 // in shared memory from the child's matrix (global, row-major), then the
 // coarse element matrix (global, accumulated over the 8 children) gets
@@ -1275,12 +1228,68 @@ bool launch_assemble_2d(bool solid, const int32_t* elems, int ne, const double* 
   return true;
 }
 
-void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
-                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st) {
-  if (ne <= 0) return;
-  const int64_t n = (int64_t)ne * kNdofe * kNdofe;
-  k_scatter_2d<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(elems, ne, Ke, Re, elem_nodes, elem_map, n_nodes, val,
-                                                            res);
+// Deterministic gather of the element matrices into the block-sparse values
+// and of the element residuals into the residual: one thread per matrix
+// entry (or residual entry) sums its element contributions in list order
+// (colour-group order, the order of a coloured scatter into zeroed arrays)
+// and writes the entry once; padding entries of the pressure blocks get 0.
+template <int NLOC, int B, int NDOFE>
+__global__ void __launch_bounds__(256) k_gather_blocks(int64_t nnzb, const int32_t* __restrict__ ptr,
+                                                       const int32_t* __restrict__ src,
+                                                       const double* __restrict__ Ke, double* __restrict__ val) {
+  constexpr int NN = NLOC * B, NP = NDOFE - NN, NL1 = NLOC + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzb * B * B) return;
+  const int64_t blk = t / (B * B);
+  const int ij = (int)(t % (B * B)), ci = ij / B, cj = ij % B;
+  double v = 0.0;
+  const int32_t q1 = ptr[blk + 1];
+  for (int32_t q = ptr[blk]; q < q1; ++q) {
+    const int32_t sq = src[q];
+    const int e = sq / (NL1 * NL1), ab = sq % (NL1 * NL1), a = ab / NL1, b = ab % NL1;
+    const int i = a < NLOC ? a * B + ci : (ci < NP ? NN + ci : -1);
+    const int j = b < NLOC ? b * B + cj : (cj < NP ? NN + cj : -1);
+    if (i >= 0 && j >= 0) v += Ke[(int64_t)e * NDOFE * NDOFE + i * NDOFE + j];
+  }
+  val[t] = v;
+}
+
+template <int NLOC, int B, int NDOFE>
+__global__ void __launch_bounds__(256) k_gather_res(int64_t nb, const int32_t* __restrict__ ptr,
+                                                    const int32_t* __restrict__ src, const double* __restrict__ Re,
+                                                    double* __restrict__ res) {
+  constexpr int NN = NLOC * B, NP = NDOFE - NN, NL1 = NLOC + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb * B) return;
+  const int64_t r = t / B;
+  const int ci = (int)(t % B);
+  double v = 0.0;
+  const int32_t q1 = ptr[r + 1];
+  for (int32_t q = ptr[r]; q < q1; ++q) {
+    const int32_t sq = src[q];
+    const int e = sq / NL1, a = sq % NL1;
+    const int i = a < NLOC ? a * B + ci : (ci < NP ? NN + ci : -1);
+    if (i >= 0) v += Re[(int64_t)e * NDOFE + i];
+  }
+  res[t] = v;
+}
+
+void launch_gather_elements(int dim, int64_t nnzb, const int32_t* blk_ptr, const int32_t* blk_src, const double* Ke,
+                            double* val, int64_t nb, const int32_t* res_ptr, const int32_t* res_src,
+                            const double* Re, double* res, cudaStream_t st) {
+  if (dim == 2) {
+    k_gather_blocks<kNloc, kB, kNdofe><<<(unsigned)((nnzb * kB * kB + 255) / 256), 256, 0, st>>>(nnzb, blk_ptr,
+                                                                                              blk_src, Ke, val);
+    if (res)
+      k_gather_res<kNloc, kB, kNdofe><<<(unsigned)((nb * kB + 255) / 256), 256, 0, st>>>(nb, res_ptr, res_src, Re,
+                                                                                        res);
+  } else {
+    k_gather_blocks<k3Nloc, k3B, k3Ndofe><<<(unsigned)((nnzb * k3B * k3B + 255) / 256), 256, 0, st>>>(
+        nnzb, blk_ptr, blk_src, Ke, val);
+    if (res)
+      k_gather_res<k3Nloc, k3B, k3Ndofe><<<(unsigned)((nb * k3B + 255) / 256), 256, 0, st>>>(nb, res_ptr, res_src,
+                                                                                            Re, res);
+  }
 }
 
 void launch_dirichlet(const int32_t* dir_list, int64_t n_dir, const int32_t* rowptr, const int32_t* col, double* val,
@@ -1343,14 +1352,6 @@ double assemble_flops_per_element(int dim, bool solid, int mode) {
 double galerkin_flops_per_coarse_element(int dim) { return dim == 2 ? 78133.0 : 3030039.0; }
 
 int assemble_launches(int dim, int ne) { return dim == 2 || ne <= 0 ? (ne > 0) : 2 * ((ne + k3Chunk - 1) / k3Chunk); }
-
-void launch_scatter_3d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
-                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st) {
-  if (ne <= 0) return;
-  const int64_t n = (int64_t)ne * k3Ndofe * k3Ndofe;
-  k_scatter_3d<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(elems, ne, Ke, Re, elem_nodes, elem_map, n_nodes, val,
-                                                            res);
-}
 
 void launch_galerkin_3d(int ncx, int ncy, int ncz, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
                         const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,

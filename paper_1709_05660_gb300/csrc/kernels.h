@@ -38,13 +38,14 @@ size_t assemble_3d_scratch_doubles(int max_ne);
 int assemble_launches(int dim, int ne);   // kernel launches of one launch_assemble_* call
 double assemble_flops_per_element(int dim, bool solid, int mode);   // executed FP64 flops (ncu count)
 double galerkin_flops_per_coarse_element(int dim);
-void launch_scatter_3d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
-                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st);
 void launch_galerkin_3d(int ncx, int ncy, int ncz, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
                         const uint8_t* f_dir, const int32_t* c_nodes, const uint8_t* c_class, const uint8_t* c_dir,
                         double* Kc, cudaStream_t st);
-void launch_scatter_2d(const int32_t* elems, int ne, const double* Ke, const double* Re, const int32_t* elem_nodes,
-                       const int32_t* elem_map, int64_t n_nodes, double* val, double* res, cudaStream_t st);
+// element matrices -> block values (every entry written) and, with res set,
+// element residuals -> residual, summed in the order of the gather lists
+void launch_gather_elements(int dim, int64_t nnzb, const int32_t* blk_ptr, const int32_t* blk_src, const double* Ke,
+                            double* val, int64_t nb, const int32_t* res_ptr, const int32_t* res_src,
+                            const double* Re, double* res, cudaStream_t st);
 void launch_dirichlet(const int32_t* dir_list, int64_t n_dir, const int32_t* rowptr, const int32_t* col, double* val,
                       int B, const double* y, const double* g, double alpha, double* res, cudaStream_t st);
 void launch_galerkin_2d(int ncx, int ncy, const double* Kf, const int32_t* f_nodes, const uint8_t* f_class,
