@@ -474,9 +474,16 @@ __global__ void k_dirichlet(const int32_t* __restrict__ dir_list, int64_t n_dir,
 // element-wise Galerkin coarsening (2D)
 // ---------------------------------------------------------------------------
 namespace {
-// weight of parent node m at the child's local node i, child side s:
-// parent reference coordinate -1 + (2 s + i) / 2
-__device__ __forceinline__ double qw(int s, int i, int m) { return L1(m, -1.0 + 0.5 * (double)(2 * s + i)); }
+// weight of parent node m at the child's local node i, child side s: the
+// 1D quadratic Lagrange basis m at the parent reference coordinate
+// -1 + (2 s + i) / 2, i.e. at -1, -1/2, 0 (s = 0) or 0, 1/2, 1 (s = 1); the
+// values are exact binary fractions, tabulated so that forming the weights
+// costs one product each and no work on the FP64 pipe beyond it
+__device__ const double kQw1[2][3][3] = {{{1.0, 0.0, 0.0}, {0.375, 0.75, -0.125}, {0.0, 1.0, 0.0}},
+                                         {{0.0, 1.0, 0.0}, {-0.125, 0.75, 0.375}, {0.0, 0.0, 1.0}}};
+// nonzero pattern of kQw1: bit (3 s + i) 3 + m
+constexpr unsigned kQwNz = (1u << 0) | (7u << 3) | (1u << 7) | (1u << 10) | (7u << 12) | (1u << 17);
+__device__ __forceinline__ bool qw_nz(int s, int i, int m) { return (kQwNz >> ((3 * s + i) * 3 + m)) & 1u; }
 __device__ __forceinline__ int row_kind(int cls, int slot) {
   if (cls == kFluid) return slot < kDim ? 2 : 0;
   return slot < kDim ? 0 : 1;
@@ -497,6 +504,9 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
   // nonzero entries of each table row (zero weights cost no FP64 work; adding
   // an exact zero would not change the sums)
   __shared__ uint8_t nP[kNN], lP[kNN][kNloc], nR[kNN], lR[kNN][2 * kNloc];
+  __shared__ uint8_t nzP[kNN * kNloc], nzR[kNN * kNloc * 2];   // the nonzero pattern of wP and wR
+  __shared__ double sQ[2][3][3];
+  if (threadIdx.x < 18) (&sQ[0][0][0])[threadIdx.x] = (&kQw1[0][0][0])[threadIdx.x];
   const int E = blockIdx.x;
   const int cx = E % ncx, cy = E / ncx;
   const int fcx = 2 * ncx;
@@ -521,14 +531,20 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
     for (int t = threadIdx.x; t < kNN * kNloc; t += blockDim.x) {
       const int J = t / kNloc, a = t % kNloc;        // J = (b, s)
       const int b = J / kB, sl = J % kB;
-      const double q = qw(sx, a % 3, b % 3) * qw(sy, a / 3, b / 3);
-      wP[t] = (c_msk[J] && f_msk[a * kB + sl]) ? q : 0.0;
+      const int ax = a % 3, ay = a / 3, bx = b % 3, by = b / 3;
+      const bool nq = qw_nz(sx, ax, bx) && qw_nz(sy, ay, by);
+      const double q = nq ? sQ[sx][ax][bx] * sQ[sy][ay][by] : 0.0;
+      const bool mp = nq && c_msk[J] && f_msk[a * kB + sl];
+      wP[t] = mp ? q : 0.0;
+      nzP[t] = mp;
       const int comp = sl % kDim;
       const int kc = row_kind(c_cls[b], sl);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int sf = h == 0 ? comp : kDim + comp;
-        wR[t * 2 + h] = (c_msk[J] && f_msk[a * kB + sf] && row_kind(f_cls[a], sf) == kc) ? q : 0.0;
+        const bool mr = nq && c_msk[J] && f_msk[a * kB + sf] && row_kind(f_cls[a], sf) == kc;
+        wR[t * 2 + h] = mr ? q : 0.0;
+        nzR[t * 2 + h] = mr;
       }
     }
     __syncthreads();
@@ -536,9 +552,9 @@ k_galerkin_2d(int ncx, int ncy, const double* __restrict__ Kf, const int32_t* __
       const int J = threadIdx.x;
       int np = 0, nq = 0;
       for (int a = 0; a < kNloc; ++a) {
-        if (wP[J * kNloc + a] != 0.0) lP[J][np++] = (uint8_t)a;
+        if (nzP[J * kNloc + a]) lP[J][np++] = (uint8_t)a;
         for (int h = 0; h < 2; ++h)
-          if (wR[(J * kNloc + a) * 2 + h] != 0.0) lR[J][nq++] = (uint8_t)(2 * a + h);
+          if (nzR[(J * kNloc + a) * 2 + h]) lR[J][nq++] = (uint8_t)(2 * a + h);
       }
       nP[J] = (uint8_t)np;
       nR[J] = (uint8_t)nq;
@@ -1089,10 +1105,7 @@ k_galerkin_3d(int ncx, int ncy, int ncz, const double* __restrict__ Kf, const in
   (void)ncz;
   double* C = Kc + (int64_t)E * k3Ndofe * k3Ndofe;
   for (int t = threadIdx.x; t < k3Ndofe * k3Ndofe; t += blockDim.x) C[t] = 0.0;
-  if (threadIdx.x < 18) {
-    const int sd = threadIdx.x / 9, i = (threadIdx.x / 3) % 3, m = threadIdx.x % 3;
-    w1[sd][i][m] = qw(sd, i, m);
-  }
+  if (threadIdx.x < 18) (&w1[0][0][0])[threadIdx.x] = (&kQw1[0][0][0])[threadIdx.x];
   if (threadIdx.x < k3Nloc) c_cls[threadIdx.x] = c_class[c_nodes[(int64_t)E * k3Nloc + threadIdx.x]];
   if (threadIdx.x < k3NN) {
     const int a = threadIdx.x / k3B, s = threadIdx.x % k3B;

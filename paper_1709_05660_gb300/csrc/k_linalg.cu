@@ -155,10 +155,12 @@ __device__ __forceinline__ void load_x4(const TX* p, TY (&x)[4]) {
   }
 }
 
-// 8 blocks of 256 threads per SM (32 registers a thread): full occupancy, as the
-// finest levels' residual is bound by the loads in flight
+// FP32: 8 blocks of 256 threads per SM (32 registers a thread): full
+// occupancy, as the finest levels' residual is bound by the loads in flight.
+// FP64: 4 blocks (64 registers), so that a thread's four blocks of values and
+// x entries (64 registers of doubles) are loaded together
 template <int SUB, typename TV, typename TX, typename TY>
-__global__ void __launch_bounds__(256, 8) k_bsr4_residual_sub(int64_t nb, const int32_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(256, sizeof(TV) == 8 ? 4 : 8) k_bsr4_residual_sub(int64_t nb, const int32_t* __restrict__ rowptr,
                                                           const int32_t* __restrict__ col, const TV* __restrict__ val,
                                                           const TX* __restrict__ x, const TY* __restrict__ b,
                                                           TY* __restrict__ y) {
