@@ -544,8 +544,9 @@ void launch_dense_gather(int B, int64_t nb, const int32_t* rowptr, const int32_t
 // y[r] += a x[r] for r = base + lane, base + lane + 32, ... <= rhi (a warp-wide
 // update in shared memory): whole rounds of 128 rows (four per lane, all loads
 // issued before the stores: x and y are different columns, which the compiler
-// cannot prove), then the rest row by row.  The round count is warp-uniform, so
-// a short range (a narrow band) takes the plain loop only.
+// cannot prove), then the last partial round the same way with the rows past
+// rhi masked, so a short range (a narrow band) costs one round trip, not one
+// per 32 rows.
 __device__ __forceinline__ void axpy_rows(double* y, const double* x, double a, int base, int rhi) {
   int r = base + threadIdx.x % kWarp;
   const int rounds = (rhi - base + 1) / (4 * kWarp);
@@ -557,7 +558,16 @@ __device__ __forceinline__ void axpy_rows(double* y, const double* x, double a, 
     y[r + 2 * kWarp] = fma(a, x2, y2);
     y[r + 3 * kWarp] = fma(a, x3, y3);
   }
-  for (; r <= rhi; r += kWarp) y[r] = fma(a, x[r], y[r]);
+  double xv[4], yv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int rk = r + k * kWarp;
+    xv[k] = rk <= rhi ? x[rk] : 0.0;
+    yv[k] = rk <= rhi ? y[rk] : 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (r + k * kWarp <= rhi) y[r + k * kWarp] = fma(a, xv[k], yv[k]);
 }
 
 // the same with x a column of the factor in global memory (y in shared memory)
@@ -574,6 +584,26 @@ __device__ __forceinline__ void axpy_rows_g(double* y, const double* __restrict_
     y[r + 3 * kWarp] = fma(a, x3, y3);
   }
   for (; r <= rhi; r += kWarp) y[r] = fma(a, __ldg(x + r), y[r]);
+}
+
+// panel columns k0 .. k0 + nb - 1, rows k0 .. k0 + nr - 1 of M into P (R rows
+// a column): four loads in flight per thread
+__device__ __forceinline__ void load_panel(double* P, int R, const double* __restrict__ M, int64_t n, int64_t k0,
+                                           int nb, int nr) {
+  const int tot = nb * nr, step = blockDim.x;
+  for (int t0 = threadIdx.x; t0 < tot; t0 += 4 * step) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * step, j = t / nr, r = t - j * nr;
+      v[u] = t < tot ? M[(k0 + j) * n + k0 + r] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * step, j = t / nr, r = t - j * nr;
+      if (t < tot) P[j * R + r] = v[u];
+    }
+  }
 }
 
 template <int NB>
@@ -597,8 +627,7 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
     const int nb = (int)min((int64_t)NB, n - k0);
     const int nr = (int)(min(n, k0 + nb + kl) - k0);
     if (blockIdx.x == 0) {
-      for (int j = 0; j < nb; ++j)
-        for (int r = threadIdx.x; r < nr; r += blockDim.x) P[j * R + r] = M[(k0 + j) * n + k0 + r];
+      load_panel(P, R, M, n, k0, nb, nr);
       __syncthreads();
       for (int j = 0; j < nb; ++j) {
         const int rhi = min(j + kl, nr - 1);
@@ -636,16 +665,17 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
         if (threadIdx.x == 0) s_piv[j] = pr;
         __syncthreads();
       }
-      for (int j = 0; j < nb; ++j)
-        for (int r = threadIdx.x; r < nr; r += blockDim.x) M[(k0 + j) * n + k0 + r] = P[j * R + r];
+      for (int t = threadIdx.x; t < nb * nr; t += blockDim.x) {
+        const int j = t / nr, r = t - j * nr;
+        M[(k0 + j) * n + k0 + r] = P[j * R + r];
+      }
       for (int j = threadIdx.x; j < nb; j += blockDim.x) piv[k0 + j] = (int32_t)(k0 + s_piv[j]);
     }
     grid.sync();
     const int64_t c_lo = k0 + nb, c_hi = min(n - 1, k0 + nb - 1 + wmax);
     if (c_lo <= c_hi) {
       // stage multipliers and pivots (every block)
-      for (int j = 0; j < nb; ++j)
-        for (int r = threadIdx.x; r < nr; r += blockDim.x) P[j * R + r] = M[(k0 + j) * n + k0 + r];
+      load_panel(P, R, M, n, k0, nb, nr);
       for (int j = threadIdx.x; j < nb; j += blockDim.x) s_piv[j] = (int)(piv[k0 + j] - k0);
       __syncthreads();
       double* Sw = S + (size_t)wid * R;
