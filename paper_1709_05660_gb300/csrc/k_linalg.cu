@@ -43,24 +43,36 @@ __device__ double block_sum(double v, double* scratch) {
   return s;
 }
 
-// block-wide argmax of |v| (ties: lowest index); every thread gets the index
-__device__ int block_argmax(double v, int idx, double* sv, int* si) {
+// Block-wide argmax of |a| (largest wins, ties to the lower index; threads
+// without a candidate pass idx = -1) on integer keys: the bit pattern of a
+// non-negative double orders like its value, so |a| compared as a 64-bit
+// integer (NaN mapped to 0) picks the row a floating-point comparison would,
+// while keeping the comparisons off the FP64 pipe, which on GB300 retires two
+// operations per SM and cycle.
+__device__ __forceinline__ unsigned long long abs_key(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+  return b > 0x7FF0000000000000ull ? 0ull : b;   // NaN -> 0; +inf stays the largest
+}
+__device__ __forceinline__ bool key_wins(unsigned long long ok, int oi, unsigned long long k, int i) {
+  return (oi >= 0 && i < 0) || (oi >= 0 && (ok > k || (ok == k && oi < i)));
+}
+__device__ int block_argmax_key(unsigned long long v, int idx, unsigned long long* sv, int* si) {
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_down_sync(0xffffffffu, v, o);
+    const unsigned long long ov = __shfl_down_sync(0xffffffffu, v, o);
     const int oi = __shfl_down_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi < idx && oi >= 0) || (idx < 0 && oi >= 0)) { v = ov; idx = oi; }
+    if (key_wins(ov, oi, v, idx)) { v = ov; idx = oi; }
   }
   __syncthreads();
   if (lane == 0) { sv[wid] = v; si[wid] = idx; }
   __syncthreads();
   if (threadIdx.x == 0) {
     const int nw = (blockDim.x + kWarp - 1) / kWarp;
-    double bv = sv[0];
+    unsigned long long bv = sv[0];
     int bi = si[0];
     for (int w = 1; w < nw; ++w)
-      if (sv[w] > bv || (sv[w] == bv && si[w] >= 0 && (bi < 0 || si[w] < bi)) || (bi < 0 && si[w] >= 0)) {
+      if (key_wins(sv[w], si[w], bv, bi)) {
         bv = sv[w];
         bi = si[w];
       }
@@ -616,7 +628,7 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
   double* P = reinterpret_cast<double*>(smem_raw);        // R x NB, column-major
   double* S = P + (size_t)R * NB;                         // per warp: R entries of one trailing column
   __shared__ int s_piv[NB];
-  __shared__ double sv[32];
+  __shared__ unsigned long long skey[32];
   __shared__ int si[32];
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
   // the trailing update of phase B uses col_warps warps per block (one
@@ -631,14 +643,13 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
       __syncthreads();
       for (int j = 0; j < nb; ++j) {
         const int rhi = min(j + kl, nr - 1);
-        double best = -1.0;
+        unsigned long long best = 0ull;
         int bi = -1;
         for (int r = j + threadIdx.x; r <= rhi; r += blockDim.x) {
-          double a = fabs(P[j * R + r]);
-          if (!(a >= 0.0)) a = 0.0;
-          if (a > best) { best = a; bi = r; }
+          const unsigned long long a = abs_key(P[j * R + r]);
+          if (bi < 0 || a > best) { best = a; bi = r; }
         }
-        int pr = block_argmax(best, bi, sv, si);
+        int pr = block_argmax_key(best, bi, skey, si);
         if (pr < 0) pr = j;
         if (pr != j)
           for (int c = j + threadIdx.x; c < nb; c += blockDim.x) {
