@@ -49,6 +49,10 @@ __device__ double block_sum(double v, double* scratch) {
 // integer (NaN mapped to 0) picks the row a floating-point comparison would,
 // while keeping the comparisons off the FP64 pipe, which on GB300 retires two
 // operations per SM and cycle.
+// a != 0.0 (either sign of zero fails) as an integer test, off the FP64 pipe
+__device__ __forceinline__ bool nonzero(double a) {
+  return ((unsigned long long)__double_as_longlong(a) << 1) != 0ull;
+}
 __device__ __forceinline__ unsigned long long abs_key(double a) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
   return b > 0x7FF0000000000000ull ? 0ull : b;   // NaN -> 0; +inf stays the largest
@@ -630,6 +634,7 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
   __shared__ int s_piv[NB];
   __shared__ unsigned long long skey[32];
   __shared__ int si[32];
+  __shared__ double s_rp;
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp, nw = blockDim.x / kWarp;
   // the trailing update of phase B uses col_warps warps per block (one
   // shared-memory column buffer each); all warps work in phase A
@@ -657,21 +662,27 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
             P[c * R + j] = P[c * R + pr];
             P[c * R + pr] = t0;
           }
-        __syncthreads();
-        double pv = P[j * R + j];
-        if (!(fabs(pv) > 0.0) || !isfinite(pv)) {
-          if (threadIdx.x == 0) atomicExch(&status[ST_SINGULAR], 1);
-          pv = 1.0;
+        // the reciprocal pivot by one thread (it swapped column j itself):
+        // a division on every thread would occupy each SM sub-partition's
+        // FP64 pipe for the whole warp
+        if (threadIdx.x == 0) {
+          double pv = P[j * R + j];
+          if (!(fabs(pv) > 0.0) || !isfinite(pv)) {
+            atomicExch(&status[ST_SINGULAR], 1);
+            pv = 1.0;
+          }
+          s_rp = 1.0 / pv;
+          rdiag[k0 + j] = s_rp;
         }
-        const double rp = 1.0 / pv;
-        if (threadIdx.x == 0) rdiag[k0 + j] = rp;
+        __syncthreads();
+        const double rp = s_rp;
         for (int r = j + 1 + threadIdx.x; r <= rhi; r += blockDim.x) P[j * R + r] *= rp;
         __syncthreads();
         // rank-1 update of the panel's columns right of j: a warp per column,
         // lanes over rows (the column's multiplier is warp-uniform)
         for (int c = j + 1 + wid; c < nb; c += nw) {
           const double pc = P[c * R + j];
-          if (pc != 0.0) axpy_rows(P + c * R, P + j * R, -pc, j + 1, rhi);
+          if (nonzero(pc)) axpy_rows(P + c * R, P + j * R, -pc, j + 1, rhi);
         }
         if (threadIdx.x == 0) s_piv[j] = pr;
         __syncthreads();
@@ -704,7 +715,7 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
           }
           __syncwarp();
           const double t = Sw[j];
-          if (t != 0.0) axpy_rows(Sw, P + j * R, -t, j + 1, min(j + kl, nr - 1));
+          if (nonzero(t)) axpy_rows(Sw, P + j * R, -t, j + 1, min(j + kl, nr - 1));
           __syncwarp();
         }
         for (int r = lane; r < nr; r += kWarp) Mc[r] = Sw[r];
@@ -759,7 +770,7 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
       __syncwarp();
     }
     const double xk = x[k];
-    if (xk != 0.0) {
+    if (nonzero(xk)) {
 #pragma unroll
       for (int m = 0; m < MR; ++m) {
         if (32 * m >= kl) break;   // warp-uniform: no issue slots for rows beyond the band
@@ -787,10 +798,15 @@ __global__ void __launch_bounds__(128) k_band_inv_pf(int64_t n, int kl, int ku, 
   load_u(n - 1, cur, dcur);
   for (int64_t k = n - 1; k >= 0; --k) {
     load_u(k - 1, nxt, dnxt);
-    const double xk = x[k] * dcur;   // reciprocal pivot: no FP64 division on the critical chain
-    __syncwarp();
-    if (lane == 0) x[k] = xk;
-    if (xk != 0.0) {
+    // reciprocal pivot (no FP64 division on the critical chain), formed by
+    // lane 0 and broadcast, so the warp spends one lane's FP64 multiply on it
+    double xk = 0.0;
+    if (lane == 0) {
+      xk = x[k] * dcur;
+      x[k] = xk;
+    }
+    xk = __shfl_sync(0xffffffffu, xk, 0);
+    if (nonzero(xk)) {
 #pragma unroll
       for (int m = 0; m < MR; ++m) {
         if (32 * m >= w) break;
@@ -830,7 +846,7 @@ __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, con
       __syncwarp();
     }
     const double xk = x[k];
-    if (xk != 0.0) {
+    if (nonzero(xk)) {
       const int64_t r_hi = min(n - 1, k + (int64_t)kl);
       axpy_rows_g(x + k, M + k * n + k, -xk, 1, (int)(r_hi - k));
     }
@@ -842,7 +858,7 @@ __global__ void __launch_bounds__(128) k_band_inv(int64_t n, int kl, int ku, con
     if (lane == 0) x[k] *= rdiag[k];
     __syncwarp();
     const double xk = x[k];
-    if (xk != 0.0) {
+    if (nonzero(xk)) {
       const int64_t r_lo = max((int64_t)0, k - w);
       axpy_rows_g(x + r_lo, Uk + r_lo, -xk, 0, (int)(k - 1 - r_lo));
     }
