@@ -124,6 +124,8 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   __shared__ double s_yo[kEPB][kNdofe];
   __shared__ double s_geo[kEPB][2 * kDim];
   __shared__ unsigned s_iface[kEPB];
+  __shared__ double s_scl[kEPB][3];   // 2 / hx, 2 / hy, 1 / (hx hy): divided once per element
+  __shared__ double s_wq[kEPB][kQ];    // quadrature weights times the Jacobian of the element map
   __shared__ double s_N[kQ][kNloc], s_Dx[kQ][kNloc], s_Dy[kQ][kNloc];   // reference basis at the points
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int le = threadIdx.x / kNdofe;
@@ -155,6 +157,14 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
       for (int a = 0; a < kNloc; ++a)
         if (node_class[elem_nodes[(int64_t)e * kNloc + a]] == kIface) m |= 1u << a;
       s_iface[le] = m;
+      const double ghx = elem_geo[(int64_t)e * 2 * kDim + 2], ghy = elem_geo[(int64_t)e * 2 * kDim + 3];
+      s_scl[le][0] = 2.0 / ghx;
+      s_scl[le][1] = 2.0 / ghy;
+      s_scl[le][2] = 1.0 / (ghx * ghy);
+    }
+    if (j < kQ) {
+      const double vol_e = elem_geo[(int64_t)e * 2 * kDim + 2] * elem_geo[(int64_t)e * 2 * kDim + 3];
+      s_wq[le][j] = gw(j % 3) * gw(j / 3) * vol_e * 0.25;
     }
   }
   __syncthreads();
@@ -165,9 +175,9 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
   const double* ye = s_y[le_c];
   const double* yo = s_yo[le_c];
   const double hx = s_geo[le_c][2], hy = s_geo[le_c][3];
-  const double sx = 2.0 / hx, sy = 2.0 / hy;
+  const double sx = s_scl[le_c][0], sy = s_scl[le_c][1];
   const double vol = hx * hy;
-  const double kale = 1.0 / vol;
+  const double kale = s_scl[le_c][2];
 
   // 1. field values at the points
   if (active) {
@@ -214,7 +224,7 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         for (int o = 0; o < kNO; ++o) dout[o] = 0.0;
         continue;
       }
-      const double wq = gw(q % 3) * gw(q / 3) * vol * 0.25;
+      const double wq = s_wq[le_c][q];
       Dual gd[2][2], gu[2][2], u[2], ut[2], dt_[2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
@@ -1354,7 +1364,7 @@ bool launch_assemble_3d(bool solid, const int32_t* elems, int ne, const double* 
 // 1 BDF, 2 Crank-Nicolson; Mooney-Rivlin adds a few percent in the solid);
 // used for the FP64-ALU fraction of the assembly in the per-class timings.
 double assemble_flops_per_element(int dim, bool solid, int mode) {
-  static const double f2[2][3] = {{115524.0, 123226.0, 157692.0}, {87338.0, 94222.0, 106269.0}};
+  static const double f2[2][3] = {{113705.0, 121355.0, 155816.0}, {85909.0, 92740.0, 104785.0}};
   // 3D: flux derivatives + columns
   static const double f3[2][3] = {{437386.0 + 5908383.0, 539270.0 + 5908383.0, 1057103.0 + 5908383.0},
                                   {242394.0 + 4286875.0, 313563.0 + 4286875.0, 502750.0 + 4286875.0}};
