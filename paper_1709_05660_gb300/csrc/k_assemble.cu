@@ -37,6 +37,12 @@ __device__ __forceinline__ Dual operator/(Dual a, Dual b) {
   const double q = a.v * inv;
   return {q, (a.d - b.d * q) * inv};
 }
+// a / b given inv = 1 / b.v (the same arithmetic as operator/, with the one
+// reciprocal shared by several quotients of the same divisor)
+__device__ __forceinline__ Dual div_inv(Dual a, Dual b, double inv) {
+  const double q = a.v * inv;
+  return {q, (a.d - b.d * q) * inv};
+}
 
 // 1D quadratic Lagrange basis (nodes -1, 0, 1) and derivative at the three
 // Gauss points -sqrt(3/5), 0, sqrt(3/5).
@@ -247,8 +253,9 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
       const Dual J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
       if (!(J.v > 0.0)) tangled = true;
       Dual Fi[2][2];
-      Fi[0][0] = F[1][1] / J; Fi[0][1] = -F[0][1] / J;
-      Fi[1][0] = -F[1][0] / J; Fi[1][1] = F[0][0] / J;
+      const double iJ = 1.0 / J.v;
+      Fi[0][0] = div_inv(F[1][1], J, iJ); Fi[0][1] = div_inv(-F[0][1], J, iJ);
+      Fi[1][0] = div_inv(-F[1][0], J, iJ); Fi[1][1] = div_inv(F[0][0], J, iJ);
       Dual out[kNO];
       if (CN) {
         // Crank-Nicolson (Sec. 2.5): stresses and convection averaged over
@@ -268,8 +275,9 @@ k_assemble_2d(const int32_t* __restrict__ elems, int ne, const double* __restric
         }
         const Dual Jn = Fn[0][0] * Fn[1][1] - Fn[0][1] * Fn[1][0];
         if (!(Jn.v > 0.0)) tangled = true;
-        Fin[0][0] = Fn[1][1] / Jn; Fin[0][1] = -Fn[0][1] / Jn;
-        Fin[1][0] = -Fn[1][0] / Jn; Fin[1][1] = Fn[0][0] / Jn;
+        const double iJn = 1.0 / Jn.v;
+        Fin[0][0] = div_inv(Fn[1][1], Jn, iJn); Fin[0][1] = div_inv(-Fn[0][1], Jn, iJn);
+        Fin[1][0] = div_inv(-Fn[1][0], Jn, iJn); Fin[1][1] = div_inv(Fn[0][0], Jn, iJn);
         const Dual pn = mk(fv[25], 0.0);
         if (SOLID) {
           Dual P1[2][2], Pn[2][2];
