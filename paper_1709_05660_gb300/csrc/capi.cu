@@ -630,11 +630,34 @@ bool gather_mixed(Ctx& c, GjLevels& lv, int& first, int& max_n) {
   float* ws = reinterpret_cast<float*>(c.dense_ws);
   int64_t off = 0;
   bool ok = true;
+  // the gathers of all levels in one launch when the table holds them
+  GatherLevels gl{};
+  gl.B = c.B;
+  int gblocks = 0;
+  const bool one_launch = L - 1 <= kGjMaxLevels;
   for (int l = 1; l < L; ++l) {
     DevLevel& D = c.dl[l];
-    launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off, D.p_boff,
-                                 D.p_pad_off, D.p_padpos, D.val, c.B, ws + off, D.p_idx_off, D.dr32, D.dc32, c.stream);
+    if (one_launch) {
+      if (D.n_patches > 0)
+        gl.l[gl.nlev++] = GatherLevel{D.p_n,    D.p_dense_off, D.p_gmap_off, D.p_gmap,      D.p_boff_off,
+                                      D.p_boff, D.p_pad_off,   D.p_padpos,   D.val,         ws + off,
+                                      D.p_idx_off, D.dr32,     D.dc32,       gblocks};
+      gblocks += D.n_patches;
+    } else {
+      launch_patch_gather_t<float>(D.n_patches, D.p_n, D.p_dense_off, D.p_gmap_off, D.p_gmap, D.p_boff_off,
+                                   D.p_boff, D.p_pad_off, D.p_padpos, D.val, c.B, ws + off, D.p_idx_off, D.dr32,
+                                   D.dc32, c.stream);
+      counted(c);
+    }
+    off += D.dense_total;
+  }
+  if (one_launch && gblocks > 0) {
+    launch_patch_gather_levels(gl, gblocks, c.stream);
     counted(c);
+  }
+  off = 0;
+  for (int l = 1; l < L; ++l) {
+    DevLevel& D = c.dl[l];
     const bool ilu = c.opts.local_solver == 1;
     const int nsel = ilu ? D.n_lu : D.n_patches;
     if (ilu) {   // the fluid blocks: ILU(0) in place in the workspace
@@ -685,7 +708,9 @@ void schwarz_factor(Ctx& c) {
       by += D.factor_bytes;
       fl += D.factor_flops;
     }
-    Prof pr(c, FSI_K_PATCH_FACTOR, by, fl, L);
+    // launches: one gather for all levels (one per level past the table's
+    // capacity) and the tensor-core factorisation
+    Prof pr(c, FSI_K_PATCH_FACTOR, by, fl, (L - 1 <= kGjMaxLevels ? 1 : L - 1) + 1);
     const bool all = gather_mixed(c, lv, first, max_n);
     if (all && (lv.nlev == 0 || launch_patch_gj_tc_levels(lv, first, max_n, c.status, c.stream, c.gj_panel))) {
       if (lv.nlev > 0) counted(c);

@@ -82,13 +82,14 @@ __device__ __forceinline__ bool gather_pos(const int32_t* __restrict__ gmap, con
 }
 
 template <typename T>
-__global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t* __restrict__ dense_off,
-                                 const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
-                                 const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff,
-                                 const int64_t* __restrict__ pad_off, const int32_t* __restrict__ padpos,
-                                 const double* __restrict__ bsr_val, int B, T* __restrict__ dense,
-                                 const int64_t* __restrict__ idx_off, T* __restrict__ dr, T* __restrict__ dc) {
-  const int p = blockIdx.x;
+__device__ __forceinline__ void gather_block(int p, const int32_t* __restrict__ p_n,
+                                             const int64_t* __restrict__ dense_off,
+                                             const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
+                                             const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff,
+                                             const int64_t* __restrict__ pad_off, const int32_t* __restrict__ padpos,
+                                             const double* __restrict__ bsr_val, int B, T* __restrict__ dense,
+                                             const int64_t* __restrict__ idx_off, T* __restrict__ dr,
+                                             T* __restrict__ dc) {
   const int n = p_n[p];
   T* D = dense + dense_off[p];
   const int32_t* bo = boff + boff_off[p];
@@ -1189,6 +1190,36 @@ k_patch_apply_t(const int32_t* __restrict__ p_n, const int32_t* __restrict__ p_n
     __syncthreads();
   }
 }
+
+// one Schwarz block per thread block (the level's own launch)
+template <typename T>
+__global__ void k_patch_gather_t(const int32_t* __restrict__ p_n, const int64_t* __restrict__ dense_off,
+                                 const int64_t* __restrict__ gmap_off, const int32_t* __restrict__ gmap,
+                                 const int64_t* __restrict__ boff_off, const int32_t* __restrict__ boff,
+                                 const int64_t* __restrict__ pad_off, const int32_t* __restrict__ padpos,
+                                 const double* __restrict__ bsr_val, int B, T* __restrict__ dense,
+                                 const int64_t* __restrict__ idx_off, T* __restrict__ dr, T* __restrict__ dc) {
+  gather_block<T>(blockIdx.x, p_n, dense_off, gmap_off, gmap, boff_off, boff, pad_off, padpos, bsr_val, B, dense,
+                  idx_off, dr, dc);
+}
+
+// the FP32 gathers of several levels in one launch (thread block i gathers
+// block i - first of the level whose range holds i), so that the coarse
+// levels' few blocks run beside the finest level's instead of each paying a
+// launch of their own
+__global__ void __launch_bounds__(512) k_patch_gather_levels(const GatherLevels lv) {
+  int l = 0;
+  while (l + 1 < lv.nlev && (int)blockIdx.x >= lv.l[l + 1].first) ++l;
+  const GatherLevel& G = lv.l[l];
+  gather_block<float>((int)blockIdx.x - G.first, G.p_n, G.dense_off, G.gmap_off, G.gmap, G.boff_off, G.boff,
+                      G.pad_off, G.padpos, G.bsr_val, lv.B, G.dense, G.idx_off, G.dr, G.dc);
+}
+
+void launch_patch_gather_levels(const GatherLevels& lv, int nblocks, cudaStream_t st) {
+  if (nblocks <= 0 || lv.nlev < 1) return;
+  k_patch_gather_levels<<<nblocks, 512, 0, st>>>(lv);
+}
+
 
 // ---------------------------------------------------------------------------
 template <typename T>

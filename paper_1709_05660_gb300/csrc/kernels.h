@@ -109,6 +109,28 @@ bool launch_patch_gj_tc_levels(const GjLevels& lv, int nblocks, int max_n, int32
 // panel width of the tensor-core variant that launch_patch_gj_tc_levels picks
 // for blocks up to max_n with preference `panel` (0: none fits)
 int gj_tc_variant(int max_n, int panel);
+// the FP32 gathers of the Schwarz levels of one instance in one launch
+struct GatherLevel {
+  const int32_t* p_n;
+  const int64_t* dense_off;
+  const int64_t* gmap_off;
+  const int32_t* gmap;
+  const int64_t* boff_off;
+  const int32_t* boff;
+  const int64_t* pad_off;
+  const int32_t* padpos;
+  const double* bsr_val;
+  float* dense;
+  const int64_t* idx_off;
+  float* dr;
+  float* dc;
+  int first;   // first thread block of the level
+};
+struct GatherLevels {
+  int nlev, B;
+  GatherLevel l[kGjMaxLevels];
+};
+void launch_patch_gather_levels(const GatherLevels& lv, int nblocks, cudaStream_t st);
 // boff / boff_off: per local block of a Schwarz block its dense offset * 8 + width
 template <typename T>
 void launch_patch_gather_t(int np, const int32_t* p_n, const int64_t* dense_off, const int64_t* gmap_off,
