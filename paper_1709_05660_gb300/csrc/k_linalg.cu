@@ -704,7 +704,14 @@ __global__ void __launch_bounds__(512) k_band_lu_blk(int64_t n, int kl, int ku, 
       for (int64_t c = c_lo + (int64_t)blockIdx.x * nwb + wid; wid < nwb && c <= c_hi;
            c += (int64_t)gridDim.x * nwb) {
         double* Mc = M + c * n + k0;
-        for (int r = lane; r < nr; r += kWarp) Sw[r] = Mc[r];
+        for (int r0 = lane; r0 < nr; r0 += 4 * kWarp) {   // four loads in flight per lane
+          double v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = r0 + u * kWarp < nr ? Mc[r0 + u * kWarp] : 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (r0 + u * kWarp < nr) Sw[r0 + u * kWarp] = v[u];
+        }
         __syncwarp();
         for (int j = 0; j < nb; ++j) {
           const int pr = s_piv[j];
